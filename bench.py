@@ -1,0 +1,409 @@
+#!/usr/bin/env python
+"""Benchmark: Parareal solves/s at 1e-6 relative error against the serial fine
+solution, on one B300 (or N independent replicas).
+
+Workload (the PINN-coarse Parareal configuration): European call, K=1,
+sigma=0.2, r=0.05, T=1, S in [0, 4] on Nx=1024 points, P=32 slices,
+Crank-Nicolson 1024 steps per slice (FP64); coarse propagator = tanh MLP
+2->4x64->1 in (S, tau), Xavier init from seed 0, trained 5000 full-batch Adam
+steps (lr 1e-3, FP32) on 16384 uniform interior + 1024 boundary/expiry points.
+
+A timed step is one complete Parareal solve through the C ABI: network table
+on the grid (one pinn_eval), initial iterate, then fine propagation + fused
+correction + increment norm per iteration until the stop rule.  The stop
+tolerance is the largest of 1e-6, 3e-7, 1e-7, ... whose result is within 1e-6
+of serial fine (checked before timing and after).  Inputs are resident in HBM;
+L2 (126 MB) is flushed with a 256 MB write between timed steps, outside the
+events.  Also reported: implicit-Euler-coarse Parareal and serial fine on the
+same grid, a training step, the fine kernel's roofline, the end-to-end rate
+with host buffers, and the oracle on the host cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+CFG = dict(K=1.0, sigma=0.2, r=0.05, T=1.0, Smax=4.0, Nx=1024, P=32, fine_steps=1024, coarse_steps=1)
+WIDTHS = [2, 64, 64, 64, 64, 1]
+N_INTERIOR, N_BOUNDARY, N_EXPIRY = 16384, 512, 512
+TARGET = 1e-6
+METRIC = "Parareal solves/s at 1e-6 vs serial fine"
+WORKLOAD = ("PINN-coarse Parareal, BS call K=1 sigma=0.2 r=0.05 T=1, Nx=1024 S in [0,4], P=32, "
+            "CN 1024 steps/slice FP64, MLP 2->4x64 tanh trained 5k Adam steps on 16384+1024 points")
+FLOPS_PER_PT_STEP = 11.0  # CN right-hand side 5 + factored solve 6 (algorithmic, per interior point-step)
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    import torch
+
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def allreduce_max(ws, v: float) -> float:
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rel_error(U, Uref, P, Nx):
+    """max over slices n = 1..P of ||U_n - Uref_n||_2 / ||Uref_n||_2 (harness measurement)."""
+    a = U.view(P + 1, Nx)[1:]
+    b = Uref.view(P + 1, Nx)[1:]
+    return float(((a - b).norm(dim=1) / b.norm(dim=1)).max().item())
+
+
+def train_network(B, torch, steps, seed=0):
+    from paper_2303_03848_b300 import synth
+
+    X, kind = synth.collocation(seed, N_INTERIOR, N_BOUNDARY, N_EXPIRY, CFG["Smax"], CFG["T"])
+    Xd = torch.tensor(X, device="cuda")
+    kd = torch.tensor(kind, device="cuda")
+    m = B.PinnModel(WIDTHS, [0.0, 0.0], [CFG["Smax"], CFG["T"]], seed=seed)
+    loss0 = m.train_step(Xd, kd, CFG, lr=1e-3, prec=B.FP32, want_loss=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    timed = min(200, max(steps - 1, 1))
+    for i in range(1, steps):
+        if i == steps - timed:
+            e0.record()
+        m.train_step(Xd, kd, CFG, lr=1e-3, prec=B.FP32)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / timed if steps > 1 else float("nan")
+    loss1 = m.train_step(Xd, kd, CFG, lr=1e-3, prec=B.FP32, want_loss=True)
+    return m, dict(steps=steps, ms_per_step=ms, points=len(kind), loss_first=loss0, loss_last=loss1,
+                   points_per_s=len(kind) / (ms * 1e-3) if ms == ms else None)
+
+
+def choose_tol(prob, kind, model, prec, Uf, B):
+    for tol in (1e-6, 3e-7, 1e-7, 3e-8, 1e-8, 3e-9, 1e-9, 1e-10, 1e-11, 0.0):
+        U, norms, stats, rc = prob.parareal_solve(kind, model=model, prec=prec, tol=tol)
+        err = rel_error(U, Uf, CFG["P"], CFG["Nx"])
+        if err <= TARGET:
+            return tol, stats[0]["iterations"], err
+    return 0.0, CFG["P"], err
+
+
+def time_solves(prob, kind, model, prec, tol, steps, warmup, torch, flush):
+    for _ in range(warmup):
+        prob.parareal_solve(kind, model=model, prec=prec, tol=tol, want_stats=False)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    U = None
+    for i in range(steps):
+        flush.add_(1.0)  # 256 MB write: evicts L2 between timed steps
+        evs[i][0].record()
+        U, *_ = prob.parareal_solve(kind, model=model, prec=prec, tol=tol, want_stats=False)
+        evs[i][1].record()
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in evs]
+    return ms, U
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2303_03848_b300 import binding as B
+    from paper_2303_03848_b300 import build as BUILD
+
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    BUILD.build()
+    prec = B.PREC[args.prec]
+    peaks = _peaks()
+
+    t0 = time.perf_counter()
+    prob = B.Problem(CFG)
+    setup_ms = (time.perf_counter() - t0) * 1e3
+    model, train = train_network(B, torch, args.train_steps)
+    Uf = prob.serial_fine()
+    torch.cuda.synchronize()
+
+    tol, iters, err = choose_tol(prob, B.COARSE_PINN, model, prec, Uf, B)
+    flush = torch.zeros(32 * 1024 * 1024, dtype=torch.float64, device="cuda")
+    barrier(ws)
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        w0 = time.perf_counter()
+        ms, U = time_solves(prob, B.COARSE_PINN, model, prec, tol, args.steps, args.warmup, torch, flush)
+        wall = time.perf_counter() - w0
+    barrier(ws)
+    err_after = rel_error(U, Uf, CFG["P"], CFG["Nx"])
+    ms_step = allreduce_max(ws, sum(ms) / len(ms))
+    value = ws * 1e3 / ms_step
+
+    # fine kernel alone: iteration-0 launch shape (all P slices), CUDA events on the current stream
+    U0 = Uf.view(CFG["P"] + 1, CFG["Nx"])[:-1].contiguous().view(-1)
+    Fo = torch.empty_like(U0)
+    for _ in range(2):
+        prob.fine_propagate(U0, Fo)
+    torch.cuda.synchronize()
+    fe = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(3)]
+    for a, b in fe:
+        a.record()
+        prob.fine_propagate(U0, Fo)
+        b.record()
+    torch.cuda.synchronize()
+    fine_ms = statistics.mean(a.elapsed_time(b) for a, b in fe)
+    pt_steps = (CFG["Nx"] - 2) * CFG["fine_steps"] * CFG["P"]
+    fine_tflops = FLOPS_PER_PT_STEP * pt_steps / (fine_ms * 1e-3) / 1e12
+    fp64_peak = 148 * 2 * 2 * float(peaks.get("sm_max_mhz", 2032.0)) * 1e6 / 1e12
+
+    # implicit Euler coarse and serial fine on the same grid
+    tol_ie, it_ie, err_ie = choose_tol(prob, B.COARSE_IE, None, prec, Uf, B)
+    ms_ie, _ = time_solves(prob, B.COARSE_IE, None, prec, tol_ie, max(2, args.steps // 2), 1, torch, flush)
+    sf = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(2)]
+    for a, b in sf:
+        a.record()
+        prob.serial_fine(Uf)
+        b.record()
+    torch.cuda.synchronize()
+    serial_ms = statistics.mean(a.elapsed_time(b) for a, b in sf)
+
+    # per-precision network tables at the same accuracy target
+    per_prec = {}
+    for name, p in B.PREC.items():
+        tl, itp, ep = choose_tol(prob, B.COARSE_PINN, model, p, Uf, B)
+        msp, _ = time_solves(prob, B.COARSE_PINN, model, p, tl, 2, 1, torch, flush)
+        per_prec[name] = dict(tol=tl, iterations=itp, err_vs_serial_fine=ep, ms_per_solve=statistics.mean(msp))
+
+    # end to end through the C ABI with host buffers
+    w_host = torch.tensor(model.get_weights()).pin_memory()
+    U_host = torch.empty(prob.total_state, dtype=torch.float64).pin_memory()
+    e2e_ms = []
+    for i in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        s0 = time.perf_counter()
+        model.set_weights(w_host.numpy())
+        Ud, *_ = prob.parareal_solve(B.COARSE_PINN, model=model, prec=prec, tol=tol, want_stats=False)
+        U_host.copy_(Ud, non_blocking=True)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            e2e_ms.append((time.perf_counter() - s0) * 1e3)
+    e2e_step = allreduce_max(ws, statistics.mean(e2e_ms))
+
+    cpu = None
+    if rank == 0:
+        cpu = cpu_baseline(model.get_weights(), iters, budget_s=args.cpu_seconds)
+
+    if rank != 0:
+        return
+    kmax = CFG["P"]
+    out = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "solves/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "coarse": "pinn", "pinn_precision": args.prec, "tol": tol,
+                   "iterations": iters, "err_vs_serial_fine": err_after, "l2_flush": "256 MB write between steps",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+        "e2e": {"value": ws * 1e3 / e2e_step, "unit": "solves/s", "h2d_bytes_per_step": 8 * model.n_params,
+                "d2h_bytes_per_step": 8 * prob.total_state},
+        "gpu_launches": 3 + 1 + 2 * kmax + 1,
+        "roofline": {"bound": "alu", "achieved": fine_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
+                     "frac": fine_tflops / fp64_peak, "traffic": None, "kernel": "prop_kernel<8,4,CN>",
+                     "peak_note": "FP64: 148 SM x 2 DFMA lanes/clk (measured) x 2 flop x max SM clock"},
+        "cpu_baseline": cpu,
+        "clocks": clk.summary(),
+        "fine_kernel": {"ms": fine_ms, "grid_pt_steps_per_s": pt_steps / (fine_ms * 1e-3)},
+        "ie_coarse": {"tol": tol_ie, "iterations": it_ie, "err_vs_serial_fine": err_ie,
+                      "solves_per_s": 1e3 / statistics.mean(ms_ie)},
+        "serial_fine_ms": serial_ms,
+        "speedup_vs_serial_fine": {"pinn": serial_ms / ms_step, "ie": serial_ms / statistics.mean(ms_ie)},
+        "per_precision": per_prec,
+        "train_step": train,
+        "setup_ms": setup_ms,
+        "wall_s_timed": wall,
+    }
+    print(json.dumps(out), flush=True)
+
+
+def cpu_baseline(weights, iters, budget_s=20.0):
+    """The oracle, as it stands, on the host: one Parareal-PINN iteration per sample."""
+    import numpy as np
+
+    import oracle as orc
+
+    p = orc.params(**CFG)
+    m = orc.MLP(WIDTHS, weights, [0.0, 0.0], [CFG["Smax"], CFG["T"]])
+    t0 = time.perf_counter()
+    g = orc.pinn_table(p, m)
+    t_table = time.perf_counter() - t0
+    done = 0
+    t1 = time.perf_counter()
+    while True:
+        done += 1
+        orc.parareal(p, orc.COARSE_PINN, g=g, tol=0.0, max_iter=done)
+        if time.perf_counter() - t1 > budget_s or done >= iters:
+            break
+    # parareal(max_iter=k) reruns iterations 0..k-1; total work sum_{k<=done} k iterations
+    t_all = time.perf_counter() - t1
+    work = done * (done + 1) / 2
+    t_iter = t_all / work
+    t_solve = t_table + iters * t_iter
+    return {"value": 1.0 / t_solve, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": f"network table + Parareal iterations 1..{done} of the same workload, "
+                      f"per-iteration time extrapolated to the {iters} iterations the solve needs"}
+
+
+def run_reference(args):
+    import numpy as np
+
+    import oracle as orc
+    from paper_2303_03848_b300 import synth
+
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    orc.build()
+    p = orc.params(**CFG)
+    m = orc.MLP(WIDTHS, synth.xavier_params(WIDTHS, 0), [0.0, 0.0], [CFG["Smax"], CFG["T"]])
+    t0 = time.perf_counter()
+    g = orc.pinn_table(p, m)
+    t_table = time.perf_counter() - t0
+    # one bounded sample per step: the first Parareal iteration (F on all 32 slices,
+    # correction, norm); a solve to 1e-6 with this coarse propagator needs at most P iterations
+    t_iter = []
+    for i in range(args.warmup + args.steps):
+        s0 = time.perf_counter()
+        orc.parareal(p, orc.COARSE_PINN, g=g, tol=0.0, max_iter=1)
+        if i >= args.warmup:
+            t_iter.append(time.perf_counter() - s0)
+    it = statistics.mean(t_iter)
+    K = CFG["P"]
+    t_solve = t_table + K * it
+    v = 1.0 / t_solve
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": it * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "coarse": "pinn"},
+        "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                         "sample": f"per step one Parareal iteration over all {CFG['P']} slices; solve = network "
+                                   f"table + {K} iterations (P, the count that reproduces serial fine)"},
+        "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="bf16", choices=["fp64", "fp32", "tf32", "bf16"])
+    ap.add_argument("--train-steps", type=int, default=5000)
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

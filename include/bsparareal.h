@@ -1,0 +1,214 @@
+/*
+ * bsparareal.h -- C ABI of the B300 (sm_103a) Parareal/PINN library for the
+ * Black-Scholes European call.
+ *
+ * Method: Ibrahim, Goetschel, Ruprecht, "Parareal with a physics-informed
+ * neural network as coarse propagator" (arXiv:2303.03848).
+ *   - PDE: Eq. 1 (Section 3), solved in time-to-maturity tau = T - t, with the
+ *     payoff (Eq. 2) as initial value and Dirichlet values V(tau, 0) = 0 (Eq. 3),
+ *     V(tau, Smax) = Smax - K exp(-r tau) (far-field reading of Eq. 4).
+ *   - Space: second-order centred differences on S_j = j dS, j = 0..Nx-1,
+ *     dS = Smax / (Nx - 1) (Eqs. 9-10, Section 3.2).
+ *   - Fine propagator F: Crank-Nicolson; numerical coarse G: implicit Euler
+ *     (Section 3.2).  PINN coarse: a tanh MLP in (S, tau) (Section 3.3).
+ *   - Parareal: Eq. 7 (Section 3.1).
+ *
+ * General conventions
+ *   - Every function returns a bs_status (int).  BS_EINVAL means the
+ *     arguments were rejected and nothing was launched.  No function aborts.
+ *   - Device buffers are owned by the caller, must be 16-byte aligned, dense
+ *     and resident on the current CUDA device.  Host buffers are marked "host".
+ *   - stream is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *     asynchronous on that stream unless stated otherwise.
+ *   - Handles (bs_problem, pinn_model) are created and destroyed by the
+ *     library.  A handle must not be used from two streams at once.
+ *   - Layout of state arrays: instance i owns (P_i + 1) * Nx_i doubles for
+ *     slice-boundary states (parareal_solve, serial_fine) or P_i * Nx_i doubles
+ *     for slice inputs/outputs (fine_propagate, coarse_propagate), instances
+ *     packed back to back in the order given to bs_problem_init; slice n of
+ *     instance i is the Nx_i doubles at offset (off_i + n * Nx_i).
+ */
+#ifndef BSPARAREAL_H
+#define BSPARAREAL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+typedef enum {
+  BS_OK = 0,
+  BS_EINVAL = 1,          /* invalid argument; nothing launched */
+  BS_ECUDA = 2,           /* a CUDA call failed (launch or copy) */
+  BS_ENOMEM = 3,          /* device or host allocation failed */
+  BS_NOT_CONVERGED = 4,   /* max_iter reached before tol (parareal_solve) */
+  BS_DIVERGED = 5,        /* a non-finite value reached the convergence norm */
+  BS_TIMEOUT = 6,         /* a bounded device wait gave up */
+  BS_EUNSUPPORTED = 7     /* size or mode outside what this build supports */
+} bs_status;
+
+/* Coarse propagator kinds for parareal_solve (Sections 3.1 and 3.3). */
+typedef enum {
+  BS_COARSE_IE = 0,        /* implicit Euler, coarse_steps steps per slice (Section 3.2) */
+  BS_COARSE_PINN = 1,      /* G(U_n) = u_theta(S_j, tau_{n+1}), Dirichlet nodes exact */
+  BS_COARSE_PINN_INCR = 2  /* G(U_n) = U_n + u_theta(., tau_{n+1}) - u_theta(., tau_n) */
+} bs_coarse_kind;
+
+/* Arithmetic of the network evaluation.  Fine/coarse solves are always FP64. */
+typedef enum { BS_FP64 = 0, BS_FP32 = 1, BS_TF32 = 2, BS_BF16 = 3 } bs_precision;
+
+/* One pricing instance.  Nx counts grid points including both Dirichlet nodes. */
+typedef struct {
+  double K, sigma, r, T, Smax;
+  int32_t Nx, P, fine_steps, coarse_steps;
+} bs_params;
+
+/* Per-instance result of parareal_solve (host). */
+typedef struct {
+  int32_t iterations;  /* Parareal iterations done (k) */
+  int32_t status;      /* bs_status of this instance */
+  double final_norm;   /* last increment norm e_k */
+} bs_instance_stats;
+
+typedef struct bs_problem bs_problem;
+typedef struct pinn_model pinn_model;
+
+/* Text for a status code (static storage). */
+const char* bs_status_string(int status);
+
+/* Library version string. */
+const char* bs_version(void);
+
+/*
+ * bs_problem_init -- set up n_instances pricing problems on the current device.
+ *   p: host array of n_instances parameter sets.  Requirements per instance:
+ *      K > 0, sigma > 0, r >= 0, T > 0, Smax > K, 5 <= Nx <= 4097, P >= 1,
+ *      fine_steps >= 1, coarse_steps >= 1, all finite.
+ *   Builds the Eq. 10 coefficients and factorises the Crank-Nicolson matrix
+ *   (I - dtau_f/2 L) and the implicit Euler matrix (I - dtau_g L) on the
+ *   device (Section 3.2), once; later calls reuse them.
+ *   Synchronous.  *out receives the handle.  Errors: BS_EINVAL (argument),
+ *   BS_EUNSUPPORTED (Nx above the largest grid this build keeps on chip),
+ *   BS_ENOMEM, BS_ECUDA.
+ */
+int bs_problem_init(const bs_params* p, int32_t n_instances, bs_problem** out);
+
+/* Release the handle and its device memory.  NULL is accepted. */
+void bs_problem_destroy(bs_problem* prob);
+
+/* Instance count and the lengths (doubles) of state ((P+1)-slice) and slice (P-slice) arrays. */
+int bs_problem_info(const bs_problem* prob, int32_t* n_instances, int64_t* total_state_doubles,
+                    int64_t* total_slice_doubles);
+
+/*
+ * fine_propagate -- the fine propagator F of Eq. 6 on every slice at once:
+ *   U_out[n] = F_n(U_in[n]): fine_steps Crank-Nicolson steps of
+ *   dtau_f = T / (P * fine_steps) from tau_n = n T / P to tau_{n+1}.
+ *   U_in, U_out: device, sum_i P_i * Nx_i doubles (slice layout above).
+ *   Dirichlet nodes of U_in are ignored (V_0 = 0; the Smax node is taken as
+ *   the exact value at tau_n); U_out carries exact Dirichlet values.
+ *   active: device, nullable; one byte per (instance, slice) in the same order;
+ *   slices with 0 are left untouched in U_out.  U_in and U_out must not overlap.
+ */
+int fine_propagate(bs_problem* prob, const double* U_in, double* U_out, const uint8_t* active, void* stream);
+
+/*
+ * coarse_propagate -- the implicit Euler coarse propagator G on every slice:
+ * coarse_steps steps of dtau_g = T / (P * coarse_steps).  Same layout and
+ * rules as fine_propagate.
+ */
+int coarse_propagate(bs_problem* prob, const double* U_in, double* U_out, const uint8_t* active, void* stream);
+
+/*
+ * serial_fine -- classical time stepping (Eq. 6 for n = 0..P-1) from the payoff:
+ *   U_out[0] = payoff, U_out[n+1] = F_n(U_out[n]).  U_out: device, state layout.
+ *   Each slice restarts from the stored vector, so slice n equals
+ *   fine_propagate applied to U_out[n-1] bit for bit.
+ */
+int serial_fine(bs_problem* prob, double* U_out, void* stream);
+
+/*
+ * pinn_create -- a fully connected tanh network (Section 3.3) with
+ * n_layers linear layers: widths[0] = d_in (2: inputs (S, tau);
+ * 5: (S, tau, sigma, r, K)), widths[1..n_layers-1] hidden (<= 256),
+ * widths[n_layers] = 1.  Hidden layers use tanh; the output layer is linear.
+ * Parameters are laid out per layer as W [w_out][w_in] row-major then b [w_out].
+ * Initialisation: Xavier-uniform weights, zero biases, drawn from SplitMix64
+ * in counter form (parameter index q uses output q+1 of the sequence started
+ * at `seed`; W = (2u - 1) sqrt(6 / (fan_in + fan_out)), u the top 53 bits).
+ * in_lo/in_hi (host, d_in each): the input box; inputs are mapped affinely to
+ * [-1, 1] inside the model.  Synchronous.
+ */
+int pinn_create(const int32_t* widths, int32_t n_layers, const double* in_lo, const double* in_hi, uint64_t seed,
+                pinn_model** out);
+void pinn_destroy(pinn_model* m);
+/* Number of parameters (doubles in the flat layout). */
+int pinn_num_params(const pinn_model* m, int64_t* n);
+/* Copy FP64 parameters in (host), refresh the reduced-precision copies, reset Adam state.  Synchronous. */
+int pinn_set_weights(pinn_model* m, const double* flat_host);
+/* Copy the FP64 master parameters out (host).  Synchronous. */
+int pinn_get_weights(const pinn_model* m, double* flat_host);
+
+/*
+ * pinn_eval -- u = u_theta(X) at N points (Section 3.3).
+ *   X: device [N][d_in] doubles.  u: device [N] doubles.
+ *   derivs: device, nullable, [N][3] = (u_S, u_SS, u_tau) by forward-mode
+ *   differentiation through every layer (the paper uses automatic
+ *   differentiation).  prec selects the arithmetic of the layers: FP64, FP32,
+ *   TF32 or BF16 (reduced precisions accumulate in FP32); outputs are FP64.
+ *   derivs requires FP64 or FP32.
+ */
+int pinn_eval(const pinn_model* m, int prec, const double* X, int64_t N, double* u, double* derivs, void* stream);
+
+/*
+ * pinn_loss_grad -- loss terms and gradient at the current weights, no update.
+ * Loss Eq. 11 = MSE_f (Eq. 12, residual u_tau - 1/2 sigma^2 S^2 u_SS - r S u_S + r u)
+ *             + MSE_b (Eq. 13) + MSE_exp (Eq. 14), each the mean over its points.
+ *   X: device [N][d_in] doubles; kind: device [N] int8: 0 interior,
+ *   1 boundary S = 0 (target 0), 2 boundary S = Smax (target Smax - K e^{-r tau}),
+ *   3 expiry tau = 0 (target max(S - K, 0)).  prob_params (host): K, sigma, r,
+ *   Smax of the loss (a 5-input network takes sigma, r, K per point from X;
+ *   then Smax of kind-2 points is smax_over_K * K when smax_over_K > 0).
+ *   prec: BS_FP64, BS_FP32, or BS_BF16 (BF16 operands, FP32 accumulation).
+ *   loss3 (device, 3 doubles: MSE_f, MSE_b, MSE_exp) and grad (device,
+ *   n_params doubles) are written asynchronously.
+ */
+int pinn_loss_grad(const pinn_model* m, const double* X, const int8_t* kind, int64_t N,
+                   const bs_params* prob_params, double smax_over_K, int prec, double* loss3, double* grad,
+                   void* stream);
+
+/*
+ * pinn_train_step -- pinn_loss_grad followed by one full-batch Adam step
+ * (Section 3.3; beta1 0.9, beta2 0.999, eps 1e-8, step size lr) on the FP64
+ * master parameters.  loss3: host, nullable; if given the call synchronises the
+ * stream and stores the loss terms evaluated BEFORE the update.  grad_out:
+ * device, nullable, n_params doubles: receives the gradient used.
+ */
+int pinn_train_step(pinn_model* m, const double* X, const int8_t* kind, int64_t N, const bs_params* prob_params,
+                    double smax_over_K, int prec, double lr, double* loss3, double* grad_out, void* stream);
+
+/*
+ * parareal_solve -- Parareal (Eq. 7) on every instance:
+ *   U^{k+1}_{n+1} = F(U^k_n) + (G(U^{k+1}_n) - G(U^k_n)),
+ * with G chosen by coarse_kind (model required for the network kinds; the
+ * network is evaluated once per call in arithmetic prec on (S_j, tau_n) and
+ * its Dirichlet nodes replaced by the exact values).  Iteration k runs F on
+ * slices n >= k only.  Stops per instance when the increment norm
+ *   e_k = max_n ||U^{k+1}_n - U^k_n||_2 / ||U^{k+1}_n||_2 <= tol,
+ * or k = P (then Parareal equals serial fine), or k = max_iter.
+ *   U_out: device, state layout, the final iterate.
+ *   norms: host, nullable, n_instances * max_iter doubles (e_k per iteration;
+ *   NaN where not run).  stats: host, nullable, n_instances entries.
+ * Synchronises the stream before returning when norms or stats is given.
+ * Returns BS_OK when every instance converged, else the worst instance status.
+ */
+int parareal_solve(bs_problem* prob, int coarse_kind, const pinn_model* model, int prec, double tol,
+                   int32_t max_iter, double* U_out, double* norms, bs_instance_stats* stats, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BSPARAREAL_H */

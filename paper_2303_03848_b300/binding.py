@@ -1,0 +1,300 @@
+"""ctypes binding of libbsparareal.so (C ABI in include/bsparareal.h).
+
+Argument marshalling only: torch tensors provide device memory and the current
+stream; every numerical step runs in the library's kernels.  If the library or
+a CUDA device is missing, the calls raise: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbsparareal.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "bsparareal.h")
+
+BS_OK, BS_EINVAL, BS_ECUDA, BS_ENOMEM, BS_NOT_CONVERGED, BS_DIVERGED, BS_TIMEOUT, BS_EUNSUPPORTED = range(8)
+COARSE_IE, COARSE_PINN, COARSE_PINN_INCR = 0, 1, 2
+FP64, FP32, TF32, BF16 = 0, 1, 2, 3
+PREC = {"fp64": FP64, "fp32": FP32, "tf32": TF32, "bf16": BF16}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class BsError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {status_string(code)} ({code})")
+
+
+class BsParams(ctypes.Structure):
+    _fields_ = [
+        ("K", ctypes.c_double),
+        ("sigma", ctypes.c_double),
+        ("r", ctypes.c_double),
+        ("T", ctypes.c_double),
+        ("Smax", ctypes.c_double),
+        ("Nx", ctypes.c_int32),
+        ("P", ctypes.c_int32),
+        ("fine_steps", ctypes.c_int32),
+        ("coarse_steps", ctypes.c_int32),
+    ]
+
+
+class InstanceStats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("status", ctypes.c_int32), ("final_norm", ctypes.c_double)]
+
+
+def lib() -> ctypes.CDLL:
+    """Load the library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run `python -m paper_2303_03848_b300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        P = ctypes.POINTER
+        L.bs_status_string.argtypes = [ctypes.c_int]
+        L.bs_status_string.restype = ctypes.c_char_p
+        L.bs_version.argtypes = []
+        L.bs_version.restype = ctypes.c_char_p
+        L.bs_problem_init.argtypes = [P(BsParams), i32, P(vp)]
+        L.bs_problem_destroy.argtypes = [vp]
+        L.bs_problem_destroy.restype = None
+        L.bs_problem_info.argtypes = [vp, P(i32), P(i64), P(i64)]
+        for f in (L.fine_propagate, L.coarse_propagate):
+            f.argtypes = [vp, vp, vp, vp, vp]
+        L.serial_fine.argtypes = [vp, vp, vp]
+        L.pinn_create.argtypes = [P(i32), i32, P(dbl), P(dbl), ctypes.c_uint64, P(vp)]
+        L.pinn_destroy.argtypes = [vp]
+        L.pinn_destroy.restype = None
+        L.pinn_num_params.argtypes = [vp, P(i64)]
+        L.pinn_set_weights.argtypes = [vp, P(dbl)]
+        L.pinn_get_weights.argtypes = [vp, P(dbl)]
+        L.pinn_eval.argtypes = [vp, ctypes.c_int, vp, i64, vp, vp, vp]
+        L.pinn_loss_grad.argtypes = [vp, vp, vp, i64, P(BsParams), dbl, ctypes.c_int, vp, vp, vp]
+        L.pinn_train_step.argtypes = [vp, vp, vp, i64, P(BsParams), dbl, ctypes.c_int, dbl, P(dbl), vp, vp]
+        L.parareal_solve.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, dbl, i32, vp, P(dbl), P(InstanceStats), vp]
+        _lib = L
+        return L
+
+
+def status_string(code: int) -> str:
+    return lib().bs_status_string(code).decode()
+
+
+def version() -> str:
+    return lib().bs_version().decode()
+
+
+def header_functions() -> list[str]:
+    """Names of the functions the public header declares."""
+    import re
+
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?(?:int|void|char\s*\*|const char\s*\*)\s*\*?\s*(\w+)\s*\(",
+                                 src, flags=re.M)))
+
+
+def _check(rc: int, what: str):
+    if rc != BS_OK:
+        raise BsError(rc, what)
+
+
+def _stream():
+    import torch
+
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dev(t, dtype, what):
+    import torch
+
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise TypeError(f"{what}: expected a contiguous CUDA tensor of {dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def params(K=1.0, sigma=0.2, r=0.05, T=1.0, Smax=4.0, Nx=256, P=8, fine_steps=128, coarse_steps=1) -> dict:
+    return dict(K=K, sigma=sigma, r=r, T=T, Smax=Smax, Nx=Nx, P=P, fine_steps=fine_steps, coarse_steps=coarse_steps)
+
+
+def _to_struct(d) -> BsParams:
+    return BsParams(d["K"], d["sigma"], d["r"], d["T"], d["Smax"], d["Nx"], d["P"], d["fine_steps"],
+                    d["coarse_steps"])
+
+
+class Problem:
+    """Handle of bs_problem_init: one or more pricing instances on the current device."""
+
+    def __init__(self, instances):
+        if isinstance(instances, dict):
+            instances = [instances]
+        self.instances = [dict(p) for p in instances]
+        arr = (BsParams * len(self.instances))(*[_to_struct(p) for p in self.instances])
+        h = ctypes.c_void_p()
+        _check(lib().bs_problem_init(arr, len(self.instances), ctypes.byref(h)), "bs_problem_init")
+        self._h = h
+        n, ts, tl = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().bs_problem_info(h, ctypes.byref(n), ctypes.byref(ts), ctypes.byref(tl)), "bs_problem_info")
+        self.n_instances, self.total_state, self.total_slice = n.value, ts.value, tl.value
+        self.state_off, self.slice_off = [], []
+        so = sl = 0
+        for p in self.instances:
+            self.state_off.append(so)
+            self.slice_off.append(sl)
+            so += (p["P"] + 1) * p["Nx"]
+            sl += p["P"] * p["Nx"]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().bs_problem_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # views -------------------------------------------------------------
+    def state_view(self, U, i: int):
+        p = self.instances[i]
+        o = self.state_off[i]
+        return U[o:o + (p["P"] + 1) * p["Nx"]].view(p["P"] + 1, p["Nx"])
+
+    def slice_view(self, U, i: int):
+        p = self.instances[i]
+        o = self.slice_off[i]
+        return U[o:o + p["P"] * p["Nx"]].view(p["P"], p["Nx"])
+
+    # calls -------------------------------------------------------------
+    def _prop(self, fn, U_in, U_out, active):
+        import torch
+
+        if U_out is None:
+            U_out = torch.empty(self.total_slice, dtype=torch.float64, device=U_in.device)
+        if U_in.numel() != self.total_slice or U_out.numel() != self.total_slice:
+            raise ValueError("slice arrays must hold sum_i P_i * Nx_i doubles")
+        act = _dev(active, torch.uint8, "active") if active is not None else None
+        _check(fn(self._h, _dev(U_in, torch.float64, "U_in"), _dev(U_out, torch.float64, "U_out"), act, _stream()),
+               fn.__name__)
+        return U_out
+
+    def fine_propagate(self, U_in, U_out=None, active=None):
+        return self._prop(lib().fine_propagate, U_in, U_out, active)
+
+    def coarse_propagate(self, U_in, U_out=None, active=None):
+        return self._prop(lib().coarse_propagate, U_in, U_out, active)
+
+    def serial_fine(self, U_out=None):
+        import torch
+
+        if U_out is None:
+            U_out = torch.empty(self.total_state, dtype=torch.float64, device="cuda")
+        _check(lib().serial_fine(self._h, _dev(U_out, torch.float64, "U_out"), _stream()), "serial_fine")
+        return U_out
+
+    def parareal_solve(self, coarse_kind=COARSE_IE, model=None, prec=FP64, tol=1e-10, max_iter=None, U_out=None,
+                       want_stats=True):
+        """Returns (U, norms [n_inst, max_iter] or None, stats list or None, status)."""
+        import torch
+
+        if max_iter is None:
+            max_iter = max(p["P"] for p in self.instances)
+        if U_out is None:
+            U_out = torch.empty(self.total_state, dtype=torch.float64, device="cuda")
+        norms = stats = None
+        np_norms = None
+        if want_stats:
+            np_norms = np.empty(self.n_instances * max_iter)
+            stats = (InstanceStats * self.n_instances)()
+        rc = lib().parareal_solve(self._h, coarse_kind, model._h if model is not None else None, prec, tol, max_iter,
+                                  _dev(U_out, torch.float64, "U_out"),
+                                  np_norms.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if want_stats else None,
+                                  stats, _stream())
+        if rc not in (BS_OK, BS_NOT_CONVERGED, BS_DIVERGED):
+            raise BsError(rc, "parareal_solve")
+        if want_stats:
+            norms = np_norms.reshape(self.n_instances, max_iter)
+            stats = [dict(iterations=s.iterations, status=s.status, final_norm=s.final_norm) for s in stats]
+        return U_out, norms, stats, rc
+
+
+class PinnModel:
+    """Handle of pinn_create: tanh MLP in (S, tau) [, sigma, r, K]."""
+
+    def __init__(self, widths, lo, hi, seed=0):
+        self.widths = [int(w) for w in widths]
+        w = (ctypes.c_int32 * len(self.widths))(*self.widths)
+        lo_a = (ctypes.c_double * len(lo))(*[float(v) for v in lo])
+        hi_a = (ctypes.c_double * len(hi))(*[float(v) for v in hi])
+        h = ctypes.c_void_p()
+        _check(lib().pinn_create(w, len(self.widths) - 1, lo_a, hi_a, seed, ctypes.byref(h)), "pinn_create")
+        self._h = h
+        n = ctypes.c_int64()
+        _check(lib().pinn_num_params(h, ctypes.byref(n)), "pinn_num_params")
+        self.n_params = n.value
+        self.lo, self.hi = list(lo), list(hi)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().pinn_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_weights(self, flat: np.ndarray):
+        flat = np.ascontiguousarray(flat, dtype=np.float64)
+        if flat.size != self.n_params:
+            raise ValueError("wrong parameter count")
+        _check(lib().pinn_set_weights(self._h, flat.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+               "pinn_set_weights")
+
+    def get_weights(self) -> np.ndarray:
+        out = np.empty(self.n_params)
+        _check(lib().pinn_get_weights(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+               "pinn_get_weights")
+        return out
+
+    def eval(self, X, prec=FP64, derivs=False):
+        import torch
+
+        N = X.shape[0]
+        u = torch.empty(N, dtype=torch.float64, device=X.device)
+        d = torch.empty(N, 3, dtype=torch.float64, device=X.device) if derivs else None
+        _check(lib().pinn_eval(self._h, prec, _dev(X, torch.float64, "X"), N, _dev(u, torch.float64, "u"),
+                               _dev(d, torch.float64, "derivs") if d is not None else None, _stream()), "pinn_eval")
+        return (u, d) if derivs else u
+
+    def loss_grad(self, X, kind, prob: dict, smax_over_K=0.0, prec=FP32):
+        import torch
+
+        loss3 = torch.empty(3, dtype=torch.float64, device=X.device)
+        grad = torch.empty(self.n_params, dtype=torch.float64, device=X.device)
+        pp = _to_struct(prob)
+        _check(lib().pinn_loss_grad(self._h, _dev(X, torch.float64, "X"), _dev(kind, torch.int8, "kind"), X.shape[0],
+                                    ctypes.byref(pp), smax_over_K, prec, _dev(loss3, torch.float64, "loss3"),
+                                    _dev(grad, torch.float64, "grad"), _stream()), "pinn_loss_grad")
+        return loss3, grad
+
+    def train_step(self, X, kind, prob: dict, lr=1e-3, smax_over_K=0.0, prec=FP32, want_loss=False, grad_out=None):
+        import torch
+
+        pp = _to_struct(prob)
+        loss = (ctypes.c_double * 3)() if want_loss else None
+        g = _dev(grad_out, torch.float64, "grad_out") if grad_out is not None else None
+        _check(lib().pinn_train_step(self._h, _dev(X, torch.float64, "X"), _dev(kind, torch.int8, "kind"), X.shape[0],
+                                     ctypes.byref(pp), smax_over_K, prec, lr, loss, g, _stream()), "pinn_train_step")
+        return list(loss) if want_loss else None

@@ -1,0 +1,575 @@
+// api.cu -- the C ABI declared in include/bsparareal.h.
+//
+// Host code here validates arguments, owns the device memory of the handles
+// and enqueues kernels; every step of the numerical path runs in the kernels
+// of solver.cu and pinn.cu.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/bsparareal.h"
+#include "bs_common.cuh"
+#include "bs_internal.h"
+
+using bsp::Inst;
+
+namespace {
+
+struct Class {
+  int M = 0, NW = 0, maxP = 0;
+  std::vector<int32_t> ids;
+  int32_t* d_ids = nullptr;
+};
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+}
+
+int map_err(cudaError_t e) {
+  if (e == cudaSuccess) return BS_OK;
+  if (e == cudaErrorMemoryAllocation) return BS_ENOMEM;
+  return BS_ECUDA;
+}
+
+bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+// Partition of the Nx-1 rows (interior + Dirichlet row at Smax) over NW warps
+// x 32 lanes x M rows.
+bool choose_partition(int Nx, int* M, int* NW) {
+  const int rows = Nx - 1;
+  if (rows <= 64) { *NW = 1; *M = 2; return true; }
+  if (rows <= 128) { *NW = 2; *M = 2; return true; }
+  if (rows <= 256) { *NW = 4; *M = 2; return true; }
+  if (rows <= 512) { *NW = 4; *M = 4; return true; }
+  if (rows <= 1024) { *NW = 4; *M = 8; return true; }
+  if (rows <= 2048) { *NW = 4; *M = 16; return true; }
+  if (rows <= 4096) { *NW = 4; *M = 32; return true; }
+  return false;
+}
+
+}  // namespace
+
+struct bs_problem {
+  int n_inst = 0;
+  std::vector<Inst> h_insts;
+  Inst* d_insts = nullptr;
+  double* pool = nullptr;
+  double* exptab = nullptr;
+  std::vector<Class> classes;
+  int64_t total_state = 0, total_slice = 0, total_tasks = 0, total_tasks1 = 0;
+  int maxP = 0;
+  // Parareal workspace (allocated on first use)
+  double *buf0 = nullptr, *buf1 = nullptr, *fbuf = nullptr, *gold = nullptr, *gtab = nullptr, *normbuf = nullptr;
+  double* Xgrid = nullptr;
+  int xgrid_din = 0;
+  double* norms_dev = nullptr;
+  int norms_cap = 0;
+  bsp::Ctrl* ctrl = nullptr;
+};
+
+struct pinn_model {
+  bsp::MlpDev dev{};
+  int64_t n_params = 0;
+  double* p64 = nullptr;
+  float* p32 = nullptr;
+  double* mom1 = nullptr;
+  double* mom2 = nullptr;
+  double* grad = nullptr;
+  double* loss3 = nullptr;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  int step = 0;
+};
+
+extern "C" {
+
+const char* bs_status_string(int status) {
+  switch (status) {
+    case BS_OK: return "ok";
+    case BS_EINVAL: return "invalid argument";
+    case BS_ECUDA: return "CUDA error";
+    case BS_ENOMEM: return "out of memory";
+    case BS_NOT_CONVERGED: return "not converged";
+    case BS_DIVERGED: return "diverged (non-finite norm)";
+    case BS_TIMEOUT: return "timeout";
+    case BS_EUNSUPPORTED: return "unsupported size or mode";
+  }
+  return "unknown status";
+}
+
+const char* bs_version(void) { return "bsparareal 0.1 sm_103a"; }
+
+void bs_problem_destroy(bs_problem* prob) {
+  if (!prob) return;
+  cudaFree(prob->d_insts);
+  cudaFree(prob->pool);
+  cudaFree(prob->exptab);
+  for (auto& c : prob->classes) cudaFree(c.d_ids);
+  cudaFree(prob->buf0);
+  cudaFree(prob->buf1);
+  cudaFree(prob->fbuf);
+  cudaFree(prob->gold);
+  cudaFree(prob->gtab);
+  cudaFree(prob->normbuf);
+  cudaFree(prob->Xgrid);
+  cudaFree(prob->norms_dev);
+  cudaFree(prob->ctrl);
+  delete prob;
+}
+
+int bs_problem_init(const bs_params* p, int32_t n_instances, bs_problem** out) {
+  if (!p || !out || n_instances <= 0) return BS_EINVAL;
+  *out = nullptr;
+  for (int i = 0; i < n_instances; ++i) {
+    const bs_params& q = p[i];
+    if (!finite_pos(q.K) || !finite_pos(q.sigma) || !std::isfinite(q.r) || q.r < 0.0 || !finite_pos(q.T) ||
+        !finite_pos(q.Smax) || !(q.Smax > q.K) || q.Nx < 5 || q.P < 1 || q.fine_steps < 1 || q.coarse_steps < 1)
+      return BS_EINVAL;
+    int M, NW;
+    if (!choose_partition(q.Nx, &M, &NW)) return BS_EUNSUPPORTED;
+  }
+  bs_problem* prob = new (std::nothrow) bs_problem();
+  if (!prob) return BS_ENOMEM;
+  prob->n_inst = n_instances;
+  prob->h_insts.resize(n_instances);
+  int64_t coef = 0, ex = 0;
+  for (int i = 0; i < n_instances; ++i) {
+    const bs_params& q = p[i];
+    Inst in{};
+    in.K = q.K;
+    in.sigma = q.sigma;
+    in.r = q.r;
+    in.T = q.T;
+    in.Smax = q.Smax;
+    in.dS = q.Smax / (double)(q.Nx - 1);
+    in.Nx = q.Nx;
+    in.P = q.P;
+    in.Mf = q.fine_steps;
+    in.Mg = q.coarse_steps;
+    choose_partition(q.Nx, &in.M, &in.NW);
+    in.R = in.NW * 32 * in.M;
+    in.Np = in.R - (q.Nx - 1);
+    const int64_t bs = bsp::coef_block_size(in.M, in.NW * 32, in.NW);
+    in.coef_cn = coef;
+    coef += bs;
+    in.coef_ie = coef;
+    coef += bs;
+    in.exp_cn = ex;
+    ex += q.fine_steps + 1;
+    in.exp_ie = ex;
+    ex += q.coarse_steps + 1;
+    in.state_off = prob->total_state;
+    prob->total_state += (int64_t)(q.P + 1) * q.Nx;
+    in.slice_off = prob->total_slice;
+    prob->total_slice += (int64_t)q.P * q.Nx;
+    in.task_off = prob->total_tasks;
+    prob->total_tasks += q.P;
+    in.task1_off = prob->total_tasks1;
+    prob->total_tasks1 += q.P + 1;
+    if (q.P > prob->maxP) prob->maxP = q.P;
+    prob->h_insts[i] = in;
+    Class* cl = nullptr;
+    for (auto& c : prob->classes)
+      if (c.M == in.M && c.NW == in.NW) cl = &c;
+    if (!cl) {
+      prob->classes.push_back(Class{});
+      cl = &prob->classes.back();
+      cl->M = in.M;
+      cl->NW = in.NW;
+    }
+    cl->ids.push_back(i);
+    if (q.P > cl->maxP) cl->maxP = q.P;
+  }
+  cudaError_t e = cudaSuccess;
+  if ((e = dalloc(&prob->d_insts, n_instances)) != cudaSuccess ||
+      (e = dalloc(&prob->pool, (size_t)coef)) != cudaSuccess || (e = dalloc(&prob->exptab, (size_t)ex)) != cudaSuccess) {
+    bs_problem_destroy(prob);
+    return map_err(e);
+  }
+  e = cudaMemcpy(prob->d_insts, prob->h_insts.data(), sizeof(Inst) * n_instances, cudaMemcpyHostToDevice);
+  for (auto& c : prob->classes) {
+    if (e == cudaSuccess) e = dalloc(&c.d_ids, c.ids.size());
+    if (e == cudaSuccess)
+      e = cudaMemcpy(c.d_ids, c.ids.data(), sizeof(int32_t) * c.ids.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = bsp::launch_setup(prob->d_insts, c.d_ids, (int)c.ids.size(), prob->pool, prob->exptab, 0);
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    bs_problem_destroy(prob);
+    return map_err(e);
+  }
+  *out = prob;
+  return BS_OK;
+}
+
+int bs_problem_info(const bs_problem* prob, int32_t* n_instances, int64_t* total_state_doubles,
+                    int64_t* total_slice_doubles) {
+  if (!prob) return BS_EINVAL;
+  if (n_instances) *n_instances = prob->n_inst;
+  if (total_state_doubles) *total_state_doubles = prob->total_state;
+  if (total_slice_doubles) *total_slice_doubles = prob->total_slice;
+  return BS_OK;
+}
+
+static int propagate(bs_problem* prob, bool cn, const double* U_in, double* U_out, const uint8_t* active,
+                     void* stream) {
+  if (!prob || !U_in || !U_out) return BS_EINVAL;
+  if (((uintptr_t)U_in | (uintptr_t)U_out) & 15) return BS_EINVAL;
+  const double* ie = U_in + prob->total_slice;
+  const double* oe = U_out + prob->total_slice;
+  if (U_in < oe && U_out < ie) return BS_EINVAL;  // overlap
+  cudaStream_t s = (cudaStream_t)stream;
+  for (auto& c : prob->classes) {
+    bsp::PropArgs a{};
+    a.insts = prob->d_insts;
+    a.ids = c.d_ids;
+    a.pool = prob->pool;
+    a.exptab = prob->exptab;
+    a.in = U_in;
+    a.out = U_out;
+    a.in_state = 0;
+    a.out_state = 0;
+    a.mode = bsp::PropArgs::kPlain;
+    a.k_iter = -1;
+    a.active = active;
+    cudaError_t e = bsp::launch_prop(c.M, c.NW, cn, a, (int)c.ids.size(), c.maxP, s);
+    if (e != cudaSuccess) return map_err(e);
+  }
+  return BS_OK;
+}
+
+int fine_propagate(bs_problem* prob, const double* U_in, double* U_out, const uint8_t* active, void* stream) {
+  return propagate(prob, true, U_in, U_out, active, stream);
+}
+
+int coarse_propagate(bs_problem* prob, const double* U_in, double* U_out, const uint8_t* active, void* stream) {
+  return propagate(prob, false, U_in, U_out, active, stream);
+}
+
+int serial_fine(bs_problem* prob, double* U_out, void* stream) {
+  if (!prob || !U_out || ((uintptr_t)U_out & 15)) return BS_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  for (auto& c : prob->classes) {
+    bsp::SerialArgs a{prob->d_insts, c.d_ids, prob->pool, prob->exptab, U_out};
+    cudaError_t e = bsp::launch_serial(c.M, c.NW, a, (int)c.ids.size(), s);
+    if (e != cudaSuccess) return map_err(e);
+  }
+  return BS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Network handles
+// ---------------------------------------------------------------------------
+
+// SplitMix64 (Steele, Lea, Flood 2014): output number i+1 of the sequence whose state starts at `seed`.
+static uint64_t splitmix64(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+void pinn_destroy(pinn_model* m) {
+  if (!m) return;
+  cudaFree(m->p64);
+  cudaFree(m->p32);
+  cudaFree(m->mom1);
+  cudaFree(m->mom2);
+  cudaFree(m->grad);
+  cudaFree(m->loss3);
+  cudaFree(m->ws);
+  delete m;
+}
+
+static int upload_params(pinn_model* m, const double* host) {
+  cudaError_t e = cudaMemcpy(m->p64, host, sizeof(double) * m->n_params, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = bsp::launch_f64_to_f32(m->p64, m->p32, m->n_params, 0);
+  if (e == cudaSuccess) e = cudaMemset(m->mom1, 0, sizeof(double) * m->n_params);
+  if (e == cudaSuccess) e = cudaMemset(m->mom2, 0, sizeof(double) * m->n_params);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  m->step = 0;
+  return map_err(e);
+}
+
+int pinn_create(const int32_t* widths, int32_t n_layers, const double* in_lo, const double* in_hi, uint64_t seed,
+                pinn_model** out) {
+  if (!widths || !out || !in_lo || !in_hi || n_layers < 1 || n_layers > 15) return BS_EINVAL;
+  *out = nullptr;
+  const int d_in = widths[0];
+  if (!(d_in == 2 || d_in == 5) || widths[n_layers] != 1) return BS_EINVAL;
+  int max_w = 0;
+  for (int l = 0; l <= n_layers; ++l) {
+    if (widths[l] < 1 || widths[l] > 256) return BS_EINVAL;
+    if (widths[l] > max_w) max_w = widths[l];
+  }
+  for (int i = 0; i < d_in; ++i)
+    if (!std::isfinite(in_lo[i]) || !std::isfinite(in_hi[i]) || !(in_hi[i] > in_lo[i])) return BS_EINVAL;
+  pinn_model* m = new (std::nothrow) pinn_model();
+  if (!m) return BS_ENOMEM;
+  m->dev.n_lin = n_layers;
+  m->dev.d_in = d_in;
+  m->dev.max_w = max_w;
+  int64_t off = 0;
+  for (int l = 0; l <= n_layers; ++l) m->dev.widths[l] = widths[l];
+  for (int l = 1; l <= n_layers; ++l) {
+    m->dev.poff[l] = off;
+    off += (int64_t)widths[l] * widths[l - 1] + widths[l];
+  }
+  for (int i = 0; i < d_in; ++i) {
+    m->dev.lo[i] = in_lo[i];
+    m->dev.hi[i] = in_hi[i];
+  }
+  m->n_params = off;
+  cudaError_t e;
+  if ((e = dalloc(&m->p64, off)) != cudaSuccess || (e = dalloc(&m->p32, off)) != cudaSuccess ||
+      (e = dalloc(&m->mom1, off)) != cudaSuccess || (e = dalloc(&m->mom2, off)) != cudaSuccess ||
+      (e = dalloc(&m->grad, off)) != cudaSuccess || (e = dalloc(&m->loss3, 4)) != cudaSuccess) {
+    pinn_destroy(m);
+    return map_err(e);
+  }
+  m->dev.p64 = m->p64;
+  m->dev.p32 = m->p32;
+  // Xavier-uniform weights, zero biases
+  std::vector<double> h(off, 0.0);
+  for (int l = 1; l <= n_layers; ++l) {
+    const double a = std::sqrt(6.0 / (double)(widths[l - 1] + widths[l]));
+    const int64_t nw = (int64_t)widths[l] * widths[l - 1];
+    for (int64_t q = 0; q < nw; ++q) {
+      const int64_t idx = m->dev.poff[l] + q;
+      const double u = (double)(splitmix64(seed, (uint64_t)idx) >> 11) * (1.0 / 9007199254740992.0);
+      h[idx] = (2.0 * u - 1.0) * a;
+    }
+  }
+  int rc = upload_params(m, h.data());
+  if (rc != BS_OK) {
+    pinn_destroy(m);
+    return rc;
+  }
+  *out = m;
+  return BS_OK;
+}
+
+int pinn_num_params(const pinn_model* m, int64_t* n) {
+  if (!m || !n) return BS_EINVAL;
+  *n = m->n_params;
+  return BS_OK;
+}
+
+int pinn_set_weights(pinn_model* m, const double* flat_host) {
+  if (!m || !flat_host) return BS_EINVAL;
+  for (int64_t i = 0; i < m->n_params; ++i)
+    if (!std::isfinite(flat_host[i])) return BS_EINVAL;
+  return upload_params(m, flat_host);
+}
+
+int pinn_get_weights(const pinn_model* m, double* flat_host) {
+  if (!m || !flat_host) return BS_EINVAL;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(flat_host, m->p64, sizeof(double) * m->n_params, cudaMemcpyDeviceToHost);
+  return map_err(e);
+}
+
+int pinn_eval(const pinn_model* m, int prec, const double* X, int64_t N, double* u, double* derivs, void* stream) {
+  if (!m || N < 0 || prec < BS_FP64 || prec > BS_BF16) return BS_EINVAL;
+  if (N == 0) return BS_OK;
+  if (!X || !u || (((uintptr_t)X | (uintptr_t)u | (uintptr_t)derivs) & 15)) return BS_EINVAL;
+  if (derivs && !(prec == BS_FP64 || prec == BS_FP32)) return BS_EINVAL;
+  return map_err(bsp::launch_mlp_eval(m->dev, prec, X, N, u, derivs, (cudaStream_t)stream));
+}
+
+static int loss_grad_common(const pinn_model* mc, const double* X, const int8_t* kind, int64_t N,
+                            const bs_params* pp, double smax_over_K, int prec, double* loss3, double* grad,
+                            cudaStream_t s) {
+  pinn_model* m = const_cast<pinn_model*>(mc);
+  if (!m || !X || !kind || !pp || N <= 0) return BS_EINVAL;
+  if (!(prec == BS_FP64 || prec == BS_FP32 || prec == BS_BF16)) return BS_EINVAL;
+  if (((uintptr_t)X & 15) || ((uintptr_t)grad & 7) || ((uintptr_t)loss3 & 7) || !std::isfinite(pp->K) ||
+      !std::isfinite(pp->sigma) || !std::isfinite(pp->r) || !std::isfinite(pp->Smax) || !std::isfinite(smax_over_K))
+    return BS_EINVAL;
+  const size_t need = bsp::loss_grad_workspace_bytes(m->dev, N);
+  if (need > m->ws_bytes) {
+    cudaError_t e = cudaStreamSynchronize(s);  // the old workspace may still be in use
+    if (e != cudaSuccess) return map_err(e);
+    cudaFree(m->ws);
+    m->ws = nullptr;
+    m->ws_bytes = 0;
+    e = cudaMalloc(&m->ws, need);
+    if (e != cudaSuccess) return map_err(e);
+    m->ws_bytes = need;
+  }
+  bsp::LossArgs la{X, kind, N, pp->K, pp->sigma, pp->r, pp->Smax, smax_over_K, prec};
+  return map_err(bsp::launch_loss_grad(m->dev, la, loss3, grad, m->ws, m->ws_bytes, s));
+}
+
+int pinn_loss_grad(const pinn_model* m, const double* X, const int8_t* kind, int64_t N,
+                   const bs_params* prob_params, double smax_over_K, int prec, double* loss3, double* grad,
+                   void* stream) {
+  if (!loss3 || !grad) return BS_EINVAL;
+  return loss_grad_common(m, X, kind, N, prob_params, smax_over_K, prec, loss3, grad, (cudaStream_t)stream);
+}
+
+int pinn_train_step(pinn_model* m, const double* X, const int8_t* kind, int64_t N, const bs_params* prob_params,
+                    double smax_over_K, int prec, double lr, double* loss3, double* grad_out, void* stream) {
+  if (!m || !std::isfinite(lr) || lr <= 0.0) return BS_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  double* g = grad_out ? grad_out : m->grad;
+  int rc = loss_grad_common(m, X, kind, N, prob_params, smax_over_K, prec, m->loss3, g, s);
+  if (rc != BS_OK) return rc;
+  m->step += 1;
+  cudaError_t e = bsp::launch_adam(m->n_params, m->p64, m->mom1, m->mom2, g, m->step, lr, m->p32, s);
+  if (e != cudaSuccess) return map_err(e);
+  if (loss3) {
+    e = cudaMemcpyAsync(loss3, m->loss3, 3 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return map_err(e);
+  }
+  return BS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Parareal
+// ---------------------------------------------------------------------------
+
+static cudaError_t ensure_parareal_ws(bs_problem* prob, int max_iter, int d_in) {
+  cudaError_t e = cudaSuccess;
+  if (!prob->buf0) {
+    if ((e = dalloc(&prob->buf0, prob->total_state)) != cudaSuccess) return e;
+    if ((e = dalloc(&prob->buf1, prob->total_state)) != cudaSuccess) return e;
+    if ((e = dalloc(&prob->fbuf, prob->total_slice)) != cudaSuccess) return e;
+    if ((e = dalloc(&prob->gold, prob->total_slice)) != cudaSuccess) return e;
+    if ((e = dalloc(&prob->gtab, prob->total_state)) != cudaSuccess) return e;
+    if ((e = dalloc(&prob->normbuf, 2 * prob->total_tasks1)) != cudaSuccess) return e;
+    if ((e = dalloc(&prob->ctrl, prob->n_inst)) != cudaSuccess) return e;
+    if ((e = cudaMemset(prob->normbuf, 0, sizeof(double) * 2 * prob->total_tasks1)) != cudaSuccess) return e;
+  }
+  if (max_iter > prob->norms_cap) {
+    cudaFree(prob->norms_dev);
+    prob->norms_dev = nullptr;
+    if ((e = dalloc(&prob->norms_dev, (size_t)prob->n_inst * max_iter)) != cudaSuccess) return e;
+    prob->norms_cap = max_iter;
+  }
+  if (d_in > 0 && prob->xgrid_din != d_in) {
+    cudaFree(prob->Xgrid);
+    prob->Xgrid = nullptr;
+    if ((e = dalloc(&prob->Xgrid, (size_t)prob->total_state * d_in)) != cudaSuccess) return e;
+    prob->xgrid_din = d_in;
+  }
+  return e;
+}
+
+int parareal_solve(bs_problem* prob, int coarse_kind, const pinn_model* model, int prec, double tol,
+                   int32_t max_iter, double* U_out, double* norms, bs_instance_stats* stats, void* stream) {
+  if (!prob || !U_out || ((uintptr_t)U_out & 15) || max_iter < 1 || !(tol >= 0.0)) return BS_EINVAL;
+  if (coarse_kind < BS_COARSE_IE || coarse_kind > BS_COARSE_PINN_INCR) return BS_EINVAL;
+  const bool pinn = coarse_kind != BS_COARSE_IE;
+  if (pinn && !model) return BS_EINVAL;
+  if (pinn && (prec < BS_FP64 || prec > BS_BF16)) return BS_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = ensure_parareal_ws(prob, max_iter, pinn ? model->dev.d_in : 0);
+  if (e != cudaSuccess) return map_err(e);
+  const int n = prob->n_inst;
+  // a1: network table on (S_j, tau_n), Dirichlet nodes exact
+  if (pinn) {
+    const int d_in = model->dev.d_in;
+    if ((e = bsp::launch_grid_points(prob->d_insts, n, d_in, prob->Xgrid, s)) != cudaSuccess) return map_err(e);
+    if ((e = bsp::launch_mlp_eval(model->dev, prec, prob->Xgrid, prob->total_state, prob->gtab, nullptr, s)) !=
+        cudaSuccess)
+      return map_err(e);
+    if ((e = bsp::launch_table_fix(prob->d_insts, n, prob->gtab, s)) != cudaSuccess) return map_err(e);
+  }
+  // a2: initial iterate
+  if ((e = bsp::launch_parareal_init(prob->d_insts, n, prob->buf0, prob->buf1, prob->gtab,
+                                     coarse_kind == BS_COARSE_PINN, prob->ctrl, prob->norms_dev, max_iter, s)) !=
+      cudaSuccess)
+    return map_err(e);
+  const int sweep_kind = coarse_kind == BS_COARSE_IE ? 0 : 1;
+  auto sweep = [&](int k, double* cur, double* nxt) -> cudaError_t {
+    for (auto& c : prob->classes) {
+      bsp::SweepArgs a{};
+      a.insts = prob->d_insts;
+      a.ids = c.d_ids;
+      a.pool = prob->pool;
+      a.exptab = prob->exptab;
+      a.kind = sweep_kind;
+      a.k_iter = k;
+      a.ctrl = k < 0 ? nullptr : prob->ctrl;
+      a.ucur = cur;
+      a.unext = nxt;
+      a.gold = prob->gold;
+      a.fbuf = prob->fbuf;
+      a.gtab = prob->gtab;
+      a.normbuf = prob->normbuf;
+      cudaError_t ee = bsp::launch_sweep(c.M, c.NW, a, (int)c.ids.size(), s);
+      if (ee != cudaSuccess) return ee;
+    }
+    return cudaSuccess;
+  };
+  if (coarse_kind != BS_COARSE_PINN) {
+    if ((e = sweep(-1, prob->buf0, prob->buf0)) != cudaSuccess) return map_err(e);
+  }
+  const int kmax = max_iter < prob->maxP ? max_iter : prob->maxP;
+  for (int k = 0; k < kmax; ++k) {
+    double* cur = (k & 1) ? prob->buf1 : prob->buf0;
+    double* nxt = (k & 1) ? prob->buf0 : prob->buf1;
+    // a3 (+ a5 fused for the state-independent network coarse propagator)
+    for (auto& c : prob->classes) {
+      bsp::PropArgs a{};
+      a.insts = prob->d_insts;
+      a.ids = c.d_ids;
+      a.pool = prob->pool;
+      a.exptab = prob->exptab;
+      a.in = cur;
+      a.in_state = 1;
+      a.k_iter = k;
+      a.ctrl = prob->ctrl;
+      if (coarse_kind == BS_COARSE_PINN) {
+        a.out = nxt;
+        a.out_state = 1;
+        a.mode = bsp::PropArgs::kPinnFused;
+        a.gtab = prob->gtab;
+        a.uold = cur;
+        a.normbuf = prob->normbuf;
+      } else {
+        a.out = prob->fbuf;
+        a.out_state = 0;
+        a.mode = bsp::PropArgs::kPlain;
+      }
+      if ((e = bsp::launch_prop(c.M, c.NW, true, a, (int)c.ids.size(), c.maxP, s)) != cudaSuccess) return map_err(e);
+    }
+    // a4 + a5: serial coarse sweep with the correction
+    if (coarse_kind != BS_COARSE_PINN) {
+      if ((e = sweep(k, cur, nxt)) != cudaSuccess) return map_err(e);
+    }
+    if ((e = bsp::launch_parareal_finalize(prob->d_insts, n, prob->normbuf, k, tol, max_iter, prob->ctrl,
+                                           prob->norms_dev, s)) != cudaSuccess)
+      return map_err(e);
+  }
+  if ((e = bsp::launch_copy_result(prob->d_insts, n, prob->ctrl, prob->buf0, prob->buf1, U_out, s)) != cudaSuccess)
+    return map_err(e);
+  if (!norms && !stats) return BS_OK;
+  std::vector<bsp::Ctrl> hc(n);
+  if ((e = cudaMemcpyAsync(hc.data(), prob->ctrl, sizeof(bsp::Ctrl) * n, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return map_err(e);
+  if (norms &&
+      (e = cudaMemcpyAsync(norms, prob->norms_dev, sizeof(double) * (size_t)n * max_iter, cudaMemcpyDeviceToHost, s)) !=
+          cudaSuccess)
+    return map_err(e);
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return map_err(e);
+  int worst = BS_OK;
+  for (int i = 0; i < n; ++i) {
+    if (stats) {
+      stats[i].iterations = hc[i].iterations;
+      stats[i].status = hc[i].status;
+      stats[i].final_norm = hc[i].last_norm;
+    }
+    if (hc[i].status != BS_OK && (worst == BS_OK || hc[i].status == BS_DIVERGED)) worst = hc[i].status;
+  }
+  return worst;
+}
+
+}  // extern "C"

@@ -1,0 +1,99 @@
+// bs_internal.h -- host-side declarations shared by the translation units of
+// the library (launch wrappers and their argument blocks).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "bs_common.cuh"
+
+namespace bsp {
+
+// Arguments of the slice propagation kernel (fine or coarse over all slices).
+struct PropArgs {
+  enum Mode { kPlain = 0, kPinnFused = 1 };
+  const Inst* insts;
+  const int32_t* ids;        // instances of this partition class
+  const double* pool;        // coefficient blocks
+  const double* exptab;      // exp(-r m dtau) tables
+  const double* in;          // input states
+  double* out;               // outputs
+  int in_state;              // 1: input slice n at state_off + n*Nx; 0: at slice_off + n*Nx
+  int out_state;             // 1: output at state_off + (n+1)*Nx; 0: at slice_off + n*Nx
+  int mode;
+  int k_iter;                // Parareal iteration, slices n < k_iter skipped (-1: none)
+  const uint8_t* active;     // nullable, per (instance, slice)
+  const Ctrl* ctrl;          // nullable, done flags
+  const double* gtab;        // kPinnFused: network table (state layout)
+  const double* uold;        // kPinnFused: U^k (state layout)
+  double* normbuf;           // kPinnFused: (num, den) per (instance, boundary index)
+};
+
+struct SerialArgs {
+  const Inst* insts;
+  const int32_t* ids;
+  const double* pool;
+  const double* exptab;
+  double* out;  // state layout
+};
+
+struct SweepArgs {
+  const Inst* insts;
+  const int32_t* ids;
+  const double* pool;
+  const double* exptab;
+  int kind;            // 0 implicit Euler, 1 network increment
+  int k_iter;          // -1: initial sweep
+  const Ctrl* ctrl;
+  const double* ucur;  // U^k (state layout)
+  double* unext;       // U^{k+1} (state layout)
+  double* gold;        // G(U^k_n) per slice (slice layout), updated in place
+  const double* fbuf;  // F(U^k_n) (slice layout)
+  const double* gtab;  // network table (state layout), increment kind
+  double* normbuf;
+};
+
+cudaError_t launch_setup(const Inst* d_insts, const int32_t* d_ids, int n, double* pool, double* exptab,
+                         cudaStream_t s);
+cudaError_t launch_prop(int M, int NW, bool cn, const PropArgs& a, int n_inst, int maxP, cudaStream_t s);
+cudaError_t launch_serial(int M, int NW, const SerialArgs& a, int n_inst, cudaStream_t s);
+cudaError_t launch_sweep(int M, int NW, const SweepArgs& a, int n_inst, cudaStream_t s);
+cudaError_t launch_parareal_init(const Inst* d_insts, int n_inst, double* buf0, double* buf1, const double* gtab,
+                                 int pinn, Ctrl* ctrl, double* norms, int max_iter, cudaStream_t s);
+cudaError_t launch_parareal_finalize(const Inst* d_insts, int n_inst, const double* normbuf, int k, double tol,
+                                     int max_iter, Ctrl* ctrl, double* norms, cudaStream_t s);
+cudaError_t launch_copy_result(const Inst* d_insts, int n_inst, const Ctrl* ctrl, const double* buf0,
+                               const double* buf1, double* out, cudaStream_t s);
+cudaError_t launch_grid_points(const Inst* d_insts, int n_inst, int d_in, double* X, cudaStream_t s);
+cudaError_t launch_table_fix(const Inst* d_insts, int n_inst, double* g, cudaStream_t s);
+
+// ---- network (pinn.cu) ----
+struct MlpDev {
+  int n_lin;
+  int d_in;
+  int max_w;
+  int32_t widths[16];
+  int64_t poff[16];          // parameter offset of layer l (1-based), in elements
+  double lo[8], hi[8];
+  const double* p64;         // FP64 master parameters
+  const float* p32;          // FP32 copy
+};
+
+cudaError_t launch_mlp_eval(const MlpDev& m, int prec, const double* X, int64_t N, double* u, double* derivs,
+                            cudaStream_t s);
+cudaError_t launch_f64_to_f32(const double* src, float* dst, int64_t n, cudaStream_t s);
+
+// Loss terms and gradient (pinn.cu).  loss3 and grad are device buffers.
+struct LossArgs {
+  const double* X;
+  const int8_t* kind;
+  int64_t N;
+  double K, sigma, r, Smax, smax_over_K;
+  int prec;
+};
+cudaError_t launch_loss_grad(const MlpDev& m, const LossArgs& la, double* loss3, double* grad, void* workspace,
+                             size_t ws_bytes, cudaStream_t s);
+size_t loss_grad_workspace_bytes(const MlpDev& m, int64_t N);
+cudaError_t launch_adam(int64_t n, double* theta, double* mom1, double* mom2, const double* g, int step, double lr,
+                        float* p32, cudaStream_t s);
+
+}  // namespace bsp

@@ -1,0 +1,164 @@
+"""GPU parity of the network path (evaluation, derivatives, loss, adjoint
+gradient, Adam) against the oracle, through the C ABI.
+
+Tolerances (relative to the largest magnitude of the compared quantity):
+  FP64: 1e-12 for u, 1e-10 for derivatives and gradients (the GPU sums in a
+        different order; second derivatives and long dot products lose a few
+        more digits);
+  FP32: 2e-5 for u and derivatives, 1e-4 for loss terms and gradients
+        (unit roundoff 6e-8 amplified by 4-8 layers of width <= 256);
+  TF32: 1e-2 and BF16: 4e-2 for u (operands rounded to 10 / 7 mantissa bits,
+        FP32 accumulation); BF16 gradients 1e-1 (operands of both passes rounded).
+"""
+import numpy as np
+import pytest
+
+from paper_2303_03848_b300 import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+TOL_EVAL = {0: 1e-12, 1: 2e-5, 2: 1e-2, 3: 4e-2}
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2303_03848_b300 import binding, build
+
+    build.build()
+    return binding
+
+
+def _rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+ARCHS = {
+    "2-4x64": [2, 64, 64, 64, 64, 1],
+    "2-6x128": [2] + [128] * 6 + [1],
+    "5-6x128": [5] + [128] * 6 + [1],
+    "2-8x256": [2] + [256] * 8 + [1],
+}
+LO5 = [0.0, 0.0, 0.1, 0.0, 0.5]
+HI5 = [8.0, 2.0, 0.5, 0.08, 2.0]
+
+
+def _box(widths):
+    d = widths[0]
+    return ([0.0, 0.0], [4.0, 1.0]) if d == 2 else (LO5, HI5)
+
+
+def _points(widths, n, seed):
+    lo, hi = _box(widths)
+    u = synth.uniform(seed, n * widths[0]).reshape(n, widths[0])
+    return np.asarray(lo) + (np.asarray(hi) - np.asarray(lo)) * u
+
+
+def _model(B, orc, widths, seed):
+    lo, hi = _box(widths)
+    m = B.PinnModel(widths, lo, hi, seed=seed)
+    w = synth.xavier_params(widths, seed)
+    w[np.arange(w.size) % 7 == 1] += 0.05
+    m.set_weights(w)
+    return m, orc.MLP(widths, w, lo, hi)
+
+
+def test_pinn_create_initialisation_matches_generator(B):
+    widths = ARCHS["2-4x64"]
+    m = B.PinnModel(widths, [0.0, 0.0], [4.0, 1.0], seed=1234)
+    np.testing.assert_array_equal(m.get_weights(), synth.xavier_params(widths, 1234))
+
+
+@pytest.mark.parametrize("arch", list(ARCHS))
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+def test_eval_matches_oracle(B, orc, arch, prec):
+    widths = ARCHS[arch]
+    if prec == 0 and arch == "2-8x256":
+        n = 300
+    else:
+        n = 1000 + 37  # several CTAs and a ragged tail
+    m, om = _model(B, orc, widths, 5)
+    X = _points(widths, n, 9)
+    ref = orc.mlp_eval(om, X, with_derivs=False)
+    u = m.eval(torch.tensor(X, device="cuda"), prec=prec).cpu().numpy()
+    assert _rel(u, ref) <= TOL_EVAL[prec]
+
+
+@pytest.mark.parametrize("arch", ["2-4x64", "2-6x128", "5-6x128"])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_eval_derivatives_match_oracle(B, orc, arch, prec):
+    widths = ARCHS[arch]
+    m, om = _model(B, orc, widths, 6)
+    X = _points(widths, 517, 10)
+    ru, rd = orc.mlp_eval(om, X)
+    u, d = m.eval(torch.tensor(X, device="cuda"), prec=prec, derivs=True)
+    u, d = u.cpu().numpy(), d.cpu().numpy()
+    tol_u = TOL_EVAL[prec]
+    tol_d = 1e-10 if prec == 0 else 2e-5
+    assert _rel(u, ru) <= tol_u
+    for c in range(3):
+        assert _rel(d[:, c], rd[:, c]) <= tol_d, c
+
+
+def test_eval_empty_batch_is_noop(B, orc):
+    m, _ = _model(B, orc, ARCHS["2-4x64"], 1)
+    X = torch.empty(0, 2, dtype=torch.float64, device="cuda")
+    assert m.eval(X).numel() == 0
+
+
+def _loss_case(widths, n_int, n_b, n_e, seed):
+    if widths[0] == 2:
+        X, kind = synth.collocation(seed, n_int, n_b, n_e, 4.0, 1.0)
+        prob = dict(K=1.0, sigma=0.2, r=0.05, T=1.0, Smax=4.0, Nx=5, P=1, fine_steps=1, coarse_steps=1)
+        return X, kind, prob, 0.0
+    X, kind = synth.collocation_parametric(seed, n_int, n_b, n_e, 4.0, 2.0)
+    prob = dict(K=1.0, sigma=0.2, r=0.05, T=2.0, Smax=8.0, Nx=5, P=1, fine_steps=1, coarse_steps=1)
+    return X, kind, prob, 4.0
+
+
+@pytest.mark.parametrize("arch", ["2-4x64", "2-6x128", "5-6x128"])
+@pytest.mark.parametrize("prec", [0, 1, 3])
+def test_loss_and_gradient_match_oracle(B, orc, arch, prec):
+    widths = ARCHS[arch]
+    m, om = _model(B, orc, widths, 8)
+    X, kind, prob, sok = _loss_case(widths, 1500, 128, 128, 4)
+    terms, grad = orc.pinn_loss_grad(om, X, kind, prob["K"], prob["sigma"], prob["r"], prob["Smax"], sok)
+    l3, g = m.loss_grad(torch.tensor(X, device="cuda"), torch.tensor(kind, device="cuda"), prob, sok, prec=prec)
+    l3, g = l3.cpu().numpy(), g.cpu().numpy()
+    tol_l, tol_g = {0: (1e-12, 1e-10), 1: (1e-4, 1e-4), 3: (5e-2, 1e-1)}[prec]
+    for c in range(3):
+        assert abs(l3[c] - terms[c]) <= tol_l * max(abs(terms[c]), 1e-300), (c, l3[c], terms[c])
+    assert _rel(g, grad) <= tol_g
+
+
+def test_train_step_is_adam_on_the_gradient(B, orc):
+    widths = ARCHS["2-4x64"]
+    m, om = _model(B, orc, widths, 12)
+    X, kind, prob, sok = _loss_case(widths, 700, 64, 64, 6)
+    Xd, kd = torch.tensor(X, device="cuda"), torch.tensor(kind, device="cuda")
+    th = om.params.copy()
+    m1, m2 = np.zeros_like(th), np.zeros_like(th)
+    for t in (1, 2):
+        terms, grad = orc.pinn_loss_grad(orc.MLP(widths, th, om.lo, om.hi), X, kind, 1.0, 0.2, 0.05, 4.0)
+        loss = m.train_step(Xd, kd, prob, lr=1e-3, prec=B.FP64, want_loss=True)
+        np.testing.assert_allclose(loss, terms, rtol=1e-12)
+        orc.adam(th, m1, m2, grad, t, 1e-3)
+        # Adam divides by sqrt(v): a gradient entry that is ~0 makes that
+        # parameter's step sensitive to its rounding, so compare absolutely
+        assert np.abs(m.get_weights() - th).max() <= 1e-12
+
+
+def test_training_reduces_loss_fp32(B, orc):
+    widths = ARCHS["2-4x64"]
+    m = B.PinnModel(widths, [0.0, 0.0], [4.0, 1.0], seed=0)
+    X, kind = synth.collocation(0, 2048, 128, 128, 4.0, 1.0)
+    Xd, kd = torch.tensor(X, device="cuda"), torch.tensor(kind, device="cuda")
+    prob = dict(K=1.0, sigma=0.2, r=0.05, T=1.0, Smax=4.0, Nx=5, P=1, fine_steps=1, coarse_steps=1)
+    first = sum(m.train_step(Xd, kd, prob, lr=1e-3, prec=B.FP32, want_loss=True))
+    for _ in range(200):
+        m.train_step(Xd, kd, prob, lr=1e-3, prec=B.FP32)
+    last = sum(m.train_step(Xd, kd, prob, lr=1e-3, prec=B.FP32, want_loss=True))
+    assert last < 0.2 * first

@@ -1,0 +1,223 @@
+"""GPU parity of the FP64 solver path against the oracle (through the C ABI).
+
+Tolerance: FP64 results within 1e-12 of the oracle relative to the largest
+magnitude of the compared vector (the GPU runs the same recurrences in a
+different order: partitioned Thomas + PCR instead of one Thomas sweep, and
+Crank-Nicolson in the Z = V^{m+1} + V^m form), the bar the method statement
+sets for FP64.
+"""
+import numpy as np
+import pytest
+
+from paper_2303_03848_b300 import synth
+
+pytestmark = pytest.mark.gpu
+RTOL = 1e-12
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2303_03848_b300 import binding, build
+
+    build.build()
+    return binding
+
+
+def _oparams(orc, d):
+    return orc.params(**d)
+
+
+def _close(a, b, rtol=RTOL):
+    a, b = np.asarray(a), np.asarray(b)
+    scale = max(np.abs(b).max(), 1e-300)
+    err = np.abs(a - b).max() / scale
+    assert err <= rtol, f"relative error {err:.3e} > {rtol:.1e}"
+    return err
+
+
+# grids covering every partition class, ragged padding and the largest size
+NX_SET = [5, 33, 65, 66, 129, 200, 256, 257, 513, 777, 1024, 1025, 2049, 4097]
+
+
+def _mixed_instances(steps=6, P=3):
+    out = []
+    for i, Nx in enumerate(NX_SET):
+        K = 0.6 + 0.1 * i
+        out.append(dict(K=K, sigma=0.15 + 0.02 * i, r=0.01 * (i % 5), T=0.5 + 0.1 * i, Smax=4.0 * K, Nx=Nx, P=P,
+                        fine_steps=steps, coarse_steps=2))
+    return out
+
+
+def _random_slices(orc, insts, seed):
+    """Slice-layout inputs: noisy states with exact Dirichlet nodes at tau_n."""
+    parts = []
+    for i, p in enumerate(insts):
+        op = _oparams(orc, p)
+        S = synth.random_states(seed + i, p["P"], p["Nx"], scale=p["Smax"])
+        for n in range(p["P"]):
+            S[n, 0] = 0.0
+            S[n, -1] = orc.right_bc(op, p["T"] * n / p["P"])
+        parts.append(S)
+    return parts
+
+
+@pytest.mark.parametrize("kind", ["fine", "coarse"])
+def test_propagators_match_oracle_all_partition_classes(B, orc, kind):
+    insts = _mixed_instances()
+    prob = B.Problem(insts)
+    parts = _random_slices(orc, insts, 100)
+    Uin = torch.tensor(np.concatenate([p.ravel() for p in parts]), device="cuda")
+    Uout = prob.fine_propagate(Uin) if kind == "fine" else prob.coarse_propagate(Uin)
+    Uout = Uout.cpu().numpy()
+    for i, p in enumerate(insts):
+        op = _oparams(orc, p)
+        got = Uout[prob.slice_off[i]:prob.slice_off[i] + p["P"] * p["Nx"]].reshape(p["P"], p["Nx"])
+        for n in range(p["P"]):
+            ref = orc.fine(op, n, parts[i][n]) if kind == "fine" else orc.coarse_ie(op, n, parts[i][n])
+            _close(got[n], ref)
+            assert got[n, 0] == 0.0
+
+
+def test_active_mask_leaves_inactive_slices_untouched(B, orc):
+    insts = _mixed_instances()[3:6]
+    prob = B.Problem(insts)
+    parts = _random_slices(orc, insts, 7)
+    Uin = torch.tensor(np.concatenate([p.ravel() for p in parts]), device="cuda")
+    Uout = torch.full_like(Uin, -7.0)
+    active = torch.tensor([1, 0, 1] * len(insts), dtype=torch.uint8, device="cuda")
+    prob.fine_propagate(Uin, Uout, active)
+    for i, p in enumerate(insts):
+        got = prob.slice_view(Uout, i).cpu().numpy()
+        assert np.all(got[1] == -7.0)
+        _close(got[0], orc.fine(_oparams(orc, p), 0, parts[i][0]))
+        _close(got[2], orc.fine(_oparams(orc, p), 2, parts[i][2]))
+
+
+@pytest.mark.parametrize("cfg", [
+    dict(K=1.0, sigma=0.2, r=0.05, T=1.0, Smax=4.0, Nx=256, P=8, fine_steps=128, coarse_steps=1),
+    dict(K=1.0, sigma=0.2, r=0.05, T=1.0, Smax=4.0, Nx=1024, P=32, fine_steps=1024, coarse_steps=1),
+], ids=["nx256_p8", "nx1024_p32_m1024"])
+def test_serial_fine_matches_oracle(B, orc, cfg):
+    prob = B.Problem(cfg)
+    U = prob.serial_fine().cpu().numpy().reshape(cfg["P"] + 1, cfg["Nx"])
+    ref = orc.serial_fine(_oparams(orc, cfg))
+    for n in range(cfg["P"] + 1):
+        _close(U[n], ref[n])
+    # accuracy against the closed-form price (Fig. 3 measure, context): the
+    # discretisation error, far above the parity bar
+    dS = cfg["Smax"] / (cfg["Nx"] - 1)
+    ex = np.array([orc.bs_call(j * dS, cfg["K"], cfg["r"], cfg["sigma"], cfg["T"]) for j in range(cfg["Nx"])])
+    assert np.abs(U[-1] - ex).max() < 1e-4
+
+
+def test_serial_fine_slices_equal_fine_propagate_bitwise(B):
+    cfg = dict(K=1.0, sigma=0.3, r=0.03, T=2.0, Smax=5.0, Nx=777, P=5, fine_steps=20, coarse_steps=1)
+    prob = B.Problem(cfg)
+    U = prob.serial_fine()
+    Uv = U.view(cfg["P"] + 1, cfg["Nx"])
+    F = prob.fine_propagate(Uv[:-1].contiguous().view(-1)).view(cfg["P"], cfg["Nx"])
+    assert torch.equal(F, Uv[1:])
+
+
+def _cfg1():
+    return dict(K=1.0, sigma=0.2, r=0.05, T=1.0, Smax=4.0, Nx=256, P=8, fine_steps=128, coarse_steps=1)
+
+
+def test_parareal_ie_matches_oracle(B, orc):
+    cfg = _cfg1()
+    prob = B.Problem(cfg)
+    U, norms, stats, rc = prob.parareal_solve(B.COARSE_IE, tol=1e-10)
+    Ur, nr, st = orc.parareal(_oparams(orc, cfg), orc.COARSE_IE, tol=1e-10)
+    assert rc == B.BS_OK and st == 0
+    assert stats[0]["iterations"] == len(nr)
+    np.testing.assert_allclose(norms[0, :len(nr)], nr, rtol=1e-6)
+    _close(U.cpu().numpy(), Ur.ravel())
+
+
+def test_parareal_k_equals_P_is_gpu_serial_fine_bitwise(B):
+    cfg = dict(_cfg1(), P=6, Nx=300, fine_steps=24)
+    prob = B.Problem(cfg)
+    U, norms, stats, rc = prob.parareal_solve(B.COARSE_IE, tol=0.0)
+    assert rc == B.BS_OK and stats[0]["iterations"] == cfg["P"]
+    assert torch.equal(U, prob.serial_fine())
+
+
+def test_parareal_first_k_slices_exact_and_status(B):
+    cfg = dict(_cfg1(), P=6, Nx=300, fine_steps=24)
+    prob = B.Problem(cfg)
+    Uf = prob.serial_fine().view(cfg["P"] + 1, cfg["Nx"])
+    for k in (1, 3):
+        U, norms, stats, rc = prob.parareal_solve(B.COARSE_IE, tol=0.0, max_iter=k)
+        assert rc == B.BS_NOT_CONVERGED and stats[0]["status"] == B.BS_NOT_CONVERGED
+        assert stats[0]["iterations"] == k
+        Uv = U.view(cfg["P"] + 1, cfg["Nx"])
+        assert torch.equal(Uv[:k + 1], Uf[:k + 1])
+        assert np.isnan(norms[0, k:]).all() if k < norms.shape[1] else True
+
+
+def _random_net(B, orc, widths, seed, lo, hi):
+    m = B.PinnModel(widths, lo, hi, seed=seed)
+    w = synth.xavier_params(widths, seed)
+    w[np.arange(w.size) % 5 == 2] += 0.05
+    m.set_weights(w)
+    return m, orc.MLP(widths, w, lo, hi)
+
+
+@pytest.mark.parametrize("kind", ["pinn", "pinn_incr"])
+def test_parareal_network_coarse_matches_oracle(B, orc, kind):
+    cfg = dict(_cfg1(), Nx=200, P=6, fine_steps=32)
+    m, om = _random_net(B, orc, [2, 16, 16, 1], 3, [0.0, 0.0], [cfg["Smax"], cfg["T"]])
+    k_gpu = B.COARSE_PINN if kind == "pinn" else B.COARSE_PINN_INCR
+    k_or = orc.COARSE_PINN if kind == "pinn" else orc.COARSE_PINN_INCR
+    prob = B.Problem(cfg)
+    U, norms, stats, rc = prob.parareal_solve(k_gpu, model=m, prec=B.FP64, tol=1e-9)
+    op = _oparams(orc, cfg)
+    g = orc.pinn_table(op, om)
+    Ur, nr, st = orc.parareal(op, k_or, g=g, tol=1e-9)
+    assert stats[0]["iterations"] == len(nr)
+    np.testing.assert_allclose(norms[0, :len(nr)], nr, rtol=1e-6)
+    _close(U.cpu().numpy(), Ur.ravel())
+
+
+def test_batched_parareal_matches_oracle_per_instance(B, orc):
+    insts = synth.batched_instances(5, 6, P=5, fine_steps=12, coarse_steps=1, Nx_choices=(65, 256, 300, 1024))
+    prob = B.Problem(insts)
+    U, norms, stats, rc = prob.parareal_solve(B.COARSE_IE, tol=1e-8)
+    assert rc == B.BS_OK
+    U = U.cpu().numpy()
+    for i, p in enumerate(insts):
+        Ur, nr, st = orc.parareal(_oparams(orc, p), orc.COARSE_IE, tol=1e-8)
+        assert stats[i]["iterations"] == len(nr)
+        _close(U[prob.state_off[i]:prob.state_off[i] + (p["P"] + 1) * p["Nx"]], Ur.ravel())
+
+
+def test_non_finite_network_reports_diverged(B, orc):
+    # fault injected from the host: output weights so large that the network
+    # table overflows to inf, so G_new - G_old = inf - inf = NaN reaches the norm
+    cfg = dict(_cfg1(), Nx=65, P=4, fine_steps=4)
+    widths = [2, 4, 1]
+    m = B.PinnModel(widths, [0.0, 0.0], [4.0, 1.0], seed=1)
+    w = np.zeros(m.n_params)
+    w[:8] = 0.5
+    w[12:16] = 1e308
+    m.set_weights(w)
+    prob = B.Problem(cfg)
+    U, norms, stats, rc = prob.parareal_solve(B.COARSE_PINN, model=m, prec=B.FP64, tol=1e-6)
+    assert rc == B.BS_DIVERGED and stats[0]["status"] == B.BS_DIVERGED
+    assert stats[0]["iterations"] == 1 and np.isnan(norms[0, 0])
+
+
+def test_repeat_calls_are_deterministic(B):
+    cfg = dict(_cfg1(), Nx=1024, P=4, fine_steps=16)
+    prob = B.Problem(cfg)
+    a = prob.serial_fine().clone()
+    b = prob.serial_fine()
+    assert torch.equal(a, b)
+    U1, *_ = prob.parareal_solve(B.COARSE_IE, tol=1e-12)
+    U1 = U1.clone()
+    U2, *_ = prob.parareal_solve(B.COARSE_IE, tol=1e-12)
+    assert torch.equal(U1, U2)
