@@ -4,7 +4,11 @@ Tolerance: FP64 results within 1e-12 of the oracle relative to the largest
 magnitude of the compared vector (the GPU runs the same recurrences in a
 different order: partitioned Thomas + PCR instead of one Thomas sweep, and
 Crank-Nicolson in the Z = V^{m+1} + V^m form), the bar the method statement
-sets for FP64.
+sets for FP64.  The stress cases with uniform noise at large mesh ratios use
+the calibrated bound max(1e-12, 2 kappa u), kappa = 1 + h max_j(|a_j|+|b_j|+|c_j|),
+u = 2^-53: forming the oracle's right-hand side (I + h L) V sums terms kappa
+times larger than the result, and the oracle itself is that far from a
+long-double recomputation (pinned on the CPU in test_oracle.py).
 """
 import numpy as np
 import pytest
@@ -65,6 +69,16 @@ def _random_slices(orc, insts, seed):
     return parts
 
 
+def _kappa_tol(p, kind):
+    steps = p["fine_steps"] if kind == "fine" else p["coarse_steps"]
+    dt = p["T"] / (p["P"] * steps)
+    h = 0.5 * dt if kind == "fine" else dt
+    j = p["Nx"] - 2
+    s2 = p["sigma"] ** 2
+    kappa = 1.0 + h * (2.0 * s2 * j * j + p["r"] * j + p["r"])
+    return max(RTOL, 2.0 * kappa * 2.0 ** -53)
+
+
 @pytest.mark.parametrize("kind", ["fine", "coarse"])
 def test_propagators_match_oracle_all_partition_classes(B, orc, kind):
     insts = _mixed_instances()
@@ -78,7 +92,7 @@ def test_propagators_match_oracle_all_partition_classes(B, orc, kind):
         got = Uout[prob.slice_off[i]:prob.slice_off[i] + p["P"] * p["Nx"]].reshape(p["P"], p["Nx"])
         for n in range(p["P"]):
             ref = orc.fine(op, n, parts[i][n]) if kind == "fine" else orc.coarse_ie(op, n, parts[i][n])
-            _close(got[n], ref)
+            _close(got[n], ref, _kappa_tol(p, kind))
             assert got[n, 0] == 0.0
 
 
@@ -93,8 +107,8 @@ def test_active_mask_leaves_inactive_slices_untouched(B, orc):
     for i, p in enumerate(insts):
         got = prob.slice_view(Uout, i).cpu().numpy()
         assert np.all(got[1] == -7.0)
-        _close(got[0], orc.fine(_oparams(orc, p), 0, parts[i][0]))
-        _close(got[2], orc.fine(_oparams(orc, p), 2, parts[i][2]))
+        _close(got[0], orc.fine(_oparams(orc, p), 0, parts[i][0]), _kappa_tol(p, "fine"))
+        _close(got[2], orc.fine(_oparams(orc, p), 2, parts[i][2]), _kappa_tol(p, "fine"))
 
 
 @pytest.mark.parametrize("cfg", [

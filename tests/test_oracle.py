@@ -407,3 +407,48 @@ def test_adam_matches_torch_and_hand_step(orc):
         opt.step()
         orc.adam(th, m, v, g, t, 0.05)
     np.testing.assert_allclose(th, w.detach().numpy(), rtol=1e-14, atol=1e-15)
+
+
+def _cn_longdouble(p, n, V):
+    """Crank-Nicolson slice in 80-bit long double (calibration of the oracle's rounding only)."""
+    ld = np.longdouble
+    Nx, M = p.Nx, p.fine_steps
+    dt = ld(p.T) / (ld(p.P) * M)
+    j = np.arange(Nx, dtype=ld)
+    s2, r = ld(p.sigma) ** 2, ld(p.r)
+    a, b, c = 0.5 * s2 * j * j - 0.5 * r * j, -s2 * j * j - r, 0.5 * s2 * j * j + 0.5 * r * j
+    V = V.astype(ld).copy()
+    nn = Nx - 2
+    for m in range(M):
+        tau = ld(p.T) * (n * M + m + 1) / (p.P * M)
+        Bn = ld(p.Smax) - ld(p.K) * np.exp(-r * tau)
+        d = 0.5 * dt * a[1:-1] * V[:-2] + (1 + 0.5 * dt * b[1:-1]) * V[1:-1] + 0.5 * dt * c[1:-1] * V[2:]
+        d[-1] += 0.5 * dt * c[Nx - 2] * Bn
+        lo, di, up = -0.5 * dt * a[1:-1], 1 - 0.5 * dt * b[1:-1], -0.5 * dt * c[1:-1]
+        cp, dp = np.zeros(nn, ld), np.zeros(nn, ld)
+        cp[0], dp[0] = up[0] / di[0], d[0] / di[0]
+        for i in range(1, nn):
+            pv = di[i] - lo[i] * cp[i - 1]
+            cp[i], dp[i] = up[i] / pv, (d[i] - lo[i] * dp[i - 1]) / pv
+        x = np.zeros(nn, ld)
+        x[-1] = dp[-1]
+        for i in range(nn - 2, -1, -1):
+            x[i] = dp[i] - cp[i] * x[i + 1]
+        V[1:-1], V[0], V[-1] = x, 0, Bn
+    return V
+
+
+def test_oracle_rounding_within_calibrated_bound(orc):
+    # noisy state at mesh ratio h sigma^2 j^2 ~ 6e3: the oracle's own distance to
+    # a long-double recomputation stays within 2 kappa u, the bound the GPU
+    # parity tests use for such stress cases (and exceeds 1e-12 here)
+    K = 1.7
+    p = orc.params(K=K, sigma=0.37, r=0.01, T=1.6, Smax=4 * K, Nx=1025, P=3, fine_steps=6)
+    S = synth.random_states(111, 1, p.Nx, scale=p.Smax)[0]
+    S[0], S[-1] = 0.0, orc.right_bc(p, 0.0)
+    ref = _cn_longdouble(p, 0, S)
+    err = float(np.abs(orc.fine(p, 0, S) - ref).max() / np.abs(ref).max())
+    h = 0.5 * p.T / (p.P * p.fine_steps)
+    j = p.Nx - 2
+    kappa = 1 + h * (2 * p.sigma ** 2 * j * j + p.r * j + p.r)
+    assert 1e-13 < err <= 2 * kappa * 2.0 ** -53
