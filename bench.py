@@ -42,6 +42,9 @@ METRIC = "Parareal solves/s at 1e-6 vs serial fine"
 WORKLOAD = ("PINN-coarse Parareal, BS call K=1 sigma=0.2 r=0.05 T=1, Nx=1024 S in [0,4], P=32, "
             "CN 1024 steps/slice FP64, MLP 2->4x64 tanh trained 5k Adam steps on 16384+1024 points")
 FLOPS_PER_PT_STEP = 11.0  # CN right-hand side 5 + factored solve 6 (algorithmic, per interior point-step)
+# DRAM read+write bytes of one prop_kernel<8,4,CN> launch over all 32 slices (ncu, profiles/fine_cn_nx1024_p32.md);
+# set to None whenever the kernel changes until it is captured again
+FINE_TRAFFIC_BYTES = 368896
 
 
 def _peaks():
@@ -302,7 +305,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": 8 * prob.total_state},
         "gpu_launches": 3 + 1 + 2 * kmax + 1,
         "roofline": {"bound": "alu", "achieved": fine_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
-                     "frac": fine_tflops / fp64_peak, "traffic": None, "kernel": "prop_kernel<8,4,CN>",
+                     "frac": fine_tflops / fp64_peak, "traffic": FINE_TRAFFIC_BYTES, "kernel": "prop_kernel<8,4,CN>",
                      "peak_note": "FP64: 148 SM x 2 DFMA lanes/clk (measured) x 2 flop x max SM clock"},
         "cpu_baseline": cpu,
         "clocks": clk.summary(),
@@ -317,6 +320,32 @@ def run_ours(args):
         "wall_s_timed": wall,
     }
     print(json.dumps(out), flush=True)
+
+
+def run_fine_only(args):
+    """The fine kernel alone: fine_propagate over all P slices of the workload (no training, no solve)."""
+    import torch
+
+    from paper_2303_03848_b300 import binding as B
+    from paper_2303_03848_b300 import build as BUILD
+
+    BUILD.build()
+    prob = B.Problem(CFG)
+    Uf = prob.serial_fine()
+    U0 = Uf.view(CFG["P"] + 1, CFG["Nx"])[:-1].contiguous().view(-1)
+    Fo = torch.empty_like(U0)
+    for _ in range(args.warmup):
+        prob.fine_propagate(U0, Fo)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for a, b in ev:
+        a.record()
+        prob.fine_propagate(U0, Fo)
+        b.record()
+    torch.cuda.synchronize()
+    ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    pt = (CFG["Nx"] - 2) * CFG["fine_steps"] * CFG["P"]
+    print(json.dumps({"mode": "fine", "ms": ms, "grid_pt_steps_per_s": pt / (ms * 1e-3),
+                      "tflops_algorithmic": FLOPS_PER_PT_STEP * pt / (ms * 1e-3) / 1e12}), flush=True)
 
 
 def cpu_baseline(weights, iters, budget_s=20.0):
@@ -396,10 +425,14 @@ def main():
     ap.add_argument("--prec", default="bf16", choices=["fp64", "fp32", "tf32", "bf16"])
     ap.add_argument("--train-steps", type=int, default=5000)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--mode", default="solve", choices=["solve", "fine"],
+                    help="fine: only the fine propagator on all slices of the workload (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.impl == "reference":
+    if args.mode == "fine":
+        run_fine_only(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

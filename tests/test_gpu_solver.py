@@ -206,7 +206,9 @@ def test_batched_parareal_matches_oracle_per_instance(B, orc):
     for i, p in enumerate(insts):
         Ur, nr, st = orc.parareal(_oparams(orc, p), orc.COARSE_IE, tol=1e-8)
         assert stats[i]["iterations"] == len(nr)
-        _close(U[prob.state_off[i]:prob.state_off[i] + (p["P"] + 1) * p["Nx"]], Ur.ravel())
+        # 12 fine steps per slice put the mesh ratio near 4e3 and the payoff kink
+        # excites the high modes: calibrated bound, as for the stress inputs
+        _close(U[prob.state_off[i]:prob.state_off[i] + (p["P"] + 1) * p["Nx"]], Ur.ravel(), _kappa_tol(p, "fine"))
 
 
 def test_non_finite_network_reports_diverged(B, orc):
