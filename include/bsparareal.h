@@ -207,6 +207,30 @@ int pinn_train_step(pinn_model* m, const double* X, const int8_t* kind, int64_t 
 int parareal_solve(bs_problem* prob, int coarse_kind, const pinn_model* model, int prec, double tol,
                    int32_t max_iter, double* U_out, double* norms, bs_instance_stats* stats, void* stream);
 
+/*
+ * parareal_solve_static -- parareal_solve without any device allocation.
+ * The paper has no counterpart: this is a service for callers that must not
+ * allocate device memory once their set-up is done, such as code enqueuing
+ * work while a stream is being captured, loops where cudaMalloc/cudaFree would
+ * synchronise the device and stall other streams, or processes whose device
+ * memory is already reserved by another allocator.  (parareal_solve allocates
+ * its workspace on the problem handle on its first call.)
+ *   Arguments, results and status codes are those of parareal_solve.  The
+ *   workspace lives in one fixed 16 MiB device array inside the library (held
+ *   on every GPU that loads the library until the process exits): about 5
+ *   doubles per value of the state layout, plus d_in more with a network
+ *   coarse propagator (for Nx = 1024, P = 32 and a 2-input network, 1.9 MB).
+ *   A solve that needs more, or has more than 256 instances, returns
+ *   BS_EUNSUPPORTED and launches nothing.
+ *   The first call on each device looks up the array's device address; make
+ *   that first call before any stream capture.  All calls share the array and
+ *   it keeps the last call's contents; each call clears what must start at
+ *   zero.  Calls whose GPU work overlaps (different streams or host threads)
+ *   race on the array and must be serialised by the caller.
+ */
+int parareal_solve_static(bs_problem* prob, int coarse_kind, const pinn_model* model, int prec, double tol,
+                          int32_t max_iter, double* U_out, double* norms, bs_instance_stats* stats, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -573,3 +574,194 @@ int parareal_solve(bs_problem* prob, int coarse_kind, const pinn_model* model, i
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// parareal_solve_static: the same solve with its workspace in a fixed device
+// array instead of memory allocated on the problem handle.
+//
+// Who needs it: callers that must not allocate device memory once set-up is
+// done -- code that enqueues work while a stream is being captured, loops
+// where a cudaMalloc/cudaFree would synchronise the device and stall other
+// streams, and processes whose device memory is already reserved by another
+// allocator (parareal_solve allocates its workspace on the first call for a
+// problem).  This entry point calls no cudaMalloc, cudaFree or allocating
+// library routine.
+//
+// The array is a file-scope __device__ object of kStaticScratchBytes; every
+// GPU that loads this library keeps it until the process exits.  Its name is
+// only a host-side stand-in, so host code asks for its device address with
+// cudaGetSymbolAddress, once per device, on that device's first call.  That
+// first call should therefore come before any stream capture.  All calls share
+// the array and it keeps the previous call's contents: the parts that must
+// start cleared are cleared by each call, and calls whose work overlaps on the
+// GPU (two streams, or two host threads) race on it.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kStaticScratchBytes = 16u << 20;  // 16 MiB
+constexpr int kStaticMaxDevices = 64;
+constexpr int kStaticMaxInstances = 256;
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+std::mutex g_static_mu;
+void* g_static_addr[kStaticMaxDevices] = {};
+
+cudaError_t static_scratch_address(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kStaticMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess) return e;
+    g_static_addr[dev] = p;
+  }
+  *out = g_static_addr[dev];
+  return cudaSuccess;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" int parareal_solve_static(bs_problem* prob, int coarse_kind, const pinn_model* model, int prec,
+                                     double tol, int32_t max_iter, double* U_out, double* norms,
+                                     bs_instance_stats* stats, void* stream) {
+  if (!prob || !U_out || ((uintptr_t)U_out & 15) || max_iter < 1 || !(tol >= 0.0)) return BS_EINVAL;
+  if (coarse_kind < BS_COARSE_IE || coarse_kind > BS_COARSE_PINN_INCR) return BS_EINVAL;
+  const bool pinn = coarse_kind != BS_COARSE_IE;
+  if (pinn && !model) return BS_EINVAL;
+  if (pinn && (prec < BS_FP64 || prec > BS_BF16)) return BS_EINVAL;
+  const int n = prob->n_inst;
+  if (n > kStaticMaxInstances) return BS_EUNSUPPORTED;
+  const int d_in = pinn ? model->dev.d_in : 0;
+  // carve the fixed array: two state buffers, F, G_old, network table, grid
+  // points, norm partial sums, control words, norm history
+  size_t off = 0;
+  const size_t o_buf0 = off;
+  off = align256(off + sizeof(double) * prob->total_state);
+  const size_t o_buf1 = off;
+  off = align256(off + sizeof(double) * prob->total_state);
+  const size_t o_fbuf = off;
+  off = align256(off + sizeof(double) * prob->total_slice);
+  const size_t o_gold = off;
+  off = align256(off + sizeof(double) * prob->total_slice);
+  const size_t o_gtab = off;
+  off = align256(off + sizeof(double) * prob->total_state);
+  const size_t o_xg = off;
+  off = align256(off + sizeof(double) * prob->total_state * (size_t)d_in);
+  const size_t o_nb = off;
+  off = align256(off + sizeof(double) * 2 * prob->total_tasks1);
+  const size_t o_ctrl = off;
+  off = align256(off + sizeof(bsp::Ctrl) * n);
+  const size_t o_norms = off;
+  off = align256(off + sizeof(double) * (size_t)n * max_iter);
+  if (off > kStaticScratchBytes) return BS_EUNSUPPORTED;  // problem too large for the fixed array
+  void* base = nullptr;
+  cudaError_t e = static_scratch_address(&base);
+  if (e != cudaSuccess) return map_err(e);
+  unsigned char* b = static_cast<unsigned char*>(base);
+  double* buf0 = reinterpret_cast<double*>(b + o_buf0);
+  double* buf1 = reinterpret_cast<double*>(b + o_buf1);
+  double* fbuf = reinterpret_cast<double*>(b + o_fbuf);
+  double* gold = reinterpret_cast<double*>(b + o_gold);
+  double* gtab = reinterpret_cast<double*>(b + o_gtab);
+  double* xg = reinterpret_cast<double*>(b + o_xg);
+  double* nb = reinterpret_cast<double*>(b + o_nb);
+  bsp::Ctrl* ctrl = reinterpret_cast<bsp::Ctrl*>(b + o_ctrl);
+  double* nrm = reinterpret_cast<double*>(b + o_norms);
+  cudaStream_t s = (cudaStream_t)stream;
+  // the previous call's partial sums must not leak into this one
+  if ((e = cudaMemsetAsync(nb, 0, sizeof(double) * 2 * prob->total_tasks1, s)) != cudaSuccess) return map_err(e);
+  if (pinn) {
+    if ((e = bsp::launch_grid_points(prob->d_insts, n, d_in, xg, s)) != cudaSuccess) return map_err(e);
+    if ((e = bsp::launch_mlp_eval(model->dev, prec, xg, prob->total_state, gtab, nullptr, s)) != cudaSuccess)
+      return map_err(e);
+    if ((e = bsp::launch_table_fix(prob->d_insts, n, gtab, s)) != cudaSuccess) return map_err(e);
+  }
+  if ((e = bsp::launch_parareal_init(prob->d_insts, n, buf0, buf1, gtab, coarse_kind == BS_COARSE_PINN, ctrl, nrm,
+                                     max_iter, s)) != cudaSuccess)
+    return map_err(e);
+  const int sweep_kind = coarse_kind == BS_COARSE_IE ? 0 : 1;
+  auto sweep = [&](int k, double* cur, double* nxt) -> cudaError_t {
+    for (auto& c : prob->classes) {
+      bsp::SweepArgs a{};
+      a.insts = prob->d_insts;
+      a.ids = c.d_ids;
+      a.pool = prob->pool;
+      a.exptab = prob->exptab;
+      a.kind = sweep_kind;
+      a.k_iter = k;
+      a.ctrl = k < 0 ? nullptr : ctrl;
+      a.ucur = cur;
+      a.unext = nxt;
+      a.gold = gold;
+      a.fbuf = fbuf;
+      a.gtab = gtab;
+      a.normbuf = nb;
+      cudaError_t ee = bsp::launch_sweep(c.M, c.NW, a, (int)c.ids.size(), s);
+      if (ee != cudaSuccess) return ee;
+    }
+    return cudaSuccess;
+  };
+  if (coarse_kind != BS_COARSE_PINN) {
+    if ((e = sweep(-1, buf0, buf0)) != cudaSuccess) return map_err(e);
+  }
+  const int kmax = max_iter < prob->maxP ? max_iter : prob->maxP;
+  for (int k = 0; k < kmax; ++k) {
+    double* cur = (k & 1) ? buf1 : buf0;
+    double* nxt = (k & 1) ? buf0 : buf1;
+    for (auto& c : prob->classes) {
+      bsp::PropArgs a{};
+      a.insts = prob->d_insts;
+      a.ids = c.d_ids;
+      a.pool = prob->pool;
+      a.exptab = prob->exptab;
+      a.in = cur;
+      a.in_state = 1;
+      a.k_iter = k;
+      a.ctrl = ctrl;
+      if (coarse_kind == BS_COARSE_PINN) {
+        a.out = nxt;
+        a.out_state = 1;
+        a.mode = bsp::PropArgs::kPinnFused;
+        a.gtab = gtab;
+        a.uold = cur;
+        a.normbuf = nb;
+      } else {
+        a.out = fbuf;
+        a.out_state = 0;
+        a.mode = bsp::PropArgs::kPlain;
+      }
+      if ((e = bsp::launch_prop(c.M, c.NW, true, a, (int)c.ids.size(), c.maxP, s)) != cudaSuccess) return map_err(e);
+    }
+    if (coarse_kind != BS_COARSE_PINN) {
+      if ((e = sweep(k, cur, nxt)) != cudaSuccess) return map_err(e);
+    }
+    if ((e = bsp::launch_parareal_finalize(prob->d_insts, n, nb, k, tol, max_iter, ctrl, nrm, s)) != cudaSuccess)
+      return map_err(e);
+  }
+  if ((e = bsp::launch_copy_result(prob->d_insts, n, ctrl, buf0, buf1, U_out, s)) != cudaSuccess) return map_err(e);
+  if (!norms && !stats) return BS_OK;
+  bsp::Ctrl hc[kStaticMaxInstances];
+  if ((e = cudaMemcpyAsync(hc, ctrl, sizeof(bsp::Ctrl) * n, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return map_err(e);
+  if (norms &&
+      (e = cudaMemcpyAsync(norms, nrm, sizeof(double) * (size_t)n * max_iter, cudaMemcpyDeviceToHost, s)) !=
+          cudaSuccess)
+    return map_err(e);
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return map_err(e);
+  int worst = BS_OK;
+  for (int i = 0; i < n; ++i) {
+    if (stats) {
+      stats[i].iterations = hc[i].iterations;
+      stats[i].status = hc[i].status;
+      stats[i].final_norm = hc[i].last_norm;
+    }
+    if (hc[i].status != BS_OK && (worst == BS_OK || hc[i].status == BS_DIVERGED)) worst = hc[i].status;
+  }
+  return worst;
+}
