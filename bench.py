@@ -42,9 +42,9 @@ METRIC = "Parareal solves/s at 1e-6 vs serial fine"
 WORKLOAD = ("PINN-coarse Parareal, BS call K=1 sigma=0.2 r=0.05 T=1, Nx=1024 S in [0,4], P=32, "
             "CN 1024 steps/slice FP64, MLP 2->4x64 tanh trained 5k Adam steps on 16384+1024 points")
 FLOPS_PER_PT_STEP = 11.0  # CN right-hand side 5 + factored solve 6 (algorithmic, per interior point-step)
-# DRAM read+write bytes of one prop_kernel<8,4,CN> launch over all 32 slices (ncu, profiles/fine_cn_nx1024_p32.md);
-# set to None whenever the kernel changes until it is captured again
-FINE_TRAFFIC_BYTES = 368896
+# DRAM read+write bytes of one fine launch over all 32 slices from the ncu capture in profiles/;
+# None whenever the kernel has changed since the last capture
+FINE_TRAFFIC_BYTES = None
 
 
 def _peaks():
@@ -211,6 +211,8 @@ def run_ours(args):
     t0 = time.perf_counter()
     prob = B.Problem(CFG)
     setup_ms = (time.perf_counter() - t0) * 1e3
+    part = prob.partition(0)
+    fine_kernel_name = "prop_kernel<M={M},NW={NW},C={C},CN> ({C} CTA cluster per slice)".format(**part)
     model, train = train_network(B, torch, args.train_steps)
     Uf = prob.serial_fine()
     torch.cuda.synchronize()
@@ -305,7 +307,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": 8 * prob.total_state},
         "gpu_launches": 3 + 1 + 2 * kmax + 1,
         "roofline": {"bound": "alu", "achieved": fine_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
-                     "frac": fine_tflops / fp64_peak, "traffic": FINE_TRAFFIC_BYTES, "kernel": "prop_kernel<8,4,CN>",
+                     "frac": fine_tflops / fp64_peak, "traffic": FINE_TRAFFIC_BYTES, "kernel": fine_kernel_name,
                      "peak_note": "FP64: 148 SM x 2 DFMA lanes/clk (measured) x 2 flop x max SM clock"},
         "cpu_baseline": cpu,
         "clocks": clk.summary(),

@@ -84,11 +84,15 @@ const char* bs_version(void);
 /*
  * bs_problem_init -- set up n_instances pricing problems on the current device.
  *   p: host array of n_instances parameter sets.  Requirements per instance:
- *      K > 0, sigma > 0, r >= 0, T > 0, Smax > K, 5 <= Nx <= 4097, P >= 1,
+ *      K > 0, sigma > 0, r >= 0, T > 0, Smax > K, 5 <= Nx <= 65537, P >= 1,
  *      fine_steps >= 1, coarse_steps >= 1, all finite.
  *   Builds the Eq. 10 coefficients and factorises the Crank-Nicolson matrix
  *   (I - dtau_f/2 L) and the implicit Euler matrix (I - dtau_g L) on the
  *   device (Section 3.2), once; later calls reuse them.
+ *   Each grid is laid out over one CTA (one SM) or, when the problem has few
+ *   slices or more than 4096 rows, over a cluster of up to 16 CTAs that
+ *   exchange interface values through distributed shared memory; the
+ *   environment variable BSP_CLUSTER (1, 2, 4, 8, 16) overrides the choice.
  *   Synchronous.  *out receives the handle.  Errors: BS_EINVAL (argument),
  *   BS_EUNSUPPORTED (Nx above the largest grid this build keeps on chip),
  *   BS_ENOMEM, BS_ECUDA.
@@ -101,6 +105,9 @@ void bs_problem_destroy(bs_problem* prob);
 /* Instance count and the lengths (doubles) of state ((P+1)-slice) and slice (P-slice) arrays. */
 int bs_problem_info(const bs_problem* prob, int32_t* n_instances, int64_t* total_state_doubles,
                     int64_t* total_slice_doubles);
+
+/* Partition of instance i's grid: rows per thread M, warps per CTA NW, CTAs per grid C (cluster size). */
+int bs_problem_partition(const bs_problem* prob, int32_t i, int32_t* M, int32_t* NW, int32_t* C);
 
 /*
  * fine_propagate -- the fine propagator F of Eq. 6 on every slice at once:

@@ -68,6 +68,7 @@ def lib() -> ctypes.CDLL:
         L.bs_problem_destroy.argtypes = [vp]
         L.bs_problem_destroy.restype = None
         L.bs_problem_info.argtypes = [vp, P(i32), P(i64), P(i64)]
+        L.bs_problem_partition.argtypes = [vp, i32, P(i32), P(i32), P(i32)]
         for f in (L.fine_propagate, L.coarse_propagate):
             f.argtypes = [vp, vp, vp, vp, vp]
         L.serial_fine.argtypes = [vp, vp, vp]
@@ -163,6 +164,13 @@ class Problem:
             self.close()
         except Exception:
             pass
+
+    def partition(self, i: int = 0) -> dict:
+        """Rows per thread M, warps per CTA NW and CTAs per grid C chosen for instance i."""
+        M, NW, C = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().bs_problem_partition(self._h, i, ctypes.byref(M), ctypes.byref(NW), ctypes.byref(C)),
+               "bs_problem_partition")
+        return dict(M=M.value, NW=NW.value, C=C.value)
 
     # views -------------------------------------------------------------
     def state_view(self, U, i: int):

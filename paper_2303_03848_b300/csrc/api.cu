@@ -5,6 +5,7 @@
 // of solver.cu and pinn.cu.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -19,7 +20,7 @@ using bsp::Inst;
 namespace {
 
 struct Class {
-  int M = 0, NW = 0, maxP = 0;
+  int M = 0, NW = 0, C = 1, maxP = 0;
   std::vector<int32_t> ids;
   int32_t* d_ids = nullptr;
 };
@@ -39,18 +40,53 @@ int map_err(cudaError_t e) {
 
 bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 
-// Partition of the Nx-1 rows (interior + Dirichlet row at Smax) over NW warps
-// x 32 lanes x M rows.
-bool choose_partition(int Nx, int* M, int* NW) {
+// Partition of the Nx-1 rows (interior + Dirichlet row at Smax) over a
+// cluster of C CTAs x NW warps x 32 lanes x M rows.  cl_target is the number of
+// SMs one grid may occupy: the problem's slices share the 148 SMs, so few
+// slices spread each grid over a cluster of several CTAs (several SMs), many
+// slices keep one CTA per grid.  Grids above 4096 rows need a cluster.
+bool choose_partition(int Nx, int cl_target, int* M, int* NW, int* C) {
   const int rows = Nx - 1;
-  if (rows <= 64) { *NW = 1; *M = 2; return true; }
-  if (rows <= 128) { *NW = 2; *M = 2; return true; }
-  if (rows <= 256) { *NW = 4; *M = 2; return true; }
-  if (rows <= 512) { *NW = 4; *M = 4; return true; }
-  if (rows <= 1024) { *NW = 4; *M = 8; return true; }
-  if (rows <= 2048) { *NW = 4; *M = 16; return true; }
-  if (rows <= 4096) { *NW = 4; *M = 32; return true; }
+  if (rows <= 4096 && (cl_target <= 1 || rows < 2 * 4 * 32 * 2)) {
+    *C = 1;
+    if (rows <= 64) { *NW = 1; *M = 2; return true; }
+    if (rows <= 128) { *NW = 2; *M = 2; return true; }
+    *NW = 4;
+    int m = 2;
+    while (m * 128 < rows) m *= 2;
+    *M = m;
+    return true;
+  }
+  int c = 1;
+  while (c < cl_target && c < 16) c *= 2;
+  while (c * 4 * 32 * 2 > 2 * rows && c > 1) c /= 2;  // at most half of the rows padding
+  while (c * 4 * 32 * 32 < rows && c < 16) c *= 2;  // at most 32 rows per thread
+  for (; c >= 1; c /= 2) {
+    int m = 2;
+    while (m * 128 * c < rows && m < 32) m *= 2;
+    if (m * 128 * c < rows) return false;
+    if (bsp::partition_supported(m, 4, c)) {
+      *C = c;
+      *NW = 4;
+      *M = m;
+      return true;
+    }
+  }
   return false;
+}
+
+// SMs per grid from the number of slices that run at once (148 SMs), or the
+// BSP_CLUSTER environment variable (1, 2, 4, 8 or 16) when set.
+int cluster_target(const bs_params* p, int n) {
+  if (const char* env = getenv("BSP_CLUSTER")) {
+    const int v = atoi(env);
+    if (v >= 1 && v <= 16) return v;
+  }
+  int64_t slices = 0;
+  for (int i = 0; i < n; ++i) slices += p[i].P;
+  int c = 1;
+  while (c < 16 && slices * (2 * c) <= 148) c *= 2;
+  return c;
 }
 
 }  // namespace
@@ -62,7 +98,7 @@ struct bs_problem {
   double* pool = nullptr;
   double* exptab = nullptr;
   std::vector<Class> classes;
-  int64_t total_state = 0, total_slice = 0, total_tasks = 0, total_tasks1 = 0;
+  int64_t total_state = 0, total_slice = 0, total_tasks = 0, total_tasks1 = 0, total_norm = 0;
   int maxP = 0;
   // Parareal workspace (allocated on first use)
   double *buf0 = nullptr, *buf1 = nullptr, *fbuf = nullptr, *gold = nullptr, *gtab = nullptr, *normbuf = nullptr;
@@ -131,8 +167,11 @@ int bs_problem_init(const bs_params* p, int32_t n_instances, bs_problem** out) {
     if (!finite_pos(q.K) || !finite_pos(q.sigma) || !std::isfinite(q.r) || q.r < 0.0 || !finite_pos(q.T) ||
         !finite_pos(q.Smax) || !(q.Smax > q.K) || q.Nx < 5 || q.P < 1 || q.fine_steps < 1 || q.coarse_steps < 1)
       return BS_EINVAL;
-    int M, NW;
-    if (!choose_partition(q.Nx, &M, &NW)) return BS_EUNSUPPORTED;
+  }
+  const int cl_target = cluster_target(p, n_instances);
+  for (int i = 0; i < n_instances; ++i) {
+    int M, NW, C;
+    if (!choose_partition(p[i].Nx, cl_target, &M, &NW, &C)) return BS_EUNSUPPORTED;
   }
   bs_problem* prob = new (std::nothrow) bs_problem();
   if (!prob) return BS_ENOMEM;
@@ -152,10 +191,11 @@ int bs_problem_init(const bs_params* p, int32_t n_instances, bs_problem** out) {
     in.P = q.P;
     in.Mf = q.fine_steps;
     in.Mg = q.coarse_steps;
-    choose_partition(q.Nx, &in.M, &in.NW);
-    in.R = in.NW * 32 * in.M;
+    choose_partition(q.Nx, cl_target, &in.M, &in.NW, &in.C);
+    in.Ws = in.C * in.NW;
+    in.R = in.Ws * 32 * in.M;
     in.Np = in.R - (q.Nx - 1);
-    const int64_t bs = bsp::coef_block_size(in.M, in.NW * 32, in.NW);
+    const int64_t bs = bsp::coef_block_size(in.M, in.Ws * 32, in.Ws);
     in.coef_cn = coef;
     coef += bs;
     in.coef_ie = coef;
@@ -172,16 +212,19 @@ int bs_problem_init(const bs_params* p, int32_t n_instances, bs_problem** out) {
     prob->total_tasks += q.P;
     in.task1_off = prob->total_tasks1;
     prob->total_tasks1 += q.P + 1;
+    in.norm_off = prob->total_norm;
+    prob->total_norm += (int64_t)(q.P + 1) * in.C;
     if (q.P > prob->maxP) prob->maxP = q.P;
     prob->h_insts[i] = in;
     Class* cl = nullptr;
     for (auto& c : prob->classes)
-      if (c.M == in.M && c.NW == in.NW) cl = &c;
+      if (c.M == in.M && c.NW == in.NW && c.C == in.C) cl = &c;
     if (!cl) {
       prob->classes.push_back(Class{});
       cl = &prob->classes.back();
       cl->M = in.M;
       cl->NW = in.NW;
+      cl->C = in.C;
     }
     cl->ids.push_back(i);
     if (q.P > cl->maxP) cl->maxP = q.P;
@@ -197,7 +240,8 @@ int bs_problem_init(const bs_params* p, int32_t n_instances, bs_problem** out) {
     if (e == cudaSuccess) e = dalloc(&c.d_ids, c.ids.size());
     if (e == cudaSuccess)
       e = cudaMemcpy(c.d_ids, c.ids.data(), sizeof(int32_t) * c.ids.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = bsp::launch_setup(prob->d_insts, c.d_ids, (int)c.ids.size(), prob->pool, prob->exptab, 0);
+    if (e == cudaSuccess)
+      e = bsp::launch_setup(prob->d_insts, c.d_ids, (int)c.ids.size(), c.NW * c.C, prob->pool, prob->exptab, 0);
   }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
@@ -214,6 +258,14 @@ int bs_problem_info(const bs_problem* prob, int32_t* n_instances, int64_t* total
   if (n_instances) *n_instances = prob->n_inst;
   if (total_state_doubles) *total_state_doubles = prob->total_state;
   if (total_slice_doubles) *total_slice_doubles = prob->total_slice;
+  return BS_OK;
+}
+
+int bs_problem_partition(const bs_problem* prob, int32_t i, int32_t* M, int32_t* NW, int32_t* C) {
+  if (!prob || i < 0 || i >= prob->n_inst) return BS_EINVAL;
+  if (M) *M = prob->h_insts[i].M;
+  if (NW) *NW = prob->h_insts[i].NW;
+  if (C) *C = prob->h_insts[i].C;
   return BS_OK;
 }
 
@@ -238,7 +290,7 @@ static int propagate(bs_problem* prob, bool cn, const double* U_in, double* U_ou
     a.mode = bsp::PropArgs::kPlain;
     a.k_iter = -1;
     a.active = active;
-    cudaError_t e = bsp::launch_prop(c.M, c.NW, cn, a, (int)c.ids.size(), c.maxP, s);
+    cudaError_t e = bsp::launch_prop(c.M, c.NW, c.C, cn, a, (int)c.ids.size(), c.maxP, s);
     if (e != cudaSuccess) return map_err(e);
   }
   return BS_OK;
@@ -257,7 +309,7 @@ int serial_fine(bs_problem* prob, double* U_out, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   for (auto& c : prob->classes) {
     bsp::SerialArgs a{prob->d_insts, c.d_ids, prob->pool, prob->exptab, U_out};
-    cudaError_t e = bsp::launch_serial(c.M, c.NW, a, (int)c.ids.size(), s);
+    cudaError_t e = bsp::launch_serial(c.M, c.NW, c.C, a, (int)c.ids.size(), s);
     if (e != cudaSuccess) return map_err(e);
   }
   return BS_OK;
@@ -444,9 +496,9 @@ static cudaError_t ensure_parareal_ws(bs_problem* prob, int max_iter, int d_in) 
     if ((e = dalloc(&prob->fbuf, prob->total_slice)) != cudaSuccess) return e;
     if ((e = dalloc(&prob->gold, prob->total_slice)) != cudaSuccess) return e;
     if ((e = dalloc(&prob->gtab, prob->total_state)) != cudaSuccess) return e;
-    if ((e = dalloc(&prob->normbuf, 2 * prob->total_tasks1)) != cudaSuccess) return e;
+    if ((e = dalloc(&prob->normbuf, 2 * prob->total_norm)) != cudaSuccess) return e;
     if ((e = dalloc(&prob->ctrl, prob->n_inst)) != cudaSuccess) return e;
-    if ((e = cudaMemset(prob->normbuf, 0, sizeof(double) * 2 * prob->total_tasks1)) != cudaSuccess) return e;
+    if ((e = cudaMemset(prob->normbuf, 0, sizeof(double) * 2 * prob->total_norm)) != cudaSuccess) return e;
   }
   if (max_iter > prob->norms_cap) {
     cudaFree(prob->norms_dev);
@@ -505,7 +557,7 @@ int parareal_solve(bs_problem* prob, int coarse_kind, const pinn_model* model, i
       a.fbuf = prob->fbuf;
       a.gtab = prob->gtab;
       a.normbuf = prob->normbuf;
-      cudaError_t ee = bsp::launch_sweep(c.M, c.NW, a, (int)c.ids.size(), s);
+      cudaError_t ee = bsp::launch_sweep(c.M, c.NW, c.C, a, (int)c.ids.size(), s);
       if (ee != cudaSuccess) return ee;
     }
     return cudaSuccess;
@@ -540,7 +592,7 @@ int parareal_solve(bs_problem* prob, int coarse_kind, const pinn_model* model, i
         a.out_state = 0;
         a.mode = bsp::PropArgs::kPlain;
       }
-      if ((e = bsp::launch_prop(c.M, c.NW, true, a, (int)c.ids.size(), c.maxP, s)) != cudaSuccess) return map_err(e);
+      if ((e = bsp::launch_prop(c.M, c.NW, c.C, true, a, (int)c.ids.size(), c.maxP, s)) != cudaSuccess) return map_err(e);
     }
     // a4 + a5: serial coarse sweep with the correction
     if (coarse_kind != BS_COARSE_PINN) {
@@ -654,7 +706,7 @@ extern "C" int parareal_solve_static(bs_problem* prob, int coarse_kind, const pi
   const size_t o_xg = off;
   off = align256(off + sizeof(double) * prob->total_state * (size_t)d_in);
   const size_t o_nb = off;
-  off = align256(off + sizeof(double) * 2 * prob->total_tasks1);
+  off = align256(off + sizeof(double) * 2 * prob->total_norm);
   const size_t o_ctrl = off;
   off = align256(off + sizeof(bsp::Ctrl) * n);
   const size_t o_norms = off;
@@ -675,7 +727,7 @@ extern "C" int parareal_solve_static(bs_problem* prob, int coarse_kind, const pi
   double* nrm = reinterpret_cast<double*>(b + o_norms);
   cudaStream_t s = (cudaStream_t)stream;
   // the previous call's partial sums must not leak into this one
-  if ((e = cudaMemsetAsync(nb, 0, sizeof(double) * 2 * prob->total_tasks1, s)) != cudaSuccess) return map_err(e);
+  if ((e = cudaMemsetAsync(nb, 0, sizeof(double) * 2 * prob->total_norm, s)) != cudaSuccess) return map_err(e);
   if (pinn) {
     if ((e = bsp::launch_grid_points(prob->d_insts, n, d_in, xg, s)) != cudaSuccess) return map_err(e);
     if ((e = bsp::launch_mlp_eval(model->dev, prec, xg, prob->total_state, gtab, nullptr, s)) != cudaSuccess)
@@ -702,7 +754,7 @@ extern "C" int parareal_solve_static(bs_problem* prob, int coarse_kind, const pi
       a.fbuf = fbuf;
       a.gtab = gtab;
       a.normbuf = nb;
-      cudaError_t ee = bsp::launch_sweep(c.M, c.NW, a, (int)c.ids.size(), s);
+      cudaError_t ee = bsp::launch_sweep(c.M, c.NW, c.C, a, (int)c.ids.size(), s);
       if (ee != cudaSuccess) return ee;
     }
     return cudaSuccess;
@@ -736,7 +788,7 @@ extern "C" int parareal_solve_static(bs_problem* prob, int coarse_kind, const pi
         a.out_state = 0;
         a.mode = bsp::PropArgs::kPlain;
       }
-      if ((e = bsp::launch_prop(c.M, c.NW, true, a, (int)c.ids.size(), c.maxP, s)) != cudaSuccess) return map_err(e);
+      if ((e = bsp::launch_prop(c.M, c.NW, c.C, true, a, (int)c.ids.size(), c.maxP, s)) != cudaSuccess) return map_err(e);
     }
     if (coarse_kind != BS_COARSE_PINN) {
       if ((e = sweep(k, cur, nxt)) != cudaSuccess) return map_err(e);

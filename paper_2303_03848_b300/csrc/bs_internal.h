@@ -25,7 +25,7 @@ struct PropArgs {
   const Ctrl* ctrl;          // nullable, done flags
   const double* gtab;        // kPinnFused: network table (state layout)
   const double* uold;        // kPinnFused: U^k (state layout)
-  double* normbuf;           // kPinnFused: (num, den) per (instance, boundary index)
+  double* normbuf;           // kPinnFused: (num, den) per (instance, boundary index, cluster rank)
 };
 
 struct SerialArgs {
@@ -52,11 +52,12 @@ struct SweepArgs {
   double* normbuf;
 };
 
-cudaError_t launch_setup(const Inst* d_insts, const int32_t* d_ids, int n, double* pool, double* exptab,
+bool partition_supported(int M, int NW, int C);
+cudaError_t launch_setup(const Inst* d_insts, const int32_t* d_ids, int n, int Ws, double* pool, double* exptab,
                          cudaStream_t s);
-cudaError_t launch_prop(int M, int NW, bool cn, const PropArgs& a, int n_inst, int maxP, cudaStream_t s);
-cudaError_t launch_serial(int M, int NW, const SerialArgs& a, int n_inst, cudaStream_t s);
-cudaError_t launch_sweep(int M, int NW, const SweepArgs& a, int n_inst, cudaStream_t s);
+cudaError_t launch_prop(int M, int NW, int C, bool cn, const PropArgs& a, int n_inst, int maxP, cudaStream_t s);
+cudaError_t launch_serial(int M, int NW, int C, const SerialArgs& a, int n_inst, cudaStream_t s);
+cudaError_t launch_sweep(int M, int NW, int C, const SweepArgs& a, int n_inst, cudaStream_t s);
 cudaError_t launch_parareal_init(const Inst* d_insts, int n_inst, double* buf0, double* buf1, const double* gtab,
                                  int pinn, Ctrl* ctrl, double* norms, int max_iter, cudaStream_t s);
 cudaError_t launch_parareal_finalize(const Inst* d_insts, int n_inst, const double* normbuf, int k, double tol,

@@ -6,24 +6,31 @@
 //
 // FP64 on this part issues one warp-wide DFMA per 64 cycles per SM
 // sub-partition with a dependent-issue latency of the same length, so the
-// cost of a step is the number of warp-level FP64 instructions it issues.  The
-// design keeps that count near 5 per grid row per step:
+// cost of a step is the number of warp-level FP64 instructions it issues and
+// the latency of whatever else sits on its critical path.  The design keeps
+// the FP64 count near 5 per grid row per step:
 //   * Crank-Nicolson is rewritten with Z = V^{m+1} + V^m:
 //       (I - h L) Z = 2 V^m + boundary,  V^{m+1} = Z - V^m,  h = dtau/2,
 //     and the state is carried scaled, W = 2 V / delta (delta = local LU
 //     pivots), so the forward sweep needs no separate right-hand side product.
 //   * Each thread eliminates its M-1 inner rows with a local Thomas sweep
 //     (factorised once at set-up); the M-th row of every thread forms a
-//     tridiagonal interface system that one warp solves by parallel cyclic
-//     reduction over shuffles (multipliers precomputed); a tiny dense system
-//     couples the warps of a CTA.  A final fixup adds the interface responses
-//     to the inner rows.
+//     tridiagonal interface system that each warp reduces by parallel cyclic
+//     reduction over shuffles (multipliers precomputed); the warps' lane-31
+//     unknowns form a small system across the CTA -- or across a cluster of
+//     CTAs that shares one grid over several SMs -- solved with a precomputed
+//     inverse after one barrier per step.  A final fixup adds the interface
+//     responses to the inner rows.
 // The whole grid stays in registers and shared memory for all steps of a slice.
+#include <cooperative_groups.h>
+
 #include <cmath>
 #include <cstdio>
 
 #include "bs_common.cuh"
 #include "bs_internal.h"
+
+namespace cg = cooperative_groups;
 
 namespace bsp {
 
@@ -52,32 +59,36 @@ __device__ inline void mat_row(const Inst& in, double h, int r, double& l, doubl
   u = -h * c;
 }
 
-__global__ void __launch_bounds__(128) setup_kernel(const Inst* insts, const int32_t* ids, double* pool,
-                                                    double* exptab) {
-  const Inst in = insts[ids[blockIdx.x]];
-  const int kind = blockIdx.y;  // 0: Crank-Nicolson (fine), 1: implicit Euler (coarse)
-  const int NW = in.NW, M = in.M, T = NW * 32;
-  const int t = threadIdx.x;
-  const int L = t & 31;
-  const int steps = kind == 0 ? in.Mf : in.Mg;
+__device__ inline void kind_consts(const Inst& in, int kind, double& h, double& crhs, int& steps) {
+  steps = kind == 0 ? in.Mf : in.Mg;
   const double dt = in.T / ((double)in.P * (double)steps);
-  const double h = kind == 0 ? 0.5 * dt : dt;
-  const double crhs = kind == 0 ? 2.0 : 1.0;
-  double* cb = pool + (kind == 0 ? in.coef_cn : in.coef_ie);
-  double* et = exptab + (kind == 0 ? in.exp_cn : in.exp_ie);
+  h = kind == 0 ? 0.5 * dt : dt;
+  crhs = kind == 0 ? 2.0 : 1.0;
+}
 
-  __shared__ double s_alp0[128], s_bet0[128], s_A[128], s_C[128], s_ra[128], s_rc[128];
-
-  for (int m = t; m <= steps; m += blockDim.x) et[m] = exp(-in.r * ((double)m * dt));
-
-  const bool act = t < T;
-  double alp_last = 0.0, bet_last = 0.0;
-  if (act) {
-    // local LU of the M-1 inner rows of thread t
+// Phase 1, one warp per (warp of the partition, instance): local LU of each
+// thread's inner rows and their responses to the two neighbouring interfaces.
+__global__ void __launch_bounds__(32) setup_rows_kernel(const Inst* insts, const int32_t* ids, double* pool,
+                                                        double* exptab) {
+  const Inst in = insts[ids[blockIdx.y]];
+  const int w = blockIdx.x;
+  if (w >= in.Ws) return;
+  const int M = in.M, GT = in.Ws * 32;
+  const int g = w * 32 + threadIdx.x;
+  for (int kind = 0; kind < 2; ++kind) {
+    double h, crhs;
+    int steps;
+    kind_consts(in, kind, h, crhs, steps);
+    double* cb = pool + (kind == 0 ? in.coef_cn : in.coef_ie);
+    if (w == 0) {
+      double* et = exptab + (kind == 0 ? in.exp_cn : in.exp_ie);
+      const double dt = in.T / ((double)in.P * (double)steps);
+      for (int m = threadIdx.x; m <= steps; m += 32) et[m] = exp(-in.r * ((double)m * dt));
+    }
     double lam[32], mu[32], del[32];
     double prev_u = 0.0;
     for (int k = 0; k < M - 1; ++k) {
-      const int r = t * M + k;
+      const int r = g * M + k;
       double l, d, u;
       mat_row(in, h, r, l, d, u);
       del[k] = (k == 0) ? d : d - l * (prev_u / del[k - 1]);
@@ -85,56 +96,72 @@ __global__ void __launch_bounds__(128) setup_kernel(const Inst* insts, const int
       mu[k] = u / del[k];
       prev_u = u;
       const bool pad = r < in.Np;
-      cb[coef_rows_off(0, k, t, M, T)] = lam[k];
-      cb[coef_rows_off(1, k, t, M, T)] = mu[k];
-      cb[coef_rows_off(2, k, t, M, T)] = pad ? 0.0 : crhs / del[k];
-      cb[coef_rows_off(5, k, t, M, T)] = pad ? 0.0 : del[k] / crhs;
+      cb[coef_rows_off(0, k, g, M, GT)] = lam[k];
+      cb[coef_rows_off(1, k, g, M, GT)] = mu[k];
+      cb[coef_rows_off(2, k, g, M, GT)] = pad ? 0.0 : crhs / del[k];
+      cb[coef_rows_off(5, k, g, M, GT)] = pad ? 0.0 : del[k] / crhs;
     }
-    // responses of the inner rows to the left interface X_{t-1} (alpha) and
-    // the right interface X_t (beta)
     double phi[32];
     phi[0] = -lam[0];
     for (int k = 1; k < M - 1; ++k) phi[k] = -lam[k] * phi[k - 1];
     double alp = phi[M - 2], bet = -mu[M - 2];
-    cb[coef_rows_off(3, M - 2, t, M, T)] = alp;
-    cb[coef_rows_off(4, M - 2, t, M, T)] = bet;
-    alp_last = alp;
-    bet_last = bet;
+    cb[coef_rows_off(3, M - 2, g, M, GT)] = alp;
+    cb[coef_rows_off(4, M - 2, g, M, GT)] = bet;
+    cb[coef_scr_off(2, g, M, GT)] = alp;
+    cb[coef_scr_off(3, g, M, GT)] = bet;
     for (int k = M - 3; k >= 0; --k) {
       alp = phi[k] - mu[k] * alp;
       bet = -mu[k] * bet;
-      cb[coef_rows_off(3, k, t, M, T)] = alp;
-      cb[coef_rows_off(4, k, t, M, T)] = bet;
+      cb[coef_rows_off(3, k, g, M, GT)] = alp;
+      cb[coef_rows_off(4, k, g, M, GT)] = bet;
     }
-    for (int q = 0; q < 6; ++q) cb[coef_rows_off(q, M - 1, t, M, T)] = 0.0;  // interface row slots unused
-    s_alp0[t] = alp;
-    s_bet0[t] = bet;
+    cb[coef_scr_off(0, g, M, GT)] = alp;
+    cb[coef_scr_off(1, g, M, GT)] = bet;
+    for (int q = 0; q < 6; ++q) cb[coef_rows_off(q, M - 1, g, M, GT)] = 0.0;  // interface row slots unused
   }
-  __syncthreads();
-  if (act) {
+}
+
+// Phase 2: interface rows, in-warp PCR multipliers and responses.
+__global__ void __launch_bounds__(32) setup_iface_kernel(const Inst* insts, const int32_t* ids, double* pool) {
+  const Inst in = insts[ids[blockIdx.y]];
+  const int w = blockIdx.x;
+  if (w >= in.Ws) return;
+  const int M = in.M, GT = in.Ws * 32, Ws = in.Ws;
+  const int L = threadIdx.x, g = w * 32 + L;
+  for (int kind = 0; kind < 2; ++kind) {
+    double h, crhs;
+    int steps;
+    kind_consts(in, kind, h, crhs, steps);
+    double* cb = pool + (kind == 0 ? in.coef_cn : in.coef_ie);
     double A = 0.0, C = 0.0, kap = 0.0, nu = 0.0, sigp = 0.0, isigp = 0.0;
-    if (t < T - 1) {
+    if (g < GT - 1) {
       // interface row p: l x_{p-1} + d x_p + u x_{p+1} = r_p with the inner
       // neighbours written through their interface responses, divided by D
-      const int p = t * M + M - 1;
+      const int p = g * M + M - 1;
       double l, d, u;
       mat_row(in, h, p, l, d, u);
-      const double D = d + l * bet_last + u * s_alp0[t + 1];
-      A = l * alp_last / D;
-      C = u * s_bet0[t + 1] / D;
+      const double a_last = cb[coef_scr_off(2, g, M, GT)], b_last = cb[coef_scr_off(3, g, M, GT)];
+      const double a_next = cb[coef_scr_off(0, g + 1, M, GT)], b_next = cb[coef_scr_off(1, g + 1, M, GT)];
+      const double D = d + l * b_last + u * a_next;
+      A = l * a_last / D;
+      C = u * b_next / D;
       kap = l / D;
       nu = u / D;
       const bool pad = p < in.Np;
       sigp = pad ? 0.0 : crhs / D;
       isigp = pad ? 0.0 : D / crhs;
     }
-    cb[coef_if_off(0, t, M, T)] = kap;
-    cb[coef_if_off(1, t, M, T)] = nu;
-    cb[coef_if_off(2, t, M, T)] = sigp;
-    cb[coef_if_off(3, t, M, T)] = isigp;
-    cb[coef_if_off(4, t, M, T)] = A;
-    cb[coef_if_off(5, t, M, T)] = C;
-
+    cb[coef_if_off(0, g, M, GT)] = kap;
+    cb[coef_if_off(1, g, M, GT)] = nu;
+    cb[coef_if_off(2, g, M, GT)] = sigp;
+    cb[coef_if_off(3, g, M, GT)] = isigp;
+    cb[coef_if_off(4, g, M, GT)] = A;
+    cb[coef_if_off(5, g, M, GT)] = C;
+    if (L == 31) {
+      cb[coef_warp_off(0, w, M, GT, Ws)] = nu;
+      cb[coef_warp_off(1, w, M, GT, Ws)] = A;
+      cb[coef_warp_off(2, w, M, GT, Ws)] = C;
+    }
     // PCR multipliers of the in-warp interface system with zero external
     // couplings (lane 31 is the warp's cross-warp unknown, solved separately).
     double a_ = (L == 0 || L == 31) ? 0.0 : A;
@@ -159,11 +186,11 @@ __global__ void __launch_bounds__(128) setup_kernel(const Inst* insts, const int
       d_ = nd;
       m1[lv] = k1;
       m2[lv] = k2;
-      cb[coef_pcr_off(lv, t, M, T)] = k1;
-      cb[coef_pcr_off(5 + lv, t, M, T)] = k2;
+      cb[coef_pcr_off(lv, g, M, GT)] = k1;
+      cb[coef_pcr_off(5 + lv, g, M, GT)] = k2;
     }
     const double inv = 1.0 / d_;
-    cb[coef_pcr_off(10, t, M, T)] = inv;
+    cb[coef_pcr_off(10, g, M, GT)] = inv;
     // responses of lanes 0..30 to Y_{w-1} (enters lane 0 as -A) and Y_w
     // (enters lane 30 as -C), with the same recursion the step uses
     double ea = (L == 0) ? -A : 0.0, ec = (L == 30) ? -C : 0.0;
@@ -175,53 +202,75 @@ __global__ void __launch_bounds__(128) setup_kernel(const Inst* insts, const int
       ea = fma(-m1[lv], ua, fma(-m2[lv], da, ea));
       ec = fma(-m1[lv], uc, fma(-m2[lv], dc, ec));
     }
-    const double ra = (L == 31) ? 0.0 : ea * inv;
-    const double rc = (L == 31) ? 0.0 : ec * inv;
-    cb[coef_resp_off(0, t, M, T)] = ra;
-    cb[coef_resp_off(1, t, M, T)] = rc;
-    s_A[t] = A;
-    s_C[t] = C;
-    s_ra[t] = ra;
-    s_rc[t] = rc;
+    cb[coef_resp_off(0, g, M, GT)] = (L == 31) ? 0.0 : ea * inv;
+    cb[coef_resp_off(1, g, M, GT)] = (L == 31) ? 0.0 : ec * inv;
+  }
+}
+
+// Phase 3, one CTA per (instance, propagator): the cross-warp system over
+// Y_w = X at lane 31 of warp w (Y_{Ws-1} is the Dirichlet row) and its inverse
+// by Gauss-Jordan with partial pivoting.
+__global__ void __launch_bounds__(128) setup_cross_kernel(const Inst* insts, const int32_t* ids, double* pool) {
+  extern __shared__ double mx_raw[];
+  __shared__ int s_piv;
+  const Inst in = insts[ids[blockIdx.x]];
+  const int kind = blockIdx.y;
+  const int M = in.M, GT = in.Ws * 32, Ws = in.Ws;
+  const int ld = 2 * Ws + 1;
+  auto Mx = [&](int i) -> double* { return mx_raw + (size_t)i * ld; };
+  double* cb = pool + (kind == 0 ? in.coef_cn : in.coef_ie);
+  const int t = threadIdx.x;
+  for (int e = t; e < Ws * 2 * Ws; e += blockDim.x) {
+    const int i = e / (2 * Ws), j = e % (2 * Ws);
+    Mx(i)[j] = (j == Ws + i) ? 1.0 : 0.0;
   }
   __syncthreads();
-  if (t == 0) {
-    // cross-warp system over Y_w = X at lane 31 of warp w; Y_{NW-1} is the Dirichlet row
-    double Mx[kMaxNW][2 * kMaxNW];
-    for (int i = 0; i < NW; ++i)
-      for (int j = 0; j < 2 * NW; ++j) Mx[i][j] = (j == NW + i) ? 1.0 : 0.0;
-    for (int w = 0; w < NW; ++w) {
-      if (w == NW - 1) {
-        Mx[w][w] = 1.0;
-        continue;
-      }
-      const int t31 = 32 * w + 31, t30 = 32 * w + 30, tn0 = 32 * (w + 1);
-      const double A31 = s_A[t31], C31 = s_C[t31];
-      if (w > 0) Mx[w][w - 1] = A31 * s_ra[t30];
-      Mx[w][w] = 1.0 + A31 * s_rc[t30] + C31 * s_ra[tn0];
-      Mx[w][w + 1] = C31 * s_rc[tn0];
+  for (int w = t; w < Ws; w += blockDim.x) {
+    if (w == Ws - 1) {
+      Mx(w)[w] = 1.0;
+      continue;
     }
-    // Gauss-Jordan with partial pivoting
-    for (int c = 0; c < NW; ++c) {
+    const int t30 = 32 * w + 30, tn0 = 32 * (w + 1);
+    const double A31 = cb[coef_warp_off(1, w, M, GT, Ws)], C31 = cb[coef_warp_off(2, w, M, GT, Ws)];
+    const double ra30 = cb[coef_resp_off(0, t30, M, GT)], rc30 = cb[coef_resp_off(1, t30, M, GT)];
+    const double ra0 = cb[coef_resp_off(0, tn0, M, GT)], rc0 = cb[coef_resp_off(1, tn0, M, GT)];
+    if (w > 0) Mx(w)[w - 1] = A31 * ra30;
+    Mx(w)[w] = 1.0 + A31 * rc30 + C31 * ra0;
+    Mx(w)[w + 1] = C31 * rc0;
+  }
+  __syncthreads();
+  for (int c = 0; c < Ws; ++c) {
+    if (t == 0) {
       int piv = c;
-      for (int i = c + 1; i < NW; ++i)
-        if (fabs(Mx[i][c]) > fabs(Mx[piv][c])) piv = i;
-      if (piv != c)
-        for (int j = 0; j < 2 * NW; ++j) {
-          const double tmp = Mx[c][j];
-          Mx[c][j] = Mx[piv][j];
-          Mx[piv][j] = tmp;
-        }
-      const double ip = 1.0 / Mx[c][c];
-      for (int j = 0; j < 2 * NW; ++j) Mx[c][j] *= ip;
-      for (int i = 0; i < NW; ++i) {
-        if (i == c) continue;
-        const double f = Mx[i][c];
-        for (int j = 0; j < 2 * NW; ++j) Mx[i][j] -= f * Mx[c][j];
-      }
+      for (int i = c + 1; i < Ws; ++i)
+        if (fabs(Mx(i)[c]) > fabs(Mx(piv)[c])) piv = i;
+      s_piv = piv;
     }
-    for (int v = 0; v < NW; ++v)
-      for (int u = 0; u < NW; ++u) cb[coef_G_off(v, u, M, T, NW)] = Mx[v][NW + u];
+    __syncthreads();
+    const int piv = s_piv;
+    if (piv != c)
+      for (int j = t; j < 2 * Ws; j += blockDim.x) {
+        const double tmp = Mx(c)[j];
+        Mx(c)[j] = Mx(piv)[j];
+        Mx(piv)[j] = tmp;
+      }
+    __syncthreads();
+    const double ip = 1.0 / Mx(c)[c];
+    __syncthreads();
+    for (int j = t; j < 2 * Ws; j += blockDim.x) Mx(c)[j] *= ip;
+    __syncthreads();
+    for (int e = t; e < Ws * 2 * Ws; e += blockDim.x) {
+      const int i = e / (2 * Ws), j = e % (2 * Ws);
+      if (i != c && j != c) Mx(i)[j] -= Mx(i)[c] * Mx(c)[j];
+    }
+    __syncthreads();
+    for (int i = t; i < Ws; i += blockDim.x)
+      if (i != c) Mx(i)[c] = 0.0;
+    __syncthreads();
+  }
+  for (int e = t; e < Ws * Ws; e += blockDim.x) {
+    const int v = e / Ws, u = e % Ws;
+    cb[coef_G_off(v, u, M, GT, Ws)] = Mx(v)[Ws + u];
   }
 }
 
@@ -229,11 +278,13 @@ __global__ void __launch_bounds__(128) setup_kernel(const Inst* insts, const int
 // One time step of the partitioned solver.
 // ---------------------------------------------------------------------------
 
-template <int M, int NW>
+template <int M, int NW, int C>
 struct SolverSmem {
-  double rows[5][M][NW * 32];  // lambda, mu, sigma, alpha, beta
-  double A31[NW], C31[NW], G[NW * NW];
-  double x0[NW], X0[NW], X30[NW], R31[NW];
+  static constexpr int T = NW * 32, Ws = C * NW;
+  double rows[5][M][T];     // lambda, mu, sigma, alpha, beta of this CTA's threads
+  double G2[NW][2][Ws];     // rows w-1 and w of the cross-warp inverse, per local warp
+  double nu31[Ws], A31[Ws], C31[Ws];
+  double pub[2][4][Ws];     // [step parity][x0, X0, X30, R31][global warp], written by every CTA
   double red[2][NW];
 };
 
@@ -242,52 +293,79 @@ struct SolverRegs {
   double m1[kPcrLevels], m2[kPcrLevels], inv, ra, rc;
 };
 
-template <int M, int NW>
-__device__ __forceinline__ void load_solver(const double* __restrict__ cb, SolverSmem<M, NW>& sm, SolverRegs& rg) {
-  constexpr int T = NW * 32;
-  const int t = threadIdx.x;
-  double* dst = &sm.rows[0][0][0];
-  for (int i = t; i < 5 * M * T; i += T) dst[i] = cb[i];  // rows [q][k][t], q = 0..4, same order
-  rg.kap = cb[coef_if_off(0, t, M, T)];
-  rg.nu = cb[coef_if_off(1, t, M, T)];
-  rg.sigp = cb[coef_if_off(2, t, M, T)];
-  rg.isigp = cb[coef_if_off(3, t, M, T)];
+template <int C>
+__device__ __forceinline__ int cta_rank() {
+  if constexpr (C == 1) {
+    return 0;
+  } else {
+    return (int)cg::this_cluster().block_rank();
+  }
+}
+
+template <int C>
+__device__ __forceinline__ void step_barrier() {
+  if constexpr (C == 1) {
+    __syncthreads();
+  } else {
+    cg::this_cluster().sync();
+  }
+}
+
+template <int M, int NW, int C>
+__device__ __forceinline__ void load_solver(const double* __restrict__ cb, SolverSmem<M, NW, C>& sm,
+                                            SolverRegs& rg) {
+  constexpr int T = NW * 32, Ws = C * NW, GT = C * T;
+  const int t = threadIdx.x, c = cta_rank<C>();
+  const int g = c * T + t;
+  for (int q = 0; q < 5; ++q)
+    for (int k = 0; k < M; ++k) sm.rows[q][k][t] = cb[coef_rows_off(q, k, g, M, GT)];
+  rg.kap = cb[coef_if_off(0, g, M, GT)];
+  rg.nu = cb[coef_if_off(1, g, M, GT)];
+  rg.sigp = cb[coef_if_off(2, g, M, GT)];
+  rg.isigp = cb[coef_if_off(3, g, M, GT)];
 #pragma unroll
   for (int lv = 0; lv < kPcrLevels; ++lv) {
-    rg.m1[lv] = cb[coef_pcr_off(lv, t, M, T)];
-    rg.m2[lv] = cb[coef_pcr_off(5 + lv, t, M, T)];
+    rg.m1[lv] = cb[coef_pcr_off(lv, g, M, GT)];
+    rg.m2[lv] = cb[coef_pcr_off(5 + lv, g, M, GT)];
   }
-  rg.inv = cb[coef_pcr_off(10, t, M, T)];
-  rg.ra = cb[coef_resp_off(0, t, M, T)];
-  rg.rc = cb[coef_resp_off(1, t, M, T)];
-  if (t < NW) {
-    sm.A31[t] = cb[coef_if_off(4, 32 * t + 31, M, T)];
-    sm.C31[t] = cb[coef_if_off(5, 32 * t + 31, M, T)];
+  rg.inv = cb[coef_pcr_off(10, g, M, GT)];
+  rg.ra = cb[coef_resp_off(0, g, M, GT)];
+  rg.rc = cb[coef_resp_off(1, g, M, GT)];
+  for (int i = t; i < Ws; i += T) {
+    sm.nu31[i] = cb[coef_warp_off(0, i, M, GT, Ws)];
+    sm.A31[i] = cb[coef_warp_off(1, i, M, GT, Ws)];
+    sm.C31[i] = cb[coef_warp_off(2, i, M, GT, Ws)];
   }
-  if (t < NW * NW) sm.G[t] = cb[coef_G_off(t / NW, t % NW, M, T, NW)];
+  for (int i = t; i < NW * 2 * Ws; i += T) {
+    const int wl = i / (2 * Ws), side = (i / Ws) % 2, u = i % Ws;
+    const int row = c * NW + wl - 1 + side;  // global warp w-1 (side 0) or w (side 1)
+    sm.G2[wl][side][u] = row >= 0 ? cb[coef_G_off(row, u, M, GT, Ws)] : 0.0;
+  }
   __syncthreads();
 }
 
 // x receives the solution of the step (Z for Crank-Nicolson, V^{m+1} for
 // implicit Euler) on the thread's rows; W is advanced to the next scaled state.
-template <int M, int NW, bool CN>
-__device__ __forceinline__ void tri_step(double (&W)[M], double (&x)[M], SolverSmem<M, NW>& sm, const SolverRegs& rg,
-                                         double Zb) {
-  constexpr int T = NW * 32;
-  const int t = threadIdx.x, L = t & 31, w = t >> 5;
+// Zb is the Dirichlet value of the step (used by the grid's last thread).
+template <int M, int NW, int C, bool CN>
+__device__ __forceinline__ void tri_step(double (&W)[M], double (&x)[M], SolverSmem<M, NW, C>& sm,
+                                         const SolverRegs& rg, double Zb, int par) {
+  constexpr int Ws = C * NW;
+  const int t = threadIdx.x, L = t & 31, wl = t >> 5;
+  const int c = cta_rank<C>();
+  const int w = c * NW + wl;
   // 1. local forward and backward sweeps over the inner rows (zero interfaces)
   x[0] = W[0];
 #pragma unroll
   for (int k = 1; k <= M - 2; ++k) x[k] = fma(-sm.rows[0][k][t], x[k - 1], W[k]);
 #pragma unroll
   for (int k = M - 3; k >= 0; --k) x[k] = fma(-sm.rows[1][k][t], x[k + 1], x[k]);
-  // 2. interface right-hand side: needs the first inner value of thread t+1
-  double xs_next = __shfl_down_sync(kFull, x[0], 1);
-  if (L == 0) sm.x0[w] = x[0];
-  __syncthreads();
-  if (L == 31) xs_next = (w + 1 < NW) ? sm.x0[w + 1] : 0.0;
-  double R = fma(-rg.nu, xs_next, fma(-rg.kap, x[M - 2], W[M - 1]));
-  if (t == T - 1) R = Zb;  // Dirichlet row at Smax
+  // 2. interface right-hand side; lane 31 completes its term with the next
+  //    warp's first inner value after the barrier
+  const double xs_next = __shfl_down_sync(kFull, x[0], 1);
+  double R = fma(-rg.kap, x[M - 2], W[M - 1]);
+  if (L != 31) R = fma(-rg.nu, xs_next, R);
+  if (w == Ws - 1 && L == 31) R = Zb;  // Dirichlet row at Smax
   // 3. in-warp PCR on lanes 0..30 with zero external couplings
   double Rp = (L == 31) ? 0.0 : R;
 #pragma unroll
@@ -298,30 +376,58 @@ __device__ __forceinline__ void tri_step(double (&W)[M], double (&x)[M], SolverS
     Rp = fma(-rg.m1[lv], up, fma(-rg.m2[lv], dn, Rp));
   }
   const double Xt = Rp * rg.inv;
-  if (L == 0) sm.X0[w] = Xt;
-  if (L == 30) sm.X30[w] = Xt;
-  if (L == 31) sm.R31[w] = R;
-  __syncthreads();
-  // 4. cross-warp unknowns Y_u (lane 31 of warp u): rho_u by lane u, then
-  //    Y_{w-1} (lane 0) and Y_w (lane 1) from the precomputed inverse
-  double rho = 0.0;
-  if (L < NW) {
-    rho = (L == NW - 1) ? sm.R31[L] : fma(-sm.C31[L], sm.X0[L + 1], fma(-sm.A31[L], sm.X30[L], sm.R31[L]));
+  // 4. publish this warp's boundary values to every CTA of the grid, one barrier
+  const double p0 = __shfl_sync(kFull, x[0], 0);
+  const double p1 = __shfl_sync(kFull, Xt, 0);
+  const double p2 = __shfl_sync(kFull, Xt, 30);
+  const double p3 = __shfl_sync(kFull, R, 31);
+  if constexpr (C == 1) {
+    if (L == 0) {
+      sm.pub[par][0][w] = p0;
+      sm.pub[par][1][w] = p1;
+      sm.pub[par][2][w] = p2;
+      sm.pub[par][3][w] = p3;
+    }
+  } else {
+    if (L < C) {
+      double* rp = cg::this_cluster().map_shared_rank(&sm.pub[par][0][0], L);
+      rp[0 * Ws + w] = p0;
+      rp[1 * Ws + w] = p1;
+      rp[2 * Ws + w] = p2;
+      rp[3 * Ws + w] = p3;
+    }
   }
-  const int grow = (L == 0) ? w - 1 : w;
-  double y = 0.0;
+  step_barrier<C>();
+  // 5. cross-warp unknowns: rho_u by lane u, then Y_{w-1} and Y_w as dot
+  //    products with rows of the precomputed inverse (butterfly sum)
+  double pl = 0.0, pr = 0.0;
 #pragma unroll
-  for (int u = 0; u < NW; ++u) {
-    const double ru = __shfl_sync(kFull, rho, u);
-    const double gc = (grow >= 0) ? sm.G[grow * NW + u] : 0.0;
-    y = fma(gc, ru, y);
+  for (int u0 = 0; u0 < Ws; u0 += 32) {
+    const int u = u0 + L;
+    if (u < Ws) {
+      double rho;
+      if (u == Ws - 1) {
+        rho = sm.pub[par][3][u];
+      } else {
+        rho = fma(-sm.nu31[u], sm.pub[par][0][u + 1], sm.pub[par][3][u]);
+        rho = fma(-sm.A31[u], sm.pub[par][2][u], rho);
+        rho = fma(-sm.C31[u], sm.pub[par][1][u + 1], rho);
+      }
+      pl = fma(sm.G2[wl][0][u], rho, pl);
+      pr = fma(sm.G2[wl][1][u], rho, pr);
+    }
   }
-  const double Yl = __shfl_sync(kFull, y, 0);
-  const double Yr = __shfl_sync(kFull, y, 1);
+#pragma unroll
+  for (int s = 1; s < (Ws < 32 ? Ws : 32); s <<= 1) {
+    pl += __shfl_xor_sync(kFull, pl, s);
+    pr += __shfl_xor_sync(kFull, pr, s);
+  }
+  const double Yl = __shfl_sync(kFull, pl, 0);
+  const double Yr = __shfl_sync(kFull, pr, 0);
   const double X = (L == 31) ? Yr : fma(rg.rc, Yr, fma(rg.ra, Yl, Xt));
   double Xprev = __shfl_up_sync(kFull, X, 1);
   if (L == 0) Xprev = Yl;
-  // 5. fixup of the inner rows and the scaled state update
+  // 6. fixup of the inner rows and the scaled state update
 #pragma unroll
   for (int k = 0; k <= M - 2; ++k) {
     const double xv = fma(sm.rows[4][k][t], X, fma(sm.rows[3][k][t], Xprev, x[k]));
@@ -333,36 +439,37 @@ __device__ __forceinline__ void tri_step(double (&W)[M], double (&x)[M], SolverS
 }
 
 // Read the Nx-vector V into the thread's rows and scale it into W.
-template <int M, int NW>
-__device__ __forceinline__ void load_state(const Inst& in, const double* __restrict__ V, const SolverSmem<M, NW>& sm,
-                                           const SolverRegs& rg, double (&W)[M]) {
-  const int t = threadIdx.x;
+template <int M, int NW, int C>
+__device__ __forceinline__ void load_state(const Inst& in, const double* __restrict__ V,
+                                           const SolverSmem<M, NW, C>& sm, const SolverRegs& rg, double (&W)[M]) {
+  const int t = threadIdx.x, g = cta_rank<C>() * NW * 32 + t;
 #pragma unroll
   for (int k = 0; k < M; ++k) {
-    const int j = t * M + k - in.Np + 1;
+    const int j = g * M + k - in.Np + 1;
     const double v = (j >= 1 && j <= in.Nx - 2) ? V[j] : 0.0;
     W[k] = (k < M - 1) ? sm.rows[2][k][t] * v : rg.sigp * v;
   }
 }
 
 // Value of row k of this thread after a slice: V = W / sigma (CN) or x (IE).
-template <int M, int NW, bool CN>
+template <int M, int NW, int C, bool CN>
 __device__ __forceinline__ double row_value(const double* __restrict__ cb, int k, const double (&W)[M],
                                             const double (&x)[M], double isigp) {
   if (!CN) return x[k];
-  const double is = (k < M - 1) ? cb[coef_rows_off(5, k, threadIdx.x, M, NW * 32)] : isigp;
+  const int g = cta_rank<C>() * NW * 32 + threadIdx.x;
+  const double is = (k < M - 1) ? cb[coef_rows_off(5, k, g, M, C * NW * 32)] : isigp;
   return W[k] * is;
 }
 
 // Run `steps` steps of the propagator on slice n starting from scaled state W.
-template <int M, int NW, bool CN>
+template <int M, int NW, int C, bool CN>
 __device__ __forceinline__ void run_slice(const Inst& in, int n, const double* __restrict__ et, int steps,
-                                          double (&W)[M], double (&x)[M], SolverSmem<M, NW>& sm,
-                                          const SolverRegs& rg) {
+                                          double (&W)[M], double (&x)[M], SolverSmem<M, NW, C>& sm,
+                                          const SolverRegs& rg, int& par) {
   const double tau_n = in.T * (double)n / (double)in.P;
   const double KeN = in.K * exp(-in.r * tau_n);
   double Bold = in.Smax - KeN;  // exp(0) = 1
-  const bool last_warp = (threadIdx.x >> 5) == NW - 1;
+  const bool last_warp = cta_rank<C>() == C - 1 && (threadIdx.x >> 5) == NW - 1;
   for (int m = 0; m < steps; ++m) {
     double Zb = 0.0;
     if (last_warp) {
@@ -370,7 +477,8 @@ __device__ __forceinline__ void run_slice(const Inst& in, int n, const double* _
       Zb = CN ? Bold + Bnew : Bnew;
       Bold = Bnew;
     }
-    tri_step<M, NW, CN>(W, x, sm, rg, Zb);
+    tri_step<M, NW, C, CN>(W, x, sm, rg, Zb, par);
+    par ^= 1;
   }
 }
 
@@ -397,171 +505,200 @@ __device__ __forceinline__ void block_sum2(double& a, double& b, double (*red)[N
   }
 }
 
+__device__ __forceinline__ double bc_right(const Inst& in, int n) {
+  return in.Smax - in.K * exp(-in.r * (in.T * (double)n / (double)in.P));
+}
+
 // ---------------------------------------------------------------------------
 // Propagation over slices: fine (Crank-Nicolson) or coarse (implicit Euler).
-// One CTA per (instance, slice).
+// One cluster of C CTAs per (instance, slice): blockIdx.x = slice * C + rank.
 // ---------------------------------------------------------------------------
 
-template <int M, int NW, bool CN>
+template <int M, int NW, int C, bool CN>
 __global__ void __launch_bounds__(NW * 32, 1) prop_kernel(PropArgs a) {
   constexpr int T = NW * 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  SolverSmem<M, NW>& sm = *reinterpret_cast<SolverSmem<M, NW>*>(smem_raw);
+  SolverSmem<M, NW, C>& sm = *reinterpret_cast<SolverSmem<M, NW, C>*>(smem_raw);
   const int idx = a.ids[blockIdx.y];
   const Inst in = a.insts[idx];
-  const int n = blockIdx.x;
+  const int n = blockIdx.x / C;
+  // every exit condition below is uniform over the cluster (same slice, same instance)
   if (n >= in.P) return;
   if (a.k_iter >= 0 && n < a.k_iter) return;
   if (a.ctrl != nullptr && a.ctrl[idx].done) return;
   if (a.active != nullptr && !a.active[in.task_off + n]) return;
-  const int t = threadIdx.x;
+  const int t = threadIdx.x, c = cta_rank<C>();
   const double* cb = a.pool + (CN ? in.coef_cn : in.coef_ie);
   const double* et = a.exptab + (CN ? in.exp_cn : in.exp_ie);
   const int steps = CN ? in.Mf : in.Mg;
   SolverRegs rg;
-  load_solver<M, NW>(cb, sm, rg);
+  load_solver<M, NW, C>(cb, sm, rg);
+  if constexpr (C > 1) cg::this_cluster().sync();  // every CTA of the grid is running
 
   const int Nx = in.Nx;
   const double* Vin = a.in + (a.in_state ? in.state_off : in.slice_off) + (int64_t)n * Nx;
   double W[M], x[M];
-  load_state<M, NW>(in, Vin, sm, rg, W);
+  load_state<M, NW, C>(in, Vin, sm, rg, W);
 #pragma unroll
   for (int k = 0; k < M; ++k) x[k] = 0.0;
-  run_slice<M, NW, CN>(in, n, et, steps, W, x, sm, rg);
+  int par = 0;
+  run_slice<M, NW, C, CN>(in, n, et, steps, W, x, sm, rg, par);
 
-  const double Bend = in.Smax - in.K * exp(-in.r * (in.T * (double)(n + 1) / (double)in.P));
+  const bool first_thread = c == 0 && t == 0;
+  const bool last_thread = c == C - 1 && t == T - 1;
+  const int g = c * T + t;
+  const double Bend = bc_right(in, n + 1);
   double* Vout = a.out + (a.out_state ? in.state_off + (int64_t)(n + 1) * Nx : in.slice_off + (int64_t)n * Nx);
   if (a.mode == PropArgs::kPlain) {
 #pragma unroll
     for (int k = 0; k < M; ++k) {
-      const int j = t * M + k - in.Np + 1;
-      if (j >= 1 && j <= Nx - 2) Vout[j] = row_value<M, NW, CN>(cb, k, W, x, rg.isigp);
+      const int j = g * M + k - in.Np + 1;
+      if (j >= 1 && j <= Nx - 2) Vout[j] = row_value<M, NW, C, CN>(cb, k, W, x, rg.isigp);
     }
-    if (t == 0) Vout[0] = 0.0;
-    if (t == T - 1) Vout[Nx - 1] = Bend;
-    return;
-  }
-  // kPinnFused: U^{k+1}_{n+1} = F(U^k_n) + (G_new - G_old) with G = the network
-  // table at tau_{n+1} for both terms (Eq. 7); increment-norm partial sums.
-  const double* g = a.gtab + in.state_off + (int64_t)(n + 1) * Nx;
-  const double* Uold = a.uold + in.state_off + (int64_t)(n + 1) * Nx;
-  double num = 0.0, den = 0.0;
+    if (first_thread) Vout[0] = 0.0;
+    if (last_thread) Vout[Nx - 1] = Bend;
+  } else {
+    // kPinnFused: U^{k+1}_{n+1} = F(U^k_n) + (G_new - G_old) with G = the network
+    // table at tau_{n+1} for both terms (Eq. 7); increment-norm partial sums.
+    const double* gg = a.gtab + in.state_off + (int64_t)(n + 1) * Nx;
+    const double* Uold = a.uold + in.state_off + (int64_t)(n + 1) * Nx;
+    double num = 0.0, den = 0.0;
 #pragma unroll
-  for (int k = 0; k < M; ++k) {
-    const int j = t * M + k - in.Np + 1;
-    if (j >= 1 && j <= Nx - 2) {
-      const double f = row_value<M, NW, CN>(cb, k, W, x, rg.isigp);
-      const double v = f + (g[j] - g[j]);
-      Vout[j] = v;
-      const double d = v - Uold[j];
+    for (int k = 0; k < M; ++k) {
+      const int j = g * M + k - in.Np + 1;
+      if (j >= 1 && j <= Nx - 2) {
+        const double f = row_value<M, NW, C, CN>(cb, k, W, x, rg.isigp);
+        const double v = f + (gg[j] - gg[j]);
+        Vout[j] = v;
+        const double d = v - Uold[j];
+        num = fma(d, d, num);
+        den = fma(v, v, den);
+      }
+    }
+    if (first_thread) {
+      const double v = 0.0 + (gg[0] - gg[0]);
+      Vout[0] = v;
+      const double d = v - Uold[0];
       num = fma(d, d, num);
       den = fma(v, v, den);
     }
+    if (last_thread) {
+      const double v = Bend + (gg[Nx - 1] - gg[Nx - 1]);
+      Vout[Nx - 1] = v;
+      const double d = v - Uold[Nx - 1];
+      num = fma(d, d, num);
+      den = fma(v, v, den);
+    }
+    // the slice that becomes exact this iteration keeps its start value
+    if (a.k_iter >= 0 && n == a.k_iter) {
+      double* Fz = a.out + in.state_off + (int64_t)n * Nx;
+      for (int j = g; j < Nx; j += C * T) Fz[j] = Vin[j];
+    }
+    block_sum2<NW>(num, den, sm.red);
+    if (t == 0) {
+      const int64_t slot = (in.norm_off + (int64_t)(n + 1) * C + c) * 2;
+      a.normbuf[slot + 0] = num;
+      a.normbuf[slot + 1] = den;
+    }
   }
-  if (t == 0) {
-    const double v = 0.0 + (g[0] - g[0]);
-    Vout[0] = v;
-    const double d = v - Uold[0];
-    num = fma(d, d, num);
-    den = fma(v, v, den);
-  }
-  if (t == T - 1) {
-    const double v = Bend + (g[Nx - 1] - g[Nx - 1]);
-    Vout[Nx - 1] = v;
-    const double d = v - Uold[Nx - 1];
-    num = fma(d, d, num);
-    den = fma(v, v, den);
-  }
-  // the slice that becomes exact this iteration keeps its start value
-  if (a.k_iter >= 0 && n == a.k_iter) {
-    double* Fz = a.out + in.state_off + (int64_t)n * Nx;
-    for (int j = t; j < Nx; j += T) Fz[j] = Vin[j];
-  }
-  block_sum2<NW>(num, den, sm.red);
-  if (t == 0) {
-    a.normbuf[2 * (in.task1_off + n + 1) + 0] = num;
-    a.normbuf[2 * (in.task1_off + n + 1) + 1] = den;
-  }
+  if constexpr (C > 1) cg::this_cluster().sync();  // no CTA leaves while its shared memory may be read
 }
 
-// Classical serial fine time stepping (Eq. 6): one CTA per instance walks the
-// slices; every slice restarts from the stored vector, exactly like an
+// Classical serial fine time stepping (Eq. 6): one cluster per instance walks
+// the slices; every slice restarts from the stored vector, exactly like an
 // independent fine_propagate call on that slice.
-template <int M, int NW>
+template <int M, int NW, int C>
 __global__ void __launch_bounds__(NW * 32, 1) serial_fine_kernel(SerialArgs a) {
   constexpr int T = NW * 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  SolverSmem<M, NW>& sm = *reinterpret_cast<SolverSmem<M, NW>*>(smem_raw);
-  const Inst in = a.insts[a.ids[blockIdx.x]];
-  const int t = threadIdx.x, Nx = in.Nx;
+  SolverSmem<M, NW, C>& sm = *reinterpret_cast<SolverSmem<M, NW, C>*>(smem_raw);
+  const Inst in = a.insts[a.ids[blockIdx.y]];
+  const int t = threadIdx.x, Nx = in.Nx, c = cta_rank<C>();
+  const int g = c * T + t;
   const double* cb = a.pool + in.coef_cn;
   const double* et = a.exptab + in.exp_cn;
   SolverRegs rg;
-  load_solver<M, NW>(cb, sm, rg);
+  load_solver<M, NW, C>(cb, sm, rg);
   double* U = a.out + in.state_off;
-  for (int j = t; j < Nx; j += T) {
+  for (int j = g; j < Nx; j += C * T) {
     const double S = j * in.dS;
     U[j] = S - in.K > 0.0 ? S - in.K : 0.0;
   }
-  __syncthreads();
+  if constexpr (C > 1) {
+    cg::this_cluster().sync();
+  } else {
+    __syncthreads();
+  }
+  int par = 0;
   for (int n = 0; n < in.P; ++n) {
     double W[M], x[M];
-    load_state<M, NW>(in, U + (int64_t)n * Nx, sm, rg, W);
+    load_state<M, NW, C>(in, U + (int64_t)n * Nx, sm, rg, W);
 #pragma unroll
     for (int k = 0; k < M; ++k) x[k] = 0.0;
-    run_slice<M, NW, true>(in, n, et, in.Mf, W, x, sm, rg);
+    run_slice<M, NW, C, true>(in, n, et, in.Mf, W, x, sm, rg, par);
     double* Vout = U + (int64_t)(n + 1) * Nx;
 #pragma unroll
     for (int k = 0; k < M; ++k) {
-      const int j = t * M + k - in.Np + 1;
-      if (j >= 1 && j <= Nx - 2) Vout[j] = row_value<M, NW, true>(cb, k, W, x, rg.isigp);
+      const int j = g * M + k - in.Np + 1;
+      if (j >= 1 && j <= Nx - 2) Vout[j] = row_value<M, NW, C, true>(cb, k, W, x, rg.isigp);
     }
-    if (t == 0) Vout[0] = 0.0;
-    if (t == T - 1) Vout[Nx - 1] = in.Smax - in.K * exp(-in.r * (in.T * (double)(n + 1) / (double)in.P));
-    __syncthreads();
+    if (c == 0 && t == 0) Vout[0] = 0.0;
+    if (c == C - 1 && t == T - 1) Vout[Nx - 1] = bc_right(in, n + 1);
+    // the next slice reads values other CTAs wrote (global memory, cluster scope)
+    __threadfence();
+    if constexpr (C > 1) {
+      cg::this_cluster().sync();
+    } else {
+      __syncthreads();
+    }
   }
 }
 
 // ---------------------------------------------------------------------------
-// Serial coarse sweep with the Parareal correction (Eq. 7), one CTA per
+// Serial coarse sweep with the Parareal correction (Eq. 7), one cluster per
 // instance.  IE: G = coarse_steps implicit Euler steps.  Increment kind:
 // G(V) = V + g_{n+1} - g_n (elementwise).  k_iter < 0 is the initial sweep
 // U^0_{n+1} = G(U^0_n).
 // ---------------------------------------------------------------------------
-template <int M, int NW>
+template <int M, int NW, int C>
 __global__ void __launch_bounds__(NW * 32, 1) sweep_kernel(SweepArgs a) {
   constexpr int T = NW * 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  SolverSmem<M, NW>& sm = *reinterpret_cast<SolverSmem<M, NW>*>(smem_raw);
-  const int idx = a.ids[blockIdx.x];
+  SolverSmem<M, NW, C>& sm = *reinterpret_cast<SolverSmem<M, NW, C>*>(smem_raw);
+  const int idx = a.ids[blockIdx.y];
   const Inst in = a.insts[idx];
-  if (a.ctrl != nullptr && a.ctrl[idx].done) return;
-  const int t = threadIdx.x, Nx = in.Nx;
+  if (a.ctrl != nullptr && a.ctrl[idx].done) return;  // uniform over the cluster
+  const int t = threadIdx.x, Nx = in.Nx, c = cta_rank<C>();
+  const int g = c * T + t;
+  const bool first_thread = c == 0 && t == 0;
+  const bool last_thread = c == C - 1 && t == T - 1;
   const bool ie = a.kind == 0;
   const double* cb = a.pool + in.coef_ie;
   const double* et = a.exptab + in.exp_ie;
   SolverRegs rg{};
-  if (ie) load_solver<M, NW>(cb, sm, rg);
+  if (ie) load_solver<M, NW, C>(cb, sm, rg);
+  if constexpr (C > 1) cg::this_cluster().sync();
   const bool init = a.k_iter < 0;
   const int n0 = init ? 0 : a.k_iter;
   double* Un = a.unext + in.state_off;          // U^{k+1}
   const double* Uc = a.ucur + in.state_off;     // U^k
   double* Gold = a.gold + in.slice_off;         // G(U^k_n), P slices
   const double* Fv = a.fbuf + in.slice_off;     // F(U^k_n), P slices
-  const double* g = a.gtab + in.state_off;      // network table
+  const double* gt = a.gtab + in.state_off;     // network table
   // iteration k starts from U^{k+1}_k = U^k_k (exact since iteration k-1);
   // the initial sweep starts from the payoff already in slot 0
   const double* Vs = (init ? Un : Uc) + (int64_t)n0 * Nx;
   double V[M];
 #pragma unroll
   for (int k = 0; k < M; ++k) {
-    const int j = t * M + k - in.Np + 1;
+    const int j = g * M + k - in.Np + 1;
     V[k] = (j >= 1 && j <= Nx - 2) ? Vs[j] : 0.0;
   }
   double V0 = Vs[0], VB = Vs[Nx - 1];
   if (!init) {
-    for (int j = t; j < Nx; j += T) Un[(int64_t)n0 * Nx + j] = Vs[j];
+    for (int j = g; j < Nx; j += C * T) Un[(int64_t)n0 * Nx + j] = Vs[j];
   }
+  int par = 0;
   for (int n = n0; n < in.P; ++n) {
     double Gv[M];
     double G0, GB;
@@ -569,24 +706,24 @@ __global__ void __launch_bounds__(NW * 32, 1) sweep_kernel(SweepArgs a) {
       double W[M], x[M];
 #pragma unroll
       for (int k = 0; k < M; ++k) {
-        const int j = t * M + k - in.Np + 1;
+        const int j = g * M + k - in.Np + 1;
         const double v = (j >= 1 && j <= Nx - 2) ? V[k] : 0.0;
         W[k] = (k < M - 1) ? sm.rows[2][k][t] * v : rg.sigp * v;
         x[k] = 0.0;
       }
-      run_slice<M, NW, false>(in, n, et, in.Mg, W, x, sm, rg);
+      run_slice<M, NW, C, false>(in, n, et, in.Mg, W, x, sm, rg, par);
 #pragma unroll
       for (int k = 0; k < M; ++k) Gv[k] = x[k];
       G0 = 0.0;
-      GB = in.Smax - in.K * exp(-in.r * (in.T * (double)(n + 1) / (double)in.P));
+      GB = bc_right(in, n + 1);
     } else {
 #pragma unroll
       for (int k = 0; k < M; ++k) {
-        const int j = t * M + k - in.Np + 1;
-        Gv[k] = (j >= 1 && j <= Nx - 2) ? V[k] + (g[(int64_t)(n + 1) * Nx + j] - g[(int64_t)n * Nx + j]) : 0.0;
+        const int j = g * M + k - in.Np + 1;
+        Gv[k] = (j >= 1 && j <= Nx - 2) ? V[k] + (gt[(int64_t)(n + 1) * Nx + j] - gt[(int64_t)n * Nx + j]) : 0.0;
       }
-      G0 = V0 + (g[(int64_t)(n + 1) * Nx] - g[(int64_t)n * Nx]);
-      GB = VB + (g[(int64_t)(n + 1) * Nx + Nx - 1] - g[(int64_t)n * Nx + Nx - 1]);
+      G0 = V0 + (gt[(int64_t)(n + 1) * Nx] - gt[(int64_t)n * Nx]);
+      GB = VB + (gt[(int64_t)(n + 1) * Nx + Nx - 1] - gt[(int64_t)n * Nx + Nx - 1]);
     }
     double num = 0.0, den = 0.0;
     double* out = Un + (int64_t)(n + 1) * Nx;
@@ -595,7 +732,7 @@ __global__ void __launch_bounds__(NW * 32, 1) sweep_kernel(SweepArgs a) {
     const double* fv = Fv + (int64_t)n * Nx;
 #pragma unroll
     for (int k = 0; k < M; ++k) {
-      const int j = t * M + k - in.Np + 1;
+      const int j = g * M + k - in.Np + 1;
       if (j >= 1 && j <= Nx - 2) {
         const double v = init ? Gv[k] : fv[j] + (Gv[k] - go[j]);
         go[j] = Gv[k];
@@ -608,39 +745,41 @@ __global__ void __launch_bounds__(NW * 32, 1) sweep_kernel(SweepArgs a) {
         }
       }
     }
-    // Dirichlet nodes follow the same formula (exact values in, exact out)
-    const double v0 = init ? G0 : fv[0] + (G0 - go[0]);
-    const double vB = init ? GB : fv[Nx - 1] + (GB - go[Nx - 1]);
-    __syncthreads();
-    if (t == 0) {
+    // Dirichlet nodes follow the same formula (exact values in, exact out);
+    // each is read and written by one thread only
+    if (first_thread) {
+      const double v0 = init ? G0 : fv[0] + (G0 - go[0]);
       go[0] = G0;
       out[0] = v0;
+      V0 = v0;
       if (!init) {
         const double d = v0 - old[0];
         num = fma(d, d, num);
         den = fma(v0, v0, den);
       }
     }
-    if (t == T - 1) {
+    if (last_thread) {
+      const double vB = init ? GB : fv[Nx - 1] + (GB - go[Nx - 1]);
       go[Nx - 1] = GB;
       out[Nx - 1] = vB;
+      VB = vB;
       if (!init) {
         const double d = vB - old[Nx - 1];
         num = fma(d, d, num);
         den = fma(vB, vB, den);
       }
     }
-    V0 = v0;
-    VB = vB;
     if (!init) {
       block_sum2<NW>(num, den, sm.red);
       if (t == 0) {
-        a.normbuf[2 * (in.task1_off + n + 1) + 0] = num;
-        a.normbuf[2 * (in.task1_off + n + 1) + 1] = den;
+        const int64_t slot = (in.norm_off + (int64_t)(n + 1) * C + c) * 2;
+        a.normbuf[slot + 0] = num;
+        a.normbuf[slot + 1] = den;
       }
     }
     __syncthreads();
   }
+  if constexpr (C > 1) cg::this_cluster().sync();
 }
 
 // ---------------------------------------------------------------------------
@@ -675,22 +814,34 @@ __global__ void parareal_init_kernel(const Inst* insts, int n_inst, double* buf0
 }
 
 // e_k = max_n ||U^{k+1}_n - U^k_n|| / ||U^{k+1}_n|| over the slices updated in
-// iteration k, then the stop rule of parareal_solve.
+// iteration k, then the stop rule of parareal_solve.  One warp per instance.
 __global__ void parareal_finalize_kernel(const Inst* insts, int n_inst, const double* normbuf, int k, double tol,
                                          int max_iter, Ctrl* ctrl, double* norms) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int idx = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const int L = threadIdx.x & 31;
   if (idx >= n_inst) return;
-  if (ctrl[idx].done) return;
+  if (ctrl[idx].done) return;  // uniform over the warp
   const Inst in = insts[idx];
   double e = 0.0;
   bool bad = false;
-  for (int i = k + 1; i <= in.P; ++i) {
-    const double num = sqrt(normbuf[2 * (in.task1_off + i)]);
-    const double den = sqrt(normbuf[2 * (in.task1_off + i) + 1]);
+  for (int i = k + 1 + L; i <= in.P; i += 32) {
+    double sn = 0.0, sd = 0.0;
+    for (int c = 0; c < in.C; ++c) {
+      const int64_t slot = (in.norm_off + (int64_t)i * in.C + c) * 2;
+      sn += normbuf[slot];
+      sd += normbuf[slot + 1];
+    }
+    const double num = sqrt(sn), den = sqrt(sd);
     const double q = den > 0.0 ? num / den : num;
     if (!(q == q) || isinf(q)) bad = true;
     if (q > e) e = q;
   }
+  for (int s = 16; s >= 1; s >>= 1) {
+    const double o = __shfl_xor_sync(kFull, e, s);
+    e = o > e ? o : e;
+  }
+  bad = __any_sync(kFull, bad);
+  if (L != 0) return;
   norms[(int64_t)idx * max_iter + k] = bad ? nan("") : e;
   ctrl[idx].iterations = k + 1;
   ctrl[idx].last_norm = bad ? nan("") : e;
@@ -742,75 +893,99 @@ __global__ void table_fix_kernel(const Inst* insts, int n_inst, double* g) {
   if (idx >= n_inst) return;
   const Inst in = insts[idx];
   for (int n = threadIdx.x; n <= in.P; n += blockDim.x) {
-    const double tau = in.T * (double)n / (double)in.P;
     g[in.state_off + (int64_t)n * in.Nx] = 0.0;
-    g[in.state_off + (int64_t)n * in.Nx + in.Nx - 1] = in.Smax - in.K * exp(-in.r * tau);
+    g[in.state_off + (int64_t)n * in.Nx + in.Nx - 1] = bc_right(in, n);
   }
 }
 
 // ---------------------------------------------------------------------------
-// Host-side dispatch over the (M, NW) partition classes.
+// Host-side dispatch over the (M, NW, C) partition classes.
 // ---------------------------------------------------------------------------
 
-#define BSP_FOR_EACH_CLASS(X) X(2, 1) X(2, 2) X(2, 4) X(4, 4) X(8, 4) X(16, 4) X(32, 4)
+#define BSP_FOR_EACH_CLASS(X)                                                                        \
+  X(2, 1, 1) X(2, 2, 1) X(2, 4, 1) X(4, 4, 1) X(8, 4, 1) X(16, 4, 1) X(32, 4, 1) X(2, 4, 2) X(4, 4, 2) \
+  X(8, 4, 2) X(16, 4, 2) X(32, 4, 2) X(2, 4, 4) X(4, 4, 4) X(8, 4, 4) X(16, 4, 4) X(32, 4, 4)         \
+  X(2, 4, 8) X(4, 4, 8) X(8, 4, 8) X(16, 4, 8) X(32, 4, 8) X(4, 4, 16) X(8, 4, 16) X(16, 4, 16)       \
+  X(32, 4, 16)
 
-cudaError_t launch_setup(const Inst* d_insts, const int32_t* d_ids, int n, double* pool, double* exptab,
+bool partition_supported(int M, int NW, int C) {
+#define X(MM, WW, CC) \
+  if (M == MM && NW == WW && C == CC) return true;
+  BSP_FOR_EACH_CLASS(X)
+#undef X
+  return false;
+}
+
+cudaError_t launch_setup(const Inst* d_insts, const int32_t* d_ids, int n, int Ws, double* pool, double* exptab,
                          cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  setup_kernel<<<dim3(n, 2), 128, 0, s>>>(d_insts, d_ids, pool, exptab);
+  setup_rows_kernel<<<dim3(Ws, n), 32, 0, s>>>(d_insts, d_ids, pool, exptab);
+  setup_iface_kernel<<<dim3(Ws, n), 32, 0, s>>>(d_insts, d_ids, pool);
+  const int smem = (int)(sizeof(double) * (size_t)Ws * (2 * Ws + 1));
+  cudaError_t e = cudaFuncSetAttribute(setup_cross_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  setup_cross_kernel<<<dim3(n, 2), 128, smem, s>>>(d_insts, d_ids, pool);
   return cudaGetLastError();
 }
 
-template <typename K>
-static cudaError_t set_smem(K kernel, int bytes) {
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+template <typename Kern, typename Arg>
+static cudaError_t launch_cluster(Kern kernel, dim3 grid, int threads, int C, int smem, cudaStream_t s,
+                                  const Arg& arg) {
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  if (C > 8) {
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(threads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, arg);
 }
 
-cudaError_t launch_prop(int M, int NW, bool cn, const PropArgs& a, int n_inst, int maxP, cudaStream_t s) {
+cudaError_t launch_prop(int M, int NW, int C, bool cn, const PropArgs& a, int n_inst, int maxP, cudaStream_t s) {
   if (n_inst <= 0) return cudaSuccess;
-  dim3 grid(maxP, n_inst);
-#define X(MM, WW)                                                                \
-  if (M == MM && NW == WW) {                                                     \
-    const int sz = (int)sizeof(SolverSmem<MM, WW>);                              \
-    cudaError_t e;                                                               \
-    if (cn) {                                                                    \
-      if ((e = set_smem(prop_kernel<MM, WW, true>, sz)) != cudaSuccess) return e;  \
-      prop_kernel<MM, WW, true><<<grid, WW * 32, sz, s>>>(a);                    \
-    } else {                                                                     \
-      if ((e = set_smem(prop_kernel<MM, WW, false>, sz)) != cudaSuccess) return e; \
-      prop_kernel<MM, WW, false><<<grid, WW * 32, sz, s>>>(a);                   \
-    }                                                                            \
-    return cudaGetLastError();                                                   \
+  dim3 grid(maxP * C, n_inst);
+#define X(MM, WW, CC)                                                                                            \
+  if (M == MM && NW == WW && C == CC) {                                                                          \
+    const int sz = (int)sizeof(SolverSmem<MM, WW, CC>);                                                          \
+    return cn ? launch_cluster(prop_kernel<MM, WW, CC, true>, grid, WW * 32, CC, sz, s, a)                       \
+              : launch_cluster(prop_kernel<MM, WW, CC, false>, grid, WW * 32, CC, sz, s, a);                      \
   }
   BSP_FOR_EACH_CLASS(X)
 #undef X
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_serial(int M, int NW, const SerialArgs& a, int n_inst, cudaStream_t s) {
+cudaError_t launch_serial(int M, int NW, int C, const SerialArgs& a, int n_inst, cudaStream_t s) {
   if (n_inst <= 0) return cudaSuccess;
-#define X(MM, WW)                                                             \
-  if (M == MM && NW == WW) {                                                  \
-    const int sz = (int)sizeof(SolverSmem<MM, WW>);                           \
-    cudaError_t e = set_smem(serial_fine_kernel<MM, WW>, sz);                 \
-    if (e != cudaSuccess) return e;                                           \
-    serial_fine_kernel<MM, WW><<<n_inst, WW * 32, sz, s>>>(a);                \
-    return cudaGetLastError();                                                \
+  dim3 grid(C, n_inst);
+#define X(MM, WW, CC)                                                                             \
+  if (M == MM && NW == WW && C == CC) {                                                           \
+    const int sz = (int)sizeof(SolverSmem<MM, WW, CC>);                                           \
+    return launch_cluster(serial_fine_kernel<MM, WW, CC>, grid, WW * 32, CC, sz, s, a);           \
   }
   BSP_FOR_EACH_CLASS(X)
 #undef X
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_sweep(int M, int NW, const SweepArgs& a, int n_inst, cudaStream_t s) {
+cudaError_t launch_sweep(int M, int NW, int C, const SweepArgs& a, int n_inst, cudaStream_t s) {
   if (n_inst <= 0) return cudaSuccess;
-#define X(MM, WW)                                                             \
-  if (M == MM && NW == WW) {                                                  \
-    const int sz = (int)sizeof(SolverSmem<MM, WW>);                           \
-    cudaError_t e = set_smem(sweep_kernel<MM, WW>, sz);                       \
-    if (e != cudaSuccess) return e;                                           \
-    sweep_kernel<MM, WW><<<n_inst, WW * 32, sz, s>>>(a);                      \
-    return cudaGetLastError();                                                \
+  dim3 grid(C, n_inst);
+#define X(MM, WW, CC)                                                                        \
+  if (M == MM && NW == WW && C == CC) {                                                      \
+    const int sz = (int)sizeof(SolverSmem<MM, WW, CC>);                                      \
+    return launch_cluster(sweep_kernel<MM, WW, CC>, grid, WW * 32, CC, sz, s, a);            \
   }
   BSP_FOR_EACH_CLASS(X)
 #undef X
@@ -825,8 +1000,7 @@ cudaError_t launch_parareal_init(const Inst* d_insts, int n_inst, double* buf0, 
 
 cudaError_t launch_parareal_finalize(const Inst* d_insts, int n_inst, const double* normbuf, int k, double tol,
                                      int max_iter, Ctrl* ctrl, double* norms, cudaStream_t s) {
-  parareal_finalize_kernel<<<(n_inst + 127) / 128, 128, 0, s>>>(d_insts, n_inst, normbuf, k, tol, max_iter, ctrl,
-                                                                norms);
+  parareal_finalize_kernel<<<(n_inst + 3) / 4, 128, 0, s>>>(d_insts, n_inst, normbuf, k, tol, max_iter, ctrl, norms);
   return cudaGetLastError();
 }
 

@@ -43,7 +43,7 @@ def test_problem_init_rejects_bad_parameters(L, bad):
 
 def test_problem_init_rejects_oversized_grid(L):
     with pytest.raises(B.BsError) as e:
-        B.Problem(B.params(Nx=4098))
+        B.Problem(B.params(Nx=65538))
     assert e.value.code == B.BS_EUNSUPPORTED
 
 

@@ -1,0 +1,130 @@
+"""Grids spread over clusters of CTAs (distributed shared memory interface
+exchange): parity against the oracle for every cluster size, the largest grid
+(65536 points over a 16-CTA cluster), and bitwise consistency between the
+serial and the parallel fine paths.  Tolerances as in test_gpu_solver.py.
+"""
+import numpy as np
+import pytest
+
+from paper_2303_03848_b300 import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+RTOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2303_03848_b300 import binding, build
+
+    build.build()
+    return binding
+
+
+def _tol(p, kind, chain_slices=1):
+    steps = p["fine_steps"] if kind == "fine" else p["coarse_steps"]
+    dt = p["T"] / (p["P"] * steps)
+    h = 0.5 * dt if kind == "fine" else dt
+    j = p["Nx"] - 2
+    kappa = 1.0 + h * (2.0 * p["sigma"] ** 2 * j * j + p["r"] * j + p["r"])
+    return max(RTOL, 2.0 * kappa * 2.0 ** -53 * (steps * chain_slices))
+
+
+def _close(a, b, rtol):
+    a, b = np.asarray(a), np.asarray(b)
+    err = np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+    assert err <= rtol, f"relative error {err:.3e} > {rtol:.1e}"
+
+
+def _slices(orc, p, seed, smooth=False):
+    op = orc.params(**p)
+    if smooth:
+        S = np.tile(orc.payoff(op), (p["P"], 1))
+    else:
+        S = synth.random_states(seed, p["P"], p["Nx"], scale=p["Smax"])
+    for n in range(p["P"]):
+        S[n, 0] = 0.0
+        S[n, -1] = orc.right_bc(op, p["T"] * n / p["P"])
+    return S
+
+
+@pytest.mark.parametrize("C", [1, 2, 4, 8, 16])
+def test_propagators_match_oracle_forced_cluster(B, orc, monkeypatch, C):
+    monkeypatch.setenv("BSP_CLUSTER", str(C))
+    insts = [dict(K=1.0 + 0.2 * i, sigma=0.2 + 0.05 * i, r=0.02 * i, T=1.0, Smax=4.0 * (1.0 + 0.2 * i), Nx=Nx, P=2,
+                  fine_steps=6, coarse_steps=2) for i, Nx in enumerate((1024, 2049, 4097))]
+    prob = B.Problem(insts)
+    parts = [_slices(orc, p, 40 + i) for i, p in enumerate(insts)]
+    Uin = torch.tensor(np.concatenate([s.ravel() for s in parts]), device="cuda")
+    F = prob.fine_propagate(Uin).cpu().numpy()
+    G = prob.coarse_propagate(Uin).cpu().numpy()
+    for i, p in enumerate(insts):
+        op = orc.params(**p)
+        o = prob.slice_off[i]
+        for n in range(p["P"]):
+            sl = slice(o + n * p["Nx"], o + (n + 1) * p["Nx"])
+            _close(F[sl], orc.fine(op, n, parts[i][n]), _tol(p, "fine"))
+            _close(G[sl], orc.coarse_ie(op, n, parts[i][n]), _tol(p, "coarse"))
+
+
+def test_largest_grid_65536_points(B, orc):
+    # the large single-instance grid (S in [0, 8], sigma 0.3, r 0.03, T 2, K 1),
+    # 65536 points over a 16-CTA cluster; few steps so the oracle is quick, which
+    # puts the mesh ratio near 1e8 -- the calibrated bound applies
+    p = dict(K=1.0, sigma=0.3, r=0.03, T=2.0, Smax=8.0, Nx=65536, P=2, fine_steps=4, coarse_steps=1)
+    prob = B.Problem(p)
+    parts = _slices(orc, p, 0, smooth=True)
+    Uin = torch.tensor(parts.ravel(), device="cuda")
+    F = prob.fine_propagate(Uin).cpu().numpy().reshape(p["P"], p["Nx"])
+    G = prob.coarse_propagate(Uin).cpu().numpy().reshape(p["P"], p["Nx"])
+    op = orc.params(**p)
+    for n in range(p["P"]):
+        _close(F[n], orc.fine(op, n, parts[n]), _tol(p, "fine"))
+        _close(G[n], orc.coarse_ie(op, n, parts[n]), _tol(p, "coarse"))
+
+
+def test_largest_grid_serial_fine_and_parareal(B, orc):
+    p = dict(K=1.0, sigma=0.3, r=0.03, T=0.05, Smax=8.0, Nx=65536, P=3, fine_steps=16, coarse_steps=1)
+    prob = B.Problem(p)
+    Uf = prob.serial_fine()
+    ref = orc.serial_fine(orc.params(**p))
+    _close(Uf.cpu().numpy(), ref.ravel(), _tol(p, "fine", p["P"]))
+    U, norms, stats, rc = prob.parareal_solve(B.COARSE_IE, tol=0.0)
+    assert rc == B.BS_OK and stats[0]["iterations"] == p["P"]
+    assert torch.equal(U, Uf)
+
+
+@pytest.mark.parametrize("C", [2, 4, 8])
+def test_parareal_ie_with_clusters_matches_oracle(B, orc, monkeypatch, C):
+    monkeypatch.setenv("BSP_CLUSTER", str(C))
+    p = dict(K=1.0, sigma=0.2, r=0.05, T=1.0, Smax=4.0, Nx=2048, P=6, fine_steps=64, coarse_steps=1)
+    prob = B.Problem(p)
+    U, norms, stats, rc = prob.parareal_solve(B.COARSE_IE, tol=1e-10)
+    Ur, nr, st = orc.parareal(orc.params(**p), orc.COARSE_IE, tol=1e-10)
+    assert rc == B.BS_OK and stats[0]["iterations"] == len(nr)
+    np.testing.assert_allclose(norms[0, :len(nr)], nr, rtol=1e-6)
+    _close(U.cpu().numpy(), Ur.ravel(), _tol(p, "fine", p["P"]))
+
+
+@pytest.mark.parametrize("C", [2, 4])
+def test_cluster_serial_fine_equals_fine_propagate_bitwise(B, monkeypatch, C):
+    monkeypatch.setenv("BSP_CLUSTER", str(C))
+    p = dict(K=1.0, sigma=0.3, r=0.03, T=2.0, Smax=5.0, Nx=1500, P=4, fine_steps=20, coarse_steps=1)
+    prob = B.Problem(p)
+    U = prob.serial_fine()
+    Uv = U.view(p["P"] + 1, p["Nx"])
+    F = prob.fine_propagate(Uv[:-1].contiguous().view(-1)).view(p["P"], p["Nx"])
+    assert torch.equal(F, Uv[1:])
+
+
+def test_partitions_agree(B, monkeypatch):
+    # one CTA per grid against a 4-CTA cluster on the benchmark grid: different
+    # summation orders, same answer to rounding
+    p = dict(K=1.0, sigma=0.2, r=0.05, T=1.0, Smax=4.0, Nx=1024, P=4, fine_steps=128, coarse_steps=1)
+    out = []
+    for C in ("1", "4"):
+        monkeypatch.setenv("BSP_CLUSTER", C)
+        out.append(B.Problem(p).serial_fine().cpu().numpy())
+    _close(out[1], out[0], 1e-13)

@@ -440,8 +440,8 @@ def _cn_longdouble(p, n, V):
 
 def test_oracle_rounding_within_calibrated_bound(orc):
     # noisy state at mesh ratio h sigma^2 j^2 ~ 6e3: the oracle's own distance to
-    # a long-double recomputation stays within 2 kappa u sqrt(N) (N = 6 CN steps),
-    # the bound the GPU parity tests use for such stress cases, and exceeds 1e-12
+    # a long-double recomputation stays within 2 kappa u N (N = 6 CN steps), the
+    # bound the GPU parity tests use for such stress cases, and exceeds 1e-12
     K = 1.7
     p = orc.params(K=K, sigma=0.37, r=0.01, T=1.6, Smax=4 * K, Nx=1025, P=3, fine_steps=6)
     S = synth.random_states(111, 1, p.Nx, scale=p.Smax)[0]
@@ -451,4 +451,4 @@ def test_oracle_rounding_within_calibrated_bound(orc):
     h = 0.5 * p.T / (p.P * p.fine_steps)
     j = p.Nx - 2
     kappa = 1 + h * (2 * p.sigma ** 2 * j * j + p.r * j + p.r)
-    assert 1e-12 < err <= 2 * kappa * 2.0 ** -53 * p.fine_steps ** 0.5
+    assert 1e-12 < err <= 2 * kappa * 2.0 ** -53 * p.fine_steps
