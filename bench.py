@@ -44,7 +44,7 @@ WORKLOAD = ("PINN-coarse Parareal, BS call K=1 sigma=0.2 r=0.05 T=1, Nx=1024 S i
 FLOPS_PER_PT_STEP = 11.0  # CN right-hand side 5 + factored solve 6 (algorithmic, per interior point-step)
 # DRAM read+write bytes of one fine launch over all 32 slices from the ncu capture in profiles/;
 # None whenever the kernel has changed since the last capture
-FINE_TRAFFIC_BYTES = None
+FINE_TRAFFIC_BYTES = 411136  # prop_kernel<2,4,4,CN>: 411 KB read, 0 written (profiles/fine_cn_cluster4_nx1024_p32.md)
 
 
 def _peaks():
@@ -280,6 +280,8 @@ def run_ours(args):
             e2e_ms.append((time.perf_counter() - s0) * 1e3)
     e2e_step = allreduce_max(ws, statistics.mean(e2e_ms))
 
+    batched = batched_leg(B, torch) if args.batched else None
+
     cpu = None
     if rank == 0:
         cpu = cpu_baseline(model.get_weights(), iters, budget_s=args.cpu_seconds)
@@ -318,6 +320,7 @@ def run_ours(args):
         "speedup_vs_serial_fine": {"pinn": serial_ms / ms_step, "ie": serial_ms / statistics.mean(ms_ie)},
         "per_precision": per_prec,
         "train_step": train,
+        "batched": batched,
         "setup_ms": setup_ms,
         "wall_s_timed": wall,
     }
@@ -348,6 +351,55 @@ def run_fine_only(args):
     pt = (CFG["Nx"] - 2) * CFG["fine_steps"] * CFG["P"]
     print(json.dumps({"mode": "fine", "ms": ms, "grid_pt_steps_per_s": pt / (ms * 1e-3),
                       "tflops_algorithmic": FLOPS_PER_PT_STEP * pt / (ms * 1e-3) / 1e12}), flush=True)
+
+
+def batched_leg(B, torch, n_inst=4096, solve=True):
+    """Batched workload: n_inst instances (K, sigma, r, T, Nx seeded), P=64, CN 256 steps/slice.
+
+    Times fine_propagate over every slice of every instance (one launch per
+    partition class) and, optionally, one implicit-Euler-coarse Parareal solve
+    of the whole batch at tol 1e-6.
+    """
+    from paper_2303_03848_b300 import synth
+
+    insts = synth.batched_instances(0, n_inst, P=64, fine_steps=256, coarse_steps=1)
+    t0 = time.perf_counter()
+    prob = B.Problem(insts)
+    setup_s = time.perf_counter() - t0
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(0)
+    Uin = torch.rand(prob.total_slice, dtype=torch.float64, device="cuda", generator=gen)
+    Fo = torch.empty_like(Uin)
+    prob.fine_propagate(Uin, Fo)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(2)]
+    for a, b in ev:
+        a.record()
+        prob.fine_propagate(Uin, Fo)
+        b.record()
+    torch.cuda.synchronize()
+    ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    pt = sum((p["Nx"] - 2) * p["fine_steps"] * p["P"] for p in insts)
+    tf = FLOPS_PER_PT_STEP * pt / (ms * 1e-3) / 1e12
+    peak = 148 * 2 * 2 * float(_peaks().get("sm_max_mhz", 2032.0)) * 1e6 / 1e12
+    out = {"instances": n_inst, "P": 64, "fine_steps": 256, "Nx": "uniform over 256..4096",
+           "setup_s": setup_s, "fine_ms": ms, "grid_pt_steps_per_s": pt / (ms * 1e-3),
+           "fine_tflops_algorithmic": tf, "fine_frac_of_fp64_peak": tf / peak}
+    del Uin, Fo
+    if solve:
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record()
+        U, norms, stats, rc = prob.parareal_solve(B.COARSE_IE, tol=1e-6, max_iter=64)
+        s1.record()
+        torch.cuda.synchronize()
+        its = [st["iterations"] for st in stats]
+        out.update({"ie_solve_ms": s0.elapsed_time(s1), "ie_solves_per_s": n_inst / (s0.elapsed_time(s1) * 1e-3),
+                    "ie_iterations_mean": float(sum(its)) / len(its), "ie_iterations_max": max(its),
+                    "ie_status": rc})
+        del U
+    prob.close()
+    torch.cuda.empty_cache()
+    return out
 
 
 def cpu_baseline(weights, iters, budget_s=20.0):
@@ -427,13 +479,24 @@ def main():
     ap.add_argument("--prec", default="bf16", choices=["fp64", "fp32", "tf32", "bf16"])
     ap.add_argument("--train-steps", type=int, default=5000)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
-    ap.add_argument("--mode", default="solve", choices=["solve", "fine"],
-                    help="fine: only the fine propagator on all slices of the workload (profiling)")
+    ap.add_argument("--mode", default="solve", choices=["solve", "fine", "batched"],
+                    help="fine / batched: only the fine propagator on all slices of the benchmark / "
+                         "batched workload (profiling)")
+    ap.add_argument("--batched", type=int, default=1, help="include the batched-workload leg (1/0)")
+    ap.add_argument("--instances", type=int, default=4096, help="instances of --mode batched")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.mode == "fine":
         run_fine_only(args)
+    elif args.mode == "batched":
+        import torch
+
+        from paper_2303_03848_b300 import binding as B
+        from paper_2303_03848_b300 import build as BUILD
+
+        BUILD.build()
+        print(json.dumps(batched_leg(B, torch, n_inst=args.instances, solve=False)), flush=True)
     elif args.impl == "reference":
         run_reference(args)
     else:
