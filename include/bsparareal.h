@@ -159,12 +159,23 @@ int pinn_set_weights(pinn_model* m, const double* flat_host);
 int pinn_get_weights(const pinn_model* m, double* flat_host);
 
 /*
+ * pinn_device_status -- synchronises the device and reports the network's
+ * device status word: BS_OK, or BS_TIMEOUT if a bounded wait inside a
+ * tensor-core kernel gave up (its results are then invalid).
+ */
+int pinn_device_status(const pinn_model* m, int* status);
+
+/*
  * pinn_eval -- u = u_theta(X) at N points (Section 3.3).
  *   X: device [N][d_in] doubles.  u: device [N] doubles.
  *   derivs: device, nullable, [N][3] = (u_S, u_SS, u_tau) by forward-mode
  *   differentiation through every layer (the paper uses automatic
  *   differentiation).  prec selects the arithmetic of the layers: FP64, FP32,
  *   TF32 or BF16 (reduced precisions accumulate in FP32); outputs are FP64.
+ *   BF16 runs the hidden layers on the tensor cores (tcgen05, FP32
+ *   accumulation in tensor memory) when every hidden layer is w x w with w a
+ *   multiple of 32 up to 256; TF32 and other shapes round the operands on
+ *   CUDA cores.
  *   derivs requires FP64 or FP32.
  */
 int pinn_eval(const pinn_model* m, int prec, const double* X, int64_t N, double* u, double* derivs, void* stream);

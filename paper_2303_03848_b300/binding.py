@@ -79,6 +79,7 @@ def lib() -> ctypes.CDLL:
         L.pinn_set_weights.argtypes = [vp, P(dbl)]
         L.pinn_get_weights.argtypes = [vp, P(dbl)]
         L.pinn_eval.argtypes = [vp, ctypes.c_int, vp, i64, vp, vp, vp]
+        L.pinn_device_status.argtypes = [vp, P(ctypes.c_int)]
         L.pinn_loss_grad.argtypes = [vp, vp, vp, i64, P(BsParams), dbl, ctypes.c_int, vp, vp, vp]
         L.pinn_train_step.argtypes = [vp, vp, vp, i64, P(BsParams), dbl, ctypes.c_int, dbl, P(dbl), vp, vp]
         L.parareal_solve.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, dbl, i32, vp, P(dbl), P(InstanceStats), vp]
@@ -275,6 +276,12 @@ class PinnModel:
         _check(lib().pinn_get_weights(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
                "pinn_get_weights")
         return out
+
+    def device_status(self) -> int:
+        """Synchronise and read the device status word (BS_OK or BS_TIMEOUT)."""
+        s = ctypes.c_int(0)
+        _check(lib().pinn_device_status(self._h, ctypes.byref(s)), "pinn_device_status")
+        return s.value
 
     def eval(self, X, prec=FP64, derivs=False):
         import torch

@@ -121,6 +121,8 @@ struct pinn_model {
   void* ws = nullptr;
   size_t ws_bytes = 0;
   int step = 0;
+  unsigned char* tc_packed = nullptr;
+  int* status = nullptr;
 };
 
 extern "C" {
@@ -336,6 +338,8 @@ void pinn_destroy(pinn_model* m) {
   cudaFree(m->grad);
   cudaFree(m->loss3);
   cudaFree(m->ws);
+  cudaFree(m->tc_packed);
+  cudaFree(m->status);
   delete m;
 }
 
@@ -387,6 +391,18 @@ int pinn_create(const int32_t* widths, int32_t n_layers, const double* in_lo, co
   }
   m->dev.p64 = m->p64;
   m->dev.p32 = m->p32;
+  if ((e = dalloc(&m->status, 1)) != cudaSuccess || (e = cudaMemset(m->status, 0, sizeof(int))) != cudaSuccess) {
+    pinn_destroy(m);
+    return map_err(e);
+  }
+  m->dev.status = m->status;
+  if (bsp::tc_supported(m->dev)) {
+    if ((e = dalloc(&m->tc_packed, bsp::tc_packed_bytes(m->dev, 1) + 16)) != cudaSuccess) {
+      pinn_destroy(m);
+      return map_err(e);
+    }
+    m->dev.tc_packed = m->tc_packed;
+  }
   // Xavier-uniform weights, zero biases
   std::vector<double> h(off, 0.0);
   for (int l = 1; l <= n_layers; ++l) {
@@ -405,6 +421,13 @@ int pinn_create(const int32_t* widths, int32_t n_layers, const double* in_lo, co
   }
   *out = m;
   return BS_OK;
+}
+
+int pinn_device_status(const pinn_model* m, int* status) {
+  if (!m || !status) return BS_EINVAL;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(status, m->status, sizeof(int), cudaMemcpyDeviceToHost);
+  return map_err(e);
 }
 
 int pinn_num_params(const pinn_model* m, int64_t* n) {

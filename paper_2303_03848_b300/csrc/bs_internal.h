@@ -77,7 +77,16 @@ struct MlpDev {
   double lo[8], hi[8];
   const double* p64;         // FP64 master parameters
   const float* p32;          // FP32 copy
+  unsigned char* tc_packed;  // square layers in the tensor-core operand layout (pinn_tc.cu)
+  int* status;               // device status word: BS_TIMEOUT if a bounded wait gave up
 };
+
+// Tensor-core evaluation (pinn_tc.cu): hidden layers w x w on tcgen05.
+bool tc_supported(const MlpDev& m);
+bool tc_fits(const MlpDev& m, int tf32);
+size_t tc_packed_bytes(const MlpDev& m, int tf32);
+cudaError_t launch_mlp_eval_tc(const MlpDev& m, int tf32, unsigned char* packed, const double* X, int64_t N,
+                               double* u, int* status, cudaStream_t s);
 
 cudaError_t launch_mlp_eval(const MlpDev& m, int prec, const double* X, int64_t N, double* u, double* derivs,
                             cudaStream_t s);

@@ -8,7 +8,9 @@
 //   z' = W h',  h' = t' z',  h'' = t' z'' + t'' (z')^2,  t' = 1 - t^2,  t'' = -2 t t'.
 //
 // This translation unit holds the SIMT paths: FP64 and FP32 arithmetic, and
-// TF32 / BF16 operand rounding with FP32 accumulation.
+// TF32 / BF16 operand rounding with FP32 accumulation for networks whose
+// hidden layers are not all w x w.  TF32 / BF16 evaluation of w x w hidden
+// layers runs on the tensor cores (pinn_tc.cu).
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -174,6 +176,7 @@ cudaError_t launch_mlp_eval(const MlpDev& m, int prec, const double* X, int64_t 
     case 2:
       return eval_launch<float, 1, 1>(m, X, N, u, nullptr, s);
     case 3:
+      if (tc_fits(m, 0)) return launch_mlp_eval_tc(m, 0, m.tc_packed, X, N, u, m.status, s);
       return eval_launch<float, 2, 1>(m, X, N, u, nullptr, s);
   }
   return cudaErrorInvalidValue;

@@ -1,5 +1,6 @@
 """GPU parity of the network path (evaluation, derivatives, loss, adjoint
-gradient, Adam) against the oracle, through the C ABI.
+gradient, Adam) against the oracle, through the C ABI.  BF16 evaluation of
+the w x w hidden layers runs on the tensor cores (tcgen05).
 
 Tolerances (relative to the largest magnitude of the compared quantity):
   FP64: 1e-12 for u, 1e-10 for derivatives and gradients (the GPU sums in a
@@ -84,6 +85,7 @@ def test_eval_matches_oracle(B, orc, arch, prec):
     X = _points(widths, n, 9)
     ref = orc.mlp_eval(om, X, with_derivs=False)
     u = m.eval(torch.tensor(X, device="cuda"), prec=prec).cpu().numpy()
+    assert m.device_status() == B.BS_OK
     assert _rel(u, ref) <= TOL_EVAL[prec]
 
 
@@ -162,3 +164,17 @@ def test_training_reduces_loss_fp32(B, orc):
         m.train_step(Xd, kd, prob, lr=1e-3, prec=B.FP32)
     last = sum(m.train_step(Xd, kd, prob, lr=1e-3, prec=B.FP32, want_loss=True))
     assert last < 0.2 * first
+
+
+@pytest.mark.parametrize("w,n_hidden,d_in", [(32, 1, 2), (32, 3, 2), (64, 4, 2), (128, 6, 5), (256, 3, 2)])
+@pytest.mark.parametrize("prec", [2, 3])
+def test_tensor_core_eval_shapes_and_ragged_tiles(B, orc, w, n_hidden, d_in, prec):
+    # tiles of 128 points: 1, 127, 128, 129 and a few thousand points
+    widths = [d_in] + [w] * n_hidden + [1]
+    m, om = _model(B, orc, widths, 21)
+    for n in (1, 127, 128, 129, 2500):
+        X = _points(widths, n, 30 + n)
+        ref = orc.mlp_eval(om, X, with_derivs=False)
+        u = m.eval(torch.tensor(X, device="cuda"), prec=prec).cpu().numpy()
+        assert m.device_status() == B.BS_OK
+        assert _rel(u, ref) <= TOL_EVAL[prec], (n, _rel(u, ref))
