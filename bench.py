@@ -281,6 +281,7 @@ def run_ours(args):
     e2e_step = allreduce_max(ws, statistics.mean(e2e_ms))
 
     batched = batched_leg(B, torch) if args.batched else None
+    pinn = pinn_leg(B, torch)
 
     cpu = None
     if rank == 0:
@@ -321,6 +322,7 @@ def run_ours(args):
         "per_precision": per_prec,
         "train_step": train,
         "batched": batched,
+        "pinn_eval": pinn,
         "setup_ms": setup_ms,
         "wall_s_timed": wall,
     }
@@ -402,6 +404,91 @@ def batched_leg(B, torch, n_inst=4096, solve=True):
     return out
 
 
+def pinn_leg(B, torch, n_points=1 << 24):
+    """Network evaluation throughput: the batched workload's 5->6x128 network on n_points points."""
+    from paper_2303_03848_b300 import synth
+
+    widths = [5] + [128] * 6 + [1]
+    lo, hi = [0.0, 0.0, 0.1, 0.0, 0.5], [8.0, 2.0, 0.5, 0.08, 2.0]
+    m = B.PinnModel(widths, lo, hi, seed=0)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(1)
+    X = torch.rand(n_points, 5, dtype=torch.float64, device="cuda", generator=gen)
+    X = X * (torch.tensor(hi, device="cuda", dtype=torch.float64) - torch.tensor(lo, device="cuda", dtype=torch.float64)) \
+        + torch.tensor(lo, device="cuda", dtype=torch.float64)
+    flops_pt = 2 * sum(widths[l] * widths[l - 1] for l in range(1, len(widths)))
+    tensor_flops_pt = 2 * 5 * 128 * 128
+    tanh_pt = 6 * 128
+    mhz = float(_peaks().get("sm_max_mhz", 2032.0))
+    mufu_peak = 148 * 16 * mhz * 1e6  # tanh.approx.f32: 16 per clock per SM (measured)
+    bf16_peak = float(_peaks().get("bf16_tflops", 1754.7))
+    out = {"network": "5->6x128 tanh->1", "points": n_points}
+    for name, prec in (("fp64", B.FP64), ("fp32", B.FP32), ("bf16", B.BF16)):
+        n = n_points if name != "fp64" else n_points // 16
+        Xn = X[:n].contiguous()
+        m.eval(Xn, prec=prec)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(3):
+            m.eval(Xn, prec=prec)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / 3
+        pps = n / (ms * 1e-3)
+        rec = {"ms": ms, "points": n, "points_per_s": pps, "tflops_algorithmic": flops_pt * pps / 1e12}
+        if name == "bf16":
+            rec.update({"path": "tcgen05 (hidden 128x128 layers), FP32 accumulation in TMEM",
+                        "tensor_tflops": tensor_flops_pt * pps / 1e12,
+                        "tensor_frac_of_bf16_peak": tensor_flops_pt * pps / 1e12 / bf16_peak,
+                        "tanh_per_s": tanh_pt * pps, "tanh_frac_of_mufu_peak": tanh_pt * pps / mufu_peak})
+        out[name] = rec
+    assert m.device_status() == B.BS_OK
+    return out
+
+
+def run_large(args):
+    """Large single instance: Nx=65536, S in [0,8], sigma 0.3, r 0.03, T 2, K 1, P=256, CN 4096 steps/slice."""
+    import torch
+
+    from paper_2303_03848_b300 import binding as B
+    from paper_2303_03848_b300 import build as BUILD
+
+    BUILD.build()
+    cfg = dict(K=1.0, sigma=0.3, r=0.03, T=2.0, Smax=8.0, Nx=65536, P=256, fine_steps=4096, coarse_steps=1)
+    prob = B.Problem(cfg)
+    part = prob.partition(0)
+    ev = lambda: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    a, b = ev()
+    a.record()
+    Uf = prob.serial_fine()
+    b.record()
+    torch.cuda.synchronize()
+    serial_ms = a.elapsed_time(b)
+    U0 = Uf.view(cfg["P"] + 1, cfg["Nx"])[:-1].contiguous().view(-1)
+    Fo = torch.empty_like(U0)
+    a, b = ev()
+    a.record()
+    prob.fine_propagate(U0, Fo)
+    b.record()
+    torch.cuda.synchronize()
+    fine_ms = a.elapsed_time(b)
+    pt = (cfg["Nx"] - 2) * cfg["fine_steps"] * cfg["P"]
+    tf = FLOPS_PER_PT_STEP * pt / (fine_ms * 1e-3) / 1e12
+    peak = 148 * 2 * 2 * float(_peaks().get("sm_max_mhz", 2032.0)) * 1e6 / 1e12
+    a, b = ev()
+    a.record()
+    U, norms, stats, rc = prob.parareal_solve(B.COARSE_IE, tol=1e-9, max_iter=cfg["P"])
+    b.record()
+    torch.cuda.synchronize()
+    err = rel_error(U, Uf, cfg["P"], cfg["Nx"])
+    print(json.dumps({"mode": "large", "config": cfg, "partition": part, "serial_fine_ms": serial_ms,
+                      "fine_ms": fine_ms, "grid_pt_steps_per_s": pt / (fine_ms * 1e-3), "fine_tflops_algorithmic": tf,
+                      "fine_frac_of_fp64_peak": tf / peak, "ie_solve_ms": a.elapsed_time(b),
+                      "ie_iterations": stats[0]["iterations"], "ie_err_vs_serial_fine": err,
+                      "speedup_vs_serial_fine": serial_ms / a.elapsed_time(b), "status": rc}), flush=True)
+
+
 def cpu_baseline(weights, iters, budget_s=20.0):
     """The oracle, as it stands, on the host: one Parareal-PINN iteration per sample."""
     import numpy as np
@@ -479,7 +566,7 @@ def main():
     ap.add_argument("--prec", default="bf16", choices=["fp64", "fp32", "tf32", "bf16"])
     ap.add_argument("--train-steps", type=int, default=5000)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
-    ap.add_argument("--mode", default="solve", choices=["solve", "fine", "batched"],
+    ap.add_argument("--mode", default="solve", choices=["solve", "fine", "batched", "large", "pinn"],
                     help="fine / batched: only the fine propagator on all slices of the benchmark / "
                          "batched workload (profiling)")
     ap.add_argument("--batched", type=int, default=1, help="include the batched-workload leg (1/0)")
@@ -489,6 +576,16 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.mode == "fine":
         run_fine_only(args)
+    elif args.mode == "large":
+        run_large(args)
+    elif args.mode == "pinn":
+        import torch
+
+        from paper_2303_03848_b300 import binding as B
+        from paper_2303_03848_b300 import build as BUILD
+
+        BUILD.build()
+        print(json.dumps(pinn_leg(B, torch)), flush=True)
     elif args.mode == "batched":
         import torch
 
