@@ -4,7 +4,7 @@
 //
 // One CTA of 128 threads owns a tile of 128 points (the M = 128 rows of every
 // layer GEMM, thread t = point t = TMEM lane t).  Per tile:
-//   * input layer (d_in <= 8 inputs -> w): CUDA cores, FP32, tanh, written as
+//   * input layer (2 or 5 inputs -> w): CUDA cores, FP32, tanh, written as
 //     the A operand of the first square layer;
 //   * each square layer h' = tanh(W h + b): one thread issues w/K tcgen05.mma
 //     (M = 128, N = w, K = 16 for BF16 / 8 for TF32) into a TMEM accumulator and
@@ -161,7 +161,7 @@ struct TcArgs {
   int* status;   // BS_TIMEOUT recorded here if a wait gave up
 };
 
-template <bool TF32>
+template <bool TF32, int DIN>
 __global__ void __launch_bounds__(128) mlp_tc_kernel(TcArgs a) {
   constexpr int E = TF32 ? 4 : 2;
   constexpr int KSTEP = TF32 ? 8 : 16;  // K of one MMA
@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(128) mlp_tc_kernel(TcArgs a) {
   const MlpDev& m = a.m;
   const int w = a.w, t = threadIdx.x, warp = t >> 5;
   const int n_sq = m.n_lin - 2;
-  const int d_in = m.d_in;
+  constexpr int d_in = DIN;  // 2 or 5 inputs
   const uint32_t wbytes = (uint32_t)w * w * E;
   // shared memory carve-up
   unsigned char* sW = smem;                                       // n_sq (resident) or 1 square layer
@@ -219,7 +219,8 @@ __global__ void __launch_bounds__(128) mlp_tc_kernel(TcArgs a) {
     const int64_t p = tile * 128 + t;
     const bool valid = p < a.N;
     // input layer on CUDA cores
-    float xh[8];
+    float xh[DIN];
+#pragma unroll
     for (int i = 0; i < d_in; ++i) {
       const double x = valid ? a.X[p * d_in + i] : 0.0;
       xh[i] = (float)(2.0 / (m.hi[i] - m.lo[i]) * (x - m.lo[i]) - 1.0);
@@ -234,6 +235,7 @@ __global__ void __launch_bounds__(128) mlp_tc_kernel(TcArgs a) {
 #pragma unroll
         for (int j = 0; j < 16 / E; ++j) {
           float z = sB[ob + j];
+#pragma unroll
           for (int i = 0; i < d_in; ++i) z = fmaf(sW1[(ob + j) * d_in + i], xh[i], z);
           hv[j] = tanh_fast(z);
         }
@@ -289,10 +291,22 @@ __global__ void __launch_bounds__(128) mlp_tc_kernel(TcArgs a) {
         float v[32];
         tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) v[j] = tanh_fast(v[j] + bl[c + j]);
+        for (int j = 0; j < 32; j += 4) {
+          const float4 bq = *reinterpret_cast<const float4*>(bl + c + j);
+          v[j] = tanh_fast(v[j] + bq.x);
+          v[j + 1] = tanh_fast(v[j + 1] + bq.y);
+          v[j + 2] = tanh_fast(v[j + 2] + bq.z);
+          v[j + 3] = tanh_fast(v[j + 3] + bq.w);
+        }
         if (last) {
 #pragma unroll
-          for (int j = 0; j < 32; ++j) dot = fmaf(sWo[c + j], v[j], dot);
+          for (int j = 0; j < 32; j += 4) {
+            const float4 wq = *reinterpret_cast<const float4*>(sWo + c + j);
+            dot = fmaf(wq.x, v[j], dot);
+            dot = fmaf(wq.y, v[j + 1], dot);
+            dot = fmaf(wq.z, v[j + 2], dot);
+            dot = fmaf(wq.w, v[j + 3], dot);
+          }
         } else if (TF32) {
 #pragma unroll
           for (int j = 0; j < 32; j += 4) {
@@ -329,9 +343,9 @@ __global__ void __launch_bounds__(128) mlp_tc_kernel(TcArgs a) {
 }
 
 // Shape supported by the tensor-core path: all hidden layers w x w (w a multiple
-// of 32, 32 <= w <= 256), d_in <= 8, output width 1.
+// of 32, 32 <= w <= 256), 2 or 5 inputs, output width 1.
 bool tc_supported(const MlpDev& m) {
-  if (m.n_lin < 2 || m.d_in > 8) return false;
+  if (m.n_lin < 2 || !(m.d_in == 2 || m.d_in == 5)) return false;
   const int w = m.widths[1];
   if (w < 32 || w > 256 || (w % 32) != 0) return false;
   for (int l = 1; l < m.n_lin; ++l)
@@ -347,7 +361,9 @@ static size_t tc_smem_bytes(const MlpDev& m, int tf32, int* resident) {
   const size_t wbytes = (size_t)w * w * E;
   const size_t fixed = (size_t)128 * w * E +
                        sizeof(float) * ((size_t)w * m.d_in + (size_t)(m.n_lin - 1) * w + w + 2) + 16 + 1024;
-  const int res = (n_sq > 0 && (size_t)n_sq * wbytes + fixed <= 200 * 1024) ? 1 : 0;
+  // resident only while it still leaves room for several CTAs per SM (latency
+  // hiding); otherwise each layer is reloaded from L2 per tile
+  const int res = (n_sq > 0 && (size_t)n_sq * wbytes + fixed <= 96 * 1024) ? 1 : 0;
   if (resident) *resident = res;
   return (res ? (size_t)n_sq : 1) * wbytes + fixed;
 }
@@ -374,17 +390,30 @@ cudaError_t launch_mlp_eval_tc(const MlpDev& m, int tf32, unsigned char* packed,
   const size_t smem = tc_smem_bytes(m, tf32, &resident);
   if (smem > 220 * 1024) return cudaErrorInvalidValue;
   TcArgs a{m, packed, X, N, u, w, resident, status};
-  auto kern = tf32 ? mlp_tc_kernel<true> : mlp_tc_kernel<false>;
+  auto kern = tf32 ? (m.d_in == 2 ? mlp_tc_kernel<true, 2> : mlp_tc_kernel<true, 5>)
+                   : (m.d_in == 2 ? mlp_tc_kernel<false, 2> : mlp_tc_kernel<false, 5>);
   if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
     return e;
-  int per_sm = 1;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, smem)) != cudaSuccess) return e;
-  if (per_sm < 1) per_sm = 1;
-  if (per_sm > 2) per_sm = 2;  // tensor memory: at most 2 x 256 columns per SM
-  const int64_t ntiles = (N + 127) / 128;
-  int dev = 0, nsm = 148;
+  // CTAs per SM from the shared memory each one takes (dynamic + static + the
+  // per-block reservation) with the carveout at its maximum; the registers
+  // (128 threads x <= 255) never limit below 2
+  if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  if ((e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess) return e;
+  int dev = 0, nsm = 148, sm_smem = 0, reserved = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  int per_sm = (int)((size_t)sm_smem / (smem + fa.sharedSizeBytes + (size_t)reserved));
+  const int by_regs = 65536 / (128 * (fa.numRegs > 0 ? fa.numRegs : 255));
+  if (per_sm > by_regs) per_sm = by_regs;
+  if (per_sm < 1) per_sm = 1;
+  int ncols = 32;
+  while (ncols < w) ncols <<= 1;
+  if (per_sm > 512 / ncols) per_sm = 512 / ncols;  // tensor memory: 512 columns per SM
+  if (per_sm > 4) per_sm = 4;
+  const int64_t ntiles = (N + 127) / 128;
   const int64_t grid = ntiles < (int64_t)nsm * per_sm ? ntiles : (int64_t)nsm * per_sm;
   kern<<<(unsigned)grid, 128, smem, s>>>(a);
   return cudaGetLastError();
