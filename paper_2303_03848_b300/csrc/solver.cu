@@ -302,12 +302,20 @@ __device__ __forceinline__ int cta_rank() {
   }
 }
 
+// The per-step barrier, split so that work independent of the other CTAs'
+// values can run while it completes: arrive (release) after publishing, wait
+// (acquire) before reading.  One CTA: a plain block barrier at the wait.
 template <int C>
-__device__ __forceinline__ void step_barrier() {
+__device__ __forceinline__ void step_arrive() {
+  if constexpr (C > 1) asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+
+template <int C>
+__device__ __forceinline__ void step_wait() {
   if constexpr (C == 1) {
     __syncthreads();
   } else {
-    cg::this_cluster().sync();
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
   }
 }
 
@@ -344,12 +352,16 @@ __device__ __forceinline__ void load_solver(const double* __restrict__ cb, Solve
   __syncthreads();
 }
 
+// One step in two halves around the barrier.  step_reduce: local sweeps,
+// interface right-hand side, in-warp PCR, publication of the warp's boundary
+// values, barrier arrival.  step_finish: barrier wait, cross-warp unknowns,
+// interface values, fixup of the inner rows and the scaled state update.
 // x receives the solution of the step (Z for Crank-Nicolson, V^{m+1} for
 // implicit Euler) on the thread's rows; W is advanced to the next scaled state.
 // Zb is the Dirichlet value of the step (used by the grid's last thread).
-template <int M, int NW, int C, bool CN>
-__device__ __forceinline__ void tri_step(double (&W)[M], double (&x)[M], SolverSmem<M, NW, C>& sm,
-                                         const SolverRegs& rg, double Zb, int par) {
+template <int M, int NW, int C>
+__device__ __forceinline__ double step_reduce(const double (&W)[M], double (&x)[M], SolverSmem<M, NW, C>& sm,
+                                              const SolverRegs& rg, double Zb, int par) {
   constexpr int Ws = C * NW;
   const int t = threadIdx.x, L = t & 31, wl = t >> 5;
   const int c = cta_rank<C>();
@@ -376,7 +388,7 @@ __device__ __forceinline__ void tri_step(double (&W)[M], double (&x)[M], SolverS
     Rp = fma(-rg.m1[lv], up, fma(-rg.m2[lv], dn, Rp));
   }
   const double Xt = Rp * rg.inv;
-  // 4. publish this warp's boundary values to every CTA of the grid, one barrier
+  // 4. publish this warp's boundary values to every CTA of the grid
   const double p0 = __shfl_sync(kFull, x[0], 0);
   const double p1 = __shfl_sync(kFull, Xt, 0);
   const double p2 = __shfl_sync(kFull, Xt, 30);
@@ -397,33 +409,57 @@ __device__ __forceinline__ void tri_step(double (&W)[M], double (&x)[M], SolverS
       rp[3 * Ws + w] = p3;
     }
   }
-  step_barrier<C>();
+  step_arrive<C>();
+  return Xt;
+}
+
+template <int M, int NW, int C, bool CN>
+__device__ __forceinline__ void step_finish(double (&W)[M], double (&x)[M], SolverSmem<M, NW, C>& sm,
+                                            const SolverRegs& rg, double Xt, int par) {
+  constexpr int Ws = C * NW;
+  constexpr int NU = (Ws + 31) / 32;
+  const int t = threadIdx.x, L = t & 31, wl = t >> 5;
+  // constants of the cross-warp solve for the lanes' warps u, read while the
+  // barrier completes
+  double cnu[NU], ca[NU], cc[NU], g0[NU], g1[NU];
+#pragma unroll
+  for (int q = 0; q < NU; ++q) {
+    const int u = q * 32 + L;
+    const bool ok = u < Ws;
+    cnu[q] = ok ? sm.nu31[u] : 0.0;
+    ca[q] = ok ? sm.A31[u] : 0.0;
+    cc[q] = ok ? sm.C31[u] : 0.0;
+    g0[q] = ok ? sm.G2[wl][0][u] : 0.0;
+    g1[q] = ok ? sm.G2[wl][1][u] : 0.0;
+  }
+  step_wait<C>();
   // 5. cross-warp unknowns: rho_u by lane u, then Y_{w-1} and Y_w as dot
-  //    products with rows of the precomputed inverse (butterfly sum)
+  //    products with rows of the precomputed inverse
   double pl = 0.0, pr = 0.0;
 #pragma unroll
-  for (int u0 = 0; u0 < Ws; u0 += 32) {
-    const int u = u0 + L;
+  for (int q = 0; q < NU; ++q) {
+    const int u = q * 32 + L;
     if (u < Ws) {
       double rho;
       if (u == Ws - 1) {
         rho = sm.pub[par][3][u];
       } else {
-        rho = fma(-sm.nu31[u], sm.pub[par][0][u + 1], sm.pub[par][3][u]);
-        rho = fma(-sm.A31[u], sm.pub[par][2][u], rho);
-        rho = fma(-sm.C31[u], sm.pub[par][1][u + 1], rho);
+        rho = fma(-cnu[q], sm.pub[par][0][u + 1], sm.pub[par][3][u]);
+        rho = fma(-ca[q], sm.pub[par][2][u], rho);
+        rho = fma(-cc[q], sm.pub[par][1][u + 1], rho);
       }
-      pl = fma(sm.G2[wl][0][u], rho, pl);
-      pr = fma(sm.G2[wl][1][u], rho, pr);
+      pl = fma(g0[q], rho, pl);
+      pr = fma(g1[q], rho, pr);
     }
   }
+  // reduce-scatter of the two sums: the first level leaves the Y_{w-1} partial
+  // on even lanes and the Y_w partial on odd lanes, then one sum per level
+  const bool odd = (L & 1) != 0;
+  double v = (odd ? pr : pl) + __shfl_xor_sync(kFull, odd ? pl : pr, 1);
 #pragma unroll
-  for (int s = 1; s < (Ws < 32 ? Ws : 32); s <<= 1) {
-    pl += __shfl_xor_sync(kFull, pl, s);
-    pr += __shfl_xor_sync(kFull, pr, s);
-  }
-  const double Yl = __shfl_sync(kFull, pl, 0);
-  const double Yr = __shfl_sync(kFull, pr, 0);
+  for (int s = 2; s < (Ws < 32 ? Ws : 32); s <<= 1) v += __shfl_xor_sync(kFull, v, s);
+  const double Yl = __shfl_sync(kFull, v, 0);
+  const double Yr = __shfl_sync(kFull, v, 1);
   const double X = (L == 31) ? Yr : fma(rg.rc, Yr, fma(rg.ra, Yl, Xt));
   double Xprev = __shfl_up_sync(kFull, X, 1);
   if (L == 0) Xprev = Yl;
@@ -462,22 +498,32 @@ __device__ __forceinline__ double row_value(const double* __restrict__ cb, int k
 }
 
 // Run `steps` steps of the propagator on slice n starting from scaled state W.
+// The right Dirichlet value of the next step is formed while the barrier
+// completes, from exp(-r m dtau) read one step ahead.
 template <int M, int NW, int C, bool CN>
 __device__ __forceinline__ void run_slice(const Inst& in, int n, const double* __restrict__ et, int steps,
                                           double (&W)[M], double (&x)[M], SolverSmem<M, NW, C>& sm,
                                           const SolverRegs& rg, int& par) {
   const double tau_n = in.T * (double)n / (double)in.P;
   const double KeN = in.K * exp(-in.r * tau_n);
-  double Bold = in.Smax - KeN;  // exp(0) = 1
   const bool last_warp = cta_rank<C>() == C - 1 && (threadIdx.x >> 5) == NW - 1;
+  double Bold = in.Smax - KeN;  // exp(0) = 1
+  double Zb = 0.0, e_next = 0.0;
+  if (last_warp) {
+    const double Bnew = fma(-KeN, __ldg(et + 1), in.Smax);
+    Zb = CN ? Bold + Bnew : Bnew;
+    Bold = Bnew;
+    if (steps >= 2) e_next = __ldg(et + 2);
+  }
   for (int m = 0; m < steps; ++m) {
-    double Zb = 0.0;
-    if (last_warp) {
-      const double Bnew = fma(-KeN, __ldg(et + m + 1), in.Smax);
+    const double Xt = step_reduce<M, NW, C>(W, x, sm, rg, Zb, par);
+    if (last_warp) {  // Dirichlet value of step m + 1 (unused after the last step)
+      const double Bnew = fma(-KeN, e_next, in.Smax);
       Zb = CN ? Bold + Bnew : Bnew;
       Bold = Bnew;
+      if (m + 3 <= steps) e_next = __ldg(et + m + 3);
     }
-    tri_step<M, NW, C, CN>(W, x, sm, rg, Zb, par);
+    step_finish<M, NW, C, CN>(W, x, sm, rg, Xt, par);
     par ^= 1;
   }
 }
