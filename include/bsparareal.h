@@ -110,6 +110,16 @@ int bs_problem_info(const bs_problem* prob, int32_t* n_instances, int64_t* total
 int bs_problem_partition(const bs_problem* prob, int32_t i, int32_t* M, int32_t* NW, int32_t* C);
 
 /*
+ * bs_problem_device_status -- synchronises the device and reports the
+ * problem's device status word: BS_OK, or BS_TIMEOUT if a bounded wait of the
+ * per-step exchange between the CTAs of a cluster gave up (the results of that
+ * call are then invalid).  The word is sticky until the handle is destroyed.
+ * parareal_solve and parareal_solve_static return BS_TIMEOUT themselves when
+ * they read statistics back.
+ */
+int bs_problem_device_status(const bs_problem* prob, int* status);
+
+/*
  * fine_propagate -- the fine propagator F of Eq. 6 on every slice at once:
  *   U_out[n] = F_n(U_in[n]): fine_steps Crank-Nicolson steps of
  *   dtau_f = T / (P * fine_steps) from tau_n = n T / P to tau_{n+1}.

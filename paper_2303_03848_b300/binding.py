@@ -69,6 +69,7 @@ def lib() -> ctypes.CDLL:
         L.bs_problem_destroy.restype = None
         L.bs_problem_info.argtypes = [vp, P(i32), P(i64), P(i64)]
         L.bs_problem_partition.argtypes = [vp, i32, P(i32), P(i32), P(i32)]
+        L.bs_problem_device_status.argtypes = [vp, P(ctypes.c_int)]
         for f in (L.fine_propagate, L.coarse_propagate):
             f.argtypes = [vp, vp, vp, vp, vp]
         L.serial_fine.argtypes = [vp, vp, vp]
@@ -172,6 +173,12 @@ class Problem:
         _check(lib().bs_problem_partition(self._h, i, ctypes.byref(M), ctypes.byref(NW), ctypes.byref(C)),
                "bs_problem_partition")
         return dict(M=M.value, NW=NW.value, C=C.value)
+
+    def device_status(self) -> int:
+        """Synchronises and returns the problem's device status word (BS_OK or BS_TIMEOUT)."""
+        s = ctypes.c_int()
+        _check(lib().bs_problem_device_status(self._h, ctypes.byref(s)), "bs_problem_device_status")
+        return s.value
 
     # views -------------------------------------------------------------
     def state_view(self, U, i: int):

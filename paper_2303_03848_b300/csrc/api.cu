@@ -107,6 +107,7 @@ struct bs_problem {
   double* norms_dev = nullptr;
   int norms_cap = 0;
   bsp::Ctrl* ctrl = nullptr;
+  int* d_status = nullptr;  // BS_TIMEOUT once a bounded exchange wait gave up
 };
 
 struct pinn_model {
@@ -158,6 +159,7 @@ void bs_problem_destroy(bs_problem* prob) {
   cudaFree(prob->Xgrid);
   cudaFree(prob->norms_dev);
   cudaFree(prob->ctrl);
+  cudaFree(prob->d_status);
   delete prob;
 }
 
@@ -233,7 +235,8 @@ int bs_problem_init(const bs_params* p, int32_t n_instances, bs_problem** out) {
   }
   cudaError_t e = cudaSuccess;
   if ((e = dalloc(&prob->d_insts, n_instances)) != cudaSuccess ||
-      (e = dalloc(&prob->pool, (size_t)coef)) != cudaSuccess || (e = dalloc(&prob->exptab, (size_t)ex)) != cudaSuccess) {
+      (e = dalloc(&prob->pool, (size_t)coef)) != cudaSuccess || (e = dalloc(&prob->exptab, (size_t)ex)) != cudaSuccess ||
+      (e = dalloc(&prob->d_status, 1)) != cudaSuccess || (e = cudaMemset(prob->d_status, 0, sizeof(int))) != cudaSuccess) {
     bs_problem_destroy(prob);
     return map_err(e);
   }
@@ -261,6 +264,13 @@ int bs_problem_info(const bs_problem* prob, int32_t* n_instances, int64_t* total
   if (total_state_doubles) *total_state_doubles = prob->total_state;
   if (total_slice_doubles) *total_slice_doubles = prob->total_slice;
   return BS_OK;
+}
+
+int bs_problem_device_status(const bs_problem* prob, int* status) {
+  if (!prob || !status) return BS_EINVAL;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(status, prob->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  return map_err(e);
 }
 
 int bs_problem_partition(const bs_problem* prob, int32_t i, int32_t* M, int32_t* NW, int32_t* C) {
@@ -292,6 +302,7 @@ static int propagate(bs_problem* prob, bool cn, const double* U_in, double* U_ou
     a.mode = bsp::PropArgs::kPlain;
     a.k_iter = -1;
     a.active = active;
+    a.status = prob->d_status;
     cudaError_t e = bsp::launch_prop(c.M, c.NW, c.C, cn, a, (int)c.ids.size(), c.maxP, s);
     if (e != cudaSuccess) return map_err(e);
   }
@@ -310,7 +321,7 @@ int serial_fine(bs_problem* prob, double* U_out, void* stream) {
   if (!prob || !U_out || ((uintptr_t)U_out & 15)) return BS_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   for (auto& c : prob->classes) {
-    bsp::SerialArgs a{prob->d_insts, c.d_ids, prob->pool, prob->exptab, U_out};
+    bsp::SerialArgs a{prob->d_insts, c.d_ids, prob->pool, prob->exptab, U_out, prob->d_status};
     cudaError_t e = bsp::launch_serial(c.M, c.NW, c.C, a, (int)c.ids.size(), s);
     if (e != cudaSuccess) return map_err(e);
   }
@@ -580,6 +591,7 @@ int parareal_solve(bs_problem* prob, int coarse_kind, const pinn_model* model, i
       a.fbuf = prob->fbuf;
       a.gtab = prob->gtab;
       a.normbuf = prob->normbuf;
+      a.status = prob->d_status;
       cudaError_t ee = bsp::launch_sweep(c.M, c.NW, c.C, a, (int)c.ids.size(), s);
       if (ee != cudaSuccess) return ee;
     }
@@ -603,6 +615,7 @@ int parareal_solve(bs_problem* prob, int coarse_kind, const pinn_model* model, i
       a.in_state = 1;
       a.k_iter = k;
       a.ctrl = prob->ctrl;
+      a.status = prob->d_status;
       if (coarse_kind == BS_COARSE_PINN) {
         a.out = nxt;
         a.out_state = 1;
@@ -629,7 +642,10 @@ int parareal_solve(bs_problem* prob, int coarse_kind, const pinn_model* model, i
     return map_err(e);
   if (!norms && !stats) return BS_OK;
   std::vector<bsp::Ctrl> hc(n);
+  int dev_status = 0;
   if ((e = cudaMemcpyAsync(hc.data(), prob->ctrl, sizeof(bsp::Ctrl) * n, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return map_err(e);
+  if ((e = cudaMemcpyAsync(&dev_status, prob->d_status, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
     return map_err(e);
   if (norms &&
       (e = cudaMemcpyAsync(norms, prob->norms_dev, sizeof(double) * (size_t)n * max_iter, cudaMemcpyDeviceToHost, s)) !=
@@ -645,7 +661,7 @@ int parareal_solve(bs_problem* prob, int coarse_kind, const pinn_model* model, i
     }
     if (hc[i].status != BS_OK && (worst == BS_OK || hc[i].status == BS_DIVERGED)) worst = hc[i].status;
   }
-  return worst;
+  return dev_status != 0 ? BS_TIMEOUT : worst;
 }
 
 }  // extern "C"
@@ -777,6 +793,7 @@ extern "C" int parareal_solve_static(bs_problem* prob, int coarse_kind, const pi
       a.fbuf = fbuf;
       a.gtab = gtab;
       a.normbuf = nb;
+      a.status = prob->d_status;
       cudaError_t ee = bsp::launch_sweep(c.M, c.NW, c.C, a, (int)c.ids.size(), s);
       if (ee != cudaSuccess) return ee;
     }
@@ -799,6 +816,7 @@ extern "C" int parareal_solve_static(bs_problem* prob, int coarse_kind, const pi
       a.in_state = 1;
       a.k_iter = k;
       a.ctrl = ctrl;
+      a.status = prob->d_status;
       if (coarse_kind == BS_COARSE_PINN) {
         a.out = nxt;
         a.out_state = 1;
@@ -822,7 +840,10 @@ extern "C" int parareal_solve_static(bs_problem* prob, int coarse_kind, const pi
   if ((e = bsp::launch_copy_result(prob->d_insts, n, ctrl, buf0, buf1, U_out, s)) != cudaSuccess) return map_err(e);
   if (!norms && !stats) return BS_OK;
   bsp::Ctrl hc[kStaticMaxInstances];
+  int dev_status = 0;
   if ((e = cudaMemcpyAsync(hc, ctrl, sizeof(bsp::Ctrl) * n, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return map_err(e);
+  if ((e = cudaMemcpyAsync(&dev_status, prob->d_status, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
     return map_err(e);
   if (norms &&
       (e = cudaMemcpyAsync(norms, nrm, sizeof(double) * (size_t)n * max_iter, cudaMemcpyDeviceToHost, s)) !=
@@ -838,5 +859,5 @@ extern "C" int parareal_solve_static(bs_problem* prob, int coarse_kind, const pi
     }
     if (hc[i].status != BS_OK && (worst == BS_OK || hc[i].status == BS_DIVERGED)) worst = hc[i].status;
   }
-  return worst;
+  return dev_status != 0 ? BS_TIMEOUT : worst;
 }

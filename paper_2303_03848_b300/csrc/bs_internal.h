@@ -26,6 +26,7 @@ struct PropArgs {
   const double* gtab;        // kPinnFused: network table (state layout)
   const double* uold;        // kPinnFused: U^k (state layout)
   double* normbuf;           // kPinnFused: (num, den) per (instance, boundary index, cluster rank)
+  int* status;               // nullable: BS_TIMEOUT recorded here if a bounded wait gave up
 };
 
 struct SerialArgs {
@@ -34,6 +35,7 @@ struct SerialArgs {
   const double* pool;
   const double* exptab;
   double* out;  // state layout
+  int* status;  // nullable: BS_TIMEOUT recorded here if a bounded wait gave up
 };
 
 struct SweepArgs {
@@ -50,6 +52,7 @@ struct SweepArgs {
   const double* fbuf;  // F(U^k_n) (slice layout)
   const double* gtab;  // network table (state layout), increment kind
   double* normbuf;
+  int* status;         // nullable: BS_TIMEOUT recorded here if a bounded wait gave up
 };
 
 bool partition_supported(int M, int NW, int C);

@@ -284,14 +284,58 @@ struct SolverSmem {
   double rows[5][M][T];     // lambda, mu, sigma, alpha, beta of this CTA's threads
   double G2[NW][2][Ws];     // rows w-1 and w of the cross-warp inverse, per local warp
   double nu31[Ws], A31[Ws], C31[Ws];
-  double pub[2][4][Ws];     // [step parity][x0, X0, X30, R31][global warp], written by every CTA
+  alignas(16) double pub[2][Ws][4];  // [step parity][global warp][x0, X0, X30, R31], written by every CTA
   double red[2][NW];
+  alignas(8) unsigned long long bar[2];  // C > 1: arrival of a step's values, per parity buffer
 };
 
 struct SolverRegs {
   double kap, nu, sigp, isigp;
   double m1[kPcrLevels], m2[kPcrLevels], inv, ra, rc;
+  int fail;  // a bounded wait gave up (sticky; later waits are skipped)
 };
+
+// Clusters exchange the per-step values with st.async into every CTA's
+// buffer, each store completing transaction bytes on the receiver's mbarrier:
+// one point-to-point arrival per step instead of a cluster-wide barrier.
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint32_t cluster_addr(uint32_t a, int rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t a) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(a) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect(uint32_t a, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void st_async2(uint32_t raddr, double v0, double v1, uint32_t rbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f64 [%0], {%1, %2}, [%3];" ::"r"(raddr),
+               "d"(v0), "d"(v1), "r"(rbar)
+               : "memory");
+}
+
+// Wait for phase parity ph of the mbarrier at a, at most about 2^31 cycles (one
+// second); false when the limit was reached.
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t ph) {
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(ph)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > (1ll << 31)) return false;
+  }
+}
 
 template <int C>
 __device__ __forceinline__ int cta_rank() {
@@ -299,23 +343,6 @@ __device__ __forceinline__ int cta_rank() {
     return 0;
   } else {
     return (int)cg::this_cluster().block_rank();
-  }
-}
-
-// The per-step barrier, split so that work independent of the other CTAs'
-// values can run while it completes: arrive (release) after publishing, wait
-// (acquire) before reading.  One CTA: a plain block barrier at the wait.
-template <int C>
-__device__ __forceinline__ void step_arrive() {
-  if constexpr (C > 1) asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
-}
-
-template <int C>
-__device__ __forceinline__ void step_wait() {
-  if constexpr (C == 1) {
-    __syncthreads();
-  } else {
-    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
   }
 }
 
@@ -349,7 +376,25 @@ __device__ __forceinline__ void load_solver(const double* __restrict__ cb, Solve
     const int row = c * NW + wl - 1 + side;  // global warp w-1 (side 0) or w (side 1)
     sm.G2[wl][side][u] = row >= 0 ? cb[coef_G_off(row, u, M, GT, Ws)] : 0.0;
   }
-  __syncthreads();
+  rg.fail = 0;
+  if (C > 1 && t == 0) {
+    mbar_init(smem_addr(&sm.bar[0]));
+    mbar_init(smem_addr(&sm.bar[1]));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();  // the kernel's cluster barrier follows before any exchange
+}
+
+// A CTA whose wait gave up records BS_TIMEOUT and waits (again bounded) for the
+// values of the last two steps that may still be arriving in its buffers.
+template <int M, int NW, int C>
+__device__ __forceinline__ void exchange_drain(SolverSmem<M, NW, C>& sm, const SolverRegs& rg, int seq, int* status) {
+  if constexpr (C > 1) {
+    if (!rg.fail) return;
+    for (int q = seq - 2; q < seq; ++q)
+      if (q >= 0) (void)mbar_wait(smem_addr(&sm.bar[q & 1]), (uint32_t)(q >> 1) & 1u);
+    if (status != nullptr && threadIdx.x == 0) atomicExch(status, 6);  // BS_TIMEOUT
+  }
 }
 
 // One step in two halves around the barrier.  step_reduce: local sweeps,
@@ -361,7 +406,8 @@ __device__ __forceinline__ void load_solver(const double* __restrict__ cb, Solve
 // Zb is the Dirichlet value of the step (used by the grid's last thread).
 template <int M, int NW, int C>
 __device__ __forceinline__ double step_reduce(const double (&W)[M], double (&x)[M], SolverSmem<M, NW, C>& sm,
-                                              const SolverRegs& rg, double Zb, int par) {
+                                              const SolverRegs& rg, double Zb, int seq) {
+  const int par = seq & 1;
   constexpr int Ws = C * NW;
   const int t = threadIdx.x, L = t & 31, wl = t >> 5;
   const int c = cta_rank<C>();
@@ -395,32 +441,34 @@ __device__ __forceinline__ double step_reduce(const double (&W)[M], double (&x)[
   const double p3 = __shfl_sync(kFull, R, 31);
   if constexpr (C == 1) {
     if (L == 0) {
-      sm.pub[par][0][w] = p0;
-      sm.pub[par][1][w] = p1;
-      sm.pub[par][2][w] = p2;
-      sm.pub[par][3][w] = p3;
+      sm.pub[par][w][0] = p0;
+      sm.pub[par][w][1] = p1;
+      sm.pub[par][w][2] = p2;
+      sm.pub[par][w][3] = p3;
     }
   } else {
+    // this CTA expects 32 bytes from every warp of the grid; lane L sends this
+    // warp's 32 bytes to CTA L
+    if (t == 0) mbar_expect(smem_addr(&sm.bar[par]), (uint32_t)Ws * 32u);
     if (L < C) {
-      double* rp = cg::this_cluster().map_shared_rank(&sm.pub[par][0][0], L);
-      rp[0 * Ws + w] = p0;
-      rp[1 * Ws + w] = p1;
-      rp[2 * Ws + w] = p2;
-      rp[3 * Ws + w] = p3;
+      const uint32_t slot = cluster_addr(smem_addr(&sm.pub[par][w][0]), L);
+      const uint32_t rbar = cluster_addr(smem_addr(&sm.bar[par]), L);
+      st_async2(slot, p0, p1, rbar);
+      st_async2(slot + 16u, p2, p3, rbar);
     }
   }
-  step_arrive<C>();
   return Xt;
 }
 
 template <int M, int NW, int C, bool CN>
 __device__ __forceinline__ void step_finish(double (&W)[M], double (&x)[M], SolverSmem<M, NW, C>& sm,
-                                            const SolverRegs& rg, double Xt, int par) {
+                                            SolverRegs& rg, double Xt, int seq) {
+  const int par = seq & 1;
   constexpr int Ws = C * NW;
   constexpr int NU = (Ws + 31) / 32;
   const int t = threadIdx.x, L = t & 31, wl = t >> 5;
   // constants of the cross-warp solve for the lanes' warps u, read while the
-  // barrier completes
+  // other CTAs' values arrive
   double cnu[NU], ca[NU], cc[NU], g0[NU], g1[NU];
 #pragma unroll
   for (int q = 0; q < NU; ++q) {
@@ -432,7 +480,11 @@ __device__ __forceinline__ void step_finish(double (&W)[M], double (&x)[M], Solv
     g0[q] = ok ? sm.G2[wl][0][u] : 0.0;
     g1[q] = ok ? sm.G2[wl][1][u] : 0.0;
   }
-  step_wait<C>();
+  if constexpr (C == 1) {
+    __syncthreads();
+  } else {
+    if (!rg.fail && !mbar_wait(smem_addr(&sm.bar[par]), (uint32_t)(seq >> 1) & 1u)) rg.fail = 1;
+  }
   // 5. cross-warp unknowns: rho_u by lane u, then Y_{w-1} and Y_w as dot
   //    products with rows of the precomputed inverse
   double pl = 0.0, pr = 0.0;
@@ -442,11 +494,11 @@ __device__ __forceinline__ void step_finish(double (&W)[M], double (&x)[M], Solv
     if (u < Ws) {
       double rho;
       if (u == Ws - 1) {
-        rho = sm.pub[par][3][u];
+        rho = sm.pub[par][u][3];
       } else {
-        rho = fma(-cnu[q], sm.pub[par][0][u + 1], sm.pub[par][3][u]);
-        rho = fma(-ca[q], sm.pub[par][2][u], rho);
-        rho = fma(-cc[q], sm.pub[par][1][u + 1], rho);
+        rho = fma(-cnu[q], sm.pub[par][u + 1][0], sm.pub[par][u][3]);
+        rho = fma(-ca[q], sm.pub[par][u][2], rho);
+        rho = fma(-cc[q], sm.pub[par][u + 1][1], rho);
       }
       pl = fma(g0[q], rho, pl);
       pr = fma(g1[q], rho, pr);
@@ -503,7 +555,7 @@ __device__ __forceinline__ double row_value(const double* __restrict__ cb, int k
 template <int M, int NW, int C, bool CN>
 __device__ __forceinline__ void run_slice(const Inst& in, int n, const double* __restrict__ et, int steps,
                                           double (&W)[M], double (&x)[M], SolverSmem<M, NW, C>& sm,
-                                          const SolverRegs& rg, int& par) {
+                                          SolverRegs& rg, int& seq) {
   const double tau_n = in.T * (double)n / (double)in.P;
   const double KeN = in.K * exp(-in.r * tau_n);
   const bool last_warp = cta_rank<C>() == C - 1 && (threadIdx.x >> 5) == NW - 1;
@@ -516,15 +568,15 @@ __device__ __forceinline__ void run_slice(const Inst& in, int n, const double* _
     if (steps >= 2) e_next = __ldg(et + 2);
   }
   for (int m = 0; m < steps; ++m) {
-    const double Xt = step_reduce<M, NW, C>(W, x, sm, rg, Zb, par);
+    const double Xt = step_reduce<M, NW, C>(W, x, sm, rg, Zb, seq);
     if (last_warp) {  // Dirichlet value of step m + 1 (unused after the last step)
       const double Bnew = fma(-KeN, e_next, in.Smax);
       Zb = CN ? Bold + Bnew : Bnew;
       Bold = Bnew;
       if (m + 3 <= steps) e_next = __ldg(et + m + 3);
     }
-    step_finish<M, NW, C, CN>(W, x, sm, rg, Xt, par);
-    par ^= 1;
+    step_finish<M, NW, C, CN>(W, x, sm, rg, Xt, seq);
+    ++seq;
   }
 }
 
@@ -587,8 +639,8 @@ __global__ void __launch_bounds__(NW * 32, 1) prop_kernel(PropArgs a) {
   load_state<M, NW, C>(in, Vin, sm, rg, W);
 #pragma unroll
   for (int k = 0; k < M; ++k) x[k] = 0.0;
-  int par = 0;
-  run_slice<M, NW, C, CN>(in, n, et, steps, W, x, sm, rg, par);
+  int seq = 0;
+  run_slice<M, NW, C, CN>(in, n, et, steps, W, x, sm, rg, seq);
 
   const bool first_thread = c == 0 && t == 0;
   const bool last_thread = c == C - 1 && t == T - 1;
@@ -647,7 +699,8 @@ __global__ void __launch_bounds__(NW * 32, 1) prop_kernel(PropArgs a) {
       a.normbuf[slot + 1] = den;
     }
   }
-  if constexpr (C > 1) cg::this_cluster().sync();  // no CTA leaves while its shared memory may be read
+  exchange_drain<M, NW, C>(sm, rg, seq, a.status);
+  if constexpr (C > 1) cg::this_cluster().sync();  // no CTA leaves while its shared memory may be written
 }
 
 // Classical serial fine time stepping (Eq. 6): one cluster per instance walks
@@ -675,13 +728,13 @@ __global__ void __launch_bounds__(NW * 32, 1) serial_fine_kernel(SerialArgs a) {
   } else {
     __syncthreads();
   }
-  int par = 0;
+  int seq = 0;
   for (int n = 0; n < in.P; ++n) {
     double W[M], x[M];
     load_state<M, NW, C>(in, U + (int64_t)n * Nx, sm, rg, W);
 #pragma unroll
     for (int k = 0; k < M; ++k) x[k] = 0.0;
-    run_slice<M, NW, C, true>(in, n, et, in.Mf, W, x, sm, rg, par);
+    run_slice<M, NW, C, true>(in, n, et, in.Mf, W, x, sm, rg, seq);
     double* Vout = U + (int64_t)(n + 1) * Nx;
 #pragma unroll
     for (int k = 0; k < M; ++k) {
@@ -698,6 +751,8 @@ __global__ void __launch_bounds__(NW * 32, 1) serial_fine_kernel(SerialArgs a) {
       __syncthreads();
     }
   }
+  exchange_drain<M, NW, C>(sm, rg, seq, a.status);
+  if constexpr (C > 1) cg::this_cluster().sync();
 }
 
 // ---------------------------------------------------------------------------
@@ -744,7 +799,7 @@ __global__ void __launch_bounds__(NW * 32, 1) sweep_kernel(SweepArgs a) {
   if (!init) {
     for (int j = g; j < Nx; j += C * T) Un[(int64_t)n0 * Nx + j] = Vs[j];
   }
-  int par = 0;
+  int seq = 0;
   for (int n = n0; n < in.P; ++n) {
     double Gv[M];
     double G0, GB;
@@ -757,7 +812,7 @@ __global__ void __launch_bounds__(NW * 32, 1) sweep_kernel(SweepArgs a) {
         W[k] = (k < M - 1) ? sm.rows[2][k][t] * v : rg.sigp * v;
         x[k] = 0.0;
       }
-      run_slice<M, NW, C, false>(in, n, et, in.Mg, W, x, sm, rg, par);
+      run_slice<M, NW, C, false>(in, n, et, in.Mg, W, x, sm, rg, seq);
 #pragma unroll
       for (int k = 0; k < M; ++k) Gv[k] = x[k];
       G0 = 0.0;
@@ -825,6 +880,7 @@ __global__ void __launch_bounds__(NW * 32, 1) sweep_kernel(SweepArgs a) {
     }
     __syncthreads();
   }
+  exchange_drain<M, NW, C>(sm, rg, seq, a.status);
   if constexpr (C > 1) cg::this_cluster().sync();
 }
 

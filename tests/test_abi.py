@@ -56,6 +56,7 @@ def test_null_arguments_rejected(L):
     assert L.serial_fine(None, None, None) == B.BS_EINVAL
     assert L.parareal_solve(None, 0, None, 0, 1e-6, 4, None, None, None, None) == B.BS_EINVAL
     assert L.pinn_eval(None, 0, None, 1, None, None, None) == B.BS_EINVAL
+    assert L.bs_problem_device_status(None, None) == B.BS_EINVAL
     L.bs_problem_destroy(None)
     L.pinn_destroy(None)
 

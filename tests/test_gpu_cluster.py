@@ -67,6 +67,8 @@ def test_propagators_match_oracle_forced_cluster(B, orc, monkeypatch, C):
             sl = slice(o + n * p["Nx"], o + (n + 1) * p["Nx"])
             _close(F[sl], orc.fine(op, n, parts[i][n]), _tol(p, "fine"))
             _close(G[sl], orc.coarse_ie(op, n, parts[i][n]), _tol(p, "coarse"))
+    # no bounded wait of the per-step exchange gave up
+    assert prob.device_status() == B.BS_OK
 
 
 def test_largest_grid_65536_points(B, orc):
@@ -94,6 +96,7 @@ def test_largest_grid_serial_fine_and_parareal(B, orc):
     U, norms, stats, rc = prob.parareal_solve(B.COARSE_IE, tol=0.0)
     assert rc == B.BS_OK and stats[0]["iterations"] == p["P"]
     assert torch.equal(U, Uf)
+    assert prob.device_status() == B.BS_OK
 
 
 @pytest.mark.parametrize("C", [2, 4, 8])
