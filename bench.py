@@ -179,20 +179,32 @@ def choose_tol(prob, kind, model, prec, Uf, B):
     return 0.0, CFG["P"], err
 
 
-def time_solves(prob, kind, model, prec, tol, steps, warmup, torch, flush):
+def time_solves(prob, kind, model, prec, tol, steps, warmup, torch, flush, graph=True):
+    """Device time per solve (CUDA events), L2 flushed between solves.  graph: the
+    solve is captured once in a CUDA graph and replayed (one launch per solve);
+    otherwise each solve is enqueued by the host loop of parareal_solve."""
+    from paper_2303_03848_b300 import binding as B
+
+    g = B.SolveGraph(prob, kind, model=model, prec=prec, tol=tol) if graph else None
+
+    def once():
+        if g is not None:
+            return g.replay()
+        return prob.parareal_solve(kind, model=model, prec=prec, tol=tol, want_stats=False)[0]
+
     for _ in range(warmup):
-        prob.parareal_solve(kind, model=model, prec=prec, tol=tol, want_stats=False)
+        once()
     torch.cuda.synchronize()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     U = None
     for i in range(steps):
         flush.add_(1.0)  # 256 MB write: evicts L2 between timed steps
         evs[i][0].record()
-        U, *_ = prob.parareal_solve(kind, model=model, prec=prec, tol=tol, want_stats=False)
+        U = once()
         evs[i][1].record()
     torch.cuda.synchronize()
     ms = [a.elapsed_time(b) for a, b in evs]
-    return ms, U
+    return ms, U.clone()
 
 
 def run_ours(args):
@@ -229,6 +241,7 @@ def run_ours(args):
     err_after = rel_error(U, Uf, CFG["P"], CFG["Nx"])
     ms_step = allreduce_max(ws, sum(ms) / len(ms))
     value = ws * 1e3 / ms_step
+    ms_direct, _ = time_solves(prob, B.COARSE_PINN, model, prec, tol, 2, 1, torch, flush, graph=False)
 
     # fine kernel alone: iteration-0 launch shape (all P slices), CUDA events on the current stream
     U0 = Uf.view(CFG["P"] + 1, CFG["Nx"])[:-1].contiguous().view(-1)
@@ -305,6 +318,8 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "coarse": "pinn", "pinn_precision": args.prec, "tol": tol,
                    "iterations": iters, "err_vs_serial_fine": err_after, "l2_flush": "256 MB write between steps",
+                   "launch": "whole solve captured in one CUDA graph, replayed per step",
+                   "ms_per_solve_host_loop": statistics.mean(ms_direct),
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
         "e2e": {"value": ws * 1e3 / e2e_step, "unit": "solves/s", "h2d_bytes_per_step": 8 * model.n_params,
                 "d2h_bytes_per_step": 8 * prob.total_state},
@@ -355,39 +370,57 @@ def run_fine_only(args):
                       "tflops_algorithmic": FLOPS_PER_PT_STEP * pt / (ms * 1e-3) / 1e12}), flush=True)
 
 
-def batched_leg(B, torch, n_inst=4096, solve=True):
+def batched_leg(B, torch, n_inst=4096, solve=True, rule_too=False):
     """Batched workload: n_inst instances (K, sigma, r, T, Nx seeded), P=64, CN 256 steps/slice.
 
-    Times fine_propagate over every slice of every instance (one launch per
-    partition class) and, optionally, one implicit-Euler-coarse Parareal solve
-    of the whole batch at tol 1e-6.
+    The partition of every grid size is picked by the autotuner
+    (bs_problem_init_tuned).  Times fine_propagate over every slice of every
+    instance (one launch per partition class) and, optionally, one
+    implicit-Euler-coarse Parareal solve of the whole batch at tol 1e-6.
+    rule_too: also time the built-in partition rule for comparison.
     """
     from paper_2303_03848_b300 import synth
 
     insts = synth.batched_instances(0, n_inst, P=64, fine_steps=256, coarse_steps=1)
-    t0 = time.perf_counter()
-    prob = B.Problem(insts)
-    setup_s = time.perf_counter() - t0
+    pt = sum((p["Nx"] - 2) * p["fine_steps"] * p["P"] for p in insts)
+    peak = 148 * 2 * 2 * float(_peaks().get("sm_max_mhz", 2032.0)) * 1e6 / 1e12
     gen = torch.Generator(device="cuda")
     gen.manual_seed(0)
-    Uin = torch.rand(prob.total_slice, dtype=torch.float64, device="cuda", generator=gen)
-    Fo = torch.empty_like(Uin)
-    prob.fine_propagate(Uin, Fo)
-    torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(2)]
-    for a, b in ev:
-        a.record()
+
+    def time_fine(prob):
+        Uin = torch.rand(prob.total_slice, dtype=torch.float64, device="cuda", generator=gen)
+        Fo = torch.empty_like(Uin)
         prob.fine_propagate(Uin, Fo)
-        b.record()
-    torch.cuda.synchronize()
-    ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
-    pt = sum((p["Nx"] - 2) * p["fine_steps"] * p["P"] for p in insts)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(2)]
+        for a, b in ev:
+            a.record()
+            prob.fine_propagate(Uin, Fo)
+            b.record()
+        torch.cuda.synchronize()
+        assert prob.device_status() == B.BS_OK
+        return statistics.mean(a.elapsed_time(b) for a, b in ev)
+
+    out = {"instances": n_inst, "P": 64, "fine_steps": 256, "Nx": "uniform over 256..4096"}
+    if rule_too:
+        rule = B.Problem(insts)
+        ms = time_fine(rule)
+        out["rule_partition"] = {"fine_ms": ms, "fine_frac_of_fp64_peak": FLOPS_PER_PT_STEP * pt / (ms * 1e-3) / 1e12 / peak,
+                                 "partitions": sorted({(p["Nx"], tuple(rule.partition(i).values()))
+                                                       for i, p in enumerate(insts)})}
+        rule.close()
+        torch.cuda.empty_cache()
+    t0 = time.perf_counter()
+    prob = B.Problem(insts, tuned=True)
+    setup_s = time.perf_counter() - t0
+    ms = time_fine(prob)
     tf = FLOPS_PER_PT_STEP * pt / (ms * 1e-3) / 1e12
-    peak = 148 * 2 * 2 * float(_peaks().get("sm_max_mhz", 2032.0)) * 1e6 / 1e12
-    out = {"instances": n_inst, "P": 64, "fine_steps": 256, "Nx": "uniform over 256..4096",
-           "setup_s": setup_s, "fine_ms": ms, "grid_pt_steps_per_s": pt / (ms * 1e-3),
-           "fine_tflops_algorithmic": tf, "fine_frac_of_fp64_peak": tf / peak}
-    del Uin, Fo
+    chosen = {r["Nx"]: "M=%d NW=%d C=%d" % (r["M"], r["NW"], r["C"]) for r in prob.tuning if r["chosen"]}
+    out.update({"setup_s_with_tuning": setup_s, "tuned_partitions": {str(k): v for k, v in sorted(chosen.items())},
+                "candidates_timed": len(prob.tuning),
+                "fine_ms": ms, "grid_pt_steps_per_s": pt / (ms * 1e-3),
+                "fine_tflops_algorithmic": tf, "fine_frac_of_fp64_peak": tf / peak})
+    torch.cuda.empty_cache()
     if solve:
         s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s0.record()
@@ -593,7 +626,7 @@ def main():
         from paper_2303_03848_b300 import build as BUILD
 
         BUILD.build()
-        print(json.dumps(batched_leg(B, torch, n_inst=args.instances, solve=False)), flush=True)
+        print(json.dumps(batched_leg(B, torch, n_inst=args.instances, solve=False, rule_too=True)), flush=True)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -92,12 +92,40 @@ const char* bs_version(void);
  *   Each grid is laid out over one CTA (one SM) or, when the problem has few
  *   slices or more than 4096 rows, over a cluster of up to 16 CTAs that
  *   exchange interface values through distributed shared memory; the
- *   environment variable BSP_CLUSTER (1, 2, 4, 8, 16) overrides the choice.
+ *   environment variable BSP_CLUSTER (1, 2, 4, 8, 16) overrides the cluster
+ *   size, and BSP_PARTITION="M,NW,C" forces one compiled partition (M rows per
+ *   thread, NW warps per CTA, C CTAs) on every instance (BS_EUNSUPPORTED if it
+ *   is not compiled or holds fewer than Nx - 1 rows).
  *   Synchronous.  *out receives the handle.  Errors: BS_EINVAL (argument),
  *   BS_EUNSUPPORTED (Nx above the largest grid this build keeps on chip),
  *   BS_ENOMEM, BS_ECUDA.
  */
 int bs_problem_init(const bs_params* p, int32_t n_instances, bs_problem** out);
+
+/* One timed candidate of bs_problem_init_tuned. */
+typedef struct {
+  int32_t Nx;            /* grid size the candidate was timed for */
+  int32_t M, NW, C;      /* rows per thread, warps per CTA, CTAs per grid */
+  float ms;              /* device time of one fine propagation of the tuning subset */
+  int32_t chosen;        /* 1 for the partition kept for this grid size */
+} bs_tuning;
+
+/*
+ * bs_problem_init_tuned -- bs_problem_init with the partition of every grid
+ * size picked by measurement instead of the built-in rule: for each distinct
+ * Nx, every compiled partition (M rows per thread x NW warps x C CTAs) that
+ * holds the grid with at most half of its rows padding is set up for a subset
+ * of the problem's own instances of that size (enough for >= 4096 slices, fine
+ * steps capped at 128) and timed on one fine propagation (CUDA events, best of
+ * two after a warm-up); the fastest is kept.  Few slices favour clusters and
+ * several warps per grid (latency), many slices one warp per grid with more
+ * rows per thread (throughput).  report (host, nullable when report_cap = 0)
+ * receives up to report_cap timed candidates and *n_report (nullable) their
+ * number.  Synchronous; the tuning runs on the default stream.  Errors as
+ * bs_problem_init; BS_TIMEOUT if a timed candidate's exchange wait gave up.
+ */
+int bs_problem_init_tuned(const bs_params* p, int32_t n_instances, bs_problem** out, bs_tuning* report,
+                          int32_t report_cap, int32_t* n_report);
 
 /* Release the handle and its device memory.  NULL is accepted. */
 void bs_problem_destroy(bs_problem* prob);

@@ -49,6 +49,11 @@ class InstanceStats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("status", ctypes.c_int32), ("final_norm", ctypes.c_double)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("Nx", ctypes.c_int32), ("M", ctypes.c_int32), ("NW", ctypes.c_int32), ("C", ctypes.c_int32),
+                ("ms", ctypes.c_float), ("chosen", ctypes.c_int32)]
+
+
 def lib() -> ctypes.CDLL:
     """Load the library (raises if it has not been built)."""
     global _lib
@@ -65,6 +70,7 @@ def lib() -> ctypes.CDLL:
         L.bs_version.argtypes = []
         L.bs_version.restype = ctypes.c_char_p
         L.bs_problem_init.argtypes = [P(BsParams), i32, P(vp)]
+        L.bs_problem_init_tuned.argtypes = [P(BsParams), i32, P(vp), P(Tuning), i32, P(i32)]
         L.bs_problem_destroy.argtypes = [vp]
         L.bs_problem_destroy.restype = None
         L.bs_problem_info.argtypes = [vp, P(i32), P(i64), P(i64)]
@@ -137,13 +143,25 @@ def _to_struct(d) -> BsParams:
 class Problem:
     """Handle of bs_problem_init: one or more pricing instances on the current device."""
 
-    def __init__(self, instances):
+    def __init__(self, instances, tuned: bool = False):
+        """tuned: pick each grid size's partition by timing (bs_problem_init_tuned); the
+        timed candidates are kept in self.tuning."""
         if isinstance(instances, dict):
             instances = [instances]
         self.instances = [dict(p) for p in instances]
         arr = (BsParams * len(self.instances))(*[_to_struct(p) for p in self.instances])
         h = ctypes.c_void_p()
-        _check(lib().bs_problem_init(arr, len(self.instances), ctypes.byref(h)), "bs_problem_init")
+        self.tuning = []
+        if tuned:
+            cap = 256
+            rep = (Tuning * cap)()
+            nrep = ctypes.c_int32()
+            _check(lib().bs_problem_init_tuned(arr, len(self.instances), ctypes.byref(h), rep, cap, ctypes.byref(nrep)),
+                   "bs_problem_init_tuned")
+            self.tuning = [dict(Nx=r.Nx, M=r.M, NW=r.NW, C=r.C, ms=r.ms, chosen=bool(r.chosen))
+                           for r in rep[:min(nrep.value, cap)]]
+        else:
+            _check(lib().bs_problem_init(arr, len(self.instances), ctypes.byref(h)), "bs_problem_init")
         self._h = h
         n, ts, tl = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64()
         _check(lib().bs_problem_info(h, ctypes.byref(n), ctypes.byref(ts), ctypes.byref(tl)), "bs_problem_info")
@@ -242,6 +260,35 @@ class Problem:
             norms = np_norms.reshape(self.n_instances, max_iter)
             stats = [dict(iterations=s.iterations, status=s.status, final_norm=s.final_norm) for s in stats]
         return U_out, norms, stats, rc
+
+
+class SolveGraph:
+    """One Parareal solve captured in a CUDA graph: replay() re-runs the whole
+    solve (network table, initial iterate, every iteration's propagation,
+    correction and stop test) as one graph launch on the current stream.
+
+    The device-side stop rule makes the captured iterations past convergence
+    return at once.  A first solve outside the capture allocates the
+    workspace; the captured call reads nothing back, so statistics come from a
+    separate parareal_solve call."""
+
+    def __init__(self, prob, coarse_kind=COARSE_IE, model=None, prec=FP64, tol=1e-10, max_iter=None):
+        import torch
+
+        self.prob = prob
+        self.U = torch.empty(prob.total_state, dtype=torch.float64, device="cuda")
+        args = dict(coarse_kind=coarse_kind, model=model, prec=prec, tol=tol, max_iter=max_iter, U_out=self.U,
+                    want_stats=False)
+        prob.parareal_solve(**args)
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, capture_error_mode="thread_local"):
+            prob.parareal_solve(**args)
+        torch.cuda.synchronize()
+
+    def replay(self):
+        self.graph.replay()
+        return self.U
 
 
 class PinnModel:

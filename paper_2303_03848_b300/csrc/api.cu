@@ -89,7 +89,37 @@ int cluster_target(const bs_params* p, int n) {
   return c;
 }
 
+struct Part {
+  int M, NW, C;
+};
+
+// Every compiled partition that holds an Nx-point grid with at most half of
+// its rows padding.
+std::vector<Part> candidate_partitions(int Nx) {
+  std::vector<Part> out;
+  const int rows = Nx - 1;
+  for (int C = 1; C <= 16; C *= 2)
+    for (int NW = 1; NW <= 4; NW *= 2)
+      for (int M = 2; M <= 32; M *= 2) {
+        const int64_t R = (int64_t)M * NW * 32 * C;
+        if (R >= rows && 2 * (R - rows) <= R && bsp::partition_supported(M, NW, C)) out.push_back(Part{M, NW, C});
+      }
+  return out;
+}
+
+int validate(const bs_params* p, int32_t n_instances) {
+  for (int i = 0; i < n_instances; ++i) {
+    const bs_params& q = p[i];
+    if (!finite_pos(q.K) || !finite_pos(q.sigma) || !std::isfinite(q.r) || q.r < 0.0 || !finite_pos(q.T) ||
+        !finite_pos(q.Smax) || !(q.Smax > q.K) || q.Nx < 5 || q.P < 1 || q.fine_steps < 1 || q.coarse_steps < 1)
+      return BS_EINVAL;
+  }
+  return BS_OK;
+}
+
 }  // namespace
+
+static int problem_create(const bs_params* p, int32_t n_instances, const Part* parts, bs_problem** out);
 
 struct bs_problem {
   int n_inst = 0;
@@ -163,20 +193,11 @@ void bs_problem_destroy(bs_problem* prob) {
   delete prob;
 }
 
-int bs_problem_init(const bs_params* p, int32_t n_instances, bs_problem** out) {
-  if (!p || !out || n_instances <= 0) return BS_EINVAL;
+}  // extern "C"
+
+// The handle for given partitions (one per instance): device tables, set-up kernels.
+static int problem_create(const bs_params* p, int32_t n_instances, const Part* parts, bs_problem** out) {
   *out = nullptr;
-  for (int i = 0; i < n_instances; ++i) {
-    const bs_params& q = p[i];
-    if (!finite_pos(q.K) || !finite_pos(q.sigma) || !std::isfinite(q.r) || q.r < 0.0 || !finite_pos(q.T) ||
-        !finite_pos(q.Smax) || !(q.Smax > q.K) || q.Nx < 5 || q.P < 1 || q.fine_steps < 1 || q.coarse_steps < 1)
-      return BS_EINVAL;
-  }
-  const int cl_target = cluster_target(p, n_instances);
-  for (int i = 0; i < n_instances; ++i) {
-    int M, NW, C;
-    if (!choose_partition(p[i].Nx, cl_target, &M, &NW, &C)) return BS_EUNSUPPORTED;
-  }
   bs_problem* prob = new (std::nothrow) bs_problem();
   if (!prob) return BS_ENOMEM;
   prob->n_inst = n_instances;
@@ -195,7 +216,9 @@ int bs_problem_init(const bs_params* p, int32_t n_instances, bs_problem** out) {
     in.P = q.P;
     in.Mf = q.fine_steps;
     in.Mg = q.coarse_steps;
-    choose_partition(q.Nx, cl_target, &in.M, &in.NW, &in.C);
+    in.M = parts[i].M;
+    in.NW = parts[i].NW;
+    in.C = parts[i].C;
     in.Ws = in.C * in.NW;
     in.R = in.Ws * 32 * in.M;
     in.Np = in.R - (q.Nx - 1);
@@ -255,6 +278,127 @@ int bs_problem_init(const bs_params* p, int32_t n_instances, bs_problem** out) {
   }
   *out = prob;
   return BS_OK;
+}
+
+extern "C" {
+
+int bs_problem_init(const bs_params* p, int32_t n_instances, bs_problem** out) {
+  if (!p || !out || n_instances <= 0) return BS_EINVAL;
+  *out = nullptr;
+  if (validate(p, n_instances) != BS_OK) return BS_EINVAL;
+  const int cl_target = cluster_target(p, n_instances);
+  std::vector<Part> parts(n_instances);
+  Part forced{0, 0, 0};
+  if (const char* env = getenv("BSP_PARTITION")) {  // "M,NW,C" for every instance
+    if (sscanf(env, "%d,%d,%d", &forced.M, &forced.NW, &forced.C) != 3 ||
+        !bsp::partition_supported(forced.M, forced.NW, forced.C))
+      return BS_EUNSUPPORTED;
+  }
+  for (int i = 0; i < n_instances; ++i) {
+    if (forced.M > 0) {
+      if ((int64_t)forced.M * forced.NW * 32 * forced.C < p[i].Nx - 1) return BS_EUNSUPPORTED;
+      parts[i] = forced;
+    } else if (!choose_partition(p[i].Nx, cl_target, &parts[i].M, &parts[i].NW, &parts[i].C)) {
+      return BS_EUNSUPPORTED;
+    }
+  }
+  return problem_create(p, n_instances, parts.data(), out);
+}
+
+// Device time of one fine_propagate over the instances `sub` (all with the
+// partition `part`) on zero states, best of two runs after one warm-up run.
+static int time_partition(const std::vector<bs_params>& sub, Part part, float* ms) {
+  std::vector<Part> parts(sub.size(), part);
+  bs_problem* pr = nullptr;
+  int rc = problem_create(sub.data(), (int32_t)sub.size(), parts.data(), &pr);
+  if (rc != BS_OK) return rc;
+  double *a = nullptr, *b = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = dalloc(&a, pr->total_slice);
+  if (e == cudaSuccess) e = dalloc(&b, pr->total_slice);
+  if (e == cudaSuccess) e = cudaMemset(a, 0, sizeof(double) * pr->total_slice);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  float best = 0.0f;
+  for (int run = 0; run < 3 && e == cudaSuccess && rc == BS_OK; ++run) {
+    e = cudaEventRecord(e0, 0);
+    if (e == cudaSuccess) rc = fine_propagate(pr, a, b, nullptr, nullptr);
+    if (e == cudaSuccess && rc == BS_OK) e = cudaEventRecord(e1, 0);
+    if (e == cudaSuccess && rc == BS_OK) e = cudaEventSynchronize(e1);
+    float t = 0.0f;
+    if (e == cudaSuccess && rc == BS_OK) e = cudaEventElapsedTime(&t, e0, e1);
+    if (run == 1 || (run == 2 && t < best)) best = t;
+  }
+  if (rc == BS_OK && e == cudaSuccess) {
+    int st = 0;
+    e = cudaMemcpy(&st, pr->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && st != 0) rc = BS_TIMEOUT;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(a);
+  cudaFree(b);
+  bs_problem_destroy(pr);
+  if (rc == BS_OK && e != cudaSuccess) rc = map_err(e);
+  *ms = best;
+  return rc;
+}
+
+int bs_problem_init_tuned(const bs_params* p, int32_t n_instances, bs_problem** out, bs_tuning* report,
+                          int32_t report_cap, int32_t* n_report) {
+  if (!p || !out || n_instances <= 0 || (report_cap > 0 && !report)) return BS_EINVAL;
+  *out = nullptr;
+  if (n_report) *n_report = 0;
+  if (validate(p, n_instances) != BS_OK) return BS_EINVAL;
+  std::vector<Part> parts(n_instances);
+  std::vector<int> done(n_instances, 0);
+  int32_t nr = 0;
+  for (int i0 = 0; i0 < n_instances; ++i0) {
+    if (done[i0]) continue;
+    const int Nx = p[i0].Nx;
+    const std::vector<Part> cand = candidate_partitions(Nx);
+    if (cand.empty()) return BS_EUNSUPPORTED;
+    // tuning subset: instances of this grid size, enough for >= 4096 slices
+    std::vector<int> group;
+    for (int i = i0; i < n_instances; ++i)
+      if (p[i].Nx == Nx) group.push_back(i);
+    std::vector<bs_params> sub;
+    int64_t slices = 0;
+    for (int i : group) {
+      if (slices >= 4096) break;
+      bs_params q = p[i];
+      if (q.fine_steps > 128) q.fine_steps = 128;
+      q.coarse_steps = 1;
+      sub.push_back(q);
+      slices += q.P;
+    }
+    Part best = cand[0];
+    float best_ms = -1.0f;
+    for (const Part& c : cand) {
+      float ms = 0.0f;
+      const int rc = time_partition(sub, c, &ms);
+      if (rc == BS_TIMEOUT) return rc;
+      if (rc != BS_OK) {  // this candidate does not fit (memory, launch resources)
+        (void)cudaGetLastError();
+        continue;
+      }
+      if (nr < report_cap) report[nr] = bs_tuning{Nx, c.M, c.NW, c.C, ms, 0};
+      ++nr;
+      if (best_ms < 0.0f || ms < best_ms) {
+        best_ms = ms;
+        best = c;
+      }
+    }
+    if (best_ms < 0.0f) return BS_EUNSUPPORTED;
+    for (int k = 0; k < (nr < report_cap ? nr : report_cap); ++k)
+      if (report[k].Nx == Nx) report[k].chosen = (report[k].M == best.M && report[k].NW == best.NW && report[k].C == best.C);
+    for (int i : group) {
+      parts[i] = best;
+      done[i] = 1;
+    }
+  }
+  if (n_report) *n_report = nr;
+  return problem_create(p, n_instances, parts.data(), out);
 }
 
 int bs_problem_info(const bs_problem* prob, int32_t* n_instances, int64_t* total_state_doubles,
@@ -408,7 +552,7 @@ int pinn_create(const int32_t* widths, int32_t n_layers, const double* in_lo, co
   }
   m->dev.status = m->status;
   if (bsp::tc_supported(m->dev)) {
-    if ((e = dalloc(&m->tc_packed, bsp::tc_packed_bytes(m->dev, 1) + 16)) != cudaSuccess) {
+    if ((e = dalloc(&m->tc_packed, bsp::tc_packed_bytes(m->dev) + 16)) != cudaSuccess) {
       pinn_destroy(m);
       return map_err(e);
     }

@@ -176,7 +176,7 @@ cudaError_t launch_mlp_eval(const MlpDev& m, int prec, const double* X, int64_t 
     case 2:
       return eval_launch<float, 1, 1>(m, X, N, u, nullptr, s);
     case 3:
-      if (tc_fits(m, 0)) return launch_mlp_eval_tc(m, 0, m.tc_packed, X, N, u, m.status, s);
+      if (tc_fits(m)) return launch_mlp_eval_tc(m, m.tc_packed, X, N, u, m.status, s);
       return eval_launch<float, 2, 1>(m, X, N, u, nullptr, s);
   }
   return cudaErrorInvalidValue;

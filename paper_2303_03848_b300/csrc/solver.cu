@@ -1005,7 +1005,8 @@ __global__ void table_fix_kernel(const Inst* insts, int n_inst, double* g) {
 // ---------------------------------------------------------------------------
 
 #define BSP_FOR_EACH_CLASS(X)                                                                        \
-  X(2, 1, 1) X(2, 2, 1) X(2, 4, 1) X(4, 4, 1) X(8, 4, 1) X(16, 4, 1) X(32, 4, 1) X(2, 4, 2) X(4, 4, 2) \
+  X(2, 1, 1) X(4, 1, 1) X(8, 1, 1) X(16, 1, 1) X(32, 1, 1) X(2, 2, 1) X(4, 2, 1) X(8, 2, 1) X(16, 2, 1) \
+  X(32, 2, 1) X(2, 4, 1) X(4, 4, 1) X(8, 4, 1) X(16, 4, 1) X(32, 4, 1) X(2, 4, 2) X(4, 4, 2)             \
   X(8, 4, 2) X(16, 4, 2) X(32, 4, 2) X(2, 4, 4) X(4, 4, 4) X(8, 4, 4) X(16, 4, 4) X(32, 4, 4)         \
   X(2, 4, 8) X(4, 4, 8) X(8, 4, 8) X(16, 4, 8) X(32, 4, 8) X(4, 4, 16) X(8, 4, 16) X(16, 4, 16)       \
   X(32, 4, 16)

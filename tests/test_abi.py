@@ -36,9 +36,10 @@ def test_status_strings_and_version(L):
 def test_problem_init_rejects_bad_parameters(L, bad):
     p = B.params()
     p.update(bad)
-    with pytest.raises(B.BsError) as e:
-        B.Problem(p)
-    assert e.value.code == B.BS_EINVAL
+    for tuned in (False, True):
+        with pytest.raises(B.BsError) as e:
+            B.Problem(p, tuned=tuned)
+        assert e.value.code == B.BS_EINVAL
 
 
 def test_problem_init_rejects_oversized_grid(L):
@@ -57,6 +58,8 @@ def test_null_arguments_rejected(L):
     assert L.parareal_solve(None, 0, None, 0, 1e-6, 4, None, None, None, None) == B.BS_EINVAL
     assert L.pinn_eval(None, 0, None, 1, None, None, None) == B.BS_EINVAL
     assert L.bs_problem_device_status(None, None) == B.BS_EINVAL
+    assert L.bs_problem_init_tuned(None, 1, ctypes.byref(h), None, 0, None) == B.BS_EINVAL
+    assert L.bs_problem_init_tuned(ctypes.byref(p), 1, ctypes.byref(h), None, 4, None) == B.BS_EINVAL
     L.bs_problem_destroy(None)
     L.pinn_destroy(None)
 
@@ -78,6 +81,7 @@ def test_struct_layout_matches_header(L):
     # bs_params: 5 doubles then 4 int32 = 56 bytes; bs_instance_stats: 16 bytes
     assert ctypes.sizeof(B.BsParams) == 56
     assert ctypes.sizeof(B.InstanceStats) == 16
+    assert ctypes.sizeof(B.Tuning) == 24
     assert B.BsParams.Nx.offset == 40
 
 

@@ -1,0 +1,127 @@
+"""Partition choice: every compiled partition of a grid (forced with
+BSP_PARTITION) matches the oracle, and bs_problem_init_tuned times the
+candidates, keeps one per grid size and gives the same answers.  Tolerances as
+in test_gpu_solver.py (calibrated FP64 bound, at least 1e-12 relative).
+"""
+import numpy as np
+import pytest
+
+from paper_2303_03848_b300 import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+RTOL = 1e-12
+# partitions (M rows per thread, NW warps per CTA, C CTAs per grid) tried per grid
+SHAPES = [(m, nw, c) for c in (1, 2, 4, 8, 16) for nw in (1, 2, 4) for m in (2, 4, 8, 16, 32)]
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2303_03848_b300 import binding, build
+
+    build.build()
+    return binding
+
+
+def _tol(p, kind):
+    steps = p["fine_steps"] if kind == "fine" else p["coarse_steps"]
+    dt = p["T"] / (p["P"] * steps)
+    h = 0.5 * dt if kind == "fine" else dt
+    j = p["Nx"] - 2
+    kappa = 1.0 + h * (2.0 * p["sigma"] ** 2 * j * j + p["r"] * j + p["r"])
+    return max(RTOL, 2.0 * kappa * 2.0 ** -53 * steps)
+
+
+def _close(a, b, rtol):
+    a, b = np.asarray(a), np.asarray(b)
+    err = np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+    assert err <= rtol, f"relative error {err:.3e} > {rtol:.1e}"
+
+
+def _slices(orc, p, seed):
+    op = orc.params(**p)
+    S = synth.random_states(seed, p["P"], p["Nx"], scale=p["Smax"])
+    for n in range(p["P"]):
+        S[n, 0] = 0.0
+        S[n, -1] = orc.right_bc(op, p["T"] * n / p["P"])
+    return S
+
+
+def _check_against_oracle(B, orc, prob, insts, parts):
+    Uin = torch.tensor(np.concatenate([s.ravel() for s in parts]), device="cuda")
+    F = prob.fine_propagate(Uin).cpu().numpy()
+    G = prob.coarse_propagate(Uin).cpu().numpy()
+    assert prob.device_status() == B.BS_OK
+    for i, p in enumerate(insts):
+        op = orc.params(**p)
+        o = prob.slice_off[i]
+        for n in range(p["P"]):
+            sl = slice(o + n * p["Nx"], o + (n + 1) * p["Nx"])
+            _close(F[sl], orc.fine(op, n, parts[i][n]), _tol(p, "fine"))
+            _close(G[sl], orc.coarse_ie(op, n, parts[i][n]), _tol(p, "coarse"))
+
+
+@pytest.mark.parametrize("Nx", [256, 1000, 2049])
+def test_every_partition_matches_oracle(B, orc, monkeypatch, Nx):
+    p = dict(K=1.0, sigma=0.25, r=0.04, T=1.0, Smax=4.0, Nx=Nx, P=2, fine_steps=6, coarse_steps=2)
+    parts = [_slices(orc, p, 70 + Nx)]
+    tried = 0
+    for m, nw, c in SHAPES:
+        R = m * nw * 32 * c
+        if R < Nx - 1 or 2 * (R - (Nx - 1)) > R:
+            continue
+        monkeypatch.setenv("BSP_PARTITION", f"{m},{nw},{c}")
+        try:
+            prob = B.Problem(p)
+        except B.BsError as e:
+            assert e.code == B.BS_EUNSUPPORTED  # not a compiled class
+            continue
+        assert prob.partition(0) == dict(M=m, NW=nw, C=c)
+        _check_against_oracle(B, orc, prob, [p], parts)
+        tried += 1
+    assert tried >= 3
+
+
+def test_forced_partition_too_small_is_rejected(B, monkeypatch):
+    monkeypatch.setenv("BSP_PARTITION", "2,1,1")
+    with pytest.raises(B.BsError) as e:
+        B.Problem(dict(K=1.0, sigma=0.2, r=0.05, T=1.0, Smax=4.0, Nx=1024, P=2, fine_steps=4, coarse_steps=1))
+    assert e.value.code == B.BS_EUNSUPPORTED
+
+
+def test_tuned_init_keeps_one_partition_per_grid_and_matches_oracle(B, orc):
+    insts = [dict(K=0.8 + 0.1 * i, sigma=0.15 + 0.03 * i, r=0.01 * i, T=0.5 + 0.25 * i, Smax=4.0 * (0.8 + 0.1 * i),
+                  Nx=Nx, P=3, fine_steps=8, coarse_steps=1)
+             for i, Nx in enumerate((256, 1024, 256, 513, 1024, 513))]
+    prob = B.Problem(insts, tuned=True)
+    rep = prob.tuning
+    assert {r["Nx"] for r in rep} == {256, 513, 1024}
+    for Nx in (256, 513, 1024):
+        mine = [r for r in rep if r["Nx"] == Nx]
+        chosen = [r for r in mine if r["chosen"]]
+        assert len(chosen) == 1 and all(r["ms"] > 0.0 for r in mine)
+        best = min(mine, key=lambda r: r["ms"])
+        assert chosen[0] == best
+        for r in mine:
+            R = r["M"] * r["NW"] * 32 * r["C"]
+            assert R >= Nx - 1 and 2 * (R - (Nx - 1)) <= R
+        for i, p in enumerate(insts):
+            if p["Nx"] == Nx:
+                assert prob.partition(i) == dict(M=best["M"], NW=best["NW"], C=best["C"])
+    parts = [_slices(orc, p, 90 + i) for i, p in enumerate(insts)]
+    _check_against_oracle(B, orc, prob, insts, parts)
+
+
+def test_tuned_parareal_matches_oracle(B, orc):
+    p = dict(K=1.0, sigma=0.2, r=0.05, T=1.0, Smax=4.0, Nx=256, P=8, fine_steps=128, coarse_steps=1)
+    prob = B.Problem([p], tuned=True)
+    U, norms, stats, rc = prob.parareal_solve(B.COARSE_IE, tol=1e-10)
+    Ur, nr, st = orc.parareal(orc.params(**p), orc.COARSE_IE, tol=1e-10)
+    assert rc == B.BS_OK and stats[0]["iterations"] == len(nr)
+    np.testing.assert_allclose(norms[0, :len(nr)], nr, rtol=1e-6)
+    steps = p["fine_steps"] * p["P"]
+    j = p["Nx"] - 2
+    kappa = 1.0 + 0.5 * p["T"] / steps * (2.0 * p["sigma"] ** 2 * j * j + p["r"] * j + p["r"])
+    _close(U.cpu().numpy(), Ur.ravel(), max(RTOL, 2.0 * kappa * 2.0 ** -53 * steps))
