@@ -106,6 +106,13 @@ struct LossArgs {
 cudaError_t launch_loss_grad(const MlpDev& m, const LossArgs& la, double* loss3, double* grad, void* workspace,
                              size_t ws_bytes, cudaStream_t s);
 size_t loss_grad_workspace_bytes(const MlpDev& m, int64_t N);
+// Weight gradient of the square hidden layers on tcgen05 (pinn_train_tc.cu),
+// BF16 operands: gW (w x w) and gb (w) of one layer from its adjoints dz
+// ([4][w][N]) and the stored streams act ([4][w][N]) of the layer below.
+bool wgrad_tc_supported(const MlpDev& m);
+size_t wgrad_tc_partial_bytes(const MlpDev& m, int64_t N);
+cudaError_t launch_wgrad_tc(const MlpDev& m, int64_t N, const float* dz, const float* act, double* gW, double* gb,
+                            float* partial, cudaStream_t s);
 cudaError_t launch_adam(int64_t n, double* theta, double* mom1, double* mom2, const double* g, int step, double lr,
                         float* p32, cudaStream_t s);
 

@@ -226,9 +226,11 @@ static TrainLayout train_layout(const MlpDev& m, int64_t N) {
   return L;
 }
 
+// Activations and adjoints (sized for FP64), the loss accumulators, and the
+// partial sums of the tensor-core weight gradient.
 size_t loss_grad_workspace_bytes(const MlpDev& m, int64_t N) {
   const TrainLayout L = train_layout(m, N);
-  return (size_t)L.total * sizeof(double) + 64;
+  return (size_t)L.total * sizeof(double) + 512 + wgrad_tc_partial_bytes(m, N);
 }
 
 __global__ void count_kinds_kernel(const int8_t* __restrict__ kind, int64_t N, unsigned long long* cnt) {
@@ -505,6 +507,9 @@ static cudaError_t loss_grad_impl(const MlpDev& m, const LossArgs& la, double* l
                                   size_t ws_bytes, cudaStream_t s) {
   const TrainLayout TL = train_layout(m, la.N);
   if ((size_t)TL.total * sizeof(Tp) + 64 > ws_bytes) return cudaErrorInvalidValue;
+  if (RND == 2 && wgrad_tc_supported(m) &&
+      ((size_t)TL.total * sizeof(Tp) + 64 + 511) / 256 * 256 + wgrad_tc_partial_bytes(m, la.N) > ws_bytes)
+    return cudaErrorInvalidValue;
   Tp* ws = reinterpret_cast<Tp*>(workspace);
   // small accumulators live after the activations
   unsigned char* tail = reinterpret_cast<unsigned char*>(workspace) + (size_t)TL.total * sizeof(Tp);
@@ -536,11 +541,24 @@ static cudaError_t loss_grad_impl(const MlpDev& m, const LossArgs& la, double* l
     train_bwd_kernel<Tp, RND><<<(unsigned)((la.N + TP - 1) / TP), TP, smem, s>>>(m, la.N, TL, ws);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  // weight gradients
+  // weight gradients: BF16 square hidden layers on the tensor cores, the rest
+  // (and every layer of the other precisions) on CUDA cores
   const int64_t chunk = 2048;
   const unsigned nz = (unsigned)((la.N + chunk - 1) / chunk);
+  const bool tc = RND == 2 && wgrad_tc_supported(m);
+  float* partial = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(workspace) +
+                                            ((size_t)TL.total * sizeof(Tp) + 64 + 511) / 256 * 256);
   for (int l = 1; l <= m.n_lin; ++l) {
     const int wi = m.widths[l - 1], wo = m.widths[l];
+    if (tc && l >= 2 && l <= m.n_lin - 1) {
+      if constexpr (RND == 2) {
+        double* gW = grad + m.poff[l];
+        e = launch_wgrad_tc(m, la.N, ws + TL.dz_off[l], ws + TL.act_off[l - 1], gW, gW + (int64_t)wo * wi, partial,
+                            s);
+        if (e != cudaSuccess) return e;
+      }
+      continue;
+    }
     dim3 grid((wi + 1 + 15) / 16, (wo + 15) / 16, nz);
     grad_reduce_kernel<Tp, RND><<<grid, dim3(16, 16), 0, s>>>(m, la, TL, ws, l, grad, chunk);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
