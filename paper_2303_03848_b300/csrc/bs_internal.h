@@ -110,6 +110,15 @@ size_t loss_grad_workspace_bytes(const MlpDev& m, int64_t N);
 // BF16 operands: gW (w x w) and gb (w) of one layer from its adjoints dz
 // ([4][w][N]) and the stored streams act ([4][w][N]) of the layer below.
 bool wgrad_tc_supported(const MlpDev& m);
+// Forward with the derivative streams on tcgen05 (pinn_train_tc.cu), BF16
+// operands, hidden widths w <= 128: act[l] (l = 1..n_lin-1) and the loss seeds
+// as the CUDA-core forward writes them; wpack holds the packed square layers
+// (W then W^T, train_tc_pack_bytes).
+bool train_tc_supported(const MlpDev& m);
+size_t train_tc_pack_bytes(const MlpDev& m);
+cudaError_t launch_train_fwd_tc(const MlpDev& m, const LossArgs& la, float* const* act, float* seeds,
+                                unsigned char* wpack, const unsigned long long* cnt, double* loss_acc,
+                                cudaStream_t s);
 size_t wgrad_tc_partial_bytes(const MlpDev& m, int64_t N);
 cudaError_t launch_wgrad_tc(const MlpDev& m, int64_t N, const float* dz, const float* act, double* gW, double* gb,
                             float* partial, cudaStream_t s);

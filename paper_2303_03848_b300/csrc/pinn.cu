@@ -17,6 +17,7 @@
 #include <cstdio>
 
 #include "bs_internal.h"
+#include "pinn_loss.cuh"
 
 namespace bsp {
 
@@ -226,11 +227,24 @@ static TrainLayout train_layout(const MlpDev& m, int64_t N) {
   return L;
 }
 
-// Activations and adjoints (sized for FP64), the loss accumulators, and the
-// partial sums of the tensor-core weight gradient.
+// Workspace: activations and adjoints, then the loss accumulators, the partial
+// sums of the tensor-core weight gradient and the packed square layers.
+struct WsTail {
+  size_t acc, partial, pack, total;
+};
+
+static WsTail ws_tail(const MlpDev& m, const TrainLayout& L, size_t elem, int64_t N) {
+  WsTail w;
+  w.acc = ((size_t)L.total * elem + 15) / 16 * 16;
+  w.partial = (w.acc + 64 + 255) / 256 * 256;
+  w.pack = (w.partial + wgrad_tc_partial_bytes(m, N) + 255) / 256 * 256;
+  w.total = w.pack + train_tc_pack_bytes(m);
+  return w;
+}
+
 size_t loss_grad_workspace_bytes(const MlpDev& m, int64_t N) {
   const TrainLayout L = train_layout(m, N);
-  return (size_t)L.total * sizeof(double) + 512 + wgrad_tc_partial_bytes(m, N);
+  return ws_tail(m, L, sizeof(double), N).total + 256;
 }
 
 __global__ void count_kinds_kernel(const int8_t* __restrict__ kind, int64_t N, unsigned long long* cnt) {
@@ -251,25 +265,6 @@ __global__ void count_kinds_kernel(const int8_t* __restrict__ kind, int64_t N, u
     atomicAdd(cnt + 1, c1);
     atomicAdd(cnt + 2, c2);
   }
-}
-
-// Targets of Eqs. 13-14 and the per-point parameters.
-__device__ __forceinline__ void point_setup(const LossArgs& la, int d_in, const double* x, int kind, double& Ki,
-                                            double& si, double& ri, double& tgt) {
-  Ki = la.K;
-  si = la.sigma;
-  ri = la.r;
-  if (d_in >= 5) {
-    si = x[2];
-    ri = x[3];
-    Ki = x[4];
-  }
-  const double Sm = (la.smax_over_K > 0.0 && d_in >= 5) ? la.smax_over_K * Ki : la.Smax;
-  const double S = x[0], tau = x[1];
-  if (kind == 1) tgt = 0.0;
-  else if (kind == 2) tgt = Sm - Ki * exp(-ri * tau);
-  else if (kind == 3) tgt = S - Ki > 0.0 ? S - Ki : 0.0;
-  else tgt = 0.0;
 }
 
 template <typename Tp, int RND>
@@ -506,14 +501,12 @@ template <typename Tp, int RND>
 static cudaError_t loss_grad_impl(const MlpDev& m, const LossArgs& la, double* loss3, double* grad, void* workspace,
                                   size_t ws_bytes, cudaStream_t s) {
   const TrainLayout TL = train_layout(m, la.N);
-  if ((size_t)TL.total * sizeof(Tp) + 64 > ws_bytes) return cudaErrorInvalidValue;
-  if (RND == 2 && wgrad_tc_supported(m) &&
-      ((size_t)TL.total * sizeof(Tp) + 64 + 511) / 256 * 256 + wgrad_tc_partial_bytes(m, la.N) > ws_bytes)
-    return cudaErrorInvalidValue;
+  const WsTail WT = ws_tail(m, TL, sizeof(Tp), la.N);
+  if (WT.total > ws_bytes) return cudaErrorInvalidValue;
   Tp* ws = reinterpret_cast<Tp*>(workspace);
+  unsigned char* base = reinterpret_cast<unsigned char*>(workspace);
   // small accumulators live after the activations
-  unsigned char* tail = reinterpret_cast<unsigned char*>(workspace) + (size_t)TL.total * sizeof(Tp);
-  tail = reinterpret_cast<unsigned char*>(((uintptr_t)tail + 15) & ~(uintptr_t)15);
+  unsigned char* tail = base + WT.acc;
   unsigned long long* cnt = reinterpret_cast<unsigned long long*>(tail);
   double* acc = reinterpret_cast<double*>(tail + 24);
   cudaError_t e = cudaMemsetAsync(tail, 0, 48, s);
@@ -523,7 +516,14 @@ static cudaError_t loss_grad_impl(const MlpDev& m, const LossArgs& la, double* l
   e = cudaMemsetAsync(grad, 0, (size_t)np * sizeof(double), s);
   if (e != cudaSuccess) return e;
   count_kinds_kernel<<<148, 256, 0, s>>>(la.kind, la.N, cnt);
-  {  // forward
+  if (RND == 2 && train_tc_supported(m)) {  // forward on the tensor cores
+    if constexpr (RND == 2) {
+      float* act[16] = {};
+      for (int l = 1; l < m.n_lin; ++l) act[l] = ws + TL.act_off[l];
+      e = launch_train_fwd_tc(m, la, act, ws + TL.dz_off[m.n_lin], base + WT.pack, cnt, acc, s);
+      if (e != cudaSuccess) return e;
+    }
+  } else {  // forward on CUDA cores
     const size_t per_thread = 2 * 4 * (size_t)m.max_w * sizeof(Tp);
     const int TP = points_per_cta(per_thread);
     const size_t smem = per_thread * TP;
@@ -546,8 +546,7 @@ static cudaError_t loss_grad_impl(const MlpDev& m, const LossArgs& la, double* l
   const int64_t chunk = 2048;
   const unsigned nz = (unsigned)((la.N + chunk - 1) / chunk);
   const bool tc = RND == 2 && wgrad_tc_supported(m);
-  float* partial = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(workspace) +
-                                            ((size_t)TL.total * sizeof(Tp) + 64 + 511) / 256 * 256);
+  float* partial = reinterpret_cast<float*>(base + WT.partial);
   for (int l = 1; l <= m.n_lin; ++l) {
     const int wi = m.widths[l - 1], wo = m.widths[l];
     if (tc && l >= 2 && l <= m.n_lin - 1) {

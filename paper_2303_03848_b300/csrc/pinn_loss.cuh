@@ -1,0 +1,57 @@
+// pinn_loss.cuh -- per-point pieces of the training loss (Section 3.3,
+// Eqs. 11-14) shared by the CUDA-core and tensor-core training kernels.
+#pragma once
+
+#include <cmath>
+
+#include "bs_internal.h"
+
+namespace bsp {
+
+// Targets of Eqs. 13-14 and the per-point parameters.
+__device__ __forceinline__ void point_setup(const LossArgs& la, int d_in, const double* x, int kind, double& Ki,
+                                            double& si, double& ri, double& tgt) {
+  Ki = la.K;
+  si = la.sigma;
+  ri = la.r;
+  if (d_in >= 5) {
+    si = x[2];
+    ri = x[3];
+    Ki = x[4];
+  }
+  const double Sm = (la.smax_over_K > 0.0 && d_in >= 5) ? la.smax_over_K * Ki : la.Smax;
+  const double S = x[0], tau = x[1];
+  if (kind == 1) tgt = 0.0;
+  else if (kind == 2) tgt = Sm - Ki * exp(-ri * tau);
+  else if (kind == 3) tgt = S - Ki > 0.0 ? S - Ki : 0.0;
+  else tgt = 0.0;
+}
+
+// Loss terms and adjoint seeds of one point from its output streams
+// (u, u_S, u_SS, u_tau): kind 0 interior (residual of Eq. 1 in tau), 1/2 the
+// S = 0 / S = Smax boundary (Eq. 13), 3 expiry (Eq. 14).  sq[term] receives the
+// squared error, g[4] = dLoss/d(u, u_S, u_SS, u_tau) with each term a mean
+// over its cnt points.
+__device__ __forceinline__ void point_loss(const LossArgs& la, int d_in, const double* x, int kd, const double (&out)[4],
+                                           const unsigned long long* cnt, double (&sq)[3], double (&g)[4]) {
+  double Ki, si, ri, tgt;
+  point_setup(la, d_in, x, kd, Ki, si, ri, tgt);
+  const double S = x[0];
+  g[0] = g[1] = g[2] = g[3] = 0.0;
+  if (kd == 0) {
+    const double f = out[3] - 0.5 * si * si * S * S * out[2] - ri * S * out[1] + ri * out[0];
+    sq[0] = f * f;
+    const double gf = 2.0 * f / (double)cnt[0];
+    g[3] = gf;
+    g[2] = -0.5 * si * si * S * S * gf;
+    g[1] = -ri * S * gf;
+    g[0] = ri * gf;
+  } else {
+    const double e = out[0] - tgt;
+    const int tt = (kd == 3) ? 2 : 1;
+    sq[tt] = e * e;
+    g[0] = 2.0 * e / (double)cnt[tt];
+  }
+}
+
+}  // namespace bsp

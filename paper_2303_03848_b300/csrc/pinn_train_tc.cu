@@ -26,6 +26,7 @@
 #include <cstdio>
 
 #include "bs_internal.h"
+#include "pinn_loss.cuh"
 #include "tcgen05.cuh"
 
 namespace bsp {
@@ -209,7 +210,307 @@ void wgrad_grid(int w, int64_t N, int* ot, int* per_cta, int* ny) {
 
 size_t wgrad_smem_bytes(int w) { return 2 * (size_t)128 * kChunk * 2 + 2 * (size_t)w * kChunk * 2 + 64; }
 
+// Pack the square layers for training: W_l (rows o, K = i) for the forward and
+// W_l^T (rows i, K = o) for the adjoint, BF16 core-matrix layout.
+__global__ void pack_train_kernel(MlpDev m, int w, unsigned char* fwd, unsigned char* bwd) {
+  const int n_sq = m.n_lin - 2;
+  const int64_t per = (int64_t)w * w;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < per * n_sq;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int sq = (int)(q / per);
+    const int o = (int)((q % per) / w), i = (int)(q % w);
+    const __nv_bfloat16 v = __float2bfloat16_rn(m.p32[m.poff[sq + 2] + (int64_t)o * w + i]);
+    *reinterpret_cast<__nv_bfloat16*>(fwd + sq * per * 2 + canon_off(o, i, w)) = v;
+    *reinterpret_cast<__nv_bfloat16*>(bwd + sq * per * 2 + canon_off(i, o, w)) = v;
+  }
+}
+
+__device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+// ---------------------------------------------------------------------------
+// Forward with the four derivative streams on the tensor cores.  A CTA of 128
+// threads takes 32 points at a time; row r = 32 s + q of every layer GEMM is
+// stream s (warp s) of point q (lane q), so each thread reads its own row of
+// the accumulator.  Per hidden layer the value stream's warp forms t = tanh(z)
+// and the S-stream's warp publishes z_S through shared memory; then every
+// stream forms its input to the next layer:
+//   h_0 = t, h_1 = t' z_S, h_2 = t' z_SS + t'' z_S^2, h_3 = t' z_tau,
+// stores (t, z_S, z_SS, z_tau) for the adjoint and writes h_s in BF16 as the
+// next A operand.  Input layer, output layer and the loss seeds on CUDA cores.
+// ---------------------------------------------------------------------------
+struct FwdArgs {
+  MlpDev m;
+  LossArgs la;
+  float* act[16];      // act[l], l = 1..n_lin-1: [4][w][N] = (t, z_S, z_SS, z_tau)
+  float* seeds;        // dLoss/d(u, u_S, u_SS, u_tau): [4][N]
+  const unsigned char* wpack;  // square layers, W_l (rows o, K = i)
+  const unsigned long long* cnt;
+  double* loss_acc;
+};
+
+template <int DIN>
+__global__ void __launch_bounds__(128) train_fwd_tc_kernel(FwdArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const MlpDev& m = a.m;
+  const int w = m.widths[1], n_sq = m.n_lin - 2;
+  const int t = threadIdx.x, s = t >> 5, q = t & 31;
+  const int64_t N = a.la.N;
+  const uint32_t wbytes = (uint32_t)w * w * 2;
+  unsigned char* sW = smem;
+  unsigned char* sA = sW + wbytes;
+  float* xt = reinterpret_cast<float*>(sA + (size_t)128 * w * 2);  // [2][32][33] tanh of a column chunk
+  float* xs = xt + 2 * 32 * 33;                                     // [2][32][33] z_S of a column chunk
+  float* sW1 = xs + 2 * 32 * 33;                                    // w x DIN
+  float* sB = sW1 + w * DIN;                                        // hidden biases, (n_lin-1) x w
+  float* sWo = sB + (m.n_lin - 1) * w;                              // output weights, w
+  float* su = sWo + w;                                              // [4][32] output streams
+  uint64_t* bar = reinterpret_cast<uint64_t*>(su + 128);            // [0] MMA done, [1] weights landed
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
+  __shared__ int s_fail;
+  __shared__ double s_acc[3];
+
+  for (int i = t; i < w * DIN; i += 128) sW1[i] = bf16r(m.p32[m.poff[1] + i]);
+  for (int l = 1; l < m.n_lin; ++l)
+    for (int o = t; o < w; o += 128) sB[(l - 1) * w + o] = m.p32[m.poff[l] + (int64_t)w * m.widths[l - 1] + o];
+  for (int o = t; o < w; o += 128) sWo[o] = bf16r(m.p32[m.poff[m.n_lin] + o]);
+  const float bout = m.p32[m.poff[m.n_lin] + w];
+  float sc[DIN], of[DIN];
+#pragma unroll
+  for (int i = 0; i < DIN; ++i) {
+    const double g = 2.0 / (m.hi[i] - m.lo[i]);
+    sc[i] = (float)g;
+    of[i] = (float)(-g * m.lo[i] - 1.0);
+  }
+  const int64_t ntiles = (N + 31) / 32;
+  if (t == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    s_fail = 0;
+    s_acc[0] = s_acc[1] = s_acc[2] = 0.0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  bool w_pending = false;
+  uint32_t ph_w = 0, ph_mma = 0;
+  if (t == 0 && (int64_t)blockIdx.x < ntiles) {
+    bulk_load(sW, a.wpack, wbytes, &bar[1]);
+    w_pending = true;
+  }
+  uint32_t ncols = 32;
+  while ((int)ncols < w) ncols <<= 1;
+  if (s == 0) tmem_alloc(tslot, ncols);
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tslot;
+  const uint32_t idesc = make_idesc_bf16(w);
+  const uint32_t sbo = (uint32_t)(w / 8) * 128;
+  const uint32_t trow = tmem + ((uint32_t)(s * 32) << 16);
+
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t p = tile * 32 + q;
+    const bool valid = p < N;
+    const bool last_tile = tile + gridDim.x >= ntiles;
+    // input layer on CUDA cores (every stream recomputes the point's z)
+    float xh[DIN];
+#pragma unroll
+    for (int i = 0; i < DIN; ++i) xh[i] = bf16r(fmaf(valid ? (float)a.la.X[p * DIN + i] : 0.0f, sc[i], of[i]));
+    {
+      float* act1 = a.act[1];
+      for (int o0 = 0; o0 < w; o0 += 8) {
+        float hv[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int o = o0 + j;
+          float z = sB[o];
+#pragma unroll
+          for (int i = 0; i < DIN; ++i) z = fmaf(sW1[o * DIN + i], xh[i], z);
+          const float tt = tanh_fast(z), d1 = 1.0f - tt * tt;
+          const float zS = sW1[o * DIN + 0] * sc[0], zT = sW1[o * DIN + 1] * sc[1];
+          float h, av;
+          if (s == 0) {
+            h = tt;
+            av = tt;
+          } else if (s == 1) {
+            h = d1 * zS;
+            av = zS;
+          } else if (s == 2) {
+            h = -2.0f * tt * d1 * zS * zS;
+            av = 0.0f;
+          } else {
+            h = d1 * zT;
+            av = zT;
+          }
+          hv[j] = h;
+          if (valid) act1[((int64_t)s * w + o) * N + p] = av;
+        }
+        *reinterpret_cast<uint4*>(sA + canon_off(t, o0, w)) =
+            make_uint4(pack2(hv[0], hv[1]), pack2(hv[2], hv[3]), pack2(hv[4], hv[5]), pack2(hv[6], hv[7]));
+      }
+    }
+    // square layers on the tensor cores
+    float dot = 0.0f;
+    for (int sq = 0; sq < n_sq; ++sq) {
+      const int l = sq + 2;
+      if (t == 0 && w_pending) {
+        if (mbar_wait_bounded(&bar[1], ph_w)) {
+          ph_w ^= 1u;
+          w_pending = false;
+        } else {
+          s_fail = 1;
+        }
+      }
+      fence_proxy_async();
+      fence_before();
+      __syncthreads();
+      fence_after();
+      if (s_fail) break;
+      if (t == 0) {
+        const uint32_t aa = smem_u32(sA), bb = smem_u32(sW);
+        for (int kk = 0; kk < w / 16; ++kk)
+          mma_bf16(tmem, make_desc(aa + kk * 256, 128, sbo), make_desc(bb + kk * 256, 128, sbo), idesc,
+                   kk > 0 ? 1u : 0u);
+        mma_commit(&bar[0]);
+      }
+      const bool ok = mbar_wait_bounded(&bar[0], ph_mma);
+      ph_mma ^= 1u;
+      if (!ok) s_fail = 1;
+      fence_after();
+      if (t == 0 && ok && !(last_tile && sq == n_sq - 1)) {
+        const int nxt = sq + 1 < n_sq ? sq + 1 : 0;
+        bulk_load(sW, a.wpack + (size_t)nxt * wbytes, wbytes, &bar[1]);
+        w_pending = true;
+      }
+      __syncthreads();
+      if (s_fail) break;
+      const bool last = sq == n_sq - 1;
+      const float* bl = sB + (l - 1) * w;
+      float* actl = a.act[l];
+      for (int c = 0; c < w; c += 32) {
+        const int buf = (c >> 5) & 1;
+        float v[32];
+        tmem_ld32(trow + (uint32_t)c, v);
+        if (s == 0) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            v[j] = tanh_fast(v[j] + bl[c + j]);
+            xt[(buf * 32 + q) * 33 + j] = v[j];
+          }
+        } else if (s == 1) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) xs[(buf * 32 + q) * 33 + j] = v[j];
+        }
+        __syncthreads();
+        float hv[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          float h = v[j];
+          if (s != 0) {
+            const float tt = xt[(buf * 32 + q) * 33 + j], d1 = 1.0f - tt * tt;
+            if (s == 2) {
+              const float zS = xs[(buf * 32 + q) * 33 + j];
+              h = d1 * v[j] - 2.0f * tt * d1 * zS * zS;
+            } else {
+              h = d1 * v[j];
+            }
+          }
+          hv[j] = h;
+        }
+        if (valid) {
+#pragma unroll 8
+          for (int j = 0; j < 32; ++j) actl[((int64_t)s * w + c + j) * N + p] = v[j];
+        }
+        if (last) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) dot = fmaf(sWo[c + j], bf16r(hv[j]), dot);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; j += 8)
+            *reinterpret_cast<uint4*>(sA + canon_off(t, c + j, w)) =
+                make_uint4(pack2(hv[j], hv[j + 1]), pack2(hv[j + 2], hv[j + 3]), pack2(hv[j + 4], hv[j + 5]),
+                           pack2(hv[j + 6], hv[j + 7]));
+        }
+      }
+      fence_before();
+    }
+    if (s_fail) break;
+    // output streams, loss terms and seeds (the value stream's warp)
+    su[s * 32 + q] = dot + (s == 0 ? bout : 0.0f);
+    __syncthreads();
+    if (s == 0 && valid) {
+      double xin[8];
+#pragma unroll
+      for (int i = 0; i < DIN; ++i) xin[i] = a.la.X[p * DIN + i];
+      const double out[4] = {(double)su[q], (double)su[32 + q], (double)su[64 + q], (double)su[96 + q]};
+      double sqe[3] = {0.0, 0.0, 0.0}, g[4];
+      point_loss(a.la, DIN, xin, a.la.kind[p], out, a.cnt, sqe, g);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) a.seeds[(int64_t)k * N + p] = (float)g[k];
+      for (int k = 0; k < 3; ++k)
+        if (sqe[k] != 0.0) atomicAdd(&s_acc[k], sqe[k]);
+    }
+  }
+  if (t == 0 && w_pending) (void)mbar_wait_bounded(&bar[1], ph_w);
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (t == 0) {
+    atomicAdd(a.loss_acc + 0, s_acc[0]);
+    atomicAdd(a.loss_acc + 1, s_acc[1]);
+    atomicAdd(a.loss_acc + 2, s_acc[2]);
+    if (s_fail) atomicExch(m.status, 6);  // BS_TIMEOUT
+  }
+  if (s == 0) tmem_dealloc(tmem, ncols);
+}
+
 }  // namespace
+
+bool train_tc_supported(const MlpDev& m) {
+  return wgrad_tc_supported(m) && m.widths[1] <= 128 && (m.d_in == 2 || m.d_in == 5);
+}
+
+size_t train_tc_pack_bytes(const MlpDev& m) {
+  if (!train_tc_supported(m)) return 0;
+  return 2 * (size_t)(m.n_lin - 2) * m.widths[1] * m.widths[1] * 2;
+}
+
+cudaError_t launch_train_fwd_tc(const MlpDev& m, const LossArgs& la, float* const* act, float* seeds,
+                                unsigned char* wpack, const unsigned long long* cnt, double* loss_acc,
+                                cudaStream_t s) {
+  if (la.N <= 0) return cudaSuccess;
+  if (((uintptr_t)wpack & 15) != 0) return cudaErrorInvalidValue;  // TMA source alignment
+  const int w = m.widths[1], n_sq = m.n_lin - 2;
+  unsigned char* wpackT = wpack + (size_t)n_sq * w * w * 2;
+  pack_train_kernel<<<148, 256, 0, s>>>(m, w, wpack, wpackT);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  FwdArgs a{};
+  a.m = m;
+  a.la = la;
+  for (int l = 0; l < 16; ++l) a.act[l] = act[l];
+  a.seeds = seeds;
+  a.wpack = wpack;
+  a.cnt = cnt;
+  a.loss_acc = loss_acc;
+  const size_t smem = (size_t)w * w * 2 + (size_t)128 * w * 2 +
+                      sizeof(float) * (4 * 32 * 33 + (size_t)w * m.d_in + (size_t)(m.n_lin - 1) * w + w + 128) + 64;
+  auto kern = m.d_in == 2 ? train_fwd_tc_kernel<2> : train_fwd_tc_kernel<5>;
+  if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess) return e;
+  int dev = 0, nsm = 148, sm_smem = 0, reserved = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  int per_sm = (int)((size_t)sm_smem / (smem + 2048 + (size_t)reserved));
+  if (per_sm < 1) per_sm = 1;
+  if (per_sm > 3) per_sm = 3;  // tensor memory: <= 128 columns each
+  const int64_t ntiles = (la.N + 31) / 32;
+  const int64_t grid = ntiles < (int64_t)nsm * per_sm ? ntiles : (int64_t)nsm * per_sm;
+  kern<<<(unsigned)grid, 128, smem, s>>>(a);
+  return cudaGetLastError();
+}
 
 bool wgrad_tc_supported(const MlpDev& m) {
   if (m.n_lin < 3) return false;
