@@ -119,6 +119,10 @@ size_t train_tc_pack_bytes(const MlpDev& m);
 cudaError_t launch_train_fwd_tc(const MlpDev& m, const LossArgs& la, float* const* act, float* seeds,
                                 unsigned char* wpack, const unsigned long long* cnt, double* loss_acc,
                                 cudaStream_t s);
+// Adjoint on tcgen05: dz[l] (l = 1..n_lin-1) from the seeds and act, as the
+// CUDA-core adjoint writes them; wpack as packed by launch_train_fwd_tc.
+cudaError_t launch_train_bwd_tc(const MlpDev& m, int64_t N, const float* const* act, float* const* dz,
+                                const float* seeds, const unsigned char* wpack, cudaStream_t s);
 size_t wgrad_tc_partial_bytes(const MlpDev& m, int64_t N);
 cudaError_t launch_wgrad_tc(const MlpDev& m, int64_t N, const float* dz, const float* act, double* gW, double* gb,
                             float* partial, cudaStream_t s);

@@ -532,7 +532,18 @@ static cudaError_t loss_grad_impl(const MlpDev& m, const LossArgs& la, double* l
     train_fwd_kernel<Tp, RND><<<(unsigned)((la.N + TP - 1) / TP), TP, smem, s>>>(m, la, TL, ws, cnt, acc);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  {  // adjoint
+  if (RND == 2 && train_tc_supported(m)) {  // adjoint on the tensor cores
+    if constexpr (RND == 2) {
+      const float* act[16] = {};
+      float* dzp[16] = {};
+      for (int l = 1; l < m.n_lin; ++l) {
+        act[l] = ws + TL.act_off[l];
+        dzp[l] = ws + TL.dz_off[l];
+      }
+      e = launch_train_bwd_tc(m, la.N, act, dzp, ws + TL.dz_off[m.n_lin], base + WT.pack, s);
+      if (e != cudaSuccess) return e;
+    }
+  } else {  // adjoint on CUDA cores
     const size_t per_thread = 4 * (size_t)m.max_w * sizeof(Tp);
     const int TP = points_per_cta(per_thread);
     const size_t smem = per_thread * TP;

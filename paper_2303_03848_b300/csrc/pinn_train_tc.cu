@@ -463,7 +463,213 @@ __global__ void __launch_bounds__(128) train_fwd_tc_kernel(FwdArgs a) {
   if (s == 0) tmem_dealloc(tmem, ncols);
 }
 
+// ---------------------------------------------------------------------------
+// Adjoint on the tensor cores, same tile mapping (row 32 s + q = stream s of
+// point q).  From the top hidden layer down: ah_s = W_{l+1}^T dz_{l+1,s} (the
+// output layer's is rank one, on CUDA cores; the others one GEMM with the
+// packed W^T), then the adjoint of the tanh streams of layer l,
+//   t_bar = ah_0 - 2 t' d2_bar - 2 t d1_bar,  d2_bar = ah_2 z_S^2,
+//   d1_bar = ah_1 z_S + ah_2 z_SS + ah_3 z_tau - 2 t d2_bar,
+//   dz_0 = t' t_bar,  dz_1 = t' ah_1 + 2 t'' z_S ah_2,  dz_2 = t' ah_2,  dz_3 = t' ah_3,
+// which needs every stream's ah for the value stream: streams 1..3 publish
+// theirs through shared memory.  dz_l goes to global memory (weight gradient)
+// and, in BF16, to the A operand of the next GEMM.
+// ---------------------------------------------------------------------------
+struct BwdArgs {
+  MlpDev m;
+  int64_t N;
+  const float* act[16];         // act[l], l = 1..n_lin-1
+  float* dz[16];                // dz[l], l = 1..n_lin-1 (written)
+  const float* seeds;           // dz of the output layer: [4][N]
+  const unsigned char* wpackT;  // W_l^T (rows i, K = o), square layers l = 2..n_lin-1
+};
+
+__global__ void __launch_bounds__(128) train_bwd_tc_kernel(BwdArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const MlpDev& m = a.m;
+  const int w = m.widths[1], n_sq = m.n_lin - 2;
+  const int t = threadIdx.x, s = t >> 5, q = t & 31;
+  const int64_t N = a.N;
+  const uint32_t wbytes = (uint32_t)w * w * 2;
+  unsigned char* sW = smem;
+  unsigned char* sA = sW + wbytes;
+  float* xa = reinterpret_cast<float*>(sA + (size_t)128 * w * 2);  // [2][3][32][33] ah of streams 1..3
+  float* sWo = xa + 2 * 3 * 32 * 33;                                // output weights (BF16-rounded)
+  float* sseed = sWo + w;                                           // [4][32]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sseed + 128);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
+  __shared__ int s_fail;
+  auto XA = [&](int buf, int k, int qq, int j) -> float& { return xa[((buf * 3 + k) * 32 + qq) * 33 + j]; };
+
+  for (int o = t; o < w; o += 128) sWo[o] = bf16r(m.p32[m.poff[m.n_lin] + o]);
+  const int64_t ntiles = (N + 31) / 32;
+  if (t == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  bool w_pending = false;
+  uint32_t ph_w = 0, ph_mma = 0;
+  if (t == 0 && (int64_t)blockIdx.x < ntiles) {
+    bulk_load(sW, a.wpackT + (size_t)(n_sq - 1) * wbytes, wbytes, &bar[1]);
+    w_pending = true;
+  }
+  uint32_t ncols = 32;
+  while ((int)ncols < w) ncols <<= 1;
+  if (s == 0) tmem_alloc(tslot, ncols);
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tslot;
+  const uint32_t idesc = make_idesc_bf16(w);
+  const uint32_t sbo = (uint32_t)(w / 8) * 128;
+  const uint32_t trow = tmem + ((uint32_t)(s * 32) << 16);
+
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t p = tile * 32 + q;
+    const bool valid = p < N;
+    const bool last_tile = tile + gridDim.x >= ntiles;
+    sseed[s * 32 + q] = valid ? bf16r(a.seeds[(int64_t)s * N + p]) : 0.0f;
+    __syncthreads();
+    const float seed = sseed[s * 32 + q];
+    for (int l = m.n_lin - 1; l >= 1; --l) {
+      const float* act = a.act[l];
+      float* dzl = a.dz[l];
+      const bool top = l == m.n_lin - 1;
+      for (int c = 0; c < w; c += 32) {
+        const int buf = (c >> 5) & 1;
+        float ah[32];
+        if (top) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) ah[j] = sWo[c + j] * seed;
+        } else {
+          tmem_ld32(trow + (uint32_t)c, ah);
+        }
+        if (s >= 1) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) XA(buf, s - 1, q, j) = ah[j];
+        }
+        __syncthreads();
+        float dzv[32];
+#pragma unroll 4
+        for (int j = 0; j < 32; ++j) {
+          const int64_t i = c + j;
+          const float tt = valid ? act[(0 * (int64_t)w + i) * N + p] : 0.0f;
+          const float d1 = 1.0f - tt * tt, d2 = -2.0f * tt * d1;
+          float r;
+          if (s == 0) {
+            const float zs = valid ? act[(1 * (int64_t)w + i) * N + p] : 0.0f;
+            const float zss = valid ? act[(2 * (int64_t)w + i) * N + p] : 0.0f;
+            const float zt = valid ? act[(3 * (int64_t)w + i) * N + p] : 0.0f;
+            const float ahS = XA(buf, 0, q, j), ahSS = XA(buf, 1, q, j), ahT = XA(buf, 2, q, j);
+            const float bar_d2 = ahSS * zs * zs;
+            float bar_d1 = ahS * zs + ahSS * zss + ahT * zt;
+            float bar_t = ah[j];
+            bar_t += -2.0f * d1 * bar_d2;
+            bar_d1 += -2.0f * tt * bar_d2;
+            bar_t += -2.0f * tt * bar_d1;
+            r = d1 * bar_t;
+          } else if (s == 1) {
+            const float zs = valid ? act[(1 * (int64_t)w + i) * N + p] : 0.0f;
+            r = ah[j] * d1 + 2.0f * XA(buf, 1, q, j) * d2 * zs;
+          } else {
+            r = ah[j] * d1;
+          }
+          dzv[j] = r;
+        }
+        if (valid) {
+#pragma unroll 8
+          for (int j = 0; j < 32; ++j) dzl[((int64_t)s * w + c + j) * N + p] = dzv[j];
+        }
+        if (l >= 2) {
+#pragma unroll
+          for (int j = 0; j < 32; j += 8)
+            *reinterpret_cast<uint4*>(sA + canon_off(t, c + j, w)) =
+                make_uint4(pack2(dzv[j], dzv[j + 1]), pack2(dzv[j + 2], dzv[j + 3]), pack2(dzv[j + 4], dzv[j + 5]),
+                           pack2(dzv[j + 6], dzv[j + 7]));
+        }
+      }
+      fence_before();
+      if (l < 2) break;
+      // ah of layer l-1: W_l^T dz_l on the tensor cores
+      if (t == 0 && w_pending) {
+        if (mbar_wait_bounded(&bar[1], ph_w)) {
+          ph_w ^= 1u;
+          w_pending = false;
+        } else {
+          s_fail = 1;
+        }
+      }
+      fence_proxy_async();
+      fence_before();
+      __syncthreads();
+      fence_after();
+      if (s_fail) break;
+      if (t == 0) {
+        const uint32_t aa = smem_u32(sA), bb = smem_u32(sW);
+        for (int kk = 0; kk < w / 16; ++kk)
+          mma_bf16(tmem, make_desc(aa + kk * 256, 128, sbo), make_desc(bb + kk * 256, 128, sbo), idesc,
+                   kk > 0 ? 1u : 0u);
+        mma_commit(&bar[0]);
+      }
+      const bool ok = mbar_wait_bounded(&bar[0], ph_mma);
+      ph_mma ^= 1u;
+      if (!ok) s_fail = 1;
+      fence_after();
+      if (t == 0 && ok && !(last_tile && l == 2)) {
+        const int nxt = l - 1 >= 2 ? l - 3 : n_sq - 1;  // W_{l-1}^T, or the next tile's first
+        bulk_load(sW, a.wpackT + (size_t)nxt * wbytes, wbytes, &bar[1]);
+        w_pending = true;
+      }
+      __syncthreads();
+      if (s_fail) break;
+    }
+    if (s_fail) break;
+  }
+  if (t == 0 && w_pending) (void)mbar_wait_bounded(&bar[1], ph_w);
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (s_fail && t == 0) atomicExch(m.status, 6);  // BS_TIMEOUT
+  if (s == 0) tmem_dealloc(tmem, ncols);
+}
+
 }  // namespace
+
+cudaError_t launch_train_bwd_tc(const MlpDev& m, int64_t N, const float* const* act, float* const* dz,
+                                const float* seeds, const unsigned char* wpack, cudaStream_t s) {
+  if (N <= 0) return cudaSuccess;
+  const int w = m.widths[1], n_sq = m.n_lin - 2;
+  BwdArgs a{};
+  a.m = m;
+  a.N = N;
+  for (int l = 0; l < 16; ++l) {
+    a.act[l] = act[l];
+    a.dz[l] = dz[l];
+  }
+  a.seeds = seeds;
+  a.wpackT = wpack + (size_t)n_sq * w * w * 2;
+  const size_t smem = (size_t)w * w * 2 + (size_t)128 * w * 2 + sizeof(float) * (6 * 32 * 33 + (size_t)w + 128) + 64;
+  cudaError_t e = cudaFuncSetAttribute(train_bwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(train_bwd_tc_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) !=
+      cudaSuccess)
+    return e;
+  int dev = 0, nsm = 148, sm_smem = 0, reserved = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  int per_sm = (int)((size_t)sm_smem / (smem + 2048 + (size_t)reserved));
+  if (per_sm < 1) per_sm = 1;
+  if (per_sm > 3) per_sm = 3;
+  const int64_t ntiles = (N + 31) / 32;
+  const int64_t grid = ntiles < (int64_t)nsm * per_sm ? ntiles : (int64_t)nsm * per_sm;
+  train_bwd_tc_kernel<<<(unsigned)grid, 128, smem, s>>>(a);
+  return cudaGetLastError();
+}
 
 bool train_tc_supported(const MlpDev& m) {
   return wgrad_tc_supported(m) && m.widths[1] <= 128 && (m.d_in == 2 || m.d_in == 5);
