@@ -123,6 +123,10 @@ cudaError_t launch_train_fwd_tc(const MlpDev& m, const LossArgs& la, float* cons
 // CUDA-core adjoint writes them; wpack as packed by launch_train_fwd_tc.
 cudaError_t launch_train_bwd_tc(const MlpDev& m, int64_t N, const float* const* act, float* const* dz,
                                 const float* seeds, const unsigned char* wpack, cudaStream_t s);
+// Gradients of the input layer (from dz[1] and the inputs) and the output layer
+// (from the seeds and act[n_lin-1]) on CUDA cores, BF16-rounded operands.
+cudaError_t launch_grad_edges_tc(const MlpDev& m, const double* X, int64_t N, const float* dz1, const float* act_top,
+                                 const float* seeds, double* grad, cudaStream_t s);
 size_t wgrad_tc_partial_bytes(const MlpDev& m, int64_t N);
 cudaError_t launch_wgrad_tc(const MlpDev& m, int64_t N, const float* dz, const float* act, double* gW, double* gb,
                             float* partial, cudaStream_t s);

@@ -558,8 +558,16 @@ static cudaError_t loss_grad_impl(const MlpDev& m, const LossArgs& la, double* l
   const unsigned nz = (unsigned)((la.N + chunk - 1) / chunk);
   const bool tc = RND == 2 && wgrad_tc_supported(m);
   float* partial = reinterpret_cast<float*>(base + WT.partial);
+  if (tc && train_tc_supported(m)) {
+    if constexpr (RND == 2) {
+      e = launch_grad_edges_tc(m, la.X, la.N, ws + TL.dz_off[1], ws + TL.act_off[m.n_lin - 1],
+                               ws + TL.dz_off[m.n_lin], grad, s);
+      if (e != cudaSuccess) return e;
+    }
+  }
   for (int l = 1; l <= m.n_lin; ++l) {
     const int wi = m.widths[l - 1], wo = m.widths[l];
+    if (tc && train_tc_supported(m) && (l == 1 || l == m.n_lin)) continue;
     if (tc && l >= 2 && l <= m.n_lin - 1) {
       if constexpr (RND == 2) {
         double* gW = grad + m.poff[l];

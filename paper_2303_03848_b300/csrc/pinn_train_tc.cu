@@ -42,11 +42,28 @@ struct WgArgs {
   const float* act;  // stored streams of layer l-1: [4][w][N] = (t, z_S, z_SS, z_tau)
   int64_t N;
   int w;
+  int nbr;      // rows of B: w, or w + 16 with row w = 1 on the value stream (bias gradient)
   int nb;       // 64-point blocks
   int per_cta;  // chunks per CTA along K
-  float* partial;  // [gridDim.y][w][w]
+  int vec;      // N % 4 == 0: 16-byte loads
+  float* partial;  // [gridDim.y][w][w + 1]
   int* status;
 };
+
+// 8 consecutive floats of a row from p = pb on (zero past N).
+__device__ __forceinline__ void load8(const float* src, int64_t pb, int64_t N, int vec, float (&v)[8]) {
+  if (vec && pb + 8 <= N) {
+    const float4 x = __ldg(reinterpret_cast<const float4*>(src));
+    const float4 y = __ldg(reinterpret_cast<const float4*>(src + 4));
+    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+    v[4] = y.x; v[5] = y.y; v[6] = y.z; v[7] = y.w;
+  } else {
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = pb + e < N ? __ldg(src + e) : 0.0f;
+  }
+}
+
+__device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
 __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
   __nv_bfloat162 q = __floats2bfloat162_rn(lo, hi);
@@ -58,7 +75,8 @@ __global__ void __launch_bounds__(128) wgrad_tc_kernel(WgArgs a) {
   const int w = a.w, t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int ot = blockIdx.x;
   constexpr uint32_t a_bytes = 128 * kChunk * 2;
-  const uint32_t b_bytes = (uint32_t)w * kChunk * 2;
+  const int nbr = a.nbr;
+  const uint32_t b_bytes = (uint32_t)nbr * kChunk * 2;
   auto stA = [&](int st) { return smem + st * a_bytes; };
   auto stB = [&](int st) { return smem + 2 * a_bytes + st * b_bytes; };
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * a_bytes + 2 * b_bytes);
@@ -74,13 +92,13 @@ __global__ void __launch_bounds__(128) wgrad_tc_kernel(WgArgs a) {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   uint32_t ncols = 32;
-  while ((int)ncols < w) ncols <<= 1;
+  while ((int)ncols < nbr) ncols <<= 1;
   if (warp == 0) tmem_alloc(tslot, ncols);
   fence_before();
   __syncthreads();
   fence_after();
   const uint32_t tmem = *tslot;
-  const uint32_t idesc = make_idesc_bf16(w);
+  const uint32_t idesc = make_idesc_bf16(nbr);
   const int64_t N = a.N;
   int n = 0;
   for (int c = c0; c < c1; ++c, ++n) {
@@ -97,40 +115,33 @@ __global__ void __launch_bounds__(128) wgrad_tc_kernel(WgArgs a) {
       uint4 q = make_uint4(0u, 0u, 0u, 0u);
       if (o < w) {
         const int64_t pb = p0 + kc * 8;
-        const float* src = a.dz + ((int64_t)s * w + o) * N + pb;
         float v[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) v[e] = pb + e < N ? __ldg(src + e) : 0.0f;
+        load8(a.dz + ((int64_t)s * w + o) * N + pb, pb, N, a.vec, v);
         q = make_uint4(pack2(v[0], v[1]), pack2(v[2], v[3]), pack2(v[4], v[5]), pack2(v[6], v[7]));
       }
       *reinterpret_cast<uint4*>(stA(st) + canon_off(row, kc * 8, kChunk)) = q;
     }
-    // B: w rows (i) x 64 points of h_s rebuilt from the stored streams, BF16
-    for (int it = t; it < w * (kChunk / 8); it += 128) {
+    // B: w rows (i) x 64 points of h_s rebuilt from the stored streams, BF16;
+    // then (nbr > w) the bias row (1 on the value stream) and zero rows
+    for (int it = t; it < nbr * (kChunk / 8); it += 128) {
       const int i = it >> 3, kc = it & 7;
       const int64_t pb = p0 + kc * 8;
-      const float* t0 = a.act + ((int64_t)0 * w + i) * N + pb;
-      const float* zs = a.act + ((int64_t)1 * w + i) * N + pb;
-      const float* zx = a.act + ((int64_t)(s == 3 ? 3 : 2) * w + i) * N + pb;
       float v[8];
+      if (i >= w) {
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        float h = 0.0f;
-        if (pb + e < N) {
-          const float tt = __ldg(t0 + e);
-          const float d1 = 1.0f - tt * tt;
-          if (s == 0) {
-            h = tt;
-          } else if (s == 1) {
-            h = d1 * __ldg(zs + e);
-          } else if (s == 2) {
-            const float z1 = __ldg(zs + e);
-            h = d1 * __ldg(zx + e) - 2.0f * tt * d1 * z1 * z1;
-          } else {
-            h = d1 * __ldg(zx + e);
-          }
+        for (int e = 0; e < 8; ++e) v[e] = (i == w && s == 0 && pb + e < N) ? 1.0f : 0.0f;
+      } else {
+        float tt[8], zz[8], z1[8];
+        load8(a.act + ((int64_t)0 * w + i) * N + pb, pb, N, a.vec, tt);
+        if (s != 0) load8(a.act + ((int64_t)(s == 2 ? 2 : (s == 3 ? 3 : 1)) * w + i) * N + pb, pb, N, a.vec, zz);
+        if (s == 2) load8(a.act + ((int64_t)1 * w + i) * N + pb, pb, N, a.vec, z1);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const float d1 = 1.0f - tt[e] * tt[e];
+          if (s == 0) v[e] = tt[e];
+          else if (s == 2) v[e] = d1 * zz[e] - 2.0f * tt[e] * d1 * z1[e] * z1[e];
+          else v[e] = d1 * zz[e];
         }
-        v[e] = h;
       }
       const uint4 q = make_uint4(pack2(v[0], v[1]), pack2(v[2], v[3]), pack2(v[4], v[5]), pack2(v[6], v[7]));
       *reinterpret_cast<uint4*>(stB(st) + canon_off(i, kc * 8, kChunk)) = q;
@@ -156,14 +167,15 @@ __global__ void __launch_bounds__(128) wgrad_tc_kernel(WgArgs a) {
   __syncthreads();
   if (!s_fail && n > 0) {
     const int o = ot * 128 + warp * 32 + lane;
-    float* dst = a.partial + ((int64_t)blockIdx.y * w + o) * w;
-    for (int cc = 0; cc < w; cc += 32) {
+    const int wc = nbr > w ? w + 1 : w;  // columns kept: w, and the bias
+    float* dst = a.partial + ((int64_t)blockIdx.y * w + o) * (w + 1);
+    for (int cc = 0; cc < wc; cc += 32) {
       float v[32];
       tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cc, v);
       if (o < w) {
 #pragma unroll
-        for (int e = 0; e < 32; e += 4)
-          *reinterpret_cast<float4*>(dst + cc + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+        for (int e = 0; e < 32; ++e)
+          if (cc + e < wc) dst[cc + e] = v[e];
       }
     }
   }
@@ -174,27 +186,113 @@ __global__ void __launch_bounds__(128) wgrad_tc_kernel(WgArgs a) {
   if (warp == 0) tmem_dealloc(tmem, ncols);
 }
 
-// gW[o][i] = sum over CTAs of the partial sums (FP64 accumulation).
-__global__ void wgrad_sum_kernel(const float* __restrict__ partial, int ny, int w, double* __restrict__ gW) {
-  const int64_t ww = (int64_t)w * w;
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < ww; q += (int64_t)gridDim.x * blockDim.x) {
-    double acc = 0.0;
-    for (int y = 0; y < ny; ++y) acc += (double)partial[(int64_t)y * ww + q];
-    gW[q] = acc;
-  }
+// gW[o][i] (i < w) and gb[o] (column w, when the bias row was in the GEMM):
+// sums over CTAs of the partial sums; blockIdx.y takes one group of CTAs and
+// adds its FP64 sum atomically (the gradient starts at zero).
+__global__ void wgrad_sum_kernel(const float* __restrict__ partial, int ny, int w, int with_bias,
+                                 double* __restrict__ gW, double* __restrict__ gb) {
+  const int64_t wc = (int64_t)w * (w + 1);
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= wc) return;
+  const int o = (int)(q / (w + 1)), i = (int)(q % (w + 1));
+  if (i == w && !with_bias) return;
+  const int y0 = (int)((int64_t)ny * blockIdx.y / gridDim.y), y1 = (int)((int64_t)ny * (blockIdx.y + 1) / gridDim.y);
+  float acc = 0.0f;
+  for (int y = y0; y < y1; ++y) acc += partial[(int64_t)y * wc + q];
+  atomicAdd(i < w ? gW + (int64_t)o * w + i : gb + o, (double)acc);
 }
 
-// gb[o] = sum_p dz_0[o][p], the adjoint rounded to BF16 like the GEMM operand.
+// gb[o] = sum_p dz_0[o][p] for widths without the bias row in the GEMM (w > 240),
+// the adjoint rounded to BF16 like the GEMM operand.
 __global__ void bias_grad_kernel(const float* __restrict__ dz, int64_t N, double* __restrict__ gb) {
-  __shared__ double red[4];
+  __shared__ float red[4];
   const int o = blockIdx.x, t = threadIdx.x;
-  double acc = 0.0;
-  for (int64_t p = t; p < N; p += blockDim.x)
-    acc += (double)__bfloat162float(__float2bfloat16_rn(dz[(int64_t)o * N + p]));
+  float acc = 0.0f;
+  for (int64_t p = t; p < N; p += blockDim.x) acc += bf16r(dz[(int64_t)o * N + p]);
   for (int s = 16; s >= 1; s >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, s);
   if ((t & 31) == 0) red[t >> 5] = acc;
   __syncthreads();
-  if (t == 0) gb[o] = red[0] + red[1] + red[2] + red[3];
+  if (t == 0) gb[o] = (double)red[0] + red[1] + red[2] + red[3];
+}
+
+// Input layer (d_in -> w): its input streams are the mapped inputs h_0 = x^ and
+// the constants h_1 = sc_S e_S, h_3 = sc_tau e_tau (h_2 = 0), so
+//   dL/dW_1[o][i] = sum_p dz_0[o][p] x^_i(p) + [i = 0] sc_S sum_p dz_1[o][p]
+//                   + [i = 1] sc_tau sum_p dz_3[o][p],   dL/db_1[o] = sum_p dz_0[o][p];
+// operands rounded to BF16 like the GEMM operands.  One CTA per (o, chunk).
+template <int DIN>
+__global__ void grad_input_kernel(MlpDev m, const double* __restrict__ X, int64_t N, const float* __restrict__ dz1,
+                                  double* __restrict__ grad, int64_t chunk) {
+  __shared__ float red[4][12];
+  constexpr int d = DIN;
+  const int o = blockIdx.x, t = threadIdx.x, w = m.widths[1];
+  const int64_t p0 = (int64_t)blockIdx.y * chunk, p1 = p0 + chunk < N ? p0 + chunk : N;
+  float ax[8] = {0, 0, 0, 0, 0, 0, 0, 0}, a0 = 0.0f, a1 = 0.0f, a3 = 0.0f;
+  double sc[DIN], lo[DIN];
+#pragma unroll
+  for (int i = 0; i < d; ++i) {
+    sc[i] = 2.0 / (m.hi[i] - m.lo[i]);
+    lo[i] = m.lo[i];
+  }
+  for (int64_t p = p0 + t; p < p1; p += blockDim.x) {
+    const float g0 = bf16r(dz1[(0 * (int64_t)w + o) * N + p]);
+    a0 += g0;
+    a1 += bf16r(dz1[(1 * (int64_t)w + o) * N + p]);
+    a3 += bf16r(dz1[(3 * (int64_t)w + o) * N + p]);
+#pragma unroll
+    for (int i = 0; i < d; ++i) ax[i] += g0 * bf16r((float)(sc[i] * (X[p * d + i] - lo[i]) - 1.0));
+  }
+  float v[11];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = ax[i];
+  v[8] = a0;
+  v[9] = a1;
+  v[10] = a3;
+#pragma unroll
+  for (int k = 0; k < 11; ++k) {
+    float x = v[k];
+    for (int s = 16; s >= 1; s >>= 1) x += __shfl_down_sync(0xffffffffu, x, s);
+    if ((t & 31) == 0) red[t >> 5][k] = x;
+  }
+  __syncthreads();
+  if (t < 11 && (t < d || t >= 8)) {
+    const double tot = (double)red[0][t] + red[1][t] + red[2][t] + red[3][t];
+    double* g = grad + m.poff[1];
+    if (t < d) {
+      atomicAdd(g + (int64_t)o * d + t, tot);
+    } else if (t == 8) {
+      atomicAdd(g + (int64_t)w * d + o, tot);
+    } else {
+      const int i = t == 9 ? 0 : 1;  // d/dS stream feeds input 0 (S), d/dtau stream input 1 (tau)
+      const double sc = 2.0 / (m.hi[i] - m.lo[i]);
+      atomicAdd(g + (int64_t)o * d + i, (double)bf16r((float)sc) * tot);
+    }
+  }
+}
+
+// Output layer (w -> 1): dL/dW_L[i] = sum_{s,p} dz_s[p] h_s[i][p] with h_s
+// rebuilt from the last hidden layer's stored streams; warp i = w is the bias
+// (h_0 = 1).  One warp per i, lanes over the points of a chunk.
+__global__ void grad_output_kernel(const float* __restrict__ act, const float* __restrict__ seeds, int w, int64_t N,
+                                   double* __restrict__ gW, double* __restrict__ gb, int64_t chunk) {
+  const int i = blockIdx.x * 4 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (i > w) return;
+  const int64_t p0 = (int64_t)blockIdx.y * chunk, p1 = p0 + chunk < N ? p0 + chunk : N;
+  float acc = 0.0f;
+  for (int64_t p = p0 + lane; p < p1; p += 32) {
+    const float g0 = bf16r(seeds[p]);
+    if (i == w) {
+      acc += g0;
+      continue;
+    }
+    const float g1 = bf16r(seeds[N + p]), g2 = bf16r(seeds[2 * N + p]), g3 = bf16r(seeds[3 * N + p]);
+    const float tt = act[(0 * (int64_t)w + i) * N + p], zs = act[(1 * (int64_t)w + i) * N + p];
+    const float zss = act[(2 * (int64_t)w + i) * N + p], zt = act[(3 * (int64_t)w + i) * N + p];
+    const float d1 = 1.0f - tt * tt;
+    acc += g0 * bf16r(tt) + g1 * bf16r(d1 * zs) + g2 * bf16r(d1 * zss - 2.0f * tt * d1 * zs * zs) + g3 * bf16r(d1 * zt);
+  }
+  for (int s = 16; s >= 1; s >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, s);
+  if (lane == 0) atomicAdd(i < w ? gW + i : gb, (double)acc);
 }
 
 // CTAs along K: about two per SM over all o tiles.
@@ -208,7 +306,11 @@ void wgrad_grid(int w, int64_t N, int* ot, int* per_cta, int* ny) {
   *ny = (total + pc - 1) / pc;
 }
 
-size_t wgrad_smem_bytes(int w) { return 2 * (size_t)128 * kChunk * 2 + 2 * (size_t)w * kChunk * 2 + 64; }
+int wgrad_rows_b(int w) { return w + 16 <= 256 ? w + 16 : w; }
+
+size_t wgrad_smem_bytes(int w) {
+  return 2 * (size_t)128 * kChunk * 2 + 2 * (size_t)wgrad_rows_b(w) * kChunk * 2 + 64;
+}
 
 // Pack the square layers for training: W_l (rows o, K = i) for the forward and
 // W_l^T (rows i, K = o) for the adjoint, BF16 core-matrix layout.
@@ -224,8 +326,6 @@ __global__ void pack_train_kernel(MlpDev m, int w, unsigned char* fwd, unsigned 
     *reinterpret_cast<__nv_bfloat16*>(bwd + sq * per * 2 + canon_off(i, o, w)) = v;
   }
 }
-
-__device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
 // ---------------------------------------------------------------------------
 // Forward with the four derivative streams on the tensor cores.  A CTA of 128
@@ -268,6 +368,8 @@ __global__ void __launch_bounds__(128) train_fwd_tc_kernel(FwdArgs a) {
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
   __shared__ int s_fail;
   __shared__ double s_acc[3];
+  __shared__ float* s_act[16];
+  if (t < 16) s_act[t] = a.act[t];
 
   for (int i = t; i < w * DIN; i += 128) sW1[i] = bf16r(m.p32[m.poff[1] + i]);
   for (int l = 1; l < m.n_lin; ++l)
@@ -316,7 +418,7 @@ __global__ void __launch_bounds__(128) train_fwd_tc_kernel(FwdArgs a) {
 #pragma unroll
     for (int i = 0; i < DIN; ++i) xh[i] = bf16r(fmaf(valid ? (float)a.la.X[p * DIN + i] : 0.0f, sc[i], of[i]));
     {
-      float* act1 = a.act[1];
+      float* act1 = s_act[1];
       for (int o0 = 0; o0 < w; o0 += 8) {
         float hv[8];
 #pragma unroll
@@ -385,7 +487,7 @@ __global__ void __launch_bounds__(128) train_fwd_tc_kernel(FwdArgs a) {
       if (s_fail) break;
       const bool last = sq == n_sq - 1;
       const float* bl = sB + (l - 1) * w;
-      float* actl = a.act[l];
+      float* actl = s_act[l];
       for (int c = 0; c < w; c += 32) {
         const int buf = (c >> 5) & 1;
         float v[32];
@@ -499,7 +601,13 @@ __global__ void __launch_bounds__(128) train_bwd_tc_kernel(BwdArgs a) {
   uint64_t* bar = reinterpret_cast<uint64_t*>(sseed + 128);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
   __shared__ int s_fail;
+  __shared__ const float* s_act[16];
+  __shared__ float* s_dz[16];
   auto XA = [&](int buf, int k, int qq, int j) -> float& { return xa[((buf * 3 + k) * 32 + qq) * 33 + j]; };
+  if (t < 16) {
+    s_act[t] = a.act[t];
+    s_dz[t] = a.dz[t];
+  }
 
   for (int o = t; o < w; o += 128) sWo[o] = bf16r(m.p32[m.poff[m.n_lin] + o]);
   const int64_t ntiles = (N + 31) / 32;
@@ -535,8 +643,8 @@ __global__ void __launch_bounds__(128) train_bwd_tc_kernel(BwdArgs a) {
     __syncthreads();
     const float seed = sseed[s * 32 + q];
     for (int l = m.n_lin - 1; l >= 1; --l) {
-      const float* act = a.act[l];
-      float* dzl = a.dz[l];
+      const float* act = s_act[l];
+      float* dzl = s_dz[l];
       const bool top = l == m.n_lin - 1;
       for (int c = 0; c < w; c += 32) {
         const int buf = (c >> 5) & 1;
@@ -551,18 +659,26 @@ __global__ void __launch_bounds__(128) train_bwd_tc_kernel(BwdArgs a) {
 #pragma unroll
           for (int j = 0; j < 32; ++j) XA(buf, s - 1, q, j) = ah[j];
         }
-        __syncthreads();
-        float dzv[32];
-#pragma unroll 4
+        // the layer's stored streams at (i, p) for this chunk: t for every stream,
+        // z_S for streams 0 and 1, z_SS and z_tau for stream 0 (loads issued together)
+        float tv[32], zsv[32], zssv[32], ztv[32];
+#pragma unroll
         for (int j = 0; j < 32; ++j) {
           const int64_t i = c + j;
-          const float tt = valid ? act[(0 * (int64_t)w + i) * N + p] : 0.0f;
+          tv[j] = valid ? __ldg(act + (0 * (int64_t)w + i) * N + p) : 0.0f;
+          zsv[j] = (valid && s <= 1) ? __ldg(act + (1 * (int64_t)w + i) * N + p) : 0.0f;
+          zssv[j] = (valid && s == 0) ? __ldg(act + (2 * (int64_t)w + i) * N + p) : 0.0f;
+          ztv[j] = (valid && s == 0) ? __ldg(act + (3 * (int64_t)w + i) * N + p) : 0.0f;
+        }
+        __syncthreads();
+        float dzv[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const float tt = tv[j];
           const float d1 = 1.0f - tt * tt, d2 = -2.0f * tt * d1;
           float r;
           if (s == 0) {
-            const float zs = valid ? act[(1 * (int64_t)w + i) * N + p] : 0.0f;
-            const float zss = valid ? act[(2 * (int64_t)w + i) * N + p] : 0.0f;
-            const float zt = valid ? act[(3 * (int64_t)w + i) * N + p] : 0.0f;
+            const float zs = zsv[j], zss = zssv[j], zt = ztv[j];
             const float ahS = XA(buf, 0, q, j), ahSS = XA(buf, 1, q, j), ahT = XA(buf, 2, q, j);
             const float bar_d2 = ahSS * zs * zs;
             float bar_d1 = ahS * zs + ahSS * zss + ahT * zt;
@@ -572,8 +688,7 @@ __global__ void __launch_bounds__(128) train_bwd_tc_kernel(BwdArgs a) {
             bar_t += -2.0f * tt * bar_d1;
             r = d1 * bar_t;
           } else if (s == 1) {
-            const float zs = valid ? act[(1 * (int64_t)w + i) * N + p] : 0.0f;
-            r = ah[j] * d1 + 2.0f * XA(buf, 1, q, j) * d2 * zs;
+            r = ah[j] * d1 + 2.0f * XA(buf, 1, q, j) * d2 * zsv[j];
           } else {
             r = ah[j] * d1;
           }
@@ -671,6 +786,23 @@ cudaError_t launch_train_bwd_tc(const MlpDev& m, int64_t N, const float* const* 
   return cudaGetLastError();
 }
 
+cudaError_t launch_grad_edges_tc(const MlpDev& m, const double* X, int64_t N, const float* dz1, const float* act_top,
+                                 const float* seeds, double* grad, cudaStream_t s) {
+  if (N <= 0) return cudaSuccess;
+  const int w = m.widths[1];
+  const int64_t chunk = 8192;
+  const unsigned nc = (unsigned)((N + chunk - 1) / chunk);
+  if (m.d_in == 2)
+    grad_input_kernel<2><<<dim3(w, nc), 128, 0, s>>>(m, X, N, dz1, grad, chunk);
+  else
+    grad_input_kernel<5><<<dim3(w, nc), 128, 0, s>>>(m, X, N, dz1, grad, chunk);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  double* gL = grad + m.poff[m.n_lin];
+  grad_output_kernel<<<dim3((w + 1 + 3) / 4, nc), 128, 0, s>>>(act_top, seeds, w, N, gL, gL + w, chunk);
+  return cudaGetLastError();
+}
+
 bool train_tc_supported(const MlpDev& m) {
   return wgrad_tc_supported(m) && m.widths[1] <= 128 && (m.d_in == 2 || m.d_in == 5);
 }
@@ -731,7 +863,7 @@ size_t wgrad_tc_partial_bytes(const MlpDev& m, int64_t N) {
   if (!wgrad_tc_supported(m) || N <= 0) return 0;
   int ot, pc, ny;
   wgrad_grid(m.widths[1], N, &ot, &pc, &ny);
-  return (size_t)ny * m.widths[1] * m.widths[1] * sizeof(float);
+  return (size_t)ny * m.widths[1] * (m.widths[1] + 1) * sizeof(float);
 }
 
 cudaError_t launch_wgrad_tc(const MlpDev& m, int64_t N, const float* dz, const float* act, double* gW, double* gb,
@@ -740,17 +872,22 @@ cudaError_t launch_wgrad_tc(const MlpDev& m, int64_t N, const float* dz, const f
   const int w = m.widths[1];
   int ot, pc, ny;
   wgrad_grid(w, N, &ot, &pc, &ny);
-  WgArgs a{dz, act, N, w, (int)((N + kChunk - 1) / kChunk), pc, partial, m.status};
+  const int nbr = wgrad_rows_b(w);
+  WgArgs a{dz, act, N, w, nbr, (int)((N + kChunk - 1) / kChunk), pc, (N % 4) == 0 ? 1 : 0, partial, m.status};
   const size_t smem = wgrad_smem_bytes(w);
   cudaError_t e = cudaFuncSetAttribute(wgrad_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   wgrad_tc_kernel<<<dim3(ot, ny), 128, smem, s>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  const int64_t ww = (int64_t)w * w;
-  wgrad_sum_kernel<<<(unsigned)((ww + 255) / 256), 256, 0, s>>>(partial, ny, w, gW);
+  const int64_t wc = (int64_t)w * (w + 1);
+  const int groups = ny < 8 ? ny : 8;
+  wgrad_sum_kernel<<<dim3((unsigned)((wc + 255) / 256), groups), 256, 0, s>>>(partial, ny, w, nbr > w, gW, gb);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  bias_grad_kernel<<<w, 128, 0, s>>>(dz, N, gb);
-  return cudaGetLastError();
+  if (nbr == w) {
+    bias_grad_kernel<<<w, 128, 0, s>>>(dz, N, gb);
+    e = cudaGetLastError();
+  }
+  return e;
 }
 
 }  // namespace bsp

@@ -178,3 +178,21 @@ def test_tensor_core_eval_shapes_and_ragged_tiles(B, orc, w, n_hidden, d_in, pre
         u = m.eval(torch.tensor(X, device="cuda"), prec=prec).cpu().numpy()
         assert m.device_status() == B.BS_OK
         assert _rel(u, ref) <= TOL_EVAL[prec], (n, _rel(u, ref))
+
+
+@pytest.mark.parametrize("arch", ["2-4x64", "2-6x128", "5-6x128"])
+def test_tensor_core_training_ragged_batches(B, orc, arch):
+    # BF16 loss and gradient through the tensor-core forward, adjoint and weight
+    # gradient: batches that leave a partial 32-point tile, a partial 64-point
+    # chunk and an N that is not a multiple of 4 (element-wise loads)
+    widths = ARCHS[arch]
+    m, om = _model(B, orc, widths, 31)
+    for n_int, n_b, n_e in ((1, 0, 0), (25, 3, 3), (27, 3, 3), (1501, 128, 128)):
+        X, kind, prob, sok = _loss_case(widths, n_int, n_b, n_e, 17 + n_int)
+        terms, grad = orc.pinn_loss_grad(om, X, kind, prob["K"], prob["sigma"], prob["r"], prob["Smax"], sok)
+        l3, g = m.loss_grad(torch.tensor(X, device="cuda"), torch.tensor(kind, device="cuda"), prob, sok, prec=B.BF16)
+        l3, g = l3.cpu().numpy(), g.cpu().numpy()
+        assert m.device_status() == B.BS_OK
+        for c in range(3):
+            assert abs(l3[c] - terms[c]) <= 5e-2 * max(abs(terms[c]), 1e-300), (len(kind), c, l3[c], terms[c])
+        assert _rel(g, grad) <= 1e-1, (len(kind), _rel(g, grad))
