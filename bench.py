@@ -42,8 +42,6 @@ METRIC = "Parareal solves/s at 1e-6 vs serial fine"
 WORKLOAD = ("PINN-coarse Parareal, BS call K=1 sigma=0.2 r=0.05 T=1, Nx=1024 S in [0,4], P=32, "
             "CN 1024 steps/slice FP64, MLP 2->4x64 tanh trained 5k Adam steps on 16384+1024 points")
 FLOPS_PER_PT_STEP = 11.0  # CN right-hand side 5 + factored solve 6 (algorithmic, per interior point-step)
-# DRAM read+write bytes of one fine launch over all 32 slices from the ncu capture in profiles/;
-# None whenever the kernel has changed since the last capture
 # DRAM bytes (read + write) of one fine_propagate launch over the 32 slices of the
 # benchmark workload, from one ncu capture per partition (profiles/); a partition
 # without a capture of its current code reports null
@@ -113,6 +111,8 @@ class Clocks:
 
 
 def dist_setup():
+    """One process per GPU (torchrun environment): NCCL on GPUs, gloo on a host
+    without them (the CPU tests of this host logic)."""
     import torch
 
     ws = int(os.environ.get("WORLD_SIZE", "1"))
@@ -121,8 +121,11 @@ def dist_setup():
     if ws > 1:
         import torch.distributed as dist
 
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group("gloo")
     return ws, rank, local
 
 
@@ -134,14 +137,21 @@ def barrier(ws):
 
 
 def allreduce_max(ws, v: float) -> float:
+    """The largest of the ranks' values (step time: the job is as slow as its slowest rank)."""
     if ws == 1:
         return v
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_rate(ws, ms_per_step: float) -> float:
+    """Whole-job solves/s: every rank runs one solve per step (replicas), timed by the slowest."""
+    return ws * 1e3 / ms_per_step
 
 
 def rel_error(U, Uref, P, Nx):
@@ -246,7 +256,7 @@ def run_ours(args):
     barrier(ws)
     err_after = rel_error(U, Uf, CFG["P"], CFG["Nx"])
     ms_step = allreduce_max(ws, sum(ms) / len(ms))
-    value = ws * 1e3 / ms_step
+    value = job_rate(ws, ms_step)
     ms_direct, _ = time_solves(prob, B.COARSE_PINN, model, prec, tol, 2, 1, torch, flush, graph=False)
 
     # fine kernel alone: iteration-0 launch shape (all P slices), CUDA events on the current stream
@@ -328,9 +338,11 @@ def run_ours(args):
                    "launch": "whole solve captured in one CUDA graph, replayed per step",
                    "ms_per_solve_host_loop": statistics.mean(ms_direct),
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
-        "e2e": {"value": ws * 1e3 / e2e_step, "unit": "solves/s", "h2d_bytes_per_step": 8 * model.n_params,
+        "e2e": {"value": job_rate(ws, e2e_step), "unit": "solves/s", "h2d_bytes_per_step": 8 * model.n_params,
                 "d2h_bytes_per_step": 8 * prob.total_state},
-        "gpu_launches": 3 + 1 + 2 * kmax + 1,
+        # network table (grid points, weight pack for the tensor-core path, evaluation, Dirichlet fix),
+        # initial iterate, per iteration fine propagation + stop test, result copy
+        "gpu_launches": (4 if prec == B.BF16 else 3) + 1 + 2 * kmax + 1,
         "roofline": {"bound": "alu", "achieved": fine_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
                      "frac": fine_tflops / fp64_peak, "traffic": fine_traffic, "kernel": fine_kernel_name,
                      "peak_note": "FP64: 148 SM x 2 DFMA lanes/clk (measured) x 2 flop x max SM clock"},
