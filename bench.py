@@ -535,6 +535,61 @@ def train_leg(B, torch, n_points=65536, steps=20):
     return out
 
 
+def sweep_leg(B, torch, model, Ps=(4, 8, 16, 32, 64), total_steps=32768):
+    """Speedup against P on one GPU next to the bound of Eq. 8 (the paper's Figs. 5-6):
+    the benchmark grid with a fixed total of fine steps split over P slices; per P the
+    serial fine time, and per coarse propagator the iterations and time to 1e-6 against
+    serial fine (graph-replayed solves), the speedup, and the bound
+    1 / ((1 + K/P) c_c/c_f + K/P) with c_c, c_f the measured coarse and fine
+    propagation times of one slice (all slices side by side)."""
+    from paper_2303_03848_b300 import binding as BB
+
+    ev = lambda: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        out = []
+        for _ in range(reps):
+            a, b = ev()
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            out.append(a.elapsed_time(b))
+        return min(out)
+
+    flush = torch.zeros(1, dtype=torch.float64, device="cuda")
+    rows = []
+    for P in Ps:
+        cfg = dict(CFG, P=P, fine_steps=total_steps // P)
+        prob = BB.Problem(cfg)
+        Uf = prob.serial_fine()
+        serial_ms = timed(lambda: prob.serial_fine(Uf))
+        U0 = Uf.view(P + 1, cfg["Nx"])[:-1].contiguous().view(-1)
+        Fo = torch.empty_like(U0)
+        c_f = timed(lambda: prob.fine_propagate(U0, Fo))
+        c_c = timed(lambda: prob.coarse_propagate(U0, Fo))
+        row = {"P": P, "fine_steps_per_slice": cfg["fine_steps"], "serial_fine_ms": serial_ms, "c_f_ms": c_f,
+               "c_c_ms": c_c}
+        for name, kind, mdl in (("ie", BB.COARSE_IE, None), ("pinn", BB.COARSE_PINN, model)):
+            tol = None
+            for cand in (1e-6, 1e-7, 1e-8, 1e-9, 1e-10, 0.0):
+                U, norms, stats, rc = prob.parareal_solve(kind, model=mdl, prec=BB.BF16, tol=cand)
+                err = rel_error(U, Uf, P, cfg["Nx"])
+                if err <= TARGET:
+                    tol, K = cand, stats[0]["iterations"]
+                    break
+            ms, _ = time_solves(prob, kind, mdl, BB.BF16, tol, 3, 2, torch, flush)
+            ms = statistics.mean(ms)
+            bound = 1.0 / ((1.0 + K / P) * (c_c / c_f) + K / P)
+            row[name] = {"tol": tol, "iterations": K, "ms": ms, "speedup": serial_ms / ms, "eq8_bound": bound,
+                         "parallel_efficiency": serial_ms / ms / P}
+        rows.append(row)
+        prob.close()
+    return {"grid": "Nx=1024, S in [0,4], K=1 sigma=0.2 r=0.05 T=1", "total_fine_steps": total_steps, "rows": rows}
+
+
 def run_large(args):
     """Large single instance: Nx=65536, S in [0,8], sigma 0.3, r 0.03, T 2, K 1, P=256, CN 4096 steps/slice."""
     import torch
@@ -654,7 +709,7 @@ def main():
     ap.add_argument("--prec", default="bf16", choices=["fp64", "fp32", "tf32", "bf16"])
     ap.add_argument("--train-steps", type=int, default=5000)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
-    ap.add_argument("--mode", default="solve", choices=["solve", "fine", "batched", "large", "pinn", "train"],
+    ap.add_argument("--mode", default="solve", choices=["solve", "fine", "batched", "large", "pinn", "train", "sweep"],
                     help="fine / batched: only the fine propagator on all slices of the benchmark / "
                          "batched workload (profiling)")
     ap.add_argument("--batched", type=int, default=1, help="include the batched-workload leg (1/0)")
@@ -674,6 +729,15 @@ def main():
 
         BUILD.build()
         print(json.dumps(pinn_leg(B, torch)), flush=True)
+    elif args.mode == "sweep":
+        import torch
+
+        from paper_2303_03848_b300 import binding as B
+        from paper_2303_03848_b300 import build as BUILD
+
+        BUILD.build()
+        model, _ = train_network(B, torch, args.train_steps)
+        print(json.dumps(sweep_leg(B, torch, model)), flush=True)
     elif args.mode == "train":
         import torch
 

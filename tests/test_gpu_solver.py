@@ -241,3 +241,17 @@ def test_repeat_calls_are_deterministic(B):
     U1 = U1.clone()
     U2, *_ = prob.parareal_solve(B.COARSE_IE, tol=1e-12)
     assert torch.equal(U1, U2)
+
+
+def test_single_slice_and_single_step_degenerate_cases(B, orc):
+    # P = 1: Parareal is exact after one iteration (the only slice starts from
+    # the payoff), so it equals serial fine bitwise; fine_steps = 1: one CN step
+    # per slice still matches the oracle
+    for cfg in (dict(_cfg1(), P=1, fine_steps=64), dict(_cfg1(), P=4, fine_steps=1), dict(_cfg1(), Nx=5, P=1)):
+        prob = B.Problem(cfg)
+        Uf = prob.serial_fine()
+        U, norms, stats, rc = prob.parareal_solve(B.COARSE_IE, tol=0.0)
+        assert rc == B.BS_OK and stats[0]["iterations"] == cfg["P"]
+        assert torch.equal(U, Uf)
+        ref = orc.serial_fine(_oparams(orc, cfg))
+        _close(Uf.cpu().numpy(), ref.ravel(), _kappa_tol(cfg, "fine", cfg["P"]))
