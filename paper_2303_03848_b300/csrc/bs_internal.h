@@ -27,6 +27,7 @@ struct PropArgs {
   const double* uold;        // kPinnFused: U^k (state layout)
   double* normbuf;           // kPinnFused: (num, den) per (instance, boundary index, cluster rank)
   int* status;               // nullable: BS_TIMEOUT recorded here if a bounded wait gave up
+  int n_inst, maxP;          // tasks = n_inst x maxP (instance ids[i], slice n), set by launch_prop
 };
 
 struct SerialArgs {

@@ -376,13 +376,19 @@ __device__ __forceinline__ void load_solver(const double* __restrict__ cb, Solve
     const int row = c * NW + wl - 1 + side;  // global warp w-1 (side 0) or w (side 1)
     sm.G2[wl][side][u] = row >= 0 ? cb[coef_G_off(row, u, M, GT, Ws)] : 0.0;
   }
+  __syncthreads();  // the kernel's cluster barrier follows before any exchange
+}
+
+// The exchange barriers, once per launch (a cluster barrier follows before the
+// first step; the step counter then runs on across slices and tasks).
+template <int M, int NW, int C>
+__device__ __forceinline__ void exchange_init(SolverSmem<M, NW, C>& sm, SolverRegs& rg) {
   rg.fail = 0;
-  if (C > 1 && t == 0) {
+  if (C > 1 && threadIdx.x == 0) {
     mbar_init(smem_addr(&sm.bar[0]));
     mbar_init(smem_addr(&sm.bar[1]));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  __syncthreads();  // the kernel's cluster barrier follows before any exchange
 }
 
 // A CTA whose wait gave up records BS_TIMEOUT and waits (again bounded) for the
@@ -617,87 +623,94 @@ __global__ void __launch_bounds__(NW * 32, 1) prop_kernel(PropArgs a) {
   constexpr int T = NW * 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SolverSmem<M, NW, C>& sm = *reinterpret_cast<SolverSmem<M, NW, C>*>(smem_raw);
-  const int idx = a.ids[blockIdx.y];
-  const Inst in = a.insts[idx];
-  const int n = blockIdx.x / C;
-  // every exit condition below is uniform over the cluster (same slice, same instance)
-  if (n >= in.P) return;
-  if (a.k_iter >= 0 && n < a.k_iter) return;
-  if (a.ctrl != nullptr && a.ctrl[idx].done) return;
-  if (a.active != nullptr && !a.active[in.task_off + n]) return;
   const int t = threadIdx.x, c = cta_rank<C>();
-  const double* cb = a.pool + (CN ? in.coef_cn : in.coef_ie);
-  const double* et = a.exptab + (CN ? in.exp_cn : in.exp_ie);
-  const int steps = CN ? in.Mf : in.Mg;
   SolverRegs rg;
-  load_solver<M, NW, C>(cb, sm, rg);
-  if constexpr (C > 1) cg::this_cluster().sync();  // every CTA of the grid is running
-
-  const int Nx = in.Nx;
-  const double* Vin = a.in + (a.in_state ? in.state_off : in.slice_off) + (int64_t)n * Nx;
-  double W[M], x[M];
-  load_state<M, NW, C>(in, Vin, sm, rg, W);
-#pragma unroll
-  for (int k = 0; k < M; ++k) x[k] = 0.0;
+  exchange_init<M, NW, C>(sm, rg);
   int seq = 0;
-  run_slice<M, NW, C, CN>(in, n, et, steps, W, x, sm, rg, seq);
+  // persistent: cluster q walks the (instance, slice) tasks q, q + clusters, ...;
+  // every skip below is uniform over the cluster (same task)
+  const int64_t n_cl = gridDim.x / C, ntask = (int64_t)a.n_inst * a.maxP;
+  for (int64_t task = blockIdx.x / C; task < ntask; task += n_cl) {
+    const int idx = a.ids[task / a.maxP];
+    const int n = (int)(task % a.maxP);
+    const Inst in = a.insts[idx];
+    if (n >= in.P) continue;
+    if (a.k_iter >= 0 && n < a.k_iter) continue;
+    if (a.ctrl != nullptr && a.ctrl[idx].done) continue;
+    if (a.active != nullptr && !a.active[in.task_off + n]) continue;
+    const double* cb = a.pool + (CN ? in.coef_cn : in.coef_ie);
+    const double* et = a.exptab + (CN ? in.exp_cn : in.exp_ie);
+    const int steps = CN ? in.Mf : in.Mg;
+    __syncthreads();  // the previous task is done with the shared tables
+    load_solver<M, NW, C>(cb, sm, rg);
+    if constexpr (C > 1) cg::this_cluster().sync();  // every CTA of the grid holds its tables
 
-  const bool first_thread = c == 0 && t == 0;
-  const bool last_thread = c == C - 1 && t == T - 1;
-  const int g = c * T + t;
-  const double Bend = bc_right(in, n + 1);
-  double* Vout = a.out + (a.out_state ? in.state_off + (int64_t)(n + 1) * Nx : in.slice_off + (int64_t)n * Nx);
-  if (a.mode == PropArgs::kPlain) {
+    const int Nx = in.Nx;
+    const double* Vin = a.in + (a.in_state ? in.state_off : in.slice_off) + (int64_t)n * Nx;
+    double W[M], x[M];
+    load_state<M, NW, C>(in, Vin, sm, rg, W);
 #pragma unroll
-    for (int k = 0; k < M; ++k) {
-      const int j = g * M + k - in.Np + 1;
-      if (j >= 1 && j <= Nx - 2) Vout[j] = row_value<M, NW, C, CN>(cb, k, W, x, rg.isigp);
-    }
-    if (first_thread) Vout[0] = 0.0;
-    if (last_thread) Vout[Nx - 1] = Bend;
-  } else {
-    // kPinnFused: U^{k+1}_{n+1} = F(U^k_n) + (G_new - G_old) with G = the network
-    // table at tau_{n+1} for both terms (Eq. 7); increment-norm partial sums.
-    const double* gg = a.gtab + in.state_off + (int64_t)(n + 1) * Nx;
-    const double* Uold = a.uold + in.state_off + (int64_t)(n + 1) * Nx;
-    double num = 0.0, den = 0.0;
+    for (int k = 0; k < M; ++k) x[k] = 0.0;
+    run_slice<M, NW, C, CN>(in, n, et, steps, W, x, sm, rg, seq);
+
+    const bool first_thread = c == 0 && t == 0;
+    const bool last_thread = c == C - 1 && t == T - 1;
+    const int g = c * T + t;
+    const double Bend = bc_right(in, n + 1);
+    double* Vout = a.out + (a.out_state ? in.state_off + (int64_t)(n + 1) * Nx : in.slice_off + (int64_t)n * Nx);
+    if (a.mode == PropArgs::kPlain) {
 #pragma unroll
-    for (int k = 0; k < M; ++k) {
-      const int j = g * M + k - in.Np + 1;
-      if (j >= 1 && j <= Nx - 2) {
-        const double f = row_value<M, NW, C, CN>(cb, k, W, x, rg.isigp);
-        const double v = f + (gg[j] - gg[j]);
-        Vout[j] = v;
-        const double d = v - Uold[j];
+      for (int k = 0; k < M; ++k) {
+        const int j = g * M + k - in.Np + 1;
+        if (j >= 1 && j <= Nx - 2) Vout[j] = row_value<M, NW, C, CN>(cb, k, W, x, rg.isigp);
+      }
+      if (first_thread) Vout[0] = 0.0;
+      if (last_thread) Vout[Nx - 1] = Bend;
+    } else {
+      // kPinnFused: U^{k+1}_{n+1} = F(U^k_n) + (G_new - G_old) with G = the network
+      // table at tau_{n+1} for both terms (Eq. 7); increment-norm partial sums.
+      const double* gg = a.gtab + in.state_off + (int64_t)(n + 1) * Nx;
+      const double* Uold = a.uold + in.state_off + (int64_t)(n + 1) * Nx;
+      double num = 0.0, den = 0.0;
+#pragma unroll
+      for (int k = 0; k < M; ++k) {
+        const int j = g * M + k - in.Np + 1;
+        if (j >= 1 && j <= Nx - 2) {
+          const double f = row_value<M, NW, C, CN>(cb, k, W, x, rg.isigp);
+          const double v = f + (gg[j] - gg[j]);
+          Vout[j] = v;
+          const double d = v - Uold[j];
+          num = fma(d, d, num);
+          den = fma(v, v, den);
+        }
+      }
+      if (first_thread) {
+        const double v = 0.0 + (gg[0] - gg[0]);
+        Vout[0] = v;
+        const double d = v - Uold[0];
         num = fma(d, d, num);
         den = fma(v, v, den);
       }
+      if (last_thread) {
+        const double v = Bend + (gg[Nx - 1] - gg[Nx - 1]);
+        Vout[Nx - 1] = v;
+        const double d = v - Uold[Nx - 1];
+        num = fma(d, d, num);
+        den = fma(v, v, den);
+      }
+      // the slice that becomes exact this iteration keeps its start value
+      if (a.k_iter >= 0 && n == a.k_iter) {
+        double* Fz = a.out + in.state_off + (int64_t)n * Nx;
+        for (int j = g; j < Nx; j += C * T) Fz[j] = Vin[j];
+      }
+      block_sum2<NW>(num, den, sm.red);
+      if (t == 0) {
+        const int64_t slot = (in.norm_off + (int64_t)(n + 1) * C + c) * 2;
+        a.normbuf[slot + 0] = num;
+        a.normbuf[slot + 1] = den;
+      }
     }
-    if (first_thread) {
-      const double v = 0.0 + (gg[0] - gg[0]);
-      Vout[0] = v;
-      const double d = v - Uold[0];
-      num = fma(d, d, num);
-      den = fma(v, v, den);
-    }
-    if (last_thread) {
-      const double v = Bend + (gg[Nx - 1] - gg[Nx - 1]);
-      Vout[Nx - 1] = v;
-      const double d = v - Uold[Nx - 1];
-      num = fma(d, d, num);
-      den = fma(v, v, den);
-    }
-    // the slice that becomes exact this iteration keeps its start value
-    if (a.k_iter >= 0 && n == a.k_iter) {
-      double* Fz = a.out + in.state_off + (int64_t)n * Nx;
-      for (int j = g; j < Nx; j += C * T) Fz[j] = Vin[j];
-    }
-    block_sum2<NW>(num, den, sm.red);
-    if (t == 0) {
-      const int64_t slot = (in.norm_off + (int64_t)(n + 1) * C + c) * 2;
-      a.normbuf[slot + 0] = num;
-      a.normbuf[slot + 1] = den;
-    }
+    if constexpr (C > 1) cg::this_cluster().sync();  // no CTA moves on while its tables may be read
   }
   exchange_drain<M, NW, C>(sm, rg, seq, a.status);
   if constexpr (C > 1) cg::this_cluster().sync();  // no CTA leaves while its shared memory may be written
@@ -717,6 +730,7 @@ __global__ void __launch_bounds__(NW * 32, 1) serial_fine_kernel(SerialArgs a) {
   const double* cb = a.pool + in.coef_cn;
   const double* et = a.exptab + in.exp_cn;
   SolverRegs rg;
+  exchange_init<M, NW, C>(sm, rg);
   load_solver<M, NW, C>(cb, sm, rg);
   double* U = a.out + in.state_off;
   for (int j = g; j < Nx; j += C * T) {
@@ -777,6 +791,7 @@ __global__ void __launch_bounds__(NW * 32, 1) sweep_kernel(SweepArgs a) {
   const double* cb = a.pool + in.coef_ie;
   const double* et = a.exptab + in.exp_ie;
   SolverRegs rg{};
+  exchange_init<M, NW, C>(sm, rg);
   if (ie) load_solver<M, NW, C>(cb, sm, rg);
   if constexpr (C > 1) cg::this_cluster().sync();
   const bool init = a.k_iter < 0;
@@ -1055,14 +1070,45 @@ static cudaError_t launch_cluster(Kern kernel, dim3 grid, int threads, int C, in
   return cudaLaunchKernelEx(&cfg, kernel, arg);
 }
 
+// Persistent launch: as many clusters as fit on the device at once (or one per
+// task when there are fewer tasks), each walking its share of the tasks.
+template <typename Kern>
+static cudaError_t launch_persistent(Kern kernel, int threads, int C, int smem, cudaStream_t s, PropArgs a,
+                                     int n_inst, int maxP) {
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  if (C > 8 && (e = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess)
+    return e;
+  const int64_t ntask = (int64_t)n_inst * maxP;
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3(threads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cfg.gridDim = dim3((unsigned)(ntask < 65536 ? ntask : 65536) * C, 1, 1);
+  int resident = 0;
+  if ((e = cudaOccupancyMaxActiveClusters(&resident, kernel, &cfg)) != cudaSuccess) return e;
+  if (resident < 1) resident = 1;
+  const int64_t ncl = ntask < resident ? ntask : resident;
+  cfg.gridDim = dim3((unsigned)(ncl * C), 1, 1);
+  a.n_inst = n_inst;
+  a.maxP = maxP;
+  return cudaLaunchKernelEx(&cfg, kernel, a);
+}
+
 cudaError_t launch_prop(int M, int NW, int C, bool cn, const PropArgs& a, int n_inst, int maxP, cudaStream_t s) {
   if (n_inst <= 0) return cudaSuccess;
-  dim3 grid(maxP * C, n_inst);
 #define X(MM, WW, CC)                                                                                            \
   if (M == MM && NW == WW && C == CC) {                                                                          \
     const int sz = (int)sizeof(SolverSmem<MM, WW, CC>);                                                          \
-    return cn ? launch_cluster(prop_kernel<MM, WW, CC, true>, grid, WW * 32, CC, sz, s, a)                       \
-              : launch_cluster(prop_kernel<MM, WW, CC, false>, grid, WW * 32, CC, sz, s, a);                      \
+    return cn ? launch_persistent(prop_kernel<MM, WW, CC, true>, WW * 32, CC, sz, s, a, n_inst, maxP)            \
+              : launch_persistent(prop_kernel<MM, WW, CC, false>, WW * 32, CC, sz, s, a, n_inst, maxP);           \
   }
   BSP_FOR_EACH_CLASS(X)
 #undef X
