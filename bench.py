@@ -443,16 +443,26 @@ def batched_leg(B, torch, n_inst=4096, solve=True, rule_too=False):
                 "fine_tflops_algorithmic": tf, "fine_frac_of_fp64_peak": tf / peak})
     torch.cuda.empty_cache()
     if solve:
-        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        s0.record()
+        # statistics from one direct call, time from replays of the whole batched
+        # solve captured as one CUDA graph (persistent propagation launches inside)
         U, norms, stats, rc = prob.parareal_solve(B.COARSE_IE, tol=1e-6, max_iter=64)
-        s1.record()
-        torch.cuda.synchronize()
         its = [st["iterations"] for st in stats]
-        out.update({"ie_solve_ms": s0.elapsed_time(s1), "ie_solves_per_s": n_inst / (s0.elapsed_time(s1) * 1e-3),
+        del U
+        g = B.SolveGraph(prob, B.COARSE_IE, tol=1e-6, max_iter=64)
+        reps = []
+        for _ in range(2):
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record()
+            g.replay()
+            s1.record()
+            torch.cuda.synchronize()
+            reps.append(s0.elapsed_time(s1))
+        ms_solve = min(reps)
+        out.update({"ie_solve_ms": ms_solve, "ie_solves_per_s": n_inst / (ms_solve * 1e-3),
+                    "ie_launch": "whole batched solve in one CUDA graph",
                     "ie_iterations_mean": float(sum(its)) / len(its), "ie_iterations_max": max(its),
                     "ie_status": rc})
-        del U
+        del g
     prob.close()
     torch.cuda.empty_cache()
     return out
@@ -598,7 +608,8 @@ def run_large(args):
     from paper_2303_03848_b300 import build as BUILD
 
     BUILD.build()
-    cfg = dict(K=1.0, sigma=0.3, r=0.03, T=2.0, Smax=8.0, Nx=65536, P=256, fine_steps=4096, coarse_steps=1)
+    cfg = dict(K=1.0, sigma=0.3, r=0.03, T=2.0, Smax=8.0, Nx=65536, P=args.large_p, fine_steps=args.large_steps,
+               coarse_steps=1)
     prob = B.Problem(cfg)
     part = prob.partition(0)
     ev = lambda: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -610,6 +621,7 @@ def run_large(args):
     serial_ms = a.elapsed_time(b)
     U0 = Uf.view(cfg["P"] + 1, cfg["Nx"])[:-1].contiguous().view(-1)
     Fo = torch.empty_like(U0)
+    prob.fine_propagate(U0, Fo)  # warm-up
     a, b = ev()
     a.record()
     prob.fine_propagate(U0, Fo)
@@ -714,6 +726,8 @@ def main():
                          "batched workload (profiling)")
     ap.add_argument("--batched", type=int, default=1, help="include the batched-workload leg (1/0)")
     ap.add_argument("--instances", type=int, default=4096, help="instances of --mode batched")
+    ap.add_argument("--large-p", type=int, default=256, help="slices of --mode large")
+    ap.add_argument("--large-steps", type=int, default=4096, help="CN steps per slice of --mode large")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
