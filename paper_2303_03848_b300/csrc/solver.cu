@@ -292,6 +292,9 @@ struct SolverSmem {
 struct SolverRegs {
   double kap, nu, sigp, isigp;
   double m1[kPcrLevels], m2[kPcrLevels], inv, ra, rc;
+  // M = 2: the step's state update written as K + e Y_{w-1} + f Y_w per row, with
+  // K formed before the cross-warp unknowns arrive (see step_finish)
+  double s0, sa, sb, e0, f0, sp, g1, h1;
   int fail;  // a bounded wait gave up (sticky; later waits are skipped)
 };
 
@@ -366,6 +369,27 @@ __device__ __forceinline__ void load_solver(const double* __restrict__ cb, Solve
   rg.inv = cb[coef_pcr_off(10, g, M, GT)];
   rg.ra = cb[coef_resp_off(0, g, M, GT)];
   rg.rc = cb[coef_resp_off(1, g, M, GT)];
+  if constexpr (M == 2) {
+    // X = Xt + ra Yl + rc Yr on lanes 0..30 and X = Yr on lane 31; the inner
+    // row's left neighbour is the previous lane's X (Yl on lane 0)
+    const int L = t & 31;
+    const double ra = L == 31 ? 0.0 : rg.ra, rc = L == 31 ? 1.0 : rg.rc;
+    double rap = __shfl_up_sync(kFull, ra, 1), rcp = __shfl_up_sync(kFull, rc, 1);
+    if (L == 0) {
+      rap = 1.0;
+      rcp = 0.0;
+    }
+    const double s0 = cb[coef_rows_off(2, 0, g, M, GT)];
+    const double al = cb[coef_rows_off(3, 0, g, M, GT)], be = cb[coef_rows_off(4, 0, g, M, GT)];
+    rg.s0 = s0;
+    rg.sa = L == 0 ? 0.0 : s0 * al;
+    rg.sb = L == 31 ? 0.0 : s0 * be;
+    rg.e0 = s0 * (al * rap + be * ra);
+    rg.f0 = s0 * (al * rcp + be * rc);
+    rg.sp = L == 31 ? 0.0 : rg.sigp;
+    rg.g1 = rg.sigp * ra;
+    rg.h1 = rg.sigp * rc;
+  }
   for (int i = t; i < Ws; i += T) {
     sm.nu31[i] = cb[coef_warp_off(0, i, M, GT, Ws)];
     sm.A31[i] = cb[coef_warp_off(1, i, M, GT, Ws)];
@@ -471,20 +495,31 @@ __device__ __forceinline__ void step_finish(double (&W)[M], double (&x)[M], Solv
                                             SolverRegs& rg, double Xt, int seq) {
   const int par = seq & 1;
   constexpr int Ws = C * NW;
-  constexpr int NU = (Ws + 31) / 32;
+  constexpr bool kHalves = Ws <= 16;  // lanes 0-15 form Y_{w-1}, lanes 16-31 Y_w
+  constexpr int NU = kHalves ? 1 : (Ws + 31) / 32;
   const int t = threadIdx.x, L = t & 31, wl = t >> 5;
   // constants of the cross-warp solve for the lanes' warps u, read while the
   // other CTAs' values arrive
   double cnu[NU], ca[NU], cc[NU], g0[NU], g1[NU];
 #pragma unroll
   for (int q = 0; q < NU; ++q) {
-    const int u = q * 32 + L;
+    const int u = kHalves ? (L & 15) : q * 32 + L;
     const bool ok = u < Ws;
     cnu[q] = ok ? sm.nu31[u] : 0.0;
     ca[q] = ok ? sm.A31[u] : 0.0;
     cc[q] = ok ? sm.C31[u] : 0.0;
-    g0[q] = ok ? sm.G2[wl][0][u] : 0.0;
+    g0[q] = ok ? sm.G2[wl][kHalves ? (L >> 4) : 0][u] : 0.0;
     g1[q] = ok ? sm.G2[wl][1][u] : 0.0;
+  }
+  // M = 2, the part of the state update that does not depend on the
+  // cross-warp unknowns (formed while they arrive):
+  //   W_0' = [s0 x_0 - W_0 + s0 al Xt_{L-1} + s0 be Xt] + e0 Y_{w-1} + f0 Y_w,
+  //   W_1' = [sigp Xt - W_1] + g1 Y_{w-1} + h1 Y_w   (no -W terms for implicit Euler)
+  double K0 = 0.0, K1 = 0.0;
+  if constexpr (M == 2) {
+    const double Xtp = __shfl_up_sync(kFull, Xt, 1);
+    K0 = fma(rg.sa, Xtp, fma(rg.sb, Xt, CN ? fma(rg.s0, x[0], -W[0]) : rg.s0 * x[0]));
+    K1 = CN ? fma(rg.sp, Xt, -W[1]) : rg.sp * Xt;
   }
   if constexpr (C == 1) {
     __syncthreads();
@@ -493,43 +528,70 @@ __device__ __forceinline__ void step_finish(double (&W)[M], double (&x)[M], Solv
   }
   // 5. cross-warp unknowns: rho_u by lane u, then Y_{w-1} and Y_w as dot
   //    products with rows of the precomputed inverse
-  double pl = 0.0, pr = 0.0;
-#pragma unroll
-  for (int q = 0; q < NU; ++q) {
-    const int u = q * 32 + L;
+  double Yl, Yr;
+  if constexpr (kHalves) {
+    const int u = L & 15;
+    double v = 0.0;
     if (u < Ws) {
       double rho;
       if (u == Ws - 1) {
         rho = sm.pub[par][u][3];
       } else {
-        rho = fma(-cnu[q], sm.pub[par][u + 1][0], sm.pub[par][u][3]);
-        rho = fma(-ca[q], sm.pub[par][u][2], rho);
-        rho = fma(-cc[q], sm.pub[par][u + 1][1], rho);
+        rho = fma(-cnu[0], sm.pub[par][u + 1][0], sm.pub[par][u][3]);
+        rho = fma(-ca[0], sm.pub[par][u][2], rho);
+        rho = fma(-cc[0], sm.pub[par][u + 1][1], rho);
       }
-      pl = fma(g0[q], rho, pl);
-      pr = fma(g1[q], rho, pr);
+      v = g0[0] * rho;
     }
-  }
-  // reduce-scatter of the two sums: the first level leaves the Y_{w-1} partial
-  // on even lanes and the Y_w partial on odd lanes, then one sum per level
-  const bool odd = (L & 1) != 0;
-  double v = (odd ? pr : pl) + __shfl_xor_sync(kFull, odd ? pl : pr, 1);
 #pragma unroll
-  for (int s = 2; s < (Ws < 32 ? Ws : 32); s <<= 1) v += __shfl_xor_sync(kFull, v, s);
-  const double Yl = __shfl_sync(kFull, v, 0);
-  const double Yr = __shfl_sync(kFull, v, 1);
-  const double X = (L == 31) ? Yr : fma(rg.rc, Yr, fma(rg.ra, Yl, Xt));
-  double Xprev = __shfl_up_sync(kFull, X, 1);
-  if (L == 0) Xprev = Yl;
-  // 6. fixup of the inner rows and the scaled state update
+    for (int s = 1; s < Ws; s <<= 1) v += __shfl_xor_sync(kFull, v, s);
+    Yl = __shfl_sync(kFull, v, 0);
+    Yr = __shfl_sync(kFull, v, 16);
+  } else {
+    double pl = 0.0, pr = 0.0;
 #pragma unroll
-  for (int k = 0; k <= M - 2; ++k) {
-    const double xv = fma(sm.rows[4][k][t], X, fma(sm.rows[3][k][t], Xprev, x[k]));
-    x[k] = xv;
-    W[k] = CN ? fma(sm.rows[2][k][t], xv, -W[k]) : sm.rows[2][k][t] * xv;
+    for (int q = 0; q < NU; ++q) {
+      const int u = q * 32 + L;
+      if (u < Ws) {
+        double rho;
+        if (u == Ws - 1) {
+          rho = sm.pub[par][u][3];
+        } else {
+          rho = fma(-cnu[q], sm.pub[par][u + 1][0], sm.pub[par][u][3]);
+          rho = fma(-ca[q], sm.pub[par][u][2], rho);
+          rho = fma(-cc[q], sm.pub[par][u + 1][1], rho);
+        }
+        pl = fma(g0[q], rho, pl);
+        pr = fma(g1[q], rho, pr);
+      }
+    }
+    // reduce-scatter of the two sums: the first level leaves the Y_{w-1} partial
+    // on even lanes and the Y_w partial on odd lanes, then one sum per level
+    const bool odd = (L & 1) != 0;
+    double v = (odd ? pr : pl) + __shfl_xor_sync(kFull, odd ? pl : pr, 1);
+#pragma unroll
+    for (int s = 2; s < 32; s <<= 1) v += __shfl_xor_sync(kFull, v, s);
+    Yl = __shfl_sync(kFull, v, 0);
+    Yr = __shfl_sync(kFull, v, 1);
   }
-  x[M - 1] = X;
-  W[M - 1] = CN ? fma(rg.sigp, X, -W[M - 1]) : rg.sigp * X;
+  if constexpr (M == 2) {
+    // 6. scaled state update from the pre-formed parts
+    W[0] = fma(rg.e0, Yl, fma(rg.f0, Yr, K0));
+    W[1] = fma(rg.g1, Yl, fma(rg.h1, Yr, K1));
+  } else {
+    const double X = (L == 31) ? Yr : fma(rg.rc, Yr, fma(rg.ra, Yl, Xt));
+    double Xprev = __shfl_up_sync(kFull, X, 1);
+    if (L == 0) Xprev = Yl;
+    // 6. fixup of the inner rows and the scaled state update
+#pragma unroll
+    for (int k = 0; k <= M - 2; ++k) {
+      const double xv = fma(sm.rows[4][k][t], X, fma(sm.rows[3][k][t], Xprev, x[k]));
+      x[k] = xv;
+      W[k] = CN ? fma(sm.rows[2][k][t], xv, -W[k]) : sm.rows[2][k][t] * xv;
+    }
+    x[M - 1] = X;
+    W[M - 1] = CN ? fma(rg.sigp, X, -W[M - 1]) : rg.sigp * X;
+  }
 }
 
 // Read the Nx-vector V into the thread's rows and scale it into W.
@@ -545,11 +607,13 @@ __device__ __forceinline__ void load_state(const Inst& in, const double* __restr
   }
 }
 
-// Value of row k of this thread after a slice: V = W / sigma (CN) or x (IE).
+// Value of row k of this thread after a slice, V = W / sigma (the scaled state
+// of both propagators: W = 2V/delta-scaled for Crank-Nicolson, sigma x for
+// implicit Euler).
 template <int M, int NW, int C, bool CN>
 __device__ __forceinline__ double row_value(const double* __restrict__ cb, int k, const double (&W)[M],
                                             const double (&x)[M], double isigp) {
-  if (!CN) return x[k];
+  (void)x;
   const int g = cta_rank<C>() * NW * 32 + threadIdx.x;
   const double is = (k < M - 1) ? cb[coef_rows_off(5, k, g, M, C * NW * 32)] : isigp;
   return W[k] * is;
@@ -829,7 +893,7 @@ __global__ void __launch_bounds__(NW * 32, 1) sweep_kernel(SweepArgs a) {
       }
       run_slice<M, NW, C, false>(in, n, et, in.Mg, W, x, sm, rg, seq);
 #pragma unroll
-      for (int k = 0; k < M; ++k) Gv[k] = x[k];
+      for (int k = 0; k < M; ++k) Gv[k] = row_value<M, NW, C, false>(cb, k, W, x, rg.isigp);
       G0 = 0.0;
       GB = bc_right(in, n + 1);
     } else {
