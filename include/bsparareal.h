@@ -93,9 +93,11 @@ const char* bs_version(void);
  *   slices or more than 4096 rows, over a cluster of up to 16 CTAs that
  *   exchange interface values through distributed shared memory; the
  *   environment variable BSP_CLUSTER (1, 2, 4, 8, 16) overrides the cluster
- *   size, and BSP_PARTITION="M,NW,C" forces one compiled partition (M rows per
- *   thread, NW warps per CTA, C CTAs) on every instance (BS_EUNSUPPORTED if it
- *   is not compiled or holds fewer than Nx - 1 rows).
+ *   size, and BSP_PARTITION="M,NW,C[,S2]" forces one compiled partition (M rows
+ *   per thread, NW warps per CTA, C CTAs; S2 = 2 runs two slices of an instance
+ *   per CTA in the fine propagation, sharing its tables) on every instance
+ *   (BS_EUNSUPPORTED if it is not compiled or holds fewer than Nx - 1 rows);
+ *   BSP_S2=2 selects slice pairs wherever the chosen partition supports them.
  *   Synchronous.  *out receives the handle.  Errors: BS_EINVAL (argument),
  *   BS_EUNSUPPORTED (Nx above the largest grid this build keeps on chip),
  *   BS_ENOMEM, BS_ECUDA.
@@ -106,6 +108,7 @@ int bs_problem_init(const bs_params* p, int32_t n_instances, bs_problem** out);
 typedef struct {
   int32_t Nx;            /* grid size the candidate was timed for */
   int32_t M, NW, C;      /* rows per thread, warps per CTA, CTAs per grid */
+  int32_t S2;            /* slices per CTA in the fine propagation (1, or 2: slices in pairs) */
   float ms;              /* device time of one fine propagation of the tuning subset */
   int32_t chosen;        /* 1 for the partition kept for this grid size */
 } bs_tuning;
@@ -113,8 +116,9 @@ typedef struct {
 /*
  * bs_problem_init_tuned -- bs_problem_init with the partition of every grid
  * size picked by measurement instead of the built-in rule: for each distinct
- * Nx, every compiled partition (M rows per thread x NW warps x C CTAs) that
- * holds the grid with at most half of its rows padding is set up for a subset
+ * Nx, every compiled partition (M rows per thread x NW warps x C CTAs, and for
+ * clustered partitions with 16 or more rows per thread also two slices per
+ * CTA) that holds the grid with at most half of its rows padding is set up for a subset
  * of the problem's own instances of that size (enough for >= 4096 slices, fine
  * steps capped at 128) and timed on one fine propagation (CUDA events, best of
  * two after a warm-up); the fastest is kept.  Few slices favour clusters and
@@ -136,6 +140,11 @@ int bs_problem_info(const bs_problem* prob, int32_t* n_instances, int64_t* total
 
 /* Partition of instance i's grid: rows per thread M, warps per CTA NW, CTAs per grid C (cluster size). */
 int bs_problem_partition(const bs_problem* prob, int32_t i, int32_t* M, int32_t* NW, int32_t* C);
+
+/* Slices per CTA of instance i's fine propagation: 1, or 2 when two slices of the
+ * instance share each CTA and its coefficient tables (clustered partitions with
+ * 16 or more rows per thread and enough slices to keep every cluster busy). */
+int bs_problem_slices_per_cta(const bs_problem* prob, int32_t i, int32_t* s2);
 
 /*
  * bs_problem_device_status -- synchronises the device and reports the

@@ -51,7 +51,7 @@ class InstanceStats(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("Nx", ctypes.c_int32), ("M", ctypes.c_int32), ("NW", ctypes.c_int32), ("C", ctypes.c_int32),
-                ("ms", ctypes.c_float), ("chosen", ctypes.c_int32)]
+                ("S2", ctypes.c_int32), ("ms", ctypes.c_float), ("chosen", ctypes.c_int32)]
 
 
 def lib() -> ctypes.CDLL:
@@ -75,6 +75,7 @@ def lib() -> ctypes.CDLL:
         L.bs_problem_destroy.restype = None
         L.bs_problem_info.argtypes = [vp, P(i32), P(i64), P(i64)]
         L.bs_problem_partition.argtypes = [vp, i32, P(i32), P(i32), P(i32)]
+        L.bs_problem_slices_per_cta.argtypes = [vp, i32, P(i32)]
         L.bs_problem_device_status.argtypes = [vp, P(ctypes.c_int)]
         for f in (L.fine_propagate, L.coarse_propagate):
             f.argtypes = [vp, vp, vp, vp, vp]
@@ -158,7 +159,7 @@ class Problem:
             nrep = ctypes.c_int32()
             _check(lib().bs_problem_init_tuned(arr, len(self.instances), ctypes.byref(h), rep, cap, ctypes.byref(nrep)),
                    "bs_problem_init_tuned")
-            self.tuning = [dict(Nx=r.Nx, M=r.M, NW=r.NW, C=r.C, ms=r.ms, chosen=bool(r.chosen))
+            self.tuning = [dict(Nx=r.Nx, M=r.M, NW=r.NW, C=r.C, S2=r.S2, ms=r.ms, chosen=bool(r.chosen))
                            for r in rep[:min(nrep.value, cap)]]
         else:
             _check(lib().bs_problem_init(arr, len(self.instances), ctypes.byref(h)), "bs_problem_init")
@@ -191,6 +192,12 @@ class Problem:
         _check(lib().bs_problem_partition(self._h, i, ctypes.byref(M), ctypes.byref(NW), ctypes.byref(C)),
                "bs_problem_partition")
         return dict(M=M.value, NW=NW.value, C=C.value)
+
+    def slices_per_cta(self, i: int = 0) -> int:
+        """1, or 2 when instance i's fine propagation runs two slices per CTA."""
+        s = ctypes.c_int32()
+        _check(lib().bs_problem_slices_per_cta(self._h, i, ctypes.byref(s)), "bs_problem_slices_per_cta")
+        return s.value
 
     def device_status(self) -> int:
         """Synchronises and returns the problem's device status word (BS_OK or BS_TIMEOUT)."""
@@ -330,6 +337,12 @@ class PinnModel:
         _check(lib().pinn_get_weights(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
                "pinn_get_weights")
         return out
+
+    def slices_per_cta(self, i: int = 0) -> int:
+        """1, or 2 when instance i's fine propagation runs two slices per CTA."""
+        s = ctypes.c_int32()
+        _check(lib().bs_problem_slices_per_cta(self._h, i, ctypes.byref(s)), "bs_problem_slices_per_cta")
+        return s.value
 
     def device_status(self) -> int:
         """Synchronise and read the device status word (BS_OK or BS_TIMEOUT)."""

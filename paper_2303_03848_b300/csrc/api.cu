@@ -21,6 +21,7 @@ namespace {
 
 struct Class {
   int M = 0, NW = 0, C = 1, maxP = 0;
+  int s2 = 1;  // slices per CTA of the fine propagation (2: instances' slices in pairs)
   std::vector<int32_t> ids;
   int32_t* d_ids = nullptr;
 };
@@ -91,6 +92,7 @@ int cluster_target(const bs_params* p, int n) {
 
 struct Part {
   int M, NW, C;
+  int s2 = 1;
 };
 
 // Every compiled partition that holds an Nx-point grid with at most half of
@@ -102,7 +104,10 @@ std::vector<Part> candidate_partitions(int Nx) {
     for (int NW = 1; NW <= 4; NW *= 2)
       for (int M = 2; M <= 32; M *= 2) {
         const int64_t R = (int64_t)M * NW * 32 * C;
-        if (R >= rows && 2 * (R - rows) <= R && bsp::partition_supported(M, NW, C)) out.push_back(Part{M, NW, C});
+        if (R >= rows && 2 * (R - rows) <= R && bsp::partition_supported(M, NW, C)) {
+          out.push_back(Part{M, NW, C, 1});
+          if (bsp::s2_supported(M, NW, C)) out.push_back(Part{M, NW, C, 2});
+        }
       }
   return out;
 }
@@ -245,13 +250,14 @@ static int problem_create(const bs_params* p, int32_t n_instances, const Part* p
     prob->h_insts[i] = in;
     Class* cl = nullptr;
     for (auto& c : prob->classes)
-      if (c.M == in.M && c.NW == in.NW && c.C == in.C) cl = &c;
+      if (c.M == in.M && c.NW == in.NW && c.C == in.C && c.s2 == parts[i].s2) cl = &c;
     if (!cl) {
       prob->classes.push_back(Class{});
       cl = &prob->classes.back();
       cl->M = in.M;
       cl->NW = in.NW;
       cl->C = in.C;
+      cl->s2 = parts[i].s2;
     }
     cl->ids.push_back(i);
     if (q.P > cl->maxP) cl->maxP = q.P;
@@ -288,10 +294,12 @@ int bs_problem_init(const bs_params* p, int32_t n_instances, bs_problem** out) {
   if (validate(p, n_instances) != BS_OK) return BS_EINVAL;
   const int cl_target = cluster_target(p, n_instances);
   std::vector<Part> parts(n_instances);
-  Part forced{0, 0, 0};
-  if (const char* env = getenv("BSP_PARTITION")) {  // "M,NW,C" for every instance
-    if (sscanf(env, "%d,%d,%d", &forced.M, &forced.NW, &forced.C) != 3 ||
-        !bsp::partition_supported(forced.M, forced.NW, forced.C))
+  Part forced{0, 0, 0, 1};
+  if (const char* env = getenv("BSP_PARTITION")) {  // "M,NW,C" or "M,NW,C,S2" for every instance
+    const int got = sscanf(env, "%d,%d,%d,%d", &forced.M, &forced.NW, &forced.C, &forced.s2);
+    if (got < 3 || !bsp::partition_supported(forced.M, forced.NW, forced.C)) return BS_EUNSUPPORTED;
+    if (got < 4) forced.s2 = 1;
+    if (forced.s2 != 1 && !(forced.s2 == 2 && bsp::s2_supported(forced.M, forced.NW, forced.C)))
       return BS_EUNSUPPORTED;
   }
   for (int i = 0; i < n_instances; ++i) {
@@ -300,6 +308,25 @@ int bs_problem_init(const bs_params* p, int32_t n_instances, bs_problem** out) {
       parts[i] = forced;
     } else if (!choose_partition(p[i].Nx, cl_target, &parts[i].M, &parts[i].NW, &parts[i].C)) {
       return BS_EUNSUPPORTED;
+    }
+  }
+  if (forced.M == 0) {
+    // slice pairs where the class supports them and has slices enough to keep
+    // every cluster busy twice over (throughput rather than latency);
+    // BSP_S2 = 1 or 2 decides instead
+    int s2_env = 0;
+    if (const char* env = getenv("BSP_S2")) s2_env = atoi(env);
+    int dev = 0, nsm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    for (int i = 0; i < n_instances; ++i) {
+      Part& q = parts[i];
+      if (!bsp::s2_supported(q.M, q.NW, q.C)) continue;
+      int64_t slices = 0;
+      for (int j = 0; j < n_instances; ++j)
+        if (parts[j].M == q.M && parts[j].NW == q.NW && parts[j].C == q.C) slices += p[j].P;
+      const bool pairs = s2_env ? s2_env == 2 : slices >= 2 * (int64_t)(nsm / q.C);
+      q.s2 = pairs ? 2 : 1;
     }
   }
   return problem_create(p, n_instances, parts.data(), out);
@@ -382,7 +409,7 @@ int bs_problem_init_tuned(const bs_params* p, int32_t n_instances, bs_problem** 
         (void)cudaGetLastError();
         continue;
       }
-      if (nr < report_cap) report[nr] = bs_tuning{Nx, c.M, c.NW, c.C, ms, 0};
+      if (nr < report_cap) report[nr] = bs_tuning{Nx, c.M, c.NW, c.C, c.s2, ms, 0};
       ++nr;
       if (best_ms < 0.0f || ms < best_ms) {
         best_ms = ms;
@@ -391,7 +418,9 @@ int bs_problem_init_tuned(const bs_params* p, int32_t n_instances, bs_problem** 
     }
     if (best_ms < 0.0f) return BS_EUNSUPPORTED;
     for (int k = 0; k < (nr < report_cap ? nr : report_cap); ++k)
-      if (report[k].Nx == Nx) report[k].chosen = (report[k].M == best.M && report[k].NW == best.NW && report[k].C == best.C);
+      if (report[k].Nx == Nx)
+        report[k].chosen = (report[k].M == best.M && report[k].NW == best.NW && report[k].C == best.C &&
+                            report[k].S2 == best.s2);
     for (int i : group) {
       parts[i] = best;
       done[i] = 1;
@@ -415,6 +444,17 @@ int bs_problem_device_status(const bs_problem* prob, int* status) {
   cudaError_t e = cudaDeviceSynchronize();
   if (e == cudaSuccess) e = cudaMemcpy(status, prob->d_status, sizeof(int), cudaMemcpyDeviceToHost);
   return map_err(e);
+}
+
+int bs_problem_slices_per_cta(const bs_problem* prob, int32_t i, int32_t* s2) {
+  if (!prob || !s2 || i < 0 || i >= prob->n_inst) return BS_EINVAL;
+  *s2 = 1;
+  const Inst& in = prob->h_insts[i];
+  for (const auto& c : prob->classes)
+    if (c.M == in.M && c.NW == in.NW && c.C == in.C)
+      for (int32_t id : c.ids)
+        if (id == i) *s2 = c.s2;
+  return BS_OK;
 }
 
 int bs_problem_partition(const bs_problem* prob, int32_t i, int32_t* M, int32_t* NW, int32_t* C) {
@@ -447,7 +487,7 @@ static int propagate(bs_problem* prob, bool cn, const double* U_in, double* U_ou
     a.k_iter = -1;
     a.active = active;
     a.status = prob->d_status;
-    cudaError_t e = bsp::launch_prop(c.M, c.NW, c.C, cn, a, (int)c.ids.size(), c.maxP, s);
+    cudaError_t e = bsp::launch_prop(c.M, c.NW, c.C, c.s2, cn, a, (int)c.ids.size(), c.maxP, s);
     if (e != cudaSuccess) return map_err(e);
   }
   return BS_OK;
@@ -772,7 +812,7 @@ int parareal_solve(bs_problem* prob, int coarse_kind, const pinn_model* model, i
         a.out_state = 0;
         a.mode = bsp::PropArgs::kPlain;
       }
-      if ((e = bsp::launch_prop(c.M, c.NW, c.C, true, a, (int)c.ids.size(), c.maxP, s)) != cudaSuccess) return map_err(e);
+      if ((e = bsp::launch_prop(c.M, c.NW, c.C, c.s2, true, a, (int)c.ids.size(), c.maxP, s)) != cudaSuccess) return map_err(e);
     }
     // a4 + a5: serial coarse sweep with the correction
     if (coarse_kind != BS_COARSE_PINN) {
@@ -973,7 +1013,7 @@ extern "C" int parareal_solve_static(bs_problem* prob, int coarse_kind, const pi
         a.out_state = 0;
         a.mode = bsp::PropArgs::kPlain;
       }
-      if ((e = bsp::launch_prop(c.M, c.NW, c.C, true, a, (int)c.ids.size(), c.maxP, s)) != cudaSuccess) return map_err(e);
+      if ((e = bsp::launch_prop(c.M, c.NW, c.C, c.s2, true, a, (int)c.ids.size(), c.maxP, s)) != cudaSuccess) return map_err(e);
     }
     if (coarse_kind != BS_COARSE_PINN) {
       if ((e = sweep(k, cur, nxt)) != cudaSuccess) return map_err(e);

@@ -59,7 +59,11 @@ struct SweepArgs {
 bool partition_supported(int M, int NW, int C);
 cudaError_t launch_setup(const Inst* d_insts, const int32_t* d_ids, int n, int Ws, double* pool, double* exptab,
                          cudaStream_t s);
-cudaError_t launch_prop(int M, int NW, int C, bool cn, const PropArgs& a, int n_inst, int maxP, cudaStream_t s);
+// Persistent propagation launch; s2 = 2 runs two slices of an instance per CTA
+// (fine propagator, classes with s2_supported only).
+bool s2_supported(int M, int NW, int C);
+cudaError_t launch_prop(int M, int NW, int C, int s2, bool cn, const PropArgs& a, int n_inst, int maxP,
+                        cudaStream_t s);
 cudaError_t launch_serial(int M, int NW, int C, const SerialArgs& a, int n_inst, cudaStream_t s);
 cudaError_t launch_sweep(int M, int NW, int C, const SweepArgs& a, int n_inst, cudaStream_t s);
 cudaError_t launch_parareal_init(const Inst* d_insts, int n_inst, double* buf0, double* buf1, const double* gtab,

@@ -278,16 +278,28 @@ __global__ void __launch_bounds__(128) setup_cross_kernel(const Inst* insts, con
 // One time step of the partitioned solver.
 // ---------------------------------------------------------------------------
 
-template <int M, int NW, int C>
+// S2 slices share one CTA (and its tables): thread group g = threadIdx.x / T runs
+// its own slice of the same instance with its own exchange buffers.
+template <int M, int NW, int C, int S2 = 1>
 struct SolverSmem {
   static constexpr int T = NW * 32, Ws = C * NW;
-  double rows[5][M][T];     // lambda, mu, sigma, alpha, beta of this CTA's threads
+  double rows[5][M][T];     // lambda, mu, sigma, alpha, beta of the group's threads
   double G2[NW][2][Ws];     // rows w-1 and w of the cross-warp inverse, per local warp
   double nu31[Ws], A31[Ws], C31[Ws];
-  alignas(16) double pub[2][Ws][4];  // [step parity][global warp][x0, X0, X30, R31], written by every CTA
-  double red[2][NW];
-  alignas(8) unsigned long long bar[2];  // C > 1: arrival of a step's values, per parity buffer
+  alignas(16) double pub[S2][2][Ws][4];  // [group][step parity][global warp][x0, X0, X30, R31]
+  double red[S2][2][NW];
+  alignas(8) unsigned long long bar[S2][2];  // C > 1: arrival of a step's values, per group and parity
 };
+
+// Thread index within its slice group and the group index.
+template <int NW>
+__device__ __forceinline__ int lthread() {
+  return (int)threadIdx.x % (NW * 32);
+}
+template <int NW>
+__device__ __forceinline__ int lgroup() {
+  return (int)threadIdx.x / (NW * 32);
+}
 
 struct SolverRegs {
   double kap, nu, sigp, isigp;
@@ -349,11 +361,11 @@ __device__ __forceinline__ int cta_rank() {
   }
 }
 
-template <int M, int NW, int C>
-__device__ __forceinline__ void load_solver(const double* __restrict__ cb, SolverSmem<M, NW, C>& sm,
+template <int M, int NW, int C, int S2 = 1>
+__device__ __forceinline__ void load_solver(const double* __restrict__ cb, SolverSmem<M, NW, C, S2>& sm,
                                             SolverRegs& rg) {
   constexpr int T = NW * 32, Ws = C * NW, GT = C * T;
-  const int t = threadIdx.x, c = cta_rank<C>();
+  const int t = lthread<NW>(), c = cta_rank<C>();  // both groups write the same table entries
   const int g = c * T + t;
   for (int q = 0; q < 5; ++q)
     for (int k = 0; k < M; ++k) sm.rows[q][k][t] = cb[coef_rows_off(q, k, g, M, GT)];
@@ -405,25 +417,29 @@ __device__ __forceinline__ void load_solver(const double* __restrict__ cb, Solve
 
 // The exchange barriers, once per launch (a cluster barrier follows before the
 // first step; the step counter then runs on across slices and tasks).
-template <int M, int NW, int C>
-__device__ __forceinline__ void exchange_init(SolverSmem<M, NW, C>& sm, SolverRegs& rg) {
+template <int M, int NW, int C, int S2 = 1>
+__device__ __forceinline__ void exchange_init(SolverSmem<M, NW, C, S2>& sm, SolverRegs& rg) {
   rg.fail = 0;
   if (C > 1 && threadIdx.x == 0) {
-    mbar_init(smem_addr(&sm.bar[0]));
-    mbar_init(smem_addr(&sm.bar[1]));
+    for (int g = 0; g < S2; ++g) {
+      mbar_init(smem_addr(&sm.bar[g][0]));
+      mbar_init(smem_addr(&sm.bar[g][1]));
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
 }
 
 // A CTA whose wait gave up records BS_TIMEOUT and waits (again bounded) for the
 // values of the last two steps that may still be arriving in its buffers.
-template <int M, int NW, int C>
-__device__ __forceinline__ void exchange_drain(SolverSmem<M, NW, C>& sm, const SolverRegs& rg, int seq, int* status) {
+template <int M, int NW, int C, int S2 = 1>
+__device__ __forceinline__ void exchange_drain(SolverSmem<M, NW, C, S2>& sm, const SolverRegs& rg, int seq,
+                                               int* status) {
   if constexpr (C > 1) {
     if (!rg.fail) return;
+    const int gi = lgroup<NW>();
     for (int q = seq - 2; q < seq; ++q)
-      if (q >= 0) (void)mbar_wait(smem_addr(&sm.bar[q & 1]), (uint32_t)(q >> 1) & 1u);
-    if (status != nullptr && threadIdx.x == 0) atomicExch(status, 6);  // BS_TIMEOUT
+      if (q >= 0) (void)mbar_wait(smem_addr(&sm.bar[gi][q & 1]), (uint32_t)(q >> 1) & 1u);
+    if (status != nullptr && lthread<NW>() == 0) atomicExch(status, 6);  // BS_TIMEOUT
   }
 }
 
@@ -434,12 +450,12 @@ __device__ __forceinline__ void exchange_drain(SolverSmem<M, NW, C>& sm, const S
 // x receives the solution of the step (Z for Crank-Nicolson, V^{m+1} for
 // implicit Euler) on the thread's rows; W is advanced to the next scaled state.
 // Zb is the Dirichlet value of the step (used by the grid's last thread).
-template <int M, int NW, int C>
-__device__ __forceinline__ double step_reduce(const double (&W)[M], double (&x)[M], SolverSmem<M, NW, C>& sm,
+template <int M, int NW, int C, int S2 = 1>
+__device__ __forceinline__ double step_reduce(const double (&W)[M], double (&x)[M], SolverSmem<M, NW, C, S2>& sm,
                                               const SolverRegs& rg, double Zb, int seq) {
   const int par = seq & 1;
   constexpr int Ws = C * NW;
-  const int t = threadIdx.x, L = t & 31, wl = t >> 5;
+  const int t = lthread<NW>(), L = t & 31, wl = t >> 5, gi = lgroup<NW>();
   const int c = cta_rank<C>();
   const int w = c * NW + wl;
   // 1. local forward and backward sweeps over the inner rows (zero interfaces)
@@ -471,18 +487,18 @@ __device__ __forceinline__ double step_reduce(const double (&W)[M], double (&x)[
   const double p3 = __shfl_sync(kFull, R, 31);
   if constexpr (C == 1) {
     if (L == 0) {
-      sm.pub[par][w][0] = p0;
-      sm.pub[par][w][1] = p1;
-      sm.pub[par][w][2] = p2;
-      sm.pub[par][w][3] = p3;
+      sm.pub[gi][par][w][0] = p0;
+      sm.pub[gi][par][w][1] = p1;
+      sm.pub[gi][par][w][2] = p2;
+      sm.pub[gi][par][w][3] = p3;
     }
   } else {
     // this CTA expects 32 bytes from every warp of the grid; lane L sends this
     // warp's 32 bytes to CTA L
-    if (t == 0) mbar_expect(smem_addr(&sm.bar[par]), (uint32_t)Ws * 32u);
+    if (t == 0) mbar_expect(smem_addr(&sm.bar[gi][par]), (uint32_t)Ws * 32u);
     if (L < C) {
-      const uint32_t slot = cluster_addr(smem_addr(&sm.pub[par][w][0]), L);
-      const uint32_t rbar = cluster_addr(smem_addr(&sm.bar[par]), L);
+      const uint32_t slot = cluster_addr(smem_addr(&sm.pub[gi][par][w][0]), L);
+      const uint32_t rbar = cluster_addr(smem_addr(&sm.bar[gi][par]), L);
       st_async2(slot, p0, p1, rbar);
       st_async2(slot + 16u, p2, p3, rbar);
     }
@@ -490,14 +506,15 @@ __device__ __forceinline__ double step_reduce(const double (&W)[M], double (&x)[
   return Xt;
 }
 
-template <int M, int NW, int C, bool CN>
-__device__ __forceinline__ void step_finish(double (&W)[M], double (&x)[M], SolverSmem<M, NW, C>& sm,
+template <int M, int NW, int C, bool CN, int S2 = 1>
+__device__ __forceinline__ void step_finish(double (&W)[M], double (&x)[M], SolverSmem<M, NW, C, S2>& sm,
                                             SolverRegs& rg, double Xt, int seq) {
   const int par = seq & 1;
   constexpr int Ws = C * NW;
   constexpr bool kHalves = Ws <= 16;  // lanes 0-15 form Y_{w-1}, lanes 16-31 Y_w
   constexpr int NU = kHalves ? 1 : (Ws + 31) / 32;
-  const int t = threadIdx.x, L = t & 31, wl = t >> 5;
+  const int t = lthread<NW>(), L = t & 31, wl = t >> 5, gi = lgroup<NW>();
+  auto& pub = sm.pub[gi];
   // constants of the cross-warp solve for the lanes' warps u, read while the
   // other CTAs' values arrive
   double cnu[NU], ca[NU], cc[NU], g0[NU], g1[NU];
@@ -524,7 +541,7 @@ __device__ __forceinline__ void step_finish(double (&W)[M], double (&x)[M], Solv
   if constexpr (C == 1) {
     __syncthreads();
   } else {
-    if (!rg.fail && !mbar_wait(smem_addr(&sm.bar[par]), (uint32_t)(seq >> 1) & 1u)) rg.fail = 1;
+    if (!rg.fail && !mbar_wait(smem_addr(&sm.bar[gi][par]), (uint32_t)(seq >> 1) & 1u)) rg.fail = 1;
   }
   // 5. cross-warp unknowns: rho_u by lane u, then Y_{w-1} and Y_w as dot
   //    products with rows of the precomputed inverse
@@ -535,11 +552,11 @@ __device__ __forceinline__ void step_finish(double (&W)[M], double (&x)[M], Solv
     if (u < Ws) {
       double rho;
       if (u == Ws - 1) {
-        rho = sm.pub[par][u][3];
+        rho = pub[par][u][3];
       } else {
-        rho = fma(-cnu[0], sm.pub[par][u + 1][0], sm.pub[par][u][3]);
-        rho = fma(-ca[0], sm.pub[par][u][2], rho);
-        rho = fma(-cc[0], sm.pub[par][u + 1][1], rho);
+        rho = fma(-cnu[0], pub[par][u + 1][0], pub[par][u][3]);
+        rho = fma(-ca[0], pub[par][u][2], rho);
+        rho = fma(-cc[0], pub[par][u + 1][1], rho);
       }
       v = g0[0] * rho;
     }
@@ -555,11 +572,11 @@ __device__ __forceinline__ void step_finish(double (&W)[M], double (&x)[M], Solv
       if (u < Ws) {
         double rho;
         if (u == Ws - 1) {
-          rho = sm.pub[par][u][3];
+          rho = pub[par][u][3];
         } else {
-          rho = fma(-cnu[q], sm.pub[par][u + 1][0], sm.pub[par][u][3]);
-          rho = fma(-ca[q], sm.pub[par][u][2], rho);
-          rho = fma(-cc[q], sm.pub[par][u + 1][1], rho);
+          rho = fma(-cnu[q], pub[par][u + 1][0], pub[par][u][3]);
+          rho = fma(-ca[q], pub[par][u][2], rho);
+          rho = fma(-cc[q], pub[par][u + 1][1], rho);
         }
         pl = fma(g0[q], rho, pl);
         pr = fma(g1[q], rho, pr);
@@ -595,10 +612,10 @@ __device__ __forceinline__ void step_finish(double (&W)[M], double (&x)[M], Solv
 }
 
 // Read the Nx-vector V into the thread's rows and scale it into W.
-template <int M, int NW, int C>
+template <int M, int NW, int C, int S2 = 1>
 __device__ __forceinline__ void load_state(const Inst& in, const double* __restrict__ V,
-                                           const SolverSmem<M, NW, C>& sm, const SolverRegs& rg, double (&W)[M]) {
-  const int t = threadIdx.x, g = cta_rank<C>() * NW * 32 + t;
+                                           const SolverSmem<M, NW, C, S2>& sm, const SolverRegs& rg, double (&W)[M]) {
+  const int t = lthread<NW>(), g = cta_rank<C>() * NW * 32 + t;
 #pragma unroll
   for (int k = 0; k < M; ++k) {
     const int j = g * M + k - in.Np + 1;
@@ -614,7 +631,7 @@ template <int M, int NW, int C, bool CN>
 __device__ __forceinline__ double row_value(const double* __restrict__ cb, int k, const double (&W)[M],
                                             const double (&x)[M], double isigp) {
   (void)x;
-  const int g = cta_rank<C>() * NW * 32 + threadIdx.x;
+  const int g = cta_rank<C>() * NW * 32 + lthread<NW>();
   const double is = (k < M - 1) ? cb[coef_rows_off(5, k, g, M, C * NW * 32)] : isigp;
   return W[k] * is;
 }
@@ -622,13 +639,13 @@ __device__ __forceinline__ double row_value(const double* __restrict__ cb, int k
 // Run `steps` steps of the propagator on slice n starting from scaled state W.
 // The right Dirichlet value of the next step is formed while the barrier
 // completes, from exp(-r m dtau) read one step ahead.
-template <int M, int NW, int C, bool CN>
+template <int M, int NW, int C, bool CN, int S2 = 1>
 __device__ __forceinline__ void run_slice(const Inst& in, int n, const double* __restrict__ et, int steps,
-                                          double (&W)[M], double (&x)[M], SolverSmem<M, NW, C>& sm,
+                                          double (&W)[M], double (&x)[M], SolverSmem<M, NW, C, S2>& sm,
                                           SolverRegs& rg, int& seq) {
   const double tau_n = in.T * (double)n / (double)in.P;
   const double KeN = in.K * exp(-in.r * tau_n);
-  const bool last_warp = cta_rank<C>() == C - 1 && (threadIdx.x >> 5) == NW - 1;
+  const bool last_warp = cta_rank<C>() == C - 1 && (lthread<NW>() >> 5) == NW - 1;
   double Bold = in.Smax - KeN;  // exp(0) = 1
   double Zb = 0.0, e_next = 0.0;
   if (last_warp) {
@@ -638,22 +655,23 @@ __device__ __forceinline__ void run_slice(const Inst& in, int n, const double* _
     if (steps >= 2) e_next = __ldg(et + 2);
   }
   for (int m = 0; m < steps; ++m) {
-    const double Xt = step_reduce<M, NW, C>(W, x, sm, rg, Zb, seq);
+    const double Xt = step_reduce<M, NW, C, S2>(W, x, sm, rg, Zb, seq);
     if (last_warp) {  // Dirichlet value of step m + 1 (unused after the last step)
       const double Bnew = fma(-KeN, e_next, in.Smax);
       Zb = CN ? Bold + Bnew : Bnew;
       Bold = Bnew;
       if (m + 3 <= steps) e_next = __ldg(et + m + 3);
     }
-    step_finish<M, NW, C, CN>(W, x, sm, rg, Xt, seq);
+    step_finish<M, NW, C, CN, S2>(W, x, sm, rg, Xt, seq);
     ++seq;
   }
 }
 
-// Block-wide sum of two doubles, result valid on thread 0.
+// Sum of two doubles over a slice group's NW warps, result valid on the
+// group's thread 0.  Contains CTA-wide barriers: every thread of the CTA calls it.
 template <int NW>
 __device__ __forceinline__ void block_sum2(double& a, double& b, double (*red)[NW]) {
-  const int t = threadIdx.x, L = t & 31, w = t >> 5;
+  const int t = lthread<NW>(), L = t & 31, w = t >> 5;
 #pragma unroll
   for (int s = 16; s >= 1; s >>= 1) {
     a += __shfl_down_sync(kFull, a, s);
@@ -682,93 +700,110 @@ __device__ __forceinline__ double bc_right(const Inst& in, int n) {
 // One cluster of C CTAs per (instance, slice): blockIdx.x = slice * C + rank.
 // ---------------------------------------------------------------------------
 
-template <int M, int NW, int C, bool CN>
-__global__ void __launch_bounds__(NW * 32, 1) prop_kernel(PropArgs a) {
+template <int M, int NW, int C, bool CN, int S2>
+__global__ void __launch_bounds__(S2 * NW * 32, 1) prop_kernel(PropArgs a) {
+  static_assert(S2 == 1 || C > 1, "slice pairs exchange through mbarriers only (no block barrier inside a step)");
   constexpr int T = NW * 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  SolverSmem<M, NW, C>& sm = *reinterpret_cast<SolverSmem<M, NW, C>*>(smem_raw);
-  const int t = threadIdx.x, c = cta_rank<C>();
+  SolverSmem<M, NW, C, S2>& sm = *reinterpret_cast<SolverSmem<M, NW, C, S2>*>(smem_raw);
+  const int t = lthread<NW>(), gi = lgroup<NW>(), c = cta_rank<C>();
   SolverRegs rg;
-  exchange_init<M, NW, C>(sm, rg);
+  exchange_init<M, NW, C, S2>(sm, rg);
   int seq = 0;
-  // persistent: cluster q walks the (instance, slice) tasks q, q + clusters, ...;
-  // every skip below is uniform over the cluster (same task)
-  const int64_t n_cl = gridDim.x / C, ntask = (int64_t)a.n_inst * a.maxP;
+  // persistent: cluster q walks the task groups q, q + clusters, ...; a task
+  // group is S2 consecutive slices of one instance (group gi takes slice
+  // S2 j + gi).  Skipping a whole group is uniform over the cluster; a group
+  // whose own slice is inactive still takes every block and cluster barrier.
+  const int ngrp = (a.maxP + S2 - 1) / S2;
+  const int64_t n_cl = gridDim.x / C, ntask = (int64_t)a.n_inst * ngrp;
   for (int64_t task = blockIdx.x / C; task < ntask; task += n_cl) {
-    const int idx = a.ids[task / a.maxP];
-    const int n = (int)(task % a.maxP);
+    const int idx = a.ids[task / ngrp];
+    const int n0 = (int)(task % ngrp) * S2;
     const Inst in = a.insts[idx];
-    if (n >= in.P) continue;
-    if (a.k_iter >= 0 && n < a.k_iter) continue;
-    if (a.ctrl != nullptr && a.ctrl[idx].done) continue;
-    if (a.active != nullptr && !a.active[in.task_off + n]) continue;
+    auto live = [&](int n) {
+      if (n >= in.P) return false;
+      if (a.k_iter >= 0 && n < a.k_iter) return false;
+      if (a.ctrl != nullptr && a.ctrl[idx].done) return false;
+      if (a.active != nullptr && !a.active[in.task_off + n]) return false;
+      return true;
+    };
+    bool any = false;
+#pragma unroll
+    for (int g = 0; g < S2; ++g) any = any || live(n0 + g);
+    if (!any) continue;
+    const int n = n0 + gi;
+    const bool mine = live(n);
     const double* cb = a.pool + (CN ? in.coef_cn : in.coef_ie);
     const double* et = a.exptab + (CN ? in.exp_cn : in.exp_ie);
     const int steps = CN ? in.Mf : in.Mg;
     __syncthreads();  // the previous task is done with the shared tables
-    load_solver<M, NW, C>(cb, sm, rg);
+    load_solver<M, NW, C, S2>(cb, sm, rg);
     if constexpr (C > 1) cg::this_cluster().sync();  // every CTA of the grid holds its tables
 
     const int Nx = in.Nx;
-    const double* Vin = a.in + (a.in_state ? in.state_off : in.slice_off) + (int64_t)n * Nx;
-    double W[M], x[M];
-    load_state<M, NW, C>(in, Vin, sm, rg, W);
-#pragma unroll
-    for (int k = 0; k < M; ++k) x[k] = 0.0;
-    run_slice<M, NW, C, CN>(in, n, et, steps, W, x, sm, rg, seq);
-
-    const bool first_thread = c == 0 && t == 0;
-    const bool last_thread = c == C - 1 && t == T - 1;
     const int g = c * T + t;
-    const double Bend = bc_right(in, n + 1);
-    double* Vout = a.out + (a.out_state ? in.state_off + (int64_t)(n + 1) * Nx : in.slice_off + (int64_t)n * Nx);
-    if (a.mode == PropArgs::kPlain) {
+    double num = 0.0, den = 0.0;
+    if (mine) {
+      const double* Vin = a.in + (a.in_state ? in.state_off : in.slice_off) + (int64_t)n * Nx;
+      double W[M], x[M];
+      load_state<M, NW, C, S2>(in, Vin, sm, rg, W);
 #pragma unroll
-      for (int k = 0; k < M; ++k) {
-        const int j = g * M + k - in.Np + 1;
-        if (j >= 1 && j <= Nx - 2) Vout[j] = row_value<M, NW, C, CN>(cb, k, W, x, rg.isigp);
-      }
-      if (first_thread) Vout[0] = 0.0;
-      if (last_thread) Vout[Nx - 1] = Bend;
-    } else {
-      // kPinnFused: U^{k+1}_{n+1} = F(U^k_n) + (G_new - G_old) with G = the network
-      // table at tau_{n+1} for both terms (Eq. 7); increment-norm partial sums.
-      const double* gg = a.gtab + in.state_off + (int64_t)(n + 1) * Nx;
-      const double* Uold = a.uold + in.state_off + (int64_t)(n + 1) * Nx;
-      double num = 0.0, den = 0.0;
+      for (int k = 0; k < M; ++k) x[k] = 0.0;
+      run_slice<M, NW, C, CN, S2>(in, n, et, steps, W, x, sm, rg, seq);
+
+      const bool first_thread = c == 0 && t == 0;
+      const bool last_thread = c == C - 1 && t == T - 1;
+      const double Bend = bc_right(in, n + 1);
+      double* Vout = a.out + (a.out_state ? in.state_off + (int64_t)(n + 1) * Nx : in.slice_off + (int64_t)n * Nx);
+      if (a.mode == PropArgs::kPlain) {
 #pragma unroll
-      for (int k = 0; k < M; ++k) {
-        const int j = g * M + k - in.Np + 1;
-        if (j >= 1 && j <= Nx - 2) {
-          const double f = row_value<M, NW, C, CN>(cb, k, W, x, rg.isigp);
-          const double v = f + (gg[j] - gg[j]);
-          Vout[j] = v;
-          const double d = v - Uold[j];
+        for (int k = 0; k < M; ++k) {
+          const int j = g * M + k - in.Np + 1;
+          if (j >= 1 && j <= Nx - 2) Vout[j] = row_value<M, NW, C, CN>(cb, k, W, x, rg.isigp);
+        }
+        if (first_thread) Vout[0] = 0.0;
+        if (last_thread) Vout[Nx - 1] = Bend;
+      } else {
+        // kPinnFused: U^{k+1}_{n+1} = F(U^k_n) + (G_new - G_old) with G = the network
+        // table at tau_{n+1} for both terms (Eq. 7); increment-norm partial sums.
+        const double* gg = a.gtab + in.state_off + (int64_t)(n + 1) * Nx;
+        const double* Uold = a.uold + in.state_off + (int64_t)(n + 1) * Nx;
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+          const int j = g * M + k - in.Np + 1;
+          if (j >= 1 && j <= Nx - 2) {
+            const double f = row_value<M, NW, C, CN>(cb, k, W, x, rg.isigp);
+            const double v = f + (gg[j] - gg[j]);
+            Vout[j] = v;
+            const double d = v - Uold[j];
+            num = fma(d, d, num);
+            den = fma(v, v, den);
+          }
+        }
+        if (first_thread) {
+          const double v = 0.0 + (gg[0] - gg[0]);
+          Vout[0] = v;
+          const double d = v - Uold[0];
           num = fma(d, d, num);
           den = fma(v, v, den);
         }
+        if (last_thread) {
+          const double v = Bend + (gg[Nx - 1] - gg[Nx - 1]);
+          Vout[Nx - 1] = v;
+          const double d = v - Uold[Nx - 1];
+          num = fma(d, d, num);
+          den = fma(v, v, den);
+        }
+        // the slice that becomes exact this iteration keeps its start value
+        if (a.k_iter >= 0 && n == a.k_iter) {
+          double* Fz = a.out + in.state_off + (int64_t)n * Nx;
+          for (int j = g; j < Nx; j += C * T) Fz[j] = Vin[j];
+        }
       }
-      if (first_thread) {
-        const double v = 0.0 + (gg[0] - gg[0]);
-        Vout[0] = v;
-        const double d = v - Uold[0];
-        num = fma(d, d, num);
-        den = fma(v, v, den);
-      }
-      if (last_thread) {
-        const double v = Bend + (gg[Nx - 1] - gg[Nx - 1]);
-        Vout[Nx - 1] = v;
-        const double d = v - Uold[Nx - 1];
-        num = fma(d, d, num);
-        den = fma(v, v, den);
-      }
-      // the slice that becomes exact this iteration keeps its start value
-      if (a.k_iter >= 0 && n == a.k_iter) {
-        double* Fz = a.out + in.state_off + (int64_t)n * Nx;
-        for (int j = g; j < Nx; j += C * T) Fz[j] = Vin[j];
-      }
-      block_sum2<NW>(num, den, sm.red);
-      if (t == 0) {
+    }
+    if (a.mode == PropArgs::kPinnFused) {
+      block_sum2<NW>(num, den, sm.red[gi]);  // every thread of the CTA
+      if (mine && t == 0) {
         const int64_t slot = (in.norm_off + (int64_t)(n + 1) * C + c) * 2;
         a.normbuf[slot + 0] = num;
         a.normbuf[slot + 1] = den;
@@ -776,7 +811,7 @@ __global__ void __launch_bounds__(NW * 32, 1) prop_kernel(PropArgs a) {
     }
     if constexpr (C > 1) cg::this_cluster().sync();  // no CTA moves on while its tables may be read
   }
-  exchange_drain<M, NW, C>(sm, rg, seq, a.status);
+  exchange_drain<M, NW, C, S2>(sm, rg, seq, a.status);
   if constexpr (C > 1) cg::this_cluster().sync();  // no CTA leaves while its shared memory may be written
 }
 
@@ -950,7 +985,7 @@ __global__ void __launch_bounds__(NW * 32, 1) sweep_kernel(SweepArgs a) {
       }
     }
     if (!init) {
-      block_sum2<NW>(num, den, sm.red);
+      block_sum2<NW>(num, den, sm.red[0]);
       if (t == 0) {
         const int64_t slot = (in.norm_off + (int64_t)(n + 1) * C + c) * 2;
         a.normbuf[slot + 0] = num;
@@ -1138,12 +1173,12 @@ static cudaError_t launch_cluster(Kern kernel, dim3 grid, int threads, int C, in
 // task when there are fewer tasks), each walking its share of the tasks.
 template <typename Kern>
 static cudaError_t launch_persistent(Kern kernel, int threads, int C, int smem, cudaStream_t s, PropArgs a,
-                                     int n_inst, int maxP) {
+                                     int n_inst, int maxP, int s2) {
   cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   if (C > 8 && (e = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess)
     return e;
-  const int64_t ntask = (int64_t)n_inst * maxP;
+  const int64_t ntask = (int64_t)n_inst * ((maxP + s2 - 1) / s2);
   cudaLaunchConfig_t cfg = {};
   cfg.blockDim = dim3(threads, 1, 1);
   cfg.dynamicSmemBytes = smem;
@@ -1166,13 +1201,37 @@ static cudaError_t launch_persistent(Kern kernel, int threads, int C, int smem, 
   return cudaLaunchKernelEx(&cfg, kernel, a);
 }
 
-cudaError_t launch_prop(int M, int NW, int C, bool cn, const PropArgs& a, int n_inst, int maxP, cudaStream_t s) {
+// Classes whose fine propagation can also run two slices per CTA (clusters,
+// 16 or more rows per thread: the tables are large and one CTA fills an SM).
+#define BSP_FOR_EACH_S2_CLASS(X) \
+  X(16, 4, 2) X(32, 4, 2) X(16, 4, 4) X(32, 4, 4) X(16, 4, 8) X(32, 4, 8) X(16, 4, 16) X(32, 4, 16)
+
+bool s2_supported(int M, int NW, int C) {
+#define X(MM, WW, CC) \
+  if (M == MM && NW == WW && C == CC) return true;
+  BSP_FOR_EACH_S2_CLASS(X)
+#undef X
+  return false;
+}
+
+cudaError_t launch_prop(int M, int NW, int C, int s2, bool cn, const PropArgs& a, int n_inst, int maxP,
+                        cudaStream_t s) {
   if (n_inst <= 0) return cudaSuccess;
+  if (s2 == 2 && cn) {
+#define X(MM, WW, CC)                                                                                          \
+  if (M == MM && NW == WW && C == CC) {                                                                        \
+    const int sz = (int)sizeof(SolverSmem<MM, WW, CC, 2>);                                                     \
+    return launch_persistent(prop_kernel<MM, WW, CC, true, 2>, 2 * WW * 32, CC, sz, s, a, n_inst, maxP, 2);    \
+  }
+    BSP_FOR_EACH_S2_CLASS(X)
+#undef X
+    return cudaErrorInvalidValue;
+  }
 #define X(MM, WW, CC)                                                                                            \
   if (M == MM && NW == WW && C == CC) {                                                                          \
     const int sz = (int)sizeof(SolverSmem<MM, WW, CC>);                                                          \
-    return cn ? launch_persistent(prop_kernel<MM, WW, CC, true>, WW * 32, CC, sz, s, a, n_inst, maxP)            \
-              : launch_persistent(prop_kernel<MM, WW, CC, false>, WW * 32, CC, sz, s, a, n_inst, maxP);           \
+    return cn ? launch_persistent(prop_kernel<MM, WW, CC, true, 1>, WW * 32, CC, sz, s, a, n_inst, maxP, 1)      \
+              : launch_persistent(prop_kernel<MM, WW, CC, false, 1>, WW * 32, CC, sz, s, a, n_inst, maxP, 1);     \
   }
   BSP_FOR_EACH_CLASS(X)
 #undef X

@@ -58,6 +58,7 @@ def test_null_arguments_rejected(L):
     assert L.parareal_solve(None, 0, None, 0, 1e-6, 4, None, None, None, None) == B.BS_EINVAL
     assert L.pinn_eval(None, 0, None, 1, None, None, None) == B.BS_EINVAL
     assert L.bs_problem_device_status(None, None) == B.BS_EINVAL
+    assert L.bs_problem_slices_per_cta(None, 0, None) == B.BS_EINVAL
     assert L.bs_problem_init_tuned(None, 1, ctypes.byref(h), None, 0, None) == B.BS_EINVAL
     assert L.bs_problem_init_tuned(ctypes.byref(p), 1, ctypes.byref(h), None, 4, None) == B.BS_EINVAL
     L.bs_problem_destroy(None)
@@ -81,7 +82,7 @@ def test_struct_layout_matches_header(L):
     # bs_params: 5 doubles then 4 int32 = 56 bytes; bs_instance_stats: 16 bytes
     assert ctypes.sizeof(B.BsParams) == 56
     assert ctypes.sizeof(B.InstanceStats) == 16
-    assert ctypes.sizeof(B.Tuning) == 24
+    assert ctypes.sizeof(B.Tuning) == 28
     assert B.BsParams.Nx.offset == 40
 
 

@@ -125,3 +125,63 @@ def test_tuned_parareal_matches_oracle(B, orc):
     j = p["Nx"] - 2
     kappa = 1.0 + 0.5 * p["T"] / steps * (2.0 * p["sigma"] ** 2 * j * j + p["r"] * j + p["r"])
     _close(U.cpu().numpy(), Ur.ravel(), max(RTOL, 2.0 * kappa * 2.0 ** -53 * steps))
+
+
+# two slices per CTA (slice pairs sharing the coefficient tables): same per-slice
+# arithmetic as one slice per CTA, so the results agree bit for bit; odd slice
+# counts leave one group of the last pair idle
+PAIR_CASES = [((16, 4, 2), 4000), ((32, 4, 2), 6000), ((16, 4, 4), 6000), ((32, 4, 4), 12000),
+              ((16, 4, 8), 12000), ((32, 4, 8), 30000), ((16, 4, 16), 30000), ((32, 4, 16), 65536)]
+
+
+@pytest.mark.parametrize("shape,Nx", PAIR_CASES)
+def test_slice_pairs_equal_single_slices_and_match_oracle(B, orc, monkeypatch, shape, Nx):
+    m, nw, c = shape
+    p = dict(K=1.0, sigma=0.3, r=0.03, T=0.5, Smax=8.0, Nx=Nx, P=3, fine_steps=4, coarse_steps=1)
+    parts = [_slices(orc, p, 7 + Nx)]
+    Uin = torch.tensor(parts[0].ravel(), device="cuda")
+    out = {}
+    for s2 in (1, 2):
+        monkeypatch.setenv("BSP_PARTITION", f"{m},{nw},{c},{s2}")
+        prob = B.Problem(p)
+        out[s2] = prob.fine_propagate(Uin)
+        assert prob.device_status() == B.BS_OK
+    assert torch.equal(out[1], out[2])
+    F = out[2].cpu().numpy().reshape(p["P"], Nx)
+    op = orc.params(**p)
+    for n in range(p["P"]):
+        _close(F[n], orc.fine(op, n, parts[0][n]), _tol(p, "fine"))
+
+
+@pytest.mark.parametrize("P", [4, 5])
+def test_slice_pairs_parareal_network_and_ie_bitwise(B, monkeypatch, P):
+    p = dict(K=1.0, sigma=0.3, r=0.03, T=0.5, Smax=8.0, Nx=4000, P=P, fine_steps=8, coarse_steps=1)
+    net = B.PinnModel([2, 32, 32, 1], [0.0, 0.0], [8.0, 0.5], seed=2)
+    res = {}
+    for s2 in (1, 2):
+        monkeypatch.setenv("BSP_PARTITION", f"16,4,2,{s2}")
+        prob = B.Problem(p)
+        Un, nn, sn, rn = prob.parareal_solve(B.COARSE_PINN, model=net, prec=B.FP64, tol=0.0)
+        Ui, ni, si, ri = prob.parareal_solve(B.COARSE_IE, tol=0.0)
+        assert rn == B.BS_OK and ri == B.BS_OK and prob.device_status() == B.BS_OK
+        res[s2] = (Un, nn, Ui, ni, prob.serial_fine())
+    for a, b in zip(res[1], res[2]):
+        if isinstance(a, torch.Tensor):
+            assert torch.equal(a, b)
+        else:
+            np.testing.assert_array_equal(a, b)
+    assert torch.equal(res[2][0], res[2][4])  # k = P reproduces serial fine
+
+
+def test_slice_pair_rule_follows_the_slice_count(B, monkeypatch):
+    # a 30000-point grid takes 8-CTA clusters (32 rows per thread); pairs once
+    # the slices can keep every cluster busy twice over, and on request
+    monkeypatch.delenv("BSP_PARTITION", raising=False)
+    base = dict(K=1.0, sigma=0.3, r=0.03, T=0.5, Smax=8.0, Nx=30000, fine_steps=2, coarse_steps=1)
+    few, many = B.Problem(dict(base, P=8)), B.Problem(dict(base, P=40))
+    assert few.partition(0) == dict(M=32, NW=4, C=8) == many.partition(0)
+    assert few.slices_per_cta(0) == 1 and many.slices_per_cta(0) == 2
+    monkeypatch.setenv("BSP_S2", "1")
+    assert B.Problem(dict(base, P=40)).slices_per_cta(0) == 1
+    monkeypatch.setenv("BSP_S2", "2")
+    assert B.Problem(dict(base, P=8)).slices_per_cta(0) == 2
