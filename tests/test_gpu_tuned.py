@@ -174,12 +174,13 @@ def test_slice_pairs_parareal_network_and_ie_bitwise(B, monkeypatch, P):
 
 
 def test_slice_pair_rule_follows_the_slice_count(B, monkeypatch):
-    # a 30000-point grid takes 8-CTA clusters (32 rows per thread); pairs once
-    # the slices can keep every cluster busy twice over, and on request
+    # a 30000-point grid takes a clustered partition with 16 or 32 rows per
+    # thread (16 CTAs for 8 slices, 8 CTAs for 40); pairs once the slices can
+    # keep every cluster busy twice over, and on request
     monkeypatch.delenv("BSP_PARTITION", raising=False)
     base = dict(K=1.0, sigma=0.3, r=0.03, T=0.5, Smax=8.0, Nx=30000, fine_steps=2, coarse_steps=1)
     few, many = B.Problem(dict(base, P=8)), B.Problem(dict(base, P=40))
-    assert few.partition(0) == dict(M=32, NW=4, C=8) == many.partition(0)
+    assert few.partition(0) == dict(M=16, NW=4, C=16) and many.partition(0) == dict(M=32, NW=4, C=8)
     assert few.slices_per_cta(0) == 1 and many.slices_per_cta(0) == 2
     monkeypatch.setenv("BSP_S2", "1")
     assert B.Problem(dict(base, P=40)).slices_per_cta(0) == 1
