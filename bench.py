@@ -436,7 +436,7 @@ def batched_leg(B, torch, n_inst=4096, solve=True, rule_too=False):
     setup_s = time.perf_counter() - t0
     ms = time_fine(prob)
     tf = FLOPS_PER_PT_STEP * pt / (ms * 1e-3) / 1e12
-    chosen = {r["Nx"]: "M=%d NW=%d C=%d" % (r["M"], r["NW"], r["C"]) for r in prob.tuning if r["chosen"]}
+    chosen = {r["Nx"]: "M=%d NW=%d C=%d S2=%d" % (r["M"], r["NW"], r["C"], r["S2"]) for r in prob.tuning if r["chosen"]}
     out.update({"setup_s_with_tuning": setup_s, "tuned_partitions": {str(k): v for k, v in sorted(chosen.items())},
                 "candidates_timed": len(prob.tuning),
                 "fine_ms": ms, "grid_pt_steps_per_s": pt / (ms * 1e-3),
