@@ -298,6 +298,39 @@ class SolveGraph:
         return self.U
 
 
+def _autograd_function():
+    import torch
+
+    class PinnLossFunction(torch.autograd.Function):
+        """The total training loss of Eq. 11 (residual + boundary + expiry terms)
+        as a differentiable function of the network's flat FP64 parameter
+        vector theta.  forward loads theta into the model and runs
+        pinn_loss_grad (the forward derivative streams and the adjoint on the
+        device), keeping the gradient; backward returns it times the incoming
+        gradient.  apply(theta, model, X, kind, prob, smax_over_K, prec)."""
+
+        @staticmethod
+        def forward(ctx, theta, model, X, kind, prob, smax_over_K, prec):
+            model.set_weights(theta.detach().to("cpu", torch.float64).numpy())
+            loss3, grad = model.loss_grad(X, kind, prob, smax_over_K, prec)
+            ctx.save_for_backward(grad.to(theta.device))
+            return loss3.sum().to(theta.device)
+
+        @staticmethod
+        def backward(ctx, g):
+            (grad,) = ctx.saved_tensors
+            return grad * g, None, None, None, None, None, None
+
+    return PinnLossFunction
+
+
+def pinn_loss(theta, model, X, kind, prob: dict, smax_over_K=0.0, prec=FP32):
+    """Total loss (Eq. 11) of `model` with parameters `theta` (FP64 tensor of
+    model.n_params) on collocation points X / kind; differentiable in theta
+    (the gradient is the device adjoint of pinn_loss_grad)."""
+    return _autograd_function().apply(theta, model, X, kind, prob, smax_over_K, prec)
+
+
 class PinnModel:
     """Handle of pinn_create: tanh MLP in (S, tau) [, sigma, r, K]."""
 

@@ -196,3 +196,51 @@ def test_tensor_core_training_ragged_batches(B, orc, arch):
         for c in range(3):
             assert abs(l3[c] - terms[c]) <= 5e-2 * max(abs(terms[c]), 1e-300), (len(kind), c, l3[c], terms[c])
         assert _rel(g, grad) <= 1e-1, (len(kind), _rel(g, grad))
+
+
+@pytest.mark.parametrize("prec", [0, 3])
+def test_autograd_function_gradient_matches_oracle_and_differences(B, orc, prec):
+    # binding.pinn_loss: the total loss of Eq. 11 as a torch autograd function
+    # of the flat parameter vector; .backward() gives the device adjoint
+    widths = ARCHS["2-4x64"]
+    m, om = _model(B, orc, widths, 41)
+    X, kind, prob, sok = _loss_case(widths, 700, 64, 64, 9)
+    Xd, kd = torch.tensor(X, device="cuda"), torch.tensor(kind, device="cuda")
+    theta = torch.tensor(om.params, device="cuda", requires_grad=True)
+    loss = B.pinn_loss(theta, m, Xd, kd, prob, sok, prec=prec)
+    loss.backward()
+    terms, grad = orc.pinn_loss_grad(om, X, kind, prob["K"], prob["sigma"], prob["r"], prob["Smax"], sok)
+    g = theta.grad.cpu().numpy()
+    if prec == 0:
+        assert abs(loss.item() - sum(terms)) <= 1e-12 * sum(terms)
+        assert _rel(g, grad) <= 1e-10
+        # central differences of the device forward in a few coordinates
+        rng = np.random.default_rng(3)
+        for q in rng.choice(om.params.size, 6, replace=False):
+            h = 1e-6 * max(1.0, abs(om.params[q]))
+            tp, tm = theta.detach().clone(), theta.detach().clone()
+            tp[q] += h
+            tm[q] -= h
+            fd = (B.pinn_loss(tp, m, Xd, kd, prob, sok, prec=0).item() -
+                  B.pinn_loss(tm, m, Xd, kd, prob, sok, prec=0).item()) / (2 * h)
+            assert abs(fd - g[q]) <= 1e-6 * max(np.abs(g).max(), 1e-300), (q, fd, g[q])
+    else:
+        assert _rel(g, grad) <= 1e-1
+
+
+def test_autograd_function_drives_a_torch_optimizer(B):
+    widths = ARCHS["2-4x64"]
+    m = B.PinnModel(widths, [0.0, 0.0], [4.0, 1.0], seed=5)
+    X, kind = synth.collocation(2, 1024, 64, 64, 4.0, 1.0)
+    Xd, kd = torch.tensor(X, device="cuda"), torch.tensor(kind, device="cuda")
+    prob = dict(K=1.0, sigma=0.2, r=0.05, T=1.0, Smax=4.0, Nx=5, P=1, fine_steps=1, coarse_steps=1)
+    theta = torch.tensor(synth.xavier_params(widths, 5), device="cuda", requires_grad=True)
+    opt = torch.optim.Adam([theta], lr=1e-3)
+    first = None
+    for _ in range(30):
+        opt.zero_grad()
+        loss = B.pinn_loss(theta, m, Xd, kd, prob, prec=B.FP32)
+        loss.backward()
+        opt.step()
+        first = loss.item() if first is None else first
+    assert loss.item() < first
