@@ -186,3 +186,41 @@ def test_slice_pair_rule_follows_the_slice_count(B, monkeypatch):
     assert B.Problem(dict(base, P=40)).slices_per_cta(0) == 1
     monkeypatch.setenv("BSP_S2", "2")
     assert B.Problem(dict(base, P=8)).slices_per_cta(0) == 2
+
+
+def test_slice_pairs_with_mixed_slice_counts(B, orc, monkeypatch):
+    # instances of one class with P = 3, 5, 8: pairs partly or wholly past an
+    # instance's last slice are skipped, the rest match single slices bitwise
+    insts = [dict(K=0.9 + 0.1 * i, sigma=0.2 + 0.05 * i, r=0.02 * i, T=0.5, Smax=8.0, Nx=4000, P=P, fine_steps=3,
+                  coarse_steps=1) for i, P in enumerate((3, 5, 8))]
+    parts = [_slices(orc, p, 50 + i) for i, p in enumerate(insts)]
+    Uin = torch.tensor(np.concatenate([s.ravel() for s in parts]), device="cuda")
+    out = {}
+    for s2 in (1, 2):
+        monkeypatch.setenv("BSP_PARTITION", f"16,4,2,{s2}")
+        prob = B.Problem(insts)
+        out[s2] = (prob.fine_propagate(Uin), prob.parareal_solve(B.COARSE_IE, tol=1e-9)[0])
+        assert prob.device_status() == B.BS_OK
+    assert torch.equal(out[1][0], out[2][0]) and torch.equal(out[1][1], out[2][1])
+    F = out[2][0].cpu().numpy()
+    off = 0
+    for i, p in enumerate(insts):
+        op = orc.params(**p)
+        for n in range(p["P"]):
+            _close(F[off + n * p["Nx"]:off + (n + 1) * p["Nx"]], orc.fine(op, n, parts[i][n]), _tol(p, "fine"))
+        off += p["P"] * p["Nx"]
+
+
+def test_tuner_times_slice_pairs_where_supported(B, orc):
+    insts = [dict(K=1.0, sigma=0.25, r=0.03, T=0.5, Smax=8.0, Nx=4000, P=40, fine_steps=4, coarse_steps=1)
+             for _ in range(2)]
+    prob = B.Problem(insts, tuned=True)
+    rep = prob.tuning
+    assert {r["S2"] for r in rep} == {1, 2}
+    pairs = [r for r in rep if r["S2"] == 2]
+    assert all(r["C"] > 1 and r["M"] >= 16 for r in pairs)
+    chosen = [r for r in rep if r["chosen"]]
+    assert len(chosen) == 1 and chosen[0] == min(rep, key=lambda r: r["ms"])
+    assert prob.slices_per_cta(0) == chosen[0]["S2"]
+    parts = [_slices(orc, p, 60 + i) for i, p in enumerate(insts)]
+    _check_against_oracle(B, orc, prob, insts, parts)
