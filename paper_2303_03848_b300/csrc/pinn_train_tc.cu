@@ -573,8 +573,9 @@ __global__ void __launch_bounds__(128) train_fwd_tc_kernel(FwdArgs a) {
 //   t_bar = ah_0 - 2 t' d2_bar - 2 t d1_bar,  d2_bar = ah_2 z_S^2,
 //   d1_bar = ah_1 z_S + ah_2 z_SS + ah_3 z_tau - 2 t d2_bar,
 //   dz_0 = t' t_bar,  dz_1 = t' ah_1 + 2 t'' z_S ah_2,  dz_2 = t' ah_2,  dz_3 = t' ah_3,
-// which needs every stream's ah for the value stream: streams 1..3 publish
-// theirs through shared memory.  dz_l goes to global memory (weight gradient)
+// which needs every stream's ah for the value stream: streams 1..3 form their
+// shares (ah_S z_S, ah_SS z_SS, ah_SS z_S^2, ah_tau z_tau) and publish them
+// through shared memory, so the value stream's warp reads only t.  dz_l goes to global memory (weight gradient)
 // and, in BF16, to the A operand of the next GEMM.
 // ---------------------------------------------------------------------------
 struct BwdArgs {
@@ -595,15 +596,15 @@ __global__ void __launch_bounds__(128) train_bwd_tc_kernel(BwdArgs a) {
   const uint32_t wbytes = (uint32_t)w * w * 2;
   unsigned char* sW = smem;
   unsigned char* sA = sW + wbytes;
-  float* xa = reinterpret_cast<float*>(sA + (size_t)128 * w * 2);  // [2][3][32][33] ah of streams 1..3
-  float* sWo = xa + 2 * 3 * 32 * 33;                                // output weights (BF16-rounded)
+  float* xa = reinterpret_cast<float*>(sA + (size_t)128 * w * 2);  // [2][5][32][33] stream partials
+  float* sWo = xa + 2 * 5 * 32 * 33;                                // output weights (BF16-rounded)
   float* sseed = sWo + w;                                           // [4][32]
   uint64_t* bar = reinterpret_cast<uint64_t*>(sseed + 128);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
   __shared__ int s_fail;
   __shared__ const float* s_act[16];
   __shared__ float* s_dz[16];
-  auto XA = [&](int buf, int k, int qq, int j) -> float& { return xa[((buf * 3 + k) * 32 + qq) * 33 + j]; };
+  auto XA = [&](int buf, int k, int qq, int j) -> float& { return xa[((buf * 5 + k) * 32 + qq) * 33 + j]; };
   if (t < 16) {
     s_act[t] = a.act[t];
     s_dz[t] = a.dz[t];
@@ -655,20 +656,33 @@ __global__ void __launch_bounds__(128) train_bwd_tc_kernel(BwdArgs a) {
         } else {
           tmem_ld32(trow + (uint32_t)c, ah);
         }
-        if (s >= 1) {
-#pragma unroll
-          for (int j = 0; j < 32; ++j) XA(buf, s - 1, q, j) = ah[j];
-        }
-        // the layer's stored streams at (i, p) for this chunk: t for every stream,
-        // z_S for streams 0 and 1, z_SS and z_tau for stream 0 (loads issued together)
-        float tv[32], zsv[32], zssv[32], ztv[32];
+        // the layer's stored streams at (i, p) this stream needs: t always, z_S
+        // for streams 1 and 2, z_SS for stream 2, z_tau for stream 3 (loads
+        // issued together); each stream's share of the value stream's adjoint
+        // goes to shared memory: 0 ah_S z_S, 1 ah_SS, 2 ah_SS z_S^2,
+        // 3 ah_SS z_SS, 4 ah_tau z_tau
+        float tv[32], zav[32], zbv[32];
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const int64_t i = c + j;
           tv[j] = valid ? __ldg(act + (0 * (int64_t)w + i) * N + p) : 0.0f;
-          zsv[j] = (valid && s <= 1) ? __ldg(act + (1 * (int64_t)w + i) * N + p) : 0.0f;
-          zssv[j] = (valid && s == 0) ? __ldg(act + (2 * (int64_t)w + i) * N + p) : 0.0f;
-          ztv[j] = (valid && s == 0) ? __ldg(act + (3 * (int64_t)w + i) * N + p) : 0.0f;
+          const int ka = s == 3 ? 3 : 1;
+          zav[j] = (valid && s >= 1) ? __ldg(act + ((int64_t)ka * w + i) * N + p) : 0.0f;
+          zbv[j] = (valid && s == 2) ? __ldg(act + (2 * (int64_t)w + i) * N + p) : 0.0f;
+        }
+        if (s == 1) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) XA(buf, 0, q, j) = ah[j] * zav[j];
+        } else if (s == 2) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            XA(buf, 1, q, j) = ah[j];
+            XA(buf, 2, q, j) = ah[j] * zav[j] * zav[j];
+            XA(buf, 3, q, j) = ah[j] * zbv[j];
+          }
+        } else if (s == 3) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) XA(buf, 4, q, j) = ah[j] * zav[j];
         }
         __syncthreads();
         float dzv[32];
@@ -678,17 +692,15 @@ __global__ void __launch_bounds__(128) train_bwd_tc_kernel(BwdArgs a) {
           const float d1 = 1.0f - tt * tt, d2 = -2.0f * tt * d1;
           float r;
           if (s == 0) {
-            const float zs = zsv[j], zss = zssv[j], zt = ztv[j];
-            const float ahS = XA(buf, 0, q, j), ahSS = XA(buf, 1, q, j), ahT = XA(buf, 2, q, j);
-            const float bar_d2 = ahSS * zs * zs;
-            float bar_d1 = ahS * zs + ahSS * zss + ahT * zt;
+            const float bar_d2 = XA(buf, 2, q, j);
+            float bar_d1 = XA(buf, 0, q, j) + XA(buf, 3, q, j) + XA(buf, 4, q, j);
             float bar_t = ah[j];
             bar_t += -2.0f * d1 * bar_d2;
             bar_d1 += -2.0f * tt * bar_d2;
             bar_t += -2.0f * tt * bar_d1;
             r = d1 * bar_t;
           } else if (s == 1) {
-            r = ah[j] * d1 + 2.0f * XA(buf, 1, q, j) * d2 * zsv[j];
+            r = ah[j] * d1 + 2.0f * XA(buf, 1, q, j) * d2 * zav[j];
           } else {
             r = ah[j] * d1;
           }
@@ -766,7 +778,7 @@ cudaError_t launch_train_bwd_tc(const MlpDev& m, int64_t N, const float* const* 
   }
   a.seeds = seeds;
   a.wpackT = wpack + (size_t)n_sq * w * w * 2;
-  const size_t smem = (size_t)w * w * 2 + (size_t)128 * w * 2 + sizeof(float) * (6 * 32 * 33 + (size_t)w + 128) + 64;
+  const size_t smem = (size_t)w * w * 2 + (size_t)128 * w * 2 + sizeof(float) * (10 * 32 * 33 + (size_t)w + 128) + 64;
   cudaError_t e = cudaFuncSetAttribute(train_bwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(train_bwd_tc_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) !=
