@@ -111,30 +111,17 @@ struct LossArgs {
 cudaError_t launch_loss_grad(const MlpDev& m, const LossArgs& la, double* loss3, double* grad, void* workspace,
                              size_t ws_bytes, cudaStream_t s);
 size_t loss_grad_workspace_bytes(const MlpDev& m, int64_t N);
-// Weight gradient of the square hidden layers on tcgen05 (pinn_train_tc.cu),
-// BF16 operands: gW (w x w) and gb (w) of one layer from its adjoints dz
-// ([4][w][N]) and the stored streams act ([4][w][N]) of the layer below.
-bool wgrad_tc_supported(const MlpDev& m);
-// Forward with the derivative streams on tcgen05 (pinn_train_tc.cu), BF16
-// operands, hidden widths w <= 128: act[l] (l = 1..n_lin-1) and the loss seeds
-// as the CUDA-core forward writes them; wpack holds the packed square layers
-// (W then W^T, train_tc_pack_bytes).
+// The loss gradient on tcgen05 (pinn_train_tc.cu), BF16 operands with FP32
+// accumulation: forward with the derivative streams, adjoint and every layer's
+// weight gradient for networks d_in (2 or 5) -> w x ... x w -> 1 with w in
+// {32, 64, 96, 128}.  The workspace holds the per-layer activations, adjoints
+// and partial sums (train_tc_workspace_bytes, 256-byte aligned); the loss sums
+// go to loss_acc (3 doubles) and the gradient is added to grad (zeroed by the
+// caller).
 bool train_tc_supported(const MlpDev& m);
-size_t train_tc_pack_bytes(const MlpDev& m);
-cudaError_t launch_train_fwd_tc(const MlpDev& m, const LossArgs& la, float* const* act, float* seeds,
-                                unsigned char* wpack, const unsigned long long* cnt, double* loss_acc,
-                                cudaStream_t s);
-// Adjoint on tcgen05: dz[l] (l = 1..n_lin-1) from the seeds and act, as the
-// CUDA-core adjoint writes them; wpack as packed by launch_train_fwd_tc.
-cudaError_t launch_train_bwd_tc(const MlpDev& m, int64_t N, const float* const* act, float* const* dz,
-                                const float* seeds, const unsigned char* wpack, cudaStream_t s);
-// Gradients of the input layer (from dz[1] and the inputs) and the output layer
-// (from the seeds and act[n_lin-1]) on CUDA cores, BF16-rounded operands.
-cudaError_t launch_grad_edges_tc(const MlpDev& m, const double* X, int64_t N, const float* dz1, const float* act_top,
-                                 const float* seeds, double* grad, cudaStream_t s);
-size_t wgrad_tc_partial_bytes(const MlpDev& m, int64_t N);
-cudaError_t launch_wgrad_tc(const MlpDev& m, int64_t N, const float* dz, const float* act, double* gW, double* gb,
-                            float* partial, cudaStream_t s);
+size_t train_tc_workspace_bytes(const MlpDev& m, int64_t N);
+cudaError_t launch_train_tc(const MlpDev& m, const LossArgs& la, unsigned char* ws, const unsigned long long* cnt,
+                            double* loss_acc, double* grad, cudaStream_t s);
 cudaError_t launch_adam(int64_t n, double* theta, double* mom1, double* mom2, const double* g, int step, double lr,
                         float* p32, cudaStream_t s);
 

@@ -227,24 +227,25 @@ static TrainLayout train_layout(const MlpDev& m, int64_t N) {
   return L;
 }
 
-// Workspace: activations and adjoints, then the loss accumulators, the partial
-// sums of the tensor-core weight gradient and the packed square layers.
+// Workspace: activations and adjoints (the CUDA-core layout below, or the
+// tensor-core path's own, whichever is larger), then the loss accumulators.
 struct WsTail {
-  size_t acc, partial, pack, total;
+  size_t acc, total;
 };
 
 static WsTail ws_tail(const MlpDev& m, const TrainLayout& L, size_t elem, int64_t N) {
   WsTail w;
-  w.acc = ((size_t)L.total * elem + 15) / 16 * 16;
-  w.partial = (w.acc + 64 + 255) / 256 * 256;
-  w.pack = (w.partial + wgrad_tc_partial_bytes(m, N) + 255) / 256 * 256;
-  w.total = w.pack + train_tc_pack_bytes(m);
+  size_t body = (size_t)L.total * elem;
+  const size_t tcb = train_tc_workspace_bytes(m, N);
+  if (tcb > body) body = tcb;
+  w.acc = (body + 255) / 256 * 256;
+  w.total = w.acc + 64;
   return w;
 }
 
 size_t loss_grad_workspace_bytes(const MlpDev& m, int64_t N) {
   const TrainLayout L = train_layout(m, N);
-  return ws_tail(m, L, sizeof(double), N).total + 256;
+  return ws_tail(m, L, sizeof(double), N).total + 256;  // + alignment of the caller's pointer
 }
 
 __global__ void count_kinds_kernel(const int8_t* __restrict__ kind, int64_t N, unsigned long long* cnt) {
@@ -516,70 +517,37 @@ static cudaError_t loss_grad_impl(const MlpDev& m, const LossArgs& la, double* l
   e = cudaMemsetAsync(grad, 0, (size_t)np * sizeof(double), s);
   if (e != cudaSuccess) return e;
   count_kinds_kernel<<<148, 256, 0, s>>>(la.kind, la.N, cnt);
-  if (RND == 2 && train_tc_supported(m)) {  // forward on the tensor cores
-    if constexpr (RND == 2) {
-      float* act[16] = {};
-      for (int l = 1; l < m.n_lin; ++l) act[l] = ws + TL.act_off[l];
-      e = launch_train_fwd_tc(m, la, act, ws + TL.dz_off[m.n_lin], base + WT.pack, cnt, acc, s);
-      if (e != cudaSuccess) return e;
-    }
-  } else {  // forward on CUDA cores
-    const size_t per_thread = 2 * 4 * (size_t)m.max_w * sizeof(Tp);
-    const int TP = points_per_cta(per_thread);
-    const size_t smem = per_thread * TP;
-    e = cudaFuncSetAttribute(train_fwd_kernel<Tp, RND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (RND == 2 && train_tc_supported(m)) {  // BF16 on the tensor cores
+    if (((uintptr_t)base & 255) != 0) return cudaErrorInvalidValue;
+    e = launch_train_tc(m, la, base, cnt, acc, grad, s);
     if (e != cudaSuccess) return e;
-    train_fwd_kernel<Tp, RND><<<(unsigned)((la.N + TP - 1) / TP), TP, smem, s>>>(m, la, TL, ws, cnt, acc);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
-  if (RND == 2 && train_tc_supported(m)) {  // adjoint on the tensor cores
-    if constexpr (RND == 2) {
-      const float* act[16] = {};
-      float* dzp[16] = {};
-      for (int l = 1; l < m.n_lin; ++l) {
-        act[l] = ws + TL.act_off[l];
-        dzp[l] = ws + TL.dz_off[l];
-      }
-      e = launch_train_bwd_tc(m, la.N, act, dzp, ws + TL.dz_off[m.n_lin], base + WT.pack, s);
+  } else {  // CUDA cores: forward, adjoint, per-layer reductions
+    {
+      const size_t per_thread = 2 * 4 * (size_t)m.max_w * sizeof(Tp);
+      const int TP = points_per_cta(per_thread);
+      const size_t smem = per_thread * TP;
+      e = cudaFuncSetAttribute(train_fwd_kernel<Tp, RND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
+      train_fwd_kernel<Tp, RND><<<(unsigned)((la.N + TP - 1) / TP), TP, smem, s>>>(m, la, TL, ws, cnt, acc);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-  } else {  // adjoint on CUDA cores
-    const size_t per_thread = 4 * (size_t)m.max_w * sizeof(Tp);
-    const int TP = points_per_cta(per_thread);
-    const size_t smem = per_thread * TP;
-    e = cudaFuncSetAttribute(train_bwd_kernel<Tp, RND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    train_bwd_kernel<Tp, RND><<<(unsigned)((la.N + TP - 1) / TP), TP, smem, s>>>(m, la.N, TL, ws);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
-  // weight gradients: BF16 square hidden layers on the tensor cores, the rest
-  // (and every layer of the other precisions) on CUDA cores
-  const int64_t chunk = 2048;
-  const unsigned nz = (unsigned)((la.N + chunk - 1) / chunk);
-  const bool tc = RND == 2 && wgrad_tc_supported(m);
-  float* partial = reinterpret_cast<float*>(base + WT.partial);
-  if (tc && train_tc_supported(m)) {
-    if constexpr (RND == 2) {
-      e = launch_grad_edges_tc(m, la.X, la.N, ws + TL.dz_off[1], ws + TL.act_off[m.n_lin - 1],
-                               ws + TL.dz_off[m.n_lin], grad, s);
+    {
+      const size_t per_thread = 4 * (size_t)m.max_w * sizeof(Tp);
+      const int TP = points_per_cta(per_thread);
+      const size_t smem = per_thread * TP;
+      e = cudaFuncSetAttribute(train_bwd_kernel<Tp, RND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
+      train_bwd_kernel<Tp, RND><<<(unsigned)((la.N + TP - 1) / TP), TP, smem, s>>>(m, la.N, TL, ws);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-  }
-  for (int l = 1; l <= m.n_lin; ++l) {
-    const int wi = m.widths[l - 1], wo = m.widths[l];
-    if (tc && train_tc_supported(m) && (l == 1 || l == m.n_lin)) continue;
-    if (tc && l >= 2 && l <= m.n_lin - 1) {
-      if constexpr (RND == 2) {
-        double* gW = grad + m.poff[l];
-        e = launch_wgrad_tc(m, la.N, ws + TL.dz_off[l], ws + TL.act_off[l - 1], gW, gW + (int64_t)wo * wi, partial,
-                            s);
-        if (e != cudaSuccess) return e;
-      }
-      continue;
+    const int64_t chunk = 2048;
+    const unsigned nz = (unsigned)((la.N + chunk - 1) / chunk);
+    for (int l = 1; l <= m.n_lin; ++l) {
+      const int wi = m.widths[l - 1], wo = m.widths[l];
+      dim3 grid((wi + 1 + 15) / 16, (wo + 15) / 16, nz);
+      grad_reduce_kernel<Tp, RND><<<grid, dim3(16, 16), 0, s>>>(m, la, TL, ws, l, grad, chunk);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    dim3 grid((wi + 1 + 15) / 16, (wo + 15) / 16, nz);
-    grad_reduce_kernel<Tp, RND><<<grid, dim3(16, 16), 0, s>>>(m, la, TL, ws, l, grad, chunk);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   loss_finish_kernel<<<1, 32, 0, s>>>(acc, cnt, loss3);
   return cudaGetLastError();

@@ -1,25 +1,35 @@
-// pinn_train_tc.cu -- the weight gradient of the network's square hidden layers
-// (Section 3.3 training, the adjoint of Eqs. 11-14) on the tensor cores:
-// BF16 operands, FP32 accumulation in tensor memory.
+// pinn_train_tc.cu -- the loss gradient of one training step (Section 3.3, the
+// loss of Eqs. 11-14 and its adjoint) with the network's square hidden layers
+// on the tensor cores: BF16 operands, FP32 accumulation in tensor memory.
 //
-// For a hidden layer l with w inputs and w outputs
-//   dL/dW_l[o][i] = sum over streams s and points p of dz_s[o][p] * h_s[i][p],
-// where dz_s are the adjoints of the layer's four pre-activation streams
-// (value, d/dS, d2/dS2, d/dtau) and h_s the streams of its input, rebuilt from
-// the stored (t, z_S, z_SS, z_tau) of the layer below:
-//   h_0 = t,  h_1 = t' z_S,  h_2 = t' z_SS + t'' z_S^2,  h_3 = t' z_tau,
-//   t' = 1 - t^2,  t'' = -2 t t'.
-// That is one GEMM D[o][i] = sum_k A[o][k] B[i][k] with K = 4N: A = dz (rows o,
-// K = (s, p)), B = h (rows i, K = (s, p)); both are stored point-contiguous, so
-// a 64-point slice of a row is a K-major operand chunk.
+// A tile is 128 collocation points.  Every hidden layer is four GEMMs, one per
+// derivative stream s (0 value, 1 d/dS, 2 d2/dS2, 3 d/dtau), each into its own
+// tensor-memory accumulator, so lane p of all four holds point p and one
+// thread mixes the streams of its point in registers:
+//   forward   z_s = W h_s (+ b on the value stream),  t = tanh z_0,
+//             h_0 = t, h_1 = t' z_1, h_2 = t' z_2 + t'' z_1^2, h_3 = t' z_3,
+//             t' = 1 - t^2, t'' = -2 t t';
+//   adjoint   ah_s = W^T dz_s (rank one from the loss seeds at the top), then
+//             d2_bar = ah_2 z_1^2, d1_bar = ah_1 z_1 + ah_2 z_2 + ah_3 z_3,
+//             t_bar = ah_0 - 2 t' d2_bar - 2 t (d1_bar - 2 t d2_bar),
+//             dz_0 = t' t_bar, dz_1 = t' ah_1 + 2 t'' z_1 ah_2, dz_2 = t' ah_2,
+//             dz_3 = t' ah_3;
+//   gradient  dL/dW[o][i] = sum over streams and points of dz_s[o] h_s[i],
+//             dL/db[o] = sum over points of dz_0[o].
 //
-// One CTA of 128 threads owns a 128-row tile of o and a contiguous range of
-// (stream, 64-point block) chunks.  Per chunk the threads convert the operands
-// to BF16 into one of two shared-memory stages (core-matrix layout) while the
-// tensor core works on the other; one thread issues the four K=16 MMAs and
-// commits them to the stage's mbarrier.  The FP32 partial sums of each CTA go to
-// a buffer that a second kernel adds up in FP64 into the gradient.  Every wait is
-// bounded; on expiry the kernel records BS_TIMEOUT and stops.
+// Workspace (NT = ceil(N / 128) tiles, w the hidden width):
+//   act[l]  float4 [NT][w][128]: (t, z_1, z_2, z_3) of hidden layer l at
+//           (neuron, point); the adjoint reads it with one 16-byte load per
+//           neuron, 512 contiguous bytes per warp;
+//   hb[l]   BF16 [NT][4][128 x w]: h_s of hidden layer l;
+//   dzb[l]  BF16 [NT][4][128 x w]: dz_s of hidden layer l.
+// The BF16 blocks keep the GEMM operand layout (rows = points, K = neurons,
+// no-swizzle core matrices), written by the forward / adjoint epilogues with
+// the same 16-byte stores that fill the next GEMM's operand; the weight
+// gradient copies them back with TMA bulk loads and reads them as MN-major
+// operands (the neuron index contiguous), so no transpose is ever formed.
+// The input layer (d_in -> w) and the output layer (w -> 1) run on CUDA cores.
+// Every wait is bounded; on expiry a kernel records BS_TIMEOUT and stops.
 #include <cuda_bf16.h>
 
 #include <cstdint>
@@ -35,32 +45,50 @@ using namespace tc;
 
 namespace {
 
-constexpr int kChunk = 64;  // points per K chunk
-
-struct WgArgs {
-  const float* dz;   // adjoints of layer l: [4][w][N]
-  const float* act;  // stored streams of layer l-1: [4][w][N] = (t, z_S, z_SS, z_tau)
-  int64_t N;
-  int w;
-  int nbr;      // rows of B: w, or w + 16 with row w = 1 on the value stream (bias gradient)
-  int nb;       // 64-point blocks
-  int per_cta;  // chunks per CTA along K
-  int vec;      // N % 4 == 0: 16-byte loads
-  float* partial;  // [gridDim.y][w][w + 1]
-  int* status;
+struct TcLayout {
+  size_t act[16], hb[16], dzb[16];  // byte offsets, hidden layers l = 1..n_lin-1
+  size_t seeds;                     // float [4][N]: dLoss/d(u, u_S, u_SS, u_tau)
+  size_t partial;                   // float [n_sq][ny][w][w + 1]: weight-gradient partial sums
+  size_t pack;                      // BF16 square layers: W_l then W_l^T
+  size_t total;
+  int nt;  // tiles of 128 points
+  int ny;  // weight-gradient CTAs per square layer
 };
 
-// 8 consecutive floats of a row from p = pb on (zero past N).
-__device__ __forceinline__ void load8(const float* src, int64_t pb, int64_t N, int vec, float (&v)[8]) {
-  if (vec && pb + 8 <= N) {
-    const float4 x = __ldg(reinterpret_cast<const float4*>(src));
-    const float4 y = __ldg(reinterpret_cast<const float4*>(src + 4));
-    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
-    v[4] = y.x; v[5] = y.y; v[6] = y.z; v[7] = y.w;
-  } else {
-#pragma unroll
-    for (int e = 0; e < 8; ++e) v[e] = pb + e < N ? __ldg(src + e) : 0.0f;
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
   }
+  return n;
+}
+
+TcLayout tc_layout(const MlpDev& m, int64_t N) {
+  TcLayout L{};
+  const int w = m.widths[1], n_sq = m.n_lin - 2;
+  const int64_t nt = (N + 127) / 128;
+  L.nt = (int)nt;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t r = o;
+    o = (o + bytes + 255) / 256 * 256;
+    return r;
+  };
+  for (int l = 1; l < m.n_lin; ++l) L.act[l] = take((size_t)nt * w * 128 * 16);
+  for (int l = 1; l < m.n_lin; ++l) L.hb[l] = take((size_t)nt * 4 * 128 * w * 2);
+  for (int l = 1; l < m.n_lin; ++l) L.dzb[l] = take((size_t)nt * 4 * 128 * w * 2);
+  L.seeds = take((size_t)4 * (size_t)N * sizeof(float));
+  // one wave of weight-gradient CTAs (one per SM) over all square layers
+  int ny = sm_count() / (n_sq > 0 ? n_sq : 1);
+  if (ny < 1) ny = 1;
+  if ((int64_t)ny > 4 * nt) ny = (int)(4 * nt);
+  L.ny = ny;
+  L.partial = take((size_t)n_sq * ny * w * (w + 1) * sizeof(float));
+  L.pack = take((size_t)2 * n_sq * w * w * 2);
+  L.total = o;
+  return L;
 }
 
 __device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
@@ -70,250 +98,21 @@ __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
   return *reinterpret_cast<uint32_t*>(&q);
 }
 
-__global__ void __launch_bounds__(128) wgrad_tc_kernel(WgArgs a) {
-  extern __shared__ __align__(1024) unsigned char smem[];
-  const int w = a.w, t = threadIdx.x, warp = t >> 5, lane = t & 31;
-  const int ot = blockIdx.x;
-  constexpr uint32_t a_bytes = 128 * kChunk * 2;
-  const int nbr = a.nbr;
-  const uint32_t b_bytes = (uint32_t)nbr * kChunk * 2;
-  auto stA = [&](int st) { return smem + st * a_bytes; };
-  auto stB = [&](int st) { return smem + 2 * a_bytes + st * b_bytes; };
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * a_bytes + 2 * b_bytes);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
-  __shared__ int s_fail;
-  const int total = 4 * a.nb;
-  const int c0 = blockIdx.y * a.per_cta;
-  const int c1 = c0 + a.per_cta < total ? c0 + a.per_cta : total;
-  if (t == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
-    s_fail = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  uint32_t ncols = 32;
-  while ((int)ncols < nbr) ncols <<= 1;
-  if (warp == 0) tmem_alloc(tslot, ncols);
-  fence_before();
-  __syncthreads();
-  fence_after();
-  const uint32_t tmem = *tslot;
-  const uint32_t idesc = make_idesc_bf16(nbr);
-  const int64_t N = a.N;
-  int n = 0;
-  for (int c = c0; c < c1; ++c, ++n) {
-    const int st = n & 1;
-    const int s = c / a.nb;
-    const int64_t p0 = (int64_t)(c % a.nb) * kChunk;
-    if (n >= 2 && !mbar_wait_bounded(&bar[st], (uint32_t)((n - 2) >> 1) & 1u)) s_fail = 1;  // stage free
-    __syncthreads();
-    if (s_fail) break;
-    // A: 128 rows (o) x 64 points of dz_s, BF16
-    for (int it = t; it < 128 * (kChunk / 8); it += 128) {
-      const int row = it >> 3, kc = it & 7;
-      const int o = ot * 128 + row;
-      uint4 q = make_uint4(0u, 0u, 0u, 0u);
-      if (o < w) {
-        const int64_t pb = p0 + kc * 8;
-        float v[8];
-        load8(a.dz + ((int64_t)s * w + o) * N + pb, pb, N, a.vec, v);
-        q = make_uint4(pack2(v[0], v[1]), pack2(v[2], v[3]), pack2(v[4], v[5]), pack2(v[6], v[7]));
-      }
-      *reinterpret_cast<uint4*>(stA(st) + canon_off(row, kc * 8, kChunk)) = q;
-    }
-    // B: w rows (i) x 64 points of h_s rebuilt from the stored streams, BF16;
-    // then (nbr > w) the bias row (1 on the value stream) and zero rows
-    for (int it = t; it < nbr * (kChunk / 8); it += 128) {
-      const int i = it >> 3, kc = it & 7;
-      const int64_t pb = p0 + kc * 8;
-      float v[8];
-      if (i >= w) {
-#pragma unroll
-        for (int e = 0; e < 8; ++e) v[e] = (i == w && s == 0 && pb + e < N) ? 1.0f : 0.0f;
-      } else {
-        float tt[8], zz[8], z1[8];
-        load8(a.act + ((int64_t)0 * w + i) * N + pb, pb, N, a.vec, tt);
-        if (s != 0) load8(a.act + ((int64_t)(s == 2 ? 2 : (s == 3 ? 3 : 1)) * w + i) * N + pb, pb, N, a.vec, zz);
-        if (s == 2) load8(a.act + ((int64_t)1 * w + i) * N + pb, pb, N, a.vec, z1);
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const float d1 = 1.0f - tt[e] * tt[e];
-          if (s == 0) v[e] = tt[e];
-          else if (s == 2) v[e] = d1 * zz[e] - 2.0f * tt[e] * d1 * z1[e] * z1[e];
-          else v[e] = d1 * zz[e];
-        }
-      }
-      const uint4 q = make_uint4(pack2(v[0], v[1]), pack2(v[2], v[3]), pack2(v[4], v[5]), pack2(v[6], v[7]));
-      *reinterpret_cast<uint4*>(stB(st) + canon_off(i, kc * 8, kChunk)) = q;
-    }
-    fence_proxy_async();  // generic-proxy writes of the stage visible to the tensor core
-    fence_before();
-    __syncthreads();
-    fence_after();
-    if (t == 0) {
-      const uint32_t aa = smem_u32(stA(st)), bb = smem_u32(stB(st));
-#pragma unroll
-      for (int kk = 0; kk < kChunk / 16; ++kk) {
-        const uint64_t da = make_desc(aa + kk * 256, 128, (kChunk / 8) * 128);
-        const uint64_t db = make_desc(bb + kk * 256, 128, (kChunk / 8) * 128);
-        mma_bf16(tmem, da, db, idesc, (n > 0 || kk > 0) ? 1u : 0u);
-      }
-      mma_commit(&bar[st]);
-    }
-  }
-  // the last commit covers every MMA issued before it
-  if (!s_fail && n > 0 && !mbar_wait_bounded(&bar[(n - 1) & 1], (uint32_t)((n - 1) >> 1) & 1u)) s_fail = 1;
-  fence_after();
-  __syncthreads();
-  if (!s_fail && n > 0) {
-    const int o = ot * 128 + warp * 32 + lane;
-    const int wc = nbr > w ? w + 1 : w;  // columns kept: w, and the bias
-    float* dst = a.partial + ((int64_t)blockIdx.y * w + o) * (w + 1);
-    for (int cc = 0; cc < wc; cc += 32) {
-      float v[32];
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cc, v);
-      if (o < w) {
-#pragma unroll
-        for (int e = 0; e < 32; ++e)
-          if (cc + e < wc) dst[cc + e] = v[e];
-      }
-    }
-  }
-  fence_before();
-  __syncthreads();
-  fence_after();
-  if (s_fail && t == 0) atomicExch(a.status, 6);  // BS_TIMEOUT
-  if (warp == 0) tmem_dealloc(tmem, ncols);
+__device__ __forceinline__ uint4 pack8(const float* v) {
+  return make_uint4(pack2(v[0], v[1]), pack2(v[2], v[3]), pack2(v[4], v[5]), pack2(v[6], v[7]));
 }
 
-// gW[o][i] (i < w) and gb[o] (column w, when the bias row was in the GEMM):
-// sums over CTAs of the partial sums; blockIdx.y takes one group of CTAs and
-// adds its FP64 sum atomically (the gradient starts at zero).
-__global__ void wgrad_sum_kernel(const float* __restrict__ partial, int ny, int w, int with_bias,
-                                 double* __restrict__ gW, double* __restrict__ gb) {
-  const int64_t wc = (int64_t)w * (w + 1);
-  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (q >= wc) return;
-  const int o = (int)(q / (w + 1)), i = (int)(q % (w + 1));
-  if (i == w && !with_bias) return;
-  const int y0 = (int)((int64_t)ny * blockIdx.y / gridDim.y), y1 = (int)((int64_t)ny * (blockIdx.y + 1) / gridDim.y);
-  float acc = 0.0f;
-  for (int y = y0; y < y1; ++y) acc += partial[(int64_t)y * wc + q];
-  atomicAdd(i < w ? gW + (int64_t)o * w + i : gb + o, (double)acc);
-}
-
-// gb[o] = sum_p dz_0[o][p] for widths without the bias row in the GEMM (w > 240),
-// the adjoint rounded to BF16 like the GEMM operand.
-__global__ void bias_grad_kernel(const float* __restrict__ dz, int64_t N, double* __restrict__ gb) {
-  __shared__ float red[4];
-  const int o = blockIdx.x, t = threadIdx.x;
-  float acc = 0.0f;
-  for (int64_t p = t; p < N; p += blockDim.x) acc += bf16r(dz[(int64_t)o * N + p]);
-  for (int s = 16; s >= 1; s >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, s);
-  if ((t & 31) == 0) red[t >> 5] = acc;
-  __syncthreads();
-  if (t == 0) gb[o] = (double)red[0] + red[1] + red[2] + red[3];
-}
-
-// Input layer (d_in -> w): its input streams are the mapped inputs h_0 = x^ and
-// the constants h_1 = sc_S e_S, h_3 = sc_tau e_tau (h_2 = 0), so
-//   dL/dW_1[o][i] = sum_p dz_0[o][p] x^_i(p) + [i = 0] sc_S sum_p dz_1[o][p]
-//                   + [i = 1] sc_tau sum_p dz_3[o][p],   dL/db_1[o] = sum_p dz_0[o][p];
-// operands rounded to BF16 like the GEMM operands.  One CTA per (o, chunk).
-template <int DIN>
-__global__ void grad_input_kernel(MlpDev m, const double* __restrict__ X, int64_t N, const float* __restrict__ dz1,
-                                  double* __restrict__ grad, int64_t chunk) {
-  __shared__ float red[4][12];
-  constexpr int d = DIN;
-  const int o = blockIdx.x, t = threadIdx.x, w = m.widths[1];
-  const int64_t p0 = (int64_t)blockIdx.y * chunk, p1 = p0 + chunk < N ? p0 + chunk : N;
-  float ax[8] = {0, 0, 0, 0, 0, 0, 0, 0}, a0 = 0.0f, a1 = 0.0f, a3 = 0.0f;
-  double sc[DIN], lo[DIN];
+__device__ __forceinline__ void unpack8(uint4 q, float (&v)[8]) {
+  const uint32_t u[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-  for (int i = 0; i < d; ++i) {
-    sc[i] = 2.0 / (m.hi[i] - m.lo[i]);
-    lo[i] = m.lo[i];
-  }
-  for (int64_t p = p0 + t; p < p1; p += blockDim.x) {
-    const float g0 = bf16r(dz1[(0 * (int64_t)w + o) * N + p]);
-    a0 += g0;
-    a1 += bf16r(dz1[(1 * (int64_t)w + o) * N + p]);
-    a3 += bf16r(dz1[(3 * (int64_t)w + o) * N + p]);
-#pragma unroll
-    for (int i = 0; i < d; ++i) ax[i] += g0 * bf16r((float)(sc[i] * (X[p * d + i] - lo[i]) - 1.0));
-  }
-  float v[11];
-#pragma unroll
-  for (int i = 0; i < 8; ++i) v[i] = ax[i];
-  v[8] = a0;
-  v[9] = a1;
-  v[10] = a3;
-#pragma unroll
-  for (int k = 0; k < 11; ++k) {
-    float x = v[k];
-    for (int s = 16; s >= 1; s >>= 1) x += __shfl_down_sync(0xffffffffu, x, s);
-    if ((t & 31) == 0) red[t >> 5][k] = x;
-  }
-  __syncthreads();
-  if (t < 11 && (t < d || t >= 8)) {
-    const double tot = (double)red[0][t] + red[1][t] + red[2][t] + red[3][t];
-    double* g = grad + m.poff[1];
-    if (t < d) {
-      atomicAdd(g + (int64_t)o * d + t, tot);
-    } else if (t == 8) {
-      atomicAdd(g + (int64_t)w * d + o, tot);
-    } else {
-      const int i = t == 9 ? 0 : 1;  // d/dS stream feeds input 0 (S), d/dtau stream input 1 (tau)
-      const double sc = 2.0 / (m.hi[i] - m.lo[i]);
-      atomicAdd(g + (int64_t)o * d + i, (double)bf16r((float)sc) * tot);
-    }
+  for (int k = 0; k < 4; ++k) {
+    v[2 * k] = __uint_as_float(u[k] << 16);
+    v[2 * k + 1] = __uint_as_float(u[k] & 0xFFFF0000u);
   }
 }
 
-// Output layer (w -> 1): dL/dW_L[i] = sum_{s,p} dz_s[p] h_s[i][p] with h_s
-// rebuilt from the last hidden layer's stored streams; warp i = w is the bias
-// (h_0 = 1).  One warp per i, lanes over the points of a chunk.
-__global__ void grad_output_kernel(const float* __restrict__ act, const float* __restrict__ seeds, int w, int64_t N,
-                                   double* __restrict__ gW, double* __restrict__ gb, int64_t chunk) {
-  const int i = blockIdx.x * 4 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  if (i > w) return;
-  const int64_t p0 = (int64_t)blockIdx.y * chunk, p1 = p0 + chunk < N ? p0 + chunk : N;
-  float acc = 0.0f;
-  for (int64_t p = p0 + lane; p < p1; p += 32) {
-    const float g0 = bf16r(seeds[p]);
-    if (i == w) {
-      acc += g0;
-      continue;
-    }
-    const float g1 = bf16r(seeds[N + p]), g2 = bf16r(seeds[2 * N + p]), g3 = bf16r(seeds[3 * N + p]);
-    const float tt = act[(0 * (int64_t)w + i) * N + p], zs = act[(1 * (int64_t)w + i) * N + p];
-    const float zss = act[(2 * (int64_t)w + i) * N + p], zt = act[(3 * (int64_t)w + i) * N + p];
-    const float d1 = 1.0f - tt * tt;
-    acc += g0 * bf16r(tt) + g1 * bf16r(d1 * zs) + g2 * bf16r(d1 * zss - 2.0f * tt * d1 * zs * zs) + g3 * bf16r(d1 * zt);
-  }
-  for (int s = 16; s >= 1; s >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, s);
-  if (lane == 0) atomicAdd(i < w ? gW + i : gb, (double)acc);
-}
-
-// CTAs along K: about two per SM over all o tiles.
-void wgrad_grid(int w, int64_t N, int* ot, int* per_cta, int* ny) {
-  const int nb = (int)((N + kChunk - 1) / kChunk);
-  const int total = 4 * nb;
-  *ot = (w + 127) / 128;
-  int pc = (int)(((int64_t)total * *ot + 295) / 296);
-  if (pc < 1) pc = 1;
-  *per_cta = pc;
-  *ny = (total + pc - 1) / pc;
-}
-
-int wgrad_rows_b(int w) { return w + 16 <= 256 ? w + 16 : w; }
-
-size_t wgrad_smem_bytes(int w) {
-  return 2 * (size_t)128 * kChunk * 2 + 2 * (size_t)wgrad_rows_b(w) * kChunk * 2 + 64;
-}
-
-// Pack the square layers for training: W_l (rows o, K = i) for the forward and
-// W_l^T (rows i, K = o) for the adjoint, BF16 core-matrix layout.
+// Pack the square layers: W_l (rows o, K = i) for the forward and W_l^T (rows
+// i, K = o) for the adjoint, BF16 core-matrix layout.
 __global__ void pack_train_kernel(MlpDev m, int w, unsigned char* fwd, unsigned char* bwd) {
   const int n_sq = m.n_lin - 2;
   const int64_t per = (int64_t)w * w;
@@ -327,63 +126,69 @@ __global__ void pack_train_kernel(MlpDev m, int w, unsigned char* fwd, unsigned 
   }
 }
 
+__host__ __device__ constexpr uint32_t tmem_cols_streams(int w) {
+  return 4 * w <= 128 ? 128 : (4 * w <= 256 ? 256 : 512);
+}
+
 // ---------------------------------------------------------------------------
-// Forward with the four derivative streams on the tensor cores.  A CTA of 128
-// threads takes 32 points at a time; row r = 32 s + q of every layer GEMM is
-// stream s (warp s) of point q (lane q), so each thread reads its own row of
-// the accumulator.  Per hidden layer the value stream's warp forms t = tanh(z)
-// and the S-stream's warp publishes z_S through shared memory; then every
-// stream forms its input to the next layer:
-//   h_0 = t, h_1 = t' z_S, h_2 = t' z_SS + t'' z_S^2, h_3 = t' z_tau,
-// stores (t, z_S, z_SS, z_tau) for the adjoint and writes h_s in BF16 as the
-// next A operand.  Input layer, output layer and the loss seeds on CUDA cores.
+// Forward.  A CTA of 4w threads: warp v reads accumulator lanes 32 (v % 4) ..
+// (one point per thread) and owns neurons 32 (v / 4) .. + 31 of every layer.
+// Per square layer one thread issues the four stream GEMMs (M = 128 points,
+// N = K = w) and the next layer's weights are fetched by TMA while the
+// epilogue runs.  After the top layer the output streams, the loss terms and
+// the adjoint seeds are formed per point in FP64.
 // ---------------------------------------------------------------------------
 struct FwdArgs {
   MlpDev m;
   LossArgs la;
-  float* act[16];      // act[l], l = 1..n_lin-1: [4][w][N] = (t, z_S, z_SS, z_tau)
-  float* seeds;        // dLoss/d(u, u_S, u_SS, u_tau): [4][N]
-  const unsigned char* wpack;  // square layers, W_l (rows o, K = i)
+  unsigned char* ws;
+  TcLayout L;
   const unsigned long long* cnt;
   double* loss_acc;
 };
 
-template <int DIN>
-__global__ void __launch_bounds__(128) train_fwd_tc_kernel(FwdArgs a) {
+template <int DIN, int W>
+__global__ void __launch_bounds__(4 * W, 1) train_fwd_tc_kernel(FwdArgs a) {
+  constexpr int NG = W / 32;
+  constexpr uint32_t WB = W * W * 2, AB = 128 * W * 2, SBO = (W / 8) * 128;
+  constexpr uint32_t NCOLS = tmem_cols_streams(W);
   extern __shared__ __align__(1024) unsigned char smem[];
   const MlpDev& m = a.m;
-  const int w = m.widths[1], n_sq = m.n_lin - 2;
-  const int t = threadIdx.x, s = t >> 5, q = t & 31;
-  const int64_t N = a.la.N;
-  const uint32_t wbytes = (uint32_t)w * w * 2;
+  const int n_lin = m.n_lin, n_sq = n_lin - 2;
   unsigned char* sW = smem;
-  unsigned char* sA = sW + wbytes;
-  float* xt = reinterpret_cast<float*>(sA + (size_t)128 * w * 2);  // [2][32][33] tanh of a column chunk
-  float* xs = xt + 2 * 32 * 33;                                     // [2][32][33] z_S of a column chunk
-  float* sW1 = xs + 2 * 32 * 33;                                    // w x DIN
-  float* sB = sW1 + w * DIN;                                        // hidden biases, (n_lin-1) x w
-  float* sWo = sB + (m.n_lin - 1) * w;                              // output weights, w
-  float* su = sWo + w;                                              // [4][32] output streams
-  uint64_t* bar = reinterpret_cast<uint64_t*>(su + 128);            // [0] MMA done, [1] weights landed
+  unsigned char* sA = smem + WB;                                    // [4][AB]
+  float* sW1 = reinterpret_cast<float*>(sA + 4 * AB);               // W x DIN, BF16-rounded
+  float* sB = sW1 + W * DIN;                                        // hidden biases, (n_lin - 1) x W
+  float* sWo = sB + (n_lin - 1) * W;                                // output weights, BF16-rounded
+  float* sred = sWo + W;                                            // [NG][4][128] output partial sums
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sred + NG * 4 * 128);  // [0] GEMMs done, [1] weights landed
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
   __shared__ int s_fail;
   __shared__ double s_acc[3];
-  __shared__ float* s_act[16];
-  if (t < 16) s_act[t] = a.act[t];
+  __shared__ float4* s_act[16];
+  __shared__ unsigned char* s_hb[16];
 
-  for (int i = t; i < w * DIN; i += 128) sW1[i] = bf16r(m.p32[m.poff[1] + i]);
-  for (int l = 1; l < m.n_lin; ++l)
-    for (int o = t; o < w; o += 128) sB[(l - 1) * w + o] = m.p32[m.poff[l] + (int64_t)w * m.widths[l - 1] + o];
-  for (int o = t; o < w; o += 128) sWo[o] = bf16r(m.p32[m.poff[m.n_lin] + o]);
-  const float bout = m.p32[m.poff[m.n_lin] + w];
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31, g = warp >> 2;
+  const int pl = (warp & 3) * 32 + lane, c0 = g * 32;
+  const int64_t N = a.la.N;
+  const int nt = a.L.nt;
+  if (t < 16) {
+    const bool hid = t >= 1 && t < n_lin;
+    s_act[t] = hid ? reinterpret_cast<float4*>(a.ws + a.L.act[t]) : nullptr;
+    s_hb[t] = hid ? a.ws + a.L.hb[t] : nullptr;
+  }
+  for (int i = t; i < W * DIN; i += blockDim.x) sW1[i] = bf16r(m.p32[m.poff[1] + i]);
+  for (int l = 1; l < n_lin; ++l)
+    for (int o = t; o < W; o += blockDim.x) sB[(l - 1) * W + o] = m.p32[m.poff[l] + (int64_t)W * m.widths[l - 1] + o];
+  for (int o = t; o < W; o += blockDim.x) sWo[o] = bf16r(m.p32[m.poff[n_lin] + o]);
+  const float bout = m.p32[m.poff[n_lin] + W];
   float sc[DIN], of[DIN];
 #pragma unroll
   for (int i = 0; i < DIN; ++i) {
-    const double g = 2.0 / (m.hi[i] - m.lo[i]);
-    sc[i] = (float)g;
-    of[i] = (float)(-g * m.lo[i] - 1.0);
+    const double gi = 2.0 / (m.hi[i] - m.lo[i]);
+    sc[i] = (float)gi;
+    of[i] = (float)(-gi * m.lo[i] - 1.0);
   }
-  const int64_t ntiles = (N + 31) / 32;
   if (t == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
@@ -392,66 +197,61 @@ __global__ void __launch_bounds__(128) train_fwd_tc_kernel(FwdArgs a) {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  bool w_pending = false;
+  bool w_pending = false, mma_lost = false;
   uint32_t ph_w = 0, ph_mma = 0;
-  if (t == 0 && (int64_t)blockIdx.x < ntiles) {
-    bulk_load(sW, a.wpack, wbytes, &bar[1]);
+  const unsigned char* wpack = a.ws + a.L.pack;
+  if (t == 0 && (int)blockIdx.x < nt) {
+    bulk_load(sW, wpack, WB, &bar[1]);
     w_pending = true;
   }
-  uint32_t ncols = 32;
-  while ((int)ncols < w) ncols <<= 1;
-  if (s == 0) tmem_alloc(tslot, ncols);
+  if (warp == 0) tmem_alloc(tslot, NCOLS);
   fence_before();
   __syncthreads();
   fence_after();
   const uint32_t tmem = *tslot;
-  const uint32_t idesc = make_idesc_bf16(w);
-  const uint32_t sbo = (uint32_t)(w / 8) * 128;
-  const uint32_t trow = tmem + ((uint32_t)(s * 32) << 16);
+  const uint32_t idesc = make_idesc_bf16(W);
+  const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+  const uint32_t rowoff = (uint32_t)((pl >> 3) * (W / 8) * 128 + (pl & 7) * 16) + (uint32_t)(c0 / 8) * 128;
 
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t p = tile * 32 + q;
+  for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+    const int64_t p = (int64_t)tile * 128 + pl;
     const bool valid = p < N;
-    const bool last_tile = tile + gridDim.x >= ntiles;
-    // input layer on CUDA cores (every stream recomputes the point's z)
-    float xh[DIN];
-#pragma unroll
-    for (int i = 0; i < DIN; ++i) xh[i] = bf16r(fmaf(valid ? (float)a.la.X[p * DIN + i] : 0.0f, sc[i], of[i]));
+    const bool last_tile = tile + (int)gridDim.x >= nt;
+    // input layer on CUDA cores: h_0 = t, h_1 = t' z_S, h_2 = t'' z_S^2, h_3 = t' z_tau
     {
-      float* act1 = s_act[1];
-      for (int o0 = 0; o0 < w; o0 += 8) {
-        float hv[8];
+      float xh[DIN];
+#pragma unroll
+      for (int i = 0; i < DIN; ++i) xh[i] = bf16r(fmaf(valid ? (float)a.la.X[p * DIN + i] : 0.0f, sc[i], of[i]));
+      float4* act = s_act[1] + ((size_t)tile * W + c0) * 128 + pl;
+      unsigned char* hb = s_hb[1] + (size_t)tile * 4 * AB + rowoff;
+      unsigned char* sa = sA + rowoff;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        float h[4][8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-          const int o = o0 + j;
+          const int o = c0 + 8 * k + j;
           float z = sB[o];
 #pragma unroll
           for (int i = 0; i < DIN; ++i) z = fmaf(sW1[o * DIN + i], xh[i], z);
           const float tt = tanh_fast(z), d1 = 1.0f - tt * tt;
           const float zS = sW1[o * DIN + 0] * sc[0], zT = sW1[o * DIN + 1] * sc[1];
-          float h, av;
-          if (s == 0) {
-            h = tt;
-            av = tt;
-          } else if (s == 1) {
-            h = d1 * zS;
-            av = zS;
-          } else if (s == 2) {
-            h = -2.0f * tt * d1 * zS * zS;
-            av = 0.0f;
-          } else {
-            h = d1 * zT;
-            av = zT;
-          }
-          hv[j] = h;
-          if (valid) act1[((int64_t)s * w + o) * N + p] = av;
+          h[0][j] = tt;
+          h[1][j] = d1 * zS;
+          h[2][j] = -2.0f * tt * d1 * zS * zS;
+          h[3][j] = d1 * zT;
+          act[(8 * k + j) * 128] = make_float4(tt, zS, 0.0f, zT);
         }
-        *reinterpret_cast<uint4*>(sA + canon_off(t, o0, w)) =
-            make_uint4(pack2(hv[0], hv[1]), pack2(hv[2], hv[3]), pack2(hv[4], hv[5]), pack2(hv[6], hv[7]));
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          const uint4 q = pack8(h[s]);
+          *reinterpret_cast<uint4*>(sa + s * AB + k * 128) = q;
+          *reinterpret_cast<uint4*>(hb + s * AB + k * 128) = q;
+        }
       }
     }
     // square layers on the tensor cores
-    float dot = 0.0f;
+    float dot[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     for (int sq = 0; sq < n_sq; ++sq) {
       const int l = sq + 2;
       if (t == 0 && w_pending) {
@@ -469,90 +269,90 @@ __global__ void __launch_bounds__(128) train_fwd_tc_kernel(FwdArgs a) {
       if (s_fail) break;
       if (t == 0) {
         const uint32_t aa = smem_u32(sA), bb = smem_u32(sW);
-        for (int kk = 0; kk < w / 16; ++kk)
-          mma_bf16(tmem, make_desc(aa + kk * 256, 128, sbo), make_desc(bb + kk * 256, 128, sbo), idesc,
-                   kk > 0 ? 1u : 0u);
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+          for (int kk = 0; kk < W / 16; ++kk)
+            mma_bf16(tmem + (uint32_t)(s * W), make_desc(aa + s * AB + kk * 256, 128, SBO),
+                     make_desc(bb + kk * 256, 128, SBO), idesc, kk > 0 ? 1u : 0u);
         mma_commit(&bar[0]);
       }
       const bool ok = mbar_wait_bounded(&bar[0], ph_mma);
       ph_mma ^= 1u;
-      if (!ok) s_fail = 1;
+      if (!ok) {
+        s_fail = 1;
+        mma_lost = true;
+      }
       fence_after();
-      if (t == 0 && ok && !(last_tile && sq == n_sq - 1)) {
-        const int nxt = sq + 1 < n_sq ? sq + 1 : 0;
-        bulk_load(sW, a.wpack + (size_t)nxt * wbytes, wbytes, &bar[1]);
+      if (t == 0 && ok && (sq + 1 < n_sq || !last_tile)) {
+        bulk_load(sW, wpack + (size_t)(sq + 1 < n_sq ? sq + 1 : 0) * WB, WB, &bar[1]);
         w_pending = true;
       }
       __syncthreads();
       if (s_fail) break;
-      const bool last = sq == n_sq - 1;
-      const float* bl = sB + (l - 1) * w;
-      float* actl = s_act[l];
-      for (int c = 0; c < w; c += 32) {
-        const int buf = (c >> 5) & 1;
-        float v[32];
-        tmem_ld32(trow + (uint32_t)c, v);
-        if (s == 0) {
+      const bool last = l == n_lin - 1;
+      const float* bl = sB + (l - 1) * W;
+      float4* act = s_act[l] + ((size_t)tile * W + c0) * 128 + pl;
+      unsigned char* hb = s_hb[l] + (size_t)tile * 4 * AB + rowoff;
+      unsigned char* sa = sA + rowoff;
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            v[j] = tanh_fast(v[j] + bl[c + j]);
-            xt[(buf * 32 + q) * 33 + j] = v[j];
+      for (int ch = 0; ch < 4; ++ch) {
+        uint32_t r[4][8];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) tmem_ld8_nowait(tl + (uint32_t)(s * W + c0 + 8 * ch), r[s]);
+        tmem_wait_ld();
+        float h[4][8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int o = c0 + 8 * ch + j;
+          const float z1 = __uint_as_float(r[1][j]), z2 = __uint_as_float(r[2][j]), z3 = __uint_as_float(r[3][j]);
+          const float tt = tanh_fast(__uint_as_float(r[0][j]) + bl[o]), d1 = 1.0f - tt * tt;
+          h[0][j] = tt;
+          h[1][j] = d1 * z1;
+          h[2][j] = d1 * z2 - 2.0f * tt * d1 * z1 * z1;
+          h[3][j] = d1 * z3;
+          act[(8 * ch + j) * 128] = make_float4(tt, z1, z2, z3);
+          if (last) {
+#pragma unroll
+            for (int s = 0; s < 4; ++s) dot[s] = fmaf(sWo[o], bf16r(h[s][j]), dot[s]);
           }
-        } else if (s == 1) {
-#pragma unroll
-          for (int j = 0; j < 32; ++j) xs[(buf * 32 + q) * 33 + j] = v[j];
         }
-        __syncthreads();
-        float hv[32];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          float h = v[j];
-          if (s != 0) {
-            const float tt = xt[(buf * 32 + q) * 33 + j], d1 = 1.0f - tt * tt;
-            if (s == 2) {
-              const float zS = xs[(buf * 32 + q) * 33 + j];
-              h = d1 * v[j] - 2.0f * tt * d1 * zS * zS;
-            } else {
-              h = d1 * v[j];
-            }
-          }
-          hv[j] = h;
-        }
-        if (valid) {
-#pragma unroll 8
-          for (int j = 0; j < 32; ++j) actl[((int64_t)s * w + c + j) * N + p] = v[j];
-        }
-        if (last) {
-#pragma unroll
-          for (int j = 0; j < 32; ++j) dot = fmaf(sWo[c + j], bf16r(hv[j]), dot);
-        } else {
-#pragma unroll
-          for (int j = 0; j < 32; j += 8)
-            *reinterpret_cast<uint4*>(sA + canon_off(t, c + j, w)) =
-                make_uint4(pack2(hv[j], hv[j + 1]), pack2(hv[j + 2], hv[j + 3]), pack2(hv[j + 4], hv[j + 5]),
-                           pack2(hv[j + 6], hv[j + 7]));
+        for (int s = 0; s < 4; ++s) {
+          const uint4 q = pack8(h[s]);
+          *reinterpret_cast<uint4*>(hb + s * AB + ch * 128) = q;
+          if (!last) *reinterpret_cast<uint4*>(sa + s * AB + ch * 128) = q;
         }
       }
       fence_before();
     }
     if (s_fail) break;
-    // output streams, loss terms and seeds (the value stream's warp)
-    su[s * 32 + q] = dot + (s == 0 ? bout : 0.0f);
+    // output streams, loss terms and seeds (one thread per point)
+#pragma unroll
+    for (int s = 0; s < 4; ++s) sred[(g * 4 + s) * 128 + pl] = dot[s];
     __syncthreads();
-    if (s == 0 && valid) {
+    if (g == 0 && valid) {
+      double out[4];
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        float u = sred[s * 128 + pl];
+#pragma unroll
+        for (int gg = 1; gg < NG; ++gg) u += sred[(gg * 4 + s) * 128 + pl];
+        out[s] = (double)(s == 0 ? u + bout : u);
+      }
       double xin[8];
 #pragma unroll
       for (int i = 0; i < DIN; ++i) xin[i] = a.la.X[p * DIN + i];
-      const double out[4] = {(double)su[q], (double)su[32 + q], (double)su[64 + q], (double)su[96 + q]};
-      double sqe[3] = {0.0, 0.0, 0.0}, g[4];
-      point_loss(a.la, DIN, xin, a.la.kind[p], out, a.cnt, sqe, g);
+      double sqe[3] = {0.0, 0.0, 0.0}, gs[4];
+      point_loss(a.la, DIN, xin, a.la.kind[p], out, a.cnt, sqe, gs);
+      float* seeds = reinterpret_cast<float*>(a.ws + a.L.seeds);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) a.seeds[(int64_t)k * N + p] = (float)g[k];
+      for (int k = 0; k < 4; ++k) seeds[(int64_t)k * N + p] = (float)gs[k];
       for (int k = 0; k < 3; ++k)
         if (sqe[k] != 0.0) atomicAdd(&s_acc[k], sqe[k]);
     }
   }
   if (t == 0 && w_pending) (void)mbar_wait_bounded(&bar[1], ph_w);
+  if (t == 0 && mma_lost) (void)mbar_wait_bounded(&bar[0], ph_mma ^ 1u);  // GEMMs still in flight
   fence_before();
   __syncthreads();
   fence_after();
@@ -562,56 +362,48 @@ __global__ void __launch_bounds__(128) train_fwd_tc_kernel(FwdArgs a) {
     atomicAdd(a.loss_acc + 2, s_acc[2]);
     if (s_fail) atomicExch(m.status, 6);  // BS_TIMEOUT
   }
-  if (s == 0) tmem_dealloc(tmem, ncols);
+  if (warp == 0) tmem_dealloc(tmem, NCOLS);
 }
 
 // ---------------------------------------------------------------------------
-// Adjoint on the tensor cores, same tile mapping (row 32 s + q = stream s of
-// point q).  From the top hidden layer down: ah_s = W_{l+1}^T dz_{l+1,s} (the
-// output layer's is rank one, on CUDA cores; the others one GEMM with the
-// packed W^T), then the adjoint of the tanh streams of layer l,
-//   t_bar = ah_0 - 2 t' d2_bar - 2 t d1_bar,  d2_bar = ah_2 z_S^2,
-//   d1_bar = ah_1 z_S + ah_2 z_SS + ah_3 z_tau - 2 t d2_bar,
-//   dz_0 = t' t_bar,  dz_1 = t' ah_1 + 2 t'' z_S ah_2,  dz_2 = t' ah_2,  dz_3 = t' ah_3,
-// which needs every stream's ah for the value stream: streams 1..3 form their
-// shares (ah_S z_S, ah_SS z_SS, ah_SS z_S^2, ah_tau z_tau) and publish them
-// through shared memory, so the value stream's warp reads only t.  dz_l goes to global memory (weight gradient)
-// and, in BF16, to the A operand of the next GEMM.
+// Adjoint, same thread mapping.  From the top hidden layer down: ah_s of layer
+// l (rank one from the seeds at the top, else the four stream GEMMs with the
+// packed W_{l+1}^T), the stored (t, z_1, z_2, z_3), then dz_s of layer l in
+// BF16 to the dzb block (weight gradient) and to the next GEMM's operand.
 // ---------------------------------------------------------------------------
 struct BwdArgs {
   MlpDev m;
   int64_t N;
-  const float* act[16];         // act[l], l = 1..n_lin-1
-  float* dz[16];                // dz[l], l = 1..n_lin-1 (written)
-  const float* seeds;           // dz of the output layer: [4][N]
-  const unsigned char* wpackT;  // W_l^T (rows i, K = o), square layers l = 2..n_lin-1
+  unsigned char* ws;
+  TcLayout L;
 };
 
-__global__ void __launch_bounds__(128) train_bwd_tc_kernel(BwdArgs a) {
+template <int W>
+__global__ void __launch_bounds__(4 * W, 1) train_bwd_tc_kernel(BwdArgs a) {
+  constexpr uint32_t WB = W * W * 2, AB = 128 * W * 2, SBO = (W / 8) * 128;
+  constexpr uint32_t NCOLS = tmem_cols_streams(W);
   extern __shared__ __align__(1024) unsigned char smem[];
   const MlpDev& m = a.m;
-  const int w = m.widths[1], n_sq = m.n_lin - 2;
-  const int t = threadIdx.x, s = t >> 5, q = t & 31;
-  const int64_t N = a.N;
-  const uint32_t wbytes = (uint32_t)w * w * 2;
+  const int n_lin = m.n_lin, n_sq = n_lin - 2;
   unsigned char* sW = smem;
-  unsigned char* sA = sW + wbytes;
-  float* xa = reinterpret_cast<float*>(sA + (size_t)128 * w * 2);  // [2][5][32][33] stream partials
-  float* sWo = xa + 2 * 5 * 32 * 33;                                // output weights (BF16-rounded)
-  float* sseed = sWo + w;                                           // [4][32]
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sseed + 128);
+  unsigned char* sA = smem + WB;  // [4][AB]
+  float* sWo = reinterpret_cast<float*>(sA + 4 * AB);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sWo + W);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
   __shared__ int s_fail;
-  __shared__ const float* s_act[16];
-  __shared__ float* s_dz[16];
-  auto XA = [&](int buf, int k, int qq, int j) -> float& { return xa[((buf * 5 + k) * 32 + qq) * 33 + j]; };
-  if (t < 16) {
-    s_act[t] = a.act[t];
-    s_dz[t] = a.dz[t];
-  }
+  __shared__ const float4* s_act[16];
+  __shared__ unsigned char* s_dzb[16];
 
-  for (int o = t; o < w; o += 128) sWo[o] = bf16r(m.p32[m.poff[m.n_lin] + o]);
-  const int64_t ntiles = (N + 31) / 32;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31, g = warp >> 2;
+  const int pl = (warp & 3) * 32 + lane, c0 = g * 32;
+  const int64_t N = a.N;
+  const int nt = a.L.nt;
+  if (t < 16) {
+    const bool hid = t >= 1 && t < n_lin;
+    s_act[t] = hid ? reinterpret_cast<const float4*>(a.ws + a.L.act[t]) : nullptr;
+    s_dzb[t] = hid ? a.ws + a.L.dzb[t] : nullptr;
+  }
+  for (int o = t; o < W; o += blockDim.x) sWo[o] = bf16r(m.p32[m.poff[n_lin] + o]);
   if (t == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
@@ -619,108 +411,84 @@ __global__ void __launch_bounds__(128) train_bwd_tc_kernel(BwdArgs a) {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  bool w_pending = false;
+  bool w_pending = false, mma_lost = false;
   uint32_t ph_w = 0, ph_mma = 0;
-  if (t == 0 && (int64_t)blockIdx.x < ntiles) {
-    bulk_load(sW, a.wpackT + (size_t)(n_sq - 1) * wbytes, wbytes, &bar[1]);
+  const unsigned char* wpackT = a.ws + a.L.pack + (size_t)n_sq * WB;
+  if (t == 0 && (int)blockIdx.x < nt) {
+    bulk_load(sW, wpackT + (size_t)(n_sq - 1) * WB, WB, &bar[1]);
     w_pending = true;
   }
-  uint32_t ncols = 32;
-  while ((int)ncols < w) ncols <<= 1;
-  if (s == 0) tmem_alloc(tslot, ncols);
+  if (warp == 0) tmem_alloc(tslot, NCOLS);
   fence_before();
   __syncthreads();
   fence_after();
   const uint32_t tmem = *tslot;
-  const uint32_t idesc = make_idesc_bf16(w);
-  const uint32_t sbo = (uint32_t)(w / 8) * 128;
-  const uint32_t trow = tmem + ((uint32_t)(s * 32) << 16);
+  const uint32_t idesc = make_idesc_bf16(W);
+  const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+  const uint32_t rowoff = (uint32_t)((pl >> 3) * (W / 8) * 128 + (pl & 7) * 16) + (uint32_t)(c0 / 8) * 128;
+  const float* seeds = reinterpret_cast<const float*>(a.ws + a.L.seeds);
 
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t p = tile * 32 + q;
+  for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+    const int64_t p = (int64_t)tile * 128 + pl;
     const bool valid = p < N;
-    const bool last_tile = tile + gridDim.x >= ntiles;
-    sseed[s * 32 + q] = valid ? bf16r(a.seeds[(int64_t)s * N + p]) : 0.0f;
-    __syncthreads();
-    const float seed = sseed[s * 32 + q];
-    for (int l = m.n_lin - 1; l >= 1; --l) {
-      const float* act = s_act[l];
-      float* dzl = s_dz[l];
-      const bool top = l == m.n_lin - 1;
-      for (int c = 0; c < w; c += 32) {
-        const int buf = (c >> 5) & 1;
-        float ah[32];
+    const bool last_tile = tile + (int)gridDim.x >= nt;
+    float sd[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) sd[s] = valid ? bf16r(seeds[(int64_t)s * N + p]) : 0.0f;
+    for (int l = n_lin - 1; l >= 1; --l) {
+      const bool top = l == n_lin - 1;
+      const float4* act = s_act[l] + ((size_t)tile * W + c0) * 128 + pl;
+      unsigned char* dzb = s_dzb[l] + (size_t)tile * 4 * AB + rowoff;
+      unsigned char* sa = sA + rowoff;
+#pragma unroll
+      for (int ch = 0; ch < 4; ++ch) {
+        float4 av[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) av[j] = __ldg(act + (8 * ch + j) * 128);
+        float ah[4][8];
         if (top) {
 #pragma unroll
-          for (int j = 0; j < 32; ++j) ah[j] = sWo[c + j] * seed;
+          for (int j = 0; j < 8; ++j) {
+            const float wo = sWo[c0 + 8 * ch + j];
+#pragma unroll
+            for (int s = 0; s < 4; ++s) ah[s][j] = wo * sd[s];
+          }
         } else {
-          tmem_ld32(trow + (uint32_t)c, ah);
+          uint32_t r[4][8];
+#pragma unroll
+          for (int s = 0; s < 4; ++s) tmem_ld8_nowait(tl + (uint32_t)(s * W + c0 + 8 * ch), r[s]);
+          tmem_wait_ld();
+#pragma unroll
+          for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) ah[s][j] = __uint_as_float(r[s][j]);
         }
-        // the layer's stored streams at (i, p) this stream needs: t always, z_S
-        // for streams 1 and 2, z_SS for stream 2, z_tau for stream 3 (loads
-        // issued together); each stream's share of the value stream's adjoint
-        // goes to shared memory: 0 ah_S z_S, 1 ah_SS, 2 ah_SS z_S^2,
-        // 3 ah_SS z_SS, 4 ah_tau z_tau
-        float tv[32], zav[32], zbv[32];
+        float dz[4][8];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int64_t i = c + j;
-          tv[j] = valid ? __ldg(act + (0 * (int64_t)w + i) * N + p) : 0.0f;
-          const int ka = s == 3 ? 3 : 1;
-          zav[j] = (valid && s >= 1) ? __ldg(act + ((int64_t)ka * w + i) * N + p) : 0.0f;
-          zbv[j] = (valid && s == 2) ? __ldg(act + (2 * (int64_t)w + i) * N + p) : 0.0f;
-        }
-        if (s == 1) {
-#pragma unroll
-          for (int j = 0; j < 32; ++j) XA(buf, 0, q, j) = ah[j] * zav[j];
-        } else if (s == 2) {
-#pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            XA(buf, 1, q, j) = ah[j];
-            XA(buf, 2, q, j) = ah[j] * zav[j] * zav[j];
-            XA(buf, 3, q, j) = ah[j] * zbv[j];
-          }
-        } else if (s == 3) {
-#pragma unroll
-          for (int j = 0; j < 32; ++j) XA(buf, 4, q, j) = ah[j] * zav[j];
-        }
-        __syncthreads();
-        float dzv[32];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const float tt = tv[j];
+        for (int j = 0; j < 8; ++j) {
+          const float tt = av[j].x, z1 = av[j].y, z2 = av[j].z, z3 = av[j].w;
           const float d1 = 1.0f - tt * tt, d2 = -2.0f * tt * d1;
-          float r;
-          if (s == 0) {
-            const float bar_d2 = XA(buf, 2, q, j);
-            float bar_d1 = XA(buf, 0, q, j) + XA(buf, 3, q, j) + XA(buf, 4, q, j);
-            float bar_t = ah[j];
-            bar_t += -2.0f * d1 * bar_d2;
-            bar_d1 += -2.0f * tt * bar_d2;
-            bar_t += -2.0f * tt * bar_d1;
-            r = d1 * bar_t;
-          } else if (s == 1) {
-            r = ah[j] * d1 + 2.0f * XA(buf, 1, q, j) * d2 * zav[j];
-          } else {
-            r = ah[j] * d1;
-          }
-          dzv[j] = r;
+          const float bd2 = ah[2][j] * z1 * z1;
+          float bd1 = ah[1][j] * z1 + ah[2][j] * z2 + ah[3][j] * z3;
+          float bt = ah[0][j];
+          bt += -2.0f * d1 * bd2;
+          bd1 += -2.0f * tt * bd2;
+          bt += -2.0f * tt * bd1;
+          dz[0][j] = d1 * bt;
+          dz[1][j] = ah[1][j] * d1 + 2.0f * ah[2][j] * d2 * z1;
+          dz[2][j] = ah[2][j] * d1;
+          dz[3][j] = ah[3][j] * d1;
         }
-        if (valid) {
-#pragma unroll 8
-          for (int j = 0; j < 32; ++j) dzl[((int64_t)s * w + c + j) * N + p] = dzv[j];
-        }
-        if (l >= 2) {
 #pragma unroll
-          for (int j = 0; j < 32; j += 8)
-            *reinterpret_cast<uint4*>(sA + canon_off(t, c + j, w)) =
-                make_uint4(pack2(dzv[j], dzv[j + 1]), pack2(dzv[j + 2], dzv[j + 3]), pack2(dzv[j + 4], dzv[j + 5]),
-                           pack2(dzv[j + 6], dzv[j + 7]));
+        for (int s = 0; s < 4; ++s) {
+          const uint4 q = pack8(dz[s]);
+          *reinterpret_cast<uint4*>(dzb + s * AB + ch * 128) = q;
+          if (l >= 2) *reinterpret_cast<uint4*>(sa + s * AB + ch * 128) = q;
         }
       }
       fence_before();
       if (l < 2) break;
-      // ah of layer l-1: W_l^T dz_l on the tensor cores
+      // ah of layer l-1: dz_l W_l (B = W_l^T) on the tensor cores
       if (t == 0 && w_pending) {
         if (mbar_wait_bounded(&bar[1], ph_w)) {
           ph_w ^= 1u;
@@ -736,18 +504,23 @@ __global__ void __launch_bounds__(128) train_bwd_tc_kernel(BwdArgs a) {
       if (s_fail) break;
       if (t == 0) {
         const uint32_t aa = smem_u32(sA), bb = smem_u32(sW);
-        for (int kk = 0; kk < w / 16; ++kk)
-          mma_bf16(tmem, make_desc(aa + kk * 256, 128, sbo), make_desc(bb + kk * 256, 128, sbo), idesc,
-                   kk > 0 ? 1u : 0u);
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+          for (int kk = 0; kk < W / 16; ++kk)
+            mma_bf16(tmem + (uint32_t)(s * W), make_desc(aa + s * AB + kk * 256, 128, SBO),
+                     make_desc(bb + kk * 256, 128, SBO), idesc, kk > 0 ? 1u : 0u);
         mma_commit(&bar[0]);
       }
       const bool ok = mbar_wait_bounded(&bar[0], ph_mma);
       ph_mma ^= 1u;
-      if (!ok) s_fail = 1;
+      if (!ok) {
+        s_fail = 1;
+        mma_lost = true;
+      }
       fence_after();
       if (t == 0 && ok && !(last_tile && l == 2)) {
         const int nxt = l - 1 >= 2 ? l - 3 : n_sq - 1;  // W_{l-1}^T, or the next tile's first
-        bulk_load(sW, a.wpackT + (size_t)nxt * wbytes, wbytes, &bar[1]);
+        bulk_load(sW, wpackT + (size_t)nxt * WB, WB, &bar[1]);
         w_pending = true;
       }
       __syncthreads();
@@ -756,150 +529,418 @@ __global__ void __launch_bounds__(128) train_bwd_tc_kernel(BwdArgs a) {
     if (s_fail) break;
   }
   if (t == 0 && w_pending) (void)mbar_wait_bounded(&bar[1], ph_w);
+  if (t == 0 && mma_lost) (void)mbar_wait_bounded(&bar[0], ph_mma ^ 1u);  // GEMMs still in flight
   fence_before();
   __syncthreads();
   fence_after();
   if (s_fail && t == 0) atomicExch(m.status, 6);  // BS_TIMEOUT
-  if (s == 0) tmem_dealloc(tmem, ncols);
+  if (warp == 0) tmem_dealloc(tmem, NCOLS);
+}
+
+// ---------------------------------------------------------------------------
+// Weight gradient of the square layers: D[o][i] = sum_k A[o][k] B[i][k] over
+// k = (tile, stream, point), A = dz_s (the dzb blocks of layer l), B = h_s (the
+// hb blocks of layer l - 1), both MN-major; M = 128 rows of o (rows o >= w are
+// ignored), N = w, K = 16 points per MMA.  The bias gradient is a second MMA
+// on the value-stream blocks with a constant all-ones B (N = 16) into columns
+// w .. w + 15.  One thread streams the CTA's range of blocks through S shared
+// memory stages with TMA bulk copies and issues the MMAs; the FP32 partial
+// sums go to a buffer that wgrad_sum_kernel adds up in FP64.
+// ---------------------------------------------------------------------------
+struct WgArgs {
+  unsigned char* ws;
+  TcLayout L;
+  int* status;
+};
+
+template <int W>
+struct WgShape {
+  static constexpr uint32_t AB = 128 * W * 2;
+  static constexpr uint32_t PAD = 2048;  // rows o >= w of the last K step read up to 2 KB past a block
+  static constexpr uint32_t SA = AB + PAD, ST = SA + AB;
+  static constexpr int S = (W == 128) ? 3 : 4;
+  static constexpr uint32_t NCOLS = W + 16 <= 64 ? 64 : (W + 16 <= 128 ? 128 : 256);
+};
+
+template <int W>
+__global__ void __launch_bounds__(128) train_wgrad_tc_kernel(WgArgs a) {
+  using G = WgShape<W>;
+  constexpr int S = G::S;
+  constexpr uint32_t KG = W * 16;  // bytes between 8-point groups of a block
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* ones = smem + S * G::ST;  // 16 x 16 BF16 ones
+  uint64_t* full = reinterpret_cast<uint64_t*>(ones + 512);
+  uint64_t* empty = full + S;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(empty + S);
+  __shared__ int s_fail, s_bias;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int sq = blockIdx.y, l = sq + 2;
+  const int total = 4 * a.L.nt;
+  const int per = (total + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int c0 = (int)blockIdx.x * per;
+  const int cnt = c0 < total ? (c0 + per < total ? per : total - c0) : 0;
+  const unsigned char* A = a.ws + a.L.dzb[l] + (size_t)c0 * G::AB;
+  const unsigned char* B = a.ws + a.L.hb[l - 1] + (size_t)c0 * G::AB;
+  for (int i = t; i < 128; i += 128) reinterpret_cast<uint32_t*>(ones)[i] = 0x3F803F80u;
+  if (t == 0) {
+    for (int st = 0; st < S; ++st) {
+      mbar_init(&full[st], 1);
+      mbar_init(&empty[st], 1);
+    }
+    s_fail = 0;
+    s_bias = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(tslot, G::NCOLS);
+  fence_proxy_async();
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tslot;
+  if (t == 0 && cnt > 0) {
+    const uint32_t idm = make_idesc_bf16_major(W, true, true);
+    const uint32_t idb = make_idesc_bf16_major(16, true, false);
+    const uint64_t dones = make_desc(smem_u32(ones), 128, 256);
+    auto load = [&](int n) {
+      unsigned char* st = smem + (n % S) * G::ST;
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&full[n % S])),
+                   "r"(2 * G::AB)
+                   : "memory");
+      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                       smem_u32(st)),
+                   "l"(A + (size_t)n * G::AB), "r"(G::AB), "r"(smem_u32(&full[n % S]))
+                   : "memory");
+      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                       smem_u32(st + G::SA)),
+                   "l"(B + (size_t)n * G::AB), "r"(G::AB), "r"(smem_u32(&full[n % S]))
+                   : "memory");
+    };
+    const int pre = cnt < S ? cnt : S;
+    for (int n = 0; n < pre; ++n) load(n);
+    int loaded = pre, landed = 0, committed = 0;
+    bool fail = false, bias = false;
+    for (int n = 0; n < cnt; ++n) {
+      const int st = n % S;
+      if (!mbar_wait_bounded(&full[st], (uint32_t)(n / S) & 1u)) {
+        fail = true;
+        break;
+      }
+      landed = n + 1;
+      fence_after();
+      const bool value = ((c0 + n) & 3) == 0;
+      const uint32_t aa = smem_u32(smem + st * G::ST), bb = aa + G::SA;
+#pragma unroll
+      for (int kk = 0; kk < 8; ++kk) {
+        const uint64_t da = make_desc(aa + kk * 2 * KG, KG, 128);
+        mma_bf16(tmem, da, make_desc(bb + kk * 2 * KG, KG, 128), idm, (n > 0 || kk > 0) ? 1u : 0u);
+        if (value) mma_bf16(tmem + W, da, dones, idb, (bias || kk > 0) ? 1u : 0u);
+      }
+      if (value) bias = true;
+      mma_commit(&empty[st]);
+      committed = n + 1;
+      const int pm = n - 1;  // refill the previous chunk's stage
+      if (pm >= 0 && pm + S < cnt) {
+        if (!mbar_wait_bounded(&empty[pm % S], (uint32_t)(pm / S) & 1u)) {
+          fail = true;
+          break;
+        }
+        load(pm + S);
+        loaded = pm + S + 1;
+      }
+    }
+    // the last commit covers every MMA issued before it
+    if (committed > 0 &&
+        !mbar_wait_bounded(&empty[(committed - 1) % S], (uint32_t)((committed - 1) / S) & 1u))
+      fail = true;
+    // after a failure: copies still in flight land before the stages are released
+    for (int n = landed; fail && n < loaded; ++n) (void)mbar_wait_bounded(&full[n % S], (uint32_t)(n / S) & 1u);
+    s_fail = fail ? 1 : 0;
+    s_bias = bias ? 1 : 0;
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const int o = warp * 32 + lane;  // accumulator lane = row o
+  float* dst = reinterpret_cast<float*>(a.ws + a.L.partial) +
+               ((size_t)(sq * (int)gridDim.x + (int)blockIdx.x) * W + (o < W ? o : 0)) * (W + 1);
+  const bool have = cnt > 0 && !s_fail;
+  const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll
+  for (int cc = 0; cc < W; cc += 16) {
+    uint32_t r[16];
+    tmem_ld16_nowait(tl + (uint32_t)cc, r);
+    tmem_wait_ld();
+    if (o < W) {
+#pragma unroll
+      for (int e = 0; e < 16; ++e) dst[cc + e] = have ? __uint_as_float(r[e]) : 0.0f;
+    }
+  }
+  {
+    uint32_t r[8];
+    tmem_ld8_nowait(tl + (uint32_t)W, r);
+    tmem_wait_ld();
+    if (o < W) dst[W] = (have && s_bias) ? __uint_as_float(r[0]) : 0.0f;
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (s_fail && t == 0) atomicExch(a.status, 6);  // BS_TIMEOUT
+  if (warp == 0) tmem_dealloc(tmem, G::NCOLS);
+}
+
+// gW[o][i] and gb[o] of square layer blockIdx.z + 2: sums over the layer's
+// CTAs of the partial sums; blockIdx.y takes one group of CTAs and adds its
+// sum atomically in FP64 (the gradient starts at zero).
+__global__ void wgrad_sum_kernel(MlpDev m, const float* __restrict__ partial, int ny, double* __restrict__ grad) {
+  const int w = m.widths[1], sq = blockIdx.z;
+  const int64_t wc = (int64_t)w * (w + 1);
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= wc) return;
+  const int o = (int)(q / (w + 1)), i = (int)(q % (w + 1));
+  const int y0 = (int)((int64_t)ny * blockIdx.y / gridDim.y), y1 = (int)((int64_t)ny * (blockIdx.y + 1) / gridDim.y);
+  float acc = 0.0f;
+  for (int y = y0; y < y1; ++y) acc += partial[((int64_t)sq * ny + y) * wc + q];
+  double* gW = grad + m.poff[sq + 2];
+  atomicAdd(i < w ? gW + (int64_t)o * w + i : gW + (int64_t)w * w + o, (double)acc);
+}
+
+// Input layer (d_in -> w): its input streams are the mapped inputs h_0 = x^ and
+// the constants h_1 = sc_S e_S, h_3 = sc_tau e_tau (h_2 = 0), so
+//   dL/dW_1[o][i] = sum_p dz_0[o][p] x^_i(p) + [i = 0] sc_S sum_p dz_1[o][p]
+//                   + [i = 1] sc_tau sum_p dz_3[o][p],   dL/db_1[o] = sum_p dz_0[o][p],
+// from the BF16 dzb blocks of layer 1, x^ rounded to BF16 like a GEMM operand.
+// Thread (og, pq) = neurons 8 og .. 8 og + 7, points pq, pq + 8, ... of a tile.
+template <int DIN, int W>
+__global__ void __launch_bounds__(W) grad_input_kernel(MlpDev m, const double* __restrict__ X, int64_t N,
+                                                       const unsigned char* __restrict__ dzb1,
+                                                       double* __restrict__ grad, int nt) {
+  constexpr uint32_t AB = 128 * W * 2;
+  const int t = threadIdx.x, og = t >> 3, pq = t & 7;
+  double sc[DIN], lo[DIN];
+#pragma unroll
+  for (int i = 0; i < DIN; ++i) {
+    sc[i] = 2.0 / (m.hi[i] - m.lo[i]);
+    lo[i] = m.lo[i];
+  }
+  float ax[8][DIN], a0[8], a1[8], a3[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    a0[e] = a1[e] = a3[e] = 0.0f;
+#pragma unroll
+    for (int i = 0; i < DIN; ++i) ax[e][i] = 0.0f;
+  }
+  for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+    const unsigned char* blk = dzb1 + (size_t)tile * 4 * AB;
+    for (int pl = pq; pl < 128; pl += 8) {
+      const int64_t p = (int64_t)tile * 128 + pl;
+      if (p >= N) break;
+      const uint32_t off = canon_off(pl, og * 8, W);
+      float g0[8], g1[8], g3[8];
+      unpack8(__ldg(reinterpret_cast<const uint4*>(blk + off)), g0);
+      unpack8(__ldg(reinterpret_cast<const uint4*>(blk + AB + off)), g1);
+      unpack8(__ldg(reinterpret_cast<const uint4*>(blk + 3 * AB + off)), g3);
+      float xh[DIN];
+#pragma unroll
+      for (int i = 0; i < DIN; ++i) xh[i] = bf16r((float)(sc[i] * (X[p * DIN + i] - lo[i]) - 1.0));
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        a0[e] += g0[e];
+        a1[e] += g1[e];
+        a3[e] += g3[e];
+#pragma unroll
+        for (int i = 0; i < DIN; ++i) ax[e][i] = fmaf(g0[e], xh[i], ax[e][i]);
+      }
+    }
+  }
+  auto red = [](float v) {
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    v += __shfl_xor_sync(0xffffffffu, v, 4);
+    return v;
+  };
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    a0[e] = red(a0[e]);
+    a1[e] = red(a1[e]);
+    a3[e] = red(a3[e]);
+#pragma unroll
+    for (int i = 0; i < DIN; ++i) ax[e][i] = red(ax[e][i]);
+  }
+  if (pq == 0) {
+    double* g = grad + m.poff[1];
+    const double sS = (double)bf16r((float)sc[0]), sT = (double)bf16r((float)sc[1]);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int o = og * 8 + e;
+#pragma unroll
+      for (int i = 0; i < DIN; ++i) {
+        double v = (double)ax[e][i];
+        if (i == 0) v += sS * (double)a1[e];
+        if (i == 1) v += sT * (double)a3[e];
+        atomicAdd(g + (int64_t)o * DIN + i, v);
+      }
+      atomicAdd(g + (int64_t)W * DIN + o, (double)a0[e]);
+    }
+  }
+}
+
+// Output layer (w -> 1): dL/dW_L[i] = sum over streams and points of seed_s h_s[i]
+// with h_s from the BF16 hb blocks of the top hidden layer, dL/db_L = sum of
+// seed_0; seeds rounded to BF16 like the adjoint's.  Thread mapping as above.
+template <int W>
+__global__ void __launch_bounds__(W) grad_output_kernel(MlpDev m, int64_t N, const unsigned char* __restrict__ hbtop,
+                                                        const float* __restrict__ seeds, double* __restrict__ grad,
+                                                        int nt) {
+  constexpr uint32_t AB = 128 * W * 2;
+  const int t = threadIdx.x, ig = t >> 3, pq = t & 7;
+  float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0}, ab = 0.0f;
+  for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+    const unsigned char* blk = hbtop + (size_t)tile * 4 * AB;
+    for (int pl = pq; pl < 128; pl += 8) {
+      const int64_t p = (int64_t)tile * 128 + pl;
+      if (p >= N) break;
+      const uint32_t off = canon_off(pl, ig * 8, W);
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        const float sd = bf16r(__ldg(seeds + (int64_t)s * N + p));
+        float h[8];
+        unpack8(__ldg(reinterpret_cast<const uint4*>(blk + s * AB + off)), h);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) acc[e] = fmaf(sd, h[e], acc[e]);
+        if (s == 0 && ig == 0) ab += sd;
+      }
+    }
+  }
+  auto red = [](float v) {
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    v += __shfl_xor_sync(0xffffffffu, v, 4);
+    return v;
+  };
+#pragma unroll
+  for (int e = 0; e < 8; ++e) acc[e] = red(acc[e]);
+  ab = red(ab);
+  if (pq == 0) {
+    double* g = grad + m.poff[m.n_lin];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) atomicAdd(g + ig * 8 + e, (double)acc[e]);
+    if (ig == 0) atomicAdd(g + W, (double)ab);
+  }
+}
+
+int resident_per_sm(size_t smem, int threads, uint32_t tmem_cols) {
+  int dev = 0, sm_smem = 0, reserved = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  int per = (int)((size_t)sm_smem / (smem + 1024 + (size_t)reserved));
+  if (per > 2048 / threads) per = 2048 / threads;
+  if (per > (int)(512 / tmem_cols)) per = (int)(512 / tmem_cols);
+  return per < 1 ? 1 : per;
+}
+
+template <int DIN, int W>
+cudaError_t run_train_tc(const MlpDev& m, const LossArgs& la, unsigned char* ws, const TcLayout& L,
+                         const unsigned long long* cnt, double* loss_acc, double* grad, cudaStream_t s) {
+  constexpr uint32_t WB = W * W * 2, AB = 128 * W * 2;
+  const int n_lin = m.n_lin, n_sq = n_lin - 2, nsm = sm_count();
+  cudaError_t e;
+  {
+    FwdArgs a{m, la, ws, L, cnt, loss_acc};
+    const size_t smem =
+        WB + 4 * AB + sizeof(float) * ((size_t)W * DIN + (size_t)(n_lin - 1) * W + W + (W / 32) * 4 * 128) + 64;
+    auto kern = train_fwd_tc_kernel<DIN, W>;
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+      return e;
+    const int64_t cap = (int64_t)nsm * resident_per_sm(smem, 4 * W, tmem_cols_streams(W));
+    kern<<<(unsigned)(L.nt < cap ? L.nt : cap), 4 * W, smem, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  {
+    BwdArgs a{m, la.N, ws, L};
+    const size_t smem = WB + 4 * AB + sizeof(float) * W + 64;
+    auto kern = train_bwd_tc_kernel<W>;
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+      return e;
+    const int64_t cap = (int64_t)nsm * resident_per_sm(smem, 4 * W, tmem_cols_streams(W));
+    kern<<<(unsigned)(L.nt < cap ? L.nt : cap), 4 * W, smem, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  {
+    // all of the opt-in shared memory: a descriptor read past the stages stays inside it
+    auto kern = train_wgrad_tc_kernel<W>;
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa{};
+    if ((e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess) return e;
+    using G = WgShape<W>;
+    const size_t need = (size_t)G::S * G::ST + 512 + 2 * G::S * 8 + 16;
+    const size_t avail = (size_t)optin - fa.sharedSizeBytes;
+    if (need > avail) return cudaErrorInvalidValue;
+    const size_t smem = avail;
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+      return e;
+    kern<<<dim3((unsigned)L.ny, (unsigned)n_sq), 128, smem, s>>>(WgArgs{ws, L, m.status});
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int64_t wc = (int64_t)W * (W + 1);
+    const int groups = L.ny < 8 ? L.ny : 8;
+    wgrad_sum_kernel<<<dim3((unsigned)((wc + 255) / 256), (unsigned)groups, (unsigned)n_sq), 256, 0, s>>>(
+        m, reinterpret_cast<const float*>(ws + L.partial), L.ny, grad);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  const int ge = L.nt < 4 * nsm ? L.nt : 4 * nsm;
+  grad_input_kernel<DIN, W><<<ge, W, 0, s>>>(m, la.X, la.N, ws + L.dzb[1], grad, L.nt);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  grad_output_kernel<W><<<ge, W, 0, s>>>(m, la.N, ws + L.hb[n_lin - 1], reinterpret_cast<const float*>(ws + L.seeds),
+                                         grad, L.nt);
+  return cudaGetLastError();
+}
+
+template <int DIN>
+cudaError_t run_train_tc_w(const MlpDev& m, const LossArgs& la, unsigned char* ws, const TcLayout& L,
+                           const unsigned long long* cnt, double* loss_acc, double* grad, cudaStream_t s) {
+  switch (m.widths[1]) {
+    case 32:
+      return run_train_tc<DIN, 32>(m, la, ws, L, cnt, loss_acc, grad, s);
+    case 64:
+      return run_train_tc<DIN, 64>(m, la, ws, L, cnt, loss_acc, grad, s);
+    case 96:
+      return run_train_tc<DIN, 96>(m, la, ws, L, cnt, loss_acc, grad, s);
+    case 128:
+      return run_train_tc<DIN, 128>(m, la, ws, L, cnt, loss_acc, grad, s);
+  }
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace
 
-cudaError_t launch_train_bwd_tc(const MlpDev& m, int64_t N, const float* const* act, float* const* dz,
-                                const float* seeds, const unsigned char* wpack, cudaStream_t s) {
-  if (N <= 0) return cudaSuccess;
-  const int w = m.widths[1], n_sq = m.n_lin - 2;
-  BwdArgs a{};
-  a.m = m;
-  a.N = N;
-  for (int l = 0; l < 16; ++l) {
-    a.act[l] = act[l];
-    a.dz[l] = dz[l];
-  }
-  a.seeds = seeds;
-  a.wpackT = wpack + (size_t)n_sq * w * w * 2;
-  const size_t smem = (size_t)w * w * 2 + (size_t)128 * w * 2 + sizeof(float) * (10 * 32 * 33 + (size_t)w + 128) + 64;
-  cudaError_t e = cudaFuncSetAttribute(train_bwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(train_bwd_tc_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) !=
-      cudaSuccess)
-    return e;
-  int dev = 0, nsm = 148, sm_smem = 0, reserved = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-  cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
-  int per_sm = (int)((size_t)sm_smem / (smem + 2048 + (size_t)reserved));
-  if (per_sm < 1) per_sm = 1;
-  if (per_sm > 3) per_sm = 3;
-  const int64_t ntiles = (N + 31) / 32;
-  const int64_t grid = ntiles < (int64_t)nsm * per_sm ? ntiles : (int64_t)nsm * per_sm;
-  train_bwd_tc_kernel<<<(unsigned)grid, 128, smem, s>>>(a);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_grad_edges_tc(const MlpDev& m, const double* X, int64_t N, const float* dz1, const float* act_top,
-                                 const float* seeds, double* grad, cudaStream_t s) {
-  if (N <= 0) return cudaSuccess;
-  const int w = m.widths[1];
-  const int64_t chunk = 8192;
-  const unsigned nc = (unsigned)((N + chunk - 1) / chunk);
-  if (m.d_in == 2)
-    grad_input_kernel<2><<<dim3(w, nc), 128, 0, s>>>(m, X, N, dz1, grad, chunk);
-  else
-    grad_input_kernel<5><<<dim3(w, nc), 128, 0, s>>>(m, X, N, dz1, grad, chunk);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  double* gL = grad + m.poff[m.n_lin];
-  grad_output_kernel<<<dim3((w + 1 + 3) / 4, nc), 128, 0, s>>>(act_top, seeds, w, N, gL, gL + w, chunk);
-  return cudaGetLastError();
-}
-
 bool train_tc_supported(const MlpDev& m) {
-  return wgrad_tc_supported(m) && m.widths[1] <= 128 && (m.d_in == 2 || m.d_in == 5);
-}
-
-size_t train_tc_pack_bytes(const MlpDev& m) {
-  if (!train_tc_supported(m)) return 0;
-  return 2 * (size_t)(m.n_lin - 2) * m.widths[1] * m.widths[1] * 2;
-}
-
-cudaError_t launch_train_fwd_tc(const MlpDev& m, const LossArgs& la, float* const* act, float* seeds,
-                                unsigned char* wpack, const unsigned long long* cnt, double* loss_acc,
-                                cudaStream_t s) {
-  if (la.N <= 0) return cudaSuccess;
-  if (((uintptr_t)wpack & 15) != 0) return cudaErrorInvalidValue;  // TMA source alignment
-  const int w = m.widths[1], n_sq = m.n_lin - 2;
-  unsigned char* wpackT = wpack + (size_t)n_sq * w * w * 2;
-  pack_train_kernel<<<148, 256, 0, s>>>(m, w, wpack, wpackT);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  FwdArgs a{};
-  a.m = m;
-  a.la = la;
-  for (int l = 0; l < 16; ++l) a.act[l] = act[l];
-  a.seeds = seeds;
-  a.wpack = wpack;
-  a.cnt = cnt;
-  a.loss_acc = loss_acc;
-  const size_t smem = (size_t)w * w * 2 + (size_t)128 * w * 2 +
-                      sizeof(float) * (4 * 32 * 33 + (size_t)w * m.d_in + (size_t)(m.n_lin - 1) * w + w + 128) + 64;
-  auto kern = m.d_in == 2 ? train_fwd_tc_kernel<2> : train_fwd_tc_kernel<5>;
-  if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-    return e;
-  if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess) return e;
-  int dev = 0, nsm = 148, sm_smem = 0, reserved = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-  cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
-  int per_sm = (int)((size_t)sm_smem / (smem + 2048 + (size_t)reserved));
-  if (per_sm < 1) per_sm = 1;
-  if (per_sm > 3) per_sm = 3;  // tensor memory: <= 128 columns each
-  const int64_t ntiles = (la.N + 31) / 32;
-  const int64_t grid = ntiles < (int64_t)nsm * per_sm ? ntiles : (int64_t)nsm * per_sm;
-  kern<<<(unsigned)grid, 128, smem, s>>>(a);
-  return cudaGetLastError();
-}
-
-bool wgrad_tc_supported(const MlpDev& m) {
-  if (m.n_lin < 3) return false;
+  if (m.n_lin < 3 || m.n_lin > 16 || (m.d_in != 2 && m.d_in != 5)) return false;
   const int w = m.widths[1];
-  if (w < 32 || w > 256 || (w % 32) != 0) return false;
+  if (w != 32 && w != 64 && w != 96 && w != 128) return false;
   for (int l = 1; l < m.n_lin; ++l)
     if (m.widths[l] != w) return false;
-  return true;
+  return m.widths[m.n_lin] == 1;
 }
 
-size_t wgrad_tc_partial_bytes(const MlpDev& m, int64_t N) {
-  if (!wgrad_tc_supported(m) || N <= 0) return 0;
-  int ot, pc, ny;
-  wgrad_grid(m.widths[1], N, &ot, &pc, &ny);
-  return (size_t)ny * m.widths[1] * (m.widths[1] + 1) * sizeof(float);
+size_t train_tc_workspace_bytes(const MlpDev& m, int64_t N) {
+  if (!train_tc_supported(m) || N <= 0) return 0;
+  return tc_layout(m, N).total;
 }
 
-cudaError_t launch_wgrad_tc(const MlpDev& m, int64_t N, const float* dz, const float* act, double* gW, double* gb,
-                            float* partial, cudaStream_t s) {
-  if (N <= 0) return cudaSuccess;
-  const int w = m.widths[1];
-  int ot, pc, ny;
-  wgrad_grid(w, N, &ot, &pc, &ny);
-  const int nbr = wgrad_rows_b(w);
-  WgArgs a{dz, act, N, w, nbr, (int)((N + kChunk - 1) / kChunk), pc, (N % 4) == 0 ? 1 : 0, partial, m.status};
-  const size_t smem = wgrad_smem_bytes(w);
-  cudaError_t e = cudaFuncSetAttribute(wgrad_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+cudaError_t launch_train_tc(const MlpDev& m, const LossArgs& la, unsigned char* ws, const unsigned long long* cnt,
+                            double* loss_acc, double* grad, cudaStream_t s) {
+  if (la.N <= 0) return cudaSuccess;
+  if (!train_tc_supported(m) || ((uintptr_t)ws & 255) != 0) return cudaErrorInvalidValue;
+  const TcLayout L = tc_layout(m, la.N);
+  const int w = m.widths[1], n_sq = m.n_lin - 2;
+  unsigned char* wpack = ws + L.pack;
+  pack_train_kernel<<<148, 256, 0, s>>>(m, w, wpack, wpack + (size_t)n_sq * w * w * 2);
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  wgrad_tc_kernel<<<dim3(ot, ny), 128, smem, s>>>(a);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  const int64_t wc = (int64_t)w * (w + 1);
-  const int groups = ny < 8 ? ny : 8;
-  wgrad_sum_kernel<<<dim3((unsigned)((wc + 255) / 256), groups), 256, 0, s>>>(partial, ny, w, nbr > w, gW, gb);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if (nbr == w) {
-    bias_grad_kernel<<<w, 128, 0, s>>>(dz, N, gb);
-    e = cudaGetLastError();
-  }
-  return e;
+  return m.d_in == 2 ? run_train_tc_w<2>(m, la, ws, L, cnt, loss_acc, grad, s)
+                     : run_train_tc_w<5>(m, la, ws, L, cnt, loss_acc, grad, s);
 }
 
 }  // namespace bsp

@@ -180,6 +180,45 @@ def test_tensor_core_eval_shapes_and_ragged_tiles(B, orc, w, n_hidden, d_in, pre
         assert _rel(u, ref) <= TOL_EVAL[prec], (n, _rel(u, ref))
 
 
+def _param_blocks(widths):
+    out, off = [], 0
+    for l in range(1, len(widths)):
+        nw = widths[l] * widths[l - 1]
+        out.append((f"W{l}", off, off + nw))
+        off += nw
+        out.append((f"b{l}", off, off + widths[l]))
+        off += widths[l]
+    return out
+
+
+@pytest.mark.parametrize(
+    "widths",
+    [[2, 32, 32, 1], [2, 64, 64, 64, 64, 1], [5, 96, 96, 96, 1], [2] + [128] * 6 + [1], [5] + [128] * 6 + [1]],
+    ids=["2-2x32", "2-4x64", "5-3x96", "2-6x128", "5-6x128"],
+)
+def test_tensor_core_gradient_every_layer(B, orc, widths):
+    # each weight matrix and bias vector of the BF16 tensor-core gradient on its
+    # own against the FP64 oracle, so that a lost stream, layer or bias term
+    # cannot hide under the whole-vector bound.  Bound: BF16 operands round to
+    # 8 significant bits (unit roundoff 2^-9 ~ 2e-3); every gradient entry is a
+    # sum of products of two rounded operands whose inputs passed through up to
+    # six rounded layers; 2e-2 ~ 10 roundoffs (measured worst case 7e-3).
+    m, om = _model(B, orc, widths, 8)
+    for n_int in (1500, 6000):
+        X, kind, prob, sok = _loss_case(widths, n_int, 128, 128, 4 + n_int)
+        terms, grad = orc.pinn_loss_grad(om, X, kind, prob["K"], prob["sigma"], prob["r"], prob["Smax"], sok)
+        l3, g = m.loss_grad(torch.tensor(X, device="cuda"), torch.tensor(kind, device="cuda"), prob, sok, prec=B.BF16)
+        g = g.cpu().numpy()
+        assert m.device_status() == B.BS_OK
+        for name, a, b in _param_blocks(widths):
+            err = np.abs(g[a:b] - grad[a:b]).max() / max(np.abs(grad[a:b]).max(), 1e-300)
+            assert err <= 2e-2, (n_int, name, err)
+        # the residual term cancels (u_tau against the S-derivative terms): the
+        # per-term bound of the other BF16 loss tests
+        for c in range(3):
+            assert abs(l3[c].item() - terms[c]) <= 5e-2 * abs(terms[c]), (c, l3[c].item(), terms[c])
+
+
 @pytest.mark.parametrize("arch", ["2-4x64", "2-6x128", "5-6x128"])
 def test_tensor_core_training_ragged_batches(B, orc, arch):
     # BF16 loss and gradient through the tensor-core forward, adjoint and weight
