@@ -21,14 +21,18 @@
 //   act[l]  float4 [NT][w][128]: (t, z_1, z_2, z_3) of hidden layer l at
 //           (neuron, point); the adjoint reads it with one 16-byte load per
 //           neuron, 512 contiguous bytes per warp;
-//   hb[l]   BF16 [NT][4][128 x w]: h_s of hidden layer l;
-//   dzb[l]  BF16 [NT][4][128 x w]: dz_s of hidden layer l.
+//   hb[l]   BF16 [NT][4][128 x w]: h_s of hidden layer l (l < n_lin - 1);
+//   dzb[l]  BF16 [NT][4][128 x w]: dz_s of hidden layer l (l >= 2).
 // The BF16 blocks keep the GEMM operand layout (rows = points, K = neurons,
 // no-swizzle core matrices), written by the forward / adjoint epilogues with
 // the same 16-byte stores that fill the next GEMM's operand; the weight
 // gradient copies them back with TMA bulk loads and reads them as MN-major
 // operands (the neuron index contiguous), so no transpose is ever formed.
-// The input layer (d_in -> w) and the output layer (w -> 1) run on CUDA cores.
+// The edge layers' gradients are small GEMMs on the same operands while they
+// are in shared memory: the output layer's (w -> 1) in the forward, the top
+// layer's h_s against a tile of the BF16 loss seeds; the input layer's
+// (d_in -> w) in the adjoint, dz_s of layer 1 against a tile of the mapped
+// inputs and constant rows.  The input layer's forward runs on CUDA cores.
 // Every wait is bounded; on expiry a kernel records BS_TIMEOUT and stops.
 #include <cuda_bf16.h>
 
@@ -46,7 +50,7 @@ using namespace tc;
 namespace {
 
 struct TcLayout {
-  size_t act[16], hb[16], dzb[16];  // byte offsets, hidden layers l = 1..n_lin-1
+  size_t act[16], hb[16], dzb[16];  // byte offsets by hidden layer l
   size_t seeds;                     // float [4][N]: dLoss/d(u, u_S, u_SS, u_tau)
   size_t partial;                   // float [n_sq][ny][w][w + 1]: weight-gradient partial sums
   size_t pack;                      // BF16 square layers: W_l then W_l^T
@@ -77,8 +81,8 @@ TcLayout tc_layout(const MlpDev& m, int64_t N) {
     return r;
   };
   for (int l = 1; l < m.n_lin; ++l) L.act[l] = take((size_t)nt * w * 128 * 16);
-  for (int l = 1; l < m.n_lin; ++l) L.hb[l] = take((size_t)nt * 4 * 128 * w * 2);
-  for (int l = 1; l < m.n_lin; ++l) L.dzb[l] = take((size_t)nt * 4 * 128 * w * 2);
+  for (int l = 1; l < m.n_lin - 1; ++l) L.hb[l] = take((size_t)nt * 4 * 128 * w * 2);
+  for (int l = 2; l < m.n_lin; ++l) L.dzb[l] = take((size_t)nt * 4 * 128 * w * 2);
   L.seeds = take((size_t)4 * (size_t)N * sizeof(float));
   // one wave of weight-gradient CTAs (one per SM) over all square layers
   int ny = sm_count() / (n_sq > 0 ? n_sq : 1);
@@ -102,15 +106,6 @@ __device__ __forceinline__ uint4 pack8(const float* v) {
   return make_uint4(pack2(v[0], v[1]), pack2(v[2], v[3]), pack2(v[4], v[5]), pack2(v[6], v[7]));
 }
 
-__device__ __forceinline__ void unpack8(uint4 q, float (&v)[8]) {
-  const uint32_t u[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    v[2 * k] = __uint_as_float(u[k] << 16);
-    v[2 * k + 1] = __uint_as_float(u[k] & 0xFFFF0000u);
-  }
-}
-
 // Pack the square layers: W_l (rows o, K = i) for the forward and W_l^T (rows
 // i, K = o) for the adjoint, BF16 core-matrix layout.
 __global__ void pack_train_kernel(MlpDev m, int w, unsigned char* fwd, unsigned char* bwd) {
@@ -124,6 +119,25 @@ __global__ void pack_train_kernel(MlpDev m, int w, unsigned char* fwd, unsigned 
     *reinterpret_cast<__nv_bfloat16*>(fwd + sq * per * 2 + canon_off(o, i, w)) = v;
     *reinterpret_cast<__nv_bfloat16*>(bwd + sq * per * 2 + canon_off(i, o, w)) = v;
   }
+}
+
+// Edge-layer GEMMs: D[j][n] = sum over the tile's 128 points of A[j][p] B[n][p]
+// with A a 128 x w operand block read MN-major (rows j = neurons) and B a
+// 16-row tile (rows n, K = points) in K-major core matrices: element (n, p) at
+//   ((n / 8) * 16 + p / 8) * 128 + (n % 8) * 16 + (p % 8) * 2.
+constexpr uint32_t kTileB = 16 * 128 * 2;
+__device__ __forceinline__ uint32_t tile_off(int n, int p) {
+  return (uint32_t)(((n >> 3) * 16 + (p >> 3)) * 128 + (n & 7) * 16 + (p & 7) * 2);
+}
+
+// Issue the 8 K = 16 steps of one edge GEMM (accumulating unless first).
+template <int W>
+__device__ __forceinline__ void edge_mma(uint32_t d_tmem, uint32_t a_smem, uint32_t b_smem, bool first) {
+  const uint32_t idesc = make_idesc_bf16_major(16, true, false);
+#pragma unroll
+  for (int kk = 0; kk < 8; ++kk)
+    mma_bf16(d_tmem, make_desc(a_smem + kk * 2 * (W * 16), W * 16, 128), make_desc(b_smem + kk * 256, 128, 2048),
+             idesc, (!first || kk > 0) ? 1u : 0u);
 }
 
 __host__ __device__ constexpr uint32_t tmem_cols_streams(int w) {
@@ -145,6 +159,7 @@ struct FwdArgs {
   TcLayout L;
   const unsigned long long* cnt;
   double* loss_acc;
+  double* grad;
 };
 
 template <int DIN, int W>
@@ -161,7 +176,8 @@ __global__ void __launch_bounds__(4 * W, 1) train_fwd_tc_kernel(FwdArgs a) {
   float* sB = sW1 + W * DIN;                                        // hidden biases, (n_lin - 1) x W
   float* sWo = sB + (n_lin - 1) * W;                                // output weights, BF16-rounded
   float* sred = sWo + W;                                            // [NG][4][128] output partial sums
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sred + NG * 4 * 128);  // [0] GEMMs done, [1] weights landed
+  unsigned char* sSeed = reinterpret_cast<unsigned char*>(sred + NG * 4 * 128);  // [4] seed tiles (row 0)
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sSeed + 4 * kTileB);  // [0] GEMMs done, [1] weights landed
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
   __shared__ int s_fail;
   __shared__ double s_acc[3];
@@ -181,7 +197,9 @@ __global__ void __launch_bounds__(4 * W, 1) train_fwd_tc_kernel(FwdArgs a) {
   for (int l = 1; l < n_lin; ++l)
     for (int o = t; o < W; o += blockDim.x) sB[(l - 1) * W + o] = m.p32[m.poff[l] + (int64_t)W * m.widths[l - 1] + o];
   for (int o = t; o < W; o += blockDim.x) sWo[o] = bf16r(m.p32[m.poff[n_lin] + o]);
+  for (int i = t; i < (int)(4 * kTileB / 16); i += blockDim.x) reinterpret_cast<uint4*>(sSeed)[i] = make_uint4(0, 0, 0, 0);
   const float bout = m.p32[m.poff[n_lin] + W];
+  float dwo = 0.0f, dbo = 0.0f;  // output-layer gradient: row pl of the edge GEMM, and sum of seed_0
   float sc[DIN], of[DIN];
 #pragma unroll
   for (int i = 0; i < DIN; ++i) {
@@ -292,7 +310,7 @@ __global__ void __launch_bounds__(4 * W, 1) train_fwd_tc_kernel(FwdArgs a) {
       const bool last = l == n_lin - 1;
       const float* bl = sB + (l - 1) * W;
       float4* act = s_act[l] + ((size_t)tile * W + c0) * 128 + pl;
-      unsigned char* hb = s_hb[l] + (size_t)tile * 4 * AB + rowoff;
+      unsigned char* hb = last ? nullptr : s_hb[l] + (size_t)tile * 4 * AB + rowoff;
       unsigned char* sa = sA + rowoff;
 #pragma unroll
       for (int ch = 0; ch < 4; ++ch) {
@@ -319,8 +337,8 @@ __global__ void __launch_bounds__(4 * W, 1) train_fwd_tc_kernel(FwdArgs a) {
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
           const uint4 q = pack8(h[s]);
-          *reinterpret_cast<uint4*>(hb + s * AB + ch * 128) = q;
-          if (!last) *reinterpret_cast<uint4*>(sa + s * AB + ch * 128) = q;
+          if (!last) *reinterpret_cast<uint4*>(hb + s * AB + ch * 128) = q;
+          *reinterpret_cast<uint4*>(sa + s * AB + ch * 128) = q;
         }
       }
       fence_before();
@@ -330,25 +348,61 @@ __global__ void __launch_bounds__(4 * W, 1) train_fwd_tc_kernel(FwdArgs a) {
 #pragma unroll
     for (int s = 0; s < 4; ++s) sred[(g * 4 + s) * 128 + pl] = dot[s];
     __syncthreads();
-    if (g == 0 && valid) {
-      double out[4];
+    if (g == 0) {
+      float sd[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      if (valid) {
+        double out[4];
 #pragma unroll
-      for (int s = 0; s < 4; ++s) {
-        float u = sred[s * 128 + pl];
+        for (int s = 0; s < 4; ++s) {
+          float u = sred[s * 128 + pl];
 #pragma unroll
-        for (int gg = 1; gg < NG; ++gg) u += sred[(gg * 4 + s) * 128 + pl];
-        out[s] = (double)(s == 0 ? u + bout : u);
+          for (int gg = 1; gg < NG; ++gg) u += sred[(gg * 4 + s) * 128 + pl];
+          out[s] = (double)(s == 0 ? u + bout : u);
+        }
+        double xin[8];
+#pragma unroll
+        for (int i = 0; i < DIN; ++i) xin[i] = a.la.X[p * DIN + i];
+        double sqe[3] = {0.0, 0.0, 0.0}, gs[4];
+        point_loss(a.la, DIN, xin, a.la.kind[p], out, a.cnt, sqe, gs);
+        float* seeds = reinterpret_cast<float*>(a.ws + a.L.seeds);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          seeds[(int64_t)k * N + p] = (float)gs[k];
+          sd[k] = bf16r((float)gs[k]);
+        }
+        for (int k = 0; k < 3; ++k)
+          if (sqe[k] != 0.0) atomicAdd(&s_acc[k], sqe[k]);
+        dbo += sd[0];
       }
-      double xin[8];
 #pragma unroll
-      for (int i = 0; i < DIN; ++i) xin[i] = a.la.X[p * DIN + i];
-      double sqe[3] = {0.0, 0.0, 0.0}, gs[4];
-      point_loss(a.la, DIN, xin, a.la.kind[p], out, a.cnt, sqe, gs);
-      float* seeds = reinterpret_cast<float*>(a.ws + a.L.seeds);
+      for (int s = 0; s < 4; ++s)
+        *reinterpret_cast<__nv_bfloat16*>(sSeed + s * kTileB + tile_off(0, pl)) = __float2bfloat16_rn(sd[s]);
+    }
+    // output-layer gradient: sum over streams and points of h_s[i] seed_s
+    fence_proxy_async();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (t == 0) {
 #pragma unroll
-      for (int k = 0; k < 4; ++k) seeds[(int64_t)k * N + p] = (float)gs[k];
-      for (int k = 0; k < 3; ++k)
-        if (sqe[k] != 0.0) atomicAdd(&s_acc[k], sqe[k]);
+      for (int s = 0; s < 4; ++s) edge_mma<W>(tmem, smem_u32(sA + s * AB), smem_u32(sSeed + s * kTileB), s == 0);
+      mma_commit(&bar[0]);
+    }
+    {
+      const bool ok = mbar_wait_bounded(&bar[0], ph_mma);
+      ph_mma ^= 1u;
+      if (!ok) {
+        s_fail = 1;
+        mma_lost = true;
+      }
+      fence_after();
+      if (g == 0) {
+        uint32_t r[8];
+        tmem_ld8_nowait(tl, r);
+        tmem_wait_ld();
+        dwo += __uint_as_float(r[0]);
+      }
+      fence_before();
     }
   }
   if (t == 0 && w_pending) (void)mbar_wait_bounded(&bar[1], ph_w);
@@ -356,6 +410,11 @@ __global__ void __launch_bounds__(4 * W, 1) train_fwd_tc_kernel(FwdArgs a) {
   fence_before();
   __syncthreads();
   fence_after();
+  if (g == 0 && !s_fail) {
+    double* gL = a.grad + m.poff[n_lin];
+    if (pl < W) atomicAdd(gL + pl, (double)dwo);
+    atomicAdd(gL + W, (double)dbo);
+  }
   if (t == 0) {
     atomicAdd(a.loss_acc + 0, s_acc[0]);
     atomicAdd(a.loss_acc + 1, s_acc[1]);
@@ -373,12 +432,14 @@ __global__ void __launch_bounds__(4 * W, 1) train_fwd_tc_kernel(FwdArgs a) {
 // ---------------------------------------------------------------------------
 struct BwdArgs {
   MlpDev m;
+  const double* X;
   int64_t N;
   unsigned char* ws;
   TcLayout L;
+  double* grad;
 };
 
-template <int W>
+template <int DIN, int W>
 __global__ void __launch_bounds__(4 * W, 1) train_bwd_tc_kernel(BwdArgs a) {
   constexpr uint32_t WB = W * W * 2, AB = 128 * W * 2, SBO = (W / 8) * 128;
   constexpr uint32_t NCOLS = tmem_cols_streams(W);
@@ -388,7 +449,10 @@ __global__ void __launch_bounds__(4 * W, 1) train_bwd_tc_kernel(BwdArgs a) {
   unsigned char* sW = smem;
   unsigned char* sA = smem + WB;  // [4][AB]
   float* sWo = reinterpret_cast<float*>(sA + 4 * AB);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sWo + W);
+  // input-layer tiles: [0] rows x^_0 .. x^_{d-1} and 1 (value stream), [1] row
+  // d + 1 = 1 (d/dS stream), [2] row d + 2 = 1 (d/dtau stream)
+  unsigned char* sX = reinterpret_cast<unsigned char*>(sWo + W);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sX + 3 * kTileB);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
   __shared__ int s_fail;
   __shared__ const float4* s_act[16];
@@ -404,6 +468,20 @@ __global__ void __launch_bounds__(4 * W, 1) train_bwd_tc_kernel(BwdArgs a) {
     s_dzb[t] = hid ? a.ws + a.L.dzb[t] : nullptr;
   }
   for (int o = t; o < W; o += blockDim.x) sWo[o] = bf16r(m.p32[m.poff[n_lin] + o]);
+  for (int i = t; i < (int)(3 * kTileB / 2); i += blockDim.x) {
+    const int k = i / (kTileB / 2), e = i % (kTileB / 2);  // tile, element (n, p) in tile order
+    const int cm = e >> 6, n = (cm >> 4) * 8 + ((e >> 3) & 7);
+    const bool one = (k == 0 && n == DIN) || (k == 1 && n == DIN + 1) || (k == 2 && n == DIN + 2);
+    reinterpret_cast<__nv_bfloat16*>(sX)[i] = __float2bfloat16_rn(one ? 1.0f : 0.0f);
+  }
+  float sc[DIN], of[DIN];
+#pragma unroll
+  for (int i = 0; i < DIN; ++i) {
+    const double gi = 2.0 / (m.hi[i] - m.lo[i]);
+    sc[i] = (float)gi;
+    of[i] = (float)(-gi * m.lo[i] - 1.0);
+  }
+  float dw1[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // input-layer gradient: row pl of the edge GEMM
   if (t == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
@@ -438,7 +516,7 @@ __global__ void __launch_bounds__(4 * W, 1) train_bwd_tc_kernel(BwdArgs a) {
     for (int l = n_lin - 1; l >= 1; --l) {
       const bool top = l == n_lin - 1;
       const float4* act = s_act[l] + ((size_t)tile * W + c0) * 128 + pl;
-      unsigned char* dzb = s_dzb[l] + (size_t)tile * 4 * AB + rowoff;
+      unsigned char* dzb = l >= 2 ? s_dzb[l] + (size_t)tile * 4 * AB + rowoff : nullptr;
       unsigned char* sa = sA + rowoff;
 #pragma unroll
       for (int ch = 0; ch < 4; ++ch) {
@@ -481,13 +559,51 @@ __global__ void __launch_bounds__(4 * W, 1) train_bwd_tc_kernel(BwdArgs a) {
         }
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
+          if (l < 2 && s == 2) continue;  // the input layer's d2/dS2 stream has a zero input
           const uint4 q = pack8(dz[s]);
-          *reinterpret_cast<uint4*>(dzb + s * AB + ch * 128) = q;
-          if (l >= 2) *reinterpret_cast<uint4*>(sa + s * AB + ch * 128) = q;
+          if (l >= 2) *reinterpret_cast<uint4*>(dzb + s * AB + ch * 128) = q;
+          *reinterpret_cast<uint4*>(sa + s * AB + ch * 128) = q;
         }
       }
       fence_before();
-      if (l < 2) break;
+      if (l < 2) {
+        // input-layer gradient: dz_0 against (x^, 1), dz_1 and dz_3 against ones
+        if (g == 0) {
+#pragma unroll
+          for (int i = 0; i < DIN; ++i) {
+            const float xh = bf16r(fmaf(valid ? (float)a.X[p * DIN + i] : 0.0f, sc[i], of[i]));
+            *reinterpret_cast<__nv_bfloat16*>(sX + tile_off(i, pl)) = __float2bfloat16_rn(valid ? xh : 0.0f);
+          }
+        }
+        fence_proxy_async();
+        fence_before();
+        __syncthreads();
+        fence_after();
+        if (t == 0) {
+          const uint32_t aa = smem_u32(sA), xx = smem_u32(sX);
+          edge_mma<W>(tmem, aa, xx, true);
+          edge_mma<W>(tmem, aa + AB, xx + kTileB, false);
+          edge_mma<W>(tmem, aa + 3 * AB, xx + 2 * kTileB, false);
+          mma_commit(&bar[0]);
+        }
+        const bool ok = mbar_wait_bounded(&bar[0], ph_mma);
+        ph_mma ^= 1u;
+        if (!ok) {
+          s_fail = 1;
+          mma_lost = true;
+        }
+        fence_after();
+        if (g == 0) {
+          uint32_t r[8];
+          tmem_ld8_nowait(tl, r);
+          tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < 8; ++j) dw1[j] += __uint_as_float(r[j]);
+        }
+        fence_before();
+        __syncthreads();
+        break;
+      }
       // ah of layer l-1: dz_l W_l (B = W_l^T) on the tensor cores
       if (t == 0 && w_pending) {
         if (mbar_wait_bounded(&bar[1], ph_w)) {
@@ -533,6 +649,20 @@ __global__ void __launch_bounds__(4 * W, 1) train_bwd_tc_kernel(BwdArgs a) {
   fence_before();
   __syncthreads();
   fence_after();
+  if (g == 0 && pl < W && !s_fail) {
+    // dL/dW_1[o][i] = sum dz_0 x^_i (+ sc_S sum dz_1 for i = 0, + sc_tau sum dz_3 for
+    // i = 1, the constant streams of the mapped inputs), dL/db_1[o] = sum dz_0
+    double* g1 = a.grad + m.poff[1];
+    const double sS = (double)bf16r(sc[0]), sT = (double)bf16r(sc[1]);
+#pragma unroll
+    for (int i = 0; i < DIN; ++i) {
+      double v = (double)dw1[i];
+      if (i == 0) v += sS * (double)dw1[DIN + 1];
+      if (i == 1) v += sT * (double)dw1[DIN + 2];
+      atomicAdd(g1 + (int64_t)pl * DIN + i, v);
+    }
+    atomicAdd(g1 + (int64_t)W * DIN + pl, (double)dw1[DIN]);
+  }
   if (s_fail && t == 0) atomicExch(m.status, 6);  // BS_TIMEOUT
   if (warp == 0) tmem_dealloc(tmem, NCOLS);
 }
@@ -704,137 +834,20 @@ __global__ void wgrad_sum_kernel(MlpDev m, const float* __restrict__ partial, in
   atomicAdd(i < w ? gW + (int64_t)o * w + i : gW + (int64_t)w * w + o, (double)acc);
 }
 
-// Input layer (d_in -> w): its input streams are the mapped inputs h_0 = x^ and
-// the constants h_1 = sc_S e_S, h_3 = sc_tau e_tau (h_2 = 0), so
-//   dL/dW_1[o][i] = sum_p dz_0[o][p] x^_i(p) + [i = 0] sc_S sum_p dz_1[o][p]
-//                   + [i = 1] sc_tau sum_p dz_3[o][p],   dL/db_1[o] = sum_p dz_0[o][p],
-// from the BF16 dzb blocks of layer 1, x^ rounded to BF16 like a GEMM operand.
-// Thread (og, pq) = neurons 8 og .. 8 og + 7, points pq, pq + 8, ... of a tile.
-template <int DIN, int W>
-__global__ void __launch_bounds__(W) grad_input_kernel(MlpDev m, const double* __restrict__ X, int64_t N,
-                                                       const unsigned char* __restrict__ dzb1,
-                                                       double* __restrict__ grad, int nt) {
-  constexpr uint32_t AB = 128 * W * 2;
-  const int t = threadIdx.x, og = t >> 3, pq = t & 7;
-  double sc[DIN], lo[DIN];
-#pragma unroll
-  for (int i = 0; i < DIN; ++i) {
-    sc[i] = 2.0 / (m.hi[i] - m.lo[i]);
-    lo[i] = m.lo[i];
-  }
-  float ax[8][DIN], a0[8], a1[8], a3[8];
-#pragma unroll
-  for (int e = 0; e < 8; ++e) {
-    a0[e] = a1[e] = a3[e] = 0.0f;
-#pragma unroll
-    for (int i = 0; i < DIN; ++i) ax[e][i] = 0.0f;
-  }
-  for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
-    const unsigned char* blk = dzb1 + (size_t)tile * 4 * AB;
-    for (int pl = pq; pl < 128; pl += 8) {
-      const int64_t p = (int64_t)tile * 128 + pl;
-      if (p >= N) break;
-      const uint32_t off = canon_off(pl, og * 8, W);
-      float g0[8], g1[8], g3[8];
-      unpack8(__ldg(reinterpret_cast<const uint4*>(blk + off)), g0);
-      unpack8(__ldg(reinterpret_cast<const uint4*>(blk + AB + off)), g1);
-      unpack8(__ldg(reinterpret_cast<const uint4*>(blk + 3 * AB + off)), g3);
-      float xh[DIN];
-#pragma unroll
-      for (int i = 0; i < DIN; ++i) xh[i] = bf16r((float)(sc[i] * (X[p * DIN + i] - lo[i]) - 1.0));
-#pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        a0[e] += g0[e];
-        a1[e] += g1[e];
-        a3[e] += g3[e];
-#pragma unroll
-        for (int i = 0; i < DIN; ++i) ax[e][i] = fmaf(g0[e], xh[i], ax[e][i]);
-      }
-    }
-  }
-  auto red = [](float v) {
-    v += __shfl_xor_sync(0xffffffffu, v, 1);
-    v += __shfl_xor_sync(0xffffffffu, v, 2);
-    v += __shfl_xor_sync(0xffffffffu, v, 4);
-    return v;
-  };
-#pragma unroll
-  for (int e = 0; e < 8; ++e) {
-    a0[e] = red(a0[e]);
-    a1[e] = red(a1[e]);
-    a3[e] = red(a3[e]);
-#pragma unroll
-    for (int i = 0; i < DIN; ++i) ax[e][i] = red(ax[e][i]);
-  }
-  if (pq == 0) {
-    double* g = grad + m.poff[1];
-    const double sS = (double)bf16r((float)sc[0]), sT = (double)bf16r((float)sc[1]);
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      const int o = og * 8 + e;
-#pragma unroll
-      for (int i = 0; i < DIN; ++i) {
-        double v = (double)ax[e][i];
-        if (i == 0) v += sS * (double)a1[e];
-        if (i == 1) v += sT * (double)a3[e];
-        atomicAdd(g + (int64_t)o * DIN + i, v);
-      }
-      atomicAdd(g + (int64_t)W * DIN + o, (double)a0[e]);
-    }
-  }
-}
-
-// Output layer (w -> 1): dL/dW_L[i] = sum over streams and points of seed_s h_s[i]
-// with h_s from the BF16 hb blocks of the top hidden layer, dL/db_L = sum of
-// seed_0; seeds rounded to BF16 like the adjoint's.  Thread mapping as above.
-template <int W>
-__global__ void __launch_bounds__(W) grad_output_kernel(MlpDev m, int64_t N, const unsigned char* __restrict__ hbtop,
-                                                        const float* __restrict__ seeds, double* __restrict__ grad,
-                                                        int nt) {
-  constexpr uint32_t AB = 128 * W * 2;
-  const int t = threadIdx.x, ig = t >> 3, pq = t & 7;
-  float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0}, ab = 0.0f;
-  for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
-    const unsigned char* blk = hbtop + (size_t)tile * 4 * AB;
-    for (int pl = pq; pl < 128; pl += 8) {
-      const int64_t p = (int64_t)tile * 128 + pl;
-      if (p >= N) break;
-      const uint32_t off = canon_off(pl, ig * 8, W);
-#pragma unroll
-      for (int s = 0; s < 4; ++s) {
-        const float sd = bf16r(__ldg(seeds + (int64_t)s * N + p));
-        float h[8];
-        unpack8(__ldg(reinterpret_cast<const uint4*>(blk + s * AB + off)), h);
-#pragma unroll
-        for (int e = 0; e < 8; ++e) acc[e] = fmaf(sd, h[e], acc[e]);
-        if (s == 0 && ig == 0) ab += sd;
-      }
-    }
-  }
-  auto red = [](float v) {
-    v += __shfl_xor_sync(0xffffffffu, v, 1);
-    v += __shfl_xor_sync(0xffffffffu, v, 2);
-    v += __shfl_xor_sync(0xffffffffu, v, 4);
-    return v;
-  };
-#pragma unroll
-  for (int e = 0; e < 8; ++e) acc[e] = red(acc[e]);
-  ab = red(ab);
-  if (pq == 0) {
-    double* g = grad + m.poff[m.n_lin];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) atomicAdd(g + ig * 8 + e, (double)acc[e]);
-    if (ig == 0) atomicAdd(g + W, (double)ab);
-  }
-}
-
-int resident_per_sm(size_t smem, int threads, uint32_t tmem_cols) {
+// CTAs of a kernel that fit on one SM at once (shared memory, threads,
+// registers, tensor-memory columns); the persistent grids are sized with it.
+template <typename K>
+int resident_per_sm(K kern, size_t smem, int threads, uint32_t tmem_cols) {
   int dev = 0, sm_smem = 0, reserved = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
   cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
-  int per = (int)((size_t)sm_smem / (smem + 1024 + (size_t)reserved));
+  cudaFuncAttributes fa{};
+  cudaFuncGetAttributes(&fa, kern);
+  int per = (int)((size_t)sm_smem / (smem + fa.sharedSizeBytes + (size_t)reserved));
   if (per > 2048 / threads) per = 2048 / threads;
+  if (fa.numRegs > 0 && per > 65536 / (((fa.numRegs + 7) / 8) * 8 * threads))
+    per = 65536 / (((fa.numRegs + 7) / 8) * 8 * threads);
   if (per > (int)(512 / tmem_cols)) per = (int)(512 / tmem_cols);
   return per < 1 ? 1 : per;
 }
@@ -846,23 +859,24 @@ cudaError_t run_train_tc(const MlpDev& m, const LossArgs& la, unsigned char* ws,
   const int n_lin = m.n_lin, n_sq = n_lin - 2, nsm = sm_count();
   cudaError_t e;
   {
-    FwdArgs a{m, la, ws, L, cnt, loss_acc};
-    const size_t smem =
-        WB + 4 * AB + sizeof(float) * ((size_t)W * DIN + (size_t)(n_lin - 1) * W + W + (W / 32) * 4 * 128) + 64;
+    FwdArgs a{m, la, ws, L, cnt, loss_acc, grad};
+    const size_t smem = WB + 4 * AB +
+                        sizeof(float) * ((size_t)W * DIN + (size_t)(n_lin - 1) * W + W + (W / 32) * 4 * 128) +
+                        4 * kTileB + 64;
     auto kern = train_fwd_tc_kernel<DIN, W>;
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
       return e;
-    const int64_t cap = (int64_t)nsm * resident_per_sm(smem, 4 * W, tmem_cols_streams(W));
+    const int64_t cap = (int64_t)nsm * resident_per_sm(kern, smem, 4 * W, tmem_cols_streams(W));
     kern<<<(unsigned)(L.nt < cap ? L.nt : cap), 4 * W, smem, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   {
-    BwdArgs a{m, la.N, ws, L};
-    const size_t smem = WB + 4 * AB + sizeof(float) * W + 64;
-    auto kern = train_bwd_tc_kernel<W>;
+    BwdArgs a{m, la.X, la.N, ws, L, grad};
+    const size_t smem = WB + 4 * AB + sizeof(float) * W + 3 * kTileB + 64;
+    auto kern = train_bwd_tc_kernel<DIN, W>;
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
       return e;
-    const int64_t cap = (int64_t)nsm * resident_per_sm(smem, 4 * W, tmem_cols_streams(W));
+    const int64_t cap = (int64_t)nsm * resident_per_sm(kern, smem, 4 * W, tmem_cols_streams(W));
     kern<<<(unsigned)(L.nt < cap ? L.nt : cap), 4 * W, smem, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
@@ -889,12 +903,7 @@ cudaError_t run_train_tc(const MlpDev& m, const LossArgs& la, unsigned char* ws,
         m, reinterpret_cast<const float*>(ws + L.partial), L.ny, grad);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  const int ge = L.nt < 4 * nsm ? L.nt : 4 * nsm;
-  grad_input_kernel<DIN, W><<<ge, W, 0, s>>>(m, la.X, la.N, ws + L.dzb[1], grad, L.nt);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  grad_output_kernel<W><<<ge, W, 0, s>>>(m, la.N, ws + L.hb[n_lin - 1], reinterpret_cast<const float*>(ws + L.seeds),
-                                         grad, L.nt);
-  return cudaGetLastError();
+  return cudaSuccess;
 }
 
 template <int DIN>
