@@ -18,9 +18,11 @@
 //             dL/db[o] = sum over points of dz_0[o].
 //
 // Workspace (NT = ceil(N / 128) tiles, w the hidden width):
-//   act[l]  float4 [NT][w][128]: (t, z_1, z_2, z_3) of hidden layer l at
+//   act[l]  float4 [NT][w][128]: (t, z_1, z_2, z_3) of hidden layer l >= 2 at
 //           (neuron, point); the adjoint reads it with one 16-byte load per
-//           neuron, 512 contiguous bytes per warp;
+//           neuron, 512 contiguous bytes per warp.  Layer 1 keeps t only
+//           (float [NT][w][128]): its z_1 = W_1[o][0] sc_S, z_2 = 0 and
+//           z_3 = W_1[o][1] sc_tau are constants per neuron;
 //   hb[l]   BF16 [NT][4][128 x w]: h_s of hidden layer l (l < n_lin - 1);
 //   dzb[l]  BF16 [NT][4][128 x w]: dz_s of hidden layer l (l >= 2).
 // The BF16 blocks keep the GEMM operand layout (rows = points, K = neurons,
@@ -80,7 +82,7 @@ TcLayout tc_layout(const MlpDev& m, int64_t N) {
     o = (o + bytes + 255) / 256 * 256;
     return r;
   };
-  for (int l = 1; l < m.n_lin; ++l) L.act[l] = take((size_t)nt * w * 128 * 16);
+  for (int l = 1; l < m.n_lin; ++l) L.act[l] = take((size_t)nt * w * 128 * (l == 1 ? 4 : 16));
   for (int l = 1; l < m.n_lin - 1; ++l) L.hb[l] = take((size_t)nt * 4 * 128 * w * 2);
   for (int l = 2; l < m.n_lin; ++l) L.dzb[l] = take((size_t)nt * 4 * 128 * w * 2);
   L.seeds = take((size_t)4 * (size_t)N * sizeof(float));
@@ -240,7 +242,7 @@ __global__ void __launch_bounds__(4 * W, 1) train_fwd_tc_kernel(FwdArgs a) {
       float xh[DIN];
 #pragma unroll
       for (int i = 0; i < DIN; ++i) xh[i] = bf16r(fmaf(valid ? (float)a.la.X[p * DIN + i] : 0.0f, sc[i], of[i]));
-      float4* act = s_act[1] + ((size_t)tile * W + c0) * 128 + pl;
+      float* act = reinterpret_cast<float*>(s_act[1]) + ((size_t)tile * W + c0) * 128 + pl;
       unsigned char* hb = s_hb[1] + (size_t)tile * 4 * AB + rowoff;
       unsigned char* sa = sA + rowoff;
 #pragma unroll
@@ -258,7 +260,7 @@ __global__ void __launch_bounds__(4 * W, 1) train_fwd_tc_kernel(FwdArgs a) {
           h[1][j] = d1 * zS;
           h[2][j] = -2.0f * tt * d1 * zS * zS;
           h[3][j] = d1 * zT;
-          act[(8 * k + j) * 128] = make_float4(tt, zS, 0.0f, zT);
+          act[(8 * k + j) * 128] = tt;
         }
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
@@ -451,7 +453,9 @@ __global__ void __launch_bounds__(4 * W, 1) train_bwd_tc_kernel(BwdArgs a) {
   float* sWo = reinterpret_cast<float*>(sA + 4 * AB);
   // input-layer tiles: [0] rows x^_0 .. x^_{d-1} and 1 (value stream), [1] row
   // d + 1 = 1 (d/dS stream), [2] row d + 2 = 1 (d/dtau stream)
-  unsigned char* sX = reinterpret_cast<unsigned char*>(sWo + W);
+  float* sZ1 = sWo + W;  // layer 1: z_1 = W_1[o][0] sc_S and z_3 = W_1[o][1] sc_tau per neuron
+  float* sZ3 = sZ1 + W;
+  unsigned char* sX = reinterpret_cast<unsigned char*>(sZ3 + W);
   uint64_t* bar = reinterpret_cast<uint64_t*>(sX + 3 * kTileB);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
   __shared__ int s_fail;
@@ -480,6 +484,10 @@ __global__ void __launch_bounds__(4 * W, 1) train_bwd_tc_kernel(BwdArgs a) {
     const double gi = 2.0 / (m.hi[i] - m.lo[i]);
     sc[i] = (float)gi;
     of[i] = (float)(-gi * m.lo[i] - 1.0);
+  }
+  for (int o = t; o < W; o += blockDim.x) {
+    sZ1[o] = bf16r(m.p32[m.poff[1] + (int64_t)o * DIN + 0]) * sc[0];
+    sZ3[o] = bf16r(m.p32[m.poff[1] + (int64_t)o * DIN + 1]) * sc[1];
   }
   float dw1[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // input-layer gradient: row pl of the edge GEMM
   if (t == 0) {
@@ -516,13 +524,22 @@ __global__ void __launch_bounds__(4 * W, 1) train_bwd_tc_kernel(BwdArgs a) {
     for (int l = n_lin - 1; l >= 1; --l) {
       const bool top = l == n_lin - 1;
       const float4* act = s_act[l] + ((size_t)tile * W + c0) * 128 + pl;
+      const float* act1 = reinterpret_cast<const float*>(s_act[1]) + ((size_t)tile * W + c0) * 128 + pl;
       unsigned char* dzb = l >= 2 ? s_dzb[l] + (size_t)tile * 4 * AB + rowoff : nullptr;
       unsigned char* sa = sA + rowoff;
 #pragma unroll
       for (int ch = 0; ch < 4; ++ch) {
         float4 av[8];
+        if (l >= 2) {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) av[j] = __ldg(act + (8 * ch + j) * 128);
+          for (int j = 0; j < 8; ++j) av[j] = __ldg(act + (8 * ch + j) * 128);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int o = c0 + 8 * ch + j;
+            av[j] = make_float4(__ldg(act1 + (8 * ch + j) * 128), sZ1[o], 0.0f, sZ3[o]);
+          }
+        }
         float ah[4][8];
         if (top) {
 #pragma unroll
@@ -872,7 +889,7 @@ cudaError_t run_train_tc(const MlpDev& m, const LossArgs& la, unsigned char* ws,
   }
   {
     BwdArgs a{m, la.X, la.N, ws, L, grad};
-    const size_t smem = WB + 4 * AB + sizeof(float) * W + 3 * kTileB + 64;
+    const size_t smem = WB + 4 * AB + sizeof(float) * 3 * W + 3 * kTileB + 64;
     auto kern = train_bwd_tc_kernel<DIN, W>;
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
       return e;
