@@ -53,7 +53,6 @@ namespace {
 
 struct TcLayout {
   size_t act[16], hb[16], dzb[16];  // byte offsets by hidden layer l
-  size_t seeds;                     // float [4][N]: dLoss/d(u, u_S, u_SS, u_tau)
   size_t partial;                   // float [n_sq][ny][w][w + 1]: weight-gradient partial sums
   size_t pack;                      // BF16 square layers: W_l then W_l^T
   size_t total;
@@ -85,7 +84,6 @@ TcLayout tc_layout(const MlpDev& m, int64_t N) {
   for (int l = 1; l < m.n_lin; ++l) L.act[l] = take((size_t)nt * w * 128 * (l == 1 ? 4 : 16));
   for (int l = 1; l < m.n_lin - 1; ++l) L.hb[l] = take((size_t)nt * 4 * 128 * w * 2);
   for (int l = 2; l < m.n_lin; ++l) L.dzb[l] = take((size_t)nt * 4 * 128 * w * 2);
-  L.seeds = take((size_t)4 * (size_t)N * sizeof(float));
   // one wave of weight-gradient CTAs (one per SM) over all square layers
   int ny = sm_count() / (n_sq > 0 ? n_sq : 1);
   if (ny < 1) ny = 1;
@@ -147,14 +145,20 @@ __host__ __device__ constexpr uint32_t tmem_cols_streams(int w) {
 }
 
 // ---------------------------------------------------------------------------
-// Forward.  A CTA of 4w threads: warp v reads accumulator lanes 32 (v % 4) ..
+// Forward and adjoint in one persistent kernel.  A tile's adjoint needs only
+// that tile's forward, so the stored (t, z_1, z_2, z_3) are read back while
+// they are still in L2 (stored with an evict-last policy) and dropped from it
+// after their last use (discard.global.L2: never written back to HBM); the
+// BF16 operand blocks for the weight gradient stream out with an evict-first
+// policy.  A CTA of 4w threads: warp v reads accumulator lanes 32 (v % 4) ..
 // (one point per thread) and owns neurons 32 (v / 4) .. + 31 of every layer.
 // Per square layer one thread issues the four stream GEMMs (M = 128 points,
-// N = K = w) and the next layer's weights are fetched by TMA while the
-// epilogue runs.  After the top layer the output streams, the loss terms and
-// the adjoint seeds are formed per point in FP64.
+// N = K = w); the weights of the next GEMM (W_l going up, W_l^T coming down)
+// are fetched by TMA while the epilogue runs.  Between the two passes the
+// output streams, the loss terms and the adjoint seeds are formed per point
+// in FP64.
 // ---------------------------------------------------------------------------
-struct FwdArgs {
+struct TrainArgs {
   MlpDev m;
   LossArgs la;
   unsigned char* ws;
@@ -164,51 +168,103 @@ struct FwdArgs {
   double* grad;
 };
 
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+__device__ __forceinline__ void st_hint(float4* p, float4 v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z),
+               "f"(v.w), "l"(pol)
+               : "memory");
+}
+
+__device__ __forceinline__ void st_hint(float* p, float v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol) : "memory");
+}
+
+__device__ __forceinline__ void st_hint(unsigned char* p, uint4 v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v4.u32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "r"(v.x), "r"(v.y), "r"(v.z),
+               "r"(v.w), "l"(pol)
+               : "memory");
+}
+
+// Drop a 128-byte line from L2 without writing it back (its contents become undefined).
+__device__ __forceinline__ void discard_l2(const void* p) {
+  asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
+}
+
 template <int DIN, int W>
-__global__ void __launch_bounds__(4 * W, 1) train_fwd_tc_kernel(FwdArgs a) {
+__global__ void __launch_bounds__(4 * W, 1) train_tc_kernel(TrainArgs a) {
   constexpr int NG = W / 32;
   constexpr uint32_t WB = W * W * 2, AB = 128 * W * 2, SBO = (W / 8) * 128;
   constexpr uint32_t NCOLS = tmem_cols_streams(W);
   extern __shared__ __align__(1024) unsigned char smem[];
   const MlpDev& m = a.m;
   const int n_lin = m.n_lin, n_sq = n_lin - 2;
-  unsigned char* sW = smem;
-  unsigned char* sA = smem + WB;                                    // [4][AB]
-  float* sW1 = reinterpret_cast<float*>(sA + 4 * AB);               // W x DIN, BF16-rounded
-  float* sB = sW1 + W * DIN;                                        // hidden biases, (n_lin - 1) x W
-  float* sWo = sB + (n_lin - 1) * W;                                // output weights, BF16-rounded
-  float* sred = sWo + W;                                            // [NG][4][128] output partial sums
-  unsigned char* sSeed = reinterpret_cast<unsigned char*>(sred + NG * 4 * 128);  // [4] seed tiles (row 0)
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sSeed + 4 * kTileB);  // [0] GEMMs done, [1] weights landed
+  unsigned char* sW = smem;                                   // weights of the next GEMM
+  unsigned char* sA = smem + WB;                              // [4][AB] A operand: h_s going up, dz_s coming down
+  unsigned char* sSeed = sA + 4 * AB;                         // [4] seed tiles (row 0), output-layer GEMM
+  unsigned char* sX = sSeed + 4 * kTileB;                     // [3] input tiles, input-layer GEMM
+  float* sW1 = reinterpret_cast<float*>(sX + 3 * kTileB);     // W x DIN, BF16-rounded
+  float* sB = sW1 + W * DIN;                                  // hidden biases, (n_lin - 1) x W
+  float* sWo = sB + (n_lin - 1) * W;                          // output weights, BF16-rounded
+  float* sZ1 = sWo + W;                                       // layer 1: z_1 = W_1[o][0] sc_S per neuron
+  float* sZ3 = sZ1 + W;                                       // layer 1: z_3 = W_1[o][1] sc_tau per neuron
+  float* sred = sZ3 + W;                                      // [NG][4][128] output partial sums
+  float* sSd = sred + NG * 4 * 128;                           // [4][128] BF16-rounded seeds of the tile
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sSd + 4 * 128);  // [0] GEMMs done, [1] weights landed
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
   __shared__ int s_fail;
   __shared__ double s_acc[3];
   __shared__ float4* s_act[16];
   __shared__ unsigned char* s_hb[16];
+  __shared__ unsigned char* s_dzb[16];
 
-  const int t = threadIdx.x, warp = t >> 5, lane = t & 31, g = warp >> 2;
-  const int pl = (warp & 3) * 32 + lane, c0 = g * 32;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31, g = warp >> 2, qd = warp & 3;
+  const int pl = qd * 32 + lane, c0 = g * 32;
   const int64_t N = a.la.N;
   const int nt = a.L.nt;
   if (t < 16) {
-    const bool hid = t >= 1 && t < n_lin;
-    s_act[t] = hid ? reinterpret_cast<float4*>(a.ws + a.L.act[t]) : nullptr;
-    s_hb[t] = hid ? a.ws + a.L.hb[t] : nullptr;
+    s_act[t] = (t >= 1 && t < n_lin) ? reinterpret_cast<float4*>(a.ws + a.L.act[t]) : nullptr;
+    s_hb[t] = (t >= 1 && t < n_lin - 1) ? a.ws + a.L.hb[t] : nullptr;
+    s_dzb[t] = (t >= 2 && t < n_lin) ? a.ws + a.L.dzb[t] : nullptr;
   }
+  // input map x^ = sc x + of to [-1, 1] (in shared memory: it is live in both passes)
+  __shared__ float sc[8], of[8];
+  if (t < DIN) {
+    const double gi = 2.0 / (m.hi[t] - m.lo[t]);
+    sc[t] = (float)gi;
+    of[t] = (float)(-gi * m.lo[t] - 1.0);
+  }
+  __syncthreads();
   for (int i = t; i < W * DIN; i += blockDim.x) sW1[i] = bf16r(m.p32[m.poff[1] + i]);
   for (int l = 1; l < n_lin; ++l)
     for (int o = t; o < W; o += blockDim.x) sB[(l - 1) * W + o] = m.p32[m.poff[l] + (int64_t)W * m.widths[l - 1] + o];
-  for (int o = t; o < W; o += blockDim.x) sWo[o] = bf16r(m.p32[m.poff[n_lin] + o]);
-  for (int i = t; i < (int)(4 * kTileB / 16); i += blockDim.x) reinterpret_cast<uint4*>(sSeed)[i] = make_uint4(0, 0, 0, 0);
-  const float bout = m.p32[m.poff[n_lin] + W];
-  float dwo = 0.0f, dbo = 0.0f;  // output-layer gradient: row pl of the edge GEMM, and sum of seed_0
-  float sc[DIN], of[DIN];
-#pragma unroll
-  for (int i = 0; i < DIN; ++i) {
-    const double gi = 2.0 / (m.hi[i] - m.lo[i]);
-    sc[i] = (float)gi;
-    of[i] = (float)(-gi * m.lo[i] - 1.0);
+  for (int o = t; o < W; o += blockDim.x) {
+    sWo[o] = bf16r(m.p32[m.poff[n_lin] + o]);
+    sZ1[o] = bf16r(m.p32[m.poff[1] + (int64_t)o * DIN + 0]) * sc[0];
+    sZ3[o] = bf16r(m.p32[m.poff[1] + (int64_t)o * DIN + 1]) * sc[1];
   }
+  for (int i = t; i < (int)(4 * kTileB / 16); i += blockDim.x) reinterpret_cast<uint4*>(sSeed)[i] = make_uint4(0, 0, 0, 0);
+  // input tiles: [0] rows x^_0 .. x^_{d-1} (per tile) and row d = 1 (value
+  // stream, bias), [1] row d + 1 = 1 (d/dS stream), [2] row d + 2 = 1 (d/dtau stream)
+  for (int i = t; i < (int)(3 * kTileB / 2); i += blockDim.x) {
+    const int k = i / (kTileB / 2), e = i % (kTileB / 2);  // tile, element in tile order
+    const int n = ((e >> 6) >> 4) * 8 + ((e >> 3) & 7);
+    const bool one = (k == 0 && n == DIN) || (k == 1 && n == DIN + 1) || (k == 2 && n == DIN + 2);
+    reinterpret_cast<__nv_bfloat16*>(sX)[i] = __float2bfloat16_rn(one ? 1.0f : 0.0f);
+  }
+  const float bout = m.p32[m.poff[n_lin] + W];
+  float dwo = 0.0f, dbo = 0.0f;                  // output layer: row pl of its GEMM, sum of seed_0
+  float dw1[8] = {0, 0, 0, 0, 0, 0, 0, 0};       // input layer: row pl of its GEMM
   if (t == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
@@ -217,11 +273,16 @@ __global__ void __launch_bounds__(4 * W, 1) train_fwd_tc_kernel(FwdArgs a) {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
+  // weights of GEMM q of a tile: q < n_sq -> W_{q+2} (forward), else W^T of layer
+  // 2 n_sq + 1 - q (adjoint, top down)
+  const unsigned char* wpack = a.ws + a.L.pack;
+  auto wsrc = [&](int q) {
+    return q < n_sq ? wpack + (size_t)q * WB : wpack + (size_t)n_sq * WB + (size_t)(2 * n_sq - 1 - q) * WB;
+  };
   bool w_pending = false, mma_lost = false;
   uint32_t ph_w = 0, ph_mma = 0;
-  const unsigned char* wpack = a.ws + a.L.pack;
   if (t == 0 && (int)blockIdx.x < nt) {
-    bulk_load(sW, wpack, WB, &bar[1]);
+    bulk_load(sW, wsrc(0), WB, &bar[1]);
     w_pending = true;
   }
   if (warp == 0) tmem_alloc(tslot, NCOLS);
@@ -229,15 +290,80 @@ __global__ void __launch_bounds__(4 * W, 1) train_fwd_tc_kernel(FwdArgs a) {
   __syncthreads();
   fence_after();
   const uint32_t tmem = *tslot;
-  const uint32_t idesc = make_idesc_bf16(W);
-  const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+  const uint32_t tl = tmem + ((uint32_t)(qd * 32) << 16);
   const uint32_t rowoff = (uint32_t)((pl >> 3) * (W / 8) * 128 + (pl & 7) * 16) + (uint32_t)(c0 / 8) * 128;
+  const uint64_t keep = policy_evict_last(), stream = policy_evict_first();
+
+  // GEMM q: wait for its weights, the four stream GEMMs of sA with sW, wait for
+  // them, then fetch the next weights (if `more`)
+  auto gemm = [&](int q, bool more) -> bool {
+    if (t == 0 && w_pending) {
+      if (mbar_wait_bounded(&bar[1], ph_w)) {
+        ph_w ^= 1u;
+        w_pending = false;
+      } else {
+        s_fail = 1;
+      }
+    }
+    fence_proxy_async();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (s_fail) return false;
+    if (t == 0) {
+      const uint32_t aa = smem_u32(sA), bb = smem_u32(sW), idesc = make_idesc_bf16(W);
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+        for (int kk = 0; kk < W / 16; ++kk)
+          mma_bf16(tmem + (uint32_t)(s * W), make_desc(aa + s * AB + kk * 256, 128, SBO),
+                   make_desc(bb + kk * 256, 128, SBO), idesc, kk > 0 ? 1u : 0u);
+      mma_commit(&bar[0]);
+    }
+    const bool ok = mbar_wait_bounded(&bar[0], ph_mma);
+    ph_mma ^= 1u;
+    if (!ok) {
+      s_fail = 1;
+      mma_lost = true;
+    }
+    fence_after();
+    if (t == 0 && ok && more) {
+      bulk_load(sW, wsrc(q + 1 < 2 * n_sq ? q + 1 : 0), WB, &bar[1]);
+      w_pending = true;
+    }
+    __syncthreads();
+    return !s_fail;
+  };
+  // an edge-layer GEMM issued by `issue`, then its 16 result columns of row pl
+  auto edge = [&](auto issue, uint32_t (&r)[8]) -> bool {
+    fence_proxy_async();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (s_fail) return false;
+    if (t == 0) {
+      issue();
+      mma_commit(&bar[0]);
+    }
+    const bool ok = mbar_wait_bounded(&bar[0], ph_mma);
+    ph_mma ^= 1u;
+    if (!ok) {
+      s_fail = 1;
+      mma_lost = true;
+    }
+    fence_after();
+    if (ok && g == 0) {
+      tmem_ld8_nowait(tl, r);
+      tmem_wait_ld();
+    }
+    fence_before();
+    return ok;
+  };
 
   for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
     const int64_t p = (int64_t)tile * 128 + pl;
     const bool valid = p < N;
     const bool last_tile = tile + (int)gridDim.x >= nt;
-    // input layer on CUDA cores: h_0 = t, h_1 = t' z_S, h_2 = t'' z_S^2, h_3 = t' z_tau
+    // ---- forward, input layer on CUDA cores: h_0 = t, h_1 = t' z_S, h_2 = t'' z_S^2, h_3 = t' z_tau
     {
       float xh[DIN];
 #pragma unroll
@@ -255,60 +381,26 @@ __global__ void __launch_bounds__(4 * W, 1) train_fwd_tc_kernel(FwdArgs a) {
 #pragma unroll
           for (int i = 0; i < DIN; ++i) z = fmaf(sW1[o * DIN + i], xh[i], z);
           const float tt = tanh_fast(z), d1 = 1.0f - tt * tt;
-          const float zS = sW1[o * DIN + 0] * sc[0], zT = sW1[o * DIN + 1] * sc[1];
+          const float zS = sZ1[o], zT = sZ3[o];
           h[0][j] = tt;
           h[1][j] = d1 * zS;
           h[2][j] = -2.0f * tt * d1 * zS * zS;
           h[3][j] = d1 * zT;
-          act[(8 * k + j) * 128] = tt;
+          st_hint(act + (8 * k + j) * 128, tt, keep);
         }
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
           const uint4 q = pack8(h[s]);
           *reinterpret_cast<uint4*>(sa + s * AB + k * 128) = q;
-          *reinterpret_cast<uint4*>(hb + s * AB + k * 128) = q;
+          st_hint(hb + s * AB + k * 128, q, stream);
         }
       }
     }
-    // square layers on the tensor cores
+    // ---- forward, square layers on the tensor cores
     float dot[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     for (int sq = 0; sq < n_sq; ++sq) {
       const int l = sq + 2;
-      if (t == 0 && w_pending) {
-        if (mbar_wait_bounded(&bar[1], ph_w)) {
-          ph_w ^= 1u;
-          w_pending = false;
-        } else {
-          s_fail = 1;
-        }
-      }
-      fence_proxy_async();
-      fence_before();
-      __syncthreads();
-      fence_after();
-      if (s_fail) break;
-      if (t == 0) {
-        const uint32_t aa = smem_u32(sA), bb = smem_u32(sW);
-#pragma unroll
-        for (int s = 0; s < 4; ++s)
-          for (int kk = 0; kk < W / 16; ++kk)
-            mma_bf16(tmem + (uint32_t)(s * W), make_desc(aa + s * AB + kk * 256, 128, SBO),
-                     make_desc(bb + kk * 256, 128, SBO), idesc, kk > 0 ? 1u : 0u);
-        mma_commit(&bar[0]);
-      }
-      const bool ok = mbar_wait_bounded(&bar[0], ph_mma);
-      ph_mma ^= 1u;
-      if (!ok) {
-        s_fail = 1;
-        mma_lost = true;
-      }
-      fence_after();
-      if (t == 0 && ok && (sq + 1 < n_sq || !last_tile)) {
-        bulk_load(sW, wpack + (size_t)(sq + 1 < n_sq ? sq + 1 : 0) * WB, WB, &bar[1]);
-        w_pending = true;
-      }
-      __syncthreads();
-      if (s_fail) break;
+      if (!gemm(sq, true)) break;
       const bool last = l == n_lin - 1;
       const float* bl = sB + (l - 1) * W;
       float4* act = s_act[l] + ((size_t)tile * W + c0) * 128 + pl;
@@ -330,7 +422,7 @@ __global__ void __launch_bounds__(4 * W, 1) train_fwd_tc_kernel(FwdArgs a) {
           h[1][j] = d1 * z1;
           h[2][j] = d1 * z2 - 2.0f * tt * d1 * z1 * z1;
           h[3][j] = d1 * z3;
-          act[(8 * ch + j) * 128] = make_float4(tt, z1, z2, z3);
+          st_hint(act + (8 * ch + j) * 128, make_float4(tt, z1, z2, z3), keep);
           if (last) {
 #pragma unroll
             for (int s = 0; s < 4; ++s) dot[s] = fmaf(sWo[o], bf16r(h[s][j]), dot[s]);
@@ -339,14 +431,14 @@ __global__ void __launch_bounds__(4 * W, 1) train_fwd_tc_kernel(FwdArgs a) {
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
           const uint4 q = pack8(h[s]);
-          if (!last) *reinterpret_cast<uint4*>(hb + s * AB + ch * 128) = q;
+          if (!last) st_hint(hb + s * AB + ch * 128, q, stream);
           *reinterpret_cast<uint4*>(sa + s * AB + ch * 128) = q;
         }
       }
       fence_before();
     }
     if (s_fail) break;
-    // output streams, loss terms and seeds (one thread per point)
+    // ---- output streams, loss terms and seeds (one thread per point)
 #pragma unroll
     for (int s = 0; s < 4; ++s) sred[(g * 4 + s) * 128 + pl] = dot[s];
     __syncthreads();
@@ -366,161 +458,35 @@ __global__ void __launch_bounds__(4 * W, 1) train_fwd_tc_kernel(FwdArgs a) {
         for (int i = 0; i < DIN; ++i) xin[i] = a.la.X[p * DIN + i];
         double sqe[3] = {0.0, 0.0, 0.0}, gs[4];
         point_loss(a.la, DIN, xin, a.la.kind[p], out, a.cnt, sqe, gs);
-        float* seeds = reinterpret_cast<float*>(a.ws + a.L.seeds);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          seeds[(int64_t)k * N + p] = (float)gs[k];
-          sd[k] = bf16r((float)gs[k]);
-        }
+        for (int k = 0; k < 4; ++k) sd[k] = bf16r((float)gs[k]);
         for (int k = 0; k < 3; ++k)
           if (sqe[k] != 0.0) atomicAdd(&s_acc[k], sqe[k]);
         dbo += sd[0];
       }
 #pragma unroll
-      for (int s = 0; s < 4; ++s)
+      for (int s = 0; s < 4; ++s) {
+        sSd[s * 128 + pl] = sd[s];
         *reinterpret_cast<__nv_bfloat16*>(sSeed + s * kTileB + tile_off(0, pl)) = __float2bfloat16_rn(sd[s]);
+      }
     }
-    // output-layer gradient: sum over streams and points of h_s[i] seed_s
-    fence_proxy_async();
-    fence_before();
-    __syncthreads();
-    fence_after();
-    if (t == 0) {
-#pragma unroll
-      for (int s = 0; s < 4; ++s) edge_mma<W>(tmem, smem_u32(sA + s * AB), smem_u32(sSeed + s * kTileB), s == 0);
-      mma_commit(&bar[0]);
-    }
+    // ---- output-layer gradient: sum over streams and points of h_s[i] seed_s
     {
-      const bool ok = mbar_wait_bounded(&bar[0], ph_mma);
-      ph_mma ^= 1u;
-      if (!ok) {
-        s_fail = 1;
-        mma_lost = true;
-      }
-      fence_after();
-      if (g == 0) {
-        uint32_t r[8];
-        tmem_ld8_nowait(tl, r);
-        tmem_wait_ld();
-        dwo += __uint_as_float(r[0]);
-      }
-      fence_before();
-    }
-  }
-  if (t == 0 && w_pending) (void)mbar_wait_bounded(&bar[1], ph_w);
-  if (t == 0 && mma_lost) (void)mbar_wait_bounded(&bar[0], ph_mma ^ 1u);  // GEMMs still in flight
-  fence_before();
-  __syncthreads();
-  fence_after();
-  if (g == 0 && !s_fail) {
-    double* gL = a.grad + m.poff[n_lin];
-    if (pl < W) atomicAdd(gL + pl, (double)dwo);
-    atomicAdd(gL + W, (double)dbo);
-  }
-  if (t == 0) {
-    atomicAdd(a.loss_acc + 0, s_acc[0]);
-    atomicAdd(a.loss_acc + 1, s_acc[1]);
-    atomicAdd(a.loss_acc + 2, s_acc[2]);
-    if (s_fail) atomicExch(m.status, 6);  // BS_TIMEOUT
-  }
-  if (warp == 0) tmem_dealloc(tmem, NCOLS);
-}
-
-// ---------------------------------------------------------------------------
-// Adjoint, same thread mapping.  From the top hidden layer down: ah_s of layer
-// l (rank one from the seeds at the top, else the four stream GEMMs with the
-// packed W_{l+1}^T), the stored (t, z_1, z_2, z_3), then dz_s of layer l in
-// BF16 to the dzb block (weight gradient) and to the next GEMM's operand.
-// ---------------------------------------------------------------------------
-struct BwdArgs {
-  MlpDev m;
-  const double* X;
-  int64_t N;
-  unsigned char* ws;
-  TcLayout L;
-  double* grad;
-};
-
-template <int DIN, int W>
-__global__ void __launch_bounds__(4 * W, 1) train_bwd_tc_kernel(BwdArgs a) {
-  constexpr uint32_t WB = W * W * 2, AB = 128 * W * 2, SBO = (W / 8) * 128;
-  constexpr uint32_t NCOLS = tmem_cols_streams(W);
-  extern __shared__ __align__(1024) unsigned char smem[];
-  const MlpDev& m = a.m;
-  const int n_lin = m.n_lin, n_sq = n_lin - 2;
-  unsigned char* sW = smem;
-  unsigned char* sA = smem + WB;  // [4][AB]
-  float* sWo = reinterpret_cast<float*>(sA + 4 * AB);
-  // input-layer tiles: [0] rows x^_0 .. x^_{d-1} and 1 (value stream), [1] row
-  // d + 1 = 1 (d/dS stream), [2] row d + 2 = 1 (d/dtau stream)
-  float* sZ1 = sWo + W;  // layer 1: z_1 = W_1[o][0] sc_S and z_3 = W_1[o][1] sc_tau per neuron
-  float* sZ3 = sZ1 + W;
-  unsigned char* sX = reinterpret_cast<unsigned char*>(sZ3 + W);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sX + 3 * kTileB);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
-  __shared__ int s_fail;
-  __shared__ const float4* s_act[16];
-  __shared__ unsigned char* s_dzb[16];
-
-  const int t = threadIdx.x, warp = t >> 5, lane = t & 31, g = warp >> 2;
-  const int pl = (warp & 3) * 32 + lane, c0 = g * 32;
-  const int64_t N = a.N;
-  const int nt = a.L.nt;
-  if (t < 16) {
-    const bool hid = t >= 1 && t < n_lin;
-    s_act[t] = hid ? reinterpret_cast<const float4*>(a.ws + a.L.act[t]) : nullptr;
-    s_dzb[t] = hid ? a.ws + a.L.dzb[t] : nullptr;
-  }
-  for (int o = t; o < W; o += blockDim.x) sWo[o] = bf16r(m.p32[m.poff[n_lin] + o]);
-  for (int i = t; i < (int)(3 * kTileB / 2); i += blockDim.x) {
-    const int k = i / (kTileB / 2), e = i % (kTileB / 2);  // tile, element (n, p) in tile order
-    const int cm = e >> 6, n = (cm >> 4) * 8 + ((e >> 3) & 7);
-    const bool one = (k == 0 && n == DIN) || (k == 1 && n == DIN + 1) || (k == 2 && n == DIN + 2);
-    reinterpret_cast<__nv_bfloat16*>(sX)[i] = __float2bfloat16_rn(one ? 1.0f : 0.0f);
-  }
-  float sc[DIN], of[DIN];
+      uint32_t r[8];
+      if (!edge(
+              [&] {
 #pragma unroll
-  for (int i = 0; i < DIN; ++i) {
-    const double gi = 2.0 / (m.hi[i] - m.lo[i]);
-    sc[i] = (float)gi;
-    of[i] = (float)(-gi * m.lo[i] - 1.0);
-  }
-  for (int o = t; o < W; o += blockDim.x) {
-    sZ1[o] = bf16r(m.p32[m.poff[1] + (int64_t)o * DIN + 0]) * sc[0];
-    sZ3[o] = bf16r(m.p32[m.poff[1] + (int64_t)o * DIN + 1]) * sc[1];
-  }
-  float dw1[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // input-layer gradient: row pl of the edge GEMM
-  if (t == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
-    s_fail = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
-  bool w_pending = false, mma_lost = false;
-  uint32_t ph_w = 0, ph_mma = 0;
-  const unsigned char* wpackT = a.ws + a.L.pack + (size_t)n_sq * WB;
-  if (t == 0 && (int)blockIdx.x < nt) {
-    bulk_load(sW, wpackT + (size_t)(n_sq - 1) * WB, WB, &bar[1]);
-    w_pending = true;
-  }
-  if (warp == 0) tmem_alloc(tslot, NCOLS);
-  fence_before();
-  __syncthreads();
-  fence_after();
-  const uint32_t tmem = *tslot;
-  const uint32_t idesc = make_idesc_bf16(W);
-  const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-  const uint32_t rowoff = (uint32_t)((pl >> 3) * (W / 8) * 128 + (pl & 7) * 16) + (uint32_t)(c0 / 8) * 128;
-  const float* seeds = reinterpret_cast<const float*>(a.ws + a.L.seeds);
-
-  for (int tile = blockIdx.x; tile < nt; tile += gridDim.x) {
-    const int64_t p = (int64_t)tile * 128 + pl;
-    const bool valid = p < N;
-    const bool last_tile = tile + (int)gridDim.x >= nt;
+                for (int s = 0; s < 4; ++s)
+                  edge_mma<W>(tmem, smem_u32(sA + s * AB), smem_u32(sSeed + s * kTileB), s == 0);
+              },
+              r))
+        break;
+      if (g == 0) dwo += __uint_as_float(r[0]);
+    }
+    // ---- adjoint, top hidden layer down
     float sd[4];
 #pragma unroll
-    for (int s = 0; s < 4; ++s) sd[s] = valid ? bf16r(seeds[(int64_t)s * N + p]) : 0.0f;
+    for (int s = 0; s < 4; ++s) sd[s] = sSd[s * 128 + pl];
     for (int l = n_lin - 1; l >= 1; --l) {
       const bool top = l == n_lin - 1;
       const float4* act = s_act[l] + ((size_t)tile * W + c0) * 128 + pl;
@@ -532,13 +498,10 @@ __global__ void __launch_bounds__(4 * W, 1) train_bwd_tc_kernel(BwdArgs a) {
         float4 av[8];
         if (l >= 2) {
 #pragma unroll
-          for (int j = 0; j < 8; ++j) av[j] = __ldg(act + (8 * ch + j) * 128);
+          for (int j = 0; j < 8; ++j) av[j] = act[(8 * ch + j) * 128];
         } else {
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int o = c0 + 8 * ch + j;
-            av[j] = make_float4(__ldg(act1 + (8 * ch + j) * 128), sZ1[o], 0.0f, sZ3[o]);
-          }
+          for (int j = 0; j < 8; ++j) av[j] = make_float4(act1[(8 * ch + j) * 128], sZ1[c0 + 8 * ch + j], 0.0f, sZ3[c0 + 8 * ch + j]);
         }
         float ah[4][8];
         if (top) {
@@ -578,86 +541,45 @@ __global__ void __launch_bounds__(4 * W, 1) train_bwd_tc_kernel(BwdArgs a) {
         for (int s = 0; s < 4; ++s) {
           if (l < 2 && s == 2) continue;  // the input layer's d2/dS2 stream has a zero input
           const uint4 q = pack8(dz[s]);
-          if (l >= 2) *reinterpret_cast<uint4*>(dzb + s * AB + ch * 128) = q;
+          if (l >= 2) st_hint(dzb + s * AB + ch * 128, q, stream);
           *reinterpret_cast<uint4*>(sa + s * AB + ch * 128) = q;
         }
+        // the warp's stored activations of these 8 neurons are dead: drop them from L2
+        __syncwarp();
+        const float4* wbase = s_act[l] + ((size_t)tile * W + c0 + 8 * ch) * 128 + qd * 32;
+        if (l >= 2)
+          discard_l2(reinterpret_cast<const unsigned char*>(wbase + (lane >> 2) * 128) + (lane & 3) * 128);
+        else if (lane < 8)
+          discard_l2(reinterpret_cast<const float*>(s_act[1]) + ((size_t)tile * W + c0 + 8 * ch + lane) * 128 + qd * 32);
       }
       fence_before();
-      if (l < 2) {
-        // input-layer gradient: dz_0 against (x^, 1), dz_1 and dz_3 against ones
-        if (g == 0) {
+      if (l >= 2) {
+        // ah of layer l - 1: dz_l W_l (B = W_l^T) on the tensor cores
+        if (!gemm(n_sq + (n_lin - 1 - l), l > 2 || !last_tile)) break;
+        continue;
+      }
+      // input-layer gradient: dz_0 against (x^, 1), dz_1 and dz_3 against ones
+      if (g == 0) {
 #pragma unroll
-          for (int i = 0; i < DIN; ++i) {
-            const float xh = bf16r(fmaf(valid ? (float)a.X[p * DIN + i] : 0.0f, sc[i], of[i]));
-            *reinterpret_cast<__nv_bfloat16*>(sX + tile_off(i, pl)) = __float2bfloat16_rn(valid ? xh : 0.0f);
-          }
+        for (int i = 0; i < DIN; ++i) {
+          const float xh = valid ? bf16r(fmaf((float)a.la.X[p * DIN + i], sc[i], of[i])) : 0.0f;
+          *reinterpret_cast<__nv_bfloat16*>(sX + tile_off(i, pl)) = __float2bfloat16_rn(xh);
         }
-        fence_proxy_async();
-        fence_before();
-        __syncthreads();
-        fence_after();
-        if (t == 0) {
-          const uint32_t aa = smem_u32(sA), xx = smem_u32(sX);
-          edge_mma<W>(tmem, aa, xx, true);
-          edge_mma<W>(tmem, aa + AB, xx + kTileB, false);
-          edge_mma<W>(tmem, aa + 3 * AB, xx + 2 * kTileB, false);
-          mma_commit(&bar[0]);
-        }
-        const bool ok = mbar_wait_bounded(&bar[0], ph_mma);
-        ph_mma ^= 1u;
-        if (!ok) {
-          s_fail = 1;
-          mma_lost = true;
-        }
-        fence_after();
-        if (g == 0) {
-          uint32_t r[8];
-          tmem_ld8_nowait(tl, r);
-          tmem_wait_ld();
-#pragma unroll
-          for (int j = 0; j < 8; ++j) dw1[j] += __uint_as_float(r[j]);
-        }
-        fence_before();
-        __syncthreads();
+      }
+      uint32_t r[8];
+      if (!edge(
+              [&] {
+                const uint32_t aa = smem_u32(sA), xx = smem_u32(sX);
+                edge_mma<W>(tmem, aa, xx, true);
+                edge_mma<W>(tmem, aa + AB, xx + kTileB, false);
+                edge_mma<W>(tmem, aa + 3 * AB, xx + 2 * kTileB, false);
+              },
+              r))
         break;
-      }
-      // ah of layer l-1: dz_l W_l (B = W_l^T) on the tensor cores
-      if (t == 0 && w_pending) {
-        if (mbar_wait_bounded(&bar[1], ph_w)) {
-          ph_w ^= 1u;
-          w_pending = false;
-        } else {
-          s_fail = 1;
-        }
-      }
-      fence_proxy_async();
-      fence_before();
-      __syncthreads();
-      fence_after();
-      if (s_fail) break;
-      if (t == 0) {
-        const uint32_t aa = smem_u32(sA), bb = smem_u32(sW);
+      if (g == 0) {
 #pragma unroll
-        for (int s = 0; s < 4; ++s)
-          for (int kk = 0; kk < W / 16; ++kk)
-            mma_bf16(tmem + (uint32_t)(s * W), make_desc(aa + s * AB + kk * 256, 128, SBO),
-                     make_desc(bb + kk * 256, 128, SBO), idesc, kk > 0 ? 1u : 0u);
-        mma_commit(&bar[0]);
+        for (int j = 0; j < 8; ++j) dw1[j] += __uint_as_float(r[j]);
       }
-      const bool ok = mbar_wait_bounded(&bar[0], ph_mma);
-      ph_mma ^= 1u;
-      if (!ok) {
-        s_fail = 1;
-        mma_lost = true;
-      }
-      fence_after();
-      if (t == 0 && ok && !(last_tile && l == 2)) {
-        const int nxt = l - 1 >= 2 ? l - 3 : n_sq - 1;  // W_{l-1}^T, or the next tile's first
-        bulk_load(sW, wpackT + (size_t)nxt * WB, WB, &bar[1]);
-        w_pending = true;
-      }
-      __syncthreads();
-      if (s_fail) break;
     }
     if (s_fail) break;
   }
@@ -666,21 +588,31 @@ __global__ void __launch_bounds__(4 * W, 1) train_bwd_tc_kernel(BwdArgs a) {
   fence_before();
   __syncthreads();
   fence_after();
-  if (g == 0 && pl < W && !s_fail) {
-    // dL/dW_1[o][i] = sum dz_0 x^_i (+ sc_S sum dz_1 for i = 0, + sc_tau sum dz_3 for
-    // i = 1, the constant streams of the mapped inputs), dL/db_1[o] = sum dz_0
-    double* g1 = a.grad + m.poff[1];
-    const double sS = (double)bf16r(sc[0]), sT = (double)bf16r(sc[1]);
+  if (g == 0 && !s_fail) {
+    double* gL = a.grad + m.poff[n_lin];
+    atomicAdd(gL + W, (double)dbo);
+    if (pl < W) {
+      atomicAdd(gL + pl, (double)dwo);
+      // dL/dW_1[o][i] = sum dz_0 x^_i (+ sc_S sum dz_1 for i = 0, + sc_tau sum dz_3 for
+      // i = 1: the constant streams of the mapped inputs), dL/db_1[o] = sum dz_0
+      double* g1 = a.grad + m.poff[1];
+      const double sS = (double)bf16r(sc[0]), sT = (double)bf16r(sc[1]);
 #pragma unroll
-    for (int i = 0; i < DIN; ++i) {
-      double v = (double)dw1[i];
-      if (i == 0) v += sS * (double)dw1[DIN + 1];
-      if (i == 1) v += sT * (double)dw1[DIN + 2];
-      atomicAdd(g1 + (int64_t)pl * DIN + i, v);
+      for (int i = 0; i < DIN; ++i) {
+        double v = (double)dw1[i];
+        if (i == 0) v += sS * (double)dw1[DIN + 1];
+        if (i == 1) v += sT * (double)dw1[DIN + 2];
+        atomicAdd(g1 + (int64_t)pl * DIN + i, v);
+      }
+      atomicAdd(g1 + (int64_t)W * DIN + pl, (double)dw1[DIN]);
     }
-    atomicAdd(g1 + (int64_t)W * DIN + pl, (double)dw1[DIN]);
   }
-  if (s_fail && t == 0) atomicExch(m.status, 6);  // BS_TIMEOUT
+  if (t == 0) {
+    atomicAdd(a.loss_acc + 0, s_acc[0]);
+    atomicAdd(a.loss_acc + 1, s_acc[1]);
+    atomicAdd(a.loss_acc + 2, s_acc[2]);
+    if (s_fail) atomicExch(m.status, 6);  // BS_TIMEOUT
+  }
   if (warp == 0) tmem_dealloc(tmem, NCOLS);
 }
 
@@ -876,21 +808,12 @@ cudaError_t run_train_tc(const MlpDev& m, const LossArgs& la, unsigned char* ws,
   const int n_lin = m.n_lin, n_sq = n_lin - 2, nsm = sm_count();
   cudaError_t e;
   {
-    FwdArgs a{m, la, ws, L, cnt, loss_acc, grad};
-    const size_t smem = WB + 4 * AB +
-                        sizeof(float) * ((size_t)W * DIN + (size_t)(n_lin - 1) * W + W + (W / 32) * 4 * 128) +
-                        4 * kTileB + 64;
-    auto kern = train_fwd_tc_kernel<DIN, W>;
-    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-      return e;
-    const int64_t cap = (int64_t)nsm * resident_per_sm(kern, smem, 4 * W, tmem_cols_streams(W));
-    kern<<<(unsigned)(L.nt < cap ? L.nt : cap), 4 * W, smem, s>>>(a);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
-  {
-    BwdArgs a{m, la.X, la.N, ws, L, grad};
-    const size_t smem = WB + 4 * AB + sizeof(float) * 3 * W + 3 * kTileB + 64;
-    auto kern = train_bwd_tc_kernel<DIN, W>;
+    TrainArgs a{m, la, ws, L, cnt, loss_acc, grad};
+    const size_t smem = WB + 4 * AB + 7 * kTileB +
+                        sizeof(float) * ((size_t)W * DIN + (size_t)(n_lin - 1) * W + 3 * W + (W / 32) * 4 * 128 +
+                                         4 * 128) +
+                        64;
+    auto kern = train_tc_kernel<DIN, W>;
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
       return e;
     const int64_t cap = (int64_t)nsm * resident_per_sm(kern, smem, 4 * W, tmem_cols_streams(W));
