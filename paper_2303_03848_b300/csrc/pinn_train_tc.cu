@@ -18,10 +18,12 @@
 //             dL/db[o] = sum over points of dz_0[o].
 //
 // Workspace (NT = ceil(N / 128) tiles, w the hidden width):
-//   act[l]  float4 [NT][w][128]: (t, z_1, z_2, z_3) of hidden layer l >= 2 at
-//           (neuron, point); the adjoint reads it with one 16-byte load per
-//           neuron, 512 contiguous bytes per warp.  Layer 1 keeps t only
-//           (float [NT][w][128]): its z_1 = W_1[o][0] sc_S, z_2 = 0 and
+//   act[l]  float4 [slot][w][128]: (t, z_1, z_2, z_3) of hidden layer l >= 2 at
+//           (neuron, point) of the tile a CTA is working on (one slot per CTA,
+//           reused tile after tile: activations live only between a tile's
+//           forward and its adjoint); the adjoint reads them with one 16-byte
+//           load per neuron, 512 contiguous bytes per warp.  Layer 1 keeps t
+//           only (float [slot][w][128]): its z_1 = W_1[o][0] sc_S, z_2 = 0 and
 //           z_3 = W_1[o][1] sc_tau are constants per neuron;
 //   hb[l]   BF16 [NT][4][128 x w]: h_s of hidden layer l (l < n_lin - 1);
 //   dzb[l]  BF16 [NT][4][128 x w]: dz_s of hidden layer l (l >= 2).
@@ -40,6 +42,7 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <cstdlib>
 
 #include "bs_internal.h"
 #include "pinn_loss.cuh"
@@ -56,8 +59,9 @@ struct TcLayout {
   size_t partial;                   // float [n_sq][ny][w][w + 1]: weight-gradient partial sums
   size_t pack;                      // BF16 square layers: W_l then W_l^T
   size_t total;
-  int nt;  // tiles of 128 points
-  int ny;  // weight-gradient CTAs per square layer
+  int nt;     // tiles of 128 points (of one chunk)
+  int slots;  // activation slots (CTAs of the forward + adjoint kernel)
+  int ny;     // weight-gradient CTAs per square layer
 };
 
 int sm_count() {
@@ -70,18 +74,45 @@ int sm_count() {
   return n;
 }
 
+// Points per pass of the kernels: a larger batch runs as consecutive chunks
+// (the gradient and the loss sums accumulate), so the workspace is bounded
+// whatever the batch.  BSP_TRAIN_CHUNK overrides the default (rounded up to
+// whole 128-point tiles).
+int64_t chunk_points() {
+  int64_t c = (int64_t)1 << 19;
+  if (const char* v = std::getenv("BSP_TRAIN_CHUNK")) {
+    const long long x = std::atoll(v);
+    if (x > 0) c = (x + 127) / 128 * 128;
+  }
+  return c;
+}
+
+__host__ __device__ constexpr uint32_t tmem_cols_streams(int w) {
+  return 4 * w <= 128 ? 128 : (4 * w <= 256 ? 256 : 512);
+}
+
+// Activation slots: one per resident CTA of the forward + adjoint kernel (its
+// four accumulators bound the CTAs per SM by the 512 tensor-memory columns),
+// each reused tile after tile.
+int act_slots(int64_t nt, int w) {
+  const int64_t cap = (int64_t)sm_count() * (512 / tmem_cols_streams(w));
+  return (int)(nt < cap ? nt : cap);
+}
+
 TcLayout tc_layout(const MlpDev& m, int64_t N) {
   TcLayout L{};
   const int w = m.widths[1], n_sq = m.n_lin - 2;
-  const int64_t nt = (N + 127) / 128;
+  const int64_t nc = N < chunk_points() ? N : chunk_points();
+  const int64_t nt = (nc + 127) / 128;
   L.nt = (int)nt;
+  L.slots = act_slots(nt, w);
   size_t o = 0;
   auto take = [&](size_t bytes) {
     const size_t r = o;
     o = (o + bytes + 255) / 256 * 256;
     return r;
   };
-  for (int l = 1; l < m.n_lin; ++l) L.act[l] = take((size_t)nt * w * 128 * (l == 1 ? 4 : 16));
+  for (int l = 1; l < m.n_lin; ++l) L.act[l] = take((size_t)L.slots * w * 128 * (l == 1 ? 4 : 16));
   for (int l = 1; l < m.n_lin - 1; ++l) L.hb[l] = take((size_t)nt * 4 * 128 * w * 2);
   for (int l = 2; l < m.n_lin; ++l) L.dzb[l] = take((size_t)nt * 4 * 128 * w * 2);
   // one wave of weight-gradient CTAs (one per SM) over all square layers
@@ -138,10 +169,6 @@ __device__ __forceinline__ void edge_mma(uint32_t d_tmem, uint32_t a_smem, uint3
   for (int kk = 0; kk < 8; ++kk)
     mma_bf16(d_tmem, make_desc(a_smem + kk * 2 * (W * 16), W * 16, 128), make_desc(b_smem + kk * 256, 128, 2048),
              idesc, (!first || kk > 0) ? 1u : 0u);
-}
-
-__host__ __device__ constexpr uint32_t tmem_cols_streams(int w) {
-  return 4 * w <= 128 ? 128 : (4 * w <= 256 ? 256 : 512);
 }
 
 // ---------------------------------------------------------------------------
@@ -368,7 +395,7 @@ __global__ void __launch_bounds__(4 * W, 1) train_tc_kernel(TrainArgs a) {
       float xh[DIN];
 #pragma unroll
       for (int i = 0; i < DIN; ++i) xh[i] = bf16r(fmaf(valid ? (float)a.la.X[p * DIN + i] : 0.0f, sc[i], of[i]));
-      float* act = reinterpret_cast<float*>(s_act[1]) + ((size_t)tile * W + c0) * 128 + pl;
+      float* act = reinterpret_cast<float*>(s_act[1]) + ((size_t)blockIdx.x * W + c0) * 128 + pl;
       unsigned char* hb = s_hb[1] + (size_t)tile * 4 * AB + rowoff;
       unsigned char* sa = sA + rowoff;
 #pragma unroll
@@ -403,7 +430,7 @@ __global__ void __launch_bounds__(4 * W, 1) train_tc_kernel(TrainArgs a) {
       if (!gemm(sq, true)) break;
       const bool last = l == n_lin - 1;
       const float* bl = sB + (l - 1) * W;
-      float4* act = s_act[l] + ((size_t)tile * W + c0) * 128 + pl;
+      float4* act = s_act[l] + ((size_t)blockIdx.x * W + c0) * 128 + pl;
       unsigned char* hb = last ? nullptr : s_hb[l] + (size_t)tile * 4 * AB + rowoff;
       unsigned char* sa = sA + rowoff;
 #pragma unroll
@@ -489,8 +516,8 @@ __global__ void __launch_bounds__(4 * W, 1) train_tc_kernel(TrainArgs a) {
     for (int s = 0; s < 4; ++s) sd[s] = sSd[s * 128 + pl];
     for (int l = n_lin - 1; l >= 1; --l) {
       const bool top = l == n_lin - 1;
-      const float4* act = s_act[l] + ((size_t)tile * W + c0) * 128 + pl;
-      const float* act1 = reinterpret_cast<const float*>(s_act[1]) + ((size_t)tile * W + c0) * 128 + pl;
+      const float4* act = s_act[l] + ((size_t)blockIdx.x * W + c0) * 128 + pl;
+      const float* act1 = reinterpret_cast<const float*>(s_act[1]) + ((size_t)blockIdx.x * W + c0) * 128 + pl;
       unsigned char* dzb = l >= 2 ? s_dzb[l] + (size_t)tile * 4 * AB + rowoff : nullptr;
       unsigned char* sa = sA + rowoff;
 #pragma unroll
@@ -546,11 +573,12 @@ __global__ void __launch_bounds__(4 * W, 1) train_tc_kernel(TrainArgs a) {
         }
         // the warp's stored activations of these 8 neurons are dead: drop them from L2
         __syncwarp();
-        const float4* wbase = s_act[l] + ((size_t)tile * W + c0 + 8 * ch) * 128 + qd * 32;
+        const float4* wbase = s_act[l] + ((size_t)blockIdx.x * W + c0 + 8 * ch) * 128 + qd * 32;
         if (l >= 2)
           discard_l2(reinterpret_cast<const unsigned char*>(wbase + (lane >> 2) * 128) + (lane & 3) * 128);
         else if (lane < 8)
-          discard_l2(reinterpret_cast<const float*>(s_act[1]) + ((size_t)tile * W + c0 + 8 * ch + lane) * 128 + qd * 32);
+          discard_l2(reinterpret_cast<const float*>(s_act[1]) + ((size_t)blockIdx.x * W + c0 + 8 * ch + lane) * 128 +
+                     qd * 32);
       }
       fence_before();
       if (l >= 2) {
@@ -817,7 +845,9 @@ cudaError_t run_train_tc(const MlpDev& m, const LossArgs& la, unsigned char* ws,
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
       return e;
     const int64_t cap = (int64_t)nsm * resident_per_sm(kern, smem, 4 * W, tmem_cols_streams(W));
-    kern<<<(unsigned)(L.nt < cap ? L.nt : cap), 4 * W, smem, s>>>(a);
+    int64_t grid = L.nt < cap ? L.nt : cap;
+    if (grid > L.slots) grid = L.slots;
+    kern<<<(unsigned)grid, 4 * W, smem, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   {
@@ -888,8 +918,21 @@ cudaError_t launch_train_tc(const MlpDev& m, const LossArgs& la, unsigned char* 
   pack_train_kernel<<<148, 256, 0, s>>>(m, w, wpack, wpack + (size_t)n_sq * w * w * 2);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  return m.d_in == 2 ? run_train_tc_w<2>(m, la, ws, L, cnt, loss_acc, grad, s)
-                     : run_train_tc_w<5>(m, la, ws, L, cnt, loss_acc, grad, s);
+  // consecutive chunks of the batch; the loss terms are means over the whole
+  // batch (cnt), the gradient and loss sums accumulate
+  const int64_t chunk = chunk_points();
+  for (int64_t off = 0; off < la.N; off += chunk) {
+    LossArgs lc = la;
+    lc.X = la.X + off * m.d_in;
+    lc.kind = la.kind + off;
+    lc.N = la.N - off < chunk ? la.N - off : chunk;
+    TcLayout Lc = L;
+    Lc.nt = (int)((lc.N + 127) / 128);
+    e = m.d_in == 2 ? run_train_tc_w<2>(m, lc, ws, Lc, cnt, loss_acc, grad, s)
+                    : run_train_tc_w<5>(m, lc, ws, Lc, cnt, loss_acc, grad, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace bsp

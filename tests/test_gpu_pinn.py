@@ -219,6 +219,28 @@ def test_tensor_core_gradient_every_layer(B, orc, widths):
             assert abs(l3[c].item() - terms[c]) <= 5e-2 * abs(terms[c]), (c, l3[c].item(), terms[c])
 
 
+@pytest.mark.parametrize("arch", ["2-4x64", "5-6x128"])
+def test_tensor_core_training_in_chunks(B, orc, arch, monkeypatch):
+    # a batch run as chunks of 1024 points (4 chunks, the last one ragged) gives
+    # the one-pass result up to the order of the FP32 partial sums, and the oracle's
+    widths = ARCHS[arch]
+    m, om = _model(B, orc, widths, 41)
+    X, kind, prob, sok = _loss_case(widths, 3000, 128, 128, 43)
+    Xd, kd = torch.tensor(X, device="cuda"), torch.tensor(kind, device="cuda")
+    monkeypatch.delenv("BSP_TRAIN_CHUNK", raising=False)
+    l_one, g_one = m.loss_grad(Xd, kd, prob, sok, prec=B.BF16)
+    monkeypatch.setenv("BSP_TRAIN_CHUNK", "1024")
+    l_ch, g_ch = m.loss_grad(Xd, kd, prob, sok, prec=B.BF16)
+    assert m.device_status() == B.BS_OK
+    l_one, g_one, l_ch, g_ch = (v.cpu().numpy() for v in (l_one, g_one, l_ch, g_ch))
+    np.testing.assert_allclose(l_ch, l_one, rtol=1e-12)
+    assert _rel(g_ch, g_one) <= 1e-5
+    terms, grad = orc.pinn_loss_grad(om, X, kind, prob["K"], prob["sigma"], prob["r"], prob["Smax"], sok)
+    for name, a, b in _param_blocks(widths):
+        err = np.abs(g_ch[a:b] - grad[a:b]).max() / max(np.abs(grad[a:b]).max(), 1e-300)
+        assert err <= 2e-2, (name, err)
+
+
 @pytest.mark.parametrize("arch", ["2-4x64", "2-6x128", "5-6x128"])
 def test_tensor_core_training_ragged_batches(B, orc, arch):
     # BF16 loss and gradient through the tensor-core forward, adjoint and weight
