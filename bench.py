@@ -287,12 +287,20 @@ def run_ours(args):
     torch.cuda.synchronize()
     serial_ms = statistics.mean(a.elapsed_time(b) for a, b in sf)
 
-    # per-precision network tables at the same accuracy target
+    # per-precision network tables at the same accuracy target; the coarse output's
+    # error against FP64 is the table u_theta(S_j, tau_n) on the solve's grid
+    S = torch.linspace(0.0, CFG["Smax"], CFG["Nx"], dtype=torch.float64, device="cuda")
+    tau = torch.linspace(0.0, CFG["T"], CFG["P"] + 1, dtype=torch.float64, device="cuda")
+    Xg = torch.stack(torch.meshgrid(S, tau, indexing="xy"), dim=-1).reshape(-1, 2).contiguous()
+    u64 = model.eval(Xg, prec=B.FP64)
     per_prec = {}
     for name, p in B.PREC.items():
         tl, itp, ep = choose_tol(prob, B.COARSE_PINN, model, p, Uf, B)
         msp, _ = time_solves(prob, B.COARSE_PINN, model, p, tl, 2, 1, torch, flush)
-        per_prec[name] = dict(tol=tl, iterations=itp, err_vs_serial_fine=ep, ms_per_solve=statistics.mean(msp))
+        up = model.eval(Xg, prec=p)
+        cerr = ((up - u64).abs().max() / u64.abs().max()).item()
+        per_prec[name] = dict(tol=tl, iterations=itp, err_vs_serial_fine=ep, ms_per_solve=statistics.mean(msp),
+                              coarse_err_vs_fp64=cerr)
 
     # end to end through the C ABI with host buffers
     w_host = torch.tensor(model.get_weights()).pin_memory()
