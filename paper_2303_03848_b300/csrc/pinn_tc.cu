@@ -2,9 +2,11 @@
 // on the 5th-generation tensor cores (tcgen05), BF16 operands, FP32
 // accumulation in tensor memory.
 //
-// One CTA of 128 threads owns a tile of 128 points at a time (the M = 128 rows
-// of every layer GEMM, thread t = point t = TMEM lane t) and walks the tiles
-// persistently.  Per tile:
+// One CTA of 256 threads owns a tile of 128 points at a time (the M = 128 rows
+// of every layer GEMM) and walks the tiles persistently.  Warps v and v + 4
+// read the same 32 accumulator lanes (points 32 v .. 32 v + 31) and split the
+// w columns of every layer between them, so eight warps share each tile's
+// epilogue.  Per tile:
 //   * input layer (2 or 5 inputs -> w): CUDA cores, FP32, written as the BF16
 //     A operand of the first square layer;
 //   * each square layer h' = tanh(W h + b): one thread issues w/16 tcgen05.mma
@@ -13,7 +15,7 @@
 //     the bias, apply FP32 tanh and write the BF16-rounded result as the next
 //     A operand;
 //   * output layer (w -> 1): FP32 tanh of the last hidden layer and a dot
-//     product on CUDA cores.
+//     product on CUDA cores, the two column halves added through shared memory.
 // Operands sit in shared memory in the no-swizzle K-major core-matrix layout
 // (8 rows x 16 bytes per core matrix).  The square layers are packed into that
 // layout once per call and fed to shared memory by TMA bulk copies
@@ -61,10 +63,12 @@ struct TcArgs {
 };
 
 template <int DIN>
-__global__ void __launch_bounds__(128) mlp_tc_kernel(TcArgs a) {
+__global__ void __launch_bounds__(256) mlp_tc_kernel(TcArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const MlpDev& m = a.m;
   const int w = a.w, t = threadIdx.x, warp = t >> 5;
+  const int pt = (warp & 3) * 32 + (t & 31);  // this thread's point (accumulator lane)
+  const int hw = w / 2, cb = (warp >> 2) * hw;  // and its columns [cb, cb + hw)
   const int n_sq = m.n_lin - 2;
   const uint32_t wbytes = (uint32_t)w * w * 2;
   // shared memory carve-up
@@ -76,12 +80,14 @@ __global__ void __launch_bounds__(128) mlp_tc_kernel(TcArgs a) {
   uint64_t* bar = reinterpret_cast<uint64_t*>(sWo + w + 2);             // [0] MMA done, [1] weights landed
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
   __shared__ int s_fail;
+  __shared__ float s_dot[2][128];  // output partial sums of the upper column half, by tile parity
 
   // parameters into shared memory; the input map to [-1, 1] in FP32 registers
-  for (int i = t; i < w * DIN; i += 128) sW1[i] = m.p32[m.poff[1] + i];
+  for (int i = t; i < w * DIN; i += blockDim.x) sW1[i] = m.p32[m.poff[1] + i];
   for (int l = 1; l < m.n_lin; ++l)
-    for (int o = t; o < w; o += 128) sB[(l - 1) * w + o] = m.p32[m.poff[l] + (int64_t)w * m.widths[l - 1] + o];
-  for (int o = t; o < w; o += 128) sWo[o] = m.p32[m.poff[m.n_lin] + o];
+    for (int o = t; o < w; o += blockDim.x)
+      sB[(l - 1) * w + o] = m.p32[m.poff[l] + (int64_t)w * m.widths[l - 1] + o];
+  for (int o = t; o < w; o += blockDim.x) sWo[o] = m.p32[m.poff[m.n_lin] + o];
   const float bout = m.p32[m.poff[m.n_lin] + w];
   float sc[DIN], of[DIN];
 #pragma unroll
@@ -121,14 +127,15 @@ __global__ void __launch_bounds__(128) mlp_tc_kernel(TcArgs a) {
   const uint32_t idesc = make_idesc_bf16(w);
   const uint32_t sbo = (uint32_t)(w / 8) * 128;  // next 8-row group
 
+  const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16);  // this warp's accumulator lanes
   double xn[DIN];  // inputs of this thread's point in the next tile (prefetched)
   {
-    const int64_t p = (int64_t)blockIdx.x * 128 + t;
+    const int64_t p = (int64_t)blockIdx.x * 128 + pt;
 #pragma unroll
     for (int i = 0; i < DIN; ++i) xn[i] = p < a.N ? a.X[p * DIN + i] : 0.0;
   }
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t p = tile * 128 + t;
+    const int64_t p = tile * 128 + pt;
     const bool valid = p < a.N;
     const bool last_tile = tile + gridDim.x >= ntiles;
     float xh[DIN];
@@ -141,7 +148,7 @@ __global__ void __launch_bounds__(128) mlp_tc_kernel(TcArgs a) {
     }
     // input layer on CUDA cores
     float dot = 0.0f;  // output accumulator (used here when there is no square layer)
-    for (int o0 = 0; o0 < w; o0 += 16) {
+    for (int o0 = cb; o0 < cb + hw; o0 += 16) {
 #pragma unroll
       for (int half = 0; half < 2; ++half) {
         const int ob = o0 + half * 8;
@@ -162,7 +169,7 @@ __global__ void __launch_bounds__(128) mlp_tc_kernel(TcArgs a) {
           q.y = tanh_pack_bf16x2(z[2], z[3]);
           q.z = tanh_pack_bf16x2(z[4], z[5]);
           q.w = tanh_pack_bf16x2(z[6], z[7]);
-          *reinterpret_cast<uint4*>(sA + canon_off(t, ob, w)) = q;
+          *reinterpret_cast<uint4*>(sA + canon_off(pt, ob, w)) = q;
         }
       }
     }
@@ -191,36 +198,44 @@ __global__ void __launch_bounds__(128) mlp_tc_kernel(TcArgs a) {
         }
         mma_commit(&bar[0]);
       }
-      const bool ok = mbar_wait_bounded(&bar[0], ph_mma);
-      ph_mma ^= 1u;
-      if (!ok) s_fail = 1;
-      fence_after();
-      // the MMAs have read this layer's weights: fetch the next layer's while
-      // the epilogue runs (one layer at a time when they are not resident)
-      if (t == 0 && ok && !a.resident && !(last_tile && s == n_sq - 1)) {
-        const int nxt = s + 1 < n_sq ? s + 1 : 0;
-        bulk_load(sW, a.packed + (size_t)nxt * wbytes, wbytes, &bar[1]);
-        w_pending = true;
+      // thread 0 waits for the MMAs (the others wait at the barrier without
+      // taking issue slots from the other CTAs' epilogues), then the
+      // tcgen05 fences order the accumulator reads after it
+      if (t == 0) {
+        if (!mbar_wait_bounded(&bar[0], ph_mma)) {
+          s_fail = 1;
+        } else if (!a.resident && !(last_tile && s == n_sq - 1)) {
+          // the MMAs have read this layer's weights: fetch the next layer's while
+          // the epilogue runs (one layer at a time when they are not resident)
+          const int nxt = s + 1 < n_sq ? s + 1 : 0;
+          bulk_load(sW, a.packed + (size_t)nxt * wbytes, wbytes, &bar[1]);
+          w_pending = true;
+        }
       }
+      ph_mma ^= 1u;
+      fence_before();
       __syncthreads();
+      fence_after();
       if (s_fail) break;
       // epilogue: TMEM -> registers (warp reads its 32 lanes), bias, tanh
       const bool last = s == n_sq - 1;
       const float* bl = sB + (s + 1) * w;
-      for (int c = 0; c < w; c += 32) {
-        float v[32];
-        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+      for (int c = cb; c < cb + hw; c += 16) {
+        uint32_t r[16];
+        tmem_ld16_nowait(tl + (uint32_t)c, r);
+        tmem_wait_ld();
+        float v[16];
 #pragma unroll
-        for (int j = 0; j < 32; j += 4) {
+        for (int j = 0; j < 16; j += 4) {
           const float4 bq = *reinterpret_cast<const float4*>(bl + c + j);
-          v[j] += bq.x;
-          v[j + 1] += bq.y;
-          v[j + 2] += bq.z;
-          v[j + 3] += bq.w;
+          v[j] = __uint_as_float(r[j]) + bq.x;
+          v[j + 1] = __uint_as_float(r[j + 1]) + bq.y;
+          v[j + 2] = __uint_as_float(r[j + 2]) + bq.z;
+          v[j + 3] = __uint_as_float(r[j + 3]) + bq.w;
         }
         if (last) {
 #pragma unroll
-          for (int j = 0; j < 32; j += 4) {
+          for (int j = 0; j < 16; j += 4) {
             const float4 wq = *reinterpret_cast<const float4*>(sWo + c + j);
             dot = fmaf(wq.x, tanh_fast(v[j]), dot);
             dot = fmaf(wq.y, tanh_fast(v[j + 1]), dot);
@@ -229,20 +244,25 @@ __global__ void __launch_bounds__(128) mlp_tc_kernel(TcArgs a) {
           }
         } else {
 #pragma unroll
-          for (int j = 0; j < 32; j += 8) {
+          for (int j = 0; j < 16; j += 8) {
             uint4 q;
             q.x = tanh_pack_bf16x2(v[j], v[j + 1]);
             q.y = tanh_pack_bf16x2(v[j + 2], v[j + 3]);
             q.z = tanh_pack_bf16x2(v[j + 4], v[j + 5]);
             q.w = tanh_pack_bf16x2(v[j + 6], v[j + 7]);
-            *reinterpret_cast<uint4*>(sA + canon_off(t, c + j, w)) = q;
+            *reinterpret_cast<uint4*>(sA + canon_off(pt, c + j, w)) = q;
           }
         }
       }
       fence_before();  // tensor-memory reads done before the next MMA overwrites the accumulator
     }
     if (s_fail) break;
-    if (valid) a.u[p] = (double)(dot + bout);
+    // the two column halves of the output dot product (two buffers: without a
+    // square layer this is the only barrier of a tile)
+    const int par = (int)((tile / gridDim.x) & 1);
+    if (warp >= 4) s_dot[par][pt] = dot;
+    __syncthreads();
+    if (warp < 4 && valid) a.u[p] = (double)(dot + s_dot[par][pt] + bout);
   }
   // a weight copy still in flight (only after a failed wait) lands before exit
   if (t == 0 && w_pending) (void)mbar_wait_bounded(&bar[1], ph_w);
@@ -315,7 +335,7 @@ cudaError_t launch_mlp_eval_tc(const MlpDev& m, unsigned char* packed, const dou
   cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
   cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
   int per_sm = (int)((size_t)sm_smem / (smem + fa.sharedSizeBytes + (size_t)reserved));
-  const int by_regs = 65536 / (128 * (fa.numRegs > 0 ? fa.numRegs : 255));
+  const int by_regs = 65536 / (256 * (fa.numRegs > 0 ? fa.numRegs : 255));
   if (per_sm > by_regs) per_sm = by_regs;
   if (per_sm < 1) per_sm = 1;
   int ncols = 32;
@@ -324,7 +344,7 @@ cudaError_t launch_mlp_eval_tc(const MlpDev& m, unsigned char* packed, const dou
   if (per_sm > 4) per_sm = 4;
   const int64_t ntiles = (N + 127) / 128;
   const int64_t grid = ntiles < (int64_t)nsm * per_sm ? ntiles : (int64_t)nsm * per_sm;
-  kern<<<(unsigned)grid, 128, smem, s>>>(a);
+  kern<<<(unsigned)grid, 256, smem, s>>>(a);
   return cudaGetLastError();
 }
 
