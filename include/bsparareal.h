@@ -82,6 +82,16 @@ const char* bs_status_string(int status);
 const char* bs_version(void);
 
 /*
+ * bs_wait_probe -- diagnostic of the device-side failure detection: one CTA
+ * runs a bounded mbarrier wait the way the tensor-core kernels do (try_wait
+ * with an SM clock limit of limit_cycles, 1 .. 2^34) on a barrier that one
+ * thread completes (arrive != 0) or that nothing completes (arrive == 0).
+ * *status (host) receives BS_OK or BS_TIMEOUT; the context stays usable after
+ * a timeout.  Synchronous.  Errors: BS_EINVAL, BS_ECUDA.
+ */
+int bs_wait_probe(int32_t arrive, int64_t limit_cycles, int32_t* status);
+
+/*
  * bs_problem_init -- set up n_instances pricing problems on the current device.
  *   p: host array of n_instances parameter sets.  Requirements per instance:
  *      K > 0, sigma > 0, r >= 0, T > 0, Smax > K, 5 <= Nx <= 65537, P >= 1,
@@ -204,6 +214,16 @@ int pinn_num_params(const pinn_model* m, int64_t* n);
 int pinn_set_weights(pinn_model* m, const double* flat_host);
 /* Copy the FP64 master parameters out (host).  Synchronous. */
 int pinn_get_weights(const pinn_model* m, double* flat_host);
+/*
+ * pinn_get_state / pinn_set_state -- the whole training state, for checkpoint
+ * and resume: FP64 master parameters, Adam's first and second moments (host,
+ * n_params doubles each) and the Adam step count.  pinn_set_state refreshes
+ * the reduced-precision copies; a train step after it continues exactly as
+ * after the pinn_get_state it came from.  Synchronous.  Errors: BS_EINVAL
+ * (null pointer, non-finite value, negative second moment or step), BS_ECUDA.
+ */
+int pinn_get_state(const pinn_model* m, double* theta, double* mom1, double* mom2, int64_t* step);
+int pinn_set_state(pinn_model* m, const double* theta, const double* mom1, const double* mom2, int64_t step);
 
 /*
  * pinn_device_status -- synchronises the device and reports the network's

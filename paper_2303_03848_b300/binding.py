@@ -86,6 +86,9 @@ def lib() -> ctypes.CDLL:
         L.pinn_num_params.argtypes = [vp, P(i64)]
         L.pinn_set_weights.argtypes = [vp, P(dbl)]
         L.pinn_get_weights.argtypes = [vp, P(dbl)]
+        L.pinn_get_state.argtypes = [vp, P(dbl), P(dbl), P(dbl), P(i64)]
+        L.pinn_set_state.argtypes = [vp, P(dbl), P(dbl), P(dbl), i64]
+        L.bs_wait_probe.argtypes = [i32, i64, P(i32)]
         L.pinn_eval.argtypes = [vp, ctypes.c_int, vp, i64, vp, vp, vp]
         L.pinn_device_status.argtypes = [vp, P(ctypes.c_int)]
         L.pinn_loss_grad.argtypes = [vp, vp, vp, i64, P(BsParams), dbl, ctypes.c_int, vp, vp, vp]
@@ -101,6 +104,66 @@ def status_string(code: int) -> str:
 
 def version() -> str:
     return lib().bs_version().decode()
+
+
+def wait_probe(arrive: bool, limit_cycles: int) -> int:
+    """bs_wait_probe: run one bounded device wait on a barrier that is completed
+    (arrive) or never completed; returns BS_OK or BS_TIMEOUT."""
+    s = ctypes.c_int32(-1)
+    _check(lib().bs_wait_probe(1 if arrive else 0, int(limit_cycles), ctypes.byref(s)), "bs_wait_probe")
+    return s.value
+
+
+# Checkpoint file of a network's training state: magic, then little-endian
+# int32 layer count L and widths[L + 1], float64 lo[d_in] and hi[d_in], int64
+# Adam step and n_params, then float64 theta, first and second moments.
+CKPT_MAGIC = b"BSPINN01"
+
+
+def write_checkpoint(path, widths, lo, hi, step, theta, mom1, mom2):
+    import struct
+
+    widths = [int(w) for w in widths]
+    n = len(theta)
+    if len(mom1) != n or len(mom2) != n or len(lo) != widths[0] or len(hi) != widths[0]:
+        raise ValueError("inconsistent checkpoint arrays")
+    with open(path, "wb") as f:
+        f.write(CKPT_MAGIC)
+        f.write(struct.pack("<i", len(widths) - 1))
+        f.write(struct.pack(f"<{len(widths)}i", *widths))
+        f.write(struct.pack(f"<{len(lo)}d", *[float(v) for v in lo]))
+        f.write(struct.pack(f"<{len(hi)}d", *[float(v) for v in hi]))
+        f.write(struct.pack("<qq", int(step), n))
+        for a in (theta, mom1, mom2):
+            f.write(np.ascontiguousarray(a, dtype="<f8").tobytes())
+
+
+def read_checkpoint(path) -> dict:
+    import struct
+
+    with open(path, "rb") as f:
+        data = f.read()
+    if data[:8] != CKPT_MAGIC:
+        raise ValueError("not a network checkpoint")
+    o = 8
+    (nl,) = struct.unpack_from("<i", data, o)
+    o += 4
+    if not 1 <= nl <= 15:
+        raise ValueError("bad layer count")
+    widths = list(struct.unpack_from(f"<{nl + 1}i", data, o))
+    o += 4 * (nl + 1)
+    d = widths[0]
+    lo = list(struct.unpack_from(f"<{d}d", data, o))
+    o += 8 * d
+    hi = list(struct.unpack_from(f"<{d}d", data, o))
+    o += 8 * d
+    step, n = struct.unpack_from("<qq", data, o)
+    o += 16
+    if len(data) != o + 3 * 8 * n:
+        raise ValueError("truncated or oversized checkpoint")
+    arr = np.frombuffer(data, dtype="<f8", count=3 * n, offset=o).astype(np.float64)
+    return dict(widths=widths, lo=lo, hi=hi, step=step, theta=arr[:n].copy(), mom1=arr[n:2 * n].copy(),
+                mom2=arr[2 * n:].copy())
 
 
 def header_functions() -> list[str]:
@@ -371,11 +434,34 @@ class PinnModel:
                "pinn_get_weights")
         return out
 
-    def slices_per_cta(self, i: int = 0) -> int:
-        """1, or 2 when instance i's fine propagation runs two slices per CTA."""
-        s = ctypes.c_int32()
-        _check(lib().bs_problem_slices_per_cta(self._h, i, ctypes.byref(s)), "bs_problem_slices_per_cta")
-        return s.value
+    def get_state(self):
+        """(theta, Adam first moment, second moment, Adam step) from pinn_get_state."""
+        arrs = [np.empty(self.n_params) for _ in range(3)]
+        step = ctypes.c_int64()
+        dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        _check(lib().pinn_get_state(self._h, dp(arrs[0]), dp(arrs[1]), dp(arrs[2]), ctypes.byref(step)),
+               "pinn_get_state")
+        return arrs[0], arrs[1], arrs[2], step.value
+
+    def set_state(self, theta, mom1, mom2, step: int):
+        arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (theta, mom1, mom2)]
+        if any(a.size != self.n_params for a in arrs):
+            raise ValueError("wrong parameter count")
+        dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        _check(lib().pinn_set_state(self._h, dp(arrs[0]), dp(arrs[1]), dp(arrs[2]), int(step)), "pinn_set_state")
+
+    def save(self, path):
+        """Checkpoint the training state (write_checkpoint format)."""
+        theta, m1, m2, step = self.get_state()
+        write_checkpoint(path, self.widths, self.lo, self.hi, step, theta, m1, m2)
+
+    def load(self, path):
+        """Resume from a checkpoint of a network of the same shape and input box."""
+        c = read_checkpoint(path)
+        if c["widths"] != self.widths or c["lo"] != [float(v) for v in self.lo] or \
+                c["hi"] != [float(v) for v in self.hi]:
+            raise ValueError("checkpoint of a different network")
+        self.set_state(c["theta"], c["mom1"], c["mom2"], c["step"])
 
     def device_status(self) -> int:
         """Synchronise and read the device status word (BS_OK or BS_TIMEOUT)."""

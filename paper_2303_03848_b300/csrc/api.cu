@@ -4,6 +4,7 @@
 // and enqueues kernels; every step of the numerical path runs in the kernels
 // of solver.cu and pinn.cu.
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -643,6 +644,45 @@ int pinn_get_weights(const pinn_model* m, double* flat_host) {
   cudaError_t e = cudaDeviceSynchronize();
   if (e == cudaSuccess) e = cudaMemcpy(flat_host, m->p64, sizeof(double) * m->n_params, cudaMemcpyDeviceToHost);
   return map_err(e);
+}
+
+int pinn_get_state(const pinn_model* m, double* theta, double* mom1, double* mom2, int64_t* step) {
+  if (!m || !theta || !mom1 || !mom2 || !step) return BS_EINVAL;
+  const size_t bytes = sizeof(double) * m->n_params;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(theta, m->p64, bytes, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(mom1, m->mom1, bytes, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(mom2, m->mom2, bytes, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) *step = m->step;
+  return map_err(e);
+}
+
+int pinn_set_state(pinn_model* m, const double* theta, const double* mom1, const double* mom2, int64_t step) {
+  if (!m || !theta || !mom1 || !mom2 || step < 0 || step > INT32_MAX) return BS_EINVAL;
+  for (int64_t i = 0; i < m->n_params; ++i)
+    if (!std::isfinite(theta[i]) || !std::isfinite(mom1[i]) || !std::isfinite(mom2[i]) || mom2[i] < 0.0)
+      return BS_EINVAL;
+  int rc = upload_params(m, theta);
+  if (rc != BS_OK) return rc;
+  const size_t bytes = sizeof(double) * m->n_params;
+  cudaError_t e = cudaMemcpy(m->mom1, mom1, bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(m->mom2, mom2, bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) m->step = (int)step;
+  return map_err(e);
+}
+
+int bs_wait_probe(int32_t arrive, int64_t limit_cycles, int32_t* status) {
+  if (!status || limit_cycles < 1 || limit_cycles > (int64_t)1 << 34) return BS_EINVAL;
+  int* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, sizeof(int));
+  if (e != cudaSuccess) return map_err(e);
+  int h = -1;
+  e = bsp::launch_wait_probe(arrive != 0, (long long)limit_cycles, d, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return map_err(e);
+  *status = h;
+  return BS_OK;
 }
 
 int pinn_eval(const pinn_model* m, int prec, const double* X, int64_t N, double* u, double* derivs, void* stream) {

@@ -122,6 +122,8 @@ bool train_tc_supported(const MlpDev& m);
 size_t train_tc_workspace_bytes(const MlpDev& m, int64_t N);
 cudaError_t launch_train_tc(const MlpDev& m, const LossArgs& la, unsigned char* ws, const unsigned long long* cnt,
                             double* loss_acc, double* grad, cudaStream_t s);
+// A bounded mbarrier wait that expires (arrive == 0) or completes (pinn_tc.cu).
+cudaError_t launch_wait_probe(int arrive, long long limit, int* status, cudaStream_t s);
 cudaError_t launch_adam(int64_t n, double* theta, double* mom1, double* mom2, const double* g, int step, double lr,
                         float* p32, cudaStream_t s);
 

@@ -275,6 +275,26 @@ __global__ void __launch_bounds__(256) mlp_tc_kernel(TcArgs a) {
   }
 }
 
+// One bounded wait as the network kernels do it, on a barrier that one thread
+// completes (arrive != 0) or that nothing completes: status = BS_OK or BS_TIMEOUT.
+__global__ void wait_probe_kernel(int arrive, long long limit, int* status) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (arrive && threadIdx.x == 0) mbar_arrive(&bar);
+  const bool ok = mbar_wait_bounded(&bar, 0u, limit);
+  __syncthreads();
+  if (threadIdx.x == 0) *status = ok ? 0 : 6;  // BS_OK, BS_TIMEOUT
+}
+
+cudaError_t launch_wait_probe(int arrive, long long limit, int* status, cudaStream_t s) {
+  wait_probe_kernel<<<1, 32, 0, s>>>(arrive, limit, status);
+  return cudaGetLastError();
+}
+
 // Shape supported by the tensor-core path: all hidden layers w x w (w a multiple
 // of 32, 32 <= w <= 256), 2 or 5 inputs, output width 1.
 bool tc_supported(const MlpDev& m) {

@@ -72,13 +72,18 @@ __device__ __forceinline__ uint32_t mbar_try_wait(uint64_t* bar, uint32_t parity
   return ok;
 }
 
-// Bounded wait: true when the phase completed, false after the limit.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+// Bounded wait: true when the phase completed, false after `limit` SM clock
+// cycles (default about 2 s at 2 GHz).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit = 1LL << 32) {
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > (1LL << 32)) return false;  // about 2 s at 2 GHz
+    if (clock64() - t0 > limit) return false;
   }
   return true;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 // TMA bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned)

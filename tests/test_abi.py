@@ -61,8 +61,37 @@ def test_null_arguments_rejected(L):
     assert L.bs_problem_slices_per_cta(None, 0, None) == B.BS_EINVAL
     assert L.bs_problem_init_tuned(None, 1, ctypes.byref(h), None, 0, None) == B.BS_EINVAL
     assert L.bs_problem_init_tuned(ctypes.byref(p), 1, ctypes.byref(h), None, 4, None) == B.BS_EINVAL
+    s = ctypes.c_int32()
+    assert L.bs_wait_probe(0, 0, ctypes.byref(s)) == B.BS_EINVAL  # limit out of range
+    assert L.bs_wait_probe(0, 1 << 35, ctypes.byref(s)) == B.BS_EINVAL
+    assert L.bs_wait_probe(0, 1000, None) == B.BS_EINVAL
+    assert L.pinn_get_state(None, None, None, None, None) == B.BS_EINVAL
+    assert L.pinn_set_state(None, None, None, None, 0) == B.BS_EINVAL
     L.bs_problem_destroy(None)
     L.pinn_destroy(None)
+
+
+def test_checkpoint_file_round_trip(tmp_path):
+    # the network checkpoint format: header and three FP64 arrays, exact
+    rng = np.random.default_rng(3)
+    widths, lo, hi = [5, 16, 16, 1], [0.0, 0.0, 0.1, 0.0, 0.5], [8.0, 2.0, 0.5, 0.08, 2.0]
+    n = 5 * 16 + 16 + 16 * 16 + 16 + 16 + 1
+    th, m1, m2 = rng.standard_normal(n), rng.standard_normal(n), rng.random(n)
+    path = tmp_path / "net.ckpt"
+    B.write_checkpoint(path, widths, lo, hi, 17, th, m1, m2)
+    c = B.read_checkpoint(path)
+    assert c["widths"] == widths and c["lo"] == lo and c["hi"] == hi and c["step"] == 17
+    for k, a in (("theta", th), ("mom1", m1), ("mom2", m2)):
+        assert np.array_equal(c[k], a)
+    raw = path.read_bytes()
+    (tmp_path / "cut").write_bytes(raw[:-8])
+    with pytest.raises(ValueError):
+        B.read_checkpoint(tmp_path / "cut")
+    (tmp_path / "magic").write_bytes(b"X" + raw[1:])
+    with pytest.raises(ValueError):
+        B.read_checkpoint(tmp_path / "magic")
+    with pytest.raises(ValueError):
+        B.write_checkpoint(path, widths, lo, hi, 0, th, m1[:-1], m2)
 
 
 @pytest.mark.parametrize("widths", [[3, 8, 1], [2, 8, 2], [2, 300, 1], [2, 0, 1]])

@@ -1,0 +1,71 @@
+"""Failure detection without a GPU fault, and checkpoint / resume of training.
+
+A bounded device wait on a barrier that nothing completes must give up after
+its limit and report BS_TIMEOUT through the status word, leaving the context
+usable; the same wait on a completed barrier reports BS_OK.  A network's
+training state (weights, Adam moments, step) saved to a file and loaded into
+another handle continues training as the original does."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_2303_03848_b300 import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2303_03848_b300 import binding, build
+
+    build.build()
+    return binding
+
+
+def test_bounded_wait_expires_and_the_context_stays_usable(B):
+    B.wait_probe(True, 1 << 20)  # first launch: module load out of the timing
+    t0 = time.perf_counter()
+    assert B.wait_probe(False, 4_000_000) == B.BS_TIMEOUT  # about 2 ms at 2 GHz
+    assert time.perf_counter() - t0 < 5.0
+    assert B.wait_probe(True, 4_000_000) == B.BS_OK
+    # the device still runs ordinary work after the timed-out wait
+    prob = B.Problem(B.params(Nx=64, P=2, fine_steps=8))
+    U = torch.zeros(prob.total_slice, dtype=torch.float64, device="cuda")
+    out = torch.empty_like(U)
+    prob.fine_propagate(U, out)
+    torch.cuda.synchronize()
+    assert torch.isfinite(out).all()
+    assert prob.device_status() == B.BS_OK
+
+
+@pytest.mark.parametrize("prec_name", ["FP64", "BF16"])
+def test_checkpoint_resume_continues_training(B, tmp_path, prec_name):
+    prec = getattr(B, prec_name)
+    widths, lo, hi = [2, 64, 64, 64, 1], [0.0, 0.0], [4.0, 1.0]
+    X, kind = synth.collocation(5, 900, 64, 64, 4.0, 1.0)
+    Xd, kd = torch.tensor(X, device="cuda"), torch.tensor(kind, device="cuda")
+    prob = dict(K=1.0, sigma=0.2, r=0.05, T=1.0, Smax=4.0, Nx=5, P=1, fine_steps=1, coarse_steps=1)
+    a = B.PinnModel(widths, lo, hi, seed=1)
+    for _ in range(3):
+        a.train_step(Xd, kd, prob, lr=1e-3, prec=prec)
+    saved = a.get_state()
+    a.save(tmp_path / "a.ckpt")
+    for _ in range(2):
+        a.train_step(Xd, kd, prob, lr=1e-3, prec=prec)
+    wa = a.get_weights()
+    b = B.PinnModel(widths, lo, hi, seed=2)  # other weights until the load
+    b.load(tmp_path / "a.ckpt")
+    restored = b.get_state()
+    for x, y in zip(saved[:3], restored[:3]):
+        assert np.array_equal(x, y)
+    assert restored[3] == saved[3] == 3
+    for _ in range(2):
+        b.train_step(Xd, kd, prob, lr=1e-3, prec=prec)
+    # the gradient's FP64 atomic sums may add in another order: agree to rounding
+    assert np.abs(b.get_weights() - wa).max() <= 1e-12 * max(np.abs(wa).max(), 1.0)
+    with pytest.raises(ValueError):
+        B.PinnModel([2, 32, 1], lo, hi).load(tmp_path / "a.ckpt")
