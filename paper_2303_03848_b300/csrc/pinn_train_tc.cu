@@ -17,7 +17,8 @@
 //   gradient  dL/dW[o][i] = sum over streams and points of dz_s[o] h_s[i],
 //             dL/db[o] = sum over points of dz_0[o].
 //
-// Workspace (NT = ceil(N / 128) tiles, w the hidden width):
+// Workspace (w the hidden width; a batch runs as chunks of at most 2^19 points,
+// NT = the 128-point tiles of one chunk):
 //   act[l]  float4 [slot][w][128]: (t, z_1, z_2, z_3) of hidden layer l >= 2 at
 //           (neuron, point) of the tile a CTA is working on (one slot per CTA,
 //           reused tile after tile: activations live only between a tile's
