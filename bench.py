@@ -653,13 +653,19 @@ def run_large(args):
     pt = (cfg["Nx"] - 2) * cfg["fine_steps"] * cfg["P"]
     tf = FLOPS_PER_PT_STEP * pt / (fine_ms * 1e-3) / 1e12
     peak = 148 * 2 * 2 * float(_peaks().get("sm_max_mhz", 2032.0)) * 1e6 / 1e12
-    a, b = ev()
-    a.record()
-    U, norms, stats, rc = prob.parareal_solve(B.COARSE_IE, tol=1e-9, max_iter=cfg["P"])
-    b.record()
-    torch.cuda.synchronize()
-    err = rel_error(U, Uf, cfg["P"], cfg["Nx"])
-    ie_ms = a.elapsed_time(b)
+    # implicit-Euler coarse Parareal to 1e-8 against serial fine: the loosest
+    # device tolerance (increment norm) that reaches it, each candidate solve timed
+    target = 1e-8
+    for ie_tol in (1e-7, 3e-8, 1e-8, 3e-9, 1e-9, 1e-10, 0.0):
+        a, b = ev()
+        a.record()
+        U, norms, stats, rc = prob.parareal_solve(B.COARSE_IE, tol=ie_tol, max_iter=cfg["P"])
+        b.record()
+        torch.cuda.synchronize()
+        err = rel_error(U, Uf, cfg["P"], cfg["Nx"])
+        ie_ms = a.elapsed_time(b)
+        if err <= target:
+            break
     # the network coarse propagator of this workload: 2->8x256 tanh, BF16 on the
     # tensor cores, evaluated on the (P+1) x Nx grid (the table one solve needs);
     # under a state-independent coarse propagator the solve itself needs k = P
@@ -683,7 +689,7 @@ def run_large(args):
             "status": net.device_status()}
     print(json.dumps({"mode": "large", "config": cfg, "partition": part, "serial_fine_ms": serial_ms,
                       "fine_ms": fine_ms, "grid_pt_steps_per_s": pt / (fine_ms * 1e-3), "fine_tflops_algorithmic": tf,
-                      "fine_frac_of_fp64_peak": tf / peak, "ie_solve_ms": ie_ms,
+                      "fine_frac_of_fp64_peak": tf / peak, "ie_target": target, "ie_tol": ie_tol, "ie_solve_ms": ie_ms,
                       "ie_iterations": stats[0]["iterations"], "ie_err_vs_serial_fine": err,
                       "speedup_vs_serial_fine": serial_ms / ie_ms, "status": rc, "pinn_coarse_table": pinn}),
           flush=True)
