@@ -161,26 +161,30 @@ def rel_error(U, Uref, P, Nx):
     return float(((a - b).norm(dim=1) / b.norm(dim=1)).max().item())
 
 
-def train_network(B, torch, steps, seed=0):
+def train_network(B, torch, steps, seed=0, prec=None):
+    """The benchmark network: full-batch Adam on the collocation set, BF16 operands on
+    the tensor cores (FP32 accumulation, FP64 master weights) unless prec says otherwise."""
     from paper_2303_03848_b300 import synth
 
+    prec = B.BF16 if prec is None else prec
     X, kind = synth.collocation(seed, N_INTERIOR, N_BOUNDARY, N_EXPIRY, CFG["Smax"], CFG["T"])
     Xd = torch.tensor(X, device="cuda")
     kd = torch.tensor(kind, device="cuda")
     m = B.PinnModel(WIDTHS, [0.0, 0.0], [CFG["Smax"], CFG["T"]], seed=seed)
-    loss0 = m.train_step(Xd, kd, CFG, lr=1e-3, prec=B.FP32, want_loss=True)
+    loss0 = m.train_step(Xd, kd, CFG, lr=1e-3, prec=prec, want_loss=True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     timed = min(200, max(steps - 1, 1))
     for i in range(1, steps):
         if i == steps - timed:
             e0.record()
-        m.train_step(Xd, kd, CFG, lr=1e-3, prec=B.FP32)
+        m.train_step(Xd, kd, CFG, lr=1e-3, prec=prec)
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / timed if steps > 1 else float("nan")
-    loss1 = m.train_step(Xd, kd, CFG, lr=1e-3, prec=B.FP32, want_loss=True)
-    return m, dict(steps=steps, ms_per_step=ms, points=len(kind), loss_first=loss0, loss_last=loss1,
-                   points_per_s=len(kind) / (ms * 1e-3) if ms == ms else None)
+    loss1 = m.train_step(Xd, kd, CFG, lr=1e-3, prec=prec, want_loss=True)
+    name = {B.FP64: "fp64", B.FP32: "fp32", B.BF16: "bf16 (tcgen05)"}[prec]
+    return m, dict(steps=steps, precision=name, ms_per_step=ms, points=len(kind), loss_first=loss0,
+                   loss_last=loss1, points_per_s=len(kind) / (ms * 1e-3) if ms == ms else None)
 
 
 def choose_tol(prob, kind, model, prec, Uf, B):
