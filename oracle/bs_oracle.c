@@ -12,7 +12,7 @@
  * Ibrahim, Goetschel, Ruprecht, arXiv:2303.03848) by eye: no blocking, no
  * fusion, no reordering beyond what the cited passage states.
  *
- * Conventions (readings of the paper, listed in full in the design doc):
+ * Conventions (readings of the paper where it is silent or ambiguous):
  *  - time-to-maturity tau = T - t, so the terminal condition (Eq. 2) becomes
  *    an initial condition and the solve runs forward in tau (Section 3.2
  *    solves the t-problem backwards from T; this is the same computation);
