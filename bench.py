@@ -403,7 +403,7 @@ def run_fine_only(args):
                       "tflops_algorithmic": FLOPS_PER_PT_STEP * pt / (ms * 1e-3) / 1e12}), flush=True)
 
 
-def batched_leg(B, torch, n_inst=4096, solve=True, rule_too=False):
+def batched_leg(B, torch, n_inst=4096, solve=True, rule_too=False, pinn_solve=False):
     """Batched workload: n_inst instances (K, sigma, r, T, Nx seeded), P=64, CN 256 steps/slice.
 
     The partition of every grid size is picked by the autotuner
@@ -411,6 +411,9 @@ def batched_leg(B, torch, n_inst=4096, solve=True, rule_too=False):
     instance (one launch per partition class) and, optionally, one
     implicit-Euler-coarse Parareal solve of the whole batch at tol 1e-6.
     rule_too: also time the built-in partition rule for comparison.
+    pinn_solve: also one Parareal solve of the batch with the parametric network
+    5->6x128 (BF16 table) as coarse propagator, and both solves' error against
+    the batch's serial fine solution.
     """
     from paper_2303_03848_b300 import synth
 
@@ -475,9 +478,58 @@ def batched_leg(B, torch, n_inst=4096, solve=True, rule_too=False):
                     "ie_iterations_mean": float(sum(its)) / len(its), "ie_iterations_max": max(its),
                     "ie_status": rc})
         del g
+        if pinn_solve:
+            Uf = prob.serial_fine()
+
+            def batch_error(U):
+                worst = 0.0
+                for i, p in enumerate(insts):
+                    o, P, Nx = prob.state_off[i], p["P"], p["Nx"]
+                    a = U[o + Nx:o + (P + 1) * Nx].view(P, Nx)
+                    b = Uf[o + Nx:o + (P + 1) * Nx].view(P, Nx)
+                    worst = max(worst, float(((a - b).norm(dim=1) / b.norm(dim=1)).max()))
+                return worst
+
+            U, _, _, _ = prob.parareal_solve(B.COARSE_IE, tol=1e-6, max_iter=64, want_stats=False)
+            out["ie_err_vs_serial_fine"] = batch_error(U)
+            del U
+            net, tr = train_parametric(B, torch)
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record()
+            U, norms, stats, rc = prob.parareal_solve(B.COARSE_PINN, model=net, prec=B.BF16, tol=1e-6, max_iter=64)
+            s1.record()
+            torch.cuda.synchronize()
+            pits = [st["iterations"] for st in stats]
+            pms = s0.elapsed_time(s1)
+            out["pinn_coarse"] = {"network": "5->6x128 tanh->1, BF16 table on the tensor cores", "training": tr,
+                                  "solve_ms": pms, "solves_per_s": n_inst / (pms * 1e-3), "tol": 1e-6,
+                                  "iterations_mean": float(sum(pits)) / len(pits), "iterations_max": max(pits),
+                                  "err_vs_serial_fine": batch_error(U), "status": rc,
+                                  "launch": "direct call (host loop over iterations)"}
+            del U, Uf
     prob.close()
     torch.cuda.empty_cache()
     return out
+
+
+def train_parametric(B, torch, steps=300, n_points=65536):
+    """The batched workload's coarse network 5->6x128 tanh on (S, tau, sigma, r, K):
+    BF16 full-batch Adam on seeded collocation points over the batch's parameter box."""
+    from paper_2303_03848_b300 import synth
+
+    widths = [5] + [128] * 6 + [1]
+    lo, hi = [0.0, 0.0, 0.1, 0.0, 0.5], [8.0, 2.0, 0.5, 0.08, 2.0]
+    nb = n_points // 32
+    X, kind = synth.collocation_parametric(1, n_points - 2 * nb, nb, nb, 4.0, 2.0)
+    Xd, kd = torch.tensor(X, device="cuda"), torch.tensor(kind, device="cuda")
+    prob = dict(K=1.0, sigma=0.2, r=0.05, T=2.0, Smax=8.0, Nx=5, P=1, fine_steps=1, coarse_steps=1)
+    net = B.PinnModel(widths, lo, hi, seed=0)
+    first = net.train_step(Xd, kd, prob, lr=1e-3, smax_over_K=4.0, prec=B.BF16, want_loss=True)
+    for _ in range(steps - 2):
+        net.train_step(Xd, kd, prob, lr=1e-3, smax_over_K=4.0, prec=B.BF16)
+    last = net.train_step(Xd, kd, prob, lr=1e-3, smax_over_K=4.0, prec=B.BF16, want_loss=True)
+    return net, {"steps": steps, "points": len(kind), "precision": "bf16 (tcgen05)", "loss_first": first,
+                 "loss_last": last}
 
 
 def pinn_leg(B, torch, n_points=1 << 24):
@@ -822,7 +874,8 @@ def main():
         from paper_2303_03848_b300 import build as BUILD
 
         BUILD.build()
-        print(json.dumps(batched_leg(B, torch, n_inst=args.instances, solve=False, rule_too=True)), flush=True)
+        print(json.dumps(batched_leg(B, torch, n_inst=args.instances, solve=True, rule_too=True, pinn_solve=True)),
+              flush=True)
     elif args.impl == "reference":
         run_reference(args)
     else:
