@@ -1,0 +1,122 @@
+"""Parity at the full sizes of the benchmark workloads, in the launch
+configurations bench.py times: sampled outputs against the oracle, and
+properties that hold at any size.
+
+* Benchmark workload (Nx = 1024, P = 32, 1024 Crank-Nicolson steps per slice,
+  the built-in partition): the network-coarse solve with the BF16 table on the
+  tensor cores needs k = P iterations and then equals the GPU serial fine
+  solution bitwise (that serial fine solution is held to the oracle at this
+  size in test_gpu_solver.py).
+* Batched workload (4096 seeded instances, P = 64, 256 steps per slice,
+  autotuned partitions): one fine propagation of every slice of the batch,
+  sampled (instance, slice) outputs against the oracle; the implicit-Euler-coarse
+  solve of the whole batch to 1e-6, sampled instances against the oracle's
+  serial fine solution.
+* Large instance (Nx = 65536, P = 256, 4096 steps per slice, two slices per CTA
+  on 16-CTA clusters): the first slice of GPU serial fine against the oracle;
+  two implicit-Euler-coarse Parareal iterations leave the first three slices
+  equal to GPU serial fine bitwise.
+
+FP64 tolerance: max(1e-12, 2 kappa u N) as in test_gpu_solver.py (kappa the
+mesh-ratio factor of the right-hand side, u = 2^-53, N the steps).
+"""
+import numpy as np
+import pytest
+
+from paper_2303_03848_b300 import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2303_03848_b300 import binding, build
+
+    build.build()
+    return binding
+
+
+def _kappa_tol(p, steps):
+    h = 0.5 * p["T"] / (p["P"] * p["fine_steps"])
+    j = p["Nx"] - 2
+    kappa = 1.0 + h * (2.0 * p["sigma"] ** 2 * j * j + p["r"] * j + p["r"])
+    return max(1e-12, 2.0 * kappa * 2.0 ** -53 * steps)
+
+
+def _rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def test_benchmark_network_solve_full_size_is_serial_fine(B):
+    cfg = dict(K=1.0, sigma=0.2, r=0.05, T=1.0, Smax=4.0, Nx=1024, P=32, fine_steps=1024, coarse_steps=1)
+    prob = B.Problem(cfg)
+    assert prob.partition(0) == dict(M=2, NW=4, C=4)
+    net = B.PinnModel([2, 64, 64, 64, 64, 1], [0.0, 0.0], [4.0, 1.0], seed=0)
+    U, norms, stats, rc = prob.parareal_solve(B.COARSE_PINN, model=net, prec=B.BF16, tol=1e-6, max_iter=32)
+    Uf = prob.serial_fine()
+    torch.cuda.synchronize()
+    assert stats[0]["iterations"] == 32 and prob.device_status() == B.BS_OK
+    assert torch.equal(U, Uf)
+
+
+def test_batched_workload_full_size_sampled_against_oracle(B, orc):
+    insts = synth.batched_instances(0, 4096, P=64, fine_steps=256, coarse_steps=1)
+    prob = B.Problem(insts, tuned=True)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(7)
+    Uin = torch.rand(prob.total_slice, dtype=torch.float64, device="cuda", generator=gen)
+    # one instance of every grid size, first and last slice; their inputs get the
+    # exact Dirichlet nodes at tau_n (the other slices are independent of them)
+    seen, picks = set(), []
+    for i, p in enumerate(insts):
+        if p["Nx"] not in seen:
+            seen.add(p["Nx"])
+            picks.append(i)
+    assert len(picks) == 5
+    for i in picks:
+        p = insts[i]
+        op = orc.params(**p)
+        for n in (0, p["P"] - 1):
+            o = prob.slice_off[i] + n * p["Nx"]
+            Uin[o] = 0.0
+            Uin[o + p["Nx"] - 1] = orc.right_bc(op, p["T"] * n / p["P"])
+    Fo = prob.fine_propagate(Uin)
+    torch.cuda.synchronize()
+    assert prob.device_status() == B.BS_OK
+    for i in picks:
+        p = insts[i]
+        op = orc.params(**p)
+        for n in (0, p["P"] - 1):
+            o = prob.slice_off[i] + n * p["Nx"]
+            v_in = Uin[o:o + p["Nx"]].cpu().numpy()
+            got = Fo[o:o + p["Nx"]].cpu().numpy()
+            err = _rel(got, orc.fine(op, n, v_in))
+            assert err <= _kappa_tol(p, p["fine_steps"]), (i, p["Nx"], n, err)
+    # the implicit-Euler-coarse solve of the whole batch to 1e-6
+    U, norms, stats, rc = prob.parareal_solve(B.COARSE_IE, tol=1e-6, max_iter=64)
+    assert rc == B.BS_OK and all(st["status"] == B.BS_OK for st in stats)
+    for i in picks[:3]:  # Nx = 256 .. 1024 keeps the oracle's serial fine quick
+        p = insts[i]
+        op = orc.params(**p)
+        o = prob.state_off[i]
+        Ui = U[o:o + (p["P"] + 1) * p["Nx"]].cpu().numpy()
+        assert orc.rel_error(op, Ui, orc.serial_fine(op)) <= 1e-6, (i, p["Nx"])
+
+
+def test_large_instance_full_size(B, orc):
+    cfg = dict(K=1.0, sigma=0.3, r=0.03, T=2.0, Smax=8.0, Nx=65536, P=256, fine_steps=4096, coarse_steps=1)
+    prob = B.Problem(cfg)
+    assert prob.partition(0) == dict(M=32, NW=4, C=16) and prob.slices_per_cta(0) == 2
+    Uf = prob.serial_fine()
+    U2, norms, stats, rc = prob.parareal_solve(B.COARSE_IE, tol=0.0, max_iter=2)
+    torch.cuda.synchronize()
+    assert prob.device_status() == B.BS_OK and stats[0]["iterations"] == 2
+    Nx = cfg["Nx"]
+    assert torch.equal(U2[:3 * Nx], Uf[:3 * Nx])
+    op = orc.params(**cfg)
+    first = orc.fine(op, 0, orc.payoff(op))
+    assert _rel(Uf[Nx:2 * Nx].cpu().numpy(), first) <= _kappa_tol(cfg, cfg["fine_steps"])
