@@ -16,6 +16,8 @@ properties that hold at any size.
   on 16-CTA clusters): the first slice of GPU serial fine against the oracle;
   two implicit-Euler-coarse Parareal iterations leave the first three slices
   equal to GPU serial fine bitwise.
+* Training workload (2->6x128, 65536 collocation points): every layer's BF16
+  tensor-core gradient against the FP32 CUDA-core gradient of the same batch.
 
 FP64 tolerance: max(1e-12, 2 kappa u N) as in test_gpu_solver.py (kappa the
 mesh-ratio factor of the right-hand side, u = 2^-53, N the steps).
@@ -120,3 +122,28 @@ def test_large_instance_full_size(B, orc):
     op = orc.params(**cfg)
     first = orc.fine(op, 0, orc.payoff(op))
     assert _rel(Uf[Nx:2 * Nx].cpu().numpy(), first) <= _kappa_tol(cfg, cfg["fine_steps"])
+
+
+def test_training_step_full_size_matches_fp32_path(B):
+    # the 2->6x128 training workload at its full batch (65536 points): every
+    # layer's BF16 tensor-core gradient against the FP32 CUDA-core gradient of the
+    # same batch (itself held to the oracle at small sizes), the per-layer bound
+    # of the BF16 tests
+    widths = [2] + [128] * 6 + [1]
+    nb = 65536 // 32
+    X, kind = synth.collocation(0, 65536 - 2 * nb, nb, nb, 4.0, 1.0)
+    Xd, kd = torch.tensor(X, device="cuda"), torch.tensor(kind, device="cuda")
+    prob = dict(K=1.0, sigma=0.2, r=0.05, T=1.0, Smax=4.0, Nx=5, P=1, fine_steps=1, coarse_steps=1)
+    m = B.PinnModel(widths, [0.0, 0.0], [4.0, 1.0], seed=0)
+    l16, g16 = m.loss_grad(Xd, kd, prob, 0.0, prec=B.BF16)
+    l32, g32 = m.loss_grad(Xd, kd, prob, 0.0, prec=B.FP32)
+    assert m.device_status() == B.BS_OK
+    l16, g16, l32, g32 = (v.cpu().numpy() for v in (l16, g16, l32, g32))
+    for c in range(3):
+        assert abs(l16[c] - l32[c]) <= 5e-2 * abs(l32[c]), (c, l16[c], l32[c])
+    off = 0
+    for l in range(1, len(widths)):
+        for n in (widths[l] * widths[l - 1], widths[l]):
+            a, b = g16[off:off + n], g32[off:off + n]
+            assert _rel(a, b) <= 2e-2, (l, n, _rel(a, b))
+            off += n
