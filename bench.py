@@ -321,12 +321,13 @@ def run_ours(args):
             e2e_ms.append((time.perf_counter() - s0) * 1e3)
     e2e_step = allreduce_max(ws, statistics.mean(e2e_ms))
 
-    batched = batched_leg(B, torch) if args.batched else None
-    pinn = pinn_leg(B, torch)
-    train3 = train_leg(B, torch)
-
-    cpu = None
-    if rank == 0:
+    # the single-GPU context legs and the CPU baseline run at N = 1 only (at N > 1
+    # every rank would hold its GPU meanwhile, and the baseline belongs to rank 0 at N = 1)
+    batched = pinn = train3 = cpu = None
+    if ws == 1:
+        batched = batched_leg(B, torch) if args.batched else None
+        pinn = pinn_leg(B, torch)
+        train3 = train_leg(B, torch)
         cpu = cpu_baseline(model.get_weights(), iters, budget_s=args.cpu_seconds)
 
     if rank != 0:
