@@ -219,6 +219,23 @@ def test_tensor_core_gradient_every_layer(B, orc, widths):
             assert abs(l3[c].item() - terms[c]) <= 5e-2 * abs(terms[c]), (c, l3[c].item(), terms[c])
 
 
+@pytest.mark.parametrize("widths", [[2, 48, 48, 1], [2, 256, 256, 1], [5, 40, 24, 1]], ids=["2-2x48", "2-2x256", "5-40-24"])
+def test_bf16_training_outside_the_tensor_core_shapes(B, orc, widths):
+    # BF16 loss and gradient for networks the tensor-core training does not take
+    # (width not in 32..128 by 32, or unequal widths): CUDA cores with BF16-rounded
+    # operands, the BF16 bounds of the other tests
+    m, om = _model(B, orc, widths, 9)
+    X, kind, prob, sok = _loss_case(widths, 700, 64, 64, 13)
+    terms, grad = orc.pinn_loss_grad(om, X, kind, prob["K"], prob["sigma"], prob["r"], prob["Smax"], sok)
+    l3, g = m.loss_grad(torch.tensor(X, device="cuda"), torch.tensor(kind, device="cuda"), prob, sok, prec=B.BF16)
+    l3, g = l3.cpu().numpy(), g.cpu().numpy()
+    for c in range(3):
+        assert abs(l3[c] - terms[c]) <= 5e-2 * abs(terms[c]), (c, l3[c], terms[c])
+    assert _rel(g, grad) <= 1e-1
+    for name, a, b in _param_blocks(widths):
+        assert np.abs(g[a:b] - grad[a:b]).max() / max(np.abs(grad[a:b]).max(), 1e-300) <= 2e-2, name
+
+
 @pytest.mark.parametrize("arch", ["2-4x64", "5-6x128"])
 def test_tensor_core_training_in_chunks(B, orc, arch, monkeypatch):
     # a batch run as chunks of 1024 points (4 chunks, the last one ragged) gives
