@@ -610,11 +610,12 @@ def train_leg(B, torch, n_points=65536, steps=20):
     # the tensor-core step is bound by HBM traffic: per hidden layer the stored
     # (t, z_1, z_2, z_3) in FP32 (layer 1: t only) written by the forward and read by
     # the adjoint, and the BF16 h and dz operand blocks (4 streams) written once and
-    # read once by the weight gradient; per point the inputs, kinds and loss seeds
+    # read once by the weight gradient; per point the inputs (read by the forward and
+    # by the adjoint's input-layer gradient) and the kinds
     w, nh, n = widths[1], len(widths) - 2, len(kind)
     act = (16 * (nh - 1) + 4) * 2
     blocks = 8 * (nh - 1) * 2 * 2
-    per_point = 2 * 16 + 1 + 2 * 16
+    per_point = 2 * 16 + 1
     hbm = n * (w * (act + blocks) + per_point)
     peak = _peaks().get("hbm_gbs")
     ach = hbm / (out["bf16"]["ms_per_step"] * 1e-3) / 1e9
