@@ -306,6 +306,39 @@ def run_ours(args):
         per_prec[name] = dict(tol=tl, iterations=itp, err_vs_serial_fine=ep, ms_per_solve=statistics.mean(msp),
                               coarse_err_vs_fp64=cerr)
 
+    # one solve by phase (CUDA events on graph-replayed solves): solves stopped after
+    # one and after two iterations give the cost of an iteration (fine propagation,
+    # fused correction and stop test) and the fixed part (network table, initial
+    # iterate, result copy); the table alone is timed as one evaluation on the grid
+    def replay_ms(graph, reps=3):
+        graph.replay()
+        out = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            graph.replay()
+            b.record()
+            torch.cuda.synchronize()
+            out.append(a.elapsed_time(b))
+        return min(out)
+
+    g1 = B.SolveGraph(prob, B.COARSE_PINN, model=model, prec=prec, tol=0.0, max_iter=1)
+    g2 = B.SolveGraph(prob, B.COARSE_PINN, model=model, prec=prec, tol=0.0, max_iter=2)
+    t1, t2 = replay_ms(g1), replay_ms(g2)
+    del g1, g2
+    model.eval(Xg, prec=prec)
+    tab = []
+    for _ in range(3):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        model.eval(Xg, prec=prec)
+        b.record()
+        torch.cuda.synchronize()
+        tab.append(a.elapsed_time(b))
+    phases = {"per_iteration_ms": t2 - t1, "fixed_ms": 2 * t1 - t2, "network_table_ms": min(tab),
+              "iterations": iters, "solve_ms": ms_step,
+              "note": "solve = fixed + iterations x per_iteration; the fixed part holds the table"}
+
     # end to end through the C ABI with host buffers
     w_host = torch.tensor(model.get_weights()).pin_memory()
     U_host = torch.empty(prob.total_state, dtype=torch.float64).pin_memory()
@@ -366,6 +399,7 @@ def run_ours(args):
                       "solves_per_s": 1e3 / statistics.mean(ms_ie)},
         "serial_fine_ms": serial_ms,
         "speedup_vs_serial_fine": {"pinn": serial_ms / ms_step, "ie": serial_ms / statistics.mean(ms_ie)},
+        "phases": phases,
         "per_precision": per_prec,
         "train_step": train,
         "batched": batched,

@@ -12,6 +12,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/bsparareal.h"
 #include "bs_common.cuh"
 #include "bs_internal.h"
@@ -33,6 +35,16 @@ cudaError_t dalloc(T** p, size_t count) {
   if (count == 0) count = 1;
   return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
 }
+
+// NVTX range over a scope: the phases of a call appear in profilers that
+// record NVTX (ncu --nvtx); without a tool attached a range costs a check of a
+// function pointer.
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
 
 int map_err(cudaError_t e) {
   if (e == cudaSuccess) return BS_OK;
@@ -290,6 +302,7 @@ static int problem_create(const bs_params* p, int32_t n_instances, const Part* p
 extern "C" {
 
 int bs_problem_init(const bs_params* p, int32_t n_instances, bs_problem** out) {
+  Range range_("bs_problem_init");
   if (!p || !out || n_instances <= 0) return BS_EINVAL;
   *out = nullptr;
   if (validate(p, n_instances) != BS_OK) return BS_EINVAL;
@@ -374,6 +387,7 @@ static int time_partition(const std::vector<bs_params>& sub, Part part, float* m
 
 int bs_problem_init_tuned(const bs_params* p, int32_t n_instances, bs_problem** out, bs_tuning* report,
                           int32_t report_cap, int32_t* n_report) {
+  Range range_("bs_problem_init_tuned");
   if (!p || !out || n_instances <= 0 || (report_cap > 0 && !report)) return BS_EINVAL;
   *out = nullptr;
   if (n_report) *n_report = 0;
@@ -495,14 +509,17 @@ static int propagate(bs_problem* prob, bool cn, const double* U_in, double* U_ou
 }
 
 int fine_propagate(bs_problem* prob, const double* U_in, double* U_out, const uint8_t* active, void* stream) {
+  Range range_("fine_propagate");
   return propagate(prob, true, U_in, U_out, active, stream);
 }
 
 int coarse_propagate(bs_problem* prob, const double* U_in, double* U_out, const uint8_t* active, void* stream) {
+  Range range_("coarse_propagate");
   return propagate(prob, false, U_in, U_out, active, stream);
 }
 
 int serial_fine(bs_problem* prob, double* U_out, void* stream) {
+  Range range_("serial_fine");
   if (!prob || !U_out || ((uintptr_t)U_out & 15)) return BS_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   for (auto& c : prob->classes) {
@@ -686,6 +703,7 @@ int bs_wait_probe(int32_t arrive, int64_t limit_cycles, int32_t* status) {
 }
 
 int pinn_eval(const pinn_model* m, int prec, const double* X, int64_t N, double* u, double* derivs, void* stream) {
+  Range range_("pinn_eval");
   if (!m || N < 0 || prec < BS_FP64 || prec > BS_BF16) return BS_EINVAL;
   if (N == 0) return BS_OK;
   if (!X || !u || (((uintptr_t)X | (uintptr_t)u | (uintptr_t)derivs) & 15)) return BS_EINVAL;
@@ -720,12 +738,14 @@ static int loss_grad_common(const pinn_model* mc, const double* X, const int8_t*
 int pinn_loss_grad(const pinn_model* m, const double* X, const int8_t* kind, int64_t N,
                    const bs_params* prob_params, double smax_over_K, int prec, double* loss3, double* grad,
                    void* stream) {
+  Range range_("pinn_loss_grad");
   if (!loss3 || !grad) return BS_EINVAL;
   return loss_grad_common(m, X, kind, N, prob_params, smax_over_K, prec, loss3, grad, (cudaStream_t)stream);
 }
 
 int pinn_train_step(pinn_model* m, const double* X, const int8_t* kind, int64_t N, const bs_params* prob_params,
                     double smax_over_K, int prec, double lr, double* loss3, double* grad_out, void* stream) {
+  Range range_("pinn_train_step");
   if (!m || !std::isfinite(lr) || lr <= 0.0) return BS_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   double* g = grad_out ? grad_out : m->grad;
@@ -775,6 +795,7 @@ static cudaError_t ensure_parareal_ws(bs_problem* prob, int max_iter, int d_in) 
 
 int parareal_solve(bs_problem* prob, int coarse_kind, const pinn_model* model, int prec, double tol,
                    int32_t max_iter, double* U_out, double* norms, bs_instance_stats* stats, void* stream) {
+  Range range_("parareal_solve");
   if (!prob || !U_out || ((uintptr_t)U_out & 15) || max_iter < 1 || !(tol >= 0.0)) return BS_EINVAL;
   if (coarse_kind < BS_COARSE_IE || coarse_kind > BS_COARSE_PINN_INCR) return BS_EINVAL;
   const bool pinn = coarse_kind != BS_COARSE_IE;
@@ -786,6 +807,7 @@ int parareal_solve(bs_problem* prob, int coarse_kind, const pinn_model* model, i
   const int n = prob->n_inst;
   // a1: network table on (S_j, tau_n), Dirichlet nodes exact
   if (pinn) {
+    Range r("network table");
     const int d_in = model->dev.d_in;
     if ((e = bsp::launch_grid_points(prob->d_insts, n, d_in, prob->Xgrid, s)) != cudaSuccess) return map_err(e);
     if ((e = bsp::launch_mlp_eval(model->dev, prec, prob->Xgrid, prob->total_state, prob->gtab, nullptr, s)) !=
@@ -826,6 +848,7 @@ int parareal_solve(bs_problem* prob, int coarse_kind, const pinn_model* model, i
   }
   const int kmax = max_iter < prob->maxP ? max_iter : prob->maxP;
   for (int k = 0; k < kmax; ++k) {
+    Range r("parareal iteration");
     double* cur = (k & 1) ? prob->buf1 : prob->buf0;
     double* nxt = (k & 1) ? prob->buf0 : prob->buf1;
     // a3 (+ a5 fused for the state-independent network coarse propagator)
