@@ -968,6 +968,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 extern "C" int parareal_solve_static(bs_problem* prob, int coarse_kind, const pinn_model* model, int prec,
                                      double tol, int32_t max_iter, double* U_out, double* norms,
                                      bs_instance_stats* stats, void* stream) {
+  Range range_("parareal_solve_static");
   if (!prob || !U_out || ((uintptr_t)U_out & 15) || max_iter < 1 || !(tol >= 0.0)) return BS_EINVAL;
   if (coarse_kind < BS_COARSE_IE || coarse_kind > BS_COARSE_PINN_INCR) return BS_EINVAL;
   const bool pinn = coarse_kind != BS_COARSE_IE;
