@@ -469,11 +469,14 @@ class PinnModel:
         _check(lib().pinn_device_status(self._h, ctypes.byref(s)), "pinn_device_status")
         return s.value
 
-    def eval(self, X, prec=FP64, derivs=False):
+    def eval(self, X, prec=FP64, derivs=False, out=None):
+        """u_theta at the rows of X (device [N][d_in] FP64) into out (or a new tensor)."""
         import torch
 
         N = X.shape[0]
-        u = torch.empty(N, dtype=torch.float64, device=X.device)
+        u = out if out is not None else torch.empty(N, dtype=torch.float64, device=X.device)
+        if u.shape != (N,):
+            raise ValueError("out must have shape (N,)")
         d = torch.empty(N, 3, dtype=torch.float64, device=X.device) if derivs else None
         _check(lib().pinn_eval(self._h, prec, _dev(X, torch.float64, "X"), N, _dev(u, torch.float64, "u"),
                                _dev(d, torch.float64, "derivs") if d is not None else None, _stream()), "pinn_eval")

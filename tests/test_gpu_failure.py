@@ -69,3 +69,46 @@ def test_checkpoint_resume_continues_training(B, tmp_path, prec_name):
     assert np.abs(b.get_weights() - wa).max() <= 1e-12 * max(np.abs(wa).max(), 1.0)
     with pytest.raises(ValueError):
         B.PinnModel([2, 32, 1], lo, hi).load(tmp_path / "a.ckpt")
+
+
+def test_every_output_element_is_written(B):
+    # poisoned outputs: NaN before the call, every element finite after it, for
+    # each entry point that writes a device array (a missed tile, row or
+    # instance would stay NaN)
+    insts = synth.batched_instances(3, 7, P=5, fine_steps=9, coarse_steps=1, Nx_choices=(33, 256, 300, 1025))
+    prob = B.Problem(insts)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(1)
+    Uin = torch.rand(prob.total_slice, dtype=torch.float64, device="cuda", generator=gen)
+    nan = float("nan")
+    for f in (prob.fine_propagate, prob.coarse_propagate):
+        out = torch.full_like(Uin, nan)
+        f(Uin, out)
+        torch.cuda.synchronize()
+        assert torch.isfinite(out).all()
+    Us = torch.full((prob.total_state,), nan, dtype=torch.float64, device="cuda")
+    prob.serial_fine(Us)
+    torch.cuda.synchronize()
+    assert torch.isfinite(Us).all()
+    net5 = B.PinnModel([5, 32, 32, 1], [0.0, 0.0, 0.1, 0.0, 0.5], [8.0, 2.0, 0.5, 0.08, 2.0], seed=3)
+    for kind, model, prec in ((B.COARSE_IE, None, B.FP64), (B.COARSE_PINN, net5, B.BF16)):
+        Uo = torch.full((prob.total_state,), nan, dtype=torch.float64, device="cuda")
+        prob.parareal_solve(kind, model=model, prec=prec, tol=1e-8, U_out=Uo)
+        assert torch.isfinite(Uo).all()
+    net = B.PinnModel([2, 64, 64, 1], [0.0, 0.0], [4.0, 1.0], seed=3)
+    for n in (1, 127, 129, 1000):
+        X = torch.rand(n, 2, dtype=torch.float64, device="cuda", generator=gen) * torch.tensor([4.0, 1.0], device="cuda")
+        for prec in (B.FP64, B.FP32, B.TF32, B.BF16):
+            u = torch.full((n,), nan, dtype=torch.float64, device="cuda")
+            net.eval(X, prec=prec, out=u)
+            torch.cuda.synchronize()
+            assert torch.isfinite(u).all(), (n, prec)
+    X, kind = synth.collocation(2, 300, 32, 32, 4.0, 1.0)
+    prob1 = dict(K=1.0, sigma=0.2, r=0.05, T=1.0, Smax=4.0, Nx=5, P=1, fine_steps=1, coarse_steps=1)
+    for prec in (B.FP64, B.FP32, B.BF16):
+        g = torch.full((net.n_params,), nan, dtype=torch.float64, device="cuda")
+        net.train_step(torch.tensor(X, device="cuda"), torch.tensor(kind, device="cuda"), prob1, lr=1e-3, prec=prec,
+                       grad_out=g)
+        torch.cuda.synchronize()
+        assert torch.isfinite(g).all(), prec
+    assert prob.device_status() == B.BS_OK and net.device_status() == B.BS_OK
