@@ -141,6 +141,18 @@ typedef struct {
 int bs_problem_init_tuned(const bs_params* p, int32_t n_instances, bs_problem** out, bs_tuning* report,
                           int32_t report_cap, int32_t* n_report);
 
+/*
+ * bs_problem_init_partitioned -- bs_problem_init with the partition of every
+ * grid size given: for each instance the entry of parts (host, n_parts) with
+ * the instance's Nx and chosen != 0 (the fields ms are ignored), e.g. the
+ * report of an earlier bs_problem_init_tuned kept in a cache.  Synchronous.
+ * Errors: BS_EINVAL (argument, or a grid size without a chosen entry),
+ * BS_EUNSUPPORTED (a partition not compiled or too small for its grid),
+ * BS_ENOMEM, BS_ECUDA.
+ */
+int bs_problem_init_partitioned(const bs_params* p, int32_t n_instances, const bs_tuning* parts, int32_t n_parts,
+                                bs_problem** out);
+
 /* Release the handle and its device memory.  NULL is accepted. */
 void bs_problem_destroy(bs_problem* prob);
 

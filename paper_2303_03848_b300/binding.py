@@ -71,6 +71,7 @@ def lib() -> ctypes.CDLL:
         L.bs_version.restype = ctypes.c_char_p
         L.bs_problem_init.argtypes = [P(BsParams), i32, P(vp)]
         L.bs_problem_init_tuned.argtypes = [P(BsParams), i32, P(vp), P(Tuning), i32, P(i32)]
+        L.bs_problem_init_partitioned.argtypes = [P(BsParams), i32, P(Tuning), i32, P(vp)]
         L.bs_problem_destroy.argtypes = [vp]
         L.bs_problem_destroy.restype = None
         L.bs_problem_info.argtypes = [vp, P(i32), P(i64), P(i64)]
@@ -204,19 +205,83 @@ def _to_struct(d) -> BsParams:
                     d["coarse_steps"])
 
 
+def _cache_keys(instances) -> dict:
+    """Tuning-cache key per grid size: device name, Nx and the class's slice count
+    (capped at the tuner's 4096 and rounded up to a power of two)."""
+    import torch
+
+    dev = torch.cuda.get_device_name() if torch.cuda.is_available() else "cpu"
+    slices = {}
+    for p in instances:
+        slices[p["Nx"]] = slices.get(p["Nx"], 0) + int(p["P"])
+    out = {}
+    for nx, s in slices.items():
+        b = 1
+        while b < min(s, 4096):
+            b *= 2
+        out[nx] = f"{dev}|Nx={nx}|slices={b}"
+    return out
+
+
+def _cache_lookup(path, instances):
+    import json
+    import os
+
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        cache = json.load(f)
+    got = []
+    for nx, key in _cache_keys(instances).items():
+        e = cache.get(key)
+        if e is None:
+            return None
+        got.append(dict(Nx=nx, M=int(e["M"]), NW=int(e["NW"]), C=int(e["C"]), S2=int(e["S2"])))
+    return got
+
+
+def _cache_store(path, instances, chosen):
+    import json
+    import os
+
+    cache = {}
+    if os.path.exists(path):
+        with open(path) as f:
+            cache = json.load(f)
+    keys = _cache_keys(instances)
+    for r in chosen:
+        cache[keys[r["Nx"]]] = dict(M=r["M"], NW=r["NW"], C=r["C"], S2=r["S2"])
+    tmp = f"{path}.tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
 class Problem:
     """Handle of bs_problem_init: one or more pricing instances on the current device."""
 
-    def __init__(self, instances, tuned: bool = False):
+    def __init__(self, instances, tuned: bool = False, tuning_cache=None):
         """tuned: pick each grid size's partition by timing (bs_problem_init_tuned); the
-        timed candidates are kept in self.tuning."""
+        timed candidates are kept in self.tuning.  tuning_cache: path of a JSON file of
+        earlier tuned choices, keyed by device, grid size and slice count; when it holds
+        every grid size of the instances the problem is set up from it without timing
+        (bs_problem_init_partitioned), else the tuner runs and its choices are added.
+        self.tuning_source says which ("timed", "cache" or None)."""
         if isinstance(instances, dict):
             instances = [instances]
         self.instances = [dict(p) for p in instances]
         arr = (BsParams * len(self.instances))(*[_to_struct(p) for p in self.instances])
         h = ctypes.c_void_p()
-        self.tuning = []
-        if tuned:
+        self.tuning, self.tuning_source = [], None
+        cached = _cache_lookup(tuning_cache, self.instances) if (tuned and tuning_cache) else None
+        if cached is not None:
+            parts = (Tuning * len(cached))(*[Tuning(e["Nx"], e["M"], e["NW"], e["C"], e["S2"], 0.0, 1)
+                                            for e in cached])
+            _check(lib().bs_problem_init_partitioned(arr, len(self.instances), parts, len(cached), ctypes.byref(h)),
+                   "bs_problem_init_partitioned")
+            self.tuning = [dict(e, ms=None, chosen=True) for e in cached]
+            self.tuning_source = "cache"
+        elif tuned:
             cap = 256
             rep = (Tuning * cap)()
             nrep = ctypes.c_int32()
@@ -224,6 +289,9 @@ class Problem:
                    "bs_problem_init_tuned")
             self.tuning = [dict(Nx=r.Nx, M=r.M, NW=r.NW, C=r.C, S2=r.S2, ms=r.ms, chosen=bool(r.chosen))
                            for r in rep[:min(nrep.value, cap)]]
+            self.tuning_source = "timed"
+            if tuning_cache:
+                _cache_store(tuning_cache, self.instances, [r for r in self.tuning if r["chosen"]])
         else:
             _check(lib().bs_problem_init(arr, len(self.instances), ctypes.byref(h)), "bs_problem_init")
         self._h = h

@@ -445,6 +445,28 @@ int bs_problem_init_tuned(const bs_params* p, int32_t n_instances, bs_problem** 
   return problem_create(p, n_instances, parts.data(), out);
 }
 
+int bs_problem_init_partitioned(const bs_params* p, int32_t n_instances, const bs_tuning* parts_in,
+                                int32_t n_parts, bs_problem** out) {
+  Range range_("bs_problem_init_partitioned");
+  if (!p || !out || n_instances <= 0 || !parts_in || n_parts <= 0) return BS_EINVAL;
+  *out = nullptr;
+  if (validate(p, n_instances) != BS_OK) return BS_EINVAL;
+  std::vector<Part> parts(n_instances);
+  for (int i = 0; i < n_instances; ++i) {
+    const bs_tuning* hit = nullptr;
+    for (int k = 0; k < n_parts && !hit; ++k)
+      if (parts_in[k].Nx == p[i].Nx && parts_in[k].chosen) hit = &parts_in[k];
+    if (!hit) return BS_EINVAL;  // no partition given for this grid size
+    const Part c{hit->M, hit->NW, hit->C, hit->S2};
+    if (!bsp::partition_supported(c.M, c.NW, c.C) ||
+        (c.s2 != 1 && !(c.s2 == 2 && bsp::s2_supported(c.M, c.NW, c.C))) ||
+        (int64_t)c.M * c.NW * 32 * c.C < p[i].Nx - 1)
+      return BS_EUNSUPPORTED;
+    parts[i] = c;
+  }
+  return problem_create(p, n_instances, parts.data(), out);
+}
+
 int bs_problem_info(const bs_problem* prob, int32_t* n_instances, int64_t* total_state_doubles,
                     int64_t* total_slice_doubles) {
   if (!prob) return BS_EINVAL;

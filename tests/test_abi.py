@@ -61,6 +61,11 @@ def test_null_arguments_rejected(L):
     assert L.bs_problem_slices_per_cta(None, 0, None) == B.BS_EINVAL
     assert L.bs_problem_init_tuned(None, 1, ctypes.byref(h), None, 0, None) == B.BS_EINVAL
     assert L.bs_problem_init_tuned(ctypes.byref(p), 1, ctypes.byref(h), None, 4, None) == B.BS_EINVAL
+    assert L.bs_problem_init_partitioned(None, 1, None, 0, ctypes.byref(h)) == B.BS_EINVAL
+    tun = (B.Tuning * 1)(B.Tuning(512, 2, 4, 1, 1, 0.0, 1))
+    assert L.bs_problem_init_partitioned(ctypes.byref(p), 1, tun, 1, ctypes.byref(h)) == B.BS_EINVAL  # no Nx=256
+    tun[0] = B.Tuning(256, 3, 4, 1, 1, 0.0, 1)
+    assert L.bs_problem_init_partitioned(ctypes.byref(p), 1, tun, 1, ctypes.byref(h)) == B.BS_EUNSUPPORTED
     s = ctypes.c_int32()
     assert L.bs_wait_probe(0, 0, ctypes.byref(s)) == B.BS_EINVAL  # limit out of range
     assert L.bs_wait_probe(0, 1 << 35, ctypes.byref(s)) == B.BS_EINVAL

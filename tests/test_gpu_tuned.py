@@ -224,3 +224,24 @@ def test_tuner_times_slice_pairs_where_supported(B, orc):
     assert prob.slices_per_cta(0) == chosen[0]["S2"]
     parts = [_slices(orc, p, 60 + i) for i, p in enumerate(insts)]
     _check_against_oracle(B, orc, prob, insts, parts)
+
+
+def test_tuning_cache_round_trip(B, tmp_path):
+    # the tuner's choices saved per device, grid size and slice count, then a
+    # second set-up from the file without timing: same partitions, same results
+    insts = synth.batched_instances(2, 40, P=8, fine_steps=16, coarse_steps=1, Nx_choices=(256, 1024))
+    path = str(tmp_path / "tuning.json")
+    a = B.Problem(insts, tuned=True, tuning_cache=path)
+    assert a.tuning_source == "timed"
+    b = B.Problem(insts, tuned=True, tuning_cache=path)
+    assert b.tuning_source == "cache"
+    for i in range(len(insts)):
+        assert a.partition(i) == b.partition(i) and a.slices_per_cta(i) == b.slices_per_cta(i)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(4)
+    U = torch.rand(a.total_slice, dtype=torch.float64, device="cuda", generator=gen)
+    assert torch.equal(a.fine_propagate(U), b.fine_propagate(U))
+    # another slice count is another key: timed again
+    c = B.Problem(synth.batched_instances(2, 3, P=8, fine_steps=16, coarse_steps=1, Nx_choices=(256,)), tuned=True,
+                  tuning_cache=path)
+    assert c.tuning_source == "timed"
