@@ -112,3 +112,26 @@ def test_every_output_element_is_written(B):
         torch.cuda.synchronize()
         assert torch.isfinite(g).all(), prec
     assert prob.device_status() == B.BS_OK and net.device_status() == B.BS_OK
+
+
+def test_misaligned_device_pointers_are_rejected_before_any_launch(B):
+    # device arrays must start on 16-byte boundaries (the kernels read them with
+    # 16-byte and TMA accesses): an 8-byte offset gives BS_EINVAL and leaves the
+    # output as it was
+    L = B.lib()
+    prob = B.Problem(B.params(Nx=64, P=2, fine_steps=4))
+    U = torch.zeros(prob.total_slice + 2, dtype=torch.float64, device="cuda")
+    out = torch.full((prob.total_slice + 2,), float("nan"), dtype=torch.float64, device="cuda")
+    for f in (L.fine_propagate, L.coarse_propagate):
+        assert f(prob._h, U.data_ptr() + 8, out.data_ptr(), None, None) == B.BS_EINVAL
+        assert f(prob._h, U.data_ptr(), out.data_ptr() + 8, None, None) == B.BS_EINVAL
+    assert L.serial_fine(prob._h, out.data_ptr() + 8, None) == B.BS_EINVAL
+    assert L.parareal_solve(prob._h, B.COARSE_IE, None, B.FP64, 1e-8, 2, out.data_ptr() + 8, None, None,
+                            None) == B.BS_EINVAL
+    net = B.PinnModel([2, 32, 1], [0.0, 0.0], [4.0, 1.0], seed=0)
+    X = torch.zeros(17, 2, dtype=torch.float64, device="cuda")
+    u = torch.full((18,), float("nan"), dtype=torch.float64, device="cuda")
+    assert L.pinn_eval(net._h, B.BF16, X.data_ptr() + 8, 8, u.data_ptr(), None, None) == B.BS_EINVAL
+    assert L.pinn_eval(net._h, B.BF16, X.data_ptr(), 8, u.data_ptr() + 8, None, None) == B.BS_EINVAL
+    torch.cuda.synchronize()
+    assert torch.isnan(out).all() and torch.isnan(u).all()
