@@ -147,3 +147,24 @@ def test_training_step_full_size_matches_fp32_path(B):
             a, b = g16[off:off + n], g32[off:off + n]
             assert _rel(a, b) <= 2e-2, (l, n, _rel(a, b))
             off += n
+
+
+def test_training_batch_above_the_default_chunk(B, monkeypatch):
+    # 600k points: two chunks at the default 2^19, one pass when the chunk is
+    # raised above the batch; the loss terms agree to FP64 summation order and
+    # the gradient to the order of its FP32 partial sums
+    widths = [2, 64, 64, 64, 1]
+    n = 600_000
+    nb = n // 32
+    X, kind = synth.collocation(3, n - 2 * nb, nb, nb, 4.0, 1.0)
+    Xd, kd = torch.tensor(X, device="cuda"), torch.tensor(kind, device="cuda")
+    prob = dict(K=1.0, sigma=0.2, r=0.05, T=1.0, Smax=4.0, Nx=5, P=1, fine_steps=1, coarse_steps=1)
+    m = B.PinnModel(widths, [0.0, 0.0], [4.0, 1.0], seed=5)
+    monkeypatch.delenv("BSP_TRAIN_CHUNK", raising=False)
+    l2, g2 = m.loss_grad(Xd, kd, prob, 0.0, prec=B.BF16)
+    monkeypatch.setenv("BSP_TRAIN_CHUNK", str(1 << 20))
+    l1, g1 = m.loss_grad(Xd, kd, prob, 0.0, prec=B.BF16)
+    assert m.device_status() == B.BS_OK
+    l1, g1, l2, g2 = (v.cpu().numpy() for v in (l1, g1, l2, g2))
+    np.testing.assert_allclose(l2, l1, rtol=1e-12)
+    assert _rel(g2, g1) <= 1e-5
