@@ -395,6 +395,9 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "clocks": clk.summary(),
         "fine_kernel": {"ms": fine_ms, "grid_pt_steps_per_s": pt_steps / (fine_ms * 1e-3)},
+        # iteration k (0-based) propagates slices k..P-1: executed = (Nx-2) M_f sum_k (P-k),
+        # useful = (Nx-2) M_f P (what serial fine does once)
+        "grid_pt_steps": grid_pt_steps(iters, value),
         "ie_coarse": {"tol": tol_ie, "iterations": it_ie, "err_vs_serial_fine": err_ie,
                       "solves_per_s": 1e3 / statistics.mean(ms_ie)},
         "serial_fine_ms": serial_ms,
@@ -787,6 +790,29 @@ def run_large(args):
           flush=True)
 
 
+def grid_pt_steps(iters, solves_per_s):
+    per_slice = (CFG["Nx"] - 2) * CFG["fine_steps"]
+    P = CFG["P"]
+    executed = per_slice * sum(P - k for k in range(iters))
+    useful = per_slice * P
+    return {"executed_per_solve": executed, "useful_per_solve": useful,
+            "executed_per_s": executed * solves_per_s, "useful_per_s": useful * solves_per_s}
+
+
+def host_cpu():
+    """CPU model and logical core count of the host the baseline runs on."""
+    model = "unknown"
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"cpu_model": model, "host_cores": os.cpu_count()}
+
+
 def cpu_baseline(weights, iters, budget_s=20.0):
     """The oracle, as it stands, on the host: one Parareal-PINN iteration per sample."""
     import numpy as np
@@ -810,7 +836,7 @@ def cpu_baseline(weights, iters, budget_s=20.0):
     work = done * (done + 1) / 2
     t_iter = t_all / work
     t_solve = t_table + iters * t_iter
-    return {"value": 1.0 / t_solve, "unit": "solves/s", "cores": 1, "kind": "oracle",
+    return {"value": 1.0 / t_solve, "unit": "solves/s", "cores": 1, "kind": "oracle", **host_cpu(),
             "sample": f"network table + Parareal iterations 1..{done} of the same workload, "
                       f"per-iteration time extrapolated to the {iters} iterations the solve needs"}
 
@@ -848,7 +874,7 @@ def run_reference(args):
         "warmup": args.warmup, "ms_per_step": it * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "coarse": "pinn"},
-        "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle", **host_cpu(),
                          "sample": f"per step one Parareal iteration over all {CFG['P']} slices; solve = network "
                                    f"table + {K} iterations (P, the count that reproduces serial fine)"},
         "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
