@@ -441,7 +441,7 @@ def run_fine_only(args):
                       "tflops_algorithmic": FLOPS_PER_PT_STEP * pt / (ms * 1e-3) / 1e12}), flush=True)
 
 
-def batched_leg(B, torch, n_inst=4096, solve=True, rule_too=False, pinn_solve=False):
+def batched_leg(B, torch, n_inst=4096, solve=True, rule_too=False, pinn_solve=False, cpu_seconds=10.0):
     """Batched workload: n_inst instances (K, sigma, r, T, Nx seeded), P=64, CN 256 steps/slice.
 
     The partition of every grid size is picked by the autotuner
@@ -449,6 +449,7 @@ def batched_leg(B, torch, n_inst=4096, solve=True, rule_too=False, pinn_solve=Fa
     instance (one launch per partition class) and, optionally, one
     implicit-Euler-coarse Parareal solve of the whole batch at tol 1e-6.
     rule_too: also time the built-in partition rule for comparison.
+    cpu_seconds: budget of the oracle's all-core sample of the IE solve (0: none).
     pinn_solve: also one Parareal solve of the batch with the parametric network
     5->6x128 (BF16 table) as coarse propagator, and both solves' error against
     the batch's serial fine solution.
@@ -515,6 +516,8 @@ def batched_leg(B, torch, n_inst=4096, solve=True, rule_too=False, pinn_solve=Fa
                     "ie_launch": "whole batched solve in one CUDA graph",
                     "ie_iterations_mean": float(sum(its)) / len(its), "ie_iterations_max": max(its),
                     "ie_status": rc})
+        if cpu_seconds > 0:
+            out["ie_cpu_baseline"] = batched_cpu_baseline(insts, budget_s=cpu_seconds)
         del g
         if pinn_solve:
             Uf = prob.serial_fine()
@@ -811,6 +814,53 @@ def host_cpu():
     except OSError:
         pass
     return {"cpu_model": model, "host_cores": os.cpu_count()}
+
+
+def batched_cpu_baseline(insts, budget_s=10.0, tol=1e-6):
+    """The oracle on all host cores for the batched implicit-Euler-coarse solve.
+
+    Worker threads (the oracle is C called through ctypes, which releases the
+    GIL) take the batch's seeded instances in order and run the oracle's
+    Parareal to tol until budget_s has passed; the whole batch's time is
+    extrapolated from the instances finished by their share of sum (Nx - 2).
+    """
+    import threading
+
+    import oracle as orc
+
+    orc.build()
+    cores = os.cpu_count() or 1
+    lock = threading.Lock()
+    state = {"next": 0, "done": [], "iters": []}
+    t0 = time.perf_counter()
+
+    def worker():
+        while True:
+            with lock:
+                i = state["next"]
+                if i >= len(insts) or time.perf_counter() - t0 > budget_s:
+                    return
+                state["next"] = i + 1
+            p = insts[i]
+            _, norms, _ = orc.parareal(orc.params(**p), orc.COARSE_IE, tol=tol, max_iter=p["P"])
+            with lock:
+                state["done"].append(i)
+                state["iters"].append(len(norms))
+
+    th = [threading.Thread(target=worker) for _ in range(cores)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    wall = time.perf_counter() - t0
+    done = state["done"]
+    w_done = sum(insts[i]["Nx"] - 2 for i in done)
+    w_all = sum(p["Nx"] - 2 for p in insts)
+    t_full = wall * w_all / w_done
+    return {"value": len(insts) / t_full, "unit": "solves/s", "cores": cores, "kind": "oracle", **host_cpu(),
+            "sample": f"implicit-Euler-coarse Parareal to {tol:g} on the first {len(done)} of the {len(insts)} "
+                      f"seeded instances ({wall:.1f} s on {cores} threads); batch time extrapolated by "
+                      f"sum (Nx - 2)", "iterations_mean": float(sum(state["iters"])) / len(done)}
 
 
 def cpu_baseline(weights, iters, budget_s=20.0):
