@@ -785,11 +785,30 @@ def run_large(args):
             "tensor_tflops": 7 * 2 * 256 * 256 * Xg.shape[0] / (table_ms * 1e-3) / 1e12,
             "tflops_algorithmic": flops_pt * Xg.shape[0] / (table_ms * 1e-3) / 1e12,
             "status": net.device_status()}
+    # the oracle on one host core: consecutive slices of serial fine for about
+    # cpu_seconds, extrapolated to all P slices
+    cpu = None
+    if args.cpu_seconds > 0:
+        import oracle as orc
+
+        op = orc.params(**cfg)
+        V = orc.payoff(op)
+        n_done, t0 = 0, time.perf_counter()
+        while n_done < cfg["P"] and (n_done == 0 or time.perf_counter() - t0 < args.cpu_seconds):
+            V = orc.fine(op, n_done, V)
+            n_done += 1
+        t_cpu = time.perf_counter() - t0
+        rate = (cfg["Nx"] - 2) * cfg["fine_steps"] * n_done / t_cpu
+        cpu = {"value": rate, "unit": "grid-pt-steps/s", "cores": 1, "kind": "oracle", **host_cpu(),
+               "serial_fine_s_extrapolated": t_cpu * cfg["P"] / n_done,
+               "sample": f"the oracle's serial fine, first {n_done} of {cfg['P']} slices ({t_cpu:.1f} s); "
+                         f"serial fine time extrapolated by slice count"}
     print(json.dumps({"mode": "large", "config": cfg, "partition": part, "serial_fine_ms": serial_ms,
                       "fine_ms": fine_ms, "grid_pt_steps_per_s": pt / (fine_ms * 1e-3), "fine_tflops_algorithmic": tf,
                       "fine_frac_of_fp64_peak": tf / peak, "ie_target": target, "ie_tol": ie_tol, "ie_solve_ms": ie_ms,
                       "ie_iterations": stats[0]["iterations"], "ie_err_vs_serial_fine": err,
-                      "speedup_vs_serial_fine": serial_ms / ie_ms, "status": rc, "pinn_coarse_table": pinn}),
+                      "speedup_vs_serial_fine": serial_ms / ie_ms, "status": rc, "pinn_coarse_table": pinn,
+                      "cpu_baseline": cpu}),
           flush=True)
 
 
