@@ -648,12 +648,12 @@ def train_leg(B, torch, n_points=65536, steps=20):
         out[name] = {"ms_per_step": ms, "points_per_s": pps, "tflops_algorithmic": flops_pt * pps / 1e12,
                      "loss_first": first, "loss_after": last, "steps": steps + 2}
     # the tensor-core step is bound by HBM traffic: per hidden layer the stored
-    # (t, z_1, z_2, z_3) in FP32 (layer 1: t only) written by the forward and read by
-    # the adjoint, and the BF16 h and dz operand blocks (4 streams) written once and
-    # read once by the weight gradient; per point the inputs (read by the forward and
-    # by the adjoint's input-layer gradient) and the kinds
+    # (z_0, z_1, z_2, z_3) in FP16 (layer 1: t only, FP32) written by the forward and
+    # read by the adjoint, and the BF16 h and dz operand blocks (4 streams) written
+    # once and read once by the weight gradient; per point the inputs (read by the
+    # forward and by the adjoint's input-layer gradient) and the kinds
     w, nh, n = widths[1], len(widths) - 2, len(kind)
-    act = (16 * (nh - 1) + 4) * 2
+    act = (8 * (nh - 1) + 4) * 2
     blocks = 8 * (nh - 1) * 2 * 2
     per_point = 2 * 16 + 1
     hbm = n * (w * (act + blocks) + per_point)

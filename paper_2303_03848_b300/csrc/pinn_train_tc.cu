@@ -19,12 +19,14 @@
 //
 // Workspace (w the hidden width; a batch runs as chunks of at most 2^19 points,
 // NT = the 128-point tiles of one chunk):
-//   act[l]  float4 [slot][w][128]: (t, z_1, z_2, z_3) of hidden layer l >= 2 at
-//           (neuron, point) of the tile a CTA is working on (one slot per CTA,
-//           reused tile after tile: activations live only between a tile's
-//           forward and its adjoint); the adjoint reads them with one 16-byte
-//           load per neuron, 512 contiguous bytes per warp.  Layer 1 keeps t
-//           only (float [slot][w][128]): its z_1 = W_1[o][0] sc_S, z_2 = 0 and
+//   act[l]  FP16 x 4 [slot][w][128]: (z_0, z_1, z_2, z_3) of hidden layer l >= 2
+//           at (neuron, point) of the tile a CTA is working on (z_0 with its
+//           bias; one slot per CTA, reused tile after tile: activations live
+//           only between a tile's forward and its adjoint, which recomputes
+//           t = tanh z_0 so that t' = 1 - t^2 keeps its relative accuracy on
+//           saturated neurons); the adjoint reads them with one 8-byte load per
+//           neuron, 256 contiguous bytes per warp.  Layer 1 keeps t only (float
+//           [slot][w][128]): its z_1 = W_1[o][0] sc_S, z_2 = 0 and
 //           z_3 = W_1[o][1] sc_tau are constants per neuron;
 //   hb[l]   BF16 [NT][4][128 x w]: h_s of hidden layer l (l < n_lin - 1);
 //   dzb[l]  BF16 [NT][4][128 x w]: dz_s of hidden layer l (l >= 2).
@@ -40,6 +42,7 @@
 // inputs and constant rows.  The input layer's forward runs on CUDA cores.
 // Every wait is bounded; on expiry a kernel records BS_TIMEOUT and stops.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <cstdint>
 #include <cstdio>
@@ -113,7 +116,7 @@ TcLayout tc_layout(const MlpDev& m, int64_t N) {
     o = (o + bytes + 255) / 256 * 256;
     return r;
   };
-  for (int l = 1; l < m.n_lin; ++l) L.act[l] = take((size_t)L.slots * w * 128 * (l == 1 ? 4 : 16));
+  for (int l = 1; l < m.n_lin; ++l) L.act[l] = take((size_t)L.slots * w * 128 * (l == 1 ? 4 : 8));
   for (int l = 1; l < m.n_lin - 1; ++l) L.hb[l] = take((size_t)nt * 4 * 128 * w * 2);
   for (int l = 2; l < m.n_lin; ++l) L.dzb[l] = take((size_t)nt * 4 * 128 * w * 2);
   // one wave of weight-gradient CTAs (one per SM) over all square layers
@@ -208,10 +211,20 @@ __device__ __forceinline__ uint64_t policy_evict_first() {
   return p;
 }
 
-__device__ __forceinline__ void st_hint(float4* p, float4 v, uint64_t pol) {
-  asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z),
-               "f"(v.w), "l"(pol)
-               : "memory");
+__device__ __forceinline__ void st_hint(uint2* p, uint2 v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v2.u32 [%0], {%1, %2}, %3;" ::"l"(p), "r"(v.x), "r"(v.y), "l"(pol) : "memory");
+}
+
+// Four floats rounded to FP16, packed in order.
+__device__ __forceinline__ uint2 pack_half4(float a, float b, float c, float d) {
+  __half2 lo = __floats2half2_rn(a, b), hi = __floats2half2_rn(c, d);
+  return make_uint2(*reinterpret_cast<uint32_t*>(&lo), *reinterpret_cast<uint32_t*>(&hi));
+}
+
+__device__ __forceinline__ float4 unpack_half4(uint2 v) {
+  const float2 lo = __half22float2(*reinterpret_cast<__half2*>(&v.x));
+  const float2 hi = __half22float2(*reinterpret_cast<__half2*>(&v.y));
+  return make_float4(lo.x, lo.y, hi.x, hi.y);
 }
 
 __device__ __forceinline__ void st_hint(float* p, float v, uint64_t pol) {
@@ -252,7 +265,7 @@ __global__ void __launch_bounds__(4 * W, 1) train_tc_kernel(TrainArgs a) {
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
   __shared__ int s_fail;
   __shared__ double s_acc[3];
-  __shared__ float4* s_act[16];
+  __shared__ unsigned char* s_act[16];
   __shared__ unsigned char* s_hb[16];
   __shared__ unsigned char* s_dzb[16];
 
@@ -261,7 +274,7 @@ __global__ void __launch_bounds__(4 * W, 1) train_tc_kernel(TrainArgs a) {
   const int64_t N = a.la.N;
   const int nt = a.L.nt;
   if (t < 16) {
-    s_act[t] = (t >= 1 && t < n_lin) ? reinterpret_cast<float4*>(a.ws + a.L.act[t]) : nullptr;
+    s_act[t] = (t >= 1 && t < n_lin) ? a.ws + a.L.act[t] : nullptr;
     s_hb[t] = (t >= 1 && t < n_lin - 1) ? a.ws + a.L.hb[t] : nullptr;
     s_dzb[t] = (t >= 2 && t < n_lin) ? a.ws + a.L.dzb[t] : nullptr;
   }
@@ -431,7 +444,7 @@ __global__ void __launch_bounds__(4 * W, 1) train_tc_kernel(TrainArgs a) {
       if (!gemm(sq, true)) break;
       const bool last = l == n_lin - 1;
       const float* bl = sB + (l - 1) * W;
-      float4* act = s_act[l] + ((size_t)blockIdx.x * W + c0) * 128 + pl;
+      uint2* act = reinterpret_cast<uint2*>(s_act[l]) + ((size_t)blockIdx.x * W + c0) * 128 + pl;
       unsigned char* hb = last ? nullptr : s_hb[l] + (size_t)tile * 4 * AB + rowoff;
       unsigned char* sa = sA + rowoff;
 #pragma unroll
@@ -445,12 +458,13 @@ __global__ void __launch_bounds__(4 * W, 1) train_tc_kernel(TrainArgs a) {
         for (int j = 0; j < 8; ++j) {
           const int o = c0 + 8 * ch + j;
           const float z1 = __uint_as_float(r[1][j]), z2 = __uint_as_float(r[2][j]), z3 = __uint_as_float(r[3][j]);
-          const float tt = tanh_fast(__uint_as_float(r[0][j]) + bl[o]), d1 = 1.0f - tt * tt;
+          const float z0 = __uint_as_float(r[0][j]) + bl[o];
+          const float tt = tanh_fast(z0), d1 = 1.0f - tt * tt;
           h[0][j] = tt;
           h[1][j] = d1 * z1;
           h[2][j] = d1 * z2 - 2.0f * tt * d1 * z1 * z1;
           h[3][j] = d1 * z3;
-          st_hint(act + (8 * ch + j) * 128, make_float4(tt, z1, z2, z3), keep);
+          st_hint(act + (8 * ch + j) * 128, pack_half4(z0, z1, z2, z3), keep);
           if (last) {
 #pragma unroll
             for (int s = 0; s < 4; ++s) dot[s] = fmaf(sWo[o], bf16r(h[s][j]), dot[s]);
@@ -517,7 +531,7 @@ __global__ void __launch_bounds__(4 * W, 1) train_tc_kernel(TrainArgs a) {
     for (int s = 0; s < 4; ++s) sd[s] = sSd[s * 128 + pl];
     for (int l = n_lin - 1; l >= 1; --l) {
       const bool top = l == n_lin - 1;
-      const float4* act = s_act[l] + ((size_t)blockIdx.x * W + c0) * 128 + pl;
+      const uint2* act = reinterpret_cast<const uint2*>(s_act[l]) + ((size_t)blockIdx.x * W + c0) * 128 + pl;
       const float* act1 = reinterpret_cast<const float*>(s_act[1]) + ((size_t)blockIdx.x * W + c0) * 128 + pl;
       unsigned char* dzb = l >= 2 ? s_dzb[l] + (size_t)tile * 4 * AB + rowoff : nullptr;
       unsigned char* sa = sA + rowoff;
@@ -526,7 +540,10 @@ __global__ void __launch_bounds__(4 * W, 1) train_tc_kernel(TrainArgs a) {
         float4 av[8];
         if (l >= 2) {
 #pragma unroll
-          for (int j = 0; j < 8; ++j) av[j] = act[(8 * ch + j) * 128];
+          for (int j = 0; j < 8; ++j) {
+            av[j] = unpack_half4(act[(8 * ch + j) * 128]);
+            av[j].x = tanh_fast(av[j].x);
+          }
         } else {
 #pragma unroll
           for (int j = 0; j < 8; ++j) av[j] = make_float4(act1[(8 * ch + j) * 128], sZ1[c0 + 8 * ch + j], 0.0f, sZ3[c0 + 8 * ch + j]);
@@ -574,12 +591,15 @@ __global__ void __launch_bounds__(4 * W, 1) train_tc_kernel(TrainArgs a) {
         }
         // the warp's stored activations of these 8 neurons are dead: drop them from L2
         __syncwarp();
-        const float4* wbase = s_act[l] + ((size_t)blockIdx.x * W + c0 + 8 * ch) * 128 + qd * 32;
-        if (l >= 2)
-          discard_l2(reinterpret_cast<const unsigned char*>(wbase + (lane >> 2) * 128) + (lane & 3) * 128);
-        else if (lane < 8)
+        if (l >= 2) {  // 8 neurons x 32 points x 8 bytes: two lines per neuron
+          const uint2* wbase =
+              reinterpret_cast<const uint2*>(s_act[l]) + ((size_t)blockIdx.x * W + c0 + 8 * ch) * 128 + qd * 32;
+          if (lane < 16)
+            discard_l2(reinterpret_cast<const unsigned char*>(wbase + (lane >> 1) * 128) + (lane & 1) * 128);
+        } else if (lane < 8) {
           discard_l2(reinterpret_cast<const float*>(s_act[1]) + ((size_t)blockIdx.x * W + c0 + 8 * ch + lane) * 128 +
                      qd * 32);
+        }
       }
       fence_before();
       if (l >= 2) {
