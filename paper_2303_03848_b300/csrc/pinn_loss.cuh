@@ -54,4 +54,43 @@ __device__ __forceinline__ void point_loss(const LossArgs& la, int d_in, const d
   }
 }
 
+// The same terms and seeds in FP32, for the tensor-core training path: its
+// outputs come from BF16 GEMMs and its seeds are rounded to BF16, so FP32 (and
+// the FP32 exponential) carries no error that matters there, at a fraction of
+// the FP64 cost.  inv_cnt[term] = 1 / (points of that term).
+__device__ __forceinline__ void point_loss_f32(const LossArgs& la, int d_in, const float* x, int kd,
+                                               const float (&out)[4], const float (&inv_cnt)[3], float (&sq)[3],
+                                               float (&g)[4]) {
+  float Ki = (float)la.K, si = (float)la.sigma, ri = (float)la.r;
+  if (d_in >= 5) {
+    si = x[2];
+    ri = x[3];
+    Ki = x[4];
+  }
+  const float S = x[0];
+  g[0] = g[1] = g[2] = g[3] = 0.0f;
+  if (kd == 0) {
+    const float a = 0.5f * si * si * S * S, b = ri * S;
+    const float f = out[3] - a * out[2] - b * out[1] + ri * out[0];
+    sq[0] = f * f;
+    const float gf = 2.0f * f * inv_cnt[0];
+    g[3] = gf;
+    g[2] = -a * gf;
+    g[1] = -b * gf;
+    g[0] = ri * gf;
+  } else {
+    float tgt = 0.0f;
+    if (kd == 2) {
+      const float Sm = (la.smax_over_K > 0.0 && d_in >= 5) ? (float)la.smax_over_K * Ki : (float)la.Smax;
+      tgt = Sm - Ki * expf(-ri * x[1]);
+    } else if (kd == 3) {
+      tgt = S - Ki > 0.0f ? S - Ki : 0.0f;
+    }
+    const float e = out[0] - tgt;
+    const int tt = (kd == 3) ? 2 : 1;
+    sq[tt] = e * e;
+    g[0] = 2.0f * e * inv_cnt[tt];
+  }
+}
+
 }  // namespace bsp

@@ -265,6 +265,7 @@ __global__ void __launch_bounds__(4 * W, 1) train_tc_kernel(TrainArgs a) {
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
   __shared__ int s_fail;
   __shared__ double s_acc[3];
+  __shared__ float s_icnt[3];  // 1 / points per loss term
   __shared__ unsigned char* s_act[16];
   __shared__ unsigned char* s_hb[16];
   __shared__ unsigned char* s_dzb[16];
@@ -311,6 +312,7 @@ __global__ void __launch_bounds__(4 * W, 1) train_tc_kernel(TrainArgs a) {
     mbar_init(&bar[1], 1);
     s_fail = 0;
     s_acc[0] = s_acc[1] = s_acc[2] = 0.0;
+    for (int k = 0; k < 3; ++k) s_icnt[k] = a.cnt[k] ? 1.0f / (float)a.cnt[k] : 0.0f;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
@@ -484,27 +486,38 @@ __global__ void __launch_bounds__(4 * W, 1) train_tc_kernel(TrainArgs a) {
 #pragma unroll
     for (int s = 0; s < 4; ++s) sred[(g * 4 + s) * 128 + pl] = dot[s];
     __syncthreads();
-    if (g == 0) {
-      float sd[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    if (g == 0) {  // warps 0-3, one per lane quadrant
+      float sd[4] = {0.0f, 0.0f, 0.0f, 0.0f}, sqv = 0.0f;  // a point adds to one loss term
+      int term = 0;
       if (valid) {
-        double out[4];
+        float out[4];
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
           float u = sred[s * 128 + pl];
 #pragma unroll
           for (int gg = 1; gg < NG; ++gg) u += sred[(gg * 4 + s) * 128 + pl];
-          out[s] = (double)(s == 0 ? u + bout : u);
+          out[s] = s == 0 ? u + bout : u;
         }
-        double xin[8];
+        float xin[8];
 #pragma unroll
-        for (int i = 0; i < DIN; ++i) xin[i] = a.la.X[p * DIN + i];
-        double sqe[3] = {0.0, 0.0, 0.0}, gs[4];
-        point_loss(a.la, DIN, xin, a.la.kind[p], out, a.cnt, sqe, gs);
+        for (int i = 0; i < DIN; ++i) xin[i] = (float)a.la.X[p * DIN + i];
+        float gs[4], sqe[3] = {0.0f, 0.0f, 0.0f};
+        const int kd = a.la.kind[p];
+        const float icnt[3] = {s_icnt[0], s_icnt[1], s_icnt[2]};
+        point_loss_f32(a.la, DIN, xin, kd, out, icnt, sqe, gs);
+        term = kd == 0 ? 0 : (kd == 3 ? 2 : 1);
+        sqv = sqe[0] + sqe[1] + sqe[2];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) sd[k] = bf16r((float)gs[k]);
-        for (int k = 0; k < 3; ++k)
-          if (sqe[k] != 0.0) atomicAdd(&s_acc[k], sqe[k]);
+        for (int k = 0; k < 4; ++k) sd[k] = bf16r(gs[k]);
         dbo += sd[0];
+      }
+      // the warp's squared errors: one FP64 shared atomic per warp and term
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        float v = term == k ? sqv : 0.0f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0 && v != 0.0f) atomicAdd(&s_acc[k], (double)v);
       }
 #pragma unroll
       for (int s = 0; s < 4; ++s) {
