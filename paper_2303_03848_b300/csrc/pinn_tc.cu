@@ -62,8 +62,15 @@ struct TcArgs {
   int* status;   // BS_TIMEOUT recorded here if a wait gave up
 };
 
+// First-layer row of a neuron in shared memory: DIN weights, the bias, zeros,
+// RW float4s in all (one vector load for 2 inputs, two for 5).
+template <int DIN>
+constexpr int first_row_f4() { return (DIN + 1 + 3) / 4; }
+
 template <int DIN>
 __global__ void __launch_bounds__(256) mlp_tc_kernel(TcArgs a) {
+  static_assert(DIN == 2 || DIN == 5, "2 or 5 inputs");
+  constexpr int RW = first_row_f4<DIN>();
   extern __shared__ __align__(1024) unsigned char smem[];
   const MlpDev& m = a.m;
   const int w = a.w, t = threadIdx.x, warp = t >> 5;
@@ -74,8 +81,8 @@ __global__ void __launch_bounds__(256) mlp_tc_kernel(TcArgs a) {
   // shared memory carve-up
   unsigned char* sW = smem;                                             // n_sq (resident) or 1 square layer
   unsigned char* sA = sW + (a.resident ? (size_t)n_sq : 1) * wbytes;    // 128 x w operand
-  float* sW1 = reinterpret_cast<float*>(sA + (size_t)128 * w * 2);      // w x DIN
-  float* sB = sW1 + w * DIN;                                            // biases of hidden layers, (n_lin-1) x w
+  float* sW1 = reinterpret_cast<float*>(sA + (size_t)128 * w * 2);      // w rows of RW float4 (W_1, b_1)
+  float* sB = sW1 + w * 4 * RW;                                         // biases of hidden layers, (n_lin-1) x w
   float* sWo = sB + (m.n_lin - 1) * w;                                  // output weights, w
   uint64_t* bar = reinterpret_cast<uint64_t*>(sWo + w + 2);             // [0] MMA done, [1] weights landed
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
@@ -83,7 +90,10 @@ __global__ void __launch_bounds__(256) mlp_tc_kernel(TcArgs a) {
   __shared__ float s_dot[2][128];  // output partial sums of the upper column half, by tile parity
 
   // parameters into shared memory; the input map to [-1, 1] in FP32 registers
-  for (int i = t; i < w * DIN; i += blockDim.x) sW1[i] = m.p32[m.poff[1] + i];
+  for (int i = t; i < w * 4 * RW; i += blockDim.x) {
+    const int o = i / (4 * RW), k = i % (4 * RW);
+    sW1[i] = k < DIN ? m.p32[m.poff[1] + o * DIN + k] : (k == DIN ? m.p32[m.poff[1] + w * DIN + o] : 0.0f);
+  }
   for (int l = 1; l < m.n_lin; ++l)
     for (int o = t; o < w; o += blockDim.x)
       sB[(l - 1) * w + o] = m.p32[m.poff[l] + (int64_t)w * m.widths[l - 1] + o];
@@ -155,10 +165,14 @@ __global__ void __launch_bounds__(256) mlp_tc_kernel(TcArgs a) {
         float z[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-          float s = sB[ob + j];
-#pragma unroll
-          for (int i = 0; i < DIN; ++i) s = fmaf(sW1[(ob + j) * DIN + i], xh[i], s);
-          z[j] = s;
+          const float4* row = reinterpret_cast<const float4*>(sW1) + (ob + j) * RW;
+          const float4 r0 = row[0];
+          if constexpr (DIN == 2) {
+            z[j] = fmaf(r0.y, xh[1], fmaf(r0.x, xh[0], r0.z));
+          } else {
+            const float4 r1 = row[1];
+            z[j] = fmaf(r1.x, xh[4], fmaf(r0.w, xh[3], fmaf(r0.z, xh[2], fmaf(r0.y, xh[1], fmaf(r0.x, xh[0], r1.y)))));
+          }
         }
         if (n_sq == 0) {
 #pragma unroll
@@ -312,8 +326,9 @@ bool tc_supported(const MlpDev& m) {
 static size_t tc_smem_bytes(const MlpDev& m, int* resident) {
   const int w = m.widths[1], n_sq = m.n_lin - 2;
   const size_t wbytes = (size_t)w * w * 2;
+  const size_t rw = m.d_in == 2 ? first_row_f4<2>() : first_row_f4<5>();
   const size_t fixed = (size_t)128 * w * 2 +
-                       sizeof(float) * ((size_t)w * m.d_in + (size_t)(m.n_lin - 1) * w + w + 2) + 32 + 1024;
+                       sizeof(float) * ((size_t)w * 4 * rw + (size_t)(m.n_lin - 1) * w + w + 2) + 32 + 1024;
   const int res = (n_sq > 0 && (size_t)n_sq * wbytes + fixed <= 96 * 1024) ? 1 : 0;
   if (resident) *resident = res;
   return (res ? (size_t)n_sq : 1) * wbytes + fixed;
