@@ -219,6 +219,44 @@ def test_tensor_core_gradient_every_layer(B, orc, widths):
             assert abs(l3[c].item() - terms[c]) <= 5e-2 * abs(terms[c]), (c, l3[c].item(), terms[c])
 
 
+def _saturated_fraction(widths, w, X, lo, hi):
+    # share of hidden neurons (over all points and hidden layers) with |tanh z| > 0.95, t' < 0.1
+    h = 2.0 * (X - np.asarray(lo)) / (np.asarray(hi) - np.asarray(lo)) - 1.0
+    off, sat, tot = 0, 0, 0
+    for l in range(1, len(widths) - 1):
+        W = w[off:off + widths[l] * widths[l - 1]].reshape(widths[l], widths[l - 1])
+        off += widths[l] * widths[l - 1]
+        b = w[off:off + widths[l]]
+        off += widths[l]
+        h = np.tanh(h @ W.T + b)
+        sat += int((np.abs(h) > 0.95).sum())
+        tot += h.size
+    return sat / tot
+
+
+@pytest.mark.parametrize("widths", [[2, 64, 64, 64, 1], [2] + [128] * 4 + [1]], ids=["2-3x64", "2-4x128"])
+def test_tensor_core_gradient_saturated_network(B, orc, widths):
+    # the Xavier weights times 3 push 12-17 % of the hidden neurons into
+    # saturation (t' < 0.1), where t' = 1 - t^2 loses relative accuracy if t
+    # itself is rounded; the adjoint recomputes t from the stored pre-activation.
+    # Bound: the BF16 operands' error grows with the weights' scale (measured
+    # 2.4e-2 worst block at scale 3, the same with FP32 activations); 5e-2.
+    lo, hi = _box(widths)
+    w = 3.0 * synth.xavier_params(widths, 3)
+    m = B.PinnModel(widths, lo, hi, seed=3)
+    m.set_weights(w)
+    om = orc.MLP(widths, w, lo, hi)
+    X, kind, prob, sok = _loss_case(widths, 3000, 128, 128, 21)
+    assert _saturated_fraction(widths, w, X, lo, hi) >= 0.1
+    terms, grad = orc.pinn_loss_grad(om, X, kind, prob["K"], prob["sigma"], prob["r"], prob["Smax"], sok)
+    l3, g = m.loss_grad(torch.tensor(X, device="cuda"), torch.tensor(kind, device="cuda"), prob, sok, prec=B.BF16)
+    g = g.cpu().numpy()
+    assert m.device_status() == B.BS_OK
+    for name, a, b in _param_blocks(widths):
+        err = np.abs(g[a:b] - grad[a:b]).max() / max(np.abs(grad[a:b]).max(), 1e-300)
+        assert err <= 5e-2, (name, err)
+
+
 @pytest.mark.parametrize("widths", [[2, 48, 48, 1], [2, 256, 256, 1], [5, 40, 24, 1]], ids=["2-2x48", "2-2x256", "5-40-24"])
 def test_bf16_training_outside_the_tensor_core_shapes(B, orc, widths):
     # BF16 loss and gradient for networks the tensor-core training does not take
