@@ -95,6 +95,13 @@ __host__ __device__ constexpr uint32_t tmem_cols_streams(int w) {
   return 4 * w <= 128 ? 128 : (4 * w <= 256 ? 256 : 512);
 }
 
+// Columns of one thread's group in the epilogues of the fused kernel: 16 for
+// w <= 64 (twice the warps on a tile, each with half the columns), else 32
+// (the 128-register cap of 512 threads bounds the warps); threads per CTA:
+// 4 lane quadrants x w / cols warps.
+__host__ __device__ constexpr int train_cols(int w) { return w <= 64 ? 16 : 32; }
+__host__ __device__ constexpr int train_threads(int w) { return 128 * (w / train_cols(w)); }
+
 // Activation slots: one per resident CTA of the forward + adjoint kernel (its
 // four accumulators bound the CTAs per SM by the 512 tensor-memory columns),
 // each reused tile after tile.
@@ -177,17 +184,18 @@ __device__ __forceinline__ void edge_mma(uint32_t d_tmem, uint32_t a_smem, uint3
 
 // ---------------------------------------------------------------------------
 // Forward and adjoint in one persistent kernel.  A tile's adjoint needs only
-// that tile's forward, so the stored (t, z_1, z_2, z_3) are read back while
-// they are still in L2 (stored with an evict-last policy) and dropped from it
-// after their last use (discard.global.L2: never written back to HBM); the
-// BF16 operand blocks for the weight gradient stream out with an evict-first
-// policy.  A CTA of 4w threads: warp v reads accumulator lanes 32 (v % 4) ..
-// (one point per thread) and owns neurons 32 (v / 4) .. + 31 of every layer.
-// Per square layer one thread issues the four stream GEMMs (M = 128 points,
+// that tile's forward, so the stored FP16 (z_0, z_1, z_2, z_3) are read back
+// while they are still in L2 (stored with an evict-last policy) and dropped
+// from it after their last use (discard.global.L2: never written back to HBM);
+// the BF16 operand blocks for the weight gradient stream out with an
+// evict-first policy.  A CTA of train_threads(w) threads: warp v reads
+// accumulator lanes 32 (v % 4) .. + 31 (one point per thread) and owns the
+// cw = train_cols(w) neurons cw (v / 4) .. + cw - 1 of every layer.  Per
+// square layer one thread issues the four stream GEMMs (M = 128 points,
 // N = K = w); the weights of the next GEMM (W_l going up, W_l^T coming down)
 // are fetched by TMA while the epilogue runs.  Between the two passes the
 // output streams, the loss terms and the adjoint seeds are formed per point
-// in FP64.
+// in FP32.
 // ---------------------------------------------------------------------------
 struct TrainArgs {
   MlpDev m;
@@ -243,8 +251,8 @@ __device__ __forceinline__ void discard_l2(const void* p) {
 }
 
 template <int DIN, int W>
-__global__ void __launch_bounds__(4 * W, 1) train_tc_kernel(TrainArgs a) {
-  constexpr int NG = W / 32;
+__global__ void __launch_bounds__(train_threads(W), 1) train_tc_kernel(TrainArgs a) {
+  constexpr int CW = train_cols(W), NG = W / CW, NCH = CW / 8;  // group columns, groups, 8-column chunks
   constexpr uint32_t WB = W * W * 2, AB = 128 * W * 2, SBO = (W / 8) * 128;
   constexpr uint32_t NCOLS = tmem_cols_streams(W);
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -271,7 +279,7 @@ __global__ void __launch_bounds__(4 * W, 1) train_tc_kernel(TrainArgs a) {
   __shared__ unsigned char* s_dzb[16];
 
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31, g = warp >> 2, qd = warp & 3;
-  const int pl = qd * 32 + lane, c0 = g * 32;
+  const int pl = qd * 32 + lane, c0 = g * CW;
   const int64_t N = a.la.N;
   const int nt = a.L.nt;
   if (t < 16) {
@@ -415,7 +423,7 @@ __global__ void __launch_bounds__(4 * W, 1) train_tc_kernel(TrainArgs a) {
       unsigned char* hb = s_hb[1] + (size_t)tile * 4 * AB + rowoff;
       unsigned char* sa = sA + rowoff;
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
+      for (int k = 0; k < NCH; ++k) {
         float h[4][8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
@@ -450,7 +458,7 @@ __global__ void __launch_bounds__(4 * W, 1) train_tc_kernel(TrainArgs a) {
       unsigned char* hb = last ? nullptr : s_hb[l] + (size_t)tile * 4 * AB + rowoff;
       unsigned char* sa = sA + rowoff;
 #pragma unroll
-      for (int ch = 0; ch < 4; ++ch) {
+      for (int ch = 0; ch < NCH; ++ch) {
         uint32_t r[4][8];
 #pragma unroll
         for (int s = 0; s < 4; ++s) tmem_ld8_nowait(tl + (uint32_t)(s * W + c0 + 8 * ch), r[s]);
@@ -549,7 +557,7 @@ __global__ void __launch_bounds__(4 * W, 1) train_tc_kernel(TrainArgs a) {
       unsigned char* dzb = l >= 2 ? s_dzb[l] + (size_t)tile * 4 * AB + rowoff : nullptr;
       unsigned char* sa = sA + rowoff;
 #pragma unroll
-      for (int ch = 0; ch < 4; ++ch) {
+      for (int ch = 0; ch < NCH; ++ch) {
         float4 av[8];
         if (l >= 2) {
 #pragma unroll
@@ -872,16 +880,17 @@ cudaError_t run_train_tc(const MlpDev& m, const LossArgs& la, unsigned char* ws,
   {
     TrainArgs a{m, la, ws, L, cnt, loss_acc, grad};
     const size_t smem = WB + 4 * AB + 7 * kTileB +
-                        sizeof(float) * ((size_t)W * DIN + (size_t)(n_lin - 1) * W + 3 * W + (W / 32) * 4 * 128 +
+                        sizeof(float) * ((size_t)W * DIN + (size_t)(n_lin - 1) * W + 3 * W +
+                                         (size_t)(W / train_cols(W)) * 4 * 128 +
                                          4 * 128) +
                         64;
     auto kern = train_tc_kernel<DIN, W>;
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
       return e;
-    const int64_t cap = (int64_t)nsm * resident_per_sm(kern, smem, 4 * W, tmem_cols_streams(W));
+    const int64_t cap = (int64_t)nsm * resident_per_sm(kern, smem, train_threads(W), tmem_cols_streams(W));
     int64_t grid = L.nt < cap ? L.nt : cap;
     if (grid > L.slots) grid = L.slots;
-    kern<<<(unsigned)grid, 4 * W, smem, s>>>(a);
+    kern<<<(unsigned)grid, train_threads(W), smem, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   {
