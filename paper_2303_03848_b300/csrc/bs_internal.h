@@ -115,13 +115,14 @@ size_t loss_grad_workspace_bytes(const MlpDev& m, int64_t N);
 // accumulation: forward with the derivative streams, adjoint and every layer's
 // weight gradient for networks d_in (2 or 5) -> w x ... x w -> 1 with w in
 // {32, 64, 96, 128}.  The workspace holds the per-layer activations, adjoints
-// and partial sums (train_tc_workspace_bytes, 256-byte aligned); the loss sums
-// go to loss_acc (3 doubles) and the gradient is added to grad (zeroed by the
-// caller).
+// and partial sums (train_tc_workspace_bytes, 256-byte aligned).  One prepass
+// zeroes grad and counts each loss term's points into cnt; the loss sums go to
+// loss_acc (3 doubles) and the loss terms (sum / count) to loss3.  The caller
+// zeroes cnt and loss_acc.
 bool train_tc_supported(const MlpDev& m);
 size_t train_tc_workspace_bytes(const MlpDev& m, int64_t N);
-cudaError_t launch_train_tc(const MlpDev& m, const LossArgs& la, unsigned char* ws, const unsigned long long* cnt,
-                            double* loss_acc, double* grad, cudaStream_t s);
+cudaError_t launch_train_tc(const MlpDev& m, const LossArgs& la, unsigned char* ws, unsigned long long* cnt,
+                            double* loss_acc, double* grad, double* loss3, cudaStream_t s);
 // A bounded mbarrier wait that expires (arrive == 0) or completes (pinn_tc.cu).
 cudaError_t launch_wait_probe(int arrive, long long limit, int* status, cudaStream_t s);
 cudaError_t launch_adam(int64_t n, double* theta, double* mom1, double* mom2, const double* g, int step, double lr,

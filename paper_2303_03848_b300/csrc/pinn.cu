@@ -512,16 +512,16 @@ static cudaError_t loss_grad_impl(const MlpDev& m, const LossArgs& la, double* l
   double* acc = reinterpret_cast<double*>(tail + 24);
   cudaError_t e = cudaMemsetAsync(tail, 0, 48, s);
   if (e != cudaSuccess) return e;
+  if (RND == 2 && train_tc_supported(m)) {  // BF16 on the tensor cores (zeroes grad, counts, finishes loss3)
+    if (((uintptr_t)base & 255) != 0) return cudaErrorInvalidValue;
+    return launch_train_tc(m, la, base, cnt, acc, grad, loss3, s);
+  }
   int64_t np = 0;
   for (int l = 1; l <= m.n_lin; ++l) np += (int64_t)m.widths[l] * m.widths[l - 1] + m.widths[l];
   e = cudaMemsetAsync(grad, 0, (size_t)np * sizeof(double), s);
   if (e != cudaSuccess) return e;
   count_kinds_kernel<<<148, 256, 0, s>>>(la.kind, la.N, cnt);
-  if (RND == 2 && train_tc_supported(m)) {  // BF16 on the tensor cores
-    if (((uintptr_t)base & 255) != 0) return cudaErrorInvalidValue;
-    e = launch_train_tc(m, la, base, cnt, acc, grad, s);
-    if (e != cudaSuccess) return e;
-  } else {  // CUDA cores: forward, adjoint, per-layer reductions
+  {  // CUDA cores: forward, adjoint, per-layer reductions
     {
       const size_t per_thread = 2 * 4 * (size_t)m.max_w * sizeof(Tp);
       const int TP = points_per_cta(per_thread);

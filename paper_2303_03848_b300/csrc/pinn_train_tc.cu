@@ -150,16 +150,38 @@ __device__ __forceinline__ uint4 pack8(const float* v) {
 
 // Pack the square layers: W_l (rows o, K = i) for the forward and W_l^T (rows
 // i, K = o) for the adjoint, BF16 core-matrix layout.
-__global__ void pack_train_kernel(MlpDev m, int w, unsigned char* fwd, unsigned char* bwd) {
+// The step's prepass in one launch: pack W and W^T of the square layers,
+// zero the gradient (np entries) and count the points of each loss term into
+// cnt (zeroed by the caller; kind 0 interior, 1 and 2 boundary, 3 expiry).
+__global__ void train_prep_kernel(MlpDev m, int w, unsigned char* fwd, unsigned char* bwd, const int8_t* kind,
+                                  int64_t N, unsigned long long* cnt, double* grad, int64_t np) {
   const int n_sq = m.n_lin - 2;
   const int64_t per = (int64_t)w * w;
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < per * n_sq;
-       q += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t q = i0; q < per * n_sq; q += stride) {
     const int sq = (int)(q / per);
     const int o = (int)((q % per) / w), i = (int)(q % w);
     const __nv_bfloat16 v = __float2bfloat16_rn(m.p32[m.poff[sq + 2] + (int64_t)o * w + i]);
     *reinterpret_cast<__nv_bfloat16*>(fwd + sq * per * 2 + canon_off(o, i, w)) = v;
     *reinterpret_cast<__nv_bfloat16*>(bwd + sq * per * 2 + canon_off(i, o, w)) = v;
+  }
+  for (int64_t q = i0; q < np; q += stride) grad[q] = 0.0;
+  unsigned long long c0 = 0, c1 = 0, c2 = 0;
+  for (int64_t q = i0; q < N; q += stride) {
+    const int k = kind[q];
+    if (k == 0) ++c0;
+    else if (k == 1 || k == 2) ++c1;
+    else ++c2;
+  }
+  for (int o = 16; o >= 1; o >>= 1) {
+    c0 += __shfl_down_sync(0xffffffffu, c0, o);
+    c1 += __shfl_down_sync(0xffffffffu, c1, o);
+    c2 += __shfl_down_sync(0xffffffffu, c2, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (c0) atomicAdd(cnt + 0, c0);
+    if (c1) atomicAdd(cnt + 1, c1);
+    if (c2) atomicAdd(cnt + 2, c2);
   }
 }
 
@@ -840,7 +862,13 @@ __global__ void __launch_bounds__(128) train_wgrad_tc_kernel(WgArgs a) {
 // gW[o][i] and gb[o] of square layer blockIdx.z + 2: sums over the layer's
 // CTAs of the partial sums; blockIdx.y takes one group of CTAs and adds its
 // sum atomically in FP64 (the gradient starts at zero).
-__global__ void wgrad_sum_kernel(MlpDev m, const float* __restrict__ partial, int ny, double* __restrict__ grad) {
+// With loss3 set (the batch's last chunk), block (0, 0, 0) also writes the
+// loss terms: each sum over its points divided by their count.
+__global__ void wgrad_sum_kernel(MlpDev m, const float* __restrict__ partial, int ny, double* __restrict__ grad,
+                                 const double* loss_acc, const unsigned long long* cnt, double* loss3) {
+  if (loss3 != nullptr && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0) {
+    for (int k = 0; k < 3; ++k) loss3[k] = cnt[k] ? loss_acc[k] / (double)cnt[k] : 0.0;
+  }
   const int w = m.widths[1], sq = blockIdx.z;
   const int64_t wc = (int64_t)w * (w + 1);
   const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -873,7 +901,8 @@ int resident_per_sm(K kern, size_t smem, int threads, uint32_t tmem_cols) {
 
 template <int DIN, int W>
 cudaError_t run_train_tc(const MlpDev& m, const LossArgs& la, unsigned char* ws, const TcLayout& L,
-                         const unsigned long long* cnt, double* loss_acc, double* grad, cudaStream_t s) {
+                         const unsigned long long* cnt, double* loss_acc, double* grad, double* loss3,
+                         cudaStream_t s) {
   constexpr uint32_t WB = W * W * 2, AB = 128 * W * 2;
   const int n_lin = m.n_lin, n_sq = n_lin - 2, nsm = sm_count();
   cudaError_t e;
@@ -913,7 +942,7 @@ cudaError_t run_train_tc(const MlpDev& m, const LossArgs& la, unsigned char* ws,
     const int64_t wc = (int64_t)W * (W + 1);
     const int groups = L.ny < 8 ? L.ny : 8;
     wgrad_sum_kernel<<<dim3((unsigned)((wc + 255) / 256), (unsigned)groups, (unsigned)n_sq), 256, 0, s>>>(
-        m, reinterpret_cast<const float*>(ws + L.partial), L.ny, grad);
+        m, reinterpret_cast<const float*>(ws + L.partial), L.ny, grad, loss_acc, cnt, loss3);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -921,16 +950,17 @@ cudaError_t run_train_tc(const MlpDev& m, const LossArgs& la, unsigned char* ws,
 
 template <int DIN>
 cudaError_t run_train_tc_w(const MlpDev& m, const LossArgs& la, unsigned char* ws, const TcLayout& L,
-                           const unsigned long long* cnt, double* loss_acc, double* grad, cudaStream_t s) {
+                           const unsigned long long* cnt, double* loss_acc, double* grad, double* loss3,
+                           cudaStream_t s) {
   switch (m.widths[1]) {
     case 32:
-      return run_train_tc<DIN, 32>(m, la, ws, L, cnt, loss_acc, grad, s);
+      return run_train_tc<DIN, 32>(m, la, ws, L, cnt, loss_acc, grad, loss3, s);
     case 64:
-      return run_train_tc<DIN, 64>(m, la, ws, L, cnt, loss_acc, grad, s);
+      return run_train_tc<DIN, 64>(m, la, ws, L, cnt, loss_acc, grad, loss3, s);
     case 96:
-      return run_train_tc<DIN, 96>(m, la, ws, L, cnt, loss_acc, grad, s);
+      return run_train_tc<DIN, 96>(m, la, ws, L, cnt, loss_acc, grad, loss3, s);
     case 128:
-      return run_train_tc<DIN, 128>(m, la, ws, L, cnt, loss_acc, grad, s);
+      return run_train_tc<DIN, 128>(m, la, ws, L, cnt, loss_acc, grad, loss3, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -951,14 +981,17 @@ size_t train_tc_workspace_bytes(const MlpDev& m, int64_t N) {
   return tc_layout(m, N).total;
 }
 
-cudaError_t launch_train_tc(const MlpDev& m, const LossArgs& la, unsigned char* ws, const unsigned long long* cnt,
-                            double* loss_acc, double* grad, cudaStream_t s) {
+cudaError_t launch_train_tc(const MlpDev& m, const LossArgs& la, unsigned char* ws, unsigned long long* cnt,
+                            double* loss_acc, double* grad, double* loss3, cudaStream_t s) {
   if (la.N <= 0) return cudaSuccess;
   if (!train_tc_supported(m) || ((uintptr_t)ws & 255) != 0) return cudaErrorInvalidValue;
   const TcLayout L = tc_layout(m, la.N);
   const int w = m.widths[1], n_sq = m.n_lin - 2;
+  int64_t np = 0;
+  for (int l = 1; l <= m.n_lin; ++l) np += (int64_t)m.widths[l] * m.widths[l - 1] + m.widths[l];
   unsigned char* wpack = ws + L.pack;
-  pack_train_kernel<<<148, 256, 0, s>>>(m, w, wpack, wpack + (size_t)n_sq * w * w * 2);
+  train_prep_kernel<<<sm_count(), 256, 0, s>>>(m, w, wpack, wpack + (size_t)n_sq * w * w * 2, la.kind, la.N, cnt,
+                                               grad, np);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // consecutive chunks of the batch; the loss terms are means over the whole
@@ -971,8 +1004,9 @@ cudaError_t launch_train_tc(const MlpDev& m, const LossArgs& la, unsigned char* 
     lc.N = la.N - off < chunk ? la.N - off : chunk;
     TcLayout Lc = L;
     Lc.nt = (int)((lc.N + 127) / 128);
-    e = m.d_in == 2 ? run_train_tc_w<2>(m, lc, ws, Lc, cnt, loss_acc, grad, s)
-                    : run_train_tc_w<5>(m, lc, ws, Lc, cnt, loss_acc, grad, s);
+    double* l3 = off + chunk >= la.N ? loss3 : nullptr;  // the last chunk finishes the loss terms
+    e = m.d_in == 2 ? run_train_tc_w<2>(m, lc, ws, Lc, cnt, loss_acc, grad, l3, s)
+                    : run_train_tc_w<5>(m, lc, ws, Lc, cnt, loss_acc, grad, l3, s);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
