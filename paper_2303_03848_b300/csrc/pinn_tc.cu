@@ -2,20 +2,22 @@
 // on the 5th-generation tensor cores (tcgen05), BF16 operands, FP32
 // accumulation in tensor memory.
 //
-// One CTA of 256 threads owns a tile of 128 points at a time (the M = 128 rows
-// of every layer GEMM) and walks the tiles persistently.  Warps v and v + 4
-// read the same 32 accumulator lanes (points 32 v .. 32 v + 31) and split the
-// w columns of every layer between them, so eight warps share each tile's
-// epilogue.  Per tile:
+// One CTA owns a tile of 128 points at a time (the M = 128 rows of every layer
+// GEMM) and walks the tiles persistently.  Its warps v, v + 4, ... read the
+// same 32 accumulator lanes (points 32 (v % 4) .. + 31) and split the w
+// columns of every layer between them: two warps per lane quadrant (256
+// threads) up to w = 128, four (512 threads) at w = 256, where the tensor
+// memory holds only two CTAs per SM.  Per tile:
 //   * input layer (2 or 5 inputs -> w): CUDA cores, FP32, written as the BF16
 //     A operand of the first square layer;
 //   * each square layer h' = tanh(W h + b): one thread issues w/16 tcgen05.mma
 //     (M = 128, N = w, K = 16) into a TMEM accumulator and commits them to an
-//     mbarrier; the four warps read their 32 lanes back with tcgen05.ld, add
+//     mbarrier; the warps read their 32 lanes back with tcgen05.ld, add
 //     the bias, apply FP32 tanh and write the BF16-rounded result as the next
 //     A operand;
 //   * output layer (w -> 1): FP32 tanh of the last hidden layer and a dot
-//     product on CUDA cores, the two column halves added through shared memory.
+//     product on CUDA cores, the column groups' parts added through shared
+//     memory.
 // Operands sit in shared memory in the no-swizzle K-major core-matrix layout
 // (8 rows x 16 bytes per core matrix).  The square layers are packed into that
 // layout once per call and fed to shared memory by TMA bulk copies
@@ -67,15 +69,18 @@ struct TcArgs {
 template <int DIN>
 constexpr int first_row_f4() { return (DIN + 1 + 3) / 4; }
 
-template <int DIN>
-__global__ void __launch_bounds__(256) mlp_tc_kernel(TcArgs a) {
+// NWQ warps share each lane quadrant (its 32 points), w / NWQ columns each:
+// 2 (256 threads, up to three CTAs per SM) or, for w = 256, 4 (512 threads and
+// two CTAs per SM, the most the tensor memory holds at that width).
+template <int DIN, int NWQ>
+__global__ void __launch_bounds__(128 * NWQ, NWQ == 4 ? 2 : 0) mlp_tc_kernel(TcArgs a) {
   static_assert(DIN == 2 || DIN == 5, "2 or 5 inputs");
   constexpr int RW = first_row_f4<DIN>();
   extern __shared__ __align__(1024) unsigned char smem[];
   const MlpDev& m = a.m;
   const int w = a.w, t = threadIdx.x, warp = t >> 5;
   const int pt = (warp & 3) * 32 + (t & 31);  // this thread's point (accumulator lane)
-  const int hw = w / 2, cb = (warp >> 2) * hw;  // and its columns [cb, cb + hw)
+  const int hw = w / NWQ, cb = (warp >> 2) * hw;  // and its columns [cb, cb + hw)
   const int n_sq = m.n_lin - 2;
   const uint32_t wbytes = (uint32_t)w * w * 2;
   // shared memory carve-up
@@ -87,7 +92,7 @@ __global__ void __launch_bounds__(256) mlp_tc_kernel(TcArgs a) {
   uint64_t* bar = reinterpret_cast<uint64_t*>(sWo + w + 2);             // [0] MMA done, [1] weights landed
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
   __shared__ int s_fail;
-  __shared__ float s_dot[2][128];  // output partial sums of the upper column half, by tile parity
+  __shared__ float s_dot[2][NWQ - 1][128];  // output partial sums of the other column groups, by tile parity
 
   // parameters into shared memory; the input map to [-1, 1] in FP32 registers
   for (int i = t; i < w * 4 * RW; i += blockDim.x) {
@@ -274,9 +279,14 @@ __global__ void __launch_bounds__(256) mlp_tc_kernel(TcArgs a) {
     // the two column halves of the output dot product (two buffers: without a
     // square layer this is the only barrier of a tile)
     const int par = (int)((tile / gridDim.x) & 1);
-    if (warp >= 4) s_dot[par][pt] = dot;
+    if (warp >= 4) s_dot[par][(warp >> 2) - 1][pt] = dot;
     __syncthreads();
-    if (warp < 4 && valid) a.u[p] = (double)(dot + s_dot[par][pt] + bout);
+    if (warp < 4 && valid) {
+      float u = dot;
+#pragma unroll
+      for (int q = 0; q < NWQ - 1; ++q) u += s_dot[par][q][pt];
+      a.u[p] = (double)(u + bout);
+    }
   }
   // a weight copy still in flight (only after a failed wait) lands before exit
   if (t == 0 && w_pending) (void)mbar_wait_bounded(&bar[1], ph_w);
@@ -356,7 +366,10 @@ cudaError_t launch_mlp_eval_tc(const MlpDev& m, unsigned char* packed, const dou
   const size_t smem = tc_smem_bytes(m, &resident);
   if (smem > 220 * 1024) return cudaErrorInvalidValue;
   TcArgs a{m, packed, X, N, u, w, resident, status};
-  auto kern = m.d_in == 2 ? mlp_tc_kernel<2> : mlp_tc_kernel<5>;
+  const bool wide = w == 256;  // four warps per lane quadrant
+  const int threads = wide ? 512 : 256;
+  auto kern = m.d_in == 2 ? (wide ? mlp_tc_kernel<2, 4> : mlp_tc_kernel<2, 2>)
+                          : (wide ? mlp_tc_kernel<5, 4> : mlp_tc_kernel<5, 2>);
   if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
     return e;
   // CTAs per SM from the shared memory each one takes (dynamic + static + the
@@ -370,7 +383,7 @@ cudaError_t launch_mlp_eval_tc(const MlpDev& m, unsigned char* packed, const dou
   cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
   cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
   int per_sm = (int)((size_t)sm_smem / (smem + fa.sharedSizeBytes + (size_t)reserved));
-  const int by_regs = 65536 / (256 * (fa.numRegs > 0 ? fa.numRegs : 255));
+  const int by_regs = 65536 / (threads * (fa.numRegs > 0 ? fa.numRegs : 255));
   if (per_sm > by_regs) per_sm = by_regs;
   if (per_sm < 1) per_sm = 1;
   int ncols = 32;
@@ -379,7 +392,7 @@ cudaError_t launch_mlp_eval_tc(const MlpDev& m, unsigned char* packed, const dou
   if (per_sm > 4) per_sm = 4;
   const int64_t ntiles = (N + 127) / 128;
   const int64_t grid = ntiles < (int64_t)nsm * per_sm ? ntiles : (int64_t)nsm * per_sm;
-  kern<<<(unsigned)grid, 256, smem, s>>>(a);
+  kern<<<(unsigned)grid, threads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
