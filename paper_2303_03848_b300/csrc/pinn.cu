@@ -567,8 +567,10 @@ cudaError_t launch_loss_grad(const MlpDev& m, const LossArgs& la, double* loss3,
 }
 
 // Adam (Kingma & Ba) on the FP64 master parameters; refreshes the FP32 copy.
+// ic1, ic2: reciprocals of the bias corrections 1 - b1^t, 1 - b2^t (formed once
+// on the host: FP64 division is a long instruction sequence on this part).
 __global__ void adam_kernel(int64_t n, double* __restrict__ th, double* __restrict__ m1, double* __restrict__ m2,
-                            const double* __restrict__ g, double c1, double c2, double lr, float* __restrict__ p32) {
+                            const double* __restrict__ g, double ic1, double ic2, double lr, float* __restrict__ p32) {
   const double b1 = 0.9, b2 = 0.999, eps = 1e-8;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const double gi = g[i];
@@ -576,7 +578,7 @@ __global__ void adam_kernel(int64_t n, double* __restrict__ th, double* __restri
     const double v = b2 * m2[i] + (1.0 - b2) * gi * gi;
     m1[i] = a;
     m2[i] = v;
-    const double mh = a / c1, vh = v / c2;
+    const double mh = a * ic1, vh = v * ic2;
     const double t = th[i] - lr * mh / (sqrt(vh) + eps);
     th[i] = t;
     p32[i] = (float)t;
@@ -586,7 +588,7 @@ __global__ void adam_kernel(int64_t n, double* __restrict__ th, double* __restri
 cudaError_t launch_adam(int64_t n, double* theta, double* mom1, double* mom2, const double* g, int step, double lr,
                         float* p32, cudaStream_t s) {
   const double c1 = 1.0 - pow(0.9, (double)step), c2 = 1.0 - pow(0.999, (double)step);
-  adam_kernel<<<148, 256, 0, s>>>(n, theta, mom1, mom2, g, c1, c2, lr, p32);
+  adam_kernel<<<148, 256, 0, s>>>(n, theta, mom1, mom2, g, 1.0 / c1, 1.0 / c2, lr, p32);
   return cudaGetLastError();
 }
 
