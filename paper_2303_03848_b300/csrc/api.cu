@@ -249,6 +249,8 @@ static int problem_create(const bs_params* p, int32_t n_instances, const Part* p
     ex += q.fine_steps + 1;
     in.exp_ie = ex;
     ex += q.coarse_steps + 1;
+    in.exp_sl = ex;
+    ex += q.P + 1;
     in.state_off = prob->total_state;
     prob->total_state += (int64_t)(q.P + 1) * q.Nx;
     in.slice_off = prob->total_slice;
@@ -835,7 +837,7 @@ int parareal_solve(bs_problem* prob, int coarse_kind, const pinn_model* model, i
     if ((e = bsp::launch_mlp_eval(model->dev, prec, prob->Xgrid, prob->total_state, prob->gtab, nullptr, s)) !=
         cudaSuccess)
       return map_err(e);
-    if ((e = bsp::launch_table_fix(prob->d_insts, n, prob->gtab, s)) != cudaSuccess) return map_err(e);
+    if ((e = bsp::launch_table_fix(prob->d_insts, n, prob->exptab, prob->gtab, s)) != cudaSuccess) return map_err(e);
   }
   // a2: initial iterate
   if ((e = bsp::launch_parareal_init(prob->d_insts, n, prob->buf0, prob->buf1, prob->gtab,
@@ -1041,7 +1043,7 @@ extern "C" int parareal_solve_static(bs_problem* prob, int coarse_kind, const pi
     if ((e = bsp::launch_grid_points(prob->d_insts, n, d_in, xg, s)) != cudaSuccess) return map_err(e);
     if ((e = bsp::launch_mlp_eval(model->dev, prec, xg, prob->total_state, gtab, nullptr, s)) != cudaSuccess)
       return map_err(e);
-    if ((e = bsp::launch_table_fix(prob->d_insts, n, gtab, s)) != cudaSuccess) return map_err(e);
+    if ((e = bsp::launch_table_fix(prob->d_insts, n, prob->exptab, gtab, s)) != cudaSuccess) return map_err(e);
   }
   if ((e = bsp::launch_parareal_init(prob->d_insts, n, buf0, buf1, gtab, coarse_kind == BS_COARSE_PINN, ctrl, nrm,
                                      max_iter, s)) != cudaSuccess)

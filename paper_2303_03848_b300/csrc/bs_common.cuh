@@ -28,6 +28,7 @@ struct Inst {
   int32_t C, NW, M, R, Np, Ws, pad0, pad1;  // partition of the tridiagonal rows
   int64_t coef_cn, coef_ie;    // offsets (doubles) of the two coefficient blocks in the pool
   int64_t exp_cn, exp_ie;      // offsets of exp(-r m dtau) tables (Mf+1 / Mg+1 entries)
+  int64_t exp_sl;              // offset of exp(-r tau_n), n = 0..P (P+1 entries)
   int64_t state_off;           // offset of the instance in (P+1)*Nx arrays
   int64_t slice_off;           // offset of the instance in P*Nx arrays
   int64_t task_off;            // offset of the instance in per-slice arrays (P entries)

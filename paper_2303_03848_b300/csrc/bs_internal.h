@@ -73,7 +73,7 @@ cudaError_t launch_parareal_finalize(const Inst* d_insts, int n_inst, const doub
 cudaError_t launch_copy_result(const Inst* d_insts, int n_inst, const Ctrl* ctrl, const double* buf0,
                                const double* buf1, double* out, cudaStream_t s);
 cudaError_t launch_grid_points(const Inst* d_insts, int n_inst, int d_in, double* X, cudaStream_t s);
-cudaError_t launch_table_fix(const Inst* d_insts, int n_inst, double* g, cudaStream_t s);
+cudaError_t launch_table_fix(const Inst* d_insts, int n_inst, const double* exptab, double* g, cudaStream_t s);
 
 // ---- network (pinn.cu) ----
 struct MlpDev {

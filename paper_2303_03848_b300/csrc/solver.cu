@@ -84,6 +84,10 @@ __global__ void __launch_bounds__(32) setup_rows_kernel(const Inst* insts, const
       double* et = exptab + (kind == 0 ? in.exp_cn : in.exp_ie);
       const double dt = in.T / ((double)in.P * (double)steps);
       for (int m = threadIdx.x; m <= steps; m += 32) et[m] = exp(-in.r * ((double)m * dt));
+      if (kind == 0) {  // exp(-r tau_n) at the slice boundaries, tau_n = T n / P
+        double* es = exptab + in.exp_sl;
+        for (int n = threadIdx.x; n <= in.P; n += 32) es[n] = exp(-in.r * (in.T * (double)n / (double)in.P));
+      }
     }
     double lam[32], mu[32], del[32];
     double prev_u = 0.0;
@@ -638,13 +642,12 @@ __device__ __forceinline__ double row_value(const double* __restrict__ cb, int k
 
 // Run `steps` steps of the propagator on slice n starting from scaled state W.
 // The right Dirichlet value of the next step is formed while the barrier
-// completes, from exp(-r m dtau) read one step ahead.
+// completes, from exp(-r m dtau) read one step ahead; KeN = K exp(-r tau_n) of
+// the slice's start (slice_KeN, or from the set-up table of exp(-r tau_n)).
 template <int M, int NW, int C, bool CN, int S2 = 1>
-__device__ __forceinline__ void run_slice(const Inst& in, int n, const double* __restrict__ et, int steps,
+__device__ __forceinline__ void run_slice(const Inst& in, double KeN, const double* __restrict__ et, int steps,
                                           double (&W)[M], double (&x)[M], SolverSmem<M, NW, C, S2>& sm,
                                           SolverRegs& rg, int& seq) {
-  const double tau_n = in.T * (double)n / (double)in.P;
-  const double KeN = in.K * exp(-in.r * tau_n);
   const bool last_warp = cta_rank<C>() == C - 1 && (lthread<NW>() >> 5) == NW - 1;
   double Bold = in.Smax - KeN;  // exp(0) = 1
   double Zb = 0.0, e_next = 0.0;
@@ -693,6 +696,17 @@ __device__ __forceinline__ void block_sum2(double& a, double& b, double (*red)[N
 
 __device__ __forceinline__ double bc_right(const Inst& in, int n) {
   return in.Smax - in.K * exp(-in.r * (in.T * (double)n / (double)in.P));
+}
+
+// The same from the set-up table es[n] = exp(-r tau_n) (bitwise the same value):
+// the kernels that take one step per slice use it and compute no exponential.
+__device__ __forceinline__ double bc_right(const Inst& in, const double* __restrict__ es, int n) {
+  return in.Smax - in.K * es[n];
+}
+
+__device__ __forceinline__ double slice_KeN(const Inst& in, int n) {
+  const double tau_n = in.T * (double)n / (double)in.P;
+  return in.K * exp(-in.r * tau_n);
 }
 
 // ---------------------------------------------------------------------------
@@ -749,7 +763,7 @@ __global__ void __launch_bounds__(S2 * NW * 32, 1) prop_kernel(PropArgs a) {
       load_state<M, NW, C, S2>(in, Vin, sm, rg, W);
 #pragma unroll
       for (int k = 0; k < M; ++k) x[k] = 0.0;
-      run_slice<M, NW, C, CN, S2>(in, n, et, steps, W, x, sm, rg, seq);
+      run_slice<M, NW, C, CN, S2>(in, slice_KeN(in, n), et, steps, W, x, sm, rg, seq);
 
       const bool first_thread = c == 0 && t == 0;
       const bool last_thread = c == C - 1 && t == T - 1;
@@ -847,7 +861,7 @@ __global__ void __launch_bounds__(NW * 32, 1) serial_fine_kernel(SerialArgs a) {
     load_state<M, NW, C>(in, U + (int64_t)n * Nx, sm, rg, W);
 #pragma unroll
     for (int k = 0; k < M; ++k) x[k] = 0.0;
-    run_slice<M, NW, C, true>(in, n, et, in.Mf, W, x, sm, rg, seq);
+    run_slice<M, NW, C, true>(in, in.K * __ldg(a.exptab + in.exp_sl + n), et, in.Mf, W, x, sm, rg, seq);
     double* Vout = U + (int64_t)(n + 1) * Nx;
 #pragma unroll
     for (int k = 0; k < M; ++k) {
@@ -855,7 +869,7 @@ __global__ void __launch_bounds__(NW * 32, 1) serial_fine_kernel(SerialArgs a) {
       if (j >= 1 && j <= Nx - 2) Vout[j] = row_value<M, NW, C, true>(cb, k, W, x, rg.isigp);
     }
     if (c == 0 && t == 0) Vout[0] = 0.0;
-    if (c == C - 1 && t == T - 1) Vout[Nx - 1] = bc_right(in, n + 1);
+    if (c == C - 1 && t == T - 1) Vout[Nx - 1] = bc_right(in, a.exptab + in.exp_sl, n + 1);
     // the next slice reads values other CTAs wrote (global memory, cluster scope)
     __threadfence();
     if constexpr (C > 1) {
@@ -926,11 +940,11 @@ __global__ void __launch_bounds__(NW * 32, 1) sweep_kernel(SweepArgs a) {
         W[k] = (k < M - 1) ? sm.rows[2][k][t] * v : rg.sigp * v;
         x[k] = 0.0;
       }
-      run_slice<M, NW, C, false>(in, n, et, in.Mg, W, x, sm, rg, seq);
+      run_slice<M, NW, C, false>(in, in.K * __ldg(a.exptab + in.exp_sl + n), et, in.Mg, W, x, sm, rg, seq);
 #pragma unroll
       for (int k = 0; k < M; ++k) Gv[k] = row_value<M, NW, C, false>(cb, k, W, x, rg.isigp);
       G0 = 0.0;
-      GB = bc_right(in, n + 1);
+      GB = bc_right(in, a.exptab + in.exp_sl, n + 1);
     } else {
 #pragma unroll
       for (int k = 0; k < M; ++k) {
@@ -1104,13 +1118,13 @@ __global__ void grid_points_kernel(const Inst* insts, int n_inst, int d_in, doub
 }
 
 // Dirichlet nodes of the network table replaced by the exact values.
-__global__ void table_fix_kernel(const Inst* insts, int n_inst, double* g) {
+__global__ void table_fix_kernel(const Inst* insts, int n_inst, const double* exptab, double* g) {
   const int idx = blockIdx.x;
   if (idx >= n_inst) return;
   const Inst in = insts[idx];
   for (int n = threadIdx.x; n <= in.P; n += blockDim.x) {
     g[in.state_off + (int64_t)n * in.Nx] = 0.0;
-    g[in.state_off + (int64_t)n * in.Nx + in.Nx - 1] = bc_right(in, n);
+    g[in.state_off + (int64_t)n * in.Nx + in.Nx - 1] = bc_right(in, exptab + in.exp_sl, n);
   }
 }
 
@@ -1287,8 +1301,8 @@ cudaError_t launch_grid_points(const Inst* d_insts, int n_inst, int d_in, double
   return cudaGetLastError();
 }
 
-cudaError_t launch_table_fix(const Inst* d_insts, int n_inst, double* g, cudaStream_t s) {
-  table_fix_kernel<<<n_inst, 64, 0, s>>>(d_insts, n_inst, g);
+cudaError_t launch_table_fix(const Inst* d_insts, int n_inst, const double* exptab, double* g, cudaStream_t s) {
+  table_fix_kernel<<<n_inst, 64, 0, s>>>(d_insts, n_inst, exptab, g);
   return cudaGetLastError();
 }
 
