@@ -928,9 +928,29 @@ __global__ void __launch_bounds__(NW * 32, 1) sweep_kernel(SweepArgs a) {
     for (int j = g; j < Nx; j += C * T) Un[(int64_t)n0 * Nx + j] = Vs[j];
   }
   int seq = 0;
+  // few rows per thread: the rows' 1/sigma (constant over the slices) once, and
+  // each slice's F, old G and U^k before its step, so that no global load waits
+  // behind the step (more rows would not fit in registers)
+  constexpr bool kAhead = M <= 4;
+  double irow[kAhead ? M : 1];
+  if constexpr (kAhead) {
+#pragma unroll
+    for (int k = 0; k < M; ++k) irow[k] = (k < M - 1) ? cb[coef_rows_off(5, k, g, M, C * T)] : rg.isigp;
+  }
   for (int n = n0; n < in.P; ++n) {
     double Gv[M];
     double G0, GB;
+    double fa[kAhead ? M : 1], ga[kAhead ? M : 1], oa[kAhead ? M : 1];
+    if constexpr (kAhead) {
+#pragma unroll
+      for (int k = 0; k < M; ++k) {
+        const int j = g * M + k - in.Np + 1;
+        const bool in_row = j >= 1 && j <= Nx - 2;
+        fa[k] = (in_row && !init) ? Fv[(int64_t)n * Nx + j] : 0.0;
+        ga[k] = (in_row && !init) ? Gold[(int64_t)n * Nx + j] : 0.0;
+        oa[k] = (in_row && !init) ? Uc[(int64_t)(n + 1) * Nx + j] : 0.0;
+      }
+    }
     if (ie) {
       double W[M], x[M];
 #pragma unroll
@@ -942,7 +962,13 @@ __global__ void __launch_bounds__(NW * 32, 1) sweep_kernel(SweepArgs a) {
       }
       run_slice<M, NW, C, false>(in, in.K * __ldg(a.exptab + in.exp_sl + n), et, in.Mg, W, x, sm, rg, seq);
 #pragma unroll
-      for (int k = 0; k < M; ++k) Gv[k] = row_value<M, NW, C, false>(cb, k, W, x, rg.isigp);
+      for (int k = 0; k < M; ++k) {
+        if constexpr (kAhead) {
+          Gv[k] = W[k] * irow[k];
+        } else {
+          Gv[k] = row_value<M, NW, C, false>(cb, k, W, x, rg.isigp);
+        }
+      }
       G0 = 0.0;
       GB = bc_right(in, a.exptab + in.exp_sl, n + 1);
     } else {
@@ -963,12 +989,13 @@ __global__ void __launch_bounds__(NW * 32, 1) sweep_kernel(SweepArgs a) {
     for (int k = 0; k < M; ++k) {
       const int j = g * M + k - in.Np + 1;
       if (j >= 1 && j <= Nx - 2) {
-        const double v = init ? Gv[k] : fv[j] + (Gv[k] - go[j]);
+        const double fj = kAhead ? fa[k] : (init ? 0.0 : fv[j]), gj = kAhead ? ga[k] : (init ? 0.0 : go[j]);
+        const double v = init ? Gv[k] : fj + (Gv[k] - gj);
         go[j] = Gv[k];
         out[j] = v;
         V[k] = v;
         if (!init) {
-          const double d = v - old[j];
+          const double d = v - (kAhead ? oa[k] : old[j]);
           num = fma(d, d, num);
           den = fma(v, v, den);
         }
