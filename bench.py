@@ -45,7 +45,7 @@ FLOPS_PER_PT_STEP = 11.0  # CN right-hand side 5 + factored solve 6 (algorithmic
 # DRAM bytes (read + write) of one fine_propagate launch over the 32 slices of the
 # benchmark workload, from one ncu capture per partition (profiles/); a partition
 # without a capture of its current code reports null
-FINE_TRAFFIC_BYTES = {(2, 4, 4): 424960}
+FINE_TRAFFIC_BYTES = {(2, 4, 4): 425216}
 
 
 def _peaks():
