@@ -166,7 +166,7 @@ def test_training_reduces_loss_fp32(B, orc):
     assert last < 0.2 * first
 
 
-@pytest.mark.parametrize("w,n_hidden,d_in", [(32, 1, 2), (32, 3, 2), (64, 4, 2), (128, 6, 5), (256, 3, 2)])
+@pytest.mark.parametrize("w,n_hidden,d_in", [(32, 1, 2), (32, 3, 2), (64, 4, 2), (128, 6, 5), (256, 3, 2), (256, 2, 5)])
 @pytest.mark.parametrize("prec", [2, 3])
 def test_tensor_core_eval_shapes_and_ragged_tiles(B, orc, w, n_hidden, d_in, prec):
     # tiles of 128 points: 1, 127, 128, 129 and a few thousand points
