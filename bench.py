@@ -161,27 +161,29 @@ def rel_error(U, Uref, P, Nx):
     return float(((a - b).norm(dim=1) / b.norm(dim=1)).max().item())
 
 
-def train_network(B, torch, steps, seed=0, prec=None):
+def train_network(B, torch, steps, seed=0, prec=None, params=None):
     """The benchmark network: full-batch Adam on the collocation set, BF16 operands on
-    the tensor cores (FP32 accumulation, FP64 master weights) unless prec says otherwise."""
+    the tensor cores (FP32 accumulation, FP64 master weights) unless prec says otherwise;
+    params: the problem whose PDE the loss takes (default: the benchmark's)."""
     from paper_2303_03848_b300 import synth
 
     prec = B.BF16 if prec is None else prec
+    cfg = CFG if params is None else params
     X, kind = synth.collocation(seed, N_INTERIOR, N_BOUNDARY, N_EXPIRY, CFG["Smax"], CFG["T"])
     Xd = torch.tensor(X, device="cuda")
     kd = torch.tensor(kind, device="cuda")
     m = B.PinnModel(WIDTHS, [0.0, 0.0], [CFG["Smax"], CFG["T"]], seed=seed)
-    loss0 = m.train_step(Xd, kd, CFG, lr=1e-3, prec=prec, want_loss=True)
+    loss0 = m.train_step(Xd, kd, cfg, lr=1e-3, prec=prec, want_loss=True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     timed = min(200, max(steps - 1, 1))
     for i in range(1, steps):
         if i == steps - timed:
             e0.record()
-        m.train_step(Xd, kd, CFG, lr=1e-3, prec=prec)
+        m.train_step(Xd, kd, cfg, lr=1e-3, prec=prec)
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / timed if steps > 1 else float("nan")
-    loss1 = m.train_step(Xd, kd, CFG, lr=1e-3, prec=prec, want_loss=True)
+    loss1 = m.train_step(Xd, kd, cfg, lr=1e-3, prec=prec, want_loss=True)
     name = {B.FP64: "fp64", B.FP32: "fp32", B.BF16: "bf16 (tcgen05)"}[prec]
     return m, dict(steps=steps, precision=name, ms_per_step=ms, points=len(kind), loss_first=loss0,
                    loss_last=loss1, points_per_s=len(kind) / (ms * 1e-3) if ms == ms else None)
@@ -665,6 +667,39 @@ def train_leg(B, torch, n_points=65536, steps=20):
     return out
 
 
+def generalize_leg(B, torch, train_steps, sigmas=(0.2, 0.3, 0.4, 0.5), rs=(0.01, 0.03, 0.05),
+                   tols=(1e-2, 1e-3, 1e-4, 1e-6)):
+    """Parameter generalisation (the analogue of the paper's Fig. 4): the benchmark network
+    (2->4x64 on (S, tau)) trained at sigma = 0.4, r = 0.03 is the coarse propagator of
+    benchmark-grid instances at other (sigma, r).  Per instance: the network table's own
+    error against serial fine, and per tolerance the iterations and error of the
+    network-coarse and of the implicit-Euler-coarse solve."""
+    trained = dict(CFG, sigma=0.4, r=0.03)
+    model, tr = train_network(B, torch, train_steps, params=trained)
+    S = torch.linspace(0.0, CFG["Smax"], CFG["Nx"], dtype=torch.float64, device="cuda")
+    tau = torch.linspace(0.0, CFG["T"], CFG["P"] + 1, dtype=torch.float64, device="cuda")
+    Xg = torch.stack(torch.meshgrid(S, tau, indexing="xy"), dim=-1).reshape(-1, 2).contiguous()
+    table = model.eval(Xg, prec=B.BF16)
+    rows = []
+    for sigma in sigmas:
+        for r in rs:
+            cfg = dict(CFG, sigma=sigma, r=r)
+            prob = B.Problem(cfg)
+            Uf = prob.serial_fine()
+            row = {"sigma": sigma, "r": r, "table_err_vs_serial_fine": rel_error(table, Uf, CFG["P"], CFG["Nx"])}
+            for name, kind, mdl in (("pinn", B.COARSE_PINN, model), ("ie", B.COARSE_IE, None)):
+                row[name] = []
+                for tol in tols:
+                    U, _, stats, rc = prob.parareal_solve(kind, model=mdl, prec=B.BF16, tol=tol, max_iter=CFG["P"])
+                    row[name].append({"tol": tol, "iterations": stats[0]["iterations"],
+                                      "err_vs_serial_fine": rel_error(U, Uf, CFG["P"], CFG["Nx"]), "status": rc})
+            rows.append(row)
+            prob.close()
+    return {"mode": "generalize", "grid": "Nx=1024, S in [0,4], K=1 T=1, P=32, 1024 CN steps per slice",
+            "network": "2->4x64 tanh, BF16 table", "trained_at": {"sigma": 0.4, "r": 0.03}, "training": tr,
+            "rows": rows}
+
+
 def sweep_leg(B, torch, model, Ps=(4, 8, 16, 32, 64), total_steps=32768):
     """Speedup against P on one GPU next to the bound of Eq. 8 (the paper's Figs. 5-6):
     the benchmark grid with a fixed total of fine steps split over P slices; per P the
@@ -959,7 +994,8 @@ def main():
     ap.add_argument("--prec", default="bf16", choices=["fp64", "fp32", "tf32", "bf16"])
     ap.add_argument("--train-steps", type=int, default=5000)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
-    ap.add_argument("--mode", default="solve", choices=["solve", "fine", "batched", "large", "pinn", "train", "sweep"],
+    ap.add_argument("--mode", default="solve",
+                    choices=["solve", "fine", "batched", "large", "pinn", "train", "sweep", "generalize"],
                     help="fine / batched: only the fine propagator on all slices of the benchmark / "
                          "batched workload (profiling)")
     ap.add_argument("--batched", type=int, default=1, help="include the batched-workload leg (1/0)")
@@ -990,6 +1026,14 @@ def main():
         BUILD.build()
         model, _ = train_network(B, torch, args.train_steps)
         print(json.dumps(sweep_leg(B, torch, model)), flush=True)
+    elif args.mode == "generalize":
+        import torch
+
+        from paper_2303_03848_b300 import binding as B
+        from paper_2303_03848_b300 import build as BUILD
+
+        BUILD.build()
+        print(json.dumps(generalize_leg(B, torch, args.train_steps)), flush=True)
     elif args.mode == "train":
         import torch
 
