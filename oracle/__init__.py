@@ -88,6 +88,10 @@ def lib():
             ctypes.c_int, i32p, dp, dp, dp, dp, ctypes.POINTER(ctypes.c_int8), ctypes.c_int64,
             ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp,
         ]
+        L.orc_pinn_loss_grad_y.argtypes = [
+            ctypes.c_int, i32p, dp, dp, dp, dp, ctypes.POINTER(ctypes.c_int8), dp, ctypes.c_int64,
+            ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp,
+        ]
         L.orc_adam.argtypes = [ctypes.c_int64, dp, dp, dp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                ctypes.c_double, ctypes.c_double]
         _lib = L
@@ -241,15 +245,19 @@ def pinn_table(p: Params, m: MLP) -> np.ndarray:
 
 
 def pinn_loss_grad(m: MLP, X: np.ndarray, kind: np.ndarray, K: float, sigma: float, r: float, Smax: float,
-                   smax_over_K: float = 0.0, with_grad: bool = True):
-    """Loss terms (MSE_f, MSE_b, MSE_exp) of Eqs. 12-14 and, optionally, the gradient of Eq. 11."""
+                   smax_over_K: float = 0.0, with_grad: bool = True, y: np.ndarray | None = None):
+    """Loss terms (MSE_f, MSE_b, MSE_exp) of Eqs. 12-14 and, optionally, the gradient of Eq. 11.
+
+    y: values of the kind-4 data points (their squared misfit joins term 0)."""
     X = np.ascontiguousarray(X, dtype=np.float64)
     kind = np.ascontiguousarray(kind, dtype=np.int8)
+    yv = None if y is None else np.ascontiguousarray(y, dtype=np.float64)
     terms = np.empty(3)
     g = np.empty(m.params.size) if with_grad else None
-    rc = lib().orc_pinn_loss_grad(m.n_lin, m._w(), _dp(m.params), _dp(m.lo), _dp(m.hi), _dp(X),
-                                  kind.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)), X.shape[0], K, sigma, r, Smax,
-                                  smax_over_K, _dp(terms), _dp(g) if g is not None else None)
+    rc = lib().orc_pinn_loss_grad_y(m.n_lin, m._w(), _dp(m.params), _dp(m.lo), _dp(m.hi), _dp(X),
+                                    kind.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)),
+                                    _dp(yv) if yv is not None else None, X.shape[0], K, sigma, r, Smax,
+                                    smax_over_K, _dp(terms), _dp(g) if g is not None else None)
     if rc:
         raise MemoryError("oracle loss allocation failed")
     return (terms, g) if with_grad else terms

@@ -530,7 +530,10 @@ int orc_pinn_table(const orc_params* p, int n_lin, const int32_t* widths, const 
 
 /*
  * Collocation kinds: 0 interior (residual, Eq. 12), 1 boundary S = 0 and
- * 2 boundary S = Smax (Eq. 13, both in one mean), 3 expiry tau = 0 (Eq. 14).
+ * 2 boundary S = Smax (Eq. 13, both in one mean), 3 expiry tau = 0 (Eq. 14),
+ * 4 data point: squared misfit (u - y)^2 to a given value y, in the mean of
+ * term 0 (Section 4 trains a network on fine-propagator output alone, without
+ * the PDE terms, for comparison with the PINN).
  * Residual in tau: f = u_tau - 1/2 sigma^2 S^2 u_SS - r S u_S + r u (Eq. 1 with
  * dV/dt = -dV/dtau, sign flipped; |f|^2 is unchanged).  The sigma, r, K used in
  * the residual and targets are the ones given here (a parametric network also
@@ -562,9 +565,9 @@ static void point_targets(int kind, const double* x, int d_in, double K, double 
  * For a parametric net the Smax of the S = Smax points is K-relative:
  * Smax_i = smax_over_K * K_i when smax_over_K > 0, else Smax.
  */
-int orc_pinn_loss_grad(int n_lin, const int32_t* w, const double* params, const double* lo, const double* hi,
-                       const double* X, const int8_t* kind, int64_t N, double K, double sigma, double r, double Smax,
-                       double smax_over_K, double* terms, double* grad) {
+int orc_pinn_loss_grad_y(int n_lin, const int32_t* w, const double* params, const double* lo, const double* hi,
+                         const double* X, const int8_t* kind, const double* y, int64_t N, double K, double sigma,
+                         double r, double Smax, double smax_over_K, double* terms, double* grad) {
   int d_in = w[0];
   int mw = max_width(n_lin, w);
   int64_t np_ = n_params_of(n_lin, w);
@@ -588,7 +591,7 @@ int orc_pinn_loss_grad(int n_lin, const int32_t* w, const double* params, const 
   }
   int64_t cnt[3] = {0, 0, 0};
   for (int64_t k = 0; k < N; ++k) {
-    if (kind[k] == 0) cnt[0]++;
+    if (kind[k] == 0 || kind[k] == 4) cnt[0]++;
     else if (kind[k] == 1 || kind[k] == 2) cnt[1]++;
     else cnt[2]++;
   }
@@ -613,6 +616,10 @@ int orc_pinn_loss_grad(int n_lin, const int32_t* w, const double* params, const 
       gSS = -0.5 * si * si * S * S * gf;
       gS = -ri * S * gf;
       gu = ri * gf;
+    } else if (kind[k] == 4) {
+      double e = out[0] - (y ? y[k] : 0.0);
+      sums[0] += e * e;
+      gu = 2.0 * e / (double)cnt[0];
     } else {
       double e = out[0] - tgt;
       int t = (kind[k] == 3) ? 2 : 1;
@@ -723,6 +730,14 @@ int orc_pinn_loss_grad(int n_lin, const int32_t* w, const double* params, const 
   terms[2] = cnt[2] ? sums[2] / (double)cnt[2] : 0.0;
   free(buf); free(acts); free(adj); free(x0);
   return 0;
+}
+
+/* The PINN loss alone (no data points). */
+int orc_pinn_loss_grad(int n_lin, const int32_t* w, const double* params, const double* lo, const double* hi,
+                       const double* X, const int8_t* kind, int64_t N, double K, double sigma, double r, double Smax,
+                       double smax_over_K, double* terms, double* grad) {
+  return orc_pinn_loss_grad_y(n_lin, w, params, lo, hi, X, kind, NULL, N, K, sigma, r, Smax, smax_over_K, terms,
+                              grad);
 }
 
 /*

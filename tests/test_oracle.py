@@ -302,8 +302,9 @@ def test_pinn_table_boundary_nodes(orc):
         np.testing.assert_array_equal(g[n, 1:-1], orc.mlp_eval(m, X, False))
 
 
-def _torch_loss(widths, params, lo, hi, X, kind, K, sigma, r, Smax, smax_over_K=0.0):
-    """Eqs. 11-14 with PyTorch autograd (the paper's route), FP64."""
+def _torch_loss(widths, params, lo, hi, X, kind, K, sigma, r, Smax, smax_over_K=0.0, y=None):
+    """Eqs. 11-14 with PyTorch autograd (the paper's route), FP64; kind-4 points
+    (with values y) add their squared misfit to the mean of term 0."""
     x = torch.tensor(X, dtype=torch.float64, requires_grad=True)
     P = torch.tensor(params, dtype=torch.float64, requires_grad=True)
     lo_t = torch.tensor(lo, dtype=torch.float64)
@@ -336,7 +337,10 @@ def _torch_loss(widths, params, lo, hi, X, kind, K, sigma, r, Smax, smax_over_K=
     f = uT - 0.5 * sig ** 2 * S ** 2 * uSS - rr * S * uS + rr * u
     tgt = torch.where(kind == 1, torch.zeros_like(S),
                       torch.where(kind == 2, Sm - KK * torch.exp(-rr * tau), torch.clamp(S - KK, min=0.0)))
-    mf = (f[kind == 0] ** 2).mean()
+    r0 = f[kind == 0] ** 2
+    if y is not None:
+        r0 = torch.cat([r0, (u - torch.tensor(y, dtype=torch.float64))[kind == 4] ** 2])
+    mf = r0.mean()
     mb = ((u - tgt)[(kind == 1) | (kind == 2)] ** 2).mean()
     me = ((u - tgt)[kind == 3] ** 2).mean()
     total = mf + mb + me
@@ -354,6 +358,26 @@ def test_loss_and_gradient_match_autograd(orc):
     rt, rg = _torch_loss(widths, params, lo, hi, X, kind, 1.0, 0.2, 0.05, 4.0)
     np.testing.assert_allclose(terms, rt, rtol=1e-12)
     np.testing.assert_allclose(grad, rg, rtol=1e-10, atol=1e-13)
+
+
+def test_data_points_loss_and_gradient_match_autograd(orc):
+    # kind 4: squared misfit to a given value, in term 0 with the residual points
+    # (a mixed batch) or alone (a data-only batch, no PDE terms)
+    widths = [2, 12, 12, 1]
+    params = synth.xavier_params(widths, 19)
+    lo, hi = np.array([0.0, 0.0]), np.array([4.0, 1.0])
+    m = orc.MLP(widths, params, lo, hi)
+    X, kind = synth.collocation(23, 60, 16, 12, 4.0, 1.0)
+    rng = np.random.default_rng(5)
+    kind = kind.copy()
+    kind[rng.random(kind.size) < 0.3] = 4
+    y = rng.normal(size=kind.size)
+    for kk in (kind, np.full_like(kind, 4)):
+        terms, grad = orc.pinn_loss_grad(m, X, kk, 1.0, 0.2, 0.05, 4.0, y=y)
+        rt, rg = _torch_loss(widths, params, lo, hi, X, kk, 1.0, 0.2, 0.05, 4.0, y=y)
+        rt = np.nan_to_num(rt)  # an empty term's mean is NaN in torch, 0 in the oracle
+        np.testing.assert_allclose(terms, rt, rtol=1e-12)
+        np.testing.assert_allclose(grad, rg, rtol=1e-10, atol=1e-13)
 
 
 def test_parametric_loss_gradient_matches_autograd(orc):
