@@ -292,6 +292,25 @@ int pinn_train_step(pinn_model* m, const double* X, const int8_t* kind, int64_t 
                     double smax_over_K, int prec, double lr, double* loss3, double* grad_out, void* stream);
 
 /*
+ * pinn_loss_grad_data, pinn_train_step_data -- pinn_loss_grad and
+ * pinn_train_step with data points as well (Section 4: a network trained on
+ * fine-propagator output alone, without the PDE terms, compared with the PINN).
+ * kind 4 marks a data point; its squared misfit (u - y[i])^2 joins the mean of
+ * the first loss term, so loss3[0] is the mean over kind-0 residuals and kind-4
+ * misfits together (a batch of kind 4 only trains on data alone).
+ *   y: device [N] doubles, 8-byte aligned, non-null (read at kind-4 points
+ *   only).  Every other argument, the precisions and the tensor-core path are
+ *   those of pinn_loss_grad / pinn_train_step.  BS_EINVAL for a null or
+ *   misaligned y.
+ */
+int pinn_loss_grad_data(const pinn_model* m, const double* X, const int8_t* kind, const double* y, int64_t N,
+                        const bs_params* prob_params, double smax_over_K, int prec, double* loss3, double* grad,
+                        void* stream);
+int pinn_train_step_data(pinn_model* m, const double* X, const int8_t* kind, const double* y, int64_t N,
+                         const bs_params* prob_params, double smax_over_K, int prec, double lr, double* loss3,
+                         double* grad_out, void* stream);
+
+/*
  * parareal_solve -- Parareal (Eq. 7) on every instance:
  *   U^{k+1}_{n+1} = F(U^k_n) + (G(U^{k+1}_n) - G(U^k_n)),
  * with G chosen by coarse_kind (model required for the network kinds; the

@@ -94,6 +94,8 @@ def lib() -> ctypes.CDLL:
         L.pinn_device_status.argtypes = [vp, P(ctypes.c_int)]
         L.pinn_loss_grad.argtypes = [vp, vp, vp, i64, P(BsParams), dbl, ctypes.c_int, vp, vp, vp]
         L.pinn_train_step.argtypes = [vp, vp, vp, i64, P(BsParams), dbl, ctypes.c_int, dbl, P(dbl), vp, vp]
+        L.pinn_loss_grad_data.argtypes = [vp, vp, vp, vp, i64, P(BsParams), dbl, ctypes.c_int, vp, vp, vp]
+        L.pinn_train_step_data.argtypes = [vp, vp, vp, vp, i64, P(BsParams), dbl, ctypes.c_int, dbl, P(dbl), vp, vp]
         L.parareal_solve.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, dbl, i32, vp, P(dbl), P(InstanceStats), vp]
         _lib = L
         return L
@@ -550,23 +552,39 @@ class PinnModel:
                                _dev(d, torch.float64, "derivs") if d is not None else None, _stream()), "pinn_eval")
         return (u, d) if derivs else u
 
-    def loss_grad(self, X, kind, prob: dict, smax_over_K=0.0, prec=FP32):
+    def loss_grad(self, X, kind, prob: dict, smax_over_K=0.0, prec=FP32, y=None):
+        """Loss terms and gradient; y (device doubles): values of the kind-4 data points."""
         import torch
 
         loss3 = torch.empty(3, dtype=torch.float64, device=X.device)
         grad = torch.empty(self.n_params, dtype=torch.float64, device=X.device)
         pp = _to_struct(prob)
-        _check(lib().pinn_loss_grad(self._h, _dev(X, torch.float64, "X"), _dev(kind, torch.int8, "kind"), X.shape[0],
-                                    ctypes.byref(pp), smax_over_K, prec, _dev(loss3, torch.float64, "loss3"),
-                                    _dev(grad, torch.float64, "grad"), _stream()), "pinn_loss_grad")
+        if y is None:
+            _check(lib().pinn_loss_grad(self._h, _dev(X, torch.float64, "X"), _dev(kind, torch.int8, "kind"),
+                                        X.shape[0], ctypes.byref(pp), smax_over_K, prec,
+                                        _dev(loss3, torch.float64, "loss3"), _dev(grad, torch.float64, "grad"),
+                                        _stream()), "pinn_loss_grad")
+        else:
+            _check(lib().pinn_loss_grad_data(self._h, _dev(X, torch.float64, "X"), _dev(kind, torch.int8, "kind"),
+                                             _dev(y, torch.float64, "y"), X.shape[0], ctypes.byref(pp), smax_over_K,
+                                             prec, _dev(loss3, torch.float64, "loss3"),
+                                             _dev(grad, torch.float64, "grad"), _stream()), "pinn_loss_grad_data")
         return loss3, grad
 
-    def train_step(self, X, kind, prob: dict, lr=1e-3, smax_over_K=0.0, prec=FP32, want_loss=False, grad_out=None):
+    def train_step(self, X, kind, prob: dict, lr=1e-3, smax_over_K=0.0, prec=FP32, want_loss=False, grad_out=None,
+                   y=None):
+        """One Adam step on the loss; y (device doubles): values of the kind-4 data points."""
         import torch
 
         pp = _to_struct(prob)
         loss = (ctypes.c_double * 3)() if want_loss else None
         g = _dev(grad_out, torch.float64, "grad_out") if grad_out is not None else None
-        _check(lib().pinn_train_step(self._h, _dev(X, torch.float64, "X"), _dev(kind, torch.int8, "kind"), X.shape[0],
-                                     ctypes.byref(pp), smax_over_K, prec, lr, loss, g, _stream()), "pinn_train_step")
+        if y is None:
+            _check(lib().pinn_train_step(self._h, _dev(X, torch.float64, "X"), _dev(kind, torch.int8, "kind"),
+                                         X.shape[0], ctypes.byref(pp), smax_over_K, prec, lr, loss, g, _stream()),
+                   "pinn_train_step")
+        else:
+            _check(lib().pinn_train_step_data(self._h, _dev(X, torch.float64, "X"), _dev(kind, torch.int8, "kind"),
+                                              _dev(y, torch.float64, "y"), X.shape[0], ctypes.byref(pp), smax_over_K,
+                                              prec, lr, loss, g, _stream()), "pinn_train_step_data")
         return list(loss) if want_loss else None

@@ -735,11 +735,11 @@ int pinn_eval(const pinn_model* m, int prec, const double* X, int64_t N, double*
   return map_err(bsp::launch_mlp_eval(m->dev, prec, X, N, u, derivs, (cudaStream_t)stream));
 }
 
-static int loss_grad_common(const pinn_model* mc, const double* X, const int8_t* kind, int64_t N,
+static int loss_grad_common(const pinn_model* mc, const double* X, const int8_t* kind, const double* y, int64_t N,
                             const bs_params* pp, double smax_over_K, int prec, double* loss3, double* grad,
                             cudaStream_t s) {
   pinn_model* m = const_cast<pinn_model*>(mc);
-  if (!m || !X || !kind || !pp || N <= 0) return BS_EINVAL;
+  if (!m || !X || !kind || !pp || N <= 0 || ((uintptr_t)y & 7)) return BS_EINVAL;
   if (!(prec == BS_FP64 || prec == BS_FP32 || prec == BS_BF16)) return BS_EINVAL;
   if (((uintptr_t)X & 15) || ((uintptr_t)grad & 7) || ((uintptr_t)loss3 & 7) || !std::isfinite(pp->K) ||
       !std::isfinite(pp->sigma) || !std::isfinite(pp->r) || !std::isfinite(pp->Smax) || !std::isfinite(smax_over_K))
@@ -755,7 +755,7 @@ static int loss_grad_common(const pinn_model* mc, const double* X, const int8_t*
     if (e != cudaSuccess) return map_err(e);
     m->ws_bytes = need;
   }
-  bsp::LossArgs la{X, kind, N, pp->K, pp->sigma, pp->r, pp->Smax, smax_over_K, prec};
+  bsp::LossArgs la{X, kind, N, pp->K, pp->sigma, pp->r, pp->Smax, smax_over_K, prec, y};
   return map_err(bsp::launch_loss_grad(m->dev, la, loss3, grad, m->ws, m->ws_bytes, s));
 }
 
@@ -764,16 +764,24 @@ int pinn_loss_grad(const pinn_model* m, const double* X, const int8_t* kind, int
                    void* stream) {
   Range range_("pinn_loss_grad");
   if (!loss3 || !grad) return BS_EINVAL;
-  return loss_grad_common(m, X, kind, N, prob_params, smax_over_K, prec, loss3, grad, (cudaStream_t)stream);
+  return loss_grad_common(m, X, kind, nullptr, N, prob_params, smax_over_K, prec, loss3, grad, (cudaStream_t)stream);
 }
 
-int pinn_train_step(pinn_model* m, const double* X, const int8_t* kind, int64_t N, const bs_params* prob_params,
-                    double smax_over_K, int prec, double lr, double* loss3, double* grad_out, void* stream) {
-  Range range_("pinn_train_step");
+int pinn_loss_grad_data(const pinn_model* m, const double* X, const int8_t* kind, const double* y, int64_t N,
+                        const bs_params* prob_params, double smax_over_K, int prec, double* loss3, double* grad,
+                        void* stream) {
+  Range range_("pinn_loss_grad_data");
+  if (!loss3 || !grad || !y) return BS_EINVAL;
+  return loss_grad_common(m, X, kind, y, N, prob_params, smax_over_K, prec, loss3, grad, (cudaStream_t)stream);
+}
+
+static int train_step_common(pinn_model* m, const double* X, const int8_t* kind, const double* y, int64_t N,
+                             const bs_params* prob_params, double smax_over_K, int prec, double lr, double* loss3,
+                             double* grad_out, void* stream) {
   if (!m || !std::isfinite(lr) || lr <= 0.0) return BS_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   double* g = grad_out ? grad_out : m->grad;
-  int rc = loss_grad_common(m, X, kind, N, prob_params, smax_over_K, prec, m->loss3, g, s);
+  int rc = loss_grad_common(m, X, kind, y, N, prob_params, smax_over_K, prec, m->loss3, g, s);
   if (rc != BS_OK) return rc;
   m->step += 1;
   cudaError_t e = bsp::launch_adam(m->n_params, m->p64, m->mom1, m->mom2, g, m->step, lr, m->p32, s);
@@ -784,6 +792,20 @@ int pinn_train_step(pinn_model* m, const double* X, const int8_t* kind, int64_t 
     if (e != cudaSuccess) return map_err(e);
   }
   return BS_OK;
+}
+
+int pinn_train_step(pinn_model* m, const double* X, const int8_t* kind, int64_t N, const bs_params* prob_params,
+                    double smax_over_K, int prec, double lr, double* loss3, double* grad_out, void* stream) {
+  Range range_("pinn_train_step");
+  return train_step_common(m, X, kind, nullptr, N, prob_params, smax_over_K, prec, lr, loss3, grad_out, stream);
+}
+
+int pinn_train_step_data(pinn_model* m, const double* X, const int8_t* kind, const double* y, int64_t N,
+                         const bs_params* prob_params, double smax_over_K, int prec, double lr, double* loss3,
+                         double* grad_out, void* stream) {
+  Range range_("pinn_train_step_data");
+  if (!y) return BS_EINVAL;
+  return train_step_common(m, X, kind, y, N, prob_params, smax_over_K, prec, lr, loss3, grad_out, stream);
 }
 
 // ---------------------------------------------------------------------------

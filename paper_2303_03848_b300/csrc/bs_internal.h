@@ -107,6 +107,7 @@ struct LossArgs {
   int64_t N;
   double K, sigma, r, Smax, smax_over_K;
   int prec;
+  const double* y = nullptr;  // values of the kind-4 data points (null: 0)
 };
 cudaError_t launch_loss_grad(const MlpDev& m, const LossArgs& la, double* loss3, double* grad, void* workspace,
                              size_t ws_bytes, cudaStream_t s);

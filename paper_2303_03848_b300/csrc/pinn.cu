@@ -252,7 +252,7 @@ __global__ void count_kinds_kernel(const int8_t* __restrict__ kind, int64_t N, u
   unsigned long long c0 = 0, c1 = 0, c2 = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
     const int k = kind[i];
-    if (k == 0) ++c0;
+    if (k == 0 || k == 4) ++c0;
     else if (k == 1 || k == 2) ++c1;
     else ++c2;
   }
@@ -343,6 +343,10 @@ __global__ void train_fwd_kernel(MlpDev m, LossArgs la, TrainLayout TL, Tp* __re
       gSS = -0.5 * si * si * S * S * gf;
       gS = -ri * S * gf;
       gu = ri * gf;
+    } else if (kd == 4) {  // data point: misfit to its given value, in term 0
+      const double e = (double)out[0] - (la.y != nullptr ? la.y[p] : 0.0);
+      sq[0] = e * e;
+      gu = 2.0 * e / (double)cnt[0];
     } else {
       const double e = (double)out[0] - tgt;
       const int tt = (kd == 3) ? 2 : 1;

@@ -28,37 +28,14 @@ __device__ __forceinline__ void point_setup(const LossArgs& la, int d_in, const 
 }
 
 // Loss terms and adjoint seeds of one point from its output streams
-// (u, u_S, u_SS, u_tau): kind 0 interior (residual of Eq. 1 in tau), 1/2 the
-// S = 0 / S = Smax boundary (Eq. 13), 3 expiry (Eq. 14).  sq[term] receives the
-// squared error, g[4] = dLoss/d(u, u_S, u_SS, u_tau) with each term a mean
-// over its cnt points.
-__device__ __forceinline__ void point_loss(const LossArgs& la, int d_in, const double* x, int kd, const double (&out)[4],
-                                           const unsigned long long* cnt, double (&sq)[3], double (&g)[4]) {
-  double Ki, si, ri, tgt;
-  point_setup(la, d_in, x, kd, Ki, si, ri, tgt);
-  const double S = x[0];
-  g[0] = g[1] = g[2] = g[3] = 0.0;
-  if (kd == 0) {
-    const double f = out[3] - 0.5 * si * si * S * S * out[2] - ri * S * out[1] + ri * out[0];
-    sq[0] = f * f;
-    const double gf = 2.0 * f / (double)cnt[0];
-    g[3] = gf;
-    g[2] = -0.5 * si * si * S * S * gf;
-    g[1] = -ri * S * gf;
-    g[0] = ri * gf;
-  } else {
-    const double e = out[0] - tgt;
-    const int tt = (kd == 3) ? 2 : 1;
-    sq[tt] = e * e;
-    g[0] = 2.0 * e / (double)cnt[tt];
-  }
-}
-
-// The same terms and seeds in FP32, for the tensor-core training path: its
-// outputs come from BF16 GEMMs and its seeds are rounded to BF16, so FP32 (and
-// the FP32 exponential) carries no error that matters there, at a fraction of
-// the FP64 cost.  inv_cnt[term] = 1 / (points of that term).
-__device__ __forceinline__ void point_loss_f32(const LossArgs& la, int d_in, const float* x, int kd,
+// (u, u_S, u_SS, u_tau), in FP32 for the tensor-core training path (its outputs
+// come from BF16 GEMMs and its seeds are rounded to BF16, so FP32 and the FP32
+// exponential carry no error that matters there): kind 0 interior (residual of
+// Eq. 1 in tau), 1/2 the S = 0 / S = Smax boundary (Eq. 13), 3 expiry
+// (Eq. 14), 4 data point (misfit to its value yv, in term 0).  sq[term]
+// receives the squared error, g[4] = dLoss/d(u, u_S, u_SS, u_tau) with each
+// term a mean over its points; inv_cnt[term] = 1 / (points of that term).
+__device__ __forceinline__ void point_loss_f32(const LossArgs& la, int d_in, const float* x, int kd, float yv,
                                                const float (&out)[4], const float (&inv_cnt)[3], float (&sq)[3],
                                                float (&g)[4]) {
   float Ki = (float)la.K, si = (float)la.sigma, ri = (float)la.r;
@@ -78,6 +55,10 @@ __device__ __forceinline__ void point_loss_f32(const LossArgs& la, int d_in, con
     g[2] = -a * gf;
     g[1] = -b * gf;
     g[0] = ri * gf;
+  } else if (kd == 4) {
+    const float e = out[0] - yv;
+    sq[0] = e * e;
+    g[0] = 2.0f * e * inv_cnt[0];
   } else {
     float tgt = 0.0f;
     if (kd == 2) {

@@ -152,7 +152,7 @@ __device__ __forceinline__ uint4 pack8(const float* v) {
 // i, K = o) for the adjoint, BF16 core-matrix layout.
 // The step's prepass in one launch: pack W and W^T of the square layers,
 // zero the gradient (np entries) and count the points of each loss term into
-// cnt (zeroed by the caller; kind 0 interior, 1 and 2 boundary, 3 expiry).
+// cnt (zeroed by the caller; kinds 0 interior and 4 data, 1 and 2 boundary, 3 expiry).
 __global__ void train_prep_kernel(MlpDev m, int w, unsigned char* fwd, unsigned char* bwd, const int8_t* kind,
                                   int64_t N, unsigned long long* cnt, double* grad, int64_t np) {
   const int n_sq = m.n_lin - 2;
@@ -169,7 +169,7 @@ __global__ void train_prep_kernel(MlpDev m, int w, unsigned char* fwd, unsigned 
   unsigned long long c0 = 0, c1 = 0, c2 = 0;
   for (int64_t q = i0; q < N; q += stride) {
     const int k = kind[q];
-    if (k == 0) ++c0;
+    if (k == 0 || k == 4) ++c0;
     else if (k == 1 || k == 2) ++c1;
     else ++c2;
   }
@@ -534,8 +534,9 @@ __global__ void __launch_bounds__(train_threads(W), 1) train_tc_kernel(TrainArgs
         float gs[4], sqe[3] = {0.0f, 0.0f, 0.0f};
         const int kd = a.la.kind[p];
         const float icnt[3] = {s_icnt[0], s_icnt[1], s_icnt[2]};
-        point_loss_f32(a.la, DIN, xin, kd, out, icnt, sqe, gs);
-        term = kd == 0 ? 0 : (kd == 3 ? 2 : 1);
+        const float yv = (kd == 4 && a.la.y != nullptr) ? (float)a.la.y[p] : 0.0f;
+        point_loss_f32(a.la, DIN, xin, kd, yv, out, icnt, sqe, gs);
+        term = (kd == 0 || kd == 4) ? 0 : (kd == 3 ? 2 : 1);
         sqv = sqe[0] + sqe[1] + sqe[2];
 #pragma unroll
         for (int k = 0; k < 4; ++k) sd[k] = bf16r(gs[k]);
@@ -1001,6 +1002,7 @@ cudaError_t launch_train_tc(const MlpDev& m, const LossArgs& la, unsigned char* 
     LossArgs lc = la;
     lc.X = la.X + off * m.d_in;
     lc.kind = la.kind + off;
+    lc.y = la.y != nullptr ? la.y + off : nullptr;
     lc.N = la.N - off < chunk ? la.N - off : chunk;
     TcLayout Lc = L;
     Lc.nt = (int)((lc.N + 127) / 128);

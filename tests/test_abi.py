@@ -70,6 +70,10 @@ def test_null_arguments_rejected(L):
     assert L.bs_wait_probe(0, 0, ctypes.byref(s)) == B.BS_EINVAL  # limit out of range
     assert L.bs_wait_probe(0, 1 << 35, ctypes.byref(s)) == B.BS_EINVAL
     assert L.bs_wait_probe(0, 1000, None) == B.BS_EINVAL
+    pp = B.BsParams(1.0, 0.2, 0.05, 1.0, 4.0, 5, 1, 1, 1)
+    assert L.pinn_loss_grad_data(None, None, None, None, 1, ctypes.byref(pp), 0.0, 0, None, None, None) == B.BS_EINVAL
+    assert L.pinn_train_step_data(None, None, None, None, 1, ctypes.byref(pp), 0.0, 0, 1e-3, None, None,
+                                  None) == B.BS_EINVAL
     assert L.pinn_get_state(None, None, None, None, None) == B.BS_EINVAL
     assert L.pinn_set_state(None, None, None, None, 0) == B.BS_EINVAL
     L.bs_problem_destroy(None)

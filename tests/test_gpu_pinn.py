@@ -136,6 +136,60 @@ def test_loss_and_gradient_match_oracle(B, orc, arch, prec):
     assert _rel(g, grad) <= tol_g
 
 
+def _data_case(widths, seed, share=0.4):
+    # PINN collocation points with a share turned into kind-4 data points, values y
+    X, kind, prob, sok = _loss_case(widths, 1500, 128, 128, seed)
+    rng = np.random.default_rng(seed)
+    kind = kind.copy()
+    kind[rng.random(kind.size) < share] = 4
+    return X, kind, rng.normal(size=kind.size), prob, sok
+
+
+@pytest.mark.parametrize("arch", ["2-4x64", "2-6x128"])
+@pytest.mark.parametrize("prec", [0, 1, 3])
+def test_data_points_loss_and_gradient_match_oracle(B, orc, arch, prec):
+    # kind-4 data points (squared misfit to a given value, in the mean of term 0)
+    # among the PINN points, through pinn_loss_grad_data; the per-precision bounds
+    # of the PINN loss (BF16 runs on the tensor cores for both networks)
+    widths = ARCHS[arch]
+    m, om = _model(B, orc, widths, 8)
+    X, kind, y, prob, sok = _data_case(widths, 31)
+    terms, grad = orc.pinn_loss_grad(om, X, kind, prob["K"], prob["sigma"], prob["r"], prob["Smax"], sok, y=y)
+    l3, g = m.loss_grad(torch.tensor(X, device="cuda"), torch.tensor(kind, device="cuda"), prob, sok, prec=prec,
+                        y=torch.tensor(y, device="cuda"))
+    assert m.device_status() == B.BS_OK
+    l3, g = l3.cpu().numpy(), g.cpu().numpy()
+    tol_l, tol_g = {0: (1e-12, 1e-10), 1: (1e-4, 1e-4), 3: (5e-2, 1e-1)}[prec]
+    for c in range(3):
+        assert abs(l3[c] - terms[c]) <= tol_l * max(abs(terms[c]), 1e-300), (c, l3[c], terms[c])
+    assert _rel(g, grad) <= tol_g
+
+
+def test_data_only_tensor_core_gradient_every_layer_and_chunks(B, orc, monkeypatch):
+    # a batch of data points only (no PDE terms) on the tensor cores: every
+    # parameter block against the oracle (the per-block bound of the PINN
+    # tests), and chunks of 1024 points equal to one pass (the values follow
+    # their points into every chunk)
+    widths = ARCHS["2-6x128"]
+    m, om = _model(B, orc, widths, 45)
+    X, kind, y, prob, sok = _data_case(widths, 47, share=1.0)
+    Xd, kd, yd = (torch.tensor(v, device="cuda") for v in (X, kind, y))
+    monkeypatch.delenv("BSP_TRAIN_CHUNK", raising=False)
+    l_one, g_one = m.loss_grad(Xd, kd, prob, sok, prec=B.BF16, y=yd)
+    monkeypatch.setenv("BSP_TRAIN_CHUNK", "1024")
+    l_ch, g_ch = m.loss_grad(Xd, kd, prob, sok, prec=B.BF16, y=yd)
+    assert m.device_status() == B.BS_OK
+    l_one, g_one, l_ch, g_ch = (v.cpu().numpy() for v in (l_one, g_one, l_ch, g_ch))
+    np.testing.assert_allclose(l_ch, l_one, rtol=1e-12)
+    assert _rel(g_ch, g_one) <= 1e-5
+    terms, grad = orc.pinn_loss_grad(om, X, kind, prob["K"], prob["sigma"], prob["r"], prob["Smax"], sok, y=y)
+    assert terms[1] == 0.0 and terms[2] == 0.0 and l_one[1] == 0.0 and l_one[2] == 0.0
+    assert abs(l_one[0] - terms[0]) <= 5e-2 * terms[0]
+    for name, a, b in _param_blocks(widths):
+        err = np.abs(g_one[a:b] - grad[a:b]).max() / max(np.abs(grad[a:b]).max(), 1e-300)
+        assert err <= 2e-2, (name, err)
+
+
 def test_train_step_is_adam_on_the_gradient(B, orc):
     widths = ARCHS["2-4x64"]
     m, om = _model(B, orc, widths, 12)
