@@ -700,6 +700,42 @@ def generalize_leg(B, torch, train_steps, sigmas=(0.2, 0.3, 0.4, 0.5), rs=(0.01,
             "rows": rows}
 
 
+def data_coarse_leg(B, torch, train_steps, tols=(1e-2, 1e-3, 1e-4, 1e-6)):
+    """Data-only coarse network (Section 4 trains one on fine-propagator output,
+    without the PDE terms, next to the PINN): the benchmark network trained on
+    the serial fine solution at every grid point of the benchmark workload (kind-4
+    data points), against the PINN trained as usual; per coarse propagator the
+    table's error against serial fine and, per tolerance, iterations and error."""
+    prob = B.Problem(CFG)
+    Uf = prob.serial_fine()
+    S = torch.linspace(0.0, CFG["Smax"], CFG["Nx"], dtype=torch.float64, device="cuda")
+    tau = torch.linspace(0.0, CFG["T"], CFG["P"] + 1, dtype=torch.float64, device="cuda")
+    Xg = torch.stack(torch.meshgrid(S, tau, indexing="xy"), dim=-1).reshape(-1, 2).contiguous()
+    kd = torch.full((Xg.shape[0],), 4, dtype=torch.int8, device="cuda")
+    dnet = B.PinnModel(WIDTHS, [0.0, 0.0], [CFG["Smax"], CFG["T"]], seed=0)
+    loss0 = dnet.train_step(Xg, kd, CFG, lr=1e-3, prec=B.BF16, want_loss=True, y=Uf)
+    for _ in range(1, train_steps):
+        dnet.train_step(Xg, kd, CFG, lr=1e-3, prec=B.BF16, y=Uf)
+    loss1 = dnet.train_step(Xg, kd, CFG, lr=1e-3, prec=B.BF16, want_loss=True, y=Uf)
+    pinn, tr = train_network(B, torch, train_steps)
+    out = {"mode": "datacoarse", "grid": "Nx=1024, S in [0,4], K=1 sigma=0.2 r=0.05 T=1, P=32, 1024 CN steps per slice",
+           "network": "2->4x64 tanh, BF16 table",
+           "data_training": {"points": int(Xg.shape[0]), "steps": train_steps, "precision": "bf16 (tcgen05)",
+                             "data_mse_first": loss0[0], "data_mse_last": loss1[0]},
+           "pinn_training": tr, "coarse": {}}
+    for name, kind, mdl in (("data-nn", B.COARSE_PINN, dnet), ("pinn", B.COARSE_PINN, pinn), ("ie", B.COARSE_IE, None)):
+        row = {}
+        if mdl is not None:
+            row["table_err_vs_serial_fine"] = rel_error(mdl.eval(Xg, prec=B.BF16), Uf, CFG["P"], CFG["Nx"])
+        row["solves"] = []
+        for tol in tols:
+            U, _, stats, rc = prob.parareal_solve(kind, model=mdl, prec=B.BF16, tol=tol, max_iter=CFG["P"])
+            row["solves"].append({"tol": tol, "iterations": stats[0]["iterations"],
+                                  "err_vs_serial_fine": rel_error(U, Uf, CFG["P"], CFG["Nx"]), "status": rc})
+        out["coarse"][name] = row
+    return out
+
+
 def sweep_leg(B, torch, model, Ps=(4, 8, 16, 32, 64), total_steps=32768):
     """Speedup against P on one GPU next to the bound of Eq. 8 (the paper's Figs. 5-6):
     the benchmark grid with a fixed total of fine steps split over P slices; per P the
@@ -995,7 +1031,8 @@ def main():
     ap.add_argument("--train-steps", type=int, default=5000)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--mode", default="solve",
-                    choices=["solve", "fine", "batched", "large", "pinn", "train", "sweep", "generalize"],
+                    choices=["solve", "fine", "batched", "large", "pinn", "train", "sweep", "generalize",
+                             "datacoarse"],
                     help="fine / batched: only the fine propagator on all slices of the benchmark / "
                          "batched workload (profiling)")
     ap.add_argument("--batched", type=int, default=1, help="include the batched-workload leg (1/0)")
@@ -1034,6 +1071,14 @@ def main():
 
         BUILD.build()
         print(json.dumps(generalize_leg(B, torch, args.train_steps)), flush=True)
+    elif args.mode == "datacoarse":
+        import torch
+
+        from paper_2303_03848_b300 import binding as B
+        from paper_2303_03848_b300 import build as BUILD
+
+        BUILD.build()
+        print(json.dumps(data_coarse_leg(B, torch, args.train_steps)), flush=True)
     elif args.mode == "train":
         import torch
 
