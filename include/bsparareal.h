@@ -265,7 +265,8 @@ int pinn_eval(const pinn_model* m, int prec, const double* X, int64_t N, double*
  *             + MSE_b (Eq. 13) + MSE_exp (Eq. 14), each the mean over its points.
  *   X: device [N][d_in] doubles; kind: device [N] int8: 0 interior,
  *   1 boundary S = 0 (target 0), 2 boundary S = Smax (target Smax - K e^{-r tau}),
- *   3 expiry tau = 0 (target max(S - K, 0)).  prob_params (host): K, sigma, r,
+ *   3 expiry tau = 0 (target max(S - K, 0)); kind 4 (data point) belongs to
+ *   pinn_loss_grad_data, here its value is taken as 0.  prob_params (host): K, sigma, r,
  *   Smax of the loss (a 5-input network takes sigma, r, K per point from X;
  *   then Smax of kind-2 points is smax_over_K * K when smax_over_K > 0).
  *   prec: BS_FP64, BS_FP32, or BS_BF16 (BF16 operands, FP32 accumulation).
