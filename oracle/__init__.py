@@ -27,6 +27,7 @@ _lib = None
 COARSE_IE = 0
 COARSE_PINN = 1
 COARSE_PINN_INCR = 2
+COARSE_PINN_IE = 3
 
 
 class Params(ctypes.Structure):

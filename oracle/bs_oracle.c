@@ -249,7 +249,7 @@ int orc_serial_fine(const orc_params* p, double* U) {
 /* Parareal, Eq. 7 (Section 3.1).                                            */
 /* ------------------------------------------------------------------------ */
 
-enum { ORC_COARSE_IE = 0, ORC_COARSE_PINN = 1, ORC_COARSE_PINN_INCR = 2 };
+enum { ORC_COARSE_IE = 0, ORC_COARSE_PINN = 1, ORC_COARSE_PINN_INCR = 2, ORC_COARSE_PINN_IE = 3 };
 
 /*
  * The coarse propagator G over slice n applied to V.
@@ -257,6 +257,15 @@ enum { ORC_COARSE_IE = 0, ORC_COARSE_PINN = 1, ORC_COARSE_PINN_INCR = 2 };
  *   PINN:      the network's prediction at tau_{n+1} on the grid, g[n+1]
  *              (Section 3.3 trains V~(t, S) only, so G does not depend on V).
  *   PINN_INCR: V + g[n+1] - g[n] (a state-dependent use of the same network).
+ *   PINN_IE:   the network's prediction at tau_{n+1} plus the implicit Euler
+ *              response to the deviation of V from the network's value at
+ *              tau_n (Section 3.3 / Fig. 2: the network is given V at
+ *              t_start).  IE is affine, IE(V) = A^{-1}(V + boundary terms),
+ *              so g[n+1] + A^{-1}(V - g[n]) is written as
+ *                 IE(V) + (g[n+1] - IE(g[n]))
+ *              at the interior nodes; the Dirichlet nodes are IE's exact values.
+ *              When V = g[n] it returns g[n+1]: the network's own solution is a
+ *              trajectory of this G.
  * g holds (P+1) x Nx network values whose Dirichlet nodes already carry the
  * exact boundary values.
  */
@@ -270,6 +279,16 @@ static int coarse_apply(const orc_params* p, int kind, const double* g, int n, c
   if (kind == ORC_COARSE_PINN_INCR) {
     for (int j = 0; j < Nx; ++j) out[j] = V[j] + (g[(size_t)(n + 1) * Nx + j] - g[(size_t)n * Nx + j]);
     return 0;
+  }
+  if (kind == ORC_COARSE_PINN_IE) {
+    double* gie = (double*)malloc(sizeof(double) * (size_t)Nx);
+    if (!gie) return -1;
+    int rc = orc_coarse_ie(p, n, V, out);
+    if (rc == 0) rc = orc_coarse_ie(p, n, g + (size_t)n * Nx, gie);
+    if (rc == 0)
+      for (int j = 1; j <= Nx - 2; ++j) out[j] = out[j] + (g[(size_t)(n + 1) * Nx + j] - gie[j]);
+    free(gie);
+    return rc;
   }
   return -1;
 }

@@ -220,6 +220,114 @@ def test_parareal_pinn_kind_reduces_to_fine_shift(orc):
         np.testing.assert_array_equal(U1[n + 1], orc.fine(p, n, U0[n]))
 
 
+def _ie_parareal_by_hand(orc, p, iters):
+    """Eq. 7 composed from the oracle's F and IE propagators, k iterations."""
+    P = p.P
+    U = np.empty((P + 1, p.Nx))
+    U[0] = orc.payoff(p)
+    Gold = np.empty((P, p.Nx))
+    for n in range(P):
+        Gold[n] = orc.coarse_ie(p, n, U[n])
+        U[n + 1] = Gold[n]
+    for k in range(iters):
+        F = {n: orc.fine(p, n, U[n]) for n in range(k, P)}
+        Unew = U.copy()
+        for n in range(k, P):
+            Gnew = orc.coarse_ie(p, n, Unew[n])
+            Unew[n + 1] = F[n] + (Gnew - Gold[n])
+            Gold[n] = Gnew
+        U = Unew
+    return U
+
+
+def test_parareal_ie_iterations_compose_by_hand(orc):
+    # Eq. 7 with G = implicit Euler, one and two iterations, built by hand from
+    # the oracle's propagators: bitwise the oracle's Parareal
+    p = orc.params(Nx=40, P=5, fine_steps=6)
+    for iters in (1, 2):
+        U, norms, st = orc.parareal(p, orc.COARSE_IE, tol=0.0, max_iter=iters)
+        assert st == 1 and len(norms) == iters
+        np.testing.assert_array_equal(U, _ie_parareal_by_hand(orc, p, iters))
+
+
+def _smooth_table(orc, p, U, eps):
+    """U perturbed by eps x a smooth bump in S and tau, Dirichlet nodes exact."""
+    S = np.linspace(0.0, p.Smax, p.Nx)
+    g = U.copy()
+    for n in range(p.P + 1):
+        g[n] += eps * np.sin(np.pi * S / p.Smax) * (1.0 + n / p.P) * p.Smax
+        g[n, 0] = 0.0
+        g[n, -1] = orc.right_bc(p, p.T * n / p.P)
+    return g
+
+
+def test_parareal_network_ie_one_iteration_by_hand(orc):
+    # G(V) = IE(V) + (g_{n+1} - IE(g_n)) at the interior nodes, IE's Dirichlet
+    # values at the ends: the initial sweep and one iteration composed by hand
+    p = orc.params(Nx=40, P=5, fine_steps=6)
+    g = _smooth_table(orc, p, orc.serial_fine(p), 3e-2)
+
+    def G(n, V):
+        out = orc.coarse_ie(p, n, V)
+        gi = orc.coarse_ie(p, n, g[n])
+        out[1:-1] = out[1:-1] + (g[n + 1, 1:-1] - gi[1:-1])
+        return out
+
+    U = np.empty((p.P + 1, p.Nx))
+    U[0] = orc.payoff(p)
+    Gold = [None] * p.P
+    for n in range(p.P):
+        Gold[n] = G(n, U[n])
+        U[n + 1] = Gold[n]
+    Unew = U.copy()
+    for n in range(p.P):
+        Unew[n + 1] = orc.fine(p, n, U[n]) + (G(n, Unew[n]) - Gold[n])
+    U1, norms, st = orc.parareal(p, orc.COARSE_PINN_IE, g=g, tol=0.0, max_iter=1)
+    np.testing.assert_array_equal(U1, Unew)
+
+
+def test_parareal_network_ie_reduces_to_ie_on_the_ie_trajectory(orc):
+    # with the table equal to the implicit Euler trajectory from the payoff the
+    # correction g_{n+1} - IE(g_n) is exactly 0, so the kind is IE-coarse
+    # Parareal bit for bit, iteration by iteration
+    p = orc.params(Nx=64, P=6, fine_steps=16)
+    g = np.empty((p.P + 1, p.Nx))
+    g[0] = orc.payoff(p)
+    for n in range(p.P):
+        g[n + 1] = orc.coarse_ie(p, n, g[n])
+    for iters in (1, 3):
+        Ua, na, _ = orc.parareal(p, orc.COARSE_IE, tol=0.0, max_iter=iters)
+        Ub, nb, _ = orc.parareal(p, orc.COARSE_PINN_IE, g=g, tol=0.0, max_iter=iters)
+        np.testing.assert_array_equal(Ua, Ub)
+        np.testing.assert_array_equal(na, nb)
+
+
+def test_parareal_network_ie_invariants_and_convergence(orc):
+    p = orc.params(Nx=64, P=6, fine_steps=16)
+    Uf = orc.serial_fine(p)
+    # exact table: G(F-trajectory) reproduces it up to rounding, so the first
+    # increment is at rounding level
+    U, norms, st = orc.parareal(p, orc.COARSE_PINN_IE, g=Uf, tol=1e-13)
+    assert st == 0 and len(norms) == 1 and norms[0] < 1e-14
+    np.testing.assert_allclose(U, Uf, rtol=0, atol=1e-14)
+    # Section 3.1 invariants: slices 0..k exact after k iterations, k = P is serial fine
+    g = _smooth_table(orc, p, Uf, 1e-2)
+    for k in range(1, p.P + 1):
+        U, norms, st = orc.parareal(p, orc.COARSE_PINN_IE, g=g, tol=0.0, max_iter=k)
+        assert np.array_equal(U[: k + 1], Uf[: k + 1])
+    assert np.array_equal(U, Uf)
+    # the error recursion is IE-coarse Parareal's (the correction cancels in
+    # G_new - G_old), so a table closer to the fine solution than IE's own
+    # trajectory needs no more iterations than IE coarse
+    p1 = orc.params()
+    Uf1 = orc.serial_fine(p1)
+    _, n_ie, _ = orc.parareal(p1, orc.COARSE_IE, tol=1e-10)
+    for eps in (1e-3, 1e-5):
+        U, n_pi, st = orc.parareal(p1, orc.COARSE_PINN_IE, g=_smooth_table(orc, p1, Uf1, eps), tol=1e-10)
+        assert st == 0 and len(n_pi) <= len(n_ie)
+        assert orc.rel_error(p1, U, Uf1) < 1e-9
+
+
 def test_speedup_bound(orc):
     assert orc.speedup_bound(16, 3, 0.0) == pytest.approx(16.0 / 3.0, rel=1e-15)
     # eq. 8 with c_c = c_f and K = P gives 1 / (2 + 1) ... = 1/3
