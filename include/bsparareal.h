@@ -49,11 +49,23 @@ typedef enum {
   BS_EUNSUPPORTED = 7     /* size or mode outside what this build supports */
 } bs_status;
 
-/* Coarse propagator kinds for parareal_solve (Sections 3.1 and 3.3). */
+/*
+ * Coarse propagator kinds for parareal_solve (Sections 3.1 and 3.3).  g_n
+ * below is the network table u_theta(S_j, tau_n) with exact Dirichlet nodes.
+ * BS_COARSE_PINN_IE reads the network of Section 3.3 / Fig. 2 as a propagator
+ * that is given V at t_start: the network's own value at tau_{n+1} plus the
+ * implicit Euler response to the deviation of U_n from the network's value at
+ * tau_n.  Implicit Euler is affine, so this is IE(U_n) + (g_{n+1} - IE(g_n))
+ * at the interior nodes (IE's exact values at the Dirichlet nodes); the
+ * corrections g_{n+1} - IE(g_n) are formed once per solve for all slices at
+ * once, so each step of the serial sweep costs one IE step and one addition.
+ * G(g_n) = g_{n+1}: the network's solution is a trajectory of this G.
+ */
 typedef enum {
-  BS_COARSE_IE = 0,        /* implicit Euler, coarse_steps steps per slice (Section 3.2) */
-  BS_COARSE_PINN = 1,      /* G(U_n) = u_theta(S_j, tau_{n+1}), Dirichlet nodes exact */
-  BS_COARSE_PINN_INCR = 2  /* G(U_n) = U_n + u_theta(., tau_{n+1}) - u_theta(., tau_n) */
+  BS_COARSE_IE = 0,         /* implicit Euler, coarse_steps steps per slice (Section 3.2) */
+  BS_COARSE_PINN = 1,       /* G(U_n) = g_{n+1}, independent of U_n */
+  BS_COARSE_PINN_INCR = 2,  /* G(U_n) = U_n + g_{n+1} - g_n */
+  BS_COARSE_PINN_IE = 3     /* G(U_n) = g_{n+1} + IE response to (U_n - g_n) = IE(U_n) + g_{n+1} - IE(g_n) */
 } bs_coarse_kind;
 
 /* Arithmetic of the network evaluation.  Fine/coarse solves are always FP64. */

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libbsparareal.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "bsparareal.h")
 
 BS_OK, BS_EINVAL, BS_ECUDA, BS_ENOMEM, BS_NOT_CONVERGED, BS_DIVERGED, BS_TIMEOUT, BS_EUNSUPPORTED = range(8)
-COARSE_IE, COARSE_PINN, COARSE_PINN_INCR = 0, 1, 2
+COARSE_IE, COARSE_PINN, COARSE_PINN_INCR, COARSE_PINN_IE = 0, 1, 2, 3
 FP64, FP32, TF32, BF16 = 0, 1, 2, 3
 PREC = {"fp64": FP64, "fp32": FP32, "tf32": TF32, "bf16": BF16}
 

@@ -839,34 +839,81 @@ static cudaError_t ensure_parareal_ws(bs_problem* prob, int max_iter, int d_in) 
   return e;
 }
 
-int parareal_solve(bs_problem* prob, int coarse_kind, const pinn_model* model, int prec, double tol,
-                   int32_t max_iter, double* U_out, double* norms, bs_instance_stats* stats, void* stream) {
-  Range range_("parareal_solve");
+// Arguments common to both solve entry points (nothing launched on error).
+static int solve_args_ok(const bs_problem* prob, int coarse_kind, const pinn_model* model, int prec, double tol,
+                         int32_t max_iter, const double* U_out) {
   if (!prob || !U_out || ((uintptr_t)U_out & 15) || max_iter < 1 || !(tol >= 0.0)) return BS_EINVAL;
-  if (coarse_kind < BS_COARSE_IE || coarse_kind > BS_COARSE_PINN_INCR) return BS_EINVAL;
+  if (coarse_kind < BS_COARSE_IE || coarse_kind > BS_COARSE_PINN_IE) return BS_EINVAL;
   const bool pinn = coarse_kind != BS_COARSE_IE;
   if (pinn && !model) return BS_EINVAL;
   if (pinn && (prec < BS_FP64 || prec > BS_BF16)) return BS_EINVAL;
-  cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e = ensure_parareal_ws(prob, max_iter, pinn ? model->dev.d_in : 0);
-  if (e != cudaSuccess) return map_err(e);
+  return BS_OK;
+}
+
+// Device workspace of one solve: on the problem handle (parareal_solve) or in
+// the fixed array (parareal_solve_static).
+struct SolveWs {
+  double *buf0, *buf1;  // U^k / U^{k+1} ping-pong (state layout)
+  double* fbuf;         // F(U^k_n) (slice layout)
+  double* gold;         // G(U^k_n) (slice layout)
+  double* gtab;         // network table (state layout)
+  double* xg;           // grid points of the table, d_in per point
+  double* normbuf;      // increment-norm partial sums
+  bsp::Ctrl* ctrl;      // per-instance control words
+  double* norms;        // increment-norm history, n_inst x max_iter
+  bool clear_normbuf;   // zero the partial sums first (the array keeps the last call's)
+};
+
+// One Parareal solve (Eq. 7) of every instance of the problem, enqueued on s:
+//   a1 network table, a2 initial iterate, then per iteration a3 fine
+//   propagation (+ a5 fused for the state-independent network coarse), a4 + a5
+//   the serial coarse sweep with the correction, and the stop test; the stop
+//   rule is decided on the device, so the launch sequence is fixed.
+// hc: host space for n_inst control words when norms or stats are wanted.
+static int solve_impl(bs_problem* prob, int coarse_kind, const pinn_model* model, int prec, double tol,
+                      int32_t max_iter, double* U_out, double* norms, bs_instance_stats* stats, cudaStream_t s,
+                      const SolveWs& w, bsp::Ctrl* hc) {
+  const bool pinn = coarse_kind != BS_COARSE_IE;
   const int n = prob->n_inst;
+  cudaError_t e = cudaSuccess;
+  if (w.clear_normbuf &&
+      (e = cudaMemsetAsync(w.normbuf, 0, sizeof(double) * 2 * prob->total_norm, s)) != cudaSuccess)
+    return map_err(e);
   // a1: network table on (S_j, tau_n), Dirichlet nodes exact
   if (pinn) {
     Range r("network table");
     const int d_in = model->dev.d_in;
-    if ((e = bsp::launch_grid_points(prob->d_insts, n, d_in, prob->Xgrid, s)) != cudaSuccess) return map_err(e);
-    if ((e = bsp::launch_mlp_eval(model->dev, prec, prob->Xgrid, prob->total_state, prob->gtab, nullptr, s)) !=
-        cudaSuccess)
+    if ((e = bsp::launch_grid_points(prob->d_insts, n, d_in, w.xg, s)) != cudaSuccess) return map_err(e);
+    if ((e = bsp::launch_mlp_eval(model->dev, prec, w.xg, prob->total_state, w.gtab, nullptr, s)) != cudaSuccess)
       return map_err(e);
-    if ((e = bsp::launch_table_fix(prob->d_insts, n, prob->exptab, prob->gtab, s)) != cudaSuccess) return map_err(e);
+    if ((e = bsp::launch_table_fix(prob->d_insts, n, prob->exptab, w.gtab, s)) != cudaSuccess) return map_err(e);
+  }
+  // network-anchored IE: c_n = g_{n+1} - IE(g_n) for every slice at once (IE
+  // over all slices of the table into fbuf, which iteration 0 overwrites)
+  if (coarse_kind == BS_COARSE_PINN_IE) {
+    for (auto& c : prob->classes) {
+      bsp::PropArgs a{};
+      a.insts = prob->d_insts;
+      a.ids = c.d_ids;
+      a.pool = prob->pool;
+      a.exptab = prob->exptab;
+      a.in = w.gtab;
+      a.in_state = 1;
+      a.out = w.fbuf;
+      a.out_state = 0;
+      a.mode = bsp::PropArgs::kPlain;
+      a.k_iter = -1;
+      a.status = prob->d_status;
+      if ((e = bsp::launch_prop(c.M, c.NW, c.C, 1, false, a, (int)c.ids.size(), c.maxP, s)) != cudaSuccess)
+        return map_err(e);
+    }
+    if ((e = bsp::launch_table_correction(prob->d_insts, n, w.fbuf, w.gtab, s)) != cudaSuccess) return map_err(e);
   }
   // a2: initial iterate
-  if ((e = bsp::launch_parareal_init(prob->d_insts, n, prob->buf0, prob->buf1, prob->gtab,
-                                     coarse_kind == BS_COARSE_PINN, prob->ctrl, prob->norms_dev, max_iter, s)) !=
-      cudaSuccess)
+  if ((e = bsp::launch_parareal_init(prob->d_insts, n, w.buf0, w.buf1, w.gtab, coarse_kind == BS_COARSE_PINN, w.ctrl,
+                                     w.norms, max_iter, s)) != cudaSuccess)
     return map_err(e);
-  const int sweep_kind = coarse_kind == BS_COARSE_IE ? 0 : 1;
+  const int sweep_kind = coarse_kind == BS_COARSE_IE ? 0 : coarse_kind == BS_COARSE_PINN_INCR ? 1 : 2;
   auto sweep = [&](int k, double* cur, double* nxt) -> cudaError_t {
     for (auto& c : prob->classes) {
       bsp::SweepArgs a{};
@@ -876,13 +923,13 @@ int parareal_solve(bs_problem* prob, int coarse_kind, const pinn_model* model, i
       a.exptab = prob->exptab;
       a.kind = sweep_kind;
       a.k_iter = k;
-      a.ctrl = k < 0 ? nullptr : prob->ctrl;
+      a.ctrl = k < 0 ? nullptr : w.ctrl;
       a.ucur = cur;
       a.unext = nxt;
-      a.gold = prob->gold;
-      a.fbuf = prob->fbuf;
-      a.gtab = prob->gtab;
-      a.normbuf = prob->normbuf;
+      a.gold = w.gold;
+      a.fbuf = w.fbuf;
+      a.gtab = w.gtab;
+      a.normbuf = w.normbuf;
       a.status = prob->d_status;
       cudaError_t ee = bsp::launch_sweep(c.M, c.NW, c.C, a, (int)c.ids.size(), s);
       if (ee != cudaSuccess) return ee;
@@ -890,13 +937,13 @@ int parareal_solve(bs_problem* prob, int coarse_kind, const pinn_model* model, i
     return cudaSuccess;
   };
   if (coarse_kind != BS_COARSE_PINN) {
-    if ((e = sweep(-1, prob->buf0, prob->buf0)) != cudaSuccess) return map_err(e);
+    if ((e = sweep(-1, w.buf0, w.buf0)) != cudaSuccess) return map_err(e);
   }
   const int kmax = max_iter < prob->maxP ? max_iter : prob->maxP;
   for (int k = 0; k < kmax; ++k) {
     Range r("parareal iteration");
-    double* cur = (k & 1) ? prob->buf1 : prob->buf0;
-    double* nxt = (k & 1) ? prob->buf0 : prob->buf1;
+    double* cur = (k & 1) ? w.buf1 : w.buf0;
+    double* nxt = (k & 1) ? w.buf0 : w.buf1;
     // a3 (+ a5 fused for the state-independent network coarse propagator)
     for (auto& c : prob->classes) {
       bsp::PropArgs a{};
@@ -907,42 +954,40 @@ int parareal_solve(bs_problem* prob, int coarse_kind, const pinn_model* model, i
       a.in = cur;
       a.in_state = 1;
       a.k_iter = k;
-      a.ctrl = prob->ctrl;
+      a.ctrl = w.ctrl;
       a.status = prob->d_status;
       if (coarse_kind == BS_COARSE_PINN) {
         a.out = nxt;
         a.out_state = 1;
         a.mode = bsp::PropArgs::kPinnFused;
-        a.gtab = prob->gtab;
         a.uold = cur;
-        a.normbuf = prob->normbuf;
+        a.normbuf = w.normbuf;
       } else {
-        a.out = prob->fbuf;
+        a.out = w.fbuf;
         a.out_state = 0;
         a.mode = bsp::PropArgs::kPlain;
       }
-      if ((e = bsp::launch_prop(c.M, c.NW, c.C, c.s2, true, a, (int)c.ids.size(), c.maxP, s)) != cudaSuccess) return map_err(e);
+      if ((e = bsp::launch_prop(c.M, c.NW, c.C, c.s2, true, a, (int)c.ids.size(), c.maxP, s)) != cudaSuccess)
+        return map_err(e);
     }
     // a4 + a5: serial coarse sweep with the correction
     if (coarse_kind != BS_COARSE_PINN) {
       if ((e = sweep(k, cur, nxt)) != cudaSuccess) return map_err(e);
     }
-    if ((e = bsp::launch_parareal_finalize(prob->d_insts, n, prob->normbuf, k, tol, max_iter, prob->ctrl,
-                                           prob->norms_dev, s)) != cudaSuccess)
+    if ((e = bsp::launch_parareal_finalize(prob->d_insts, n, w.normbuf, k, tol, max_iter, w.ctrl, w.norms, s)) !=
+        cudaSuccess)
       return map_err(e);
   }
-  if ((e = bsp::launch_copy_result(prob->d_insts, n, prob->ctrl, prob->buf0, prob->buf1, U_out, s)) != cudaSuccess)
+  if ((e = bsp::launch_copy_result(prob->d_insts, n, w.ctrl, w.buf0, w.buf1, U_out, s)) != cudaSuccess)
     return map_err(e);
   if (!norms && !stats) return BS_OK;
-  std::vector<bsp::Ctrl> hc(n);
   int dev_status = 0;
-  if ((e = cudaMemcpyAsync(hc.data(), prob->ctrl, sizeof(bsp::Ctrl) * n, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+  if ((e = cudaMemcpyAsync(hc, w.ctrl, sizeof(bsp::Ctrl) * n, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
     return map_err(e);
   if ((e = cudaMemcpyAsync(&dev_status, prob->d_status, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
     return map_err(e);
-  if (norms &&
-      (e = cudaMemcpyAsync(norms, prob->norms_dev, sizeof(double) * (size_t)n * max_iter, cudaMemcpyDeviceToHost, s)) !=
-          cudaSuccess)
+  if (norms && (e = cudaMemcpyAsync(norms, w.norms, sizeof(double) * (size_t)n * max_iter, cudaMemcpyDeviceToHost,
+                                    s)) != cudaSuccess)
     return map_err(e);
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return map_err(e);
   int worst = BS_OK;
@@ -955,6 +1000,21 @@ int parareal_solve(bs_problem* prob, int coarse_kind, const pinn_model* model, i
     if (hc[i].status != BS_OK && (worst == BS_OK || hc[i].status == BS_DIVERGED)) worst = hc[i].status;
   }
   return dev_status != 0 ? BS_TIMEOUT : worst;
+}
+
+int parareal_solve(bs_problem* prob, int coarse_kind, const pinn_model* model, int prec, double tol,
+                   int32_t max_iter, double* U_out, double* norms, bs_instance_stats* stats, void* stream) {
+  Range range_("parareal_solve");
+  const int rc = solve_args_ok(prob, coarse_kind, model, prec, tol, max_iter, U_out);
+  if (rc != BS_OK) return rc;
+  const bool pinn = coarse_kind != BS_COARSE_IE;
+  cudaError_t e = ensure_parareal_ws(prob, max_iter, pinn ? model->dev.d_in : 0);
+  if (e != cudaSuccess) return map_err(e);
+  SolveWs w{prob->buf0, prob->buf1, prob->fbuf, prob->gold, prob->gtab, prob->Xgrid,
+            prob->normbuf, prob->ctrl, prob->norms_dev, false};
+  std::vector<bsp::Ctrl> hc(norms || stats ? prob->n_inst : 0);
+  return solve_impl(prob, coarse_kind, model, prec, tol, max_iter, U_out, norms, stats, (cudaStream_t)stream, w,
+                    hc.data());
 }
 
 }  // extern "C"
@@ -1015,11 +1075,9 @@ extern "C" int parareal_solve_static(bs_problem* prob, int coarse_kind, const pi
                                      double tol, int32_t max_iter, double* U_out, double* norms,
                                      bs_instance_stats* stats, void* stream) {
   Range range_("parareal_solve_static");
-  if (!prob || !U_out || ((uintptr_t)U_out & 15) || max_iter < 1 || !(tol >= 0.0)) return BS_EINVAL;
-  if (coarse_kind < BS_COARSE_IE || coarse_kind > BS_COARSE_PINN_INCR) return BS_EINVAL;
+  const int rc = solve_args_ok(prob, coarse_kind, model, prec, tol, max_iter, U_out);
+  if (rc != BS_OK) return rc;
   const bool pinn = coarse_kind != BS_COARSE_IE;
-  if (pinn && !model) return BS_EINVAL;
-  if (pinn && (prec < BS_FP64 || prec > BS_BF16)) return BS_EINVAL;
   const int n = prob->n_inst;
   if (n > kStaticMaxInstances) return BS_EUNSUPPORTED;
   const int d_in = pinn ? model->dev.d_in : 0;
@@ -1049,109 +1107,11 @@ extern "C" int parareal_solve_static(bs_problem* prob, int coarse_kind, const pi
   cudaError_t e = static_scratch_address(&base);
   if (e != cudaSuccess) return map_err(e);
   unsigned char* b = static_cast<unsigned char*>(base);
-  double* buf0 = reinterpret_cast<double*>(b + o_buf0);
-  double* buf1 = reinterpret_cast<double*>(b + o_buf1);
-  double* fbuf = reinterpret_cast<double*>(b + o_fbuf);
-  double* gold = reinterpret_cast<double*>(b + o_gold);
-  double* gtab = reinterpret_cast<double*>(b + o_gtab);
-  double* xg = reinterpret_cast<double*>(b + o_xg);
-  double* nb = reinterpret_cast<double*>(b + o_nb);
-  bsp::Ctrl* ctrl = reinterpret_cast<bsp::Ctrl*>(b + o_ctrl);
-  double* nrm = reinterpret_cast<double*>(b + o_norms);
-  cudaStream_t s = (cudaStream_t)stream;
-  // the previous call's partial sums must not leak into this one
-  if ((e = cudaMemsetAsync(nb, 0, sizeof(double) * 2 * prob->total_norm, s)) != cudaSuccess) return map_err(e);
-  if (pinn) {
-    if ((e = bsp::launch_grid_points(prob->d_insts, n, d_in, xg, s)) != cudaSuccess) return map_err(e);
-    if ((e = bsp::launch_mlp_eval(model->dev, prec, xg, prob->total_state, gtab, nullptr, s)) != cudaSuccess)
-      return map_err(e);
-    if ((e = bsp::launch_table_fix(prob->d_insts, n, prob->exptab, gtab, s)) != cudaSuccess) return map_err(e);
-  }
-  if ((e = bsp::launch_parareal_init(prob->d_insts, n, buf0, buf1, gtab, coarse_kind == BS_COARSE_PINN, ctrl, nrm,
-                                     max_iter, s)) != cudaSuccess)
-    return map_err(e);
-  const int sweep_kind = coarse_kind == BS_COARSE_IE ? 0 : 1;
-  auto sweep = [&](int k, double* cur, double* nxt) -> cudaError_t {
-    for (auto& c : prob->classes) {
-      bsp::SweepArgs a{};
-      a.insts = prob->d_insts;
-      a.ids = c.d_ids;
-      a.pool = prob->pool;
-      a.exptab = prob->exptab;
-      a.kind = sweep_kind;
-      a.k_iter = k;
-      a.ctrl = k < 0 ? nullptr : ctrl;
-      a.ucur = cur;
-      a.unext = nxt;
-      a.gold = gold;
-      a.fbuf = fbuf;
-      a.gtab = gtab;
-      a.normbuf = nb;
-      a.status = prob->d_status;
-      cudaError_t ee = bsp::launch_sweep(c.M, c.NW, c.C, a, (int)c.ids.size(), s);
-      if (ee != cudaSuccess) return ee;
-    }
-    return cudaSuccess;
-  };
-  if (coarse_kind != BS_COARSE_PINN) {
-    if ((e = sweep(-1, buf0, buf0)) != cudaSuccess) return map_err(e);
-  }
-  const int kmax = max_iter < prob->maxP ? max_iter : prob->maxP;
-  for (int k = 0; k < kmax; ++k) {
-    double* cur = (k & 1) ? buf1 : buf0;
-    double* nxt = (k & 1) ? buf0 : buf1;
-    for (auto& c : prob->classes) {
-      bsp::PropArgs a{};
-      a.insts = prob->d_insts;
-      a.ids = c.d_ids;
-      a.pool = prob->pool;
-      a.exptab = prob->exptab;
-      a.in = cur;
-      a.in_state = 1;
-      a.k_iter = k;
-      a.ctrl = ctrl;
-      a.status = prob->d_status;
-      if (coarse_kind == BS_COARSE_PINN) {
-        a.out = nxt;
-        a.out_state = 1;
-        a.mode = bsp::PropArgs::kPinnFused;
-        a.gtab = gtab;
-        a.uold = cur;
-        a.normbuf = nb;
-      } else {
-        a.out = fbuf;
-        a.out_state = 0;
-        a.mode = bsp::PropArgs::kPlain;
-      }
-      if ((e = bsp::launch_prop(c.M, c.NW, c.C, c.s2, true, a, (int)c.ids.size(), c.maxP, s)) != cudaSuccess) return map_err(e);
-    }
-    if (coarse_kind != BS_COARSE_PINN) {
-      if ((e = sweep(k, cur, nxt)) != cudaSuccess) return map_err(e);
-    }
-    if ((e = bsp::launch_parareal_finalize(prob->d_insts, n, nb, k, tol, max_iter, ctrl, nrm, s)) != cudaSuccess)
-      return map_err(e);
-  }
-  if ((e = bsp::launch_copy_result(prob->d_insts, n, ctrl, buf0, buf1, U_out, s)) != cudaSuccess) return map_err(e);
-  if (!norms && !stats) return BS_OK;
-  bsp::Ctrl hc[kStaticMaxInstances];
-  int dev_status = 0;
-  if ((e = cudaMemcpyAsync(hc, ctrl, sizeof(bsp::Ctrl) * n, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
-    return map_err(e);
-  if ((e = cudaMemcpyAsync(&dev_status, prob->d_status, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
-    return map_err(e);
-  if (norms &&
-      (e = cudaMemcpyAsync(norms, nrm, sizeof(double) * (size_t)n * max_iter, cudaMemcpyDeviceToHost, s)) !=
-          cudaSuccess)
-    return map_err(e);
-  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return map_err(e);
-  int worst = BS_OK;
-  for (int i = 0; i < n; ++i) {
-    if (stats) {
-      stats[i].iterations = hc[i].iterations;
-      stats[i].status = hc[i].status;
-      stats[i].final_norm = hc[i].last_norm;
-    }
-    if (hc[i].status != BS_OK && (worst == BS_OK || hc[i].status == BS_DIVERGED)) worst = hc[i].status;
-  }
-  return dev_status != 0 ? BS_TIMEOUT : worst;
+  SolveWs w{reinterpret_cast<double*>(b + o_buf0),  reinterpret_cast<double*>(b + o_buf1),
+            reinterpret_cast<double*>(b + o_fbuf),  reinterpret_cast<double*>(b + o_gold),
+            reinterpret_cast<double*>(b + o_gtab),  reinterpret_cast<double*>(b + o_xg),
+            reinterpret_cast<double*>(b + o_nb),    reinterpret_cast<bsp::Ctrl*>(b + o_ctrl),
+            reinterpret_cast<double*>(b + o_norms), true};
+  bsp::Ctrl hc[kStaticMaxInstances];  // host control words without a heap allocation
+  return solve_impl(prob, coarse_kind, model, prec, tol, max_iter, U_out, norms, stats, (cudaStream_t)stream, w, hc);
 }

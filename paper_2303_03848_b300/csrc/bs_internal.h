@@ -23,7 +23,6 @@ struct PropArgs {
   int k_iter;                // Parareal iteration, slices n < k_iter skipped (-1: none)
   const uint8_t* active;     // nullable, per (instance, slice)
   const Ctrl* ctrl;          // nullable, done flags
-  const double* gtab;        // kPinnFused: network table (state layout)
   const double* uold;        // kPinnFused: U^k (state layout)
   double* normbuf;           // kPinnFused: (num, den) per (instance, boundary index, cluster rank)
   int* status;               // nullable: BS_TIMEOUT recorded here if a bounded wait gave up
@@ -44,14 +43,14 @@ struct SweepArgs {
   const int32_t* ids;
   const double* pool;
   const double* exptab;
-  int kind;            // 0 implicit Euler, 1 network increment
+  int kind;            // 0 implicit Euler, 1 network increment, 2 network-anchored implicit Euler
   int k_iter;          // -1: initial sweep
   const Ctrl* ctrl;
   const double* ucur;  // U^k (state layout)
   double* unext;       // U^{k+1} (state layout)
   double* gold;        // G(U^k_n) per slice (slice layout), updated in place
   const double* fbuf;  // F(U^k_n) (slice layout)
-  const double* gtab;  // network table (state layout), increment kind
+  const double* gtab;  // network table (state layout), increment kind; corrections c_n, anchored kind
   double* normbuf;
   int* status;         // nullable: BS_TIMEOUT recorded here if a bounded wait gave up
 };
@@ -74,6 +73,8 @@ cudaError_t launch_copy_result(const Inst* d_insts, int n_inst, const Ctrl* ctrl
                                const double* buf1, double* out, cudaStream_t s);
 cudaError_t launch_grid_points(const Inst* d_insts, int n_inst, int d_in, double* X, cudaStream_t s);
 cudaError_t launch_table_fix(const Inst* d_insts, int n_inst, const double* exptab, double* g, cudaStream_t s);
+// Network-anchored IE: table slots 1..P become c_n = g_{n+1} - IE(g_n) (gie: IE(g_n), slice layout).
+cudaError_t launch_table_correction(const Inst* d_insts, int n_inst, const double* gie, double* g, cudaStream_t s);
 
 // ---- network (pinn.cu) ----
 struct MlpDev {

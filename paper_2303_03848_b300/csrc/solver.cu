@@ -779,15 +779,17 @@ __global__ void __launch_bounds__(S2 * NW * 32, 1) prop_kernel(PropArgs a) {
         if (last_thread) Vout[Nx - 1] = Bend;
       } else {
         // kPinnFused: U^{k+1}_{n+1} = F(U^k_n) + (G_new - G_old) with G = the network
-        // table at tau_{n+1} for both terms (Eq. 7); increment-norm partial sums.
-        const double* gg = a.gtab + in.state_off + (int64_t)(n + 1) * Nx;
+        // table at tau_{n+1} for both terms (Eq. 7), so G_new - G_old = 0 and the
+        // update is F itself; increment-norm partial sums.  A non-finite table
+        // value needs no check here: it is in U^0 (the initial iterate), so the
+        // first iteration's increment norm is not finite and the solve stops
+        // with BS_DIVERGED.
         const double* Uold = a.uold + in.state_off + (int64_t)(n + 1) * Nx;
 #pragma unroll
         for (int k = 0; k < M; ++k) {
           const int j = g * M + k - in.Np + 1;
           if (j >= 1 && j <= Nx - 2) {
-            const double f = row_value<M, NW, C, CN>(cb, k, W, x, rg.isigp);
-            const double v = f + (gg[j] - gg[j]);
+            const double v = row_value<M, NW, C, CN>(cb, k, W, x, rg.isigp);
             Vout[j] = v;
             const double d = v - Uold[j];
             num = fma(d, d, num);
@@ -795,14 +797,14 @@ __global__ void __launch_bounds__(S2 * NW * 32, 1) prop_kernel(PropArgs a) {
           }
         }
         if (first_thread) {
-          const double v = 0.0 + (gg[0] - gg[0]);
+          const double v = 0.0;
           Vout[0] = v;
           const double d = v - Uold[0];
           num = fma(d, d, num);
           den = fma(v, v, den);
         }
         if (last_thread) {
-          const double v = Bend + (gg[Nx - 1] - gg[Nx - 1]);
+          const double v = Bend;
           Vout[Nx - 1] = v;
           const double d = v - Uold[Nx - 1];
           num = fma(d, d, num);
@@ -885,7 +887,9 @@ __global__ void __launch_bounds__(NW * 32, 1) serial_fine_kernel(SerialArgs a) {
 // ---------------------------------------------------------------------------
 // Serial coarse sweep with the Parareal correction (Eq. 7), one cluster per
 // instance.  IE: G = coarse_steps implicit Euler steps.  Increment kind:
-// G(V) = V + g_{n+1} - g_n (elementwise).  k_iter < 0 is the initial sweep
+// G(V) = V + g_{n+1} - g_n (elementwise).  Network-anchored IE: G(V) = IE(V) +
+// c_n at the interior nodes, c_n = g_{n+1} - IE(g_n) stored in slot n+1 of the
+// table (table_correction_kernel).  k_iter < 0 is the initial sweep
 // U^0_{n+1} = G(U^0_n).
 // ---------------------------------------------------------------------------
 template <int M, int NW, int C>
@@ -900,7 +904,8 @@ __global__ void __launch_bounds__(NW * 32, 1) sweep_kernel(SweepArgs a) {
   const int g = c * T + t;
   const bool first_thread = c == 0 && t == 0;
   const bool last_thread = c == C - 1 && t == T - 1;
-  const bool ie = a.kind == 0;
+  const bool ie = a.kind != 1;     // kinds 0 and 2 take implicit Euler steps
+  const bool anchored = a.kind == 2;
   const double* cb = a.pool + in.coef_ie;
   const double* et = a.exptab + in.exp_ie;
   SolverRegs rg{};
@@ -940,7 +945,7 @@ __global__ void __launch_bounds__(NW * 32, 1) sweep_kernel(SweepArgs a) {
   for (int n = n0; n < in.P; ++n) {
     double Gv[M];
     double G0, GB;
-    double fa[kAhead ? M : 1], ga[kAhead ? M : 1], oa[kAhead ? M : 1];
+    double fa[kAhead ? M : 1], ga[kAhead ? M : 1], oa[kAhead ? M : 1], ca[kAhead ? M : 1];
     if constexpr (kAhead) {
 #pragma unroll
       for (int k = 0; k < M; ++k) {
@@ -949,6 +954,7 @@ __global__ void __launch_bounds__(NW * 32, 1) sweep_kernel(SweepArgs a) {
         fa[k] = (in_row && !init) ? Fv[(int64_t)n * Nx + j] : 0.0;
         ga[k] = (in_row && !init) ? Gold[(int64_t)n * Nx + j] : 0.0;
         oa[k] = (in_row && !init) ? Uc[(int64_t)(n + 1) * Nx + j] : 0.0;
+        ca[k] = (in_row && anchored) ? gt[(int64_t)(n + 1) * Nx + j] : 0.0;
       }
     }
     if (ie) {
@@ -967,6 +973,13 @@ __global__ void __launch_bounds__(NW * 32, 1) sweep_kernel(SweepArgs a) {
           Gv[k] = W[k] * irow[k];
         } else {
           Gv[k] = row_value<M, NW, C, false>(cb, k, W, x, rg.isigp);
+        }
+      }
+      if (anchored) {  // + c_n at the interior nodes; Dirichlet nodes stay IE's exact values
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+          const int j = g * M + k - in.Np + 1;
+          if (j >= 1 && j <= Nx - 2) Gv[k] = Gv[k] + (kAhead ? ca[k] : gt[(int64_t)(n + 1) * Nx + j]);
         }
       }
       G0 = 0.0;
@@ -1155,6 +1168,21 @@ __global__ void table_fix_kernel(const Inst* insts, int n_inst, const double* ex
   }
 }
 
+// Network-anchored IE coarse propagator: slot n+1 of the table becomes the
+// correction c_n = g_{n+1} - IE(g_n) at the interior nodes (0 at the Dirichlet
+// nodes); gie holds IE(g_n) for n = 0..P-1 in slice layout.  Slot 0 keeps g_0.
+__global__ void table_correction_kernel(const Inst* insts, int n_inst, const double* gie, double* g) {
+  const int idx = blockIdx.y;
+  if (idx >= n_inst) return;
+  const Inst in = insts[idx];
+  const int64_t sz = (int64_t)in.P * in.Nx;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < sz; i += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(i % in.Nx);
+    double* c = g + in.state_off + in.Nx + i;
+    *c = (j == 0 || j == in.Nx - 1) ? 0.0 : *c - gie[in.slice_off + i];
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Host-side dispatch over the (M, NW, C) partition classes.
 // ---------------------------------------------------------------------------
@@ -1330,6 +1358,11 @@ cudaError_t launch_grid_points(const Inst* d_insts, int n_inst, int d_in, double
 
 cudaError_t launch_table_fix(const Inst* d_insts, int n_inst, const double* exptab, double* g, cudaStream_t s) {
   table_fix_kernel<<<n_inst, 64, 0, s>>>(d_insts, n_inst, exptab, g);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_table_correction(const Inst* d_insts, int n_inst, const double* gie, double* g, cudaStream_t s) {
+  table_correction_kernel<<<dim3(16, n_inst), 256, 0, s>>>(d_insts, n_inst, gie, g);
   return cudaGetLastError();
 }
 

@@ -11,7 +11,10 @@ properties that hold at any size.
   autotuned partitions): one fine propagation of every slice of the batch,
   sampled (instance, slice) outputs against the oracle; the implicit-Euler-coarse
   solve of the whole batch to 1e-6, sampled instances against the oracle's
-  serial fine solution.
+  serial fine solution; the network-coarse solves (network-anchored IE to
+  1e-6, and three iterations of the state-independent kind) of the whole batch
+  with an FP64 table, one instance of every grid size against the oracle's
+  Parareal.
 * Large instance (Nx = 65536, P = 256, 4096 steps per slice, two slices per CTA
   on 16-CTA clusters): the first slice of GPU serial fine against the oracle;
   two implicit-Euler-coarse Parareal iterations leave the first three slices
@@ -107,6 +110,56 @@ def test_batched_workload_full_size_sampled_against_oracle(B, orc):
         o = prob.state_off[i]
         Ui = U[o:o + (p["P"] + 1) * p["Nx"]].cpu().numpy()
         assert orc.rel_error(op, Ui, orc.serial_fine(op)) <= 1e-6, (i, p["Nx"])
+
+
+def _one_per_grid_size(insts):
+    seen, picks = set(), []
+    for i, p in enumerate(insts):
+        if p["Nx"] not in seen:
+            seen.add(p["Nx"])
+            picks.append(i)
+    return picks
+
+
+def test_batched_network_coarse_full_size_sampled_against_oracle(B, orc):
+    # the batched workload's network-coarse solves, every instance in one call
+    # as bench.py runs them: a 5-input network on (S, tau, sigma, r, K) with an
+    # FP64 table, network-anchored IE and state-independent kinds to 1e-6; one
+    # instance of every grid size against the oracle's Parareal with the
+    # oracle's own table (same iteration count, iterate within the calibrated
+    # bound over the whole chain of fine steps)
+    from concurrent.futures import ThreadPoolExecutor
+
+    insts = synth.batched_instances(0, 4096, P=64, fine_steps=256, coarse_steps=1)
+    prob = B.Problem(insts, tuned=True)
+    widths = [5, 32, 32, 1]
+    lo, hi = [0.0, 0.0, 0.1, 0.0, 0.5], [8.0, 2.0, 0.5, 0.08, 2.0]
+    w = synth.xavier_params(widths, 11)
+    net = B.PinnModel(widths, lo, hi, seed=11)
+    net.set_weights(w)
+    om = orc.MLP(widths, w, lo, hi)
+    picks = _one_per_grid_size(insts)
+    assert len(picks) == 5
+
+    def oracle_solve(i, kind, max_iter):
+        op = orc.params(**insts[i])
+        return orc.parareal(op, kind, g=orc.pinn_table(op, om), tol=1e-6, max_iter=max_iter)
+
+    for k_gpu, k_or, max_iter in ((B.COARSE_PINN_IE, orc.COARSE_PINN_IE, 64), (B.COARSE_PINN, orc.COARSE_PINN, 3)):
+        U, norms, stats, rc = prob.parareal_solve(k_gpu, model=net, prec=B.FP64, tol=1e-6, max_iter=max_iter)
+        torch.cuda.synchronize()
+        assert prob.device_status() == B.BS_OK
+        if k_gpu == B.COARSE_PINN_IE:
+            assert rc == B.BS_OK and all(st["status"] == B.BS_OK for st in stats)
+        with ThreadPoolExecutor(len(picks)) as ex:
+            refs = list(ex.map(lambda i: oracle_solve(i, k_or, max_iter), picks))
+        for i, (Ur, nr, st) in zip(picks, refs):
+            p = insts[i]
+            assert stats[i]["iterations"] == len(nr), (i, p["Nx"], stats[i], len(nr))
+            np.testing.assert_allclose(norms[i, :len(nr)], nr, rtol=1e-6)
+            o = prob.state_off[i]
+            got = U[o:o + (p["P"] + 1) * p["Nx"]].cpu().numpy()
+            assert _rel(got, Ur.ravel()) <= _kappa_tol(p, p["P"] * p["fine_steps"]), (i, p["Nx"])
 
 
 def test_large_instance_full_size(B, orc):

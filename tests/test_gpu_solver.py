@@ -184,12 +184,15 @@ def _random_net(B, orc, widths, seed, lo, hi):
     return m, orc.MLP(widths, w, lo, hi)
 
 
-@pytest.mark.parametrize("kind", ["pinn", "pinn_incr"])
+_KINDS = {"pinn": ("COARSE_PINN", "COARSE_PINN"), "pinn_incr": ("COARSE_PINN_INCR", "COARSE_PINN_INCR"),
+          "pinn_ie": ("COARSE_PINN_IE", "COARSE_PINN_IE")}
+
+
+@pytest.mark.parametrize("kind", ["pinn", "pinn_incr", "pinn_ie"])
 def test_parareal_network_coarse_matches_oracle(B, orc, kind):
     cfg = dict(_cfg1(), Nx=200, P=6, fine_steps=32)
     m, om = _random_net(B, orc, [2, 16, 16, 1], 3, [0.0, 0.0], [cfg["Smax"], cfg["T"]])
-    k_gpu = B.COARSE_PINN if kind == "pinn" else B.COARSE_PINN_INCR
-    k_or = orc.COARSE_PINN if kind == "pinn" else orc.COARSE_PINN_INCR
+    k_gpu, k_or = getattr(B, _KINDS[kind][0]), getattr(orc, _KINDS[kind][1])
     prob = B.Problem(cfg)
     U, norms, stats, rc = prob.parareal_solve(k_gpu, model=m, prec=B.FP64, tol=1e-9)
     op = _oparams(orc, cfg)
@@ -215,9 +218,52 @@ def test_batched_parareal_matches_oracle_per_instance(B, orc):
                _kappa_tol(p, "fine", chain_slices=p["P"]))
 
 
+@pytest.mark.parametrize("kind", ["pinn", "pinn_ie"])
+def test_batched_network_coarse_matches_oracle_per_instance(B, orc, kind):
+    # mixed grid sizes and partition classes, a 5-input network on (S, tau,
+    # sigma, r, K) with an FP64 table, several coarse steps per slice
+    insts = synth.batched_instances(9, 6, P=5, fine_steps=24, coarse_steps=2, Nx_choices=(65, 256, 300, 1024))
+    lo, hi = [0.0, 0.0, 0.1, 0.0, 0.5], [8.0, 2.0, 0.5, 0.08, 2.0]
+    m, om = _random_net(B, orc, [5, 16, 16, 1], 4, lo, hi)
+    k_gpu, k_or = getattr(B, _KINDS[kind][0]), getattr(orc, _KINDS[kind][1])
+    prob = B.Problem(insts)
+    U, norms, stats, rc = prob.parareal_solve(k_gpu, model=m, prec=B.FP64, tol=1e-9)
+    U = U.cpu().numpy()
+    for i, p in enumerate(insts):
+        op = _oparams(orc, p)
+        Ur, nr, st = orc.parareal(op, k_or, g=orc.pinn_table(op, om), tol=1e-9)
+        assert stats[i]["iterations"] == len(nr), (i, stats[i], len(nr))
+        np.testing.assert_allclose(norms[i, :len(nr)], nr, rtol=1e-6)
+        _close(U[prob.state_off[i]:prob.state_off[i] + (p["P"] + 1) * p["Nx"]], Ur.ravel(),
+               _kappa_tol(p, "fine", chain_slices=p["P"]))
+
+
+def test_network_ie_coarse_invariants_with_a_zero_network(B, orc):
+    # all weights 0: the table is 0 inside with exact Dirichlet nodes, so G is
+    # IE plus a fixed shift that is far from the solution.  Section 3.1: k = P
+    # iterations give GPU serial fine bit for bit; at tol 1e-10 the iteration
+    # count and the iterate match the oracle's
+    cfg = dict(_cfg1(), Nx=256, P=8, fine_steps=64)
+    m = B.PinnModel([2, 8, 1], [0.0, 0.0], [cfg["Smax"], cfg["T"]], seed=1)
+    m.set_weights(np.zeros(m.n_params))
+    prob = B.Problem(cfg)
+    Uf = prob.serial_fine()
+    U, norms, stats, rc = prob.parareal_solve(B.COARSE_PINN_IE, model=m, prec=B.FP64, tol=0.0)
+    assert stats[0]["iterations"] == cfg["P"]
+    assert torch.equal(U, Uf)
+    Ur, nr, st = orc.parareal(_oparams(orc, cfg), orc.COARSE_PINN_IE,
+                              g=orc.pinn_table(_oparams(orc, cfg), orc.MLP([2, 8, 1], np.zeros(m.n_params),
+                                                                           [0.0, 0.0], [cfg["Smax"], cfg["T"]])),
+                              tol=1e-10)
+    U2, n2, s2, rc2 = prob.parareal_solve(B.COARSE_PINN_IE, model=m, prec=B.FP64, tol=1e-10)
+    assert s2[0]["iterations"] == len(nr)
+    _close(U2.cpu().numpy(), Ur.ravel())
+
+
 def test_non_finite_network_reports_diverged(B, orc):
     # fault injected from the host: output weights so large that the network
-    # table overflows to inf, so G_new - G_old = inf - inf = NaN reaches the norm
+    # table overflows to inf; the table is the initial iterate, so the first
+    # increment norm is not finite
     cfg = dict(_cfg1(), Nx=65, P=4, fine_steps=4)
     widths = [2, 4, 1]
     m = B.PinnModel(widths, [0.0, 0.0], [4.0, 1.0], seed=1)
