@@ -49,7 +49,7 @@ def _rel(a, b):
     return np.abs(a - b).max() / np.abs(b).max()
 
 
-@pytest.mark.parametrize("kind", ["ie", "pinn", "pinn_incr"])
+@pytest.mark.parametrize("kind", ["ie", "pinn", "pinn_incr", "pinn_ie"])
 def test_static_solve_matches_parareal_solve_twice(B, kind):
     from paper_2303_03848_b300 import synth
 
@@ -57,7 +57,7 @@ def test_static_solve_matches_parareal_solve_twice(B, kind):
              dict(K=1.3, sigma=0.3, r=0.02, T=1.5, Smax=5.2, Nx=300, P=6, fine_steps=40, coarse_steps=2)]
     prob = B.Problem(insts)
     model = None
-    k = {"ie": B.COARSE_IE, "pinn": B.COARSE_PINN, "pinn_incr": B.COARSE_PINN_INCR}[kind]
+    k = {"ie": B.COARSE_IE, "pinn": B.COARSE_PINN, "pinn_incr": B.COARSE_PINN_INCR, "pinn_ie": B.COARSE_PINN_IE}[kind]
     if kind != "ie":
         widths = [2, 32, 32, 1]
         model = B.PinnModel(widths, [0.0, 0.0], [5.2, 1.5], seed=4)
