@@ -263,10 +263,11 @@ int pinn_device_status(const pinn_model* m, int* status);
  *   differentiation through every layer (the paper uses automatic
  *   differentiation).  prec selects the arithmetic of the layers: FP64, FP32,
  *   TF32 or BF16 (reduced precisions accumulate in FP32); outputs are FP64.
- *   BF16 runs the hidden layers on the tensor cores (tcgen05, FP32
+ *   BF16 runs the hidden layers on the tensor cores (tcgen05 kind::f16, FP32
  *   accumulation in tensor memory) when every hidden layer is w x w with w a
- *   multiple of 32 up to 256; TF32 and other shapes round the operands on
- *   CUDA cores.
+ *   multiple of 32 up to 256; TF32 likewise (kind::tf32, operands rounded to
+ *   TF32 with round-to-nearest) for w up to 128; other shapes round the
+ *   operands on CUDA cores.
  *   derivs requires FP64 or FP32.
  */
 int pinn_eval(const pinn_model* m, int prec, const double* X, int64_t N, double* u, double* derivs, void* stream);

@@ -90,12 +90,13 @@ struct MlpDev {
   int* status;               // device status word: BS_TIMEOUT if a bounded wait gave up
 };
 
-// Tensor-core evaluation (pinn_tc.cu): hidden layers w x w on tcgen05, BF16.
+// Tensor-core evaluation (pinn_tc.cu): hidden layers w x w on tcgen05, BF16
+// or TF32 operands (tf32), FP32 accumulation.
 bool tc_supported(const MlpDev& m);
-bool tc_fits(const MlpDev& m);
+bool tc_fits(const MlpDev& m, bool tf32);
 size_t tc_packed_bytes(const MlpDev& m);
 cudaError_t launch_mlp_eval_tc(const MlpDev& m, unsigned char* packed, const double* X, int64_t N, double* u,
-                               int* status, cudaStream_t s);
+                               int* status, cudaStream_t s, bool tf32);
 
 cudaError_t launch_mlp_eval(const MlpDev& m, int prec, const double* X, int64_t N, double* u, double* derivs,
                             cudaStream_t s);

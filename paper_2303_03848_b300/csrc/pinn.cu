@@ -175,9 +175,10 @@ cudaError_t launch_mlp_eval(const MlpDev& m, int prec, const double* X, int64_t 
     case 1:
       return d ? eval_launch<float, 0, 4>(m, X, N, u, derivs, s) : eval_launch<float, 0, 1>(m, X, N, u, nullptr, s);
     case 2:
+      if (tc_fits(m, true)) return launch_mlp_eval_tc(m, m.tc_packed, X, N, u, m.status, s, true);
       return eval_launch<float, 1, 1>(m, X, N, u, nullptr, s);
     case 3:
-      if (tc_fits(m)) return launch_mlp_eval_tc(m, m.tc_packed, X, N, u, m.status, s);
+      if (tc_fits(m, false)) return launch_mlp_eval_tc(m, m.tc_packed, X, N, u, m.status, s, false);
       return eval_launch<float, 2, 1>(m, X, N, u, nullptr, s);
   }
   return cudaErrorInvalidValue;

@@ -1,6 +1,7 @@
 // pinn_tc.cu -- network evaluation (Section 3.3) with the hidden w x w layers
-// on the 5th-generation tensor cores (tcgen05), BF16 operands, FP32
-// accumulation in tensor memory.
+// on the 5th-generation tensor cores (tcgen05), BF16 operands (kind::f16) or
+// TF32 operands (kind::tf32, FP32 values rounded to TF32), FP32 accumulation
+// in tensor memory.
 //
 // One CTA owns a tile of 128 points at a time (the M = 128 rows of every layer
 // GEMM) and walks the tiles persistently.  Its warps v, v + 4, ... read the
@@ -9,12 +10,12 @@
 // threads) up to w = 128, four (512 threads) at w = 256, where the tensor
 // memory holds only two CTAs per SM.  Per tile:
 //   * input layer (2 or 5 inputs -> w): CUDA cores, FP32, written as the BF16
-//     A operand of the first square layer;
-//   * each square layer h' = tanh(W h + b): one thread issues w/16 tcgen05.mma
-//     (M = 128, N = w, K = 16) into a TMEM accumulator and commits them to an
-//     mbarrier; the warps read their 32 lanes back with tcgen05.ld, add
-//     the bias, apply FP32 tanh and write the BF16-rounded result as the next
-//     A operand;
+//     (TF32) A operand of the first square layer;
+//   * each square layer h' = tanh(W h + b): one thread issues w/16 (TF32:
+//     w/8) tcgen05.mma (M = 128, N = w, K = 16 or 8: 32 bytes of each operand
+//     row) into a TMEM accumulator and commits them to an mbarrier; the warps
+//     read their 32 lanes back with tcgen05.ld, add the bias, apply FP32 tanh
+//     and write the rounded result as the next A operand;
 //   * output layer (w -> 1): FP32 tanh of the last hidden layer and a dot
 //     product on CUDA cores, the column groups' parts added through shared
 //     memory.
@@ -40,8 +41,10 @@ namespace bsp {
 using namespace tc;
 
 // Pack the square layers W_l (l = 2 .. n_lin-1, each w x w) from the FP32
-// copy into the core-matrix layout, BF16.
+// copy into the core-matrix layout, BF16 or TF32 (rounded with cvt.rna).
+template <bool TF>
 __global__ void pack_square_kernel(MlpDev m, int w, unsigned char* out) {
+  constexpr int EB = TF ? 4 : 2;
   const int n_sq = m.n_lin - 2;
   const int64_t per = (int64_t)w * w;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < per * n_sq;
@@ -49,7 +52,38 @@ __global__ void pack_square_kernel(MlpDev m, int w, unsigned char* out) {
     const int s = (int)(i / per);
     const int n = (int)((i % per) / w), k = (int)(i % w);
     const float v = m.p32[m.poff[s + 2] + (int64_t)n * w + k];
-    *reinterpret_cast<__nv_bfloat16*>(out + s * per * 2 + canon_off(n, k, w)) = __float2bfloat16_rn(v);
+    unsigned char* dst = out + s * per * EB + canon_off_eb<EB>(n, k, w);
+    if constexpr (TF) {
+      *reinterpret_cast<uint32_t*>(dst) = to_tf32(v);
+    } else {
+      *reinterpret_cast<__nv_bfloat16*>(dst) = __float2bfloat16_rn(v);
+    }
+  }
+}
+
+// Eight FP32 values (columns c .. c + 7 of one operand row) through tanh,
+// rounded to the operand type and stored at their core-matrix positions.
+template <bool TF>
+__device__ __forceinline__ void store_tanh8(unsigned char* sA, int row, int c, int w, const float (&v)[8]) {
+  if constexpr (TF) {
+    uint4 q0, q1;
+    q0.x = to_tf32(tanh_fast(v[0]));
+    q0.y = to_tf32(tanh_fast(v[1]));
+    q0.z = to_tf32(tanh_fast(v[2]));
+    q0.w = to_tf32(tanh_fast(v[3]));
+    q1.x = to_tf32(tanh_fast(v[4]));
+    q1.y = to_tf32(tanh_fast(v[5]));
+    q1.z = to_tf32(tanh_fast(v[6]));
+    q1.w = to_tf32(tanh_fast(v[7]));
+    *reinterpret_cast<uint4*>(sA + canon_off_eb<4>(row, c, w)) = q0;
+    *reinterpret_cast<uint4*>(sA + canon_off_eb<4>(row, c + 4, w)) = q1;
+  } else {
+    uint4 q;
+    q.x = tanh_pack_bf16x2(v[0], v[1]);
+    q.y = tanh_pack_bf16x2(v[2], v[3]);
+    q.z = tanh_pack_bf16x2(v[4], v[5]);
+    q.w = tanh_pack_bf16x2(v[6], v[7]);
+    *reinterpret_cast<uint4*>(sA + canon_off(row, c, w)) = q;
   }
 }
 
@@ -71,22 +105,25 @@ constexpr int first_row_f4() { return (DIN + 1 + 3) / 4; }
 
 // NWQ warps share each lane quadrant (its 32 points), w / NWQ columns each:
 // 2 (256 threads, up to three CTAs per SM) or, for w = 256, 4 (512 threads and
-// two CTAs per SM, the most the tensor memory holds at that width).
-template <int DIN, int NWQ>
+// two CTAs per SM, the most the tensor memory holds at that width).  TF: TF32
+// operands (4 bytes, K = 8 per MMA) instead of BF16 (2 bytes, K = 16).
+template <int DIN, int NWQ, bool TF>
 __global__ void __launch_bounds__(128 * NWQ, NWQ == 4 ? 2 : 0) mlp_tc_kernel(TcArgs a) {
   static_assert(DIN == 2 || DIN == 5, "2 or 5 inputs");
   constexpr int RW = first_row_f4<DIN>();
+  constexpr int EB = TF ? 4 : 2;       // operand bytes
+  constexpr int KPM = 32 / EB;         // K of one MMA
   extern __shared__ __align__(1024) unsigned char smem[];
   const MlpDev& m = a.m;
   const int w = a.w, t = threadIdx.x, warp = t >> 5;
   const int pt = (warp & 3) * 32 + (t & 31);  // this thread's point (accumulator lane)
   const int hw = w / NWQ, cb = (warp >> 2) * hw;  // and its columns [cb, cb + hw)
   const int n_sq = m.n_lin - 2;
-  const uint32_t wbytes = (uint32_t)w * w * 2;
+  const uint32_t wbytes = (uint32_t)w * w * EB;
   // shared memory carve-up
   unsigned char* sW = smem;                                             // n_sq (resident) or 1 square layer
   unsigned char* sA = sW + (a.resident ? (size_t)n_sq : 1) * wbytes;    // 128 x w operand
-  float* sW1 = reinterpret_cast<float*>(sA + (size_t)128 * w * 2);      // w rows of RW float4 (W_1, b_1)
+  float* sW1 = reinterpret_cast<float*>(sA + (size_t)128 * w * EB);     // w rows of RW float4 (W_1, b_1)
   float* sB = sW1 + w * 4 * RW;                                         // biases of hidden layers, (n_lin-1) x w
   float* sWo = sB + (m.n_lin - 1) * w;                                  // output weights, w
   uint64_t* bar = reinterpret_cast<uint64_t*>(sWo + w + 2);             // [0] MMA done, [1] weights landed
@@ -139,8 +176,8 @@ __global__ void __launch_bounds__(128 * NWQ, NWQ == 4 ? 2 : 0) mlp_tc_kernel(TcA
   __syncthreads();
   fence_after();
   const uint32_t tmem = *tslot;
-  const uint32_t idesc = make_idesc_bf16(w);
-  const uint32_t sbo = (uint32_t)(w / 8) * 128;  // next 8-row group
+  const uint32_t idesc = TF ? make_idesc_tf32(w) : make_idesc_bf16(w);
+  const uint32_t sbo = (uint32_t)(w * EB / 16) * 128;  // next 8-row group
 
   const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16);  // this warp's accumulator lanes
   double xn[DIN];  // inputs of this thread's point in the next tile (prefetched)
@@ -183,12 +220,7 @@ __global__ void __launch_bounds__(128 * NWQ, NWQ == 4 ? 2 : 0) mlp_tc_kernel(TcA
 #pragma unroll
           for (int j = 0; j < 8; ++j) dot = fmaf(sWo[ob + j], tanh_fast(z[j]), dot);
         } else {
-          uint4 q;
-          q.x = tanh_pack_bf16x2(z[0], z[1]);
-          q.y = tanh_pack_bf16x2(z[2], z[3]);
-          q.z = tanh_pack_bf16x2(z[4], z[5]);
-          q.w = tanh_pack_bf16x2(z[6], z[7]);
-          *reinterpret_cast<uint4*>(sA + canon_off(pt, ob, w)) = q;
+          store_tanh8<TF>(sA, pt, ob, w, z);
         }
       }
     }
@@ -210,10 +242,14 @@ __global__ void __launch_bounds__(128 * NWQ, NWQ == 4 ? 2 : 0) mlp_tc_kernel(TcA
       if (s_fail) break;
       if (t == 0) {
         const uint32_t aa = smem_u32(sA), bb = smem_u32(wl);
-        for (int kk = 0; kk < w / 16; ++kk) {
+        for (int kk = 0; kk < w / KPM; ++kk) {  // each MMA: 2 core matrices (32 bytes) along K
           const uint64_t da = make_desc(aa + kk * 256, 128, sbo);
           const uint64_t db = make_desc(bb + kk * 256, 128, sbo);
-          mma_bf16(tmem, da, db, idesc, kk > 0 ? 1u : 0u);
+          if constexpr (TF) {
+            mma_tf32(tmem, da, db, idesc, kk > 0 ? 1u : 0u);
+          } else {
+            mma_bf16(tmem, da, db, idesc, kk > 0 ? 1u : 0u);
+          }
         }
         mma_commit(&bar[0]);
       }
@@ -264,12 +300,8 @@ __global__ void __launch_bounds__(128 * NWQ, NWQ == 4 ? 2 : 0) mlp_tc_kernel(TcA
         } else {
 #pragma unroll
           for (int j = 0; j < 16; j += 8) {
-            uint4 q;
-            q.x = tanh_pack_bf16x2(v[j], v[j + 1]);
-            q.y = tanh_pack_bf16x2(v[j + 2], v[j + 3]);
-            q.z = tanh_pack_bf16x2(v[j + 4], v[j + 5]);
-            q.w = tanh_pack_bf16x2(v[j + 6], v[j + 7]);
-            *reinterpret_cast<uint4*>(sA + canon_off(pt, c + j, w)) = q;
+            const float (&v8)[8] = *reinterpret_cast<const float(*)[8]>(v + j);
+            store_tanh8<TF>(sA, pt, c + j, w, v8);
           }
         }
       }
@@ -333,43 +365,53 @@ bool tc_supported(const MlpDev& m) {
 // Shared memory of the tensor-core kernel: square-layer weights (all layers
 // when that still leaves room for several CTAs per SM, else one), the 128 x w
 // activation operand, the FP32 input/output layers and biases, two mbarriers.
-static size_t tc_smem_bytes(const MlpDev& m, int* resident) {
+// eb: operand bytes (2 BF16, 4 TF32).
+static size_t tc_smem_bytes(const MlpDev& m, int* resident, int eb) {
   const int w = m.widths[1], n_sq = m.n_lin - 2;
-  const size_t wbytes = (size_t)w * w * 2;
+  const size_t wbytes = (size_t)w * w * eb;
   const size_t rw = m.d_in == 2 ? first_row_f4<2>() : first_row_f4<5>();
-  const size_t fixed = (size_t)128 * w * 2 +
+  const size_t fixed = (size_t)128 * w * eb +
                        sizeof(float) * ((size_t)w * 4 * rw + (size_t)(m.n_lin - 1) * w + w + 2) + 32 + 1024;
   const int res = (n_sq > 0 && (size_t)n_sq * wbytes + fixed <= 96 * 1024) ? 1 : 0;
   if (resident) *resident = res;
   return (res ? (size_t)n_sq : 1) * wbytes + fixed;
 }
 
-bool tc_fits(const MlpDev& m) { return tc_supported(m) && tc_smem_bytes(m, nullptr) <= 220 * 1024; }
+bool tc_fits(const MlpDev& m, bool tf32) {
+  return tc_supported(m) && tc_smem_bytes(m, nullptr, tf32 ? 4 : 2) <= 220 * 1024;
+}
 
+// Room for the square layers in either operand type (TF32: 4 bytes each).
 size_t tc_packed_bytes(const MlpDev& m) {
   const int w = m.widths[1];
   const int n_sq = m.n_lin - 2;
-  return (size_t)(n_sq > 0 ? n_sq : 0) * w * w * 2;
+  return (size_t)(n_sq > 0 ? n_sq : 0) * w * w * 4;
 }
 
 cudaError_t launch_mlp_eval_tc(const MlpDev& m, unsigned char* packed, const double* X, int64_t N, double* u,
-                               int* status, cudaStream_t s) {
+                               int* status, cudaStream_t s, bool tf32) {
   if (N <= 0) return cudaSuccess;
   if (((uintptr_t)packed & 15) != 0) return cudaErrorInvalidValue;  // TMA source alignment
   const int w = m.widths[1], n_sq = m.n_lin - 2;
   cudaError_t e = cudaSuccess;
   if (n_sq > 0) {
-    pack_square_kernel<<<148, 256, 0, s>>>(m, w, packed);
+    if (tf32) {
+      pack_square_kernel<true><<<148, 256, 0, s>>>(m, w, packed);
+    } else {
+      pack_square_kernel<false><<<148, 256, 0, s>>>(m, w, packed);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   int resident = 0;
-  const size_t smem = tc_smem_bytes(m, &resident);
+  const size_t smem = tc_smem_bytes(m, &resident, tf32 ? 4 : 2);
   if (smem > 220 * 1024) return cudaErrorInvalidValue;
   TcArgs a{m, packed, X, N, u, w, resident, status};
   const bool wide = w == 256;  // four warps per lane quadrant
   const int threads = wide ? 512 : 256;
-  auto kern = m.d_in == 2 ? (wide ? mlp_tc_kernel<2, 4> : mlp_tc_kernel<2, 2>)
-                          : (wide ? mlp_tc_kernel<5, 4> : mlp_tc_kernel<5, 2>);
+  auto kern = tf32 ? (m.d_in == 2 ? (wide ? mlp_tc_kernel<2, 4, true> : mlp_tc_kernel<2, 2, true>)
+                                  : (wide ? mlp_tc_kernel<5, 4, true> : mlp_tc_kernel<5, 2, true>))
+                   : (m.d_in == 2 ? (wide ? mlp_tc_kernel<2, 4, false> : mlp_tc_kernel<2, 2, false>)
+                                  : (wide ? mlp_tc_kernel<5, 4, false> : mlp_tc_kernel<5, 2, false>));
   if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
     return e;
   // CTAs per SM from the shared memory each one takes (dynamic + static + the

@@ -34,6 +34,13 @@ __device__ __forceinline__ uint32_t make_idesc_bf16(int n) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 }
 
+// Instruction descriptor of kind::tf32: D FP32, A and B TF32 (format 2; the
+// tensor core reads the 19 high bits of each 32-bit operand), both K-major,
+// N = n, M = 128.  One MMA covers K = 8 (32 bytes of a core-matrix row pair).
+__device__ __forceinline__ uint32_t make_idesc_tf32(int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
 // The same with A and/or B stored MN-major (the M or N index contiguous in a
 // core-matrix row): instruction-descriptor bits 15 (A) and 16 (B).  In the
 // no-swizzle MN-major layout the descriptor's SBO is the byte distance of
@@ -46,6 +53,13 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
       "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
@@ -159,6 +173,20 @@ __device__ __forceinline__ uint32_t tanh_pack_bf16x2(float lo, float hi) {
 // (8 elements per 16-byte core-matrix row).
 __host__ __device__ __forceinline__ uint32_t canon_off(int row, int k, int K) {
   return (uint32_t)(((row >> 3) * (K / 8) + k / 8) * 128 + (row & 7) * 16 + (k % 8) * 2);
+}
+
+// The same for EB-byte elements (2: BF16, 4: TF32; 16 / EB per core-matrix row).
+template <int EB>
+__host__ __device__ __forceinline__ uint32_t canon_off_eb(int row, int k, int K) {
+  constexpr int PER = 16 / EB;
+  return (uint32_t)(((row >> 3) * (K / PER) + k / PER) * 128 + (row & 7) * 16 + (k % PER) * EB);
+}
+
+// FP32 rounded to TF32 (round to nearest, ties away: cvt.rna), as 32 bits.
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
 }
 
 

@@ -1,6 +1,6 @@
 """GPU parity of the network path (evaluation, derivatives, loss, adjoint
-gradient, Adam) against the oracle, through the C ABI.  BF16 evaluation of
-the w x w hidden layers runs on the tensor cores (tcgen05).
+gradient, Adam) against the oracle, through the C ABI.  BF16 and TF32
+evaluation of the w x w hidden layers runs on the tensor cores (tcgen05).
 
 Tolerances (relative to the largest magnitude of the compared quantity):
   FP64: 1e-12 for u, 1e-10 for derivatives and gradients (the GPU sums in a
@@ -232,6 +232,23 @@ def test_tensor_core_eval_shapes_and_ragged_tiles(B, orc, w, n_hidden, d_in, pre
         u = m.eval(torch.tensor(X, device="cuda"), prec=prec).cpu().numpy()
         assert m.device_status() == B.BS_OK
         assert _rel(u, ref) <= TOL_EVAL[prec], (n, _rel(u, ref))
+
+
+@pytest.mark.parametrize("arch", ["2-4x64", "2-6x128", "5-6x128"])
+def test_tf32_tensor_core_eval_is_tf32_accurate(B, orc, arch):
+    # the TF32 path keeps 10 explicit mantissa bits of both operands (BF16: 7),
+    # so on the same network its error against the oracle is several times
+    # smaller than BF16's (measured about 8-10x): a path that rounded to BF16 or
+    # lost a layer would not pass
+    widths = ARCHS[arch]
+    m, om = _model(B, orc, widths, 5)
+    X = _points(widths, 20000, 9)
+    ref = orc.mlp_eval(om, X, with_derivs=False)
+    Xd = torch.tensor(X, device="cuda")
+    e_tf = _rel(m.eval(Xd, prec=B.TF32).cpu().numpy(), ref)
+    e_bf = _rel(m.eval(Xd, prec=B.BF16).cpu().numpy(), ref)
+    assert m.device_status() == B.BS_OK
+    assert e_tf <= TOL_EVAL[2] and e_tf < 0.3 * e_bf, (e_tf, e_bf)
 
 
 def _param_blocks(widths):
