@@ -251,8 +251,11 @@ int pinn_set_state(pinn_model* m, const double* theta, const double* mom1, const
 
 /*
  * pinn_device_status -- synchronises the device and reports the network's
- * device status word: BS_OK, or BS_TIMEOUT if a bounded wait inside a
- * tensor-core kernel gave up (its results are then invalid).
+ * device status word: BS_OK; BS_TIMEOUT if a bounded wait inside a
+ * tensor-core kernel gave up (its results are then invalid); BS_EINVAL if a
+ * loss call met a point of a kind outside 0..3, or of kind 4 in a call without
+ * values y (such points were left out of that call's loss terms, counts and
+ * gradient).  The word is sticky until the handle is destroyed.
  */
 int pinn_device_status(const pinn_model* m, int* status);
 
@@ -279,7 +282,11 @@ int pinn_eval(const pinn_model* m, int prec, const double* X, int64_t N, double*
  *   X: device [N][d_in] doubles; kind: device [N] int8: 0 interior,
  *   1 boundary S = 0 (target 0), 2 boundary S = Smax (target Smax - K e^{-r tau}),
  *   3 expiry tau = 0 (target max(S - K, 0)); kind 4 (data point) belongs to
- *   pinn_loss_grad_data, here its value is taken as 0.  prob_params (host): K, sigma, r,
+ *   pinn_loss_grad_data.  The kinds live on the device, so this call does not
+ *   read them on the host: a point of any other kind (here also 4) is left out
+ *   and BS_EINVAL recorded in the network's status word (pinn_device_status).
+ *   X and kind hold N entries each (the library cannot check device lengths).
+ *   prob_params (host): K, sigma, r,
  *   Smax of the loss (a 5-input network takes sigma, r, K per point from X;
  *   then Smax of kind-2 points is smax_over_K * K when smax_over_K > 0).
  *   prec: BS_FP64, BS_FP32, or BS_BF16 (BF16 operands, FP32 accumulation).
@@ -299,8 +306,10 @@ int pinn_loss_grad(const pinn_model* m, const double* X, const int8_t* kind, int
  * pinn_train_step -- pinn_loss_grad followed by one full-batch Adam step
  * (Section 3.3; beta1 0.9, beta2 0.999, eps 1e-8, step size lr) on the FP64
  * master parameters.  loss3: host, nullable; if given the call synchronises the
- * stream and stores the loss terms evaluated BEFORE the update.  grad_out:
- * device, nullable, n_params doubles: receives the gradient used.
+ * stream, stores the loss terms evaluated BEFORE the update and returns the
+ * network's status word when it is not BS_OK (BS_EINVAL: a point of an
+ * invalid kind was left out).  grad_out: device, nullable, n_params doubles:
+ * receives the gradient used.
  */
 int pinn_train_step(pinn_model* m, const double* X, const int8_t* kind, int64_t N, const bs_params* prob_params,
                     double smax_over_K, int prec, double lr, double* loss3, double* grad_out, void* stream);
@@ -313,8 +322,9 @@ int pinn_train_step(pinn_model* m, const double* X, const int8_t* kind, int64_t 
  * the first loss term, so loss3[0] is the mean over kind-0 residuals and kind-4
  * misfits together (a batch of kind 4 only trains on data alone).
  *   y: device [N] doubles, 8-byte aligned, non-null (read at kind-4 points
- *   only).  Every other argument, the precisions and the tensor-core path are
- *   those of pinn_loss_grad / pinn_train_step.  BS_EINVAL for a null or
+ *   only; N entries).  Every other argument, the precisions and the
+ *   tensor-core path are those of pinn_loss_grad / pinn_train_step; kinds
+ *   outside 0..4 are left out and recorded as there.  BS_EINVAL for a null or
  *   misaligned y.
  */
 int pinn_loss_grad_data(const pinn_model* m, const double* X, const int8_t* kind, const double* y, int64_t N,

@@ -259,6 +259,8 @@ def pinn_loss_grad(m: MLP, X: np.ndarray, kind: np.ndarray, K: float, sigma: flo
                                     kind.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)),
                                     _dp(yv) if yv is not None else None, X.shape[0], K, sigma, r, Smax,
                                     smax_over_K, _dp(terms), _dp(g) if g is not None else None)
+    if rc == -2:
+        raise ValueError("kind outside 0..3, or kind 4 without values y")
     if rc:
         raise MemoryError("oracle loss allocation failed")
     return (terms, g) if with_grad else terms

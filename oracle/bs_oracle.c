@@ -552,7 +552,8 @@ int orc_pinn_table(const orc_params* p, int n_lin, const int32_t* widths, const 
  * 2 boundary S = Smax (Eq. 13, both in one mean), 3 expiry tau = 0 (Eq. 14),
  * 4 data point: squared misfit (u - y)^2 to a given value y, in the mean of
  * term 0 (Section 4 trains a network on fine-propagator output alone, without
- * the PDE terms, for comparison with the PINN).
+ * the PDE terms, for comparison with the PINN).  Any other kind, or a data
+ * point when no values y are given, is an input error (return -2).
  * Residual in tau: f = u_tau - 1/2 sigma^2 S^2 u_SS - r S u_S + r u (Eq. 1 with
  * dV/dt = -dV/dtau, sign flipped; |f|^2 is unchanged).  The sigma, r, K used in
  * the residual and targets are the ones given here (a parametric network also
@@ -610,9 +611,13 @@ int orc_pinn_loss_grad_y(int n_lin, const int32_t* w, const double* params, cons
   }
   int64_t cnt[3] = {0, 0, 0};
   for (int64_t k = 0; k < N; ++k) {
-    if (kind[k] == 0 || kind[k] == 4) cnt[0]++;
+    if (kind[k] == 0 || (kind[k] == 4 && y)) cnt[0]++;
     else if (kind[k] == 1 || kind[k] == 2) cnt[1]++;
-    else cnt[2]++;
+    else if (kind[k] == 3) cnt[2]++;
+    else {  /* a kind outside 0..3, or a data point without its value */
+      free(buf); free(acts); free(adj); free(x0);
+      return -2;
+    }
   }
   double sums[3] = {0.0, 0.0, 0.0};
   if (grad) memset(grad, 0, sizeof(double) * (size_t)np_);
@@ -636,7 +641,7 @@ int orc_pinn_loss_grad_y(int n_lin, const int32_t* w, const double* params, cons
       gS = -ri * S * gf;
       gu = ri * gf;
     } else if (kind[k] == 4) {
-      double e = out[0] - (y ? y[k] : 0.0);
+      double e = out[0] - y[k];
       sums[0] += e * e;
       gu = 2.0 * e / (double)cnt[0];
     } else {

@@ -198,6 +198,33 @@ def _dev(t, dtype, what):
     return ctypes.c_void_p(t.data_ptr())
 
 
+_kinds_checked = {}
+
+
+def check_loss_inputs(X, kind, y=None):
+    """Lengths and kinds of a training batch, checked before any launch: X is
+    [N][d_in], kind and y (when given) hold N entries, every kind is 0..3 or,
+    with values y, 4.  The range check reads the kinds once per tensor version
+    (a cache keyed by the tensor's storage, version and length), so a training
+    loop over one batch pays it once."""
+    n = X.shape[0] if X.dim() == 2 else -1
+    if n < 0:
+        raise ValueError("X must be a [N][d_in] tensor")
+    if kind.dim() != 1 or kind.numel() != n:
+        raise ValueError(f"kind must hold N = {n} entries (has {kind.numel()})")
+    if y is not None and (y.dim() != 1 or y.numel() != n):
+        raise ValueError(f"y must hold N = {n} entries (has {y.numel()})")
+    top = 4 if y is not None else 3
+    key = (kind.device.type, kind.data_ptr(), kind._version, n, top)
+    if key not in _kinds_checked:
+        if n and bool(((kind < 0) | (kind > top)).any()):
+            raise ValueError(f"kind values must lie in 0..{top}" + ("" if y is not None else
+                                                                     " (kind 4 needs values y)"))
+        if len(_kinds_checked) > 64:
+            _kinds_checked.clear()
+        _kinds_checked[key] = True
+
+
 def params(K=1.0, sigma=0.2, r=0.05, T=1.0, Smax=4.0, Nx=256, P=8, fine_steps=128, coarse_steps=1) -> dict:
     return dict(K=K, sigma=sigma, r=r, T=T, Smax=Smax, Nx=Nx, P=P, fine_steps=fine_steps, coarse_steps=coarse_steps)
 
@@ -440,28 +467,30 @@ def _autograd_function():
         vector theta.  forward loads theta into the model and runs
         pinn_loss_grad (the forward derivative streams and the adjoint on the
         device), keeping the gradient; backward returns it times the incoming
-        gradient.  apply(theta, model, X, kind, prob, smax_over_K, prec)."""
+        gradient.  apply(theta, model, X, kind, prob, smax_over_K, prec, y);
+        y: values of the kind-4 data points, or None."""
 
         @staticmethod
-        def forward(ctx, theta, model, X, kind, prob, smax_over_K, prec):
+        def forward(ctx, theta, model, X, kind, prob, smax_over_K, prec, y):
             model.set_weights(theta.detach().to("cpu", torch.float64).numpy())
-            loss3, grad = model.loss_grad(X, kind, prob, smax_over_K, prec)
+            loss3, grad = model.loss_grad(X, kind, prob, smax_over_K, prec, y=y)
             ctx.save_for_backward(grad.to(theta.device))
             return loss3.sum().to(theta.device)
 
         @staticmethod
         def backward(ctx, g):
             (grad,) = ctx.saved_tensors
-            return grad * g, None, None, None, None, None, None
+            return grad * g, None, None, None, None, None, None, None
 
     return PinnLossFunction
 
 
-def pinn_loss(theta, model, X, kind, prob: dict, smax_over_K=0.0, prec=FP32):
+def pinn_loss(theta, model, X, kind, prob: dict, smax_over_K=0.0, prec=FP32, y=None):
     """Total loss (Eq. 11) of `model` with parameters `theta` (FP64 tensor of
-    model.n_params) on collocation points X / kind; differentiable in theta
-    (the gradient is the device adjoint of pinn_loss_grad)."""
-    return _autograd_function().apply(theta, model, X, kind, prob, smax_over_K, prec)
+    model.n_params) on collocation points X / kind (y: values of the kind-4
+    data points); differentiable in theta (the gradient is the device adjoint
+    of pinn_loss_grad / pinn_loss_grad_data)."""
+    return _autograd_function().apply(theta, model, X, kind, prob, smax_over_K, prec, y)
 
 
 class PinnModel:
@@ -534,7 +563,7 @@ class PinnModel:
         self.set_state(c["theta"], c["mom1"], c["mom2"], c["step"])
 
     def device_status(self) -> int:
-        """Synchronise and read the device status word (BS_OK or BS_TIMEOUT)."""
+        """Synchronise and read the device status word (BS_OK, BS_TIMEOUT or BS_EINVAL)."""
         s = ctypes.c_int(0)
         _check(lib().pinn_device_status(self._h, ctypes.byref(s)), "pinn_device_status")
         return s.value
@@ -556,6 +585,7 @@ class PinnModel:
         """Loss terms and gradient; y (device doubles): values of the kind-4 data points."""
         import torch
 
+        check_loss_inputs(X, kind, y)
         loss3 = torch.empty(3, dtype=torch.float64, device=X.device)
         grad = torch.empty(self.n_params, dtype=torch.float64, device=X.device)
         pp = _to_struct(prob)
@@ -576,6 +606,7 @@ class PinnModel:
         """One Adam step on the loss; y (device doubles): values of the kind-4 data points."""
         import torch
 
+        check_loss_inputs(X, kind, y)
         pp = _to_struct(prob)
         loss = (ctypes.c_double * 3)() if want_loss else None
         g = _dev(grad_out, torch.float64, "grad_out") if grad_out is not None else None

@@ -787,9 +787,12 @@ static int train_step_common(pinn_model* m, const double* X, const int8_t* kind,
   cudaError_t e = bsp::launch_adam(m->n_params, m->p64, m->mom1, m->mom2, g, m->step, lr, m->p32, s);
   if (e != cudaSuccess) return map_err(e);
   if (loss3) {
+    int st = 0;
     e = cudaMemcpyAsync(loss3, m->loss3, 3 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&st, m->dev.status, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return map_err(e);
+    if (st != 0) return st;  // BS_EINVAL (a point of an invalid kind) or BS_TIMEOUT
   }
   return BS_OK;
 }

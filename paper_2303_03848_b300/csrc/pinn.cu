@@ -249,23 +249,30 @@ size_t loss_grad_workspace_bytes(const MlpDev& m, int64_t N) {
   return ws_tail(m, L, sizeof(double), N).total + 256;  // + alignment of the caller's pointer
 }
 
-__global__ void count_kinds_kernel(const int8_t* __restrict__ kind, int64_t N, unsigned long long* cnt) {
+// Points per loss term; a kind outside 0..3, or 4 without values (data_ok
+// false), is counted nowhere and recorded as BS_EINVAL in the status word.
+__global__ void count_kinds_kernel(const int8_t* __restrict__ kind, int64_t N, unsigned long long* cnt, int data_ok,
+                                   int* status) {
   unsigned long long c0 = 0, c1 = 0, c2 = 0;
+  bool bad = false;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
     const int k = kind[i];
-    if (k == 0 || k == 4) ++c0;
+    if (k == 0 || (k == 4 && data_ok)) ++c0;
     else if (k == 1 || k == 2) ++c1;
-    else ++c2;
+    else if (k == 3) ++c2;
+    else bad = true;
   }
   for (int s = 16; s >= 1; s >>= 1) {
     c0 += __shfl_down_sync(kFull, c0, s);
     c1 += __shfl_down_sync(kFull, c1, s);
     c2 += __shfl_down_sync(kFull, c2, s);
   }
+  bad = __any_sync(kFull, bad);
   if ((threadIdx.x & 31) == 0) {
     atomicAdd(cnt + 0, c0);
     atomicAdd(cnt + 1, c1);
     atomicAdd(cnt + 2, c2);
+    if (bad && status != nullptr) atomicExch(status, 1);  // BS_EINVAL
   }
 }
 
@@ -344,11 +351,11 @@ __global__ void train_fwd_kernel(MlpDev m, LossArgs la, TrainLayout TL, Tp* __re
       gSS = -0.5 * si * si * S * S * gf;
       gS = -ri * S * gf;
       gu = ri * gf;
-    } else if (kd == 4) {  // data point: misfit to its given value, in term 0
-      const double e = (double)out[0] - (la.y != nullptr ? la.y[p] : 0.0);
+    } else if (kd == 4 && la.y != nullptr) {  // data point: misfit to its given value, in term 0
+      const double e = (double)out[0] - la.y[p];
       sq[0] = e * e;
       gu = 2.0 * e / (double)cnt[0];
-    } else {
+    } else if (kd >= 1 && kd <= 3) {
       const double e = (double)out[0] - tgt;
       const int tt = (kd == 3) ? 2 : 1;
       sq[tt] = e * e;
@@ -525,7 +532,7 @@ static cudaError_t loss_grad_impl(const MlpDev& m, const LossArgs& la, double* l
   for (int l = 1; l <= m.n_lin; ++l) np += (int64_t)m.widths[l] * m.widths[l - 1] + m.widths[l];
   e = cudaMemsetAsync(grad, 0, (size_t)np * sizeof(double), s);
   if (e != cudaSuccess) return e;
-  count_kinds_kernel<<<148, 256, 0, s>>>(la.kind, la.N, cnt);
+  count_kinds_kernel<<<148, 256, 0, s>>>(la.kind, la.N, cnt, la.y != nullptr, m.status);
   {  // CUDA cores: forward, adjoint, per-layer reductions
     {
       const size_t per_thread = 2 * 4 * (size_t)m.max_w * sizeof(Tp);

@@ -32,9 +32,11 @@ __device__ __forceinline__ void point_setup(const LossArgs& la, int d_in, const 
 // come from BF16 GEMMs and its seeds are rounded to BF16, so FP32 and the FP32
 // exponential carry no error that matters there): kind 0 interior (residual of
 // Eq. 1 in tau), 1/2 the S = 0 / S = Smax boundary (Eq. 13), 3 expiry
-// (Eq. 14), 4 data point (misfit to its value yv, in term 0).  sq[term]
-// receives the squared error, g[4] = dLoss/d(u, u_S, u_SS, u_tau) with each
-// term a mean over its points; inv_cnt[term] = 1 / (points of that term).
+// (Eq. 14), 4 data point (misfit to its value yv, in term 0; only when the
+// call has values, la.y != null).  sq[term] receives the squared error,
+// g[4] = dLoss/d(u, u_S, u_SS, u_tau) with each term a mean over its points;
+// inv_cnt[term] = 1 / (points of that term).  Any other kind contributes
+// nothing (the counting pass records it as an input error).
 __device__ __forceinline__ void point_loss_f32(const LossArgs& la, int d_in, const float* x, int kd, float yv,
                                                const float (&out)[4], const float (&inv_cnt)[3], float (&sq)[3],
                                                float (&g)[4]) {
@@ -55,11 +57,11 @@ __device__ __forceinline__ void point_loss_f32(const LossArgs& la, int d_in, con
     g[2] = -a * gf;
     g[1] = -b * gf;
     g[0] = ri * gf;
-  } else if (kd == 4) {
+  } else if (kd == 4 && la.y != nullptr) {
     const float e = out[0] - yv;
     sq[0] = e * e;
     g[0] = 2.0f * e * inv_cnt[0];
-  } else {
+  } else if (kd >= 1 && kd <= 3) {
     float tgt = 0.0f;
     if (kd == 2) {
       const float Sm = (la.smax_over_K > 0.0 && d_in >= 5) ? (float)la.smax_over_K * Ki : (float)la.Smax;

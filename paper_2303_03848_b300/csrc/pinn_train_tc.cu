@@ -154,7 +154,7 @@ __device__ __forceinline__ uint4 pack8(const float* v) {
 // zero the gradient (np entries) and count the points of each loss term into
 // cnt (zeroed by the caller; kinds 0 interior and 4 data, 1 and 2 boundary, 3 expiry).
 __global__ void train_prep_kernel(MlpDev m, int w, unsigned char* fwd, unsigned char* bwd, const int8_t* kind,
-                                  int64_t N, unsigned long long* cnt, double* grad, int64_t np) {
+                                  int64_t N, unsigned long long* cnt, double* grad, int64_t np, int data_ok) {
   const int n_sq = m.n_lin - 2;
   const int64_t per = (int64_t)w * w;
   const int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
@@ -166,22 +166,28 @@ __global__ void train_prep_kernel(MlpDev m, int w, unsigned char* fwd, unsigned 
     *reinterpret_cast<__nv_bfloat16*>(bwd + sq * per * 2 + canon_off(i, o, w)) = v;
   }
   for (int64_t q = i0; q < np; q += stride) grad[q] = 0.0;
+  // points per loss term; a kind outside 0..3, or 4 without values, is counted
+  // nowhere and recorded as BS_EINVAL in the network's status word
   unsigned long long c0 = 0, c1 = 0, c2 = 0;
+  bool bad = false;
   for (int64_t q = i0; q < N; q += stride) {
     const int k = kind[q];
-    if (k == 0 || k == 4) ++c0;
+    if (k == 0 || (k == 4 && data_ok)) ++c0;
     else if (k == 1 || k == 2) ++c1;
-    else ++c2;
+    else if (k == 3) ++c2;
+    else bad = true;
   }
   for (int o = 16; o >= 1; o >>= 1) {
     c0 += __shfl_down_sync(0xffffffffu, c0, o);
     c1 += __shfl_down_sync(0xffffffffu, c1, o);
     c2 += __shfl_down_sync(0xffffffffu, c2, o);
   }
+  bad = __any_sync(0xffffffffu, bad);
   if ((threadIdx.x & 31) == 0) {
     if (c0) atomicAdd(cnt + 0, c0);
     if (c1) atomicAdd(cnt + 1, c1);
     if (c2) atomicAdd(cnt + 2, c2);
+    if (bad && m.status != nullptr) atomicExch(m.status, 1);  // BS_EINVAL
   }
 }
 
@@ -992,7 +998,7 @@ cudaError_t launch_train_tc(const MlpDev& m, const LossArgs& la, unsigned char* 
   for (int l = 1; l <= m.n_lin; ++l) np += (int64_t)m.widths[l] * m.widths[l - 1] + m.widths[l];
   unsigned char* wpack = ws + L.pack;
   train_prep_kernel<<<sm_count(), 256, 0, s>>>(m, w, wpack, wpack + (size_t)n_sq * w * w * 2, la.kind, la.N, cnt,
-                                               grad, np);
+                                               grad, np, la.y != nullptr);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // consecutive chunks of the batch; the loss terms are means over the whole

@@ -134,3 +134,32 @@ def test_splitmix_generator_matches_published_vectors():
     out = synth.splitmix64(1234567, np.arange(5, dtype=np.uint64))
     assert [int(v) for v in out] == [6457827717110365317, 3203168211198807973, 9817491932198370423,
                                      4593380528125082431, 16408922859458223821]
+
+
+def test_training_batch_checks_run_before_any_launch():
+    # lengths and kinds are checked on the host by the binding before the C ABI
+    # is called (the library cannot see device lengths): CPU tensors suffice
+    torch = pytest.importorskip("torch")
+    X = torch.zeros(10, 2, dtype=torch.float64)
+    kind = torch.zeros(10, dtype=torch.int8)
+    y = torch.zeros(10, dtype=torch.float64)
+    B.check_loss_inputs(X, kind)
+    B.check_loss_inputs(X, kind, y)
+    with pytest.raises(ValueError, match="kind must hold"):
+        B.check_loss_inputs(X, kind[:9])
+    with pytest.raises(ValueError, match="y must hold"):
+        B.check_loss_inputs(X, kind, y[:9])
+    k4 = kind.clone()
+    k4[3] = 4
+    B.check_loss_inputs(X, k4, y)  # a data point with its value
+    with pytest.raises(ValueError, match="0..3"):
+        B.check_loss_inputs(X, k4)  # a data point without values
+    for bad in (5, -1, 7):
+        kb = kind.clone()
+        kb[7] = bad
+        with pytest.raises(ValueError, match="kind values"):
+            B.check_loss_inputs(X, kb, y)
+    # a checked tensor modified in place is checked again
+    kind[2] = 9
+    with pytest.raises(ValueError):
+        B.check_loss_inputs(X, kind)

@@ -431,3 +431,82 @@ def test_autograd_function_drives_a_torch_optimizer(B):
         opt.step()
         first = loss.item() if first is None else first
     assert loss.item() < first
+
+
+def _c_loss_grad(B, m, X, kind, prob, sok, prec):
+    # straight through the C ABI (the binding would refuse these kinds on the host)
+    import ctypes
+
+    loss3 = torch.empty(3, dtype=torch.float64, device="cuda")
+    grad = torch.empty(m.n_params, dtype=torch.float64, device="cuda")
+    pp = B._to_struct(prob)
+    rc = B.lib().pinn_loss_grad(m._h, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(kind.data_ptr()), X.shape[0],
+                                ctypes.byref(pp), sok, prec, ctypes.c_void_p(loss3.data_ptr()),
+                                ctypes.c_void_p(grad.data_ptr()), B._stream())
+    return rc, loss3.cpu().numpy(), grad.cpu().numpy()
+
+
+@pytest.mark.parametrize("prec", [0, 3])
+def test_invalid_kinds_are_left_out_and_reported(B, orc, prec):
+    # kinds outside 0..3, and data points in a call without values, are counted
+    # nowhere and contribute nothing; the network's status word says BS_EINVAL
+    widths = ARCHS["2-4x64"]
+    X, kind, prob, sok = _loss_case(widths, 700, 64, 64, 3)
+    kb = kind.copy()
+    kb[np.arange(kind.size) % 11 == 5] = 7
+    kb[np.arange(kind.size) % 13 == 6] = 4
+    kb[np.arange(kind.size) % 17 == 8] = -3
+    keep = (kb >= 0) & (kb <= 3)
+    m_bad, _ = _model(B, orc, widths, 8)
+    rc, l_bad, g_bad = _c_loss_grad(B, m_bad, torch.tensor(X, device="cuda"), torch.tensor(kb, device="cuda"), prob,
+                                    sok, prec)
+    assert rc == B.BS_OK and m_bad.device_status() == B.BS_EINVAL
+    m_ok, om = _model(B, orc, widths, 8)
+    terms, grad = orc.pinn_loss_grad(om, X[keep], kind[keep], prob["K"], prob["sigma"], prob["r"], prob["Smax"], sok)
+    tol_l, tol_g = {0: (1e-12, 1e-10), 3: (5e-2, 1e-1)}[prec]
+    for c in range(3):
+        assert abs(l_bad[c] - terms[c]) <= tol_l * abs(terms[c]), (c, l_bad[c], terms[c])
+    assert _rel(g_bad, grad) <= tol_g
+    assert m_ok.device_status() == B.BS_OK
+
+
+def test_data_only_network_as_coarse_propagator(B):
+    # Section 4's data-only network: trained on the serial fine solution at the
+    # grid points (kind-4 data points, no PDE terms), then used as the coarse
+    # propagator.  The data loss falls, the trained table is closer to serial
+    # fine than the untrained one, and network-anchored Parareal reaches its
+    # tolerance in fewer than P iterations with the iterate within it of serial
+    # fine.  The autograd wrapper takes the data values too.
+    cfg = dict(K=1.0, sigma=0.2, r=0.05, T=1.0, Smax=4.0, Nx=64, P=8, fine_steps=64, coarse_steps=1)
+    prob = B.Problem(cfg)
+    Uf = prob.serial_fine()
+    S = torch.linspace(0.0, cfg["Smax"], cfg["Nx"], dtype=torch.float64, device="cuda")
+    tau = torch.linspace(0.0, cfg["T"], cfg["P"] + 1, dtype=torch.float64, device="cuda")
+    Xg = torch.stack([S.repeat(cfg["P"] + 1), tau.repeat_interleave(cfg["Nx"])], dim=1).contiguous()
+    kd = torch.full((Xg.shape[0],), 4, dtype=torch.int8, device="cuda")
+    widths = [2, 32, 32, 1]
+    dnet = B.PinnModel(widths, [0.0, 0.0], [cfg["Smax"], cfg["T"]], seed=0)
+    fresh = B.PinnModel(widths, [0.0, 0.0], [cfg["Smax"], cfg["T"]], seed=0)
+
+    def table_err(m):
+        g = m.eval(Xg, prec=B.FP64).view(cfg["P"] + 1, cfg["Nx"])[1:]
+        f = Uf.view(cfg["P"] + 1, cfg["Nx"])[1:]
+        return float(((g - f).norm(dim=1) / f.norm(dim=1)).max())
+
+    first = dnet.train_step(Xg, kd, cfg, lr=3e-3, prec=B.BF16, want_loss=True, y=Uf)
+    for _ in range(600):
+        dnet.train_step(Xg, kd, cfg, lr=3e-3, prec=B.BF16, y=Uf)
+    last = dnet.train_step(Xg, kd, cfg, lr=3e-3, prec=B.BF16, want_loss=True, y=Uf)
+    assert first[1] == 0.0 and first[2] == 0.0 and last[0] < 0.05 * first[0], (first, last)
+    assert table_err(dnet) < 0.5 * table_err(fresh)
+    U, norms, stats, rc = prob.parareal_solve(B.COARSE_PINN_IE, model=dnet, prec=B.BF16, tol=1e-6)
+    assert rc == B.BS_OK and stats[0]["iterations"] < cfg["P"], stats
+    f = Uf.view(cfg["P"] + 1, cfg["Nx"])[1:]
+    err = float(((U.view(cfg["P"] + 1, cfg["Nx"])[1:] - f).norm(dim=1) / f.norm(dim=1)).max())
+    assert err < 1e-5
+    theta = torch.tensor(dnet.get_weights(), dtype=torch.float64, requires_grad=True)
+    loss = B.pinn_loss(theta, dnet, Xg, kd, cfg, prec=B.FP64, y=Uf)
+    loss.backward()
+    l3, g = dnet.loss_grad(Xg, kd, cfg, prec=B.FP64, y=Uf)
+    assert abs(float(loss.detach()) - float(l3.sum())) <= 1e-12 * abs(float(l3.sum()))
+    np.testing.assert_allclose(theta.grad.numpy(), g.cpu().numpy(), rtol=0, atol=1e-12 * float(g.abs().max()))

@@ -488,6 +488,24 @@ def test_data_points_loss_and_gradient_match_autograd(orc):
         np.testing.assert_allclose(grad, rg, rtol=1e-10, atol=1e-13)
 
 
+def test_loss_rejects_invalid_kinds(orc):
+    # kinds outside 0..3, and data points (kind 4) without their values, are
+    # input errors of the loss definition, not a fifth term
+    widths = [2, 8, 1]
+    m = orc.MLP(widths, synth.xavier_params(widths, 1), [0.0, 0.0], [4.0, 1.0])
+    X, kind = synth.collocation(3, 20, 4, 4, 4.0, 1.0)
+    for bad in (5, -1):
+        kb = kind.copy()
+        kb[2] = bad
+        with pytest.raises(ValueError):
+            orc.pinn_loss_grad(m, X, kb, 1.0, 0.2, 0.05, 4.0)
+    kb = kind.copy()
+    kb[2] = 4
+    with pytest.raises(ValueError):
+        orc.pinn_loss_grad(m, X, kb, 1.0, 0.2, 0.05, 4.0)
+    orc.pinn_loss_grad(m, X, kb, 1.0, 0.2, 0.05, 4.0, y=np.zeros(len(kb)))
+
+
 def test_parametric_loss_gradient_matches_autograd(orc):
     widths = [5, 10, 10, 1]
     params = synth.xavier_params(widths, 13)
