@@ -20,7 +20,9 @@ properties that hold at any size.
   two implicit-Euler-coarse Parareal iterations leave the first three slices
   equal to GPU serial fine bitwise.
 * Training workload (2->6x128, 65536 collocation points): every layer's BF16
-  tensor-core gradient against the FP32 CUDA-core gradient of the same batch.
+  tensor-core gradient against the oracle's FP64 gradient of the whole batch
+  (computed in host threads from single-term chunks) and against the FP32
+  CUDA-core gradient of the same batch.
 
 FP64 tolerance: max(1e-12, 2 kappa u N) as in test_gpu_solver.py (kappa the
 mesh-ratio factor of the right-hand side, u = 2^-53, N the steps).
@@ -177,11 +179,39 @@ def test_large_instance_full_size(B, orc):
     assert _rel(Uf[Nx:2 * Nx].cpu().numpy(), first) <= _kappa_tol(cfg, cfg["fine_steps"])
 
 
-def test_training_step_full_size_matches_fp32_path(B):
+def _oracle_loss_grad_threaded(orc, om, X, kind, prob, sok, chunk=2048):
+    """The oracle's loss terms and gradient of a whole batch, from chunks of
+    points that feed one loss term each, run in host threads (the oracle is C
+    called through ctypes, which releases the GIL).  Each term of Eq. 11 is a
+    mean over its own points, so the batch's term t and its gradient are the
+    chunks' ones weighted by (chunk points / points of term t)."""
+    import os
+    from concurrent.futures import ThreadPoolExecutor
+
+    jobs = []
+    for t, kinds in ((0, (0,)), (1, (1, 2)), (2, (3,))):
+        idx = np.nonzero(np.isin(kind, kinds))[0]
+        for c in range(0, len(idx), chunk):
+            jobs.append((t, idx[c:c + chunk], len(idx[c:c + chunk]) / len(idx)))
+
+    def run(job):
+        t, ix, _ = job
+        return orc.pinn_loss_grad(om, X[ix], kind[ix], prob["K"], prob["sigma"], prob["r"], prob["Smax"], sok)
+
+    with ThreadPoolExecutor(os.cpu_count() or 1) as ex:
+        res = list(ex.map(run, jobs))
+    terms, grad = np.zeros(3), np.zeros(om.params.size)
+    for (t, _, wgt), (t3, g) in zip(jobs, res):
+        terms[t] += wgt * t3[t]
+        grad += wgt * g
+    return terms, grad
+
+
+def test_training_step_full_size_matches_oracle_and_fp32_path(B, orc):
     # the 2->6x128 training workload at its full batch (65536 points): every
-    # layer's BF16 tensor-core gradient against the FP32 CUDA-core gradient of the
-    # same batch (itself held to the oracle at small sizes), the per-layer bound
-    # of the BF16 tests
+    # layer's BF16 tensor-core gradient against the oracle's FP64 gradient of
+    # the whole batch and against the FP32 CUDA-core gradient of the same batch,
+    # with the per-layer bound of the BF16 tests
     widths = [2] + [128] * 6 + [1]
     nb = 65536 // 32
     X, kind = synth.collocation(0, 65536 - 2 * nb, nb, nb, 4.0, 1.0)
@@ -192,14 +222,19 @@ def test_training_step_full_size_matches_fp32_path(B):
     l32, g32 = m.loss_grad(Xd, kd, prob, 0.0, prec=B.FP32)
     assert m.device_status() == B.BS_OK
     l16, g16, l32, g32 = (v.cpu().numpy() for v in (l16, g16, l32, g32))
+    om = orc.MLP(widths, synth.xavier_params(widths, 0), [0.0, 0.0], [4.0, 1.0])
+    l64, g64 = _oracle_loss_grad_threaded(orc, om, X, kind, prob, 0.0)
     for c in range(3):
-        assert abs(l16[c] - l32[c]) <= 5e-2 * abs(l32[c]), (c, l16[c], l32[c])
+        assert abs(l16[c] - l64[c]) <= 5e-2 * abs(l64[c]), (c, l16[c], l64[c])
+        assert abs(l32[c] - l64[c]) <= 1e-4 * abs(l64[c]), (c, l32[c], l64[c])
     off = 0
     for l in range(1, len(widths)):
         for n in (widths[l] * widths[l - 1], widths[l]):
-            a, b = g16[off:off + n], g32[off:off + n]
+            a, b, ref = g16[off:off + n], g32[off:off + n], g64[off:off + n]
+            assert _rel(a, ref) <= 2e-2, (l, n, _rel(a, ref))
             assert _rel(a, b) <= 2e-2, (l, n, _rel(a, b))
             off += n
+    assert _rel(g32, g64) <= 1e-4
 
 
 def test_training_batch_above_the_default_chunk(B, monkeypatch):

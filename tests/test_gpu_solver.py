@@ -301,3 +301,26 @@ def test_single_slice_and_single_step_degenerate_cases(B, orc):
         assert torch.equal(U, Uf)
         ref = orc.serial_fine(_oparams(orc, cfg))
         _close(Uf.cpu().numpy(), ref.ravel(), _kappa_tol(cfg, "fine", cfg["P"]))
+
+
+@pytest.mark.parametrize("Nx,steps", [(1025, 6), (65536, 48)])
+def test_stress_case_no_farther_from_long_double_than_the_oracle(B, orc, Nx, steps):
+    # noisy input at a large mesh ratio: the oracle's own FP64 rounding is what
+    # the calibrated bound covers, so the GPU result is held directly to a
+    # long-double recomputation and must be no farther from it than the oracle
+    from _longdouble import cn_longdouble
+
+    K = 1.7
+    cfg = dict(K=K, sigma=0.37, r=0.01, T=1.6, Smax=4 * K, Nx=Nx, P=3, fine_steps=steps, coarse_steps=1)
+    p = _oparams(orc, cfg)
+    S = synth.random_states(111, 1, Nx, scale=cfg["Smax"])[0]
+    S[0], S[-1] = 0.0, orc.right_bc(p, 0.0)
+    ref = cn_longdouble(p, 0, S)
+    scale = float(np.abs(ref).max())
+    e_orc = float(np.abs(orc.fine(p, 0, S) - ref).max()) / scale
+    prob = B.Problem(cfg)
+    Uin = torch.zeros(prob.total_slice, dtype=torch.float64, device="cuda")
+    Uin[:Nx] = torch.tensor(S, device="cuda")
+    got = prob.fine_propagate(Uin)[:Nx].cpu().numpy()
+    e_gpu = float(np.abs(got - ref).max()) / scale
+    assert e_gpu <= e_orc, (e_gpu, e_orc)
