@@ -63,9 +63,10 @@ FLOPS_PER_PT_STEP = 11.0  # CN right-hand side 5 + factored solve 6 (algorithmic
 # partition without a capture of its current code reports null
 FINE_TRAFFIC_BYTES = {(2, 4, 4): 425216}
 # DRAM bytes (read + write) of one fine propagation of every slice of the batched
-# workload per interior grid point and slice (all partition classes, profiles/),
-# or None while no capture of the current code exists
-BATCH_TRAFFIC_PER_PT_SLICE = None
+# workload per grid point and slice (all partition classes; captured on the
+# batch's first 512 instances, profiles/), or None while no capture of the
+# current code exists
+BATCH_TRAFFIC_PER_PT_SLICE = 13.67
 
 
 def _peaks():
@@ -445,7 +446,7 @@ def run_ours(args):
     # hold its GPU meanwhile, and the baseline belongs to rank 0 at N = 1)
     single = pinn = train3 = cpu = None
     if ws == 1:
-        cpu = oracle_sample(insts, PNET_WIDTHS, w_host, PNET_LO, PNET_HI, "pinn_ie", tol, args.cpu_seconds)
+        cpu = oracle_sample(insts, PNET_WIDTHS, w_host, PNET_LO, PNET_HI, "pinn_ie", tol, args.cpu_seconds)[0]
         del graph
         torch.cuda.empty_cache()
         single = single_leg(B, torch, args) if args.single else None
@@ -641,6 +642,40 @@ def run_fine_only(args):
     pt = (CFG["Nx"] - 2) * CFG["fine_steps"] * CFG["P"]
     print(json.dumps({"mode": "fine", "ms": ms, "grid_pt_steps_per_s": pt / (ms * 1e-3),
                       "tflops_algorithmic": FLOPS_PER_PT_STEP * pt / (ms * 1e-3) / 1e12}), flush=True)
+
+
+def run_fine_batched(args):
+    """The dominant kernel of the headline alone: fine_propagate over every slice of
+    the first --instances instances of the batched workload (autotuned partitions,
+    one persistent launch per partition class), CUDA events (profiling)."""
+    import torch
+
+    from paper_2303_03848_b300 import binding as B
+    from paper_2303_03848_b300 import build as BUILD
+
+    BUILD.build()
+    insts = shard_instances(1, 0)[:args.instances]
+    prob = B.Problem(insts, tuned=True)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(0)
+    Uin = torch.rand(prob.total_slice, dtype=torch.float64, device="cuda", generator=gen)
+    Fo = torch.empty_like(Uin)
+    for _ in range(args.warmup):
+        prob.fine_propagate(Uin, Fo)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for a, b in ev:
+        a.record()
+        prob.fine_propagate(Uin, Fo)
+        b.record()
+    torch.cuda.synchronize()
+    assert prob.device_status() == B.BS_OK
+    ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    pt = sum((p["Nx"] - 2) * p["fine_steps"] * p["P"] for p in insts)
+    peak = 148 * 2 * 2 * float(_peaks().get("sm_max_mhz", 2032.0)) * 1e6 / 1e12
+    tf = FLOPS_PER_PT_STEP * pt / (ms * 1e-3) / 1e12
+    print(json.dumps({"mode": "finebatch", "instances": len(insts), "ms": ms, "grid_pt_steps_per_s": pt / (ms * 1e-3),
+                      "tflops_algorithmic": tf, "frac_of_fp64_peak": tf / peak,
+                      "sum_nx_p": sum(p["Nx"] * p["P"] for p in insts)}), flush=True)
 
 
 def batched_leg(B, torch, n_inst=4096, solve=True, rule_too=False, pinn_solve=False, cpu_seconds=10.0):
@@ -1136,6 +1171,8 @@ def oracle_sample(insts, widths, weights, lo, hi, kind: str, tol: float, budget_
     fine point-steps), so the batch time on these cores is extrapolated as
     (sum of the sampled solves' seconds / sum of their Nx) x sum of the batch's
     Nx / threads.  Returns the cpu_baseline record and the next start index."""
+    if budget_s <= 0:
+        return None, start
     import oracle as orc
 
     orc.build()
@@ -1235,8 +1272,8 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=8.0, help="oracle budget per step of --impl reference")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="oracle budget of the cpu_baseline")
     ap.add_argument("--mode", default="solve",
-                    choices=["solve", "single", "fine", "batched", "large", "pinn", "train", "sweep", "generalize",
-                             "datacoarse"],
+                    choices=["solve", "single", "fine", "finebatch", "batched", "large", "pinn", "train", "sweep",
+                             "generalize", "datacoarse"],
                     help="fine / batched: only the fine propagator on all slices of the benchmark / "
                          "batched workload (profiling)")
     ap.add_argument("--batched", type=int, default=1, help="include the batched-workload leg (1/0)")
@@ -1248,6 +1285,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.mode == "fine":
         run_fine_only(args)
+    elif args.mode == "finebatch":
+        run_fine_batched(args)
     elif args.mode == "single":
         import torch
 
