@@ -941,7 +941,8 @@ def generalize_leg(B, torch, train_steps, sigmas=(0.2, 0.3, 0.4, 0.5), rs=(0.01,
             prob = B.Problem(cfg)
             Uf = prob.serial_fine()
             row = {"sigma": sigma, "r": r, "table_err_vs_serial_fine": rel_error(table, Uf, CFG["P"], CFG["Nx"])}
-            for name, kind, mdl in (("pinn", B.COARSE_PINN, model), ("ie", B.COARSE_IE, None)):
+            for name, kind, mdl in (("pinn", B.COARSE_PINN, model), ("pinn_ie", B.COARSE_PINN_IE, model),
+                                    ("ie", B.COARSE_IE, None)):
                 row[name] = []
                 for tol in tols:
                     U, _, stats, rc = prob.parareal_solve(kind, model=mdl, prec=B.BF16, tol=tol, max_iter=CFG["P"])
@@ -977,7 +978,9 @@ def data_coarse_leg(B, torch, train_steps, tols=(1e-2, 1e-3, 1e-4, 1e-6)):
            "data_training": {"points": int(Xg.shape[0]), "steps": train_steps, "precision": "bf16 (tcgen05)",
                              "data_mse_first": loss0[0], "data_mse_last": loss1[0]},
            "pinn_training": tr, "coarse": {}}
-    for name, kind, mdl in (("data-nn", B.COARSE_PINN, dnet), ("pinn", B.COARSE_PINN, pinn), ("ie", B.COARSE_IE, None)):
+    for name, kind, mdl in (("data-nn", B.COARSE_PINN, dnet), ("pinn", B.COARSE_PINN, pinn),
+                            ("data-nn_ie", B.COARSE_PINN_IE, dnet), ("pinn_ie", B.COARSE_PINN_IE, pinn),
+                            ("ie", B.COARSE_IE, None)):
         row = {}
         if mdl is not None:
             row["table_err_vs_serial_fine"] = rel_error(mdl.eval(Xg, prec=B.BF16), Uf, CFG["P"], CFG["Nx"])
@@ -1027,7 +1030,8 @@ def sweep_leg(B, torch, model, Ps=(4, 8, 16, 32, 64), total_steps=32768):
         c_c = timed(lambda: prob.coarse_propagate(U0, Fo))
         row = {"P": P, "fine_steps_per_slice": cfg["fine_steps"], "serial_fine_ms": serial_ms, "c_f_ms": c_f,
                "c_c_ms": c_c}
-        for name, kind, mdl in (("ie", BB.COARSE_IE, None), ("pinn", BB.COARSE_PINN, model)):
+        for name, kind, mdl in (("ie", BB.COARSE_IE, None), ("pinn", BB.COARSE_PINN, model),
+                                ("pinn_ie", BB.COARSE_PINN_IE, model)):
             tol = None
             for cand in (1e-6, 1e-7, 1e-8, 1e-9, 1e-10, 0.0):
                 U, norms, stats, rc = prob.parareal_solve(kind, model=mdl, prec=BB.BF16, tol=cand)
@@ -1110,6 +1114,39 @@ def run_large(args):
             "tensor_tflops": 7 * 2 * 256 * 256 * Xg.shape[0] / (table_ms * 1e-3) / 1e12,
             "tflops_algorithmic": flops_pt * Xg.shape[0] / (table_ms * 1e-3) / 1e12,
             "status": net.device_status()}
+    # the network-anchored coarse propagator with this network (trained on the
+    # CUDA cores in FP32: the tensor-core training covers widths up to 128),
+    # Parareal to 1e-8 against serial fine, each candidate tolerance timed
+    if args.large_train_steps > 0:
+        from paper_2303_03848_b300 import synth
+
+        n_pts = 8192
+        Xc, kc = synth.collocation(5, n_pts - n_pts // 8, n_pts // 16, n_pts // 16, cfg["Smax"], cfg["T"])
+        Xcd, kcd = torch.tensor(Xc, device="cuda"), torch.tensor(kc, device="cuda")
+        a, b = ev()
+        a.record()
+        first = net.train_step(Xcd, kcd, cfg, lr=1e-3, prec=B.FP32, want_loss=True)
+        for i in range(1, args.large_train_steps - 1):
+            net.train_step(Xcd, kcd, cfg, lr=1e-3 if i < 0.75 * args.large_train_steps else 1e-4, prec=B.FP32)
+        last = net.train_step(Xcd, kcd, cfg, lr=1e-4, prec=B.FP32, want_loss=True)
+        b.record()
+        torch.cuda.synchronize()
+        pinn["training"] = {"steps": args.large_train_steps, "points": n_pts, "precision": "fp32 (CUDA cores)",
+                            "s": a.elapsed_time(b) * 1e-3, "loss_first": first, "loss_last": last}
+        pinn["table_err_vs_serial_fine"] = rel_error(net.eval(Xg, prec=B.BF16), Uf, cfg["P"], cfg["Nx"])
+        for p_tol in (1e-7, 3e-8, 1e-8, 3e-9, 1e-9, 1e-10, 0.0):
+            a, b = ev()
+            a.record()
+            U, norms, st_p, rc_p = prob.parareal_solve(B.COARSE_PINN_IE, model=net, prec=B.BF16, tol=p_tol,
+                                                       max_iter=cfg["P"])
+            b.record()
+            torch.cuda.synchronize()
+            err_p = rel_error(U, Uf, cfg["P"], cfg["Nx"])
+            if err_p <= target:
+                break
+        pinn["pinn_ie"] = {"tol": p_tol, "iterations": st_p[0]["iterations"], "solve_ms": a.elapsed_time(b),
+                           "err_vs_serial_fine": err_p, "speedup_vs_serial_fine": serial_ms / a.elapsed_time(b),
+                           "status": rc_p}
     # the oracle on one host core: consecutive slices of serial fine for about
     # cpu_seconds, extrapolated to all P slices
     cpu = None
@@ -1280,6 +1317,8 @@ def main():
     ap.add_argument("--instances", type=int, default=4096, help="instances of --mode batched")
     ap.add_argument("--large-p", type=int, default=256, help="slices of --mode large")
     ap.add_argument("--large-steps", type=int, default=4096, help="CN steps per slice of --mode large")
+    ap.add_argument("--large-train-steps", type=int, default=300,
+                    help="FP32 training steps of --mode large's 2->8x256 network (0: untrained, no network solve)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
