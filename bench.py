@@ -56,7 +56,7 @@ WORKLOAD = ("batched BS calls: 4096 seeded instances K~U[0.5,2] sigma~U[0.1,0.5]
             "Smax=4K Nx~U{256..4096}, P=64, CN 256 steps/slice FP64; coarse = network-anchored implicit Euler "
             "with the parametric 5->6x128 tanh network (BF16 table on tcgen05); whole solve one CUDA graph")
 SINGLE_WORKLOAD = ("single BS call K=1 sigma=0.2 r=0.05 T=1, Nx=1024 S in [0,4], P=32, CN 1024 steps/slice FP64, "
-                   "MLP 2->4x64 tanh trained 5k BF16 Adam steps on 16384+1024 points")
+                   "MLP 2->4x64 tanh trained 20k BF16 Adam steps on 16384+1024 points")
 FLOPS_PER_PT_STEP = 11.0  # CN right-hand side 5 + factored solve 6 (algorithmic, per interior point-step)
 # DRAM bytes (read + write) of one fine_propagate launch over the 32 slices of the
 # single-instance workload, from one ncu capture per partition (profiles/); a
@@ -182,10 +182,11 @@ def rel_error(U, Uref, P, Nx):
     return float(((a - b).norm(dim=1) / b.norm(dim=1)).max().item())
 
 
-def train_network(B, torch, steps, seed=0, prec=None, params=None):
-    """The benchmark network: full-batch Adam on the collocation set, BF16 operands on
-    the tensor cores (FP32 accumulation, FP64 master weights) unless prec says otherwise;
-    params: the problem whose PDE the loss takes (default: the benchmark's)."""
+def train_network(B, torch, steps, seed=0, prec=None, params=None, decay_at=0.75):
+    """The single-instance network: full-batch Adam on the collocation set, BF16 operands
+    on the tensor cores (FP32 accumulation, FP64 master weights) unless prec says
+    otherwise, step size 1e-3 and 1e-4 from decay_at x steps; params: the problem whose
+    PDE the loss takes (default: the single-instance workload's)."""
     from paper_2303_03848_b300 import synth
 
     prec = B.BF16 if prec is None else prec
@@ -200,14 +201,15 @@ def train_network(B, torch, steps, seed=0, prec=None, params=None):
     for i in range(1, steps):
         if i == steps - timed:
             e0.record()
-        m.train_step(Xd, kd, cfg, lr=1e-3, prec=prec)
+        m.train_step(Xd, kd, cfg, lr=1e-3 if i < decay_at * steps else 1e-4, prec=prec)
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / timed if steps > 1 else float("nan")
-    loss1 = m.train_step(Xd, kd, cfg, lr=1e-3, prec=prec, want_loss=True)
+    loss1 = m.train_step(Xd, kd, cfg, lr=1e-4, prec=prec, want_loss=True)
     name = {B.FP64: "fp64", B.FP32: "fp32", B.BF16: "bf16 (tcgen05)"}[prec]
-    return m, dict(steps=steps, precision=name, ms_per_step=ms, points=len(kind), loss_first=loss0,
-                   loss_last=loss1, points_per_s=len(kind) / (ms * 1e-3) if ms == ms else None)
+    return m, dict(steps=steps, precision=name, lr=f"1e-3, 1e-4 from step {int(decay_at * steps)}", ms_per_step=ms,
+                   points=len(kind), loss_first=loss0, loss_last=loss1,
+                   points_per_s=len(kind) / (ms * 1e-3) if ms == ms else None)
 
 
 def choose_tol(prob, kind, model, prec, Uf, B):
@@ -513,7 +515,7 @@ def run_ours(args):
 
 def single_leg(B, torch, args):
     """The single-instance workload (Nx=1024, P=32, 1024 CN steps per slice, the
-    2->4x64 network trained 5000 BF16 steps): every coarse kind to 1e-6 against
+    2->4x64 network trained 20000 BF16 steps): every coarse kind to 1e-6 against
     serial fine (graph-replayed solves), the network-anchored kind per table
     precision, the solve by phase, the fine kernel's roofline and the oracle's
     whole solves on one host core."""
@@ -790,7 +792,7 @@ def batched_leg(B, torch, n_inst=4096, solve=True, rule_too=False, pinn_solve=Fa
     return out
 
 
-def train_parametric(B, torch, steps=16000, n_points=65536, decay_at=0.75):
+def train_parametric(B, torch, steps=32000, n_points=65536, decay_at=0.75):
     """The batched workload's coarse network 5->6x128 tanh on (S, tau, sigma, r, K):
     BF16 full-batch Adam on seeded collocation points over the batch's parameter box
     (S in [0, 4K], tau in [0, 2]), step size 1e-3, then 1e-4 from decay_at x steps."""
@@ -969,9 +971,9 @@ def data_coarse_leg(B, torch, train_steps, tols=(1e-2, 1e-3, 1e-4, 1e-6)):
     kd = torch.full((Xg.shape[0],), 4, dtype=torch.int8, device="cuda")
     dnet = B.PinnModel(WIDTHS, [0.0, 0.0], [CFG["Smax"], CFG["T"]], seed=0)
     loss0 = dnet.train_step(Xg, kd, CFG, lr=1e-3, prec=B.BF16, want_loss=True, y=Uf)
-    for _ in range(1, train_steps):
-        dnet.train_step(Xg, kd, CFG, lr=1e-3, prec=B.BF16, y=Uf)
-    loss1 = dnet.train_step(Xg, kd, CFG, lr=1e-3, prec=B.BF16, want_loss=True, y=Uf)
+    for i in range(1, train_steps):  # the PINN's schedule (train_network)
+        dnet.train_step(Xg, kd, CFG, lr=1e-3 if i < 0.75 * train_steps else 1e-4, prec=B.BF16, y=Uf)
+    loss1 = dnet.train_step(Xg, kd, CFG, lr=1e-4, prec=B.BF16, want_loss=True, y=Uf)
     pinn, tr = train_network(B, torch, train_steps)
     out = {"mode": "datacoarse", "grid": "Nx=1024, S in [0,4], K=1 sigma=0.2 r=0.05 T=1, P=32, 1024 CN steps per slice",
            "network": "2->4x64 tanh, BF16 table",
@@ -1303,8 +1305,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="bf16", choices=["fp64", "fp32", "tf32", "bf16"])
-    ap.add_argument("--train-steps", type=int, default=5000, help="training steps of the single-instance network")
-    ap.add_argument("--pnet-steps", type=int, default=16000, help="training steps of the batched workload's network")
+    ap.add_argument("--train-steps", type=int, default=20000, help="training steps of the single-instance network")
+    ap.add_argument("--pnet-steps", type=int, default=32000, help="training steps of the batched workload's network")
     ap.add_argument("--single", type=int, default=1, help="include the single-instance leg (1/0)")
     ap.add_argument("--ref-seconds", type=float, default=8.0, help="oracle budget per step of --impl reference")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="oracle budget of the cpu_baseline")
