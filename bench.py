@@ -792,7 +792,7 @@ def batched_leg(B, torch, n_inst=4096, solve=True, rule_too=False, pinn_solve=Fa
     return out
 
 
-def train_parametric(B, torch, steps=32000, n_points=65536, decay_at=0.75):
+def train_parametric(B, torch, steps=16000, n_points=65536, decay_at=0.75):
     """The batched workload's coarse network 5->6x128 tanh on (S, tau, sigma, r, K):
     BF16 full-batch Adam on seeded collocation points over the batch's parameter box
     (S in [0, 4K], tau in [0, 2]), step size 1e-3, then 1e-4 from decay_at x steps."""
@@ -1306,7 +1306,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="bf16", choices=["fp64", "fp32", "tf32", "bf16"])
     ap.add_argument("--train-steps", type=int, default=20000, help="training steps of the single-instance network")
-    ap.add_argument("--pnet-steps", type=int, default=32000, help="training steps of the batched workload's network")
+    ap.add_argument("--pnet-steps", type=int, default=16000, help="training steps of the batched workload's network")
     ap.add_argument("--single", type=int, default=1, help="include the single-instance leg (1/0)")
     ap.add_argument("--ref-seconds", type=float, default=8.0, help="oracle budget per step of --impl reference")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="oracle budget of the cpu_baseline")
