@@ -680,6 +680,55 @@ def run_fine_batched(args):
                       "sum_nx_p": sum(p["Nx"] * p["P"] for p in insts)}), flush=True)
 
 
+def crossover_leg(B, torch, sizes=(8, 32, 128, 512, 1024, 2048, 4096), pnet_steps=16000):
+    """Where Parareal pays on one GPU: the first n instances of the seeded batch for
+    growing n, serial fine against network-anchored and IE-coarse Parareal to 1e-6
+    (graph-replayed solves, the loosest device tolerance within 1e-6 of serial fine).
+    Few instances leave most SMs idle under serial fine (one cluster per instance,
+    slices in sequence), so the slices' parallelism pays; thousands of instances
+    fill the GPU without it, and Parareal's extra fine work only costs."""
+    insts_all = shard_instances(1, 0)
+    net, tr = train_parametric(B, torch, steps=pnet_steps)
+    rows = []
+
+    def graph_ms(g):
+        g.replay()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        g.replay()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b)
+
+    for n in sizes:
+        insts = insts_all[:n]
+        prob = B.Problem(insts, tuned=True)
+        Uf = prob.serial_fine()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        prob.serial_fine(Uf)
+        b.record()
+        torch.cuda.synchronize()
+        row = {"instances": n, "serial_fine_ms": a.elapsed_time(b)}
+        for name, kind, mdl in (("pinn_ie", B.COARSE_PINN_IE, net), ("ie", B.COARSE_IE, None)):
+            for tol in (1e-6, 3e-7, 1e-7, 3e-8, 1e-8, 0.0):
+                U, _, stats, rc = prob.parareal_solve(kind, model=mdl, prec=B.BF16, tol=tol, max_iter=64)
+                err = float(batch_errors(prob, U, Uf, torch).max())
+                del U
+                if err <= TARGET:
+                    break
+            g = B.SolveGraph(prob, kind, model=mdl, prec=B.BF16, tol=tol, max_iter=64)
+            ms = graph_ms(g)
+            del g
+            its = [st["iterations"] for st in stats]
+            row[name] = {"tol": tol, "ms": ms, "iterations_mean": sum(its) / len(its), "speedup": row["serial_fine_ms"] / ms}
+        rows.append(row)
+        prob.close()
+        torch.cuda.empty_cache()
+    return {"mode": "crossover", "network_training": tr, "rows": rows}
+
+
 def batched_leg(B, torch, n_inst=4096, solve=True, rule_too=False, pinn_solve=False, cpu_seconds=10.0):
     """Batched workload: n_inst instances (K, sigma, r, T, Nx seeded), P=64, CN 256 steps/slice.
 
@@ -1311,8 +1360,8 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=8.0, help="oracle budget per step of --impl reference")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="oracle budget of the cpu_baseline")
     ap.add_argument("--mode", default="solve",
-                    choices=["solve", "single", "fine", "finebatch", "batched", "large", "pinn", "train", "sweep",
-                             "generalize", "datacoarse"],
+                    choices=["solve", "single", "fine", "finebatch", "batched", "crossover", "large", "pinn", "train",
+                             "sweep", "generalize", "datacoarse"],
                     help="fine / batched: only the fine propagator on all slices of the benchmark / "
                          "batched workload (profiling)")
     ap.add_argument("--batched", type=int, default=1, help="include the batched-workload leg (1/0)")
@@ -1328,6 +1377,14 @@ def main():
         run_fine_only(args)
     elif args.mode == "finebatch":
         run_fine_batched(args)
+    elif args.mode == "crossover":
+        import torch
+
+        from paper_2303_03848_b300 import binding as B
+        from paper_2303_03848_b300 import build as BUILD
+
+        BUILD.build()
+        print(json.dumps(crossover_leg(B, torch, pnet_steps=args.pnet_steps)), flush=True)
     elif args.mode == "single":
         import torch
 
