@@ -80,68 +80,195 @@ __device__ __forceinline__ void input_streams(const MlpDev& m, const double* x, 
 }
 
 // ---------------------------------------------------------------------------
-// Evaluation: one thread per point, activation columns in shared memory.
+// Evaluation on CUDA cores as one tiled GEMM per layer.  A CTA of 256 threads
+// takes a tile of 64 rows: 64 points, or 16 points x 4 derivative streams with
+// the streams of a point on 4 adjacent rows, so that the thread that holds a
+// point's four rows forms h_S, h_SS, h_tau of its neurons in registers.  The
+// tile's activations live in shared memory neuron-major ([w][64 + 4]: the 4
+// rows a thread needs at one k are one vector load); a layer's weights are
+// staged transposed ([k][o], 32 values of k at a time, zero-padded to 16 RN
+// outputs, rows padded by 4 against bank conflicts), read from global memory
+// along k so that a warp's loads are contiguous.  Thread (row group rg, column group cg) accumulates the 4 x RN
+// block rows 4 rg .. + 3, outputs RN cg .. + RN - 1 over k -- per k one vector
+// load of its rows' activations and RN / 4 (FP32) or RN / 2 (FP64) vector
+// loads of weights for 4 RN FMAs -- then writes tanh of the block back over
+// the tile once every thread has read it.  The output layer (w -> 1) is a dot
+// product per row, four threads a row.
 // ---------------------------------------------------------------------------
-template <typename Tp, int RND, int NS>
-__global__ void mlp_eval_kernel(MlpDev m, const double* __restrict__ X, int64_t N, double* __restrict__ u,
-                                double* __restrict__ derivs) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  Tp* sh = reinterpret_cast<Tp*>(smraw);
-  const int TP = blockDim.x, tid = threadIdx.x, W = m.max_w;
-  const int64_t p = (int64_t)blockIdx.x * TP + tid;
-  const bool valid = p < N;
-  // buffers [buf][stream][i][tid]
-  auto col = [&](int buf, int s, int i) -> Tp& { return sh[(((int64_t)buf * NS + s) * W + i) * TP + tid]; };
-  double xin[8];
-  for (int i = 0; i < m.d_in; ++i) xin[i] = valid ? X[p * m.d_in + i] : 0.0;
-  if (NS == 4)
-    input_streams<Tp>(m, xin, &col(0, 0, 0), &col(0, 1, 0), &col(0, 2, 0), &col(0, 3, 0), TP);
-  else
-    input_streams<Tp>(m, xin, &col(0, 0, 0), (Tp*)nullptr, (Tp*)nullptr, (Tp*)nullptr, TP);
-  if (RND != 0)
-    for (int i = 0; i < m.d_in; ++i) col(0, 0, i) = rop<RND>(col(0, 0, i));
-  const Tp* prm = params_of<Tp>(m);
-  int cur = 0;
-  for (int l = 1; l <= m.n_lin; ++l) {
-    const int wi = m.widths[l - 1], wo = m.widths[l];
-    const Tp* Wl = prm + m.poff[l];
-    const Tp* bl = Wl + (int64_t)wo * wi;
-    const bool last = l == m.n_lin;
-    for (int o = 0; o < wo; ++o) {
-      Tp z = 0, zS = 0, zSS = 0, zT = 0;
-      const Tp* wr = Wl + (int64_t)o * wi;
-      for (int i = 0; i < wi; ++i) {
-        const Tp w = rop<RND>(__ldg(wr + i));
-        z = fma(w, col(cur, 0, i), z);
-        if (NS == 4) {
-          zS = fma(w, col(cur, 1, i), zS);
-          zSS = fma(w, col(cur, 2, i), zSS);
-          zT = fma(w, col(cur, 3, i), zT);
-        }
-      }
-      z += __ldg(bl + o);
-      if (!last) {
-        const Tp t = tanh_t<Tp>(z);
-        col(cur ^ 1, 0, o) = rop<RND>(t);
-        if (NS == 4) {
-          const Tp d1 = (Tp)1 - t * t;
-          col(cur ^ 1, 1, o) = rop<RND>(d1 * zS);
-          col(cur ^ 1, 2, o) = rop<RND>(d1 * zSS - (Tp)2 * t * d1 * zS * zS);
-          col(cur ^ 1, 3, o) = rop<RND>(d1 * zT);
-        }
-      } else if (valid) {
-        u[p] = (double)z;
-        if (NS == 4 && derivs) {
-          derivs[3 * p + 0] = (double)zS;
-          derivs[3 * p + 1] = (double)zSS;
-          derivs[3 * p + 2] = (double)zT;
-        }
-      }
+constexpr int kEvRows = 64;
+constexpr int kEvRS = kEvRows + 4;  // row stride of the neuron-major tile (16-byte aligned, fewer conflicts)
+constexpr int kEvThreads = 256;
+constexpr int kEvKC = 32;
+constexpr int kEvIn = 8;  // input streams per row (d_in <= 8)
+
+template <typename Tp, int RN>
+__device__ __forceinline__ void load_vec(const Tp* __restrict__ p, Tp (&b)[RN]) {
+  if constexpr (sizeof(Tp) == 4 && RN % 4 == 0) {
+#pragma unroll
+    for (int q = 0; q < RN; q += 4) {
+      const float4 v = *reinterpret_cast<const float4*>(p + q);
+      b[q] = v.x;
+      b[q + 1] = v.y;
+      b[q + 2] = v.z;
+      b[q + 3] = v.w;
     }
-    cur ^= 1;
+  } else if constexpr (sizeof(Tp) == 8 && RN % 2 == 0) {
+#pragma unroll
+    for (int q = 0; q < RN; q += 2) {
+      const double2 v = *reinterpret_cast<const double2*>(p + q);
+      b[q] = v.x;
+      b[q + 1] = v.y;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < RN; ++q) b[q] = p[q];
   }
 }
 
+template <typename Tp>
+__device__ __forceinline__ void store4(Tp* p, Tp a, Tp b, Tp c, Tp d) {
+  if constexpr (sizeof(Tp) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+  } else {
+    *reinterpret_cast<double2*>(p) = make_double2(a, b);
+    *reinterpret_cast<double2*>(p + 2) = make_double2(c, d);
+  }
+}
+
+template <typename Tp>
+constexpr size_t eval_smem_bytes(int RN) {
+  return sizeof(Tp) * ((size_t)16 * RN * kEvRS + (size_t)kEvKC * (16 * RN + 4) + (size_t)kEvIn * kEvRS);
+}
+
+template <typename Tp, int RND, int NS, int RN>
+__global__ void __launch_bounds__(kEvThreads) mlp_eval_kernel(MlpDev m, const double* __restrict__ X, int64_t N,
+                                                              double* __restrict__ u, double* __restrict__ derivs) {
+  constexpr int WPAD = 16 * RN, WTS = WPAD + 4, PPT = kEvRows / NS;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  Tp* H = reinterpret_cast<Tp*>(smraw);  // [WPAD][kEvRS] activations of the tile, neuron-major
+  Tp* Wt = H + WPAD * kEvRS;             // [kEvKC][WTS] staged weights, W_l[o][kc + k] at [k][o]
+  Tp* Hin = Wt + kEvKC * WTS;            // [kEvIn][kEvRS] input streams
+  const int tid = threadIdx.x, rg = tid >> 4, cg = tid & 15;
+  const int r0 = rg * 4, c0 = cg * RN;
+  const int64_t p0 = (int64_t)blockIdx.x * PPT;
+  // input streams: the value x^ = affine map to [-1, 1], d/dS = (sc_0, 0, ...),
+  // d2/dS2 = 0, d/dtau = (0, sc_1, 0, ...)
+  for (int i = tid; i < kEvIn * kEvRows; i += kEvThreads) {
+    const int k = i / kEvRows, r = i % kEvRows;
+    const int pr = r / NS, st = r % NS;
+    const int64_t p = p0 + pr;
+    Tp v = (Tp)0;
+    if (k < m.d_in && p < N) {
+      const double sc = 2.0 / (m.hi[k] - m.lo[k]);
+      if (st == 0) v = rop<RND>((Tp)(sc * (X[p * m.d_in + k] - m.lo[k]) - 1.0));
+      else if (st == 1) v = k == 0 ? (Tp)sc : (Tp)0;
+      else if (st == 3) v = k == 1 ? (Tp)sc : (Tp)0;
+    }
+    Hin[k * kEvRS + r] = v;
+  }
+  const Tp* prm = params_of<Tp>(m);
+  for (int l = 1; l < m.n_lin; ++l) {  // hidden layers
+    const int wi = m.widths[l - 1], wo = m.widths[l];
+    const Tp* Wl = prm + m.poff[l];
+    const Tp* bl = Wl + (int64_t)wo * wi;
+    const Tp* Hs = l == 1 ? Hin : H;
+    Tp acc[4][RN];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int q = 0; q < RN; ++q) acc[r][q] = (Tp)0;
+    for (int kc = 0; kc < wi; kc += kEvKC) {
+      const int kn = wi - kc < kEvKC ? wi - kc : kEvKC;
+      __syncthreads();  // the previous chunk is consumed (and, at kc = 0, the tile written)
+      for (int i = tid; i < kEvKC * WPAD; i += kEvThreads) {
+        const int o = i / kEvKC, k = i % kEvKC;
+        Wt[k * WTS + o] = (k < kn && o < wo) ? rop<RND>(Wl[(int64_t)o * wi + kc + k]) : (Tp)0;
+      }
+      __syncthreads();
+      for (int k = 0; k < kn; ++k) {
+        Tp a[4], b[RN];
+        load_vec<Tp, 4>(Hs + (kc + k) * kEvRS + r0, a);
+        load_vec<Tp, RN>(Wt + k * WTS + c0, b);
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int q = 0; q < RN; ++q) acc[r][q] = fma(a[r], b[q], acc[r][q]);
+      }
+    }
+    __syncthreads();  // every thread has read the tile before it is overwritten
+#pragma unroll
+    for (int q = 0; q < RN; ++q) {
+      const int o = c0 + q;
+      const bool ok = o < wo;
+      const Tp bias = ok ? bl[o] : (Tp)0;
+      Tp h[4];
+      if constexpr (NS == 1) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) h[r] = ok ? rop<RND>(tanh_t<Tp>(acc[r][q] + bias)) : (Tp)0;
+      } else {
+        // rows r0 .. r0 + 3: the value and the S, SS, tau streams of one point
+        const Tp z = acc[0][q] + bias, zS = acc[1][q], zSS = acc[2][q], zT = acc[3][q];
+        const Tp t = tanh_t<Tp>(z);
+        const Tp d1 = (Tp)1 - t * t;
+        h[0] = ok ? rop<RND>(t) : (Tp)0;
+        h[1] = ok ? rop<RND>(d1 * zS) : (Tp)0;
+        h[2] = ok ? rop<RND>(d1 * zSS - (Tp)2 * t * d1 * zS * zS) : (Tp)0;
+        h[3] = ok ? rop<RND>(d1 * zT) : (Tp)0;
+      }
+      store4<Tp>(H + o * kEvRS + r0, h[0], h[1], h[2], h[3]);
+    }
+  }
+  __syncthreads();
+  // output layer (w -> 1, linear): four threads per row, a strided quarter each
+  {
+    const int wi = m.widths[m.n_lin - 1];
+    const Tp* Wo = prm + m.poff[m.n_lin];
+    const Tp* Hs = m.n_lin == 1 ? Hin : H;
+    const int row = tid >> 2, part = tid & 3;
+    Tp z = (Tp)0;
+    for (int k = part; k < wi; k += 4) z = fma(rop<RND>(Wo[k]), Hs[k * kEvRS + row], z);
+    z += __shfl_xor_sync(0xffffffffu, z, 1);
+    z += __shfl_xor_sync(0xffffffffu, z, 2);
+    const int64_t p = p0 + row / NS;
+    const int st = row % NS;
+    if (part == 0 && p < N) {
+      if (st == 0) {
+        u[p] = (double)(z + Wo[wi]);
+      } else if (derivs != nullptr) {
+        derivs[3 * p + st - 1] = (double)z;
+      }
+    }
+  }
+}
+
+template <typename Tp, int RND, int NS, int RN>
+static cudaError_t eval_launch_rn(const MlpDev& m, const double* X, int64_t N, double* u, double* derivs,
+                                  cudaStream_t s) {
+  const size_t smem = eval_smem_bytes<Tp>(RN);
+  cudaError_t e = cudaFuncSetAttribute(mlp_eval_kernel<Tp, RND, NS, RN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  constexpr int PPT = kEvRows / NS;
+  const int64_t blocks = (N + PPT - 1) / PPT;
+  mlp_eval_kernel<Tp, RND, NS, RN><<<(unsigned)blocks, kEvThreads, smem, s>>>(m, X, N, u, derivs);
+  return cudaGetLastError();
+}
+
+// Output block width: 16 RN >= the widest layer (RN a power of two, up to 16).
+template <typename Tp, int RND, int NS>
+static cudaError_t eval_launch(const MlpDev& m, const double* X, int64_t N, double* u, double* derivs,
+                               cudaStream_t s) {
+  if (m.d_in > kEvIn || m.max_w > 256) return cudaErrorInvalidValue;
+  if (m.max_w <= 16) return eval_launch_rn<Tp, RND, NS, 1>(m, X, N, u, derivs, s);
+  if (m.max_w <= 32) return eval_launch_rn<Tp, RND, NS, 2>(m, X, N, u, derivs, s);
+  if (m.max_w <= 64) return eval_launch_rn<Tp, RND, NS, 4>(m, X, N, u, derivs, s);
+  if (m.max_w <= 128) return eval_launch_rn<Tp, RND, NS, 8>(m, X, N, u, derivs, s);
+  return eval_launch_rn<Tp, RND, NS, 16>(m, X, N, u, derivs, s);
+}
+
+// Points per CTA of the CUDA-core training kernels (one thread per point) whose
+// per-thread shared-memory columns take per_thread bytes: at most 128, within
+// 160 KB.
 static int points_per_cta(size_t per_thread) {
   int TP = (int)((160 * 1024) / per_thread);
   if (TP >= 128) return 128;
@@ -149,20 +276,6 @@ static int points_per_cta(size_t per_thread) {
   int q = 1;
   while (q * 2 <= TP) q *= 2;
   return q;
-}
-
-template <typename Tp, int RND, int NS>
-static cudaError_t eval_launch(const MlpDev& m, const double* X, int64_t N, double* u, double* derivs,
-                               cudaStream_t s) {
-  const size_t per_thread = 2 * (size_t)NS * m.max_w * sizeof(Tp);
-  const int TP = points_per_cta(per_thread);
-  const size_t smem = per_thread * TP;
-  cudaError_t e = cudaFuncSetAttribute(mlp_eval_kernel<Tp, RND, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return e;
-  const int64_t blocks = (N + TP - 1) / TP;
-  mlp_eval_kernel<Tp, RND, NS><<<(unsigned)blocks, TP, smem, s>>>(m, X, N, u, derivs);
-  return cudaGetLastError();
 }
 
 cudaError_t launch_mlp_eval(const MlpDev& m, int prec, const double* X, int64_t N, double* u, double* derivs,
