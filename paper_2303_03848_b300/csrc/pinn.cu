@@ -266,18 +266,6 @@ static cudaError_t eval_launch(const MlpDev& m, const double* X, int64_t N, doub
   return eval_launch_rn<Tp, RND, NS, 16>(m, X, N, u, derivs, s);
 }
 
-// Points per CTA of the CUDA-core training kernels (one thread per point) whose
-// per-thread shared-memory columns take per_thread bytes: at most 128, within
-// 160 KB.
-static int points_per_cta(size_t per_thread) {
-  int TP = (int)((160 * 1024) / per_thread);
-  if (TP >= 128) return 128;
-  if (TP >= 32) return (TP / 32) * 32;
-  int q = 1;
-  while (q * 2 <= TP) q *= 2;
-  return q;
-}
-
 cudaError_t launch_mlp_eval(const MlpDev& m, int prec, const double* X, int64_t N, double* u, double* derivs,
                             cudaStream_t s) {
   if (N <= 0) return cudaSuccess;
@@ -309,15 +297,19 @@ cudaError_t launch_f64_to_f32(const double* src, float* dst, int64_t n, cudaStre
 }
 
 // ---------------------------------------------------------------------------
-// Training: loss (Eqs. 11-14) and its gradient.
+// Training on CUDA cores: loss (Eqs. 11-14) and its gradient.
 //   1. count points per loss term
-//   2. forward per point, storing (t, z_S, z_SS, z_tau) of every hidden layer
-//      and the adjoint seeds dLoss/d(u, u_S, u_SS, u_tau)
-//   3. adjoint per point, storing dLoss/d(z, z_S, z_SS, z_tau) of every layer
-//   4. weight gradient: for every layer a reduction over points and streams of
-//      dz_s (x) h_s, with h_s rebuilt from the stored activations
-// Workspace layout (Tp): act[l][s][o][p] for hidden layers, dz[l][s][o][p] for
-// all layers (the seeds are dz of the output layer).
+//   2. forward (tiled GEMMs as in the evaluation, 16 points x 4 streams per
+//      tile), storing (t, z_S, z_SS, z_tau) of every hidden layer and the
+//      adjoint seeds dLoss/d(u, u_S, u_SS, u_tau)
+//   3. adjoint (tiled GEMMs against W_l, top layer down), storing
+//      dLoss/d(z, z_S, z_SS, z_tau) of every layer
+//   4. weight gradient: for every layer a GEMM over points and streams of
+//      dz_s (x) h_s, h_s rebuilt from the stored activations, split over
+//      chunks of points whose partial sums are added into the gradient
+// Workspace layout (Tp): act[l][p][s][o] for hidden layers, dz[l][p][s][o] for
+// all layers (the seeds are dz of the output layer): a row (p, s) of a layer
+// is its w_l neurons, contiguous.
 // ---------------------------------------------------------------------------
 
 struct TrainLayout {
@@ -389,100 +381,140 @@ __global__ void count_kinds_kernel(const int8_t* __restrict__ kind, int64_t N, u
   }
 }
 
-template <typename Tp, int RND>
-__global__ void train_fwd_kernel(MlpDev m, LossArgs la, TrainLayout TL, Tp* __restrict__ ws,
-                                 const unsigned long long* __restrict__ cnt, double* __restrict__ loss_acc) {
+// Forward of a training step: the evaluation kernel's tiles (16 points x 4
+// streams, rows (p, s) on adjacent rows), storing (t, z_S, z_SS, z_tau) of
+// every hidden neuron, then the loss terms and adjoint seeds per point.
+template <typename Tp, int RND, int RN>
+__global__ void __launch_bounds__(kEvThreads) train_fwd_kernel(MlpDev m, LossArgs la, TrainLayout TL,
+                                                               Tp* __restrict__ ws,
+                                                               const unsigned long long* __restrict__ cnt,
+                                                               double* __restrict__ loss_acc) {
+  constexpr int WPAD = 16 * RN, WTS = WPAD + 4, PPT = kEvRows / 4;
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ double s_acc[3];
-  Tp* sh = reinterpret_cast<Tp*>(smraw);
-  const int TP = blockDim.x, tid = threadIdx.x, W = m.max_w;
+  Tp* H = reinterpret_cast<Tp*>(smraw);  // [WPAD][kEvRS] h of the tile, neuron-major
+  Tp* Wt = H + WPAD * kEvRS;             // [kEvKC][WTS] staged weights
+  Tp* Hin = Wt + kEvKC * WTS;            // [kEvIn][kEvRS] input streams
+  const int tid = threadIdx.x, rg = tid >> 4, cg = tid & 15;
+  const int r0 = rg * 4, c0 = cg * RN;
   const int64_t N = la.N;
-  const int64_t p = (int64_t)blockIdx.x * TP + tid;
-  const bool valid = p < N;
-  auto col = [&](int buf, int s, int i) -> Tp& { return sh[(((int64_t)buf * 4 + s) * W + i) * TP + tid]; };
-  double xin[8];
-  for (int i = 0; i < m.d_in; ++i) xin[i] = valid ? la.X[p * m.d_in + i] : 0.0;
-  input_streams<Tp>(m, xin, &col(0, 0, 0), &col(0, 1, 0), &col(0, 2, 0), &col(0, 3, 0), TP);
-  if (RND != 0)
-    for (int i = 0; i < m.d_in; ++i) col(0, 0, i) = rop<RND>(col(0, 0, i));
+  const int64_t p0 = (int64_t)blockIdx.x * PPT;
+  if (tid < 3) s_acc[tid] = 0.0;
+  for (int i = tid; i < kEvIn * kEvRows; i += kEvThreads) {
+    const int k = i / kEvRows, r = i % kEvRows;
+    const int st = r & 3;
+    const int64_t p = p0 + (r >> 2);
+    Tp v = (Tp)0;
+    if (k < m.d_in && p < N) {
+      const double sc = 2.0 / (m.hi[k] - m.lo[k]);
+      if (st == 0) v = rop<RND>((Tp)(sc * (la.X[p * m.d_in + k] - m.lo[k]) - 1.0));
+      else if (st == 1) v = k == 0 ? (Tp)sc : (Tp)0;
+      else if (st == 3) v = k == 1 ? (Tp)sc : (Tp)0;
+    }
+    Hin[k * kEvRS + r] = v;
+  }
   const Tp* prm = params_of<Tp>(m);
-  int cur = 0;
-  Tp out[4] = {0, 0, 0, 0};
-  for (int l = 1; l <= m.n_lin; ++l) {
+  const int64_t pt = p0 + rg;  // this thread's point (its rows r0 .. r0 + 3 are the point's streams)
+  for (int l = 1; l < m.n_lin; ++l) {
     const int wi = m.widths[l - 1], wo = m.widths[l];
     const Tp* Wl = prm + m.poff[l];
     const Tp* bl = Wl + (int64_t)wo * wi;
-    const bool last = l == m.n_lin;
-    for (int o = 0; o < wo; ++o) {
-      Tp z = 0, zS = 0, zSS = 0, zT = 0;
-      const Tp* wr = Wl + (int64_t)o * wi;
-      for (int i = 0; i < wi; ++i) {
-        const Tp w = rop<RND>(__ldg(wr + i));
-        z = fma(w, col(cur, 0, i), z);
-        zS = fma(w, col(cur, 1, i), zS);
-        zSS = fma(w, col(cur, 2, i), zSS);
-        zT = fma(w, col(cur, 3, i), zT);
+    const Tp* Hs = l == 1 ? Hin : H;
+    Tp acc[4][RN];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int q = 0; q < RN; ++q) acc[r][q] = (Tp)0;
+    for (int kc = 0; kc < wi; kc += kEvKC) {
+      const int kn = wi - kc < kEvKC ? wi - kc : kEvKC;
+      __syncthreads();
+      for (int i = tid; i < kEvKC * WPAD; i += kEvThreads) {
+        const int o = i / kEvKC, k = i % kEvKC;
+        Wt[k * WTS + o] = (k < kn && o < wo) ? rop<RND>(Wl[(int64_t)o * wi + kc + k]) : (Tp)0;
       }
-      z += __ldg(bl + o);
-      if (!last) {
-        const Tp t = tanh_t<Tp>(z);
-        const Tp d1 = (Tp)1 - t * t;
-        col(cur ^ 1, 0, o) = rop<RND>(t);
-        col(cur ^ 1, 1, o) = rop<RND>(d1 * zS);
-        col(cur ^ 1, 2, o) = rop<RND>(d1 * zSS - (Tp)2 * t * d1 * zS * zS);
-        col(cur ^ 1, 3, o) = rop<RND>(d1 * zT);
-        if (valid) {
-          Tp* a = ws + TL.act_off[l];
-          a[(0 * (int64_t)wo + o) * N + p] = t;
-          a[(1 * (int64_t)wo + o) * N + p] = zS;
-          a[(2 * (int64_t)wo + o) * N + p] = zSS;
-          a[(3 * (int64_t)wo + o) * N + p] = zT;
-        }
-      } else {
-        out[0] = z;
-        out[1] = zS;
-        out[2] = zSS;
-        out[3] = zT;
+      __syncthreads();
+      for (int k = 0; k < kn; ++k) {
+        Tp a[4], b[RN];
+        load_vec<Tp, 4>(Hs + (kc + k) * kEvRS + r0, a);
+        load_vec<Tp, RN>(Wt + k * WTS + c0, b);
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int q = 0; q < RN; ++q) acc[r][q] = fma(a[r], b[q], acc[r][q]);
       }
     }
-    cur ^= 1;
-  }
-  // loss terms and seeds
-  double sq[3] = {0.0, 0.0, 0.0};
-  if (valid) {
-    const int kd = la.kind[p];
-    double Ki, si, ri, tgt;
-    point_setup(la, m.d_in, xin, kd, Ki, si, ri, tgt);
-    const double S = xin[0];
-    double gu = 0.0, gS = 0.0, gSS = 0.0, gT = 0.0;
-    if (kd == 0) {
-      const double f = (double)out[3] - 0.5 * si * si * S * S * (double)out[2] - ri * S * (double)out[1] +
-                       ri * (double)out[0];
-      sq[0] = f * f;
-      const double gf = 2.0 * f / (double)cnt[0];
-      gT = gf;
-      gSS = -0.5 * si * si * S * S * gf;
-      gS = -ri * S * gf;
-      gu = ri * gf;
-    } else if (kd == 4 && la.y != nullptr) {  // data point: misfit to its given value, in term 0
-      const double e = (double)out[0] - la.y[p];
-      sq[0] = e * e;
-      gu = 2.0 * e / (double)cnt[0];
-    } else if (kd >= 1 && kd <= 3) {
-      const double e = (double)out[0] - tgt;
-      const int tt = (kd == 3) ? 2 : 1;
-      sq[tt] = e * e;
-      gu = 2.0 * e / (double)cnt[tt];
+    __syncthreads();
+    Tp* act = ws + TL.act_off[l];
+#pragma unroll
+    for (int q = 0; q < RN; ++q) {
+      const int o = c0 + q;
+      const bool ok = o < wo;
+      const Tp z = acc[0][q] + (ok ? bl[o] : (Tp)0), zS = acc[1][q], zSS = acc[2][q], zT = acc[3][q];
+      const Tp t = tanh_t<Tp>(z);
+      const Tp d1 = (Tp)1 - t * t;
+      store4<Tp>(H + o * kEvRS + r0, ok ? rop<RND>(t) : (Tp)0, ok ? rop<RND>(d1 * zS) : (Tp)0,
+                 ok ? rop<RND>(d1 * zSS - (Tp)2 * t * d1 * zS * zS) : (Tp)0, ok ? rop<RND>(d1 * zT) : (Tp)0);
+      if (ok && pt < N) {
+        act[(pt * 4 + 0) * wo + o] = t;
+        act[(pt * 4 + 1) * wo + o] = zS;
+        act[(pt * 4 + 2) * wo + o] = zSS;
+        act[(pt * 4 + 3) * wo + o] = zT;
+      }
     }
-    Tp* dz = ws + TL.dz_off[m.n_lin];
-    dz[0 * N + p] = (Tp)gu;
-    dz[1 * N + p] = (Tp)gS;
-    dz[2 * N + p] = (Tp)gSS;
-    dz[3 * N + p] = (Tp)gT;
   }
-  // block sum through shared atomics (the CTA may be narrower than a warp)
-  if (tid == 0) s_acc[0] = s_acc[1] = s_acc[2] = 0.0;
   __syncthreads();
+  // output layer (w -> 1, linear): four threads per row; the four rows of a
+  // point end on lanes base, base + 4, base + 8, base + 12 of its 16 threads
+  double sq[3] = {0.0, 0.0, 0.0};
+  {
+    const int wi = m.widths[m.n_lin - 1];
+    const Tp* Wo = prm + m.poff[m.n_lin];
+    const Tp* Hs = m.n_lin == 1 ? Hin : H;
+    const int row = tid >> 2, part = tid & 3;
+    Tp z = (Tp)0;
+    for (int k = part; k < wi; k += 4) z = fma(rop<RND>(Wo[k]), Hs[k * kEvRS + row], z);
+    z += __shfl_xor_sync(0xffffffffu, z, 1);
+    z += __shfl_xor_sync(0xffffffffu, z, 2);
+    const int base = (tid & 31) & ~15;
+    Tp out[4];
+#pragma unroll
+    for (int st = 0; st < 4; ++st) out[st] = __shfl_sync(0xffffffffu, z, base + 4 * st);
+    out[0] += Wo[wi];
+    const int64_t p = p0 + (tid >> 4);
+    if ((tid & 15) == 0 && p < N) {
+      const int kd = la.kind[p];
+      double xin[8];
+      for (int i = 0; i < m.d_in; ++i) xin[i] = la.X[p * m.d_in + i];
+      double Ki, si, ri, tgt;
+      point_setup(la, m.d_in, xin, kd, Ki, si, ri, tgt);
+      const double S = xin[0];
+      double gu = 0.0, gS = 0.0, gSS = 0.0, gT = 0.0;
+      if (kd == 0) {
+        const double f = (double)out[3] - 0.5 * si * si * S * S * (double)out[2] - ri * S * (double)out[1] +
+                         ri * (double)out[0];
+        sq[0] = f * f;
+        const double gf = 2.0 * f / (double)cnt[0];
+        gT = gf;
+        gSS = -0.5 * si * si * S * S * gf;
+        gS = -ri * S * gf;
+        gu = ri * gf;
+      } else if (kd == 4 && la.y != nullptr) {  // data point: misfit to its given value, in term 0
+        const double e = (double)out[0] - la.y[p];
+        sq[0] = e * e;
+        gu = 2.0 * e / (double)cnt[0];
+      } else if (kd >= 1 && kd <= 3) {
+        const double e = (double)out[0] - tgt;
+        const int tt = (kd == 3) ? 2 : 1;
+        sq[tt] = e * e;
+        gu = 2.0 * e / (double)cnt[tt];
+      }
+      Tp* dz = ws + TL.dz_off[m.n_lin];
+      dz[p * 4 + 0] = (Tp)gu;
+      dz[p * 4 + 1] = (Tp)gS;
+      dz[p * 4 + 2] = (Tp)gSS;
+      dz[p * 4 + 3] = (Tp)gT;
+    }
+  }
   if (sq[0] != 0.0) atomicAdd(&s_acc[0], sq[0]);
   if (sq[1] != 0.0) atomicAdd(&s_acc[1], sq[1]);
   if (sq[2] != 0.0) atomicAdd(&s_acc[2], sq[2]);
@@ -494,38 +526,68 @@ __global__ void train_fwd_kernel(MlpDev m, LossArgs la, TrainLayout TL, Tp* __re
   }
 }
 
-// Adjoint per point: dz of layer l -> dz of layer l-1 through W_l^T and tanh.
-template <typename Tp, int RND>
-__global__ void train_bwd_kernel(MlpDev m, int64_t N, TrainLayout TL, Tp* __restrict__ ws) {
+// Adjoint of a training step, top layer down, on the same tiles: the dz of
+// layer l (neuron-major in shared memory, the GEMM's A) times W_l gives
+// ah = W_l^T dz for the 4 streams of each point; the thread holding a point's
+// rows combines them with that point's stored (t, z_S, z_SS, z_tau) into the
+// dz of layer l - 1, written to the workspace and back over the tile.
+template <typename Tp, int RND, int RN>
+__global__ void __launch_bounds__(kEvThreads) train_bwd_kernel(MlpDev m, int64_t N, TrainLayout TL,
+                                                               Tp* __restrict__ ws) {
+  constexpr int WPAD = 16 * RN, WTS = WPAD + 4, PPT = kEvRows / 4;
   extern __shared__ __align__(16) unsigned char smraw[];
-  Tp* sh = reinterpret_cast<Tp*>(smraw);
-  const int TP = blockDim.x, tid = threadIdx.x, W = m.max_w;
-  const int64_t p = (int64_t)blockIdx.x * TP + tid;
-  const bool valid = p < N;
-  auto col = [&](int s, int i) -> Tp& { return sh[((int64_t)s * W + i) * TP + tid]; };
+  Tp* D = reinterpret_cast<Tp*>(smraw);  // [WPAD][kEvRS] dz of the current layer, neuron-major
+  Tp* Wt = D + WPAD * kEvRS;             // [kEvKC][WTS] staged weights, W_l[kc + k][i] at [k][i]
+  const int tid = threadIdx.x, rg = tid >> 4, cg = tid & 15;
+  const int r0 = rg * 4, c0 = cg * RN;
+  const int64_t p0 = (int64_t)blockIdx.x * PPT;
+  const int64_t pt = p0 + rg;
   const Tp* prm = params_of<Tp>(m);
+  {  // the seeds: dz of the output layer (one neuron)
+    const Tp* dzL = ws + TL.dz_off[m.n_lin];
+    for (int r = tid; r < kEvRows; r += kEvThreads) {
+      const int64_t p = p0 + (r >> 2);
+      D[r] = p < N ? rop<RND>(dzL[p * 4 + (r & 3)]) : (Tp)0;
+    }
+  }
   for (int l = m.n_lin; l >= 2; --l) {
     const int wi = m.widths[l - 1], wo = m.widths[l];
-    const Tp* dzl = ws + TL.dz_off[l];
-    for (int o = 0; o < wo; ++o)
-      for (int s = 0; s < 4; ++s) col(s, o) = valid ? rop<RND>(dzl[((int64_t)s * wo + o) * N + p]) : (Tp)0;
     const Tp* Wl = prm + m.poff[l];
+    Tp acc[4][RN];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int q = 0; q < RN; ++q) acc[r][q] = (Tp)0;
+    for (int kc = 0; kc < wo; kc += kEvKC) {
+      const int kn = wo - kc < kEvKC ? wo - kc : kEvKC;
+      __syncthreads();
+      for (int i = tid; i < kEvKC * WPAD; i += kEvThreads) {
+        const int k = i / WPAD, n = i % WPAD;
+        Wt[k * WTS + n] = (k < kn && n < wi) ? rop<RND>(Wl[(int64_t)(kc + k) * wi + n]) : (Tp)0;
+      }
+      __syncthreads();
+      for (int k = 0; k < kn; ++k) {
+        Tp a[4], b[RN];
+        load_vec<Tp, 4>(D + (kc + k) * kEvRS + r0, a);
+        load_vec<Tp, RN>(Wt + k * WTS + c0, b);
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int q = 0; q < RN; ++q) acc[r][q] = fma(a[r], b[q], acc[r][q]);
+      }
+    }
+    __syncthreads();  // every thread has read this layer's dz before it is overwritten
     const Tp* act = ws + TL.act_off[l - 1];
     Tp* dzp = ws + TL.dz_off[l - 1];
-    for (int i = 0; i < wi; ++i) {
-      Tp ah = 0, ahS = 0, ahSS = 0, ahT = 0;
-      for (int o = 0; o < wo; ++o) {
-        const Tp w = rop<RND>(__ldg(Wl + (int64_t)o * wi + i));
-        ah = fma(w, col(0, o), ah);
-        ahS = fma(w, col(1, o), ahS);
-        ahSS = fma(w, col(2, o), ahSS);
-        ahT = fma(w, col(3, o), ahT);
-      }
-      if (!valid) continue;
-      const Tp t = act[(0 * (int64_t)wi + i) * N + p];
-      const Tp zs = act[(1 * (int64_t)wi + i) * N + p];
-      const Tp zss = act[(2 * (int64_t)wi + i) * N + p];
-      const Tp zt = act[(3 * (int64_t)wi + i) * N + p];
+#pragma unroll
+    for (int q = 0; q < RN; ++q) {
+      const int i = c0 + q;
+      const bool ok = i < wi && pt < N;
+      const Tp ah = acc[0][q], ahS = acc[1][q], ahSS = acc[2][q], ahT = acc[3][q];
+      const Tp t = ok ? act[(pt * 4 + 0) * wi + i] : (Tp)0;
+      const Tp zs = ok ? act[(pt * 4 + 1) * wi + i] : (Tp)0;
+      const Tp zss = ok ? act[(pt * 4 + 2) * wi + i] : (Tp)0;
+      const Tp zt = ok ? act[(pt * 4 + 3) * wi + i] : (Tp)0;
       const Tp d1 = (Tp)1 - t * t, d2 = (Tp)-2 * t * d1;
       Tp bar_d1 = ahS * zs + ahSS * zss + ahT * zt;
       const Tp bar_d2 = ahSS * zs * zs;
@@ -533,86 +595,119 @@ __global__ void train_bwd_kernel(MlpDev m, int64_t N, TrainLayout TL, Tp* __rest
       bar_t += (Tp)-2 * d1 * bar_d2;
       bar_d1 += (Tp)-2 * t * bar_d2;
       bar_t += (Tp)-2 * t * bar_d1;
-      dzp[(0 * (int64_t)wi + i) * N + p] = d1 * bar_t;
-      dzp[(1 * (int64_t)wi + i) * N + p] = ahS * d1 + (Tp)2 * ahSS * d2 * zs;
-      dzp[(2 * (int64_t)wi + i) * N + p] = ahSS * d1;
-      dzp[(3 * (int64_t)wi + i) * N + p] = ahT * d1;
+      Tp g[4];
+      g[0] = d1 * bar_t;
+      g[1] = ahS * d1 + (Tp)2 * ahSS * d2 * zs;
+      g[2] = ahSS * d1;
+      g[3] = ahT * d1;
+      if (!ok) g[0] = g[1] = g[2] = g[3] = (Tp)0;
+      if (ok) {
+#pragma unroll
+        for (int st = 0; st < 4; ++st) dzp[(pt * 4 + st) * wi + i] = g[st];
+      }
+      store4<Tp>(D + i * kEvRS + r0, rop<RND>(g[0]), rop<RND>(g[1]), rop<RND>(g[2]), rop<RND>(g[3]));
     }
-    __syncthreads();
   }
 }
 
-// Weight gradient of layer l: gW[o][i] = sum_p sum_s dz_s[o][p] h_s[i][p],
-// gb[o] = sum_p dz_0[o][p].  One CTA per (o-tile, i-tile, point chunk);
-// 16x16 outputs per CTA, one per thread, FP64 atomics into the gradient.
+// Weight gradient of layer l as a GEMM over rows (points x streams):
+// gW[o][i] = sum over rows of dz_l[row][o] h_{l-1}[row][i], h rebuilt from the
+// stored (t, z_S, z_SS, z_tau) (layer 1: from the inputs).  A CTA of 256
+// threads owns a 64 x 64 block of (o, i) for one chunk of kWgRows rows, staged
+// 32 rows at a time; thread (ty, tx) accumulates o = 4 ty .. + 3 against
+// i = 4 tx .. + 3 and adds its partial sums into the FP64 gradient.
+constexpr int kWgRows = 2048;
+constexpr int kWgStride = 64 + 4;
+
 template <typename Tp, int RND>
-__global__ void grad_reduce_kernel(MlpDev m, LossArgs la, TrainLayout TL, const Tp* __restrict__ ws, int l,
-                                   double* __restrict__ grad, int64_t chunk) {
+__global__ void __launch_bounds__(256) train_wgrad_kernel(MlpDev m, LossArgs la, TrainLayout TL,
+                                                          const Tp* __restrict__ ws, int l,
+                                                          double* __restrict__ grad) {
+  __shared__ __align__(16) Tp sDZ[32][kWgStride];
+  __shared__ __align__(16) Tp sH[32][kWgStride];
   const int wi = m.widths[l - 1], wo = m.widths[l];
-  const int64_t N = la.N;
-  const int o = blockIdx.y * 16 + threadIdx.y;
-  const int i = blockIdx.x * 16 + threadIdx.x;  // i == wi is the bias column
-  const int64_t p0 = (int64_t)blockIdx.z * chunk;
-  const int64_t p1 = min(N, p0 + chunk);
-  __shared__ Tp sdz[4][16][33];
-  __shared__ Tp shh[4][16][33];
-  Tp acc = 0;
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  const int ob = blockIdx.y * 64, ib = blockIdx.x * 64;
+  const int64_t rows = 4 * la.N;
+  const int64_t rb = (int64_t)blockIdx.z * kWgRows;
+  const int64_t re = rb + kWgRows < rows ? rb + kWgRows : rows;
   const Tp* dz = ws + TL.dz_off[l];
-  const Tp* act = (l >= 2) ? ws + TL.act_off[l - 1] : nullptr;
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  for (int64_t pb = p0; pb < p1; pb += 32) {
-    // stage dz for 16 outputs x 32 points and h streams for 16 inputs x 32 points
-    for (int q = ty * 16 + tx; q < 16 * 32; q += 256) {
-      const int oo = q / 32, pp = q % 32;
-      const int64_t pg = pb + pp;
-      const int og = blockIdx.y * 16 + oo;
-      for (int s = 0; s < 4; ++s)
-        sdz[s][oo][pp] = (pg < p1 && og < wo) ? rop<RND>(dz[((int64_t)s * wo + og) * N + pg]) : (Tp)0;
-      const int ig = blockIdx.x * 16 + oo;
+  const Tp* act = l >= 2 ? ws + TL.act_off[l - 1] : nullptr;
+  Tp acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = (Tp)0;
+  for (int64_t r32 = rb; r32 < re; r32 += 32) {
+    __syncthreads();
+    for (int q = tid; q < 32 * 64; q += 256) {  // dz rows, coalesced along o
+      const int k = q / 64, o = q % 64;
+      const int64_t row = r32 + k;
+      sDZ[k][o] = (row < re && ob + o < wo) ? rop<RND>(dz[row * wo + ob + o]) : (Tp)0;
+    }
+    for (int q = tid; q < 8 * 64; q += 256) {  // h of 8 points x 64 inputs, 4 streams each
+      const int pp = q / 64, i = q % 64, ig = ib + i;
+      const int64_t p = (r32 >> 2) + pp;
       Tp h0 = 0, h1 = 0, h2 = 0, h3 = 0;
-      if (pg < p1) {
-        if (ig == wi) {
-          h0 = 1;  // bias column: only the value stream
-        } else if (ig < wi) {
-          if (l >= 2) {
-            const Tp t = act[((int64_t)0 * wi + ig) * N + pg];
-            const Tp zs = act[((int64_t)1 * wi + ig) * N + pg];
-            const Tp zss = act[((int64_t)2 * wi + ig) * N + pg];
-            const Tp zt = act[((int64_t)3 * wi + ig) * N + pg];
-            const Tp d1 = (Tp)1 - t * t;
-            h0 = t;
-            h1 = d1 * zs;
-            h2 = d1 * zss - (Tp)2 * t * d1 * zs * zs;
-            h3 = d1 * zt;
-          } else {
-            const double sc = 2.0 / (m.hi[ig] - m.lo[ig]);
-            h0 = (Tp)(sc * (la.X[pg * m.d_in + ig] - m.lo[ig]) - 1.0);
-            h1 = (Tp)((ig == 0) ? sc : 0.0);
-            h2 = 0;
-            h3 = (Tp)((ig == 1) ? sc : 0.0);
-          }
+      if (4 * p < re && ig < wi) {
+        if (l >= 2) {
+          const Tp t = act[(p * 4 + 0) * wi + ig], zs = act[(p * 4 + 1) * wi + ig];
+          const Tp zss = act[(p * 4 + 2) * wi + ig], zt = act[(p * 4 + 3) * wi + ig];
+          const Tp d1 = (Tp)1 - t * t;
+          h0 = t;
+          h1 = d1 * zs;
+          h2 = d1 * zss - (Tp)2 * t * d1 * zs * zs;
+          h3 = d1 * zt;
+        } else {
+          const double sc = 2.0 / (m.hi[ig] - m.lo[ig]);
+          h0 = (Tp)(sc * (la.X[p * m.d_in + ig] - m.lo[ig]) - 1.0);
+          h1 = (Tp)(ig == 0 ? sc : 0.0);
+          h3 = (Tp)(ig == 1 ? sc : 0.0);
         }
       }
-      shh[0][oo][pp] = rop<RND>(h0);
-      shh[1][oo][pp] = rop<RND>(h1);
-      shh[2][oo][pp] = rop<RND>(h2);
-      shh[3][oo][pp] = rop<RND>(h3);
+      sH[pp * 4 + 0][i] = rop<RND>(h0);
+      sH[pp * 4 + 1][i] = rop<RND>(h1);
+      sH[pp * 4 + 2][i] = rop<RND>(h2);
+      sH[pp * 4 + 3][i] = rop<RND>(h3);
     }
     __syncthreads();
 #pragma unroll 4
-    for (int pp = 0; pp < 32; ++pp) {
-      acc = fma(sdz[0][ty][pp], shh[0][tx][pp], acc);
-      acc = fma(sdz[1][ty][pp], shh[1][tx][pp], acc);
-      acc = fma(sdz[2][ty][pp], shh[2][tx][pp], acc);
-      acc = fma(sdz[3][ty][pp], shh[3][tx][pp], acc);
+    for (int k = 0; k < 32; ++k) {
+      Tp a[4], b[4];
+      load_vec<Tp, 4>(&sDZ[k][ty * 4], a);
+      load_vec<Tp, 4>(&sH[k][tx * 4], b);
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] = fma(a[x], b[y], acc[x][y]);
     }
-    __syncthreads();
   }
-  if (o < wo && i <= wi) {
-    double* g = grad + m.poff[l];
-    if (i < wi) atomicAdd(g + (int64_t)o * wi + i, (double)acc);
-    else atomicAdd(g + (int64_t)wo * wi + o, (double)acc);
+  double* g = grad + m.poff[l];
+#pragma unroll
+  for (int x = 0; x < 4; ++x) {
+    const int o = ob + ty * 4 + x;
+#pragma unroll
+    for (int y = 0; y < 4; ++y) {
+      const int i = ib + tx * 4 + y;
+      if (o < wo && i < wi) atomicAdd(g + (int64_t)o * wi + i, (double)acc[x][y]);
+    }
   }
+}
+
+// Bias gradient of layer l: gb[o] = sum over points of dz_l[(p, 0)][o] (the
+// value stream), one thread per o over a chunk of points.
+template <typename Tp, int RND>
+__global__ void train_bgrad_kernel(MlpDev m, int64_t N, TrainLayout TL, const Tp* __restrict__ ws, int l,
+                                   double* __restrict__ grad, int64_t chunk) {
+  const int wi = m.widths[l - 1], wo = m.widths[l];
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= wo) return;
+  const int64_t pb = (int64_t)blockIdx.y * chunk;
+  const int64_t pe = pb + chunk < N ? pb + chunk : N;
+  const Tp* dz = ws + TL.dz_off[l];
+  Tp acc = (Tp)0;
+  for (int64_t p = pb; p < pe; ++p) acc += rop<RND>(dz[(p * 4) * wo + o]);
+  atomicAdd(grad + m.poff[l] + (int64_t)wo * wi + o, (double)acc);
 }
 
 __global__ void loss_finish_kernel(const double* acc, const unsigned long long* cnt, double* loss3) {
@@ -621,6 +716,33 @@ __global__ void loss_finish_kernel(const double* acc, const unsigned long long* 
     loss3[1] = cnt[1] ? acc[1] / (double)cnt[1] : 0.0;
     loss3[2] = cnt[2] ? acc[2] / (double)cnt[2] : 0.0;
   }
+}
+
+template <typename Tp, int RND, int RN>
+static cudaError_t simt_train_launch(const MlpDev& m, const LossArgs& la, const TrainLayout& TL, Tp* ws,
+                                     const unsigned long long* cnt, double* acc, double* grad, cudaStream_t s) {
+  const size_t smem = eval_smem_bytes<Tp>(RN);
+  cudaError_t e = cudaFuncSetAttribute(train_fwd_kernel<Tp, RND, RN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(train_bwd_kernel<Tp, RND, RN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const unsigned tiles = (unsigned)((la.N + kEvRows / 4 - 1) / (kEvRows / 4));
+  train_fwd_kernel<Tp, RND, RN><<<tiles, kEvThreads, smem, s>>>(m, la, TL, ws, cnt, acc);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  train_bwd_kernel<Tp, RND, RN><<<tiles, kEvThreads, smem, s>>>(m, la.N, TL, ws);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const unsigned nz = (unsigned)((4 * la.N + kWgRows - 1) / kWgRows);
+  const int64_t bchunk = 1024;
+  for (int l = 1; l <= m.n_lin; ++l) {
+    const int wi = m.widths[l - 1], wo = m.widths[l];
+    train_wgrad_kernel<Tp, RND><<<dim3((wi + 63) / 64, (wo + 63) / 64, nz), 256, 0, s>>>(m, la, TL, ws, l, grad);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    train_bgrad_kernel<Tp, RND><<<dim3((wo + 127) / 128, (unsigned)((la.N + bchunk - 1) / bchunk)), 128, 0, s>>>(
+        m, la.N, TL, ws, l, grad, bchunk);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 template <typename Tp, int RND>
@@ -646,34 +768,13 @@ static cudaError_t loss_grad_impl(const MlpDev& m, const LossArgs& la, double* l
   e = cudaMemsetAsync(grad, 0, (size_t)np * sizeof(double), s);
   if (e != cudaSuccess) return e;
   count_kinds_kernel<<<148, 256, 0, s>>>(la.kind, la.N, cnt, la.y != nullptr, m.status);
-  {  // CUDA cores: forward, adjoint, per-layer reductions
-    {
-      const size_t per_thread = 2 * 4 * (size_t)m.max_w * sizeof(Tp);
-      const int TP = points_per_cta(per_thread);
-      const size_t smem = per_thread * TP;
-      e = cudaFuncSetAttribute(train_fwd_kernel<Tp, RND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      train_fwd_kernel<Tp, RND><<<(unsigned)((la.N + TP - 1) / TP), TP, smem, s>>>(m, la, TL, ws, cnt, acc);
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    {
-      const size_t per_thread = 4 * (size_t)m.max_w * sizeof(Tp);
-      const int TP = points_per_cta(per_thread);
-      const size_t smem = per_thread * TP;
-      e = cudaFuncSetAttribute(train_bwd_kernel<Tp, RND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      train_bwd_kernel<Tp, RND><<<(unsigned)((la.N + TP - 1) / TP), TP, smem, s>>>(m, la.N, TL, ws);
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    const int64_t chunk = 2048;
-    const unsigned nz = (unsigned)((la.N + chunk - 1) / chunk);
-    for (int l = 1; l <= m.n_lin; ++l) {
-      const int wi = m.widths[l - 1], wo = m.widths[l];
-      dim3 grid((wi + 1 + 15) / 16, (wo + 15) / 16, nz);
-      grad_reduce_kernel<Tp, RND><<<grid, dim3(16, 16), 0, s>>>(m, la, TL, ws, l, grad, chunk);
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-  }
+  // CUDA cores: forward, adjoint, per-layer weight and bias gradients
+  if (m.max_w <= 16) e = simt_train_launch<Tp, RND, 1>(m, la, TL, ws, cnt, acc, grad, s);
+  else if (m.max_w <= 32) e = simt_train_launch<Tp, RND, 2>(m, la, TL, ws, cnt, acc, grad, s);
+  else if (m.max_w <= 64) e = simt_train_launch<Tp, RND, 4>(m, la, TL, ws, cnt, acc, grad, s);
+  else if (m.max_w <= 128) e = simt_train_launch<Tp, RND, 8>(m, la, TL, ws, cnt, acc, grad, s);
+  else e = simt_train_launch<Tp, RND, 16>(m, la, TL, ws, cnt, acc, grad, s);
+  if (e != cudaSuccess) return e;
   loss_finish_kernel<<<1, 32, 0, s>>>(acc, cnt, loss3);
   return cudaGetLastError();
 }
