@@ -345,6 +345,31 @@ def test_bf16_training_outside_the_tensor_core_shapes(B, orc, widths):
         assert np.abs(g[a:b] - grad[a:b]).max() / max(np.abs(grad[a:b]).max(), 1e-300) <= 2e-2, name
 
 
+@pytest.mark.parametrize("widths", [[2, 7, 1], [2, 50, 50, 1], [5, 40, 24, 1], [2, 200, 130, 1]],
+                         ids=["2-7", "2-2x50", "5-40-24", "2-200-130"])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_cuda_core_paths_on_uneven_widths(B, orc, widths, prec):
+    # the CUDA-core evaluation and training tile the layers in blocks of 16 RN
+    # neurons: widths that fill no block exactly, unequal widths and a batch
+    # that is no multiple of the 16-point tile, against the oracle
+    m, om = _model(B, orc, widths, 12)
+    X, kind, prob, sok = _loss_case(widths, 701, 61, 67, 17)
+    Xd = torch.tensor(X, device="cuda")
+    ru, rd = orc.mlp_eval(om, X)
+    u, d = m.eval(Xd, prec=prec, derivs=True)
+    assert _rel(u.cpu().numpy(), ru) <= TOL_EVAL[prec]
+    for c in range(3):
+        assert _rel(d.cpu().numpy()[:, c], rd[:, c]) <= (1e-10 if prec == 0 else 2e-5), c
+    terms, grad = orc.pinn_loss_grad(om, X, kind, prob["K"], prob["sigma"], prob["r"], prob["Smax"], sok)
+    l3, g = m.loss_grad(Xd, torch.tensor(kind, device="cuda"), prob, sok, prec=prec)
+    l3, g = l3.cpu().numpy(), g.cpu().numpy()
+    tol_l, tol_g = (1e-12, 1e-10) if prec == 0 else (1e-4, 1e-4)
+    for c in range(3):
+        assert abs(l3[c] - terms[c]) <= tol_l * abs(terms[c]), (c, l3[c], terms[c])
+    assert _rel(g, grad) <= tol_g
+    assert m.device_status() == B.BS_OK
+
+
 @pytest.mark.parametrize("arch", ["2-4x64", "5-6x128"])
 def test_tensor_core_training_in_chunks(B, orc, arch, monkeypatch):
     # a batch run as chunks of 1024 points (4 chunks, the last one ragged) gives
