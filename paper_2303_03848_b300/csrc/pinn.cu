@@ -96,7 +96,13 @@ __device__ __forceinline__ void input_streams(const MlpDev& m, const double* x, 
 // product per row, four threads a row.
 // ---------------------------------------------------------------------------
 constexpr int kEvRows = 64;
-constexpr int kEvRS = kEvRows + 4;  // row stride of the neuron-major tile (16-byte aligned, fewer conflicts)
+constexpr int kEvRS = kEvRows + 4;  // row stride of the neuron-major tile (16-byte aligned)
+
+// Offset of neuron k's row in a neuron-major tile: every group of 8 rows is
+// shifted by 4 more elements, so that the 16 column groups of a warp, whose
+// blocks start 8 k apart, store their rows into different banks.
+__host__ __device__ constexpr int hrow(int k) { return k * kEvRS + (k >> 3) * 4; }
+__host__ __device__ constexpr int hrows_size(int n) { return hrow(n); }
 constexpr int kEvThreads = 256;
 constexpr int kEvKC = 32;
 constexpr int kEvIn = 8;  // input streams per row (d_in <= 8)
@@ -137,7 +143,7 @@ __device__ __forceinline__ void store4(Tp* p, Tp a, Tp b, Tp c, Tp d) {
 
 template <typename Tp>
 constexpr size_t eval_smem_bytes(int RN) {
-  return sizeof(Tp) * ((size_t)16 * RN * kEvRS + (size_t)kEvKC * (16 * RN + 4) + (size_t)kEvIn * kEvRS);
+  return sizeof(Tp) * ((size_t)hrows_size(16 * RN) + (size_t)kEvKC * (16 * RN + 4) + (size_t)hrows_size(kEvIn));
 }
 
 template <typename Tp, int RND, int NS, int RN>
@@ -146,7 +152,7 @@ __global__ void __launch_bounds__(kEvThreads) mlp_eval_kernel(MlpDev m, const do
   constexpr int WPAD = 16 * RN, WTS = WPAD + 4, PPT = kEvRows / NS;
   extern __shared__ __align__(16) unsigned char smraw[];
   Tp* H = reinterpret_cast<Tp*>(smraw);  // [WPAD][kEvRS] activations of the tile, neuron-major
-  Tp* Wt = H + WPAD * kEvRS;             // [kEvKC][WTS] staged weights, W_l[o][kc + k] at [k][o]
+  Tp* Wt = H + hrows_size(WPAD);             // [kEvKC][WTS] staged weights, W_l[o][kc + k] at [k][o]
   Tp* Hin = Wt + kEvKC * WTS;            // [kEvIn][kEvRS] input streams
   const int tid = threadIdx.x, rg = tid >> 4, cg = tid & 15;
   const int r0 = rg * 4, c0 = cg * RN;
@@ -164,7 +170,7 @@ __global__ void __launch_bounds__(kEvThreads) mlp_eval_kernel(MlpDev m, const do
       else if (st == 1) v = k == 0 ? (Tp)sc : (Tp)0;
       else if (st == 3) v = k == 1 ? (Tp)sc : (Tp)0;
     }
-    Hin[k * kEvRS + r] = v;
+    Hin[hrow(k) + r] = v;
   }
   const Tp* prm = params_of<Tp>(m);
   for (int l = 1; l < m.n_lin; ++l) {  // hidden layers
@@ -187,7 +193,7 @@ __global__ void __launch_bounds__(kEvThreads) mlp_eval_kernel(MlpDev m, const do
       __syncthreads();
       for (int k = 0; k < kn; ++k) {
         Tp a[4], b[RN];
-        load_vec<Tp, 4>(Hs + (kc + k) * kEvRS + r0, a);
+        load_vec<Tp, 4>(Hs + hrow(kc + k) + r0, a);
         load_vec<Tp, RN>(Wt + k * WTS + c0, b);
 #pragma unroll
         for (int r = 0; r < 4; ++r)
@@ -215,7 +221,7 @@ __global__ void __launch_bounds__(kEvThreads) mlp_eval_kernel(MlpDev m, const do
         h[2] = ok ? rop<RND>(d1 * zSS - (Tp)2 * t * d1 * zS * zS) : (Tp)0;
         h[3] = ok ? rop<RND>(d1 * zT) : (Tp)0;
       }
-      store4<Tp>(H + o * kEvRS + r0, h[0], h[1], h[2], h[3]);
+      store4<Tp>(H + hrow(o) + r0, h[0], h[1], h[2], h[3]);
     }
   }
   __syncthreads();
@@ -226,7 +232,7 @@ __global__ void __launch_bounds__(kEvThreads) mlp_eval_kernel(MlpDev m, const do
     const Tp* Hs = m.n_lin == 1 ? Hin : H;
     const int row = tid >> 2, part = tid & 3;
     Tp z = (Tp)0;
-    for (int k = part; k < wi; k += 4) z = fma(rop<RND>(Wo[k]), Hs[k * kEvRS + row], z);
+    for (int k = part; k < wi; k += 4) z = fma(rop<RND>(Wo[k]), Hs[hrow(k) + row], z);
     z += __shfl_xor_sync(0xffffffffu, z, 1);
     z += __shfl_xor_sync(0xffffffffu, z, 2);
     const int64_t p = p0 + row / NS;
@@ -393,7 +399,7 @@ __global__ void __launch_bounds__(kEvThreads) train_fwd_kernel(MlpDev m, LossArg
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ double s_acc[3];
   Tp* H = reinterpret_cast<Tp*>(smraw);  // [WPAD][kEvRS] h of the tile, neuron-major
-  Tp* Wt = H + WPAD * kEvRS;             // [kEvKC][WTS] staged weights
+  Tp* Wt = H + hrows_size(WPAD);             // [kEvKC][WTS] staged weights
   Tp* Hin = Wt + kEvKC * WTS;            // [kEvIn][kEvRS] input streams
   const int tid = threadIdx.x, rg = tid >> 4, cg = tid & 15;
   const int r0 = rg * 4, c0 = cg * RN;
@@ -411,7 +417,7 @@ __global__ void __launch_bounds__(kEvThreads) train_fwd_kernel(MlpDev m, LossArg
       else if (st == 1) v = k == 0 ? (Tp)sc : (Tp)0;
       else if (st == 3) v = k == 1 ? (Tp)sc : (Tp)0;
     }
-    Hin[k * kEvRS + r] = v;
+    Hin[hrow(k) + r] = v;
   }
   const Tp* prm = params_of<Tp>(m);
   const int64_t pt = p0 + rg;  // this thread's point (its rows r0 .. r0 + 3 are the point's streams)
@@ -435,7 +441,7 @@ __global__ void __launch_bounds__(kEvThreads) train_fwd_kernel(MlpDev m, LossArg
       __syncthreads();
       for (int k = 0; k < kn; ++k) {
         Tp a[4], b[RN];
-        load_vec<Tp, 4>(Hs + (kc + k) * kEvRS + r0, a);
+        load_vec<Tp, 4>(Hs + hrow(kc + k) + r0, a);
         load_vec<Tp, RN>(Wt + k * WTS + c0, b);
 #pragma unroll
         for (int r = 0; r < 4; ++r)
@@ -452,7 +458,7 @@ __global__ void __launch_bounds__(kEvThreads) train_fwd_kernel(MlpDev m, LossArg
       const Tp z = acc[0][q] + (ok ? bl[o] : (Tp)0), zS = acc[1][q], zSS = acc[2][q], zT = acc[3][q];
       const Tp t = tanh_t<Tp>(z);
       const Tp d1 = (Tp)1 - t * t;
-      store4<Tp>(H + o * kEvRS + r0, ok ? rop<RND>(t) : (Tp)0, ok ? rop<RND>(d1 * zS) : (Tp)0,
+      store4<Tp>(H + hrow(o) + r0, ok ? rop<RND>(t) : (Tp)0, ok ? rop<RND>(d1 * zS) : (Tp)0,
                  ok ? rop<RND>(d1 * zSS - (Tp)2 * t * d1 * zS * zS) : (Tp)0, ok ? rop<RND>(d1 * zT) : (Tp)0);
       if (ok && pt < N) {
         act[(pt * 4 + 0) * wo + o] = t;
@@ -472,7 +478,7 @@ __global__ void __launch_bounds__(kEvThreads) train_fwd_kernel(MlpDev m, LossArg
     const Tp* Hs = m.n_lin == 1 ? Hin : H;
     const int row = tid >> 2, part = tid & 3;
     Tp z = (Tp)0;
-    for (int k = part; k < wi; k += 4) z = fma(rop<RND>(Wo[k]), Hs[k * kEvRS + row], z);
+    for (int k = part; k < wi; k += 4) z = fma(rop<RND>(Wo[k]), Hs[hrow(k) + row], z);
     z += __shfl_xor_sync(0xffffffffu, z, 1);
     z += __shfl_xor_sync(0xffffffffu, z, 2);
     const int base = (tid & 31) & ~15;
@@ -537,7 +543,7 @@ __global__ void __launch_bounds__(kEvThreads) train_bwd_kernel(MlpDev m, int64_t
   constexpr int WPAD = 16 * RN, WTS = WPAD + 4, PPT = kEvRows / 4;
   extern __shared__ __align__(16) unsigned char smraw[];
   Tp* D = reinterpret_cast<Tp*>(smraw);  // [WPAD][kEvRS] dz of the current layer, neuron-major
-  Tp* Wt = D + WPAD * kEvRS;             // [kEvKC][WTS] staged weights, W_l[kc + k][i] at [k][i]
+  Tp* Wt = D + hrows_size(WPAD);             // [kEvKC][WTS] staged weights, W_l[kc + k][i] at [k][i]
   const int tid = threadIdx.x, rg = tid >> 4, cg = tid & 15;
   const int r0 = rg * 4, c0 = cg * RN;
   const int64_t p0 = (int64_t)blockIdx.x * PPT;
@@ -568,7 +574,7 @@ __global__ void __launch_bounds__(kEvThreads) train_bwd_kernel(MlpDev m, int64_t
       __syncthreads();
       for (int k = 0; k < kn; ++k) {
         Tp a[4], b[RN];
-        load_vec<Tp, 4>(D + (kc + k) * kEvRS + r0, a);
+        load_vec<Tp, 4>(D + hrow(kc + k) + r0, a);
         load_vec<Tp, RN>(Wt + k * WTS + c0, b);
 #pragma unroll
         for (int r = 0; r < 4; ++r)
@@ -605,7 +611,7 @@ __global__ void __launch_bounds__(kEvThreads) train_bwd_kernel(MlpDev m, int64_t
 #pragma unroll
         for (int st = 0; st < 4; ++st) dzp[(pt * 4 + st) * wi + i] = g[st];
       }
-      store4<Tp>(D + i * kEvRS + r0, rop<RND>(g[0]), rop<RND>(g[1]), rop<RND>(g[2]), rop<RND>(g[3]));
+      store4<Tp>(D + hrow(i) + r0, rop<RND>(g[0]), rop<RND>(g[1]), rop<RND>(g[2]), rop<RND>(g[3]));
     }
   }
 }
