@@ -289,14 +289,18 @@ int pinn_eval(const pinn_model* m, int prec, const double* X, int64_t N, double*
  *   prob_params (host): K, sigma, r,
  *   Smax of the loss (a 5-input network takes sigma, r, K per point from X;
  *   then Smax of kind-2 points is smax_over_K * K when smax_over_K > 0).
- *   prec: BS_FP64, BS_FP32, or BS_BF16 (BF16 operands, FP32 accumulation).
+ *   prec: BS_FP64, BS_FP32, BS_TF32 or BS_BF16 (TF32 / BF16: operands of
+ *   every layer rounded to the type, FP32 accumulation).
  *   loss3 (device, 3 doubles: MSE_f, MSE_b, MSE_exp) and grad (device,
  *   n_params doubles) are written asynchronously.
- *   BF16 with hidden layers w x w, w in {32, 64, 96, 128}, and d_in 2 or 5
- *   runs on the tensor cores; it processes the batch in chunks of 2^19 points
- *   (environment variable BSP_TRAIN_CHUNK overrides, in points), so its
- *   workspace does not grow past one chunk's whatever N; the workspace is
- *   allocated on first use and grown when a larger batch needs more.
+ *   BF16 and TF32 with hidden layers w x w, w in {32, 64, 96, 128}, at least
+ *   two of them, and d_in 2 or 5 run on the tensor cores (other shapes round
+ *   the operands the same way on CUDA cores).  BF16 processes the batch in
+ *   chunks of 2^19 points (environment variable BSP_TRAIN_CHUNK overrides, in
+ *   points), so its workspace does not grow past one chunk's whatever N; the
+ *   other precisions keep 8 N (sum of the layer widths) values.  The
+ *   workspace is allocated on first use and grown when a larger batch needs
+ *   more.
  */
 int pinn_loss_grad(const pinn_model* m, const double* X, const int8_t* kind, int64_t N,
                    const bs_params* prob_params, double smax_over_K, int prec, double* loss3, double* grad,

@@ -740,7 +740,7 @@ static int loss_grad_common(const pinn_model* mc, const double* X, const int8_t*
                             cudaStream_t s) {
   pinn_model* m = const_cast<pinn_model*>(mc);
   if (!m || !X || !kind || !pp || N <= 0 || ((uintptr_t)y & 7)) return BS_EINVAL;
-  if (!(prec == BS_FP64 || prec == BS_FP32 || prec == BS_BF16)) return BS_EINVAL;
+  if (prec < BS_FP64 || prec > BS_BF16) return BS_EINVAL;
   if (((uintptr_t)X & 15) || ((uintptr_t)grad & 7) || ((uintptr_t)loss3 & 7) || !std::isfinite(pp->K) ||
       !std::isfinite(pp->sigma) || !std::isfinite(pp->r) || !std::isfinite(pp->Smax) || !std::isfinite(smax_over_K))
     return BS_EINVAL;

@@ -113,6 +113,29 @@ struct LossArgs {
 };
 cudaError_t launch_loss_grad(const MlpDev& m, const LossArgs& la, double* loss3, double* grad, void* workspace,
                              size_t ws_bytes, cudaStream_t s);
+// Workspace of the training kernels outside the BF16 tensor-core path: 4 N w_l
+// elements per layer for the activations act[l] (hidden layers l = 1..n_lin-1)
+// and the adjoints dz[l] (l = 1..n_lin; dz of the output layer: the seeds).
+// The CUDA-core kernels keep a layer as rows (p, s) of w_l neurons; the TF32
+// tensor-core kernels as blocks of 32 rows, neuron-major inside a block, for
+// the batch padded to 32 points.
+struct TrainLayout {
+  int64_t act_off[16];  // offsets (elements) of act[l], l = 1..n_lin-1
+  int64_t dz_off[16];   // offsets of dz[l], l = 1..n_lin
+  int64_t total;        // elements
+};
+// The loss gradient with TF32 operands on tcgen05 (pinn_train_tf32.cu):
+// networks d_in (2 or 5) -> w x ... x w -> 1 with w in {32, 64, 96, 128} and
+// at least one w x w layer.  ws: FP32 workspace, 16-byte aligned, with TL the
+// layout above for the batch padded to a multiple of 32 points; pack:
+// train_tf32_pack_bytes(m) bytes (16-byte aligned) for W_l and W_l^T of the
+// square layers; cnt: the points per loss term (already counted); grad zeroed
+// by the caller, the loss sums go to loss_acc.
+bool train_tf32_supported(const MlpDev& m);
+size_t train_tf32_pack_bytes(const MlpDev& m);
+cudaError_t launch_train_tf32(const MlpDev& m, const LossArgs& la, float* ws, const TrainLayout& TL,
+                              unsigned char* pack, const unsigned long long* cnt, double* loss_acc, double* grad,
+                              cudaStream_t s);
 size_t loss_grad_workspace_bytes(const MlpDev& m, int64_t N);
 // The loss gradient on tcgen05 (pinn_train_tc.cu), BF16 operands with FP32
 // accumulation: forward with the derivative streams, adjoint and every layer's

@@ -318,12 +318,6 @@ cudaError_t launch_f64_to_f32(const double* src, float* dst, int64_t n, cudaStre
 // is its w_l neurons, contiguous.
 // ---------------------------------------------------------------------------
 
-struct TrainLayout {
-  int64_t act_off[16];  // offsets (elements) of act[l], l = 1..n_lin-1
-  int64_t dz_off[16];   // offsets of dz[l], l = 1..n_lin
-  int64_t total;        // elements
-};
-
 static TrainLayout train_layout(const MlpDev& m, int64_t N) {
   TrainLayout L{};
   int64_t o = 0;
@@ -341,8 +335,9 @@ static TrainLayout train_layout(const MlpDev& m, int64_t N) {
 
 // Workspace: activations and adjoints (the CUDA-core layout below, or the
 // tensor-core path's own, whichever is larger), then the loss accumulators.
+// The TF32 tensor-core path adds its packed W_l and W_l^T after the accumulators.
 struct WsTail {
-  size_t acc, total;
+  size_t acc, pack, total;
 };
 
 static WsTail ws_tail(const MlpDev& m, const TrainLayout& L, size_t elem, int64_t N) {
@@ -350,8 +345,13 @@ static WsTail ws_tail(const MlpDev& m, const TrainLayout& L, size_t elem, int64_
   size_t body = (size_t)L.total * elem;
   const size_t tcb = train_tc_workspace_bytes(m, N);
   if (tcb > body) body = tcb;
+  if (train_tf32_supported(m)) {  // FP32, the batch padded to 32-point tiles
+    const size_t t32 = (size_t)train_layout(m, (N + 31) / 32 * 32).total * sizeof(float);
+    if (t32 > body) body = t32;
+  }
   w.acc = (body + 255) / 256 * 256;
-  w.total = w.acc + 64;
+  w.pack = w.acc + 256;
+  w.total = w.pack + train_tf32_pack_bytes(m);
   return w;
 }
 
@@ -774,6 +774,13 @@ static cudaError_t loss_grad_impl(const MlpDev& m, const LossArgs& la, double* l
   e = cudaMemsetAsync(grad, 0, (size_t)np * sizeof(double), s);
   if (e != cudaSuccess) return e;
   count_kinds_kernel<<<148, 256, 0, s>>>(la.kind, la.N, cnt, la.y != nullptr, m.status);
+  if (RND == 1 && sizeof(Tp) == 4 && train_tf32_supported(m)) {  // TF32 on the tensor cores
+    const TrainLayout TLp = train_layout(m, (la.N + 31) / 32 * 32);
+    e = launch_train_tf32(m, la, reinterpret_cast<float*>(workspace), TLp, base + WT.pack, cnt, acc, grad, s);
+    if (e != cudaSuccess) return e;
+    loss_finish_kernel<<<1, 32, 0, s>>>(acc, cnt, loss3);
+    return cudaGetLastError();
+  }
   // CUDA cores: forward, adjoint, per-layer weight and bias gradients
   if (m.max_w <= 16) e = simt_train_launch<Tp, RND, 1>(m, la, TL, ws, cnt, acc, grad, s);
   else if (m.max_w <= 32) e = simt_train_launch<Tp, RND, 2>(m, la, TL, ws, cnt, acc, grad, s);
@@ -792,6 +799,8 @@ cudaError_t launch_loss_grad(const MlpDev& m, const LossArgs& la, double* loss3,
       return loss_grad_impl<double, 0>(m, la, loss3, grad, workspace, ws_bytes, s);
     case 1:
       return loss_grad_impl<float, 0>(m, la, loss3, grad, workspace, ws_bytes, s);
+    case 2:
+      return loss_grad_impl<float, 1>(m, la, loss3, grad, workspace, ws_bytes, s);
     case 3:
       return loss_grad_impl<float, 2>(m, la, loss3, grad, workspace, ws_bytes, s);
   }

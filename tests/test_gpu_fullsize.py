@@ -20,9 +20,9 @@ properties that hold at any size.
   two implicit-Euler-coarse Parareal iterations leave the first three slices
   equal to GPU serial fine bitwise.
 * Training workload (2->6x128, 65536 collocation points): every layer's BF16
-  tensor-core gradient against the oracle's FP64 gradient of the whole batch
-  (computed in host threads from single-term chunks) and against the FP32
-  CUDA-core gradient of the same batch.
+  and TF32 tensor-core gradients against the oracle's FP64 gradient of the
+  whole batch (computed in host threads from single-term chunks) and against
+  the FP32 CUDA-core gradient of the same batch.
 
 FP64 tolerance: max(1e-12, 2 kappa u N) as in test_gpu_solver.py (kappa the
 mesh-ratio factor of the right-hand side, u = 2^-53, N the steps).
@@ -209,9 +209,9 @@ def _oracle_loss_grad_threaded(orc, om, X, kind, prob, sok, chunk=2048):
 
 def test_training_step_full_size_matches_oracle_and_fp32_path(B, orc):
     # the 2->6x128 training workload at its full batch (65536 points): every
-    # layer's BF16 tensor-core gradient against the oracle's FP64 gradient of
-    # the whole batch and against the FP32 CUDA-core gradient of the same batch,
-    # with the per-layer bound of the BF16 tests
+    # layer's BF16 and TF32 tensor-core gradients against the oracle's FP64
+    # gradient of the whole batch and against the FP32 CUDA-core gradient of
+    # the same batch, with the per-layer bounds of the BF16 and TF32 tests
     widths = [2] + [128] * 6 + [1]
     nb = 65536 // 32
     X, kind = synth.collocation(0, 65536 - 2 * nb, nb, nb, 4.0, 1.0)
@@ -220,19 +220,22 @@ def test_training_step_full_size_matches_oracle_and_fp32_path(B, orc):
     m = B.PinnModel(widths, [0.0, 0.0], [4.0, 1.0], seed=0)
     l16, g16 = m.loss_grad(Xd, kd, prob, 0.0, prec=B.BF16)
     l32, g32 = m.loss_grad(Xd, kd, prob, 0.0, prec=B.FP32)
+    lt, gt = m.loss_grad(Xd, kd, prob, 0.0, prec=B.TF32)
     assert m.device_status() == B.BS_OK
-    l16, g16, l32, g32 = (v.cpu().numpy() for v in (l16, g16, l32, g32))
+    l16, g16, l32, g32, lt, gt = (v.cpu().numpy() for v in (l16, g16, l32, g32, lt, gt))
     om = orc.MLP(widths, synth.xavier_params(widths, 0), [0.0, 0.0], [4.0, 1.0])
     l64, g64 = _oracle_loss_grad_threaded(orc, om, X, kind, prob, 0.0)
     for c in range(3):
         assert abs(l16[c] - l64[c]) <= 5e-2 * abs(l64[c]), (c, l16[c], l64[c])
         assert abs(l32[c] - l64[c]) <= 1e-4 * abs(l64[c]), (c, l32[c], l64[c])
+        assert abs(lt[c] - l64[c]) <= 2e-2 * abs(l64[c]), (c, lt[c], l64[c])
     off = 0
     for l in range(1, len(widths)):
         for n in (widths[l] * widths[l - 1], widths[l]):
-            a, b, ref = g16[off:off + n], g32[off:off + n], g64[off:off + n]
+            a, b, ref, tf = g16[off:off + n], g32[off:off + n], g64[off:off + n], gt[off:off + n]
             assert _rel(a, ref) <= 2e-2, (l, n, _rel(a, ref))
             assert _rel(a, b) <= 2e-2, (l, n, _rel(a, b))
+            assert _rel(tf, ref) <= 5e-3, (l, n, _rel(tf, ref))
             off += n
     assert _rel(g32, g64) <= 1e-4
 
