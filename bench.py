@@ -930,7 +930,7 @@ def train_leg(B, torch, n_points=65536, steps=20):
     gemm = sum(widths[l] * widths[l - 1] for l in range(1, len(widths)))
     flops_pt = 3 * 4 * 2 * gemm
     out = {"network": "2->6x128 tanh->1", "points": len(kind)}
-    for name, prec in (("fp32", B.FP32), ("bf16", B.BF16)):
+    for name, prec in (("fp32", B.FP32), ("tf32", B.TF32), ("bf16", B.BF16)):
         m = B.PinnModel(widths, [0.0, 0.0], [4.0, 1.0], seed=0)
         first = sum(m.train_step(Xd, kd, prob, lr=1e-3, prec=prec, want_loss=True))
         torch.cuda.synchronize()
@@ -968,6 +968,22 @@ def train_leg(B, torch, n_points=65536, steps=20):
                                "hbm_bytes_per_step": hbm, "hbm_bytes_minimal": minimal,
                                "hbm_traffic_ratio": hbm / minimal,
                                "hbm_frac_of_copy_bw": (hbm / (out["bf16"]["ms_per_step"] * 1e-3) / 1e9 / hbm_peak
+                                                       if hbm_peak else None)}
+    # TF32 on the tensor cores: the same tensor-pipe work against the TF32 peak
+    # (measured BF16 burst x nominal dense TF32/BF16 = 1.1/2.25); its HBM bytes:
+    # FP32 (t, z_1, z_2, z_3) of every hidden layer written by the forward and
+    # read by the adjoint and the weight gradient, dz of every layer written by
+    # the adjoint and read by the weight gradient (16 w bytes per point and
+    # layer each time), the seeds and the inputs
+    tf32_peak = bf16_peak * 1.1 / 2.25
+    ach = tensor_pt * n / (out["tf32"]["ms_per_step"] * 1e-3) / 1e12
+    hbm = n * (5 * nh * 16 * w + 2 * 16 + per_point)
+    out["tf32"]["roofline"] = {"bound": "tensor", "achieved": ach, "peak": tf32_peak, "unit": "TFLOP/s",
+                               "frac": ach / tf32_peak, "work": "3 x 4 x 2 x 5 x 128^2 flop per point (square layers)",
+                               "peak_note": "measured BF16 burst x nominal dense TF32/BF16 (1.1/2.25)",
+                               "hbm_bytes_per_step": hbm, "hbm_bytes_minimal": minimal,
+                               "hbm_traffic_ratio": hbm / minimal,
+                               "hbm_frac_of_copy_bw": (hbm / (out["tf32"]["ms_per_step"] * 1e-3) / 1e9 / hbm_peak
                                                        if hbm_peak else None)}
     return out
 

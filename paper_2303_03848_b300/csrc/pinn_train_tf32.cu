@@ -687,18 +687,30 @@ __global__ void __launch_bounds__(256, 2) train_tf32_wgrad_kernel(WgT32Args a) {
   if (warp == 0) tmem_dealloc(tmem, NCOLS);
 }
 
+// CTAs of a kernel resident per SM, from the device's limits: shared memory
+// (dynamic + static + the per-block reservation), threads, registers and the
+// tensor-memory columns each CTA allocates.
 template <typename K>
-cudaError_t prepare(K kern, size_t smem, int threads, uint32_t tmem_cols, int sms, int* per_sm) {
+cudaError_t prepare(K kern, size_t smem, int threads, uint32_t tmem_cols, int* per_sm) {
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess) return e;
-  int occ = 0;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem)) != cudaSuccess) return e;
-  const int tcap = (int)(512 / tmem_cols);  // tensor-memory columns per SM
-  if (occ > tcap) occ = tcap;
+  cudaFuncAttributes fa;
+  if ((e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess) return e;
+  int dev = 0, sm_smem = 0, reserved = 0, sm_threads = 0, sm_regs = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  cudaDeviceGetAttribute(&sm_threads, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+  cudaDeviceGetAttribute(&sm_regs, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+  int occ = (int)(512 / tmem_cols);
+  const size_t per_block = smem + fa.sharedSizeBytes + (size_t)reserved;
+  if ((int)(sm_smem / per_block) < occ) occ = (int)(sm_smem / per_block);
+  if (sm_threads / threads < occ) occ = sm_threads / threads;
+  const int regs = ((fa.numRegs + 7) / 8) * 8 * threads;
+  if (regs > 0 && sm_regs / regs < occ) occ = sm_regs / regs;
   if (occ < 1) return cudaErrorInvalidConfiguration;
   *per_sm = occ;
-  (void)sms;
   return cudaSuccess;
 }
 
@@ -730,9 +742,9 @@ cudaError_t run_tf32(const MlpDev& m, const LossArgs& la, float* ws, const Train
   constexpr uint32_t NCOLS = W <= 32 ? 32 : (W <= 64 ? 64 : 128);
   const size_t smem = t32_smem_bytes(W, DIN, m.n_lin);
   int occ_f = 0, occ_b = 0;
-  if ((e = prepare(train_tf32_fwd_kernel<DIN, W>, smem, 4 * W, NCOLS, sms, &occ_f)) != cudaSuccess) return e;
+  if ((e = prepare(train_tf32_fwd_kernel<DIN, W>, smem, 4 * W, NCOLS, &occ_f)) != cudaSuccess) return e;
   const size_t bsmem = t32_bwd_smem_bytes(W);
-  if ((e = prepare(train_tf32_bwd_kernel<DIN, W>, bsmem, 4 * W, NCOLS, sms, &occ_b)) != cudaSuccess) return e;
+  if ((e = prepare(train_tf32_bwd_kernel<DIN, W>, bsmem, 4 * W, NCOLS, &occ_b)) != cudaSuccess) return e;
   const int gf = ta.ntiles < sms * occ_f ? ta.ntiles : sms * occ_f;
   const int gb = ta.ntiles < sms * occ_b ? ta.ntiles : sms * occ_b;
   train_tf32_fwd_kernel<DIN, W><<<gf, 4 * W, smem, s>>>(ta);
@@ -757,7 +769,7 @@ cudaError_t run_tf32(const MlpDev& m, const LossArgs& la, float* ws, const Train
   constexpr uint32_t WG_COLS = W + 16 <= 32 ? 32 : (W + 16 <= 64 ? 64 : (W + 16 <= 128 ? 128 : 256));
   const size_t wsm = wg_smem_bytes<W>();
   int occ_w = 0;
-  if ((e = prepare(train_tf32_wgrad_kernel<DIN, W>, wsm, 256, WG_COLS, sms, &occ_w)) != cudaSuccess) return e;
+  if ((e = prepare(train_tf32_wgrad_kernel<DIN, W>, wsm, 256, WG_COLS, &occ_w)) != cudaSuccess) return e;
   int c = 0;
   for (int l = 1; l <= m.n_lin; ++l) {
     int k = sms * occ_w / m.n_lin;
