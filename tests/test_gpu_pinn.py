@@ -275,9 +275,9 @@ def test_tensor_core_gradient_every_layer(B, orc, widths):
     # each weight matrix and bias vector of the BF16 tensor-core gradient on its
     # own against the FP64 oracle, so that a lost stream, layer or bias term
     # cannot hide under the whole-vector bound.  Bound: BF16 operands round to
-    # 8 significant bits (unit roundoff 2^-9 ~ 2e-3); every gradient entry is a
+    # 8 significant bits (unit roundoff 2^-8 ~ 3.9e-3); every gradient entry is a
     # sum of products of two rounded operands whose inputs passed through up to
-    # six rounded layers; 2e-2 ~ 10 roundoffs (measured worst case 7e-3).
+    # six rounded layers; 2e-2 ~ 5 roundoffs (measured worst case 7e-3).
     m, om = _model(B, orc, widths, 8)
     for n_int in (1500, 6000):
         X, kind, prob, sok = _loss_case(widths, n_int, 128, 128, 4 + n_int)
@@ -434,9 +434,9 @@ def test_tf32_tensor_core_gradient_every_layer(B, orc, shape):
     # (tcgen05 kind::tf32 in the forward, the adjoint and the weight-gradient
     # GEMM over rows) on its own against the FP64 oracle.  Bound: TF32 operands
     # keep 11 significant bits (unit roundoff 2^-11 ~ 4.9e-4) and the forward's
-    # tanh has a relative error of the same size; 5e-3 ~ 10 roundoffs, as the
-    # BF16 bound (measured worst 7.6e-4).  The same blocks in BF16 must be more
-    # than 3x farther off, so a path that rounds to BF16 cannot pass.
+    # tanh has a relative error of the same size; 5e-3 ~ 10 roundoffs (measured
+    # worst 7.6e-4).  The same blocks in BF16 must be more than 3x farther off,
+    # so a path that rounds to BF16 cannot pass.
     widths = TF32_SHAPES[shape]
     m, om = _model(B, orc, widths, 8)
     for n_int in (1500, 6000):
