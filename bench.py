@@ -206,7 +206,7 @@ def train_network(B, torch, steps, seed=0, prec=None, params=None, decay_at=0.75
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / timed if steps > 1 else float("nan")
     loss1 = m.train_step(Xd, kd, cfg, lr=1e-4, prec=prec, want_loss=True)
-    name = {B.FP64: "fp64", B.FP32: "fp32", B.BF16: "bf16 (tcgen05)"}[prec]
+    name = {B.FP64: "fp64", B.FP32: "fp32", B.TF32: "tf32 (tcgen05)", B.BF16: "bf16 (tcgen05)"}[prec]
     return m, dict(steps=steps, precision=name, lr=f"1e-3, 1e-4 from step {int(decay_at * steps)}", ms_per_step=ms,
                    points=len(kind), loss_first=loss0, loss_last=loss1,
                    points_per_s=len(kind) / (ms * 1e-3) if ms == ms else None)
@@ -325,7 +325,7 @@ def run_ours(args):
     t0 = time.perf_counter()
     prob = B.Problem(insts, tuned=True, tuning_cache=cache)
     setup_s = time.perf_counter() - t0
-    net, train = train_parametric(B, torch, steps=args.pnet_steps)
+    net, train = train_parametric(B, torch, steps=args.pnet_steps, prec=B.PREC[args.pnet_prec])
     Uf = prob.serial_fine()
     torch.cuda.synchronize()
     kind = B.COARSE_PINN_IE
@@ -527,7 +527,7 @@ def single_leg(B, torch, args):
     prob = B.Problem(CFG)
     setup_ms = (time.perf_counter() - t0) * 1e3
     part = prob.partition(0)
-    model, train = train_network(B, torch, args.train_steps)
+    model, train = train_network(B, torch, args.train_steps, prec=B.PREC[args.train_prec])
     Uf = prob.serial_fine()
     torch.cuda.synchronize()
     flush = torch.zeros(32 * 1024 * 1024, dtype=torch.float64, device="cuda")
@@ -841,10 +841,12 @@ def batched_leg(B, torch, n_inst=4096, solve=True, rule_too=False, pinn_solve=Fa
     return out
 
 
-def train_parametric(B, torch, steps=16000, n_points=65536, decay_at=0.75):
+def train_parametric(B, torch, steps=16000, n_points=65536, decay_at=0.75, prec=None):
     """The batched workload's coarse network 5->6x128 tanh on (S, tau, sigma, r, K):
-    BF16 full-batch Adam on seeded collocation points over the batch's parameter box
-    (S in [0, 4K], tau in [0, 2]), step size 1e-3, then 1e-4 from decay_at x steps."""
+    full-batch Adam (BF16 on the tensor cores unless prec says otherwise) on seeded
+    collocation points over the batch's parameter box (S in [0, 4K], tau in [0, 2]),
+    step size 1e-3, then 1e-4 from decay_at x steps."""
+    prec = B.BF16 if prec is None else prec
     from paper_2303_03848_b300 import synth
 
     nb = n_points // 32
@@ -852,15 +854,16 @@ def train_parametric(B, torch, steps=16000, n_points=65536, decay_at=0.75):
     Xd, kd = torch.tensor(X, device="cuda"), torch.tensor(kind, device="cuda")
     prob = dict(K=1.0, sigma=0.2, r=0.05, T=2.0, Smax=8.0, Nx=5, P=1, fine_steps=1, coarse_steps=1)
     net = B.PinnModel(PNET_WIDTHS, PNET_LO, PNET_HI, seed=0)
-    first = net.train_step(Xd, kd, prob, lr=1e-3, smax_over_K=4.0, prec=B.BF16, want_loss=True)
+    first = net.train_step(Xd, kd, prob, lr=1e-3, smax_over_K=4.0, prec=prec, want_loss=True)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record()
     for i in range(1, steps - 1):
-        net.train_step(Xd, kd, prob, lr=1e-3 if i < decay_at * steps else 1e-4, smax_over_K=4.0, prec=B.BF16)
+        net.train_step(Xd, kd, prob, lr=1e-3 if i < decay_at * steps else 1e-4, smax_over_K=4.0, prec=prec)
     b.record()
-    last = net.train_step(Xd, kd, prob, lr=1e-4, smax_over_K=4.0, prec=B.BF16, want_loss=True)
+    last = net.train_step(Xd, kd, prob, lr=1e-4, smax_over_K=4.0, prec=prec, want_loss=True)
     ms = a.elapsed_time(b) / max(steps - 2, 1)
-    return net, {"steps": steps, "points": len(kind), "precision": "bf16 (tcgen05)", "lr": "1e-3, 1e-4 from "
+    name = {B.BF16: "bf16 (tcgen05)", B.TF32: "tf32 (tcgen05)", B.FP32: "fp32", B.FP64: "fp64"}[prec]
+    return net, {"steps": steps, "points": len(kind), "precision": name, "lr": "1e-3, 1e-4 from "
                  f"step {int(decay_at * steps)}", "ms_per_step": ms, "loss_first": first, "loss_last": last}
 
 
@@ -1372,6 +1375,10 @@ def main():
     ap.add_argument("--prec", default="bf16", choices=["fp64", "fp32", "tf32", "bf16"])
     ap.add_argument("--train-steps", type=int, default=20000, help="training steps of the single-instance network")
     ap.add_argument("--pnet-steps", type=int, default=16000, help="training steps of the batched workload's network")
+    ap.add_argument("--train-prec", default="bf16", choices=["fp64", "fp32", "tf32", "bf16"],
+                    help="training precision of the single-instance network")
+    ap.add_argument("--pnet-prec", default="tf32", choices=["fp64", "fp32", "tf32", "bf16"],
+                    help="training precision of the batched workload's network (its table stays --prec)")
     ap.add_argument("--single", type=int, default=1, help="include the single-instance leg (1/0)")
     ap.add_argument("--ref-seconds", type=float, default=8.0, help="oracle budget per step of --impl reference")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="oracle budget of the cpu_baseline")
