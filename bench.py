@@ -13,8 +13,9 @@ collocation points over the batch's parameter box.  A timed step is one
 Parareal solve of the whole batch (network table, corrections, initial
 iterate, then per iteration the fine propagation, the serial coarse sweep with
 the correction and the stop test) replayed from one CUDA graph; the stop
-tolerance is the largest of 1e-6, 3e-7, ... whose result is within 1e-6 of
-serial fine for every instance (checked before timing and after).  Inputs
+tolerance (on the increment norm) is the largest of 5e-6, 4e-6, 3e-6, ... whose
+result is within 1e-6 of serial fine for every instance (checked before timing
+and after).  Inputs
 (4.4 GB of states) are resident in HBM and larger than L2; a 256 MB write
 between timed steps evicts L2 anyway, outside the events.
 
@@ -46,6 +47,9 @@ CFG = dict(K=1.0, sigma=0.2, r=0.05, T=1.0, Smax=4.0, Nx=1024, P=32, fine_steps=
 WIDTHS = [2, 64, 64, 64, 64, 1]
 N_INTERIOR, N_BOUNDARY, N_EXPIRY = 16384, 512, 512
 TARGET = 1e-6
+# Device stop tolerances tried, loosest first: a solve's stop tolerance is the
+# first of these whose result is within TARGET of serial fine (every instance)
+TOL_LADDER = (5e-6, 4e-6, 3e-6, 2e-6, 1e-6, 5e-7, 3e-7, 1e-7, 3e-8, 1e-8, 3e-9, 1e-9, 1e-10, 1e-11, 0.0)
 METRIC = "Parareal solves/s at 1e-6 vs serial fine"
 # headline: the batched workload
 N_INST = 4096
@@ -213,7 +217,7 @@ def train_network(B, torch, steps, seed=0, prec=None, params=None, decay_at=0.75
 
 
 def choose_tol(prob, kind, model, prec, Uf, B):
-    for tol in (1e-6, 3e-7, 1e-7, 3e-8, 1e-8, 3e-9, 1e-9, 1e-10, 1e-11, 0.0):
+    for tol in TOL_LADDER:
         U, norms, stats, rc = prob.parareal_solve(kind, model=model, prec=prec, tol=tol)
         err = rel_error(U, Uf, CFG["P"], CFG["Nx"])
         if err <= TARGET:
@@ -334,7 +338,7 @@ def run_ours(args):
     # stop tolerance: the largest device tolerance whose solve is within 1e-6 of
     # serial fine for every instance
     tol = stats = errs = None
-    for cand in (1e-6, 3e-7, 1e-7, 3e-8, 1e-8, 0.0):
+    for cand in TOL_LADDER:
         U, _, stats, rc = prob.parareal_solve(kind, model=net, prec=prec, tol=cand, max_iter=maxP)
         errs = batch_errors(prob, U, Uf, torch)
         del U
@@ -712,7 +716,7 @@ def crossover_leg(B, torch, sizes=(8, 32, 128, 512, 1024, 2048, 4096), pnet_step
         torch.cuda.synchronize()
         row = {"instances": n, "serial_fine_ms": a.elapsed_time(b)}
         for name, kind, mdl in (("pinn_ie", B.COARSE_PINN_IE, net), ("ie", B.COARSE_IE, None)):
-            for tol in (1e-6, 3e-7, 1e-7, 3e-8, 1e-8, 0.0):
+            for tol in TOL_LADDER:
                 U, _, stats, rc = prob.parareal_solve(kind, model=mdl, prec=B.BF16, tol=tol, max_iter=64)
                 err = float(batch_errors(prob, U, Uf, torch).max())
                 del U
@@ -1103,7 +1107,7 @@ def sweep_leg(B, torch, model, Ps=(4, 8, 16, 32, 64), total_steps=32768):
         for name, kind, mdl in (("ie", BB.COARSE_IE, None), ("pinn", BB.COARSE_PINN, model),
                                 ("pinn_ie", BB.COARSE_PINN_IE, model)):
             tol = None
-            for cand in (1e-6, 1e-7, 1e-8, 1e-9, 1e-10, 0.0):
+            for cand in TOL_LADDER:
                 U, norms, stats, rc = prob.parareal_solve(kind, model=mdl, prec=BB.BF16, tol=cand)
                 err = rel_error(U, Uf, P, cfg["Nx"])
                 if err <= TARGET:
@@ -1327,13 +1331,42 @@ def oracle_sample(insts, widths, weights, lo, hi, kind: str, tol: float, budget_
     return rec, nxt
 
 
+def oracle_tol(insts, widths, weights, lo, hi, kind: str, n_cal: int = 3, max_nx: int = 1024):
+    """The reference arm's stop tolerance by the rule the GPU arm applies to its
+    batch: the loosest of TOL_LADDER whose oracle solves of the first n_cal sampled
+    instances (Nx <= max_nx) are within TARGET of the oracle's serial fine (not timed)."""
+    import numpy as np
+
+    import oracle as orc
+
+    orc.build()
+    okind = {"ie": orc.COARSE_IE, "pinn": orc.COARSE_PINN, "pinn_ie": orc.COARSE_PINN_IE}[kind]
+    m = orc.MLP(widths, weights, lo, hi) if widths else None
+    cal = [p for p in insts if p["Nx"] <= max_nx][:n_cal]
+    refs = []
+    for p in cal:
+        op = orc.params(**p)
+        refs.append((op, orc.pinn_table(op, m) if m is not None else None,
+                     np.asarray(orc.serial_fine(op)).reshape(p["P"] + 1, p["Nx"])[1:]))
+    for tol in TOL_LADDER:
+        worst = 0.0
+        for (op, g, uf), p in zip(refs, cal):
+            U, _, _ = orc.parareal(op, okind, g=g, tol=tol, max_iter=p["P"])
+            u = np.asarray(U).reshape(p["P"] + 1, p["Nx"])[1:]
+            worst = max(worst, float((np.linalg.norm(u - uf, axis=1) / np.linalg.norm(uf, axis=1)).max()))
+        if worst <= TARGET:
+            return tol
+    return 0.0
+
+
 def run_reference(args):
     """The oracle, as it stands, on the host cores, on the headline workload: each
     step solves a bounded sample of the batch (oracle_sample, ~budget seconds),
     continuing in seeded order; the step's value is the batch rate extrapolated
     from it.  The oracle cannot train the 5->6x128 network in this budget, so its
     table comes from the untrained Xavier network (seed 0); its iteration count
-    is reported beside the value."""
+    is reported beside the value.  Its stop tolerance follows the GPU arm's rule
+    (oracle_tol)."""
     from paper_2303_03848_b300 import synth
 
     ws = int(os.environ.get("WORLD_SIZE", "1"))
@@ -1342,9 +1375,10 @@ def run_reference(args):
         return
     insts = shard_instances(1, 0)
     w = synth.xavier_params(PNET_WIDTHS, 0)
+    tol = oracle_tol(insts, PNET_WIDTHS, w, PNET_LO, PNET_HI, "pinn_ie")
     vals, recs, nxt = [], [], 0
     for i in range(args.warmup + args.steps):
-        rec, nxt = oracle_sample(insts, PNET_WIDTHS, w, PNET_LO, PNET_HI, "pinn_ie", TARGET, args.ref_seconds,
+        rec, nxt = oracle_sample(insts, PNET_WIDTHS, w, PNET_LO, PNET_HI, "pinn_ie", tol, args.ref_seconds,
                                  start=nxt)
         if i >= args.warmup:
             vals.append(rec["value"])
@@ -1360,7 +1394,7 @@ def run_reference(args):
         "warmup": args.warmup, "ms_per_step": 1e3 * len(insts) / v, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "instances": len(insts), "coarse": "pinn_ie (network-anchored implicit Euler)",
-                   "tol": TARGET},
+                   "tol": tol, "target": TARGET},
         "cpu_baseline": cpu,
         "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
