@@ -21,6 +21,9 @@ constexpr int kPcrLevels = 5;  // PCR inside one warp: strides 1, 2, 4, 8, 16
 constexpr int kMaxWs = 64;     // warps per grid (cluster of up to 16 CTAs x 4 warps)
 constexpr unsigned kFull = 0xffffffffu;
 
+// Bring the line holding p (global memory) into L2; a hint, with no result.
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
 // One pricing instance as the kernels see it.
 struct Inst {
   double K, sigma, r, T, Smax, dS;

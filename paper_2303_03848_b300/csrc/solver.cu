@@ -914,11 +914,12 @@ __global__ void __launch_bounds__(NW * 32, 1) sweep_kernel(SweepArgs a) {
   if constexpr (C > 1) cg::this_cluster().sync();
   const bool init = a.k_iter < 0;
   const int n0 = init ? 0 : a.k_iter;
-  double* Un = a.unext + in.state_off;          // U^{k+1}
-  const double* Uc = a.ucur + in.state_off;     // U^k
-  double* Gold = a.gold + in.slice_off;         // G(U^k_n), P slices
-  const double* Fv = a.fbuf + in.slice_off;     // F(U^k_n), P slices
-  const double* gt = a.gtab + in.state_off;     // network table
+  // five distinct buffers: no store below can change a value loaded from another
+  double* __restrict__ Un = a.unext + in.state_off;          // U^{k+1}
+  const double* __restrict__ Uc = a.ucur + in.state_off;     // U^k
+  double* __restrict__ Gold = a.gold + in.slice_off;         // G(U^k_n), P slices
+  const double* __restrict__ Fv = a.fbuf + in.slice_off;     // F(U^k_n), P slices
+  const double* __restrict__ gt = a.gtab + in.state_off;     // network table
   // iteration k starts from U^{k+1}_k = U^k_k (exact since iteration k-1);
   // the initial sweep starts from the payoff already in slot 0
   const double* Vs = (init ? Un : Uc) + (int64_t)n0 * Nx;
@@ -946,6 +947,25 @@ __global__ void __launch_bounds__(NW * 32, 1) sweep_kernel(SweepArgs a) {
     double Gv[M];
     double G0, GB;
     double fa[kAhead ? M : 1], ga[kAhead ? M : 1], oa[kAhead ? M : 1], ca[kAhead ? M : 1];
+    if constexpr (!kAhead) {
+      // this slice's F, old G, U^k and table rows of the thread into L2 while the
+      // coarse step runs (its M rows span at most two 128-byte lines per array)
+      const int ja = max(g * M - in.Np + 1, 0), jb = min(g * M + M - in.Np, Nx - 1);
+      if (ja <= jb) {
+        if (!init) {
+          prefetch_l2(Fv + (int64_t)n * Nx + ja);
+          prefetch_l2(Fv + (int64_t)n * Nx + jb);
+          prefetch_l2(Gold + (int64_t)n * Nx + ja);
+          prefetch_l2(Gold + (int64_t)n * Nx + jb);
+          prefetch_l2(Uc + (int64_t)(n + 1) * Nx + ja);
+          prefetch_l2(Uc + (int64_t)(n + 1) * Nx + jb);
+        }
+        if (anchored) {
+          prefetch_l2(gt + (int64_t)(n + 1) * Nx + ja);
+          prefetch_l2(gt + (int64_t)(n + 1) * Nx + jb);
+        }
+      }
+    }
     if constexpr (kAhead) {
 #pragma unroll
       for (int k = 0; k < M; ++k) {
@@ -994,23 +1014,39 @@ __global__ void __launch_bounds__(NW * 32, 1) sweep_kernel(SweepArgs a) {
       GB = VB + (gt[(int64_t)(n + 1) * Nx + Nx - 1] - gt[(int64_t)n * Nx + Nx - 1]);
     }
     double num = 0.0, den = 0.0;
-    double* out = Un + (int64_t)(n + 1) * Nx;
-    const double* old = Uc + (int64_t)(n + 1) * Nx;
-    double* go = Gold + (int64_t)n * Nx;
-    const double* fv = Fv + (int64_t)n * Nx;
+    double* __restrict__ out = Un + (int64_t)(n + 1) * Nx;
+    const double* __restrict__ old = Uc + (int64_t)(n + 1) * Nx;
+    double* __restrict__ go = Gold + (int64_t)n * Nx;
+    const double* __restrict__ fv = Fv + (int64_t)n * Nx;
+    // rows in chunks of KC: all loads of a chunk before its stores, so that a
+    // chunk costs one memory round trip (4 rows at M = 32, where registers run out)
+    constexpr int KC = kAhead ? M : (M < 8 ? M : (M >= 32 ? 4 : 8));
 #pragma unroll
-    for (int k = 0; k < M; ++k) {
-      const int j = g * M + k - in.Np + 1;
-      if (j >= 1 && j <= Nx - 2) {
-        const double fj = kAhead ? fa[k] : (init ? 0.0 : fv[j]), gj = kAhead ? ga[k] : (init ? 0.0 : go[j]);
-        const double v = init ? Gv[k] : fj + (Gv[k] - gj);
-        go[j] = Gv[k];
-        out[j] = v;
-        V[k] = v;
-        if (!init) {
-          const double d = v - (kAhead ? oa[k] : old[j]);
-          num = fma(d, d, num);
-          den = fma(v, v, den);
+    for (int k0 = 0; k0 < M; k0 += KC) {
+      double fj[KC], gj[KC], oj[KC];
+#pragma unroll
+      for (int q = 0; q < KC; ++q) {
+        const int k = k0 + q;
+        const int j = g * M + k - in.Np + 1;
+        const bool in_row = j >= 1 && j <= Nx - 2 && !init;
+        fj[q] = kAhead ? fa[k] : (in_row ? fv[j] : 0.0);
+        gj[q] = kAhead ? ga[k] : (in_row ? go[j] : 0.0);
+        oj[q] = kAhead ? oa[k] : (in_row ? old[j] : 0.0);
+      }
+#pragma unroll
+      for (int q = 0; q < KC; ++q) {
+        const int k = k0 + q;
+        const int j = g * M + k - in.Np + 1;
+        if (j >= 1 && j <= Nx - 2) {
+          const double v = init ? Gv[k] : fj[q] + (Gv[k] - gj[q]);
+          go[j] = Gv[k];
+          out[j] = v;
+          V[k] = v;
+          if (!init) {
+            const double d = v - oj[q];
+            num = fma(d, d, num);
+            den = fma(v, v, den);
+          }
         }
       }
     }
