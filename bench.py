@@ -684,7 +684,7 @@ def run_fine_batched(args):
                       "sum_nx_p": sum(p["Nx"] * p["P"] for p in insts)}), flush=True)
 
 
-def crossover_leg(B, torch, sizes=(8, 32, 128, 512, 1024, 2048, 4096), pnet_steps=16000):
+def crossover_leg(B, torch, sizes=(8, 32, 128, 512, 1024, 2048, 4096), pnet_steps=16000, pnet_prec=None):
     """Where Parareal pays on one GPU: the first n instances of the seeded batch for
     growing n, serial fine against network-anchored and IE-coarse Parareal to 1e-6
     (graph-replayed solves, the loosest device tolerance within 1e-6 of serial fine).
@@ -692,7 +692,7 @@ def crossover_leg(B, torch, sizes=(8, 32, 128, 512, 1024, 2048, 4096), pnet_step
     slices in sequence), so the slices' parallelism pays; thousands of instances
     fill the GPU without it, and Parareal's extra fine work only costs."""
     insts_all = shard_instances(1, 0)
-    net, tr = train_parametric(B, torch, steps=pnet_steps)
+    net, tr = train_parametric(B, torch, steps=pnet_steps, prec=pnet_prec)
     rows = []
 
     def graph_ms(g):
@@ -1441,7 +1441,7 @@ def main():
         from paper_2303_03848_b300 import build as BUILD
 
         BUILD.build()
-        print(json.dumps(crossover_leg(B, torch, pnet_steps=args.pnet_steps)), flush=True)
+        print(json.dumps(crossover_leg(B, torch, pnet_steps=args.pnet_steps, pnet_prec=B.PREC[args.pnet_prec])), flush=True)
     elif args.mode == "single":
         import torch
 
