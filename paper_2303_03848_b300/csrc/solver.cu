@@ -542,8 +542,17 @@ __device__ __forceinline__ void step_finish(double (&W)[M], double (&x)[M], Solv
     K0 = fma(rg.sa, Xtp, fma(rg.sb, Xt, CN ? fma(rg.s0, x[0], -W[0]) : rg.s0 * x[0]));
     K1 = CN ? fma(rg.sp, Xt, -W[1]) : rg.sp * Xt;
   }
-  if constexpr (C == 1) {
+  if constexpr (C == 1 && S2 == 1) {
     __syncthreads();
+  } else if constexpr (C == 1) {
+    // slice pairs in one CTA: each group waits on its own named barrier (ids 1
+    // and 2; 0 is the block barrier), so a group whose slice is inactive
+    // takes no step barrier at all
+    if (gi == 0) {
+      asm volatile("bar.sync 1, %0;" ::"n"(NW * 32) : "memory");
+    } else {
+      asm volatile("bar.sync 2, %0;" ::"n"(NW * 32) : "memory");
+    }
   } else {
     if (!rg.fail && !mbar_wait(smem_addr(&sm.bar[gi][par]), (uint32_t)(seq >> 1) & 1u)) rg.fail = 1;
   }
@@ -716,7 +725,6 @@ __device__ __forceinline__ double slice_KeN(const Inst& in, int n) {
 
 template <int M, int NW, int C, bool CN, int S2>
 __global__ void __launch_bounds__(S2 * NW * 32, 1) prop_kernel(PropArgs a) {
-  static_assert(S2 == 1 || C > 1, "slice pairs exchange through mbarriers only (no block barrier inside a step)");
   constexpr int T = NW * 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SolverSmem<M, NW, C, S2>& sm = *reinterpret_cast<SolverSmem<M, NW, C, S2>*>(smem_raw);
@@ -1306,10 +1314,13 @@ static cudaError_t launch_persistent(Kern kernel, int threads, int C, int smem, 
   return cudaLaunchKernelEx(&cfg, kernel, a);
 }
 
-// Classes whose fine propagation can also run two slices per CTA (clusters,
-// 16 or more rows per thread: the tables are large and one CTA fills an SM).
-#define BSP_FOR_EACH_S2_CLASS(X) \
-  X(16, 4, 2) X(32, 4, 2) X(16, 4, 4) X(32, 4, 4) X(16, 4, 8) X(32, 4, 8) X(16, 4, 16) X(32, 4, 16)
+// Classes whose fine propagation can also run two slices per CTA (16 or more
+// rows per thread: the tables are large, and two slices of one instance share
+// one copy; one-CTA grids step on a named barrier per slice, clusters on their
+// mbarriers).
+#define BSP_FOR_EACH_S2_CLASS(X)                                                                  \
+  X(16, 2, 1) X(32, 1, 1) X(32, 2, 1) X(16, 4, 1) X(32, 4, 1) X(16, 4, 2) X(32, 4, 2) X(16, 4, 4)      \
+  X(32, 4, 4) X(16, 4, 8) X(32, 4, 8) X(16, 4, 16) X(32, 4, 16)
 
 bool s2_supported(int M, int NW, int C) {
 #define X(MM, WW, CC) \
