@@ -289,13 +289,15 @@ def _cache_store(path, instances, chosen):
 class Problem:
     """Handle of bs_problem_init: one or more pricing instances on the current device."""
 
-    def __init__(self, instances, tuned: bool = False, tuning_cache=None):
+    def __init__(self, instances, tuned: bool = False, tuning_cache=None, partitions=None):
         """tuned: pick each grid size's partition by timing (bs_problem_init_tuned); the
         timed candidates are kept in self.tuning.  tuning_cache: path of a JSON file of
         earlier tuned choices, keyed by device, grid size and slice count; when it holds
         every grid size of the instances the problem is set up from it without timing
         (bs_problem_init_partitioned), else the tuner runs and its choices are added.
-        self.tuning_source says which ("timed", "cache" or None)."""
+        partitions: explicit choices instead, a list of dicts with keys Nx, M, NW, C, S2
+        covering every grid size (bs_problem_init_partitioned).
+        self.tuning_source says which ("timed", "cache", "given" or None)."""
         if isinstance(instances, dict):
             instances = [instances]
         self.instances = [dict(p) for p in instances]
@@ -303,7 +305,14 @@ class Problem:
         h = ctypes.c_void_p()
         self.tuning, self.tuning_source = [], None
         cached = _cache_lookup(tuning_cache, self.instances) if (tuned and tuning_cache) else None
-        if cached is not None:
+        if partitions is not None:
+            parts = (Tuning * len(partitions))(*[Tuning(e["Nx"], e["M"], e["NW"], e["C"], e.get("S2", 1), 0.0, 1)
+                                                for e in partitions])
+            _check(lib().bs_problem_init_partitioned(arr, len(self.instances), parts, len(partitions),
+                                                     ctypes.byref(h)), "bs_problem_init_partitioned")
+            self.tuning = [dict(e, ms=None, chosen=True) for e in partitions]
+            self.tuning_source = "given"
+        elif cached is not None:
             parts = (Tuning * len(cached))(*[Tuning(e["Nx"], e["M"], e["NW"], e["C"], e["S2"], 0.0, 1)
                                             for e in cached])
             _check(lib().bs_problem_init_partitioned(arr, len(self.instances), parts, len(cached), ctypes.byref(h)),
