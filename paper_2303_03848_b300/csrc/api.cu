@@ -156,6 +156,11 @@ struct bs_problem {
   int norms_cap = 0;
   bsp::Ctrl* ctrl = nullptr;
   int* d_status = nullptr;  // BS_TIMEOUT once a bounded exchange wait gave up
+  // per solve, zeroed at its start: the fine launches' task counters
+  // [(maxP + 1) x classes, iteration k at row k + 1] and the count of instances
+  // still iterating after iteration k [maxP]
+  int* d_sched = nullptr;
+  int64_t sched_n = 0;
 };
 
 struct pinn_model {
@@ -208,6 +213,7 @@ void bs_problem_destroy(bs_problem* prob) {
   cudaFree(prob->norms_dev);
   cudaFree(prob->ctrl);
   cudaFree(prob->d_status);
+  cudaFree(prob->d_sched);
   delete prob;
 }
 
@@ -281,6 +287,11 @@ static int problem_create(const bs_params* p, int32_t n_instances, const Part* p
   if ((e = dalloc(&prob->d_insts, n_instances)) != cudaSuccess ||
       (e = dalloc(&prob->pool, (size_t)coef)) != cudaSuccess || (e = dalloc(&prob->exptab, (size_t)ex)) != cudaSuccess ||
       (e = dalloc(&prob->d_status, 1)) != cudaSuccess || (e = cudaMemset(prob->d_status, 0, sizeof(int))) != cudaSuccess) {
+    bs_problem_destroy(prob);
+    return map_err(e);
+  }
+  prob->sched_n = (int64_t)(prob->maxP + 1) * (int64_t)prob->classes.size() + prob->maxP;
+  if ((e = dalloc(&prob->d_sched, (size_t)prob->sched_n)) != cudaSuccess) {
     bs_problem_destroy(prob);
     return map_err(e);
   }
@@ -882,6 +893,10 @@ static int solve_impl(bs_problem* prob, int coarse_kind, const pinn_model* model
   if (w.clear_normbuf &&
       (e = cudaMemsetAsync(w.normbuf, 0, sizeof(double) * 2 * prob->total_norm, s)) != cudaSuccess)
     return map_err(e);
+  if ((e = cudaMemsetAsync(prob->d_sched, 0, sizeof(int) * (size_t)prob->sched_n, s)) != cudaSuccess)
+    return map_err(e);
+  const int ncls = (int)prob->classes.size();
+  int* live = prob->d_sched + (int64_t)(prob->maxP + 1) * ncls;  // live[k]: after iteration k
   // a1: network table on (S_j, tau_n), Dirichlet nodes exact
   if (pinn) {
     Range r("network table");
@@ -927,6 +942,7 @@ static int solve_impl(bs_problem* prob, int coarse_kind, const pinn_model* model
       a.kind = sweep_kind;
       a.k_iter = k;
       a.ctrl = k < 0 ? nullptr : w.ctrl;
+      a.n_live = k > 0 ? live + (k - 1) : nullptr;
       a.ucur = cur;
       a.unext = nxt;
       a.gold = w.gold;
@@ -948,8 +964,11 @@ static int solve_impl(bs_problem* prob, int coarse_kind, const pinn_model* model
     double* cur = (k & 1) ? w.buf1 : w.buf0;
     double* nxt = (k & 1) ? w.buf0 : w.buf1;
     // a3 (+ a5 fused for the state-independent network coarse propagator)
-    for (auto& c : prob->classes) {
+    for (int ci = 0; ci < ncls; ++ci) {
+      const auto& c = prob->classes[ci];
       bsp::PropArgs a{};
+      a.task_ctr = prob->d_sched + (int64_t)(k + 1) * ncls + ci;
+      a.n_live = k > 0 ? live + (k - 1) : nullptr;
       a.insts = prob->d_insts;
       a.ids = c.d_ids;
       a.pool = prob->pool;
@@ -977,8 +996,8 @@ static int solve_impl(bs_problem* prob, int coarse_kind, const pinn_model* model
     if (coarse_kind != BS_COARSE_PINN) {
       if ((e = sweep(k, cur, nxt)) != cudaSuccess) return map_err(e);
     }
-    if ((e = bsp::launch_parareal_finalize(prob->d_insts, n, w.normbuf, k, tol, max_iter, w.ctrl, w.norms, s)) !=
-        cudaSuccess)
+    if ((e = bsp::launch_parareal_finalize(prob->d_insts, n, w.normbuf, k, tol, max_iter, w.ctrl, w.norms, live + k,
+                                           s)) != cudaSuccess)
       return map_err(e);
   }
   if ((e = bsp::launch_copy_result(prob->d_insts, n, w.ctrl, w.buf0, w.buf1, U_out, s)) != cudaSuccess)

@@ -26,7 +26,9 @@ struct PropArgs {
   const double* uold;        // kPinnFused: U^k (state layout)
   double* normbuf;           // kPinnFused: (num, den) per (instance, boundary index, cluster rank)
   int* status;               // nullable: BS_TIMEOUT recorded here if a bounded wait gave up
-  int n_inst, maxP;          // tasks = n_inst x maxP (instance ids[i], slice n), set by launch_prop
+  int* task_ctr;             // nullable, zero at launch: one-CTA grids take their tasks from this counter
+  const int* n_live;         // nullable: instances not yet converged; the launch does nothing when 0
+  int n_inst, maxP;          // tasks = n_inst x ceil((maxP - max(k_iter, 0)) / S2), set by launch_prop
 };
 
 struct SerialArgs {
@@ -53,6 +55,7 @@ struct SweepArgs {
   const double* gtab;  // network table (state layout), increment kind; corrections c_n, anchored kind
   double* normbuf;
   int* status;         // nullable: BS_TIMEOUT recorded here if a bounded wait gave up
+  const int* n_live;   // nullable: instances not yet converged; the launch does nothing when 0
 };
 
 bool partition_supported(int M, int NW, int C);
@@ -68,7 +71,7 @@ cudaError_t launch_sweep(int M, int NW, int C, const SweepArgs& a, int n_inst, c
 cudaError_t launch_parareal_init(const Inst* d_insts, int n_inst, double* buf0, double* buf1, const double* gtab,
                                  int pinn, Ctrl* ctrl, double* norms, int max_iter, cudaStream_t s);
 cudaError_t launch_parareal_finalize(const Inst* d_insts, int n_inst, const double* normbuf, int k, double tol,
-                                     int max_iter, Ctrl* ctrl, double* norms, cudaStream_t s);
+                                     int max_iter, Ctrl* ctrl, double* norms, int* live_out, cudaStream_t s);
 cudaError_t launch_copy_result(const Inst* d_insts, int n_inst, const Ctrl* ctrl, const double* buf0,
                                const double* buf1, double* out, cudaStream_t s);
 cudaError_t launch_grid_points(const Inst* d_insts, int n_inst, int d_in, double* X, cudaStream_t s);

@@ -727,20 +727,35 @@ template <int M, int NW, int C, bool CN, int S2>
 __global__ void __launch_bounds__(S2 * NW * 32, 1) prop_kernel(PropArgs a) {
   constexpr int T = NW * 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_task;
+  // every instance has converged: nothing to do (the same value for every CTA)
+  if (a.n_live != nullptr && *a.n_live == 0) return;
   SolverSmem<M, NW, C, S2>& sm = *reinterpret_cast<SolverSmem<M, NW, C, S2>*>(smem_raw);
   const int t = lthread<NW>(), gi = lgroup<NW>(), c = cta_rank<C>();
   SolverRegs rg;
   exchange_init<M, NW, C, S2>(sm, rg);
   int seq = 0;
-  // persistent: cluster q walks the task groups q, q + clusters, ...; a task
-  // group is S2 consecutive slices of one instance (group gi takes slice
-  // S2 j + gi).  Skipping a whole group is uniform over the cluster; a group
-  // whose own slice is inactive still takes every block and cluster barrier.
-  const int ngrp = (a.maxP + S2 - 1) / S2;
+  // persistent: a task group is S2 consecutive slices of one instance from
+  // slice kb = max(k_iter, 0) on (group gi takes slice kb + S2 j + gi), so at
+  // most one group per instance is half idle.  Clusters walk the task groups
+  // q, q + clusters, ...; one-CTA grids given a counter take the next group
+  // from it, which balances the load when slices before kb or instances that
+  // have converged leave some groups empty.  Skipping a whole group is uniform
+  // over the cluster; a group whose own slice is inactive still takes every
+  // block and cluster barrier.
+  const int kb = a.k_iter > 0 ? a.k_iter : 0;
+  const int ngrp = (a.maxP - kb + S2 - 1) / S2;
   const int64_t n_cl = gridDim.x / C, ntask = (int64_t)a.n_inst * ngrp;
-  for (int64_t task = blockIdx.x / C; task < ntask; task += n_cl) {
+  const bool dyn = C == 1 && a.task_ctr != nullptr;
+  auto grab = [&]() -> int64_t {  // every thread of the CTA calls it
+    __syncthreads();              // all threads have read the previous value
+    if (threadIdx.x == 0) s_task = atomicAdd(a.task_ctr, 1);
+    __syncthreads();
+    return (int64_t)s_task;
+  };
+  for (int64_t task = dyn ? grab() : blockIdx.x / C; task < ntask; task = dyn ? grab() : task + n_cl) {
     const int idx = a.ids[task / ngrp];
-    const int n0 = (int)(task % ngrp) * S2;
+    const int n0 = kb + (int)(task % ngrp) * S2;
     const Inst in = a.insts[idx];
     auto live = [&](int n) {
       if (n >= in.P) return false;
@@ -905,6 +920,7 @@ __global__ void __launch_bounds__(NW * 32, 1) sweep_kernel(SweepArgs a) {
   constexpr int T = NW * 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SolverSmem<M, NW, C>& sm = *reinterpret_cast<SolverSmem<M, NW, C>*>(smem_raw);
+  if (a.n_live != nullptr && *a.n_live == 0) return;  // every instance has converged
   const int idx = a.ids[blockIdx.y];
   const Inst in = a.insts[idx];
   if (a.ctrl != nullptr && a.ctrl[idx].done) return;  // uniform over the cluster
@@ -1130,7 +1146,7 @@ __global__ void parareal_init_kernel(const Inst* insts, int n_inst, double* buf0
 // e_k = max_n ||U^{k+1}_n - U^k_n|| / ||U^{k+1}_n|| over the slices updated in
 // iteration k, then the stop rule of parareal_solve.  One warp per instance.
 __global__ void parareal_finalize_kernel(const Inst* insts, int n_inst, const double* normbuf, int k, double tol,
-                                         int max_iter, Ctrl* ctrl, double* norms) {
+                                         int max_iter, Ctrl* ctrl, double* norms, int* live_out) {
   const int idx = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
   const int L = threadIdx.x & 31;
   if (idx >= n_inst) return;
@@ -1168,6 +1184,8 @@ __global__ void parareal_finalize_kernel(const Inst* insts, int n_inst, const do
   } else if (k + 1 >= max_iter) {
     ctrl[idx].done = 1;
     ctrl[idx].status = 4;
+  } else if (live_out != nullptr) {
+    atomicAdd(live_out, 1);  // still iterating after iteration k
   }
 }
 
@@ -1291,7 +1309,9 @@ static cudaError_t launch_persistent(Kern kernel, int threads, int C, int smem, 
   if (e != cudaSuccess) return e;
   if (C > 8 && (e = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess)
     return e;
-  const int64_t ntask = (int64_t)n_inst * ((maxP + s2 - 1) / s2);
+  const int kb = a.k_iter > 0 ? a.k_iter : 0;
+  const int64_t ntask = maxP > kb ? (int64_t)n_inst * ((maxP - kb + s2 - 1) / s2) : 0;
+  if (ntask <= 0) return cudaSuccess;  // no slice from kb on
   cudaLaunchConfig_t cfg = {};
   cfg.blockDim = dim3(threads, 1, 1);
   cfg.dynamicSmemBytes = smem;
@@ -1387,8 +1407,9 @@ cudaError_t launch_parareal_init(const Inst* d_insts, int n_inst, double* buf0, 
 }
 
 cudaError_t launch_parareal_finalize(const Inst* d_insts, int n_inst, const double* normbuf, int k, double tol,
-                                     int max_iter, Ctrl* ctrl, double* norms, cudaStream_t s) {
-  parareal_finalize_kernel<<<(n_inst + 3) / 4, 128, 0, s>>>(d_insts, n_inst, normbuf, k, tol, max_iter, ctrl, norms);
+                                     int max_iter, Ctrl* ctrl, double* norms, int* live_out, cudaStream_t s) {
+  parareal_finalize_kernel<<<(n_inst + 3) / 4, 128, 0, s>>>(d_insts, n_inst, normbuf, k, tol, max_iter, ctrl, norms,
+                                                            live_out);
   return cudaGetLastError();
 }
 
