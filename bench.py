@@ -70,7 +70,7 @@ FINE_TRAFFIC_BYTES = {(2, 4, 4): 425216}
 # workload per grid point and slice (all partition classes; captured on the
 # batch's first 512 instances, profiles/), or None while no capture of the
 # current code exists
-BATCH_TRAFFIC_PER_PT_SLICE = 13.60
+BATCH_TRAFFIC_PER_PT_SLICE = 13.64
 
 
 def serial_fine_ms(B, torch, prob, insts, Uf):
