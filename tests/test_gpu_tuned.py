@@ -175,6 +175,61 @@ def test_slice_pairs_parareal_network_and_ie_bitwise(B, monkeypatch, P):
     assert torch.equal(res[2][0], res[2][4])  # k = P reproduces serial fine
 
 
+@pytest.mark.parametrize("shape", [(32, 4, 1), (16, 2, 1)])
+@pytest.mark.parametrize("P", [4, 5])
+def test_counter_fed_slice_pairs_parareal_bitwise(B, orc, monkeypatch, shape, P):
+    # one-CTA grids in a Parareal solve take their task groups from a counter and
+    # start them at slice k, so with odd k the pairs are (k, k+1), ...: the
+    # iterates, norms and iteration counts equal one slice per CTA bit for bit,
+    # and the implicit-Euler solve matches the oracle's
+    m, nw, c = shape
+    Nx = {(32, 4, 1): 4000, (16, 2, 1): 1000}[shape]
+    insts = [dict(K=0.8 + 0.2 * i, sigma=0.25 + 0.05 * i, r=0.02 + 0.01 * i, T=0.5, Smax=4.0 * (0.8 + 0.2 * i),
+                  Nx=Nx, P=P, fine_steps=6, coarse_steps=1) for i in range(3)]
+    net = B.PinnModel([2, 32, 32, 1], [0.0, 0.0], [4.0, 0.5], seed=3)
+    res = {}
+    for s2 in (1, 2):
+        monkeypatch.setenv("BSP_PARTITION", f"{m},{nw},{c},{s2}")
+        prob = B.Problem(insts)
+        assert prob.slices_per_cta(0) == s2
+        Ui, ni, si, ri = prob.parareal_solve(B.COARSE_IE, tol=1e-9)
+        Ua, na, sa, ra = prob.parareal_solve(B.COARSE_PINN_IE, model=net, prec=B.FP64, tol=0.0)
+        assert ri == B.BS_OK and ra == B.BS_OK and prob.device_status() == B.BS_OK
+        res[s2] = (Ui, ni, [x["iterations"] for x in si], Ua, na, prob.serial_fine())
+    for a, b in zip(res[1], res[2]):
+        if isinstance(a, torch.Tensor):
+            assert torch.equal(a, b)
+        else:
+            np.testing.assert_array_equal(np.asarray(a), np.asarray(b))
+    assert torch.equal(res[2][3], res[2][5])  # tol 0: k = P reproduces serial fine
+    U = res[2][0].cpu().numpy()
+    off = 0
+    for i, p in enumerate(insts):
+        Ur, nr, st = orc.parareal(orc.params(**p), orc.COARSE_IE, tol=1e-9)
+        assert res[2][2][i] == len(nr)
+        np.testing.assert_allclose(res[2][1][i, :len(nr)], nr, rtol=1e-6)
+        steps = p["fine_steps"] * P
+        kappa = 1.0 + 0.5 * p["T"] / steps * (2.0 * p["sigma"] ** 2 * (Nx - 2) ** 2 + p["r"] * (Nx - 2) + p["r"])
+        _close(U[off:off + (P + 1) * Nx], Ur.ravel(), max(RTOL, 2.0 * kappa * 2.0 ** -53 * steps))
+        off += (P + 1) * Nx
+
+
+def test_converged_batch_skips_the_remaining_iterations(B):
+    # once the stop-rule kernel counts no instance still iterating, the later
+    # launches return at once: a solve allowed 64 iterations equals one allowed
+    # just past the slowest instance's count, statistics included
+    insts = synth.batched_instances(5, 6, P=16, fine_steps=32, coarse_steps=1, Nx_choices=(256, 1024))
+    prob = B.Problem(insts, tuned=True)
+    U1, n1, s1, r1 = prob.parareal_solve(B.COARSE_IE, tol=1e-6, max_iter=16)
+    kmax = max(x["iterations"] for x in s1)
+    assert r1 == B.BS_OK and kmax < 16  # the oracle takes 5 or 6 iterations on these instances
+    U2, n2, s2, r2 = prob.parareal_solve(B.COARSE_IE, tol=1e-6, max_iter=kmax)
+    assert r2 == B.BS_OK and torch.equal(U1, U2)
+    assert [x["iterations"] for x in s1] == [x["iterations"] for x in s2]
+    np.testing.assert_array_equal(n1[:, :kmax], n2[:, :kmax])
+    assert np.isnan(n1[:, kmax:]).all()
+
+
 def test_slice_pair_rule_follows_the_slice_count(B, monkeypatch):
     # a 30000-point grid takes a clustered partition with 16 or 32 rows per
     # thread (16 CTAs for 8 slices, 8 CTAs for 40); pairs once the slices can
