@@ -339,7 +339,9 @@ int bs_problem_init(const bs_params* p, int32_t n_instances, bs_problem** out) {
   }
   if (forced.M == 0) {
     // slice pairs where the class supports them and has slices enough to keep
-    // every cluster busy twice over (throughput rather than latency);
+    // every cluster busy twice over (throughput rather than latency); on one-CTA
+    // grids only with 32 rows per thread, where one slice per CTA leaves one
+    // warp per sub-partition (16 rows fit two CTAs per SM already);
     // BSP_S2 = 1 or 2 decides instead
     int s2_env = 0;
     if (const char* env = getenv("BSP_S2")) s2_env = atoi(env);
@@ -348,7 +350,7 @@ int bs_problem_init(const bs_params* p, int32_t n_instances, bs_problem** out) {
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     for (int i = 0; i < n_instances; ++i) {
       Part& q = parts[i];
-      if (!bsp::s2_supported(q.M, q.NW, q.C)) continue;
+      if (!bsp::s2_supported(q.M, q.NW, q.C) || (q.C == 1 && q.M < 32 && !s2_env)) continue;
       int64_t slices = 0;
       for (int j = 0; j < n_instances; ++j)
         if (parts[j].M == q.M && parts[j].NW == q.NW && parts[j].C == q.C) slices += p[j].P;
