@@ -308,6 +308,7 @@ __device__ __forceinline__ int lgroup() {
 struct SolverRegs {
   double kap, nu, sigp, isigp;
   double m1[kPcrLevels], m2[kPcrLevels], inv, ra, rc;
+  double mlast;  // the last PCR level's one multiplier (lanes 0-15 couple up, 16-31 down)
   // M = 2: the step's state update written as K + e Y_{w-1} + f Y_w per row, with
   // K formed before the cross-warp unknowns arrive (see step_finish)
   double s0, sa, sb, e0, f0, sp, g1, h1;
@@ -383,6 +384,7 @@ __device__ __forceinline__ void load_solver(const double* __restrict__ cb, Solve
     rg.m2[lv] = cb[coef_pcr_off(5 + lv, g, M, GT)];
   }
   rg.inv = cb[coef_pcr_off(10, g, M, GT)];
+  rg.mlast = (t & 31) < 16 ? rg.m2[kPcrLevels - 1] : rg.m1[kPcrLevels - 1];
   rg.ra = cb[coef_resp_off(0, g, M, GT)];
   rg.rc = cb[coef_resp_off(1, g, M, GT)];
   if constexpr (M == 2) {
@@ -477,12 +479,15 @@ __device__ __forceinline__ double step_reduce(const double (&W)[M], double (&x)[
   // 3. in-warp PCR on lanes 0..30 with zero external couplings
   double Rp = (L == 31) ? 0.0 : R;
 #pragma unroll
-  for (int lv = 0; lv < kPcrLevels; ++lv) {
+  for (int lv = 0; lv < kPcrLevels - 1; ++lv) {
     const int s = 1 << lv;
     const double up = __shfl_up_sync(kFull, Rp, s);
     const double dn = __shfl_down_sync(kFull, Rp, s);
     Rp = fma(-rg.m1[lv], up, fma(-rg.m2[lv], dn, Rp));
   }
+  // stride 16: lane L couples to lane L ^ 16 only (the set-up zeroes the other
+  // multiplier), so one exchange and one FMA do what the two-sided level does
+  Rp = fma(-rg.mlast, __shfl_xor_sync(kFull, Rp, 16), Rp);
   const double Xt = Rp * rg.inv;
   // 4. publish this warp's boundary values to every CTA of the grid
   const double p0 = __shfl_sync(kFull, x[0], 0);
