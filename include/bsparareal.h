@@ -139,8 +139,8 @@ typedef struct {
  * bs_problem_init_tuned -- bs_problem_init with the partition of every grid
  * size picked by measurement instead of the built-in rule: for each distinct
  * Nx, every compiled partition (M rows per thread x NW warps x C CTAs, and for
- * clustered partitions with 16 or more rows per thread also two slices per
- * CTA) that holds the grid with at most half of its rows padding is set up for a subset
+ * partitions with 16 or more rows per thread also two slices per CTA) that
+ * holds the grid with at most half of its rows padding is set up for a subset
  * of the problem's own instances of that size (enough for >= 4096 slices, fine
  * steps capped at 128) and timed on one fine propagation (CUDA events, best of
  * two after a warm-up); the fastest is kept.  Few slices favour clusters and
@@ -176,8 +176,9 @@ int bs_problem_info(const bs_problem* prob, int32_t* n_instances, int64_t* total
 int bs_problem_partition(const bs_problem* prob, int32_t i, int32_t* M, int32_t* NW, int32_t* C);
 
 /* Slices per CTA of instance i's fine propagation: 1, or 2 when two slices of the
- * instance share each CTA and its coefficient tables (clustered partitions with
- * 16 or more rows per thread and enough slices to keep every cluster busy). */
+ * instance share each CTA and its coefficient tables (partitions with 16 or more
+ * rows per thread; the built-in rule takes them for clusters, and for one-CTA
+ * grids with 32 rows per thread, when the slices keep every CTA busy twice over). */
 int bs_problem_slices_per_cta(const bs_problem* prob, int32_t i, int32_t* s2);
 
 /*
@@ -344,7 +345,10 @@ int pinn_train_step_data(pinn_model* m, const double* X, const int8_t* kind, con
  * with G chosen by coarse_kind (model required for the network kinds; the
  * network is evaluated once per call in arithmetic prec on (S_j, tau_n) and
  * its Dirichlet nodes replaced by the exact values).  Iteration k runs F on
- * slices n >= k only.  Stops per instance when the increment norm
+ * slices n >= k of the instances still iterating only; once none is, the
+ * remaining iterations' launches return at once.  Scheduling counters in the
+ * problem's device memory are cleared at the start of every call, so calls on
+ * one problem must not overlap on the GPU.  Stops per instance when the increment norm
  *   e_k = max_n ||U^{k+1}_n - U^k_n||_2 / ||U^{k+1}_n||_2 <= tol,
  * or k = P (then Parareal equals serial fine), or k = max_iter.
  *   U_out: device, state layout, the final iterate.
