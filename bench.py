@@ -1450,7 +1450,7 @@ def main():
     ap.add_argument("--instances", type=int, default=4096, help="instances of --mode batched")
     ap.add_argument("--large-p", type=int, default=256, help="slices of --mode large")
     ap.add_argument("--large-steps", type=int, default=4096, help="CN steps per slice of --mode large")
-    ap.add_argument("--large-train-steps", type=int, default=300,
+    ap.add_argument("--large-train-steps", type=int, default=3000,
                     help="FP32 training steps of --mode large's 2->8x256 network (0: untrained, no network solve)")
     args = ap.parse_args()
     if args.warmup < 3:
