@@ -1158,8 +1158,17 @@ def run_large(args):
     BUILD.build()
     cfg = dict(K=1.0, sigma=0.3, r=0.03, T=2.0, Smax=8.0, Nx=65536, P=args.large_p, fine_steps=args.large_steps,
                coarse_steps=1)
-    prob = B.Problem(cfg)
+    # the partition by the tuner (throughput over all slices); serial fine walks
+    # one slice at a time, so it is also timed on the built-in rule's partition
+    # (16-CTA clusters: the most SMs per slice) and the faster reported
+    if args.large_partition:  # "M,NW,C[,S2]": that partition instead of the tuner's (profiling)
+        os.environ["BSP_PARTITION"] = args.large_partition
+        prob = B.Problem(cfg)
+        del os.environ["BSP_PARTITION"]
+    else:
+        prob = B.Problem(cfg, tuned=True)
     part = dict(prob.partition(0), slices_per_cta=prob.slices_per_cta(0))
+    tuning = [{k: r[k] for k in ("M", "NW", "C", "S2", "ms")} for r in prob.tuning]
     ev = lambda: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
     a, b = ev()
     a.record()
@@ -1167,6 +1176,20 @@ def run_large(args):
     b.record()
     torch.cuda.synchronize()
     serial_ms = a.elapsed_time(b)
+    serial_part = dict(prob.partition(0))
+    rule = B.Problem(cfg)
+    if rule.partition(0) != prob.partition(0):
+        Ur = torch.empty_like(Uf)
+        rule.serial_fine(Ur)
+        a, b = ev()
+        a.record()
+        rule.serial_fine(Ur)
+        b.record()
+        torch.cuda.synchronize()
+        if a.elapsed_time(b) < serial_ms:
+            serial_ms, serial_part = a.elapsed_time(b), dict(rule.partition(0))
+        del Ur
+    rule.close()
     U0 = Uf.view(cfg["P"] + 1, cfg["Nx"])[:-1].contiguous().view(-1)
     Fo = torch.empty_like(U0)
     prob.fine_propagate(U0, Fo)  # warm-up
@@ -1264,7 +1287,8 @@ def run_large(args):
                "serial_fine_s_extrapolated": t_cpu * cfg["P"] / n_done,
                "sample": f"the oracle's serial fine, first {n_done} of {cfg['P']} slices ({t_cpu:.1f} s); "
                          f"serial fine time extrapolated by slice count"}
-    print(json.dumps({"mode": "large", "config": cfg, "partition": part, "serial_fine_ms": serial_ms,
+    print(json.dumps({"mode": "large", "config": cfg, "partition": part, "tuning": tuning,
+                      "serial_fine_ms": serial_ms, "serial_fine_partition": serial_part,
                       "fine_ms": fine_ms, "grid_pt_steps_per_s": pt / (fine_ms * 1e-3), "fine_tflops_algorithmic": tf,
                       "fine_frac_of_fp64_peak": tf / peak, "ie_target": target, "ie_tol": ie_tol, "ie_solve_ms": ie_ms,
                       "ie_iterations": stats[0]["iterations"], "ie_err_vs_serial_fine": err,
@@ -1450,6 +1474,8 @@ def main():
     ap.add_argument("--instances", type=int, default=4096, help="instances of --mode batched")
     ap.add_argument("--large-p", type=int, default=256, help="slices of --mode large")
     ap.add_argument("--large-steps", type=int, default=4096, help="CN steps per slice of --mode large")
+    ap.add_argument("--large-partition", default="",
+                    help="--mode large: force this partition M,NW,C[,S2] instead of the tuner's (profiling)")
     ap.add_argument("--large-train-steps", type=int, default=3000,
                     help="FP32 training steps of --mode large's 2->8x256 network (0: untrained, no network solve)")
     args = ap.parse_args()

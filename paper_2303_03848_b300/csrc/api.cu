@@ -114,7 +114,7 @@ std::vector<Part> candidate_partitions(int Nx) {
   std::vector<Part> out;
   const int rows = Nx - 1;
   for (int C = 1; C <= 16; C *= 2)
-    for (int NW = 1; NW <= 4; NW *= 2)
+    for (int NW = 1; NW <= 8; NW *= 2)
       for (int M = 2; M <= 32; M *= 2) {
         const int64_t R = (int64_t)M * NW * 32 * C;
         if (R >= rows && 2 * (R - rows) <= R && bsp::partition_supported(M, NW, C)) {

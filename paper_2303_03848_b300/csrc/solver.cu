@@ -282,12 +282,24 @@ __global__ void __launch_bounds__(128) setup_cross_kernel(const Inst* insts, con
 // One time step of the partitioned solver.
 // ---------------------------------------------------------------------------
 
+// Grids on clusters of 8 or more CTAs with 4 or more rows per thread finish a
+// step by sweeping the inner rows again with the interface values in place
+// (2 FMA per row, the same count as adding the precomputed interface
+// responses), so they keep 3 coefficient tables (24 bytes per row) in shared
+// memory instead of 5: a 16-CTA grid of 32-row threads then fits two CTAs per
+// SM, and its clusters are no longer limited to one per 16 free SMs of a GPC.
+template <int M, int C>
+__host__ __device__ constexpr bool resweep_class() {
+  return C >= 8 && M >= 4;
+}
+
 // S2 slices share one CTA (and its tables): thread group g = threadIdx.x / T runs
 // its own slice of the same instance with its own exchange buffers.
 template <int M, int NW, int C, int S2 = 1>
 struct SolverSmem {
   static constexpr int T = NW * 32, Ws = C * NW;
-  double rows[5][M][T];     // lambda, mu, sigma, alpha, beta of the group's threads
+  static constexpr int kTabs = resweep_class<M, C>() ? 3 : 5;
+  double rows[kTabs][M][T];  // lambda, mu, sigma (and alpha, beta) of the group's threads
   double G2[NW][2][Ws];     // rows w-1 and w of the cross-warp inverse, per local warp
   double nu31[Ws], A31[Ws], C31[Ws];
   alignas(16) double pub[S2][2][Ws][4];  // [group][step parity][global warp][x0, X0, X30, R31]
@@ -372,7 +384,7 @@ __device__ __forceinline__ void load_solver(const double* __restrict__ cb, Solve
   constexpr int T = NW * 32, Ws = C * NW, GT = C * T;
   const int t = lthread<NW>(), c = cta_rank<C>();  // both groups write the same table entries
   const int g = c * T + t;
-  for (int q = 0; q < 5; ++q)
+  for (int q = 0; q < SolverSmem<M, NW, C, S2>::kTabs; ++q)
     for (int k = 0; k < M; ++k) sm.rows[q][k][t] = cb[coef_rows_off(q, k, g, M, GT)];
   rg.kap = cb[coef_if_off(0, g, M, GT)];
   rg.nu = cb[coef_if_off(1, g, M, GT)];
@@ -617,12 +629,27 @@ __device__ __forceinline__ void step_finish(double (&W)[M], double (&x)[M], Solv
     const double X = (L == 31) ? Yr : fma(rg.rc, Yr, fma(rg.ra, Yl, Xt));
     double Xprev = __shfl_up_sync(kFull, X, 1);
     if (L == 0) Xprev = Yl;
-    // 6. fixup of the inner rows and the scaled state update
+    if constexpr (resweep_class<M, C>()) {
+      // 6. the inner rows swept again with the interface values in place: the
+      //    forward sweep from X_{g-1} (coupled to the first inner row through
+      //    lambda_0), the back substitution from X_g (coupled to the last one
+      //    through mu_{M-2}); then the scaled state update
+      x[0] = fma(-sm.rows[0][0][t], Xprev, W[0]);
 #pragma unroll
-    for (int k = 0; k <= M - 2; ++k) {
-      const double xv = fma(sm.rows[4][k][t], X, fma(sm.rows[3][k][t], Xprev, x[k]));
-      x[k] = xv;
-      W[k] = CN ? fma(sm.rows[2][k][t], xv, -W[k]) : sm.rows[2][k][t] * xv;
+      for (int k = 1; k <= M - 2; ++k) x[k] = fma(-sm.rows[0][k][t], x[k - 1], W[k]);
+#pragma unroll
+      for (int k = M - 2; k >= 0; --k) {
+        x[k] = fma(-sm.rows[1][k][t], k == M - 2 ? X : x[k + 1], x[k]);
+        W[k] = CN ? fma(sm.rows[2][k][t], x[k], -W[k]) : sm.rows[2][k][t] * x[k];
+      }
+    } else {
+      // 6. fixup of the inner rows and the scaled state update
+#pragma unroll
+      for (int k = 0; k <= M - 2; ++k) {
+        const double xv = fma(sm.rows[4][k][t], X, fma(sm.rows[3][k][t], Xprev, x[k]));
+        x[k] = xv;
+        W[k] = CN ? fma(sm.rows[2][k][t], xv, -W[k]) : sm.rows[2][k][t] * xv;
+      }
     }
     x[M - 1] = X;
     W[M - 1] = CN ? fma(rg.sigp, X, -W[M - 1]) : rg.sigp * X;
@@ -1259,7 +1286,7 @@ __global__ void table_correction_kernel(const Inst* insts, int n_inst, const dou
   X(32, 2, 1) X(2, 4, 1) X(4, 4, 1) X(8, 4, 1) X(16, 4, 1) X(32, 4, 1) X(2, 4, 2) X(4, 4, 2)             \
   X(8, 4, 2) X(16, 4, 2) X(32, 4, 2) X(2, 4, 4) X(4, 4, 4) X(8, 4, 4) X(16, 4, 4) X(32, 4, 4)         \
   X(2, 4, 8) X(4, 4, 8) X(8, 4, 8) X(16, 4, 8) X(32, 4, 8) X(4, 4, 16) X(8, 4, 16) X(16, 4, 16)       \
-  X(32, 4, 16)
+  X(32, 4, 16) X(32, 8, 8)
 
 bool partition_supported(int M, int NW, int C) {
 #define X(MM, WW, CC) \

@@ -12,7 +12,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 RTOL = 1e-12
 # partitions (M rows per thread, NW warps per CTA, C CTAs per grid) tried per grid
-SHAPES = [(m, nw, c) for c in (1, 2, 4, 8, 16) for nw in (1, 2, 4) for m in (2, 4, 8, 16, 32)]
+SHAPES = [(m, nw, c) for c in (1, 2, 4, 8, 16) for nw in (1, 2, 4, 8) for m in (2, 4, 8, 16, 32)]
 
 
 @pytest.fixture(scope="module")
@@ -63,7 +63,7 @@ def _check_against_oracle(B, orc, prob, insts, parts):
             _close(G[sl], orc.coarse_ie(op, n, parts[i][n]), _tol(p, "coarse"))
 
 
-@pytest.mark.parametrize("Nx", [256, 1000, 2049])
+@pytest.mark.parametrize("Nx", [256, 1000, 2049, 40000])
 def test_every_partition_matches_oracle(B, orc, monkeypatch, Nx):
     p = dict(K=1.0, sigma=0.25, r=0.04, T=1.0, Smax=4.0, Nx=Nx, P=2, fine_steps=6, coarse_steps=2)
     parts = [_slices(orc, p, 70 + Nx)]
@@ -81,7 +81,7 @@ def test_every_partition_matches_oracle(B, orc, monkeypatch, Nx):
         assert prob.partition(0) == dict(M=m, NW=nw, C=c)
         _check_against_oracle(B, orc, prob, [p], parts)
         tried += 1
-    assert tried >= 3
+    assert tried >= (2 if Nx > 32768 else 3)  # 40000 points: 32 rows x 4 warps x 16 CTAs, 32 x 8 x 8
 
 
 def test_forced_partition_too_small_is_rejected(B, monkeypatch):
