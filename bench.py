@@ -1472,6 +1472,8 @@ def main():
                          "batched workload (profiling)")
     ap.add_argument("--batched", type=int, default=1, help="include the batched-workload leg (1/0)")
     ap.add_argument("--instances", type=int, default=4096, help="instances of --mode batched")
+    ap.add_argument("--batched-pinn", type=int, default=1,
+                    help="--mode batched: also train the parametric network and solve with it (1/0)")
     ap.add_argument("--large-p", type=int, default=256, help="slices of --mode large")
     ap.add_argument("--large-steps", type=int, default=4096, help="CN steps per slice of --mode large")
     ap.add_argument("--large-partition", default="",
@@ -1551,8 +1553,8 @@ def main():
         from paper_2303_03848_b300 import build as BUILD
 
         BUILD.build()
-        print(json.dumps(batched_leg(B, torch, n_inst=args.instances, solve=True, rule_too=True, pinn_solve=True)),
-              flush=True)
+        print(json.dumps(batched_leg(B, torch, n_inst=args.instances, solve=True, rule_too=True,
+                                     pinn_solve=bool(args.batched_pinn))), flush=True)
     elif args.impl == "reference":
         run_reference(args)
     else:

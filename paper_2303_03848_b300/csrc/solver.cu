@@ -282,12 +282,13 @@ __global__ void __launch_bounds__(128) setup_cross_kernel(const Inst* insts, con
 // One time step of the partitioned solver.
 // ---------------------------------------------------------------------------
 
-// Grids on clusters of 8 or more CTAs with 4 or more rows per thread finish a
-// step by sweeping the inner rows again with the interface values in place
-// (2 FMA per row, the same count as adding the precomputed interface
-// responses), so they keep 3 coefficient tables (24 bytes per row) in shared
-// memory instead of 5: a 16-CTA grid of 32-row threads then fits two CTAs per
-// SM, and its clusters are no longer limited to one per 16 free SMs of a GPC.
+// A step can finish by sweeping the inner rows again with the interface
+// values in place (2 FMA per row, the same count as adding the precomputed
+// interface responses), which needs only 3 coefficient tables (24 bytes per
+// row) in shared memory instead of 5.  The fine propagation does so on
+// clusters of 8 or more CTAs with 4 or more rows per thread, where the smaller
+// tables let 8-CTA clusters of 8-warp CTAs hold grids that took 16-CTA
+// clusters; the coarse sweep always does (twice the instances per SM).
 template <int M, int C>
 __host__ __device__ constexpr bool resweep_class() {
   return C >= 8 && M >= 4;
@@ -295,10 +296,10 @@ __host__ __device__ constexpr bool resweep_class() {
 
 // S2 slices share one CTA (and its tables): thread group g = threadIdx.x / T runs
 // its own slice of the same instance with its own exchange buffers.
-template <int M, int NW, int C, int S2 = 1>
+template <int M, int NW, int C, int S2 = 1, bool RS = resweep_class<M, C>()>
 struct SolverSmem {
   static constexpr int T = NW * 32, Ws = C * NW;
-  static constexpr int kTabs = resweep_class<M, C>() ? 3 : 5;
+  static constexpr int kTabs = RS ? 3 : 5;
   double rows[kTabs][M][T];  // lambda, mu, sigma (and alpha, beta) of the group's threads
   double G2[NW][2][Ws];     // rows w-1 and w of the cross-warp inverse, per local warp
   double nu31[Ws], A31[Ws], C31[Ws];
@@ -378,13 +379,13 @@ __device__ __forceinline__ int cta_rank() {
   }
 }
 
-template <int M, int NW, int C, int S2 = 1>
-__device__ __forceinline__ void load_solver(const double* __restrict__ cb, SolverSmem<M, NW, C, S2>& sm,
+template <int M, int NW, int C, int S2 = 1, bool RS = resweep_class<M, C>()>
+__device__ __forceinline__ void load_solver(const double* __restrict__ cb, SolverSmem<M, NW, C, S2, RS>& sm,
                                             SolverRegs& rg) {
   constexpr int T = NW * 32, Ws = C * NW, GT = C * T;
   const int t = lthread<NW>(), c = cta_rank<C>();  // both groups write the same table entries
   const int g = c * T + t;
-  for (int q = 0; q < SolverSmem<M, NW, C, S2>::kTabs; ++q)
+  for (int q = 0; q < SolverSmem<M, NW, C, S2, RS>::kTabs; ++q)
     for (int k = 0; k < M; ++k) sm.rows[q][k][t] = cb[coef_rows_off(q, k, g, M, GT)];
   rg.kap = cb[coef_if_off(0, g, M, GT)];
   rg.nu = cb[coef_if_off(1, g, M, GT)];
@@ -435,8 +436,8 @@ __device__ __forceinline__ void load_solver(const double* __restrict__ cb, Solve
 
 // The exchange barriers, once per launch (a cluster barrier follows before the
 // first step; the step counter then runs on across slices and tasks).
-template <int M, int NW, int C, int S2 = 1>
-__device__ __forceinline__ void exchange_init(SolverSmem<M, NW, C, S2>& sm, SolverRegs& rg) {
+template <int M, int NW, int C, int S2 = 1, bool RS = resweep_class<M, C>()>
+__device__ __forceinline__ void exchange_init(SolverSmem<M, NW, C, S2, RS>& sm, SolverRegs& rg) {
   rg.fail = 0;
   if (C > 1 && threadIdx.x == 0) {
     for (int g = 0; g < S2; ++g) {
@@ -449,8 +450,8 @@ __device__ __forceinline__ void exchange_init(SolverSmem<M, NW, C, S2>& sm, Solv
 
 // A CTA whose wait gave up records BS_TIMEOUT and waits (again bounded) for the
 // values of the last two steps that may still be arriving in its buffers.
-template <int M, int NW, int C, int S2 = 1>
-__device__ __forceinline__ void exchange_drain(SolverSmem<M, NW, C, S2>& sm, const SolverRegs& rg, int seq,
+template <int M, int NW, int C, int S2 = 1, bool RS = resweep_class<M, C>()>
+__device__ __forceinline__ void exchange_drain(SolverSmem<M, NW, C, S2, RS>& sm, const SolverRegs& rg, int seq,
                                                int* status) {
   if constexpr (C > 1) {
     if (!rg.fail) return;
@@ -468,8 +469,8 @@ __device__ __forceinline__ void exchange_drain(SolverSmem<M, NW, C, S2>& sm, con
 // x receives the solution of the step (Z for Crank-Nicolson, V^{m+1} for
 // implicit Euler) on the thread's rows; W is advanced to the next scaled state.
 // Zb is the Dirichlet value of the step (used by the grid's last thread).
-template <int M, int NW, int C, int S2 = 1>
-__device__ __forceinline__ double step_reduce(const double (&W)[M], double (&x)[M], SolverSmem<M, NW, C, S2>& sm,
+template <int M, int NW, int C, int S2 = 1, bool RS = resweep_class<M, C>()>
+__device__ __forceinline__ double step_reduce(const double (&W)[M], double (&x)[M], SolverSmem<M, NW, C, S2, RS>& sm,
                                               const SolverRegs& rg, double Zb, int seq) {
   const int par = seq & 1;
   constexpr int Ws = C * NW;
@@ -527,8 +528,8 @@ __device__ __forceinline__ double step_reduce(const double (&W)[M], double (&x)[
   return Xt;
 }
 
-template <int M, int NW, int C, bool CN, int S2 = 1>
-__device__ __forceinline__ void step_finish(double (&W)[M], double (&x)[M], SolverSmem<M, NW, C, S2>& sm,
+template <int M, int NW, int C, bool CN, int S2 = 1, bool RS = resweep_class<M, C>()>
+__device__ __forceinline__ void step_finish(double (&W)[M], double (&x)[M], SolverSmem<M, NW, C, S2, RS>& sm,
                                             SolverRegs& rg, double Xt, int seq) {
   const int par = seq & 1;
   constexpr int Ws = C * NW;
@@ -629,7 +630,7 @@ __device__ __forceinline__ void step_finish(double (&W)[M], double (&x)[M], Solv
     const double X = (L == 31) ? Yr : fma(rg.rc, Yr, fma(rg.ra, Yl, Xt));
     double Xprev = __shfl_up_sync(kFull, X, 1);
     if (L == 0) Xprev = Yl;
-    if constexpr (resweep_class<M, C>()) {
+    if constexpr (RS) {
       // 6. the inner rows swept again with the interface values in place: the
       //    forward sweep from X_{g-1} (coupled to the first inner row through
       //    lambda_0), the back substitution from X_g (coupled to the last one
@@ -657,9 +658,9 @@ __device__ __forceinline__ void step_finish(double (&W)[M], double (&x)[M], Solv
 }
 
 // Read the Nx-vector V into the thread's rows and scale it into W.
-template <int M, int NW, int C, int S2 = 1>
+template <int M, int NW, int C, int S2 = 1, bool RS = resweep_class<M, C>()>
 __device__ __forceinline__ void load_state(const Inst& in, const double* __restrict__ V,
-                                           const SolverSmem<M, NW, C, S2>& sm, const SolverRegs& rg, double (&W)[M]) {
+                                           const SolverSmem<M, NW, C, S2, RS>& sm, const SolverRegs& rg, double (&W)[M]) {
   const int t = lthread<NW>(), g = cta_rank<C>() * NW * 32 + t;
 #pragma unroll
   for (int k = 0; k < M; ++k) {
@@ -685,9 +686,9 @@ __device__ __forceinline__ double row_value(const double* __restrict__ cb, int k
 // The right Dirichlet value of the next step is formed while the barrier
 // completes, from exp(-r m dtau) read one step ahead; KeN = K exp(-r tau_n) of
 // the slice's start (slice_KeN, or from the set-up table of exp(-r tau_n)).
-template <int M, int NW, int C, bool CN, int S2 = 1>
+template <int M, int NW, int C, bool CN, int S2 = 1, bool RS = resweep_class<M, C>()>
 __device__ __forceinline__ void run_slice(const Inst& in, double KeN, const double* __restrict__ et, int steps,
-                                          double (&W)[M], double (&x)[M], SolverSmem<M, NW, C, S2>& sm,
+                                          double (&W)[M], double (&x)[M], SolverSmem<M, NW, C, S2, RS>& sm,
                                           SolverRegs& rg, int& seq) {
   const bool last_warp = cta_rank<C>() == C - 1 && (lthread<NW>() >> 5) == NW - 1;
   double Bold = in.Smax - KeN;  // exp(0) = 1
@@ -951,7 +952,7 @@ template <int M, int NW, int C>
 __global__ void __launch_bounds__(NW * 32, 1) sweep_kernel(SweepArgs a) {
   constexpr int T = NW * 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  SolverSmem<M, NW, C>& sm = *reinterpret_cast<SolverSmem<M, NW, C>*>(smem_raw);
+  SolverSmem<M, NW, C, 1, true>& sm = *reinterpret_cast<SolverSmem<M, NW, C, 1, true>*>(smem_raw);
   if (a.n_live != nullptr && *a.n_live == 0) return;  // every instance has converged
   const int idx = a.ids[blockIdx.y];
   const Inst in = a.insts[idx];
@@ -1424,7 +1425,7 @@ cudaError_t launch_sweep(int M, int NW, int C, const SweepArgs& a, int n_inst, c
   dim3 grid(C, n_inst);
 #define X(MM, WW, CC)                                                                        \
   if (M == MM && NW == WW && C == CC) {                                                      \
-    const int sz = (int)sizeof(SolverSmem<MM, WW, CC>);                                      \
+    const int sz = (int)sizeof(SolverSmem<MM, WW, CC, 1, true>);                             \
     return launch_cluster(sweep_kernel<MM, WW, CC>, grid, WW * 32, CC, sz, s, a);            \
   }
   BSP_FOR_EACH_CLASS(X)
