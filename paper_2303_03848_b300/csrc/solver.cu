@@ -20,7 +20,9 @@
 //     unknowns form a small system across the CTA -- or across a cluster of
 //     CTAs that shares one grid over several SMs -- solved with a precomputed
 //     inverse after one barrier per step.  A final fixup adds the interface
-//     responses to the inner rows.
+//     responses to the inner rows, or (coarse sweep, large clusters) a second
+//     sweep over the inner rows with the interface values in place does the
+//     same with fewer tables in shared memory.
 // The whole grid stays in registers and shared memory for all steps of a slice.
 #include <cooperative_groups.h>
 
