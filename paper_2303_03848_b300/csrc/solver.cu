@@ -414,12 +414,15 @@ __device__ __forceinline__ void load_solver(const double* __restrict__ cb, Solve
     }
     const double s0 = cb[coef_rows_off(2, 0, g, M, GT)];
     const double al = cb[coef_rows_off(3, 0, g, M, GT)], be = cb[coef_rows_off(4, 0, g, M, GT)];
+    // the step hands on PCR's result before its scaling by inv (see step_reduce):
+    // the users of a lane's Xt take that lane's inv in their coefficients
+    const double inv_prev = __shfl_up_sync(kFull, rg.inv, 1);
     rg.s0 = s0;
-    rg.sa = L == 0 ? 0.0 : s0 * al;
-    rg.sb = L == 31 ? 0.0 : s0 * be;
+    rg.sa = L == 0 ? 0.0 : s0 * al * inv_prev;
+    rg.sb = L == 31 ? 0.0 : s0 * be * rg.inv;
     rg.e0 = s0 * (al * rap + be * ra);
     rg.f0 = s0 * (al * rcp + be * rc);
-    rg.sp = L == 31 ? 0.0 : rg.sigp;
+    rg.sp = L == 31 ? 0.0 : rg.sigp * rg.inv;
     rg.g1 = rg.sigp * ra;
     rg.h1 = rg.sigp * rc;
   }
@@ -427,6 +430,10 @@ __device__ __forceinline__ void load_solver(const double* __restrict__ cb, Solve
     sm.nu31[i] = cb[coef_warp_off(0, i, M, GT, Ws)];
     sm.A31[i] = cb[coef_warp_off(1, i, M, GT, Ws)];
     sm.C31[i] = cb[coef_warp_off(2, i, M, GT, Ws)];
+    if constexpr (M == 2) {  // published X30 and X0 unscaled (lane 30 of warp i, lane 0 of warp i + 1)
+      sm.A31[i] *= cb[coef_pcr_off(10, 32 * i + 30, M, GT)];
+      if (i + 1 < Ws) sm.C31[i] *= cb[coef_pcr_off(10, 32 * (i + 1), M, GT)];
+    }
   }
   for (int i = t; i < NW * 2 * Ws; i += T) {
     const int wl = i / (2 * Ws), side = (i / Ws) % 2, u = i % Ws;
@@ -503,7 +510,9 @@ __device__ __forceinline__ double step_reduce(const double (&W)[M], double (&x)[
   // stride 16: lane L couples to lane L ^ 16 only (the set-up zeroes the other
   // multiplier), so one exchange and one FMA do what the two-sided level does
   Rp = fma(-rg.mlast, __shfl_xor_sync(kFull, Rp, 16), Rp);
-  const double Xt = Rp * rg.inv;
+  // M = 2 folds the scaling by inv into the coefficients that use Xt (its own
+  // state update and the cross-warp solve), one FP64 instruction fewer per step
+  const double Xt = (M == 2) ? Rp : Rp * rg.inv;
   // 4. publish this warp's boundary values to every CTA of the grid
   const double p0 = __shfl_sync(kFull, x[0], 0);
   const double p1 = __shfl_sync(kFull, Xt, 0);
