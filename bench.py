@@ -65,7 +65,7 @@ FLOPS_PER_PT_STEP = 11.0  # CN right-hand side 5 + factored solve 6 (algorithmic
 # DRAM bytes (read + write) of one fine_propagate launch over the 32 slices of the
 # single-instance workload, from one ncu capture per partition (profiles/); a
 # partition without a capture of its current code reports null
-FINE_TRAFFIC_BYTES = {}
+FINE_TRAFFIC_BYTES = {(2, 4, 4): 423936}
 # DRAM bytes (read + write) of one fine propagation of every slice of the batched
 # workload per grid point and slice (all partition classes; captured on the
 # batch's first 512 instances, profiles/), or None while no capture of the
