@@ -774,7 +774,10 @@ __global__ void __launch_bounds__(S2 * NW * 32, 1) prop_kernel(PropArgs a) {
   __shared__ int s_task;
   // every instance has converged: nothing to do (the same value for every CTA)
   if (a.n_live != nullptr && *a.n_live == 0) return;
-  SolverSmem<M, NW, C, S2>& sm = *reinterpret_cast<SolverSmem<M, NW, C, S2>*>(smem_raw);
+  // implicit Euler (coarse_propagate, the network-anchored corrections) takes
+  // the coarse sweep's re-sweep finish, so the two give the same values bit for bit
+  constexpr bool RS = CN ? resweep_class<M, C>() : true;
+  SolverSmem<M, NW, C, S2, RS>& sm = *reinterpret_cast<SolverSmem<M, NW, C, S2, RS>*>(smem_raw);
   const int t = lthread<NW>(), gi = lgroup<NW>(), c = cta_rank<C>();
   SolverRegs rg;
   exchange_init<M, NW, C, S2>(sm, rg);
@@ -1409,9 +1412,9 @@ cudaError_t launch_prop(int M, int NW, int C, int s2, bool cn, const PropArgs& a
   }
 #define X(MM, WW, CC)                                                                                            \
   if (M == MM && NW == WW && C == CC) {                                                                          \
-    const int sz = (int)sizeof(SolverSmem<MM, WW, CC>);                                                          \
+    const int sz = (int)sizeof(SolverSmem<MM, WW, CC>), sz_ie = (int)sizeof(SolverSmem<MM, WW, CC, 1, true>);    \
     return cn ? launch_persistent(prop_kernel<MM, WW, CC, true, 1>, WW * 32, CC, sz, s, a, n_inst, maxP, 1)      \
-              : launch_persistent(prop_kernel<MM, WW, CC, false, 1>, WW * 32, CC, sz, s, a, n_inst, maxP, 1);     \
+              : launch_persistent(prop_kernel<MM, WW, CC, false, 1>, WW * 32, CC, sz_ie, s, a, n_inst, maxP, 1);  \
   }
   BSP_FOR_EACH_CLASS(X)
 #undef X

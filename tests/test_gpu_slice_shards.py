@@ -126,3 +126,19 @@ def test_slice_sharded_ie_parareal_equals_one_launch(B, blocks):
         assert stats[0]["iterations"] == iters
         assert torch.equal(got.view(-1), ref), float((got.view(-1) - ref).abs().max())
         np.testing.assert_allclose(norms, rn[0, :iters], rtol=1e-12)
+
+
+@pytest.mark.parametrize("part", ["16,4,1", "8,4,2"])
+def test_slice_sharded_ie_parareal_equals_one_launch_inner_rows(B, monkeypatch, part):
+    # partitions with inner rows per thread: the sweep's implicit Euler step and
+    # coarse_propagate finish the step the same way (a second sweep over the
+    # inner rows), so the sharded solve still equals one launch bit for bit
+    monkeypatch.setenv("BSP_PARTITION", part)
+    cfg = dict(K=1.0, sigma=0.3, r=0.03, T=0.5, Smax=4.0, Nx=2000, P=6, fine_steps=16, coarse_steps=2)
+    prob = B.Problem(cfg)
+    m, nw, c = (int(v) for v in part.split(","))
+    assert prob.partition(0) == dict(M=m, NW=nw, C=c)
+    got, norms = _sharded_ie_parareal(B, prob, cfg, 2, [(0, 3), (3, 6)])
+    ref, rn, stats, rc = prob.parareal_solve(B.COARSE_IE, tol=0.0, max_iter=2)
+    assert torch.equal(got.view(-1), ref), float((got.view(-1) - ref).abs().max())
+    np.testing.assert_allclose(norms, rn[0, :2], rtol=1e-12)
