@@ -127,6 +127,28 @@ def test_tuned_parareal_matches_oracle(B, orc):
     _close(U.cpu().numpy(), Ur.ravel(), max(RTOL, 2.0 * kappa * 2.0 ** -53 * steps))
 
 
+@pytest.mark.parametrize("part", ["32,8,8", "32,4,16", "16,4,8"])
+def test_three_table_partitions_parareal_match_oracle(B, orc, monkeypatch, part):
+    # clusters of 8 or more CTAs keep three coefficient tables and finish each
+    # step with a second sweep over the inner rows: implicit-Euler Parareal on
+    # such a grid against the oracle's, iterates and increment norms
+    monkeypatch.setenv("BSP_PARTITION", part)
+    Nx = {"32,8,8": 40000, "32,4,16": 40000, "16,4,8": 12000}[part]
+    p = dict(K=1.0, sigma=0.3, r=0.03, T=0.5, Smax=8.0, Nx=Nx, P=4, fine_steps=8, coarse_steps=1)
+    prob = B.Problem(p)
+    m, nw, c = (int(v) for v in part.split(","))
+    assert prob.partition(0) == dict(M=m, NW=nw, C=c)
+    U, norms, stats, rc = prob.parareal_solve(B.COARSE_IE, tol=1e-9)
+    assert prob.device_status() == B.BS_OK
+    Ur, nr, st = orc.parareal(orc.params(**p), orc.COARSE_IE, tol=1e-9)
+    assert rc == B.BS_OK and stats[0]["iterations"] == len(nr)
+    np.testing.assert_allclose(norms[0, :len(nr)], nr, rtol=1e-6)
+    steps = p["fine_steps"] * p["P"]
+    j = p["Nx"] - 2
+    kappa = 1.0 + 0.5 * p["T"] / steps * (2.0 * p["sigma"] ** 2 * j * j + p["r"] * j + p["r"])
+    _close(U.cpu().numpy(), Ur.ravel(), max(RTOL, 2.0 * kappa * 2.0 ** -53 * steps))
+
+
 # two slices per CTA (slice pairs sharing the coefficient tables; one-CTA grids
 # step on a named barrier per slice, clusters on mbarriers): same per-slice
 # arithmetic as one slice per CTA, so the results agree bit for bit; odd slice
