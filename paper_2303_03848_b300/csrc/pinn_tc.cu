@@ -107,8 +107,10 @@ constexpr int first_row_f4() { return (DIN + 1 + 3) / 4; }
 // 2 (256 threads, up to three CTAs per SM) or, for w = 256, 4 (512 threads and
 // two CTAs per SM, the most the tensor memory holds at that width).  TF: TF32
 // operands (4 bytes, K = 8 per MMA) instead of BF16 (2 bytes, K = 16).
-template <int DIN, int NWQ, bool TF>
-__global__ void __launch_bounds__(128 * NWQ, NWQ == 4 ? 2 : 0) mlp_tc_kernel(TcArgs a) {
+// TP tiles per CTA: the tiles share each layer's weight copy and its barriers,
+// each with its own operand buffer and accumulator (see tc_tiles_per_cta).
+template <int DIN, int NWQ, bool TF, int TP>
+__global__ void __launch_bounds__(128 * NWQ * TP, NWQ * TP == 4 ? 2 : 0) mlp_tc_kernel(TcArgs a) {
   static_assert(DIN == 2 || DIN == 5, "2 or 5 inputs");
   constexpr int RW = first_row_f4<DIN>();
   constexpr int EB = TF ? 4 : 2;       // operand bytes
@@ -116,20 +118,22 @@ __global__ void __launch_bounds__(128 * NWQ, NWQ == 4 ? 2 : 0) mlp_tc_kernel(TcA
   extern __shared__ __align__(1024) unsigned char smem[];
   const MlpDev& m = a.m;
   const int w = a.w, t = threadIdx.x, warp = t >> 5;
-  const int pt = (warp & 3) * 32 + (t & 31);  // this thread's point (accumulator lane)
-  const int hw = w / NWQ, cb = (warp >> 2) * hw;  // and its columns [cb, cb + hw)
+  const int ts = warp / (4 * NWQ), wt = warp % (4 * NWQ);  // tile slot, warp within the tile's warps
+  const int pt = (wt & 3) * 32 + (t & 31);  // this thread's point (accumulator lane)
+  const int hw = w / NWQ, cb = (wt >> 2) * hw;  // and its columns [cb, cb + hw)
   const int n_sq = m.n_lin - 2;
   const uint32_t wbytes = (uint32_t)w * w * EB;
   // shared memory carve-up
   unsigned char* sW = smem;                                             // n_sq (resident) or 1 square layer
-  unsigned char* sA = sW + (a.resident ? (size_t)n_sq : 1) * wbytes;    // 128 x w operand
-  float* sW1 = reinterpret_cast<float*>(sA + (size_t)128 * w * EB);     // w rows of RW float4 (W_1, b_1)
+  unsigned char* sA0 = sW + (a.resident ? (size_t)n_sq : 1) * wbytes;   // TP x (128 x w operand)
+  unsigned char* sA = sA0 + (size_t)ts * 128 * w * EB;                   // this thread's tile
+  float* sW1 = reinterpret_cast<float*>(sA0 + (size_t)TP * 128 * w * EB);  // w rows of RW float4 (W_1, b_1)
   float* sB = sW1 + w * 4 * RW;                                         // biases of hidden layers, (n_lin-1) x w
   float* sWo = sB + (m.n_lin - 1) * w;                                  // output weights, w
   uint64_t* bar = reinterpret_cast<uint64_t*>(sWo + w + 2);             // [0] MMA done, [1] weights landed
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
   __shared__ int s_fail;
-  __shared__ float s_dot[2][NWQ - 1][128];  // output partial sums of the other column groups, by tile parity
+  __shared__ float s_dot[2][TP][NWQ - 1][128];  // output partial sums of the other column groups, by tile parity
 
   // parameters into shared memory; the input map to [-1, 1] in FP32 registers
   for (int i = t; i < w * 4 * RW; i += blockDim.x) {
@@ -148,7 +152,7 @@ __global__ void __launch_bounds__(128 * NWQ, NWQ == 4 ? 2 : 0) mlp_tc_kernel(TcA
     sc[i] = (float)s;
     of[i] = (float)(-s * m.lo[i] - 1.0);
   }
-  const int64_t ntiles = (a.N + 127) / 128;
+  const int64_t ntiles = (a.N + 127) / 128, ngroups = (ntiles + TP - 1) / TP;
   if (t == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
@@ -159,16 +163,17 @@ __global__ void __launch_bounds__(128 * NWQ, NWQ == 4 ? 2 : 0) mlp_tc_kernel(TcA
   // first weight copy: every layer (resident) or layer 0
   bool w_pending = false;  // thread 0: a weight copy is in flight
   uint32_t ph_w = 0, ph_mma = 0;
-  if (t == 0 && n_sq > 0 && (int64_t)blockIdx.x < ntiles) {
+  if (t == 0 && n_sq > 0 && (int64_t)blockIdx.x < ngroups) {
     bulk_load(sW, a.packed, a.resident ? (uint32_t)n_sq * wbytes : wbytes, &bar[1]);
     w_pending = true;
   }
-  // tensor memory: w FP32 columns x 128 lanes
+  // tensor memory: w FP32 columns x 128 lanes per tile
   uint32_t ncols = 32;
   while ((int)ncols < w) ncols <<= 1;
+  const uint32_t nalloc = ncols * TP;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
-                 "r"(ncols)
+                 "r"(nalloc)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -179,22 +184,24 @@ __global__ void __launch_bounds__(128 * NWQ, NWQ == 4 ? 2 : 0) mlp_tc_kernel(TcA
   const uint32_t idesc = TF ? make_idesc_tf32(w) : make_idesc_bf16(w);
   const uint32_t sbo = (uint32_t)(w * EB / 16) * 128;  // next 8-row group
 
-  const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16);  // this warp's accumulator lanes
+  // this warp's accumulator lanes in its tile's columns
+  const uint32_t tl = tmem + (uint32_t)ts * ncols + ((uint32_t)((wt & 3) * 32) << 16);
   double xn[DIN];  // inputs of this thread's point in the next tile (prefetched)
   {
-    const int64_t p = (int64_t)blockIdx.x * 128 + pt;
+    const int64_t p = ((int64_t)blockIdx.x * TP + ts) * 128 + pt;
 #pragma unroll
     for (int i = 0; i < DIN; ++i) xn[i] = p < a.N ? a.X[p * DIN + i] : 0.0;
   }
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  for (int64_t grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+    const int64_t tile = grp * TP + ts;
     const int64_t p = tile * 128 + pt;
     const bool valid = p < a.N;
-    const bool last_tile = tile + gridDim.x >= ntiles;
+    const bool last_tile = grp + gridDim.x >= ngroups;
     float xh[DIN];
 #pragma unroll
     for (int i = 0; i < DIN; ++i) xh[i] = fmaf((float)xn[i], sc[i], of[i]);
     if (!last_tile) {
-      const int64_t q = p + (int64_t)gridDim.x * 128;
+      const int64_t q = p + (int64_t)gridDim.x * TP * 128;
 #pragma unroll
       for (int i = 0; i < DIN; ++i) xn[i] = q < a.N ? a.X[q * DIN + i] : 0.0;
     }
@@ -241,14 +248,18 @@ __global__ void __launch_bounds__(128 * NWQ, NWQ == 4 ? 2 : 0) mlp_tc_kernel(TcA
       fence_after();
       if (s_fail) break;
       if (t == 0) {
-        const uint32_t aa = smem_u32(sA), bb = smem_u32(wl);
-        for (int kk = 0; kk < w / KPM; ++kk) {  // each MMA: 2 core matrices (32 bytes) along K
-          const uint64_t da = make_desc(aa + kk * 256, 128, sbo);
-          const uint64_t db = make_desc(bb + kk * 256, 128, sbo);
-          if constexpr (TF) {
-            mma_tf32(tmem, da, db, idesc, kk > 0 ? 1u : 0u);
-          } else {
-            mma_bf16(tmem, da, db, idesc, kk > 0 ? 1u : 0u);
+        const uint32_t bb = smem_u32(wl);
+#pragma unroll
+        for (int q = 0; q < TP; ++q) {  // every tile of the group against the same weights
+          const uint32_t aa = smem_u32(sA0) + (uint32_t)q * 128 * w * EB, dq = tmem + (uint32_t)q * ncols;
+          for (int kk = 0; kk < w / KPM; ++kk) {  // each MMA: 2 core matrices (32 bytes) along K
+            const uint64_t da = make_desc(aa + kk * 256, 128, sbo);
+            const uint64_t db = make_desc(bb + kk * 256, 128, sbo);
+            if constexpr (TF) {
+              mma_tf32(dq, da, db, idesc, kk > 0 ? 1u : 0u);
+            } else {
+              mma_bf16(dq, da, db, idesc, kk > 0 ? 1u : 0u);
+            }
           }
         }
         mma_commit(&bar[0]);
@@ -310,13 +321,13 @@ __global__ void __launch_bounds__(128 * NWQ, NWQ == 4 ? 2 : 0) mlp_tc_kernel(TcA
     if (s_fail) break;
     // the two column halves of the output dot product (two buffers: without a
     // square layer this is the only barrier of a tile)
-    const int par = (int)((tile / gridDim.x) & 1);
-    if (warp >= 4) s_dot[par][(warp >> 2) - 1][pt] = dot;
+    const int par = (int)((grp / gridDim.x) & 1);
+    if (wt >= 4) s_dot[par][ts][(wt >> 2) - 1][pt] = dot;
     __syncthreads();
-    if (warp < 4 && valid) {
+    if (wt < 4 && valid) {
       float u = dot;
 #pragma unroll
-      for (int q = 0; q < NWQ - 1; ++q) u += s_dot[par][q][pt];
+      for (int q = 0; q < NWQ - 1; ++q) u += s_dot[par][ts][q][pt];
       a.u[p] = (double)(u + bout);
     }
   }
@@ -327,7 +338,7 @@ __global__ void __launch_bounds__(128 * NWQ, NWQ == 4 ? 2 : 0) mlp_tc_kernel(TcA
   fence_after();
   if (s_fail && t == 0) atomicExch(a.status, 6);  // BS_TIMEOUT
   if (warp == 0) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(nalloc) : "memory");
   }
 }
 
@@ -362,15 +373,23 @@ bool tc_supported(const MlpDev& m) {
   return m.widths[m.n_lin] == 1;
 }
 
+// Tiles per CTA of the tensor-core kernel: two for TF32 up to w = 128, where
+// the 4-byte operands leave room for one CTA per SM and the second tile doubles
+// the work in flight (1.44e9 -> 1.74e9 points/s on 5->6x128); one for BF16,
+// whose three independent one-tile CTAs per SM overlap one another's GEMMs and
+// epilogues better than two CTAs of two tiles in step (115.6 against 123.5 ms
+// for the batched workload's table); one at w = 256.
+static int tc_tiles_per_cta(int w, int eb) { return (eb == 4 && w <= 128) ? 2 : 1; }
+
 // Shared memory of the tensor-core kernel: square-layer weights (all layers
 // when that still leaves room for several CTAs per SM, else one), the 128 x w
-// activation operand, the FP32 input/output layers and biases, two mbarriers.
-// eb: operand bytes (2 BF16, 4 TF32).
+// activation operand of each tile, the FP32 input/output layers and biases,
+// two mbarriers.  eb: operand bytes (2 BF16, 4 TF32).
 static size_t tc_smem_bytes(const MlpDev& m, int* resident, int eb) {
   const int w = m.widths[1], n_sq = m.n_lin - 2;
   const size_t wbytes = (size_t)w * w * eb;
   const size_t rw = m.d_in == 2 ? first_row_f4<2>() : first_row_f4<5>();
-  const size_t fixed = (size_t)128 * w * eb +
+  const size_t fixed = (size_t)tc_tiles_per_cta(w, eb) * 128 * w * eb +
                        sizeof(float) * ((size_t)w * 4 * rw + (size_t)(m.n_lin - 1) * w + w + 2) + 32 + 1024;
   const int res = (n_sq > 0 && (size_t)n_sq * wbytes + fixed <= 96 * 1024) ? 1 : 0;
   if (resident) *resident = res;
@@ -406,12 +425,13 @@ cudaError_t launch_mlp_eval_tc(const MlpDev& m, unsigned char* packed, const dou
   const size_t smem = tc_smem_bytes(m, &resident, tf32 ? 4 : 2);
   if (smem > 220 * 1024) return cudaErrorInvalidValue;
   TcArgs a{m, packed, X, N, u, w, resident, status};
-  const bool wide = w == 256;  // four warps per lane quadrant
-  const int threads = wide ? 512 : 256;
-  auto kern = tf32 ? (m.d_in == 2 ? (wide ? mlp_tc_kernel<2, 4, true> : mlp_tc_kernel<2, 2, true>)
-                                  : (wide ? mlp_tc_kernel<5, 4, true> : mlp_tc_kernel<5, 2, true>))
-                   : (m.d_in == 2 ? (wide ? mlp_tc_kernel<2, 4, false> : mlp_tc_kernel<2, 2, false>)
-                                  : (wide ? mlp_tc_kernel<5, 4, false> : mlp_tc_kernel<5, 2, false>));
+  const bool wide = w == 256;  // four warps per lane quadrant, one tile per CTA
+  const int tp = tc_tiles_per_cta(w, tf32 ? 4 : 2);
+  const int threads = wide ? 512 : 256 * tp;
+  auto kern = tf32 ? (m.d_in == 2 ? (wide ? mlp_tc_kernel<2, 4, true, 1> : mlp_tc_kernel<2, 2, true, 2>)
+                                  : (wide ? mlp_tc_kernel<5, 4, true, 1> : mlp_tc_kernel<5, 2, true, 2>))
+                   : (m.d_in == 2 ? (wide ? mlp_tc_kernel<2, 4, false, 1> : mlp_tc_kernel<2, 2, false, 1>)
+                                  : (wide ? mlp_tc_kernel<5, 4, false, 1> : mlp_tc_kernel<5, 2, false, 1>));
   if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
     return e;
   // CTAs per SM from the shared memory each one takes (dynamic + static + the
@@ -430,10 +450,10 @@ cudaError_t launch_mlp_eval_tc(const MlpDev& m, unsigned char* packed, const dou
   if (per_sm < 1) per_sm = 1;
   int ncols = 32;
   while (ncols < w) ncols <<= 1;
-  if (per_sm > 512 / ncols) per_sm = 512 / ncols;  // tensor memory: 512 columns per SM
+  if (per_sm > 512 / (ncols * tp)) per_sm = 512 / (ncols * tp);  // tensor memory: 512 columns per SM
   if (per_sm > 4) per_sm = 4;
-  const int64_t ntiles = (N + 127) / 128;
-  const int64_t grid = ntiles < (int64_t)nsm * per_sm ? ntiles : (int64_t)nsm * per_sm;
+  const int64_t ngroups = ((N + 127) / 128 + tp - 1) / tp;
+  const int64_t grid = ngroups < (int64_t)nsm * per_sm ? ngroups : (int64_t)nsm * per_sm;
   kern<<<(unsigned)grid, threads, smem, s>>>(a);
   return cudaGetLastError();
 }
